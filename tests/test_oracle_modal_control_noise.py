@@ -1,0 +1,201 @@
+"""Pins of the oracle's modal basis, reconstructor, integrator/loop and noise."""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from oracle import modal as md
+from oracle import control as ct
+from oracle import noise as nz
+from oracle import optics as op
+from oracle import atmosphere as at
+from synth import tiny_config
+from synth.configs import with_, LayerSpec
+from synth.inputs import screen_white_noise
+
+
+# ---------------------------------------------------------------- Zernike / basis
+
+def test_noll_ordering_matches_published_table():
+    for j, n, m in read_golden("noll_indices.txt"):
+        assert md.noll_to_nm(int(j)) == (int(n), int(m))
+
+
+def test_low_order_zernikes_closed_forms():
+    g = np.random.default_rng(0)
+    rho = g.random(200)
+    th = g.uniform(-math.pi, math.pi, 200)
+    x, y = rho * np.cos(th), rho * np.sin(th)
+    closed = {
+        2: 2 * x, 3: 2 * y, 4: math.sqrt(3) * (2 * rho ** 2 - 1),
+        5: math.sqrt(6) * 2 * x * y, 6: math.sqrt(6) * (x ** 2 - y ** 2),
+        7: math.sqrt(8) * (3 * rho ** 2 - 2) * y, 8: math.sqrt(8) * (3 * rho ** 2 - 2) * x,
+        9: math.sqrt(8) * (3 * x ** 2 * y - y ** 3), 10: math.sqrt(8) * (x ** 3 - 3 * x * y ** 2),
+        11: math.sqrt(5) * (6 * rho ** 4 - 6 * rho ** 2 + 1),
+    }
+    for j, z in closed.items():
+        assert np.max(np.abs(md.zernike(j, rho, th) - z)) < 1e-12, j
+
+
+def test_zernikes_unit_rms_on_disc():
+    """Noll normalisation: mean of Z_j^2 over the unit disc is 1 (fine polar grid)."""
+    nr, nt = 400, 256
+    r = (np.arange(nr) + 0.5) / nr
+    t = 2 * np.pi * np.arange(nt) / nt
+    R, T = np.meshgrid(r, t, indexing="ij")
+    w = R / (np.sum(R))
+    for j in (2, 4, 7, 11, 16, 22, 37):
+        z = md.zernike(j, R, T)
+        assert abs(np.sum(w * z * z) - 1) < 2e-3, j
+    assert abs(np.sum(w * md.zernike(4, R, T) * md.zernike(11, R, T))) < 1e-3
+
+
+def test_modal_basis_orthonormal_on_mask():
+    M = md.modal_basis(64, 0.1, 100)
+    n = M.shape[0]
+    assert n == 3196
+    assert np.max(np.abs(M.T @ M / n - np.eye(100))) < 1e-10
+    # column order kept: mode 0 is tip (linear in x up to the piston removal)
+    mask = op.pupil_mask(64, 0.1)
+    X, _ = op.pixel_coords(64)
+    xx = X[mask]
+    corr = np.dot(M[:, 0], xx - xx.mean()) / (np.linalg.norm(M[:, 0]) * np.linalg.norm(xx - xx.mean()))
+    assert corr > 0.999999
+
+
+# ---------------------------------------------------------------- IM / pinv
+
+def test_pinv_identity_and_truncation():
+    g = np.random.default_rng(1)
+    IM = g.standard_normal((60, 20))
+    R = md.pseudo_inverse(IM)
+    assert np.max(np.abs(R @ IM - np.eye(20))) < 1e-12
+    # a rank-deficient column is dropped: R IM is the projector on the kept space
+    IM2 = IM.copy()
+    IM2[:, 5] = IM2[:, 4]
+    R2 = md.pseudo_inverse(IM2)
+    P = R2 @ IM2
+    assert np.max(np.abs(P @ P - P)) < 1e-10 and abs(np.trace(P) - 19) < 1e-9
+
+
+def test_interaction_matrix_mode_in_mode_out():
+    cfg = tiny_config(Np=16, N=32, n_sub=4, K=8, n_modes=6, mod_radius=2.0)
+    mask = op.pupil_mask(cfg.Np, cfg.obs)
+    M = md.modal_basis(cfg.Np, cfg.obs, cfg.n_modes)
+    valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
+    _, sn = op.pwfs_measure(np.zeros((cfg.Np, cfg.Np)), cfg, valid)
+    meas = lambda opd: op.pwfs_measure(opd, cfg, valid, sn)[1]
+    IM = md.interaction_matrix(meas, M, mask, amp_nm=5.0)
+    R = md.pseudo_inverse(IM)
+    for m in range(cfg.n_modes):
+        c = np.zeros(cfg.n_modes)
+        c[m] = 2.0
+        est = R @ meas(md.basis_to_grid(M, c, mask))
+        assert np.max(np.abs(est - c)) < 0.02 * 2.0, (m, est)
+
+
+# ---------------------------------------------------------------- integrator / loop
+
+def test_integrator_closed_form_with_identity_sensor():
+    g = 0.5
+    a = np.array([3.0, -1.0])
+    c = np.zeros(2)
+    for t in range(1, 12):
+        c = ct.integrator_step(c, a - c, g)
+        assert np.allclose(a - c, (1 - g) ** t * a, rtol=0, atol=1e-14)
+
+
+def test_wfe_removes_piston():
+    mask = op.pupil_mask(32, 0.1)
+    assert ct.residual_wfe_nm(np.where(mask, 42.0, 0.0), mask) == 0.0
+    X, _ = op.pixel_coords(32)
+    v = (100 * X)[mask]
+    assert abs(ct.residual_wfe_nm(100 * X, mask) - v.std()) < 1e-12
+
+
+def _tiny_loop_setup(static=True):
+    cfg = tiny_config(Np=16, N=32, n_sub=4, K=8, n_modes=12, mod_radius=2.0, S=64,
+                      r0_m=0.5, layers=(LayerSpec(1.0, 0.0, 0.0 if static else 2.0),))
+    mask = op.pupil_mask(cfg.Np, cfg.obs)
+    M = md.modal_basis(cfg.Np, cfg.obs, cfg.n_modes)
+    valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
+    _, sn = op.pwfs_measure(np.zeros((cfg.Np, cfg.Np)), cfg, valid)
+    IM = md.interaction_matrix(lambda o: op.pwfs_measure(o, cfg, valid, sn)[1], M, mask, 5.0)
+    R = md.pseudo_inverse(IM)
+    return cfg, mask, M, valid, sn, R
+
+
+def test_zero_atmosphere_stays_exactly_zero():
+    cfg, mask, M, valid, sn, R = _tiny_loop_setup()
+    screens = np.zeros((1, cfg.S, cfg.S))
+    out = ct.closed_loop(cfg, screens, M, R, sn, valid, 6)
+    assert np.all(out["wfe"] == 0.0) and np.all(out["cmd"] == 0.0)
+
+
+def test_static_modal_aberration_decays_geometrically():
+    """A static aberration inside the DM space decays as (1-g)^t with delay 1."""
+    cfg, mask, M, valid, sn, R = _tiny_loop_setup()
+    c_true = np.zeros(cfg.n_modes)
+    c_true[[0, 2, 5]] = [3.0, -2.0, 1.5]
+    scr = np.zeros((1, cfg.S, cfg.S))
+    scr[0, :cfg.Np, :cfg.Np] = md.basis_to_grid(M, c_true, mask)
+    out = ct.closed_loop(cfg, scr, M, R, sn, valid, 8, record=True)
+    res = np.array([np.linalg.norm(c_true - c) for c in out["cmd"]])
+    expect = np.linalg.norm(c_true) * 0.5 ** np.arange(1, 9)
+    assert np.all(np.abs(res - expect) < 0.03 * np.linalg.norm(c_true) + 0.05 * expect)
+
+
+def test_delay_two_lags_one_more_step():
+    cfg, mask, M, valid, sn, R = _tiny_loop_setup()
+    c_true = np.zeros(cfg.n_modes)
+    c_true[1] = 2.0
+    scr = np.zeros((1, cfg.S, cfg.S))
+    scr[0, :cfg.Np, :cfg.Np] = md.basis_to_grid(M, c_true, mask)
+    o1 = ct.closed_loop(cfg, scr, M, R, sn, valid, 3, delay=1)
+    o2 = ct.closed_loop(cfg, scr, M, R, sn, valid, 3, delay=2)
+    assert o1["wfe"][1] < 0.7 * o1["wfe"][0]
+    assert abs(o2["wfe"][1] - o2["wfe"][0]) < 1e-9 and o2["wfe"][2] < 0.7 * o2["wfe"][0]
+
+
+def test_closed_loop_reduces_turbulence_wfe():
+    cfg, mask, M, valid, sn, R = _tiny_loop_setup(static=False)
+    screens = at.layer_screens_nm(cfg, [screen_white_noise(cfg.S, 77)])
+    out = ct.closed_loop(cfg, screens, M, R, sn, valid, 20)
+    assert out["wfe"][10:].mean() < 0.7 * out["wfe"][0]
+
+
+# ---------------------------------------------------------------- noise
+
+def test_philox_known_answer_vectors():
+    rows = read_golden("philox4x32_10_kat.txt")
+    assert len(rows) == 3
+    for r in rows:
+        ctr = [int(v, 16) for v in r[0:4]]
+        key = [int(v, 16) for v in r[4:6]]
+        out = [int(v, 16) for v in r[6:10]]
+        assert list(nz.philox4x32_10(ctr, key)) == out
+
+
+@pytest.mark.parametrize("lam", [0.7, 5.0, 30.0, 150.0])
+def test_poisson_moments(lam):
+    n = 20000
+    x = np.array([nz.poisson(lam, 11, p, 3) for p in range(n)], dtype=np.float64)
+    se_mean = math.sqrt(lam / n)
+    se_var = lam * math.sqrt(2.0 / n) * math.sqrt(1 + 1 / (2 * lam))
+    assert abs(x.mean() - lam) < 4.5 * se_mean
+    assert abs(x.var() - lam) < 4.5 * se_var
+    if lam < 1:
+        assert abs(np.mean(x == 0) - math.exp(-lam)) < 4.5 * math.sqrt(math.exp(-lam) / n)
+
+
+def test_gaussian_moments_and_frame_noise_shape():
+    n = 20000
+    g = np.array([nz.gaussian(3, p, 0) for p in range(n)])
+    assert abs(g.mean()) < 4.5 / math.sqrt(n) and abs(g.var() - 1) < 4.5 * math.sqrt(2 / n)
+    fr = np.full((6, 6), 2.0)
+    a = nz.apply_noise(fr, 1000.0, 36 * 2, 0.5, 9, 0)
+    b = nz.apply_noise(fr, 1000.0, 36 * 2, 0.5, 9, 0)
+    c = nz.apply_noise(fr, 1000.0, 36 * 2, 0.5, 9, 1)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    assert abs(a.mean() - 2.0 * 1000 / 72) < 5
