@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark: AO loop steps/s and PWFS frames/s on one GB300 (per rank).
+
+Workload: the LBT-class single-conjugate loop (8.4 m, 240 px pupil, 480^2 FFT
+grid, 3 layers, 30x30 pyramid, 24 modulation points, 400 modes, magnitude-10
+photon noise plus 0.5 e- read noise), FP32. A step is one simulated millisecond:
+atmosphere + DM residual -> modulated pyramid -> detector noise -> slopes ->
+reconstructor -> integrator, replayed as one CUDA graph.
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on
+the launching stream, the L2 flushed (256 MiB write) between steps outside the
+events; barrier + synchronize around the timed region, max over ranks.
+Multi-GPU (torchrun): independent replicas (different seeds), weak scaling.
+
+--impl reference times the FP64 CPU oracle on this machine's host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AO loop steps/s (LBT-class SCAO, 1 GB300)"
+UNIT = "steps/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--recon", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-budget-s", type=float, default=20.0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(cfg_idx: int, budget_s: float, max_steps: int) -> dict:
+    """Time the FP64 oracle's closed-loop step (as it stands) for a bounded number
+    of steps. Setup (screens, basis) is untimed; R is a seeded random matrix of
+    the right shape (the timing does not depend on its values)."""
+    import numpy as np
+    from oracle import atmosphere as at
+    from oracle import control as ct
+    from oracle import modal as md
+    from oracle import noise as nz
+    from oracle import optics as op
+    from synth import get_config
+    from synth.inputs import layer_seeds, random_matrix, screen_white_noise
+    cfg = get_config(cfg_idx)
+    screens = at.layer_screens_nm(cfg, [screen_white_noise(cfg.S, s) for s in layer_seeds(cfg.seed, len(cfg.layers))])
+    M = md.modal_basis(cfg.Np, cfg.obs, cfg.n_modes)
+    valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
+    R = random_matrix(cfg.n_modes, 2 * valid.size, 5, 1e-3)
+    sn = np.zeros(2 * valid.size)
+    noise = None
+    if cfg.magnitude is not None:
+        npup = int(op.pupil_mask(cfg.Np, cfg.obs).sum())
+        noise = lambda fr, t: nz.apply_noise(fr, cfg.photons_per_frame(), npup, cfg.read_noise_e, cfg.seed, t)
+    # one step to size the sample
+    t0 = time.perf_counter()
+    ct.closed_loop(cfg, screens, M, R, sn, valid, 1, noise=noise)
+    t1 = time.perf_counter() - t0
+    n = int(max(1, min(max_steps, budget_s // max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    ct.closed_loop(cfg, screens, M, R, sn, valid, n, noise=noise)
+    dt = time.perf_counter() - t0
+    return {"steps": n, "seconds": dt, "value": n / dt}
+
+
+def run_oracle_subprocess(cfg_idx: int, budget_s: float, max_steps: int) -> dict:
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    with tempfile.NamedTemporaryFile("r", suffix=".json") as f:
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(max_steps), "--config",
+               str(cfg_idx), "--oracle-budget-s", str(budget_s)]
+        subprocess.run(cmd, env=env, check=True, stdout=open(f.name, "w"))
+        return json.loads(open(f.name).read().strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.path = tempfile.mktemp(suffix=".csv")
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nme, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nme)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline
+
+def algorithmic_work(cfg, n_pix, n_valid, n_modes, n_s_rows, recon_bytes_per_el):
+    """Per-launch algorithmic flops / bytes of each kernel of the step."""
+    N, Np, K, L = cfg.N, cfg.Np, cfg.K, len(cfg.layers)
+    fft_pair = 2 * 5.0 * N * math.log2(N) + 6.0 * N           # FFT + mask + IFFT
+    return {
+        "residual_kernel": {"bound": "hbm", "bytes": 4.0 * n_modes * n_pix + 12.0 * n_pix
+                            + 4.0 * L * (Np + 1) ** 2 + 4.0 * n_modes},
+        "pyr_rows_kernel": {"bound": "alu", "flops": n_s_rows * Np * (fft_pair + 20.0 * Np)},
+        "pyr_cols_kernel": {"bound": "alu", "flops": K * N * (fft_pair + 6.0 * Np + 3.0 * N)},
+        "frame_slopes_kernel": {"bound": "latency", "bytes": 4.0 * (cfg.n_det ** 2) * 2 + 8.0 * 2 * n_valid},
+        "recon_kernel": {"bound": "hbm", "bytes": recon_bytes_per_el * n_modes * 2 * n_valid + 8.0 * n_modes},
+    }
+
+
+def main():
+    args = parse()
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.config, args.oracle_budget_s, args.oracle_sample)))
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from synth import get_config
+    cfg = get_config(args.config)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        r = run_oracle_subprocess(args.config, args.oracle_budget_s, max(1, args.steps))
+        line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": args.gpus,
+                "steps": r["steps"], "warmup": 1, "ms_per_step": 1000.0 / r["value"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": cfg.name, "note": "FP64 NumPy oracle, single thread"},
+                "cpu_baseline": {"kind": "oracle", "cores": 1, "value": r["value"], "unit": UNIT,
+                                 "sample": f"{r['steps']} closed-loop steps of {cfg.name} ({r['seconds']:.1f} s)"},
+                "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    from synth.configs import with_
+
+    cfg_r = with_(cfg, seed=cfg.seed + 1000 * rank)
+    prec = pas.PAS_BF16 if args.recon == "bf16" else pas.PAS_FP32
+    t_setup = time.perf_counter()
+    sysg = SCAOSystem(cfg_r, recon_precision=prec, wfe_history=max(4096, args.steps + args.warmup + 64))
+    t_setup = time.perf_counter() - t_setup
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    props = torch.cuda.get_device_properties(local_rank)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid else None) if rank == 0 else None
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also captures the graph) and a short soak for steady clocks
+    sysg.step(max(3, args.warmup))
+    t_end = time.perf_counter() + 1.5
+    while time.perf_counter() < t_end:
+        sysg.step(50)
+    barrier()
+
+    def timed(fn, n):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    barrier()
+    t_wall = time.perf_counter()
+    ms_total = timed(lambda: sysg.step(1), args.steps)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    steps_total = args.steps * world
+    value = steps_total / (ms_total / 1000.0)
+    ms_per_step = ms_total / args.steps
+
+    # PWFS frames/s: pas_pyr_measure alone on the loop's residual
+    opd = sysg.loop_opd.clone()
+    n_fr = max(20, min(args.steps, 500))
+    ms_fr = timed(lambda: sysg.measure(opd), n_fr)
+    frames_per_s = world * n_fr / (ms_fr / 1000.0)
+
+    # per-kernel durations (eager step with events around each kernel, L2 flushed)
+    prof = {}
+    n_prof = max(10, min(args.steps, 100))
+    for _ in range(n_prof):
+        flush.zero_()
+        for k, v in pas.pas_loop_profile(sysg.loop, sysg.ctx, 1).items():
+            prof[k] = prof.get(k, 0.0) + v / n_prof
+
+    # end to end through the public API, host buffers: per step the step counter,
+    # the WFE and the modal command come back to pinned host memory
+    n_e2e = max(20, min(args.steps, 300))
+    cmd_host = torch.empty(sysg.n_modes, dtype=torch.float32, pin_memory=True)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        sysg.step(1, stats=True)
+        cmd_host.copy_(sysg.loop_cmd, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    clocks = sampler.stop() if sampler else None
+
+    wfe = sysg.wfe_nm(min(sysg.wfe_history, args.warmup + args.steps))
+    n_s_rows = cfg.K // 2 + 1 if cfg.K % 2 == 0 else cfg.K
+    work = algorithmic_work(cfg, sysg.n_pix, sysg.n_valid, sysg.n_modes, n_s_rows,
+                            2.0 if prec == pas.PAS_BF16 else 4.0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roof = []
+    for k, ms in prof.items():
+        w = work.get(k)
+        if not w or ms <= 0:
+            continue
+        if w["bound"] == "alu":
+            ach = w["flops"] / (ms * 1e-3) / 1e12
+            roof.append({"kernel": k, "ms": ms, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS})
+        else:
+            ach = w["bytes"] / (ms * 1e-3) / 1e9
+            roof.append({"kernel": k, "ms": ms, "bound": "hbm" if w["bound"] == "hbm" else w["bound"],
+                         "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak})
+    dom = max(roof, key=lambda r: r["ms"]) if roof else None
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        traffic = tr.get(cfg.name, {}).get(dom["kernel"]) if dom else None
+    except (OSError, ValueError):
+        pass
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            r = run_oracle_subprocess(args.config, args.oracle_budget_s, 50)
+            cpu = {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{r['steps']} closed-loop steps of {cfg.name}, FP64 NumPy oracle, "
+                             f"1 thread, {r['seconds']:.1f} s (setup untimed; random R)"}
+        except Exception as e:  # the baseline is reported, never fatal
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{cfg.name}: D={cfg.D} m, pupil {cfg.Np}^2 px, FFT {cfg.N}^2, "
+                               f"{len(cfg.layers)} layers, {cfg.n_sub}x{cfg.n_sub} subaps, K={cfg.K}, "
+                               f"R={cfg.mod_radius} l/D, {sysg.n_modes} modes, mag {cfg.magnitude} + "
+                               f"{cfg.read_noise_e} e- RON",
+                   "l2": "flushed (256 MiB write) between timed steps", "recon": args.recon,
+                   "parallelism": f"replicas x{world}", "graph": "whole step, CUDA graph"},
+        "pwfs_frames_per_s": frames_per_s,
+        "roofline": None if dom is None else {"bound": dom["bound"], "achieved": dom["achieved"],
+                                               "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"],
+                                               "traffic": traffic, "kernel": dom["kernel"],
+                                               "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+                                                               if dom["bound"] == "alu"
+                                                               else "MEASURED_PEAKS.json hbm_gbs (of measured)")},
+        "roofline_by_kernel": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 4 * sysg.n_modes + 16},
+        "gpu_launches": 6 * args.steps,
+        "clocks": clocks,
+        "residual_wfe_nm_mean": float(np.mean(wfe[len(wfe) // 5:])) if len(wfe) else None,
+        "setup_s": t_setup, "wall_timed_s": t_wall,
+    }
+    print(json.dumps(line))
+    sysg.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,260 @@
+/*
+ * pas.h — C ABI of the GB300 (sm_103a) modulated-pyramid single-conjugate AO loop.
+ *
+ * The calls follow the processing-object chain of the PASSATA paper (Agapito,
+ * Puglisi, Esposito, SPIE 2016): atmosphere and propagation, modulated pyramid,
+ * CCD, slope computer, modal reconstructor, integrator control and modal DM
+ * (Table 1 parameter file, Table 2 main file, Sec. Structure), run once per
+ * simulated step by a loop control object (Sec. Build and run a simulation loop).
+ * The paper's GPU areas (Sec. GPU acceleration) are the atmosphere propagation,
+ * the pyramid propagation and the influence-function multiplication; here every
+ * per-step operation of the loop runs in this library's own CUDA kernels.
+ *
+ * Conventions for every call:
+ *   - Device pointers ("d_" prefix) are caller-owned CUDA device memory of the
+ *     current device; the library never frees them. Host pointers ("h_" prefix
+ *     or documented as host) are read or written synchronously inside the call.
+ *   - Arrays are C row-major. Axis 0 of a 2-D map is x (rows), axis 1 is y.
+ *   - OPD is in nm, float32. Modal coefficients are nm RMS over the pupil.
+ *   - Objects own their internal device buffers, allocated only by *_create and
+ *     freed by *_destroy. The per-step calls (advance, measure, apply, update,
+ *     loop_step) allocate nothing.
+ *   - Every call is asynchronous on the context's stream unless documented
+ *     otherwise. Argument errors are returned synchronously as PAS_EINVAL; CUDA
+ *     launch errors as PAS_ECUDA; asynchronous device faults surface at the next
+ *     call that synchronises. pas_last_error() gives a message per context;
+ *     pas_global_error() the message of the last failed create on this thread.
+ *   - A NULL handle or pointer where one is required returns PAS_EINVAL.
+ */
+#ifndef PAS_H
+#define PAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PAS_OK = 0,
+    PAS_EINVAL = 1,   /* invalid argument or unsupported size */
+    PAS_ENOMEM = 2,   /* device allocation failed (no host fallback) */
+    PAS_ECUDA = 3,    /* CUDA runtime error */
+    PAS_ETIMEOUT = 4, /* a bounded device wait gave up */
+    PAS_ESTATE = 5    /* call not valid in the object's current state */
+} pas_status;
+
+typedef enum { PAS_FP32 = 0, PAS_BF16 = 1 } pas_precision;
+
+typedef struct pas_ctx_s*   pas_ctx_t;
+typedef struct pas_atmo_s*  pas_atmo_t;
+typedef struct pas_pyr_s*   pas_pyr_t;
+typedef struct pas_recon_s* pas_recon_t;
+typedef struct pas_dm_s*    pas_dm_t;
+typedef struct pas_loop_s*  pas_loop_t;
+
+/* ------------------------------------------------------------------ context */
+
+/* Library version (major*10000 + minor*100 + patch). Host only, no GPU needed. */
+int pas_version(void);
+
+/* Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t, borrowed, may be NULL for the legacy default stream).
+ * The context owns nothing else than an error slot and a private stream used
+ * only to capture CUDA graphs. */
+pas_status pas_ctx_create(void* cuda_stream, pas_ctx_t* out);
+void pas_ctx_destroy(pas_ctx_t ctx);
+/* Replace the borrowed stream used by later calls. */
+pas_status pas_ctx_set_stream(pas_ctx_t ctx, void* cuda_stream);
+/* Wait for all work queued on the context stream; returns PAS_ECUDA on a
+ * device fault. */
+pas_status pas_ctx_synchronize(pas_ctx_t ctx);
+const char* pas_last_error(pas_ctx_t ctx);
+const char* pas_global_error(void);
+/* Host-side fault injection for tests: the n-th following device allocation
+ * (n >= 1) made by any *_create fails with PAS_ENOMEM; n = 0 disables. */
+void pas_debug_fail_alloc_after(int n);
+
+/* ------------------------------------------------------- pupil geometry (host)
+ * Pupil stop (Table 1 pupil_stop, DM.obsratio) and the pupil index data of the
+ * slope computer (Table 1 slopec.pupdata_tag; Table 3 calibration). Host-only,
+ * integer-exact; no GPU needed.
+ *   pixel (i,j) of an Np x Np grid is in the pupil iff
+ *     d2 = (2i-Np+1)^2 + (2j-Np+1)^2 <= Np^2  and  d2 >= T,
+ *   T = ceil((obs*Np)^2 - 1e-9)  (central obstruction ratio obs).
+ *   sub-aperture (r,c) of an n_sub x n_sub grid (b = Np/n_sub pixels a side, Np a
+ *   multiple of n_sub) is valid iff 2 * (pupil pixels in its block) >= b^2. */
+
+/* Writes mask[Np*Np] (1 inside, 0 outside) if mask != NULL; *n_pix = count. */
+pas_status pas_pupil_mask(int Np, double obs, uint8_t* mask, int32_t* n_pix);
+/* Flat indices i*Np+j of the pupil pixels in row-major order into idx[cap]. */
+pas_status pas_pupil_pixels(int Np, double obs, int32_t* idx, int32_t cap, int32_t* n_pix);
+/* Flat indices r*n_sub+c of the valid sub-apertures in row-major order. */
+pas_status pas_valid_subaps(int Np, double obs, int n_sub, int32_t* valid, int32_t cap,
+                            int32_t* n_valid);
+
+/* -------------------------------------------------------------- atmosphere
+ * Layered phase screens moved by the wind and summed on the pupil along the
+ * on-axis source direction (Table 1 atmo / wind_speed / wind_direction; Table 2
+ * get_atmo_container, get_atmo_propagation; Sec. GPU acceleration, "wavefront
+ * propagation through phase screens").
+ * At step t, pupil pixel (i,j) samples layer l at (i - t*vx[l], j - t*vy[l])
+ * (screen pixels, periodic, bilinear). The displacement t*v is one FP64 product
+ * from the integer step; floor gives the integer shift and the remainder,
+ * rounded to float32, the interpolation weights. */
+typedef struct {
+    int32_t n_layers;   /* L >= 1 */
+    int32_t S;          /* screen side (pixels), >= Np + 2 */
+    int32_t Np;         /* pupil side (pixels) */
+    const double* vx;   /* host [L]: pixels per step along axis 0 */
+    const double* vy;   /* host [L]: pixels per step along axis 1 */
+} pas_atmo_params;
+
+/* d_screens: device float32 [L][S][S] OPD in nm (Cn2 weights already applied),
+ * caller-owned, must outlive the object. */
+pas_status pas_atmo_create(pas_ctx_t ctx, const pas_atmo_params* p, const float* d_screens,
+                           pas_atmo_t* out);
+/* d_opd: device float32 [Np][Np], the summed OPD of all layers at `step`
+ * (every pixel of the square, no pupil mask). */
+pas_status pas_atmo_advance(pas_atmo_t atmo, int64_t step, float* d_opd);
+void pas_atmo_destroy(pas_atmo_t atmo);
+
+/* ------------------------------------------------------ modulated pyramid
+ * Modulated four-face pyramid wavefront sensor, CCD binning and slope computer
+ * (Table 1 pyramid, detector, slopec; Sec. GPU acceleration, "pyramid
+ * propagation from wavefront to detector plane").
+ * For each modulation point k (theta_k = 2 pi k / K from axis 0, radius
+ * mod_radius lambda/D) the pupil field A exp(i(2 pi opd/lambda + psi_k)) is
+ * centred in an N x N grid, taken to the focal plane by the centred unitary DFT,
+ * multiplied by exp(i 2 pi delta (|u~|+|v~|)/N) and brought back; the intensity
+ * averaged over k is summed into b x b detector pixels, b = N/(2 n_sub).
+ * Slopes over the valid sub-apertures j (detector quadrants q_ab, a = row half,
+ * b = column half, sub-aperture (r,c) at pixel (a*n_sub+r, b*n_sub+c)):
+ *   Sx = (q10+q11-q00-q01)/F,  Sy = (q01+q11-q00-q10)/F,
+ *   F = mean over valid j of (q00+q01+q10+q11); output [Sx(0..nv-1), Sy(..)] - sn.
+ * Requirements: N = 2*Np, delta = N/4, N a multiple of 2*n_sub, N in the
+ * supported set (see pas_pyr_supported), K even or odd >= 1. */
+typedef struct {
+    int32_t Np;            /* pupil pixels across */
+    int32_t N;             /* FFT grid side */
+    int32_t K;             /* modulation points */
+    int32_t n_sub;         /* sub-apertures across */
+    double mod_radius;     /* lambda/D */
+    double wavelength_nm;  /* sensing wavelength */
+    double obs;            /* central obstruction ratio */
+    int32_t local_norm;    /* 0: global flux normalisation, 1: per sub-aperture */
+} pas_pyr_params;
+
+/* 1 if the FFT size N has compiled kernels, else 0. Host only. */
+int pas_pyr_supported(int N);
+/* h_valid: host int32 [n_valid] flat sub-aperture indices (ascending), or NULL
+ * to use the geometric rule above. The object starts with a zero slope
+ * reference and noise off. */
+pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* p, const int32_t* h_valid,
+                          int32_t n_valid, pas_pyr_t* out);
+int32_t pas_pyr_n_valid(pas_pyr_t pyr);
+/* Copy the valid sub-aperture list to host memory (synchronous). */
+pas_status pas_pyr_get_valid(pas_pyr_t pyr, int32_t* h_valid, int32_t cap);
+/* d_sn: device float32 [2*n_valid] slope reference (copied), NULL = zero. */
+pas_status pas_pyr_set_reference(pas_pyr_t pyr, const float* d_sn);
+/* Detector noise (Table 1 detector: photon_noise, readout_noise, readout_level):
+ * photons_per_frame <= 0 disables photon noise and keeps the frame in intensity
+ * units. With photons > 0 the frame is in photo-electrons:
+ *   pix_p = Poisson(photons * I_p / n_pupil_pixels) + read_noise_e * N(0,1),
+ * drawn from Philox-4x32-10 (key = seed, counter = (p, frame, block)).
+ * `frame_index` sets the counter of the next frame; each measure increments it. */
+pas_status pas_pyr_set_noise(pas_pyr_t pyr, double photons_per_frame, double read_noise_e,
+                             uint64_t seed, int64_t frame_index);
+/* d_opd: device float32 [Np][Np] residual OPD (values outside the pupil are
+ * ignored). d_frame: device float32 [2n_sub][2n_sub] out (may be NULL).
+ * d_slopes: device float32 [2*n_valid] out (may be NULL). */
+pas_status pas_pyr_measure(pas_pyr_t pyr, const float* d_opd, float* d_frame, float* d_slopes);
+/* Stand-alone detector noise on a frame (same rule as above; frame counter
+ * given explicitly; in-place allowed). n = number of pixels. */
+pas_status pas_ccd_noise(pas_ctx_t ctx, const float* d_in, float* d_out, int32_t n,
+                         double photons_per_frame, int32_t n_pupil_pixels,
+                         double read_noise_e, uint64_t seed, int64_t frame_index);
+void pas_pyr_destroy(pas_pyr_t pyr);
+
+/* ------------------------------------------------- modal reconstructor
+ * Modal reconstructor (Table 1 modalrec.recmat_tag): dmodes = R * slopes.
+ * h_R: host float32 [n_modes][n_slopes] row-major, copied. PAS_BF16 stores R in
+ * bfloat16 with one float32 scale per row (row max |R|) and accumulates in
+ * float32. */
+pas_status pas_recon_create(pas_ctx_t ctx, const float* h_R, int32_t n_modes, int32_t n_slopes,
+                            pas_precision prec, pas_recon_t* out);
+/* d_slopes: device float32 [n_slopes]; d_dmodes: device float32 [n_modes] out. */
+pas_status pas_recon_apply(pas_recon_t rec, const float* d_slopes, float* d_dmodes);
+void pas_recon_destroy(pas_recon_t rec);
+
+/* ------------------------------------------------------------- modal DM
+ * Integrator control and modal DM (Table 1 control: type 'INT', int_gain;
+ * Table 1 DM; Sec. GPU acceleration, "influence function multiplication").
+ * h_M: host float32 [n_pix][n_modes] modal basis over the pupil pixels listed
+ * (row-major order) by pas_pupil_pixels(Np, obs); copied (stored mode-major). */
+pas_status pas_dm_create(pas_ctx_t ctx, const float* h_M, int32_t n_pix, int32_t n_modes,
+                         int32_t Np, double obs, pas_precision prec, pas_dm_t* out);
+/* Integrator then DM shape:
+ *   if d_dmodes != NULL:  cmd[m] += gain[m] * dmodes[m]   (d_gain NULL: gain 1)
+ *   if d_opd_dm != NULL:  opd_dm = M * cmd on the pupil pixels, 0 elsewhere
+ * d_cmd: device float32 [n_modes] in/out; d_opd_dm: device float32 [Np][Np]. */
+pas_status pas_dm_update(pas_dm_t dm, const float* d_dmodes, const float* d_gain, float* d_cmd,
+                         float* d_opd_dm);
+/* Residual seen by the sensor: opd_res = mask * (opd_atm - M * cmd).
+ * d_opd_atm, d_opd_res: device float32 [Np][Np] (may alias); d_cmd [n_modes]. */
+pas_status pas_dm_residual(pas_dm_t dm, const float* d_opd_atm, const float* d_cmd,
+                           float* d_opd_res);
+void pas_dm_destroy(pas_dm_t dm);
+
+/* ------------------------------------------------------------------ loop
+ * Loop control (Sec. Structure; Table 2 loop.add / loop.run): one step runs
+ *   atmosphere -> residual (DM command of step t-delay) -> pyramid -> CCD ->
+ *   slopes -> reconstructor -> integrator
+ * on the context stream. The first call captures one step as a CUDA graph (on
+ * the context's private stream) and later calls replay it; call it before
+ * capturing anything else on the same stream. The integrator state, the
+ * step counter and the per-step residual WFE live on the device. */
+typedef struct {
+    int64_t step;        /* steps completed */
+    double wfe_nm;       /* residual WFE (piston removed) of the last step */
+} pas_loop_stats;
+
+/* d_gain: device float32 [n_modes] per-mode integrator gain (copied).
+ * delay >= 1: the measurement at step t sees the command of step t - delay.
+ * wfe_history: number of per-step WFE values kept (ring buffer, >= 1). */
+pas_status pas_loop_create(pas_ctx_t ctx, pas_atmo_t atmo, pas_pyr_t pyr, pas_recon_t rec,
+                           pas_dm_t dm, const float* d_gain, int32_t delay,
+                           int32_t wfe_history, pas_loop_t* out);
+/* Run n_steps >= 0 steps. If h_stats != NULL the call synchronises and fills it. */
+pas_status pas_loop_step(pas_loop_t loop, int32_t n_steps, pas_loop_stats* h_stats);
+/* Same step launched kernel by kernel without the graph (for comparison). */
+pas_status pas_loop_step_eager(pas_loop_t loop, int32_t n_steps);
+/* Device views of the loop's buffers (owned by the loop; valid until destroy):
+ * opd_res [Np][Np], frame [2n_sub]^2, slopes [2nv], dmodes [n_modes],
+ * cmd [n_modes] (command of the last completed step), wfe [wfe_history]
+ * (float64, entry t mod history = WFE of step t). Any pointer may be NULL. */
+pas_status pas_loop_buffers(pas_loop_t loop, float** opd_res, float** frame, float** slopes,
+                            float** dmodes, float** cmd, double** wfe);
+/* Checkpoint / resume: the state is the step counter, the integrator ring
+ * (delay x n_modes float32) and the noise frame counter; h_cmd_ring may be NULL
+ * on get to query only the step. Synchronous. */
+pas_status pas_loop_get_state(pas_loop_t loop, int64_t* step, float* h_cmd_ring);
+pas_status pas_loop_set_state(pas_loop_t loop, int64_t step, const float* h_cmd_ring);
+void pas_loop_destroy(pas_loop_t loop);
+
+/* Profiling: run n_steps >= 1 steps kernel by kernel with CUDA events around each
+ * launch on the context stream, synchronise, and write the mean duration in ms of
+ * each kernel of the step into h_ms[0 .. *n_kernels-1] (cap >= PAS_LOOP_KERNELS).
+ * The step's kernels, in order: residual (atmosphere + DM), pyramid rows pass,
+ * pyramid columns pass, frame + slopes, reconstructor + integrator, step counter. */
+#define PAS_LOOP_KERNELS 6
+pas_status pas_loop_profile(pas_loop_t loop, int32_t n_steps, float* h_ms, int32_t cap,
+                            int32_t* n_kernels);
+/* Name of kernel `idx` of pas_loop_profile (static string), NULL if out of range. */
+const char* pas_loop_kernel_name(int32_t idx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAS_H */

@@ -1,0 +1,110 @@
+"""One-off setup of the loop (not timed per step), host FP64.
+
+The paper's example needs three calibrations before a run (Sec. Example): the
+pupil sub-aperture indices, the slope reference vector and the reconstruction
+matrix; the DM (Table 1 ``DM``: type 'zernike', nmodes, obsratio) and the
+atmosphere (Table 1 ``atmo``/``seeing``) are built from parameters. This module:
+
+  * von Karman phase screens by the FFT method (white noise is an input);
+  * the Zernike modal basis in Noll order, orthonormalised on the pupil pixels;
+  * the slope reference (a flat wavefront measured by the GPU pyramid);
+  * the push-pull interaction matrix (GPU pyramid) and its FP64 pseudo-inverse.
+
+Per-step work never runs here: the loop runs in libpas.so's kernels.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+R0_REF_NM = 500.0
+
+
+def _psd_scale() -> float:
+    g = math.gamma
+    return (g(11.0 / 6.0) ** 2 / (2.0 * math.pi ** (11.0 / 3.0))) * (24.0 * g(6.0 / 5.0) / 5.0) ** (5.0 / 6.0)
+
+
+def fft_phase_screen_nm(S: int, pitch_m: float, r0_m: float, L0_m: float, noise: np.ndarray) -> np.ndarray:
+    """Periodic S x S von Karman OPD screen [nm], FP64: Re of the inverse DFT of
+    noise * sqrt(PSD) * df over the FFT frequency lattice, zero mean."""
+    df = 1.0 / (S * pitch_m)
+    k = np.fft.fftfreq(S) * S * df                       # cycles / m on the FFT lattice
+    f2 = np.add.outer(k * k, k * k)
+    f2[0, 0] = 1.0
+    outer = 0.0 if math.isinf(L0_m) else (1.0 / L0_m) ** 2
+    amp = np.sqrt(_psd_scale() * r0_m ** (-5.0 / 3.0) * (f2 + outer) ** (-11.0 / 6.0)) * df
+    amp[0, 0] = 0.0
+    field = np.fft.ifft2(noise * amp) * (S * S)
+    return field.real * (R0_REF_NM / (2.0 * math.pi))
+
+
+def layer_screens(cfg, noises) -> np.ndarray:
+    """float32 (L, S, S) OPD screens [nm] with the Cn2 fractions applied."""
+    out = np.empty((len(cfg.layers), cfg.S, cfg.S), dtype=np.float32)
+    for l, (ly, w) in enumerate(zip(cfg.layers, noises)):
+        out[l] = fft_phase_screen_nm(cfg.S, cfg.dx, cfg.r0_m * ly.fraction ** -0.6, cfg.L0_m, w)
+    return out
+
+
+# ----------------------------------------------------------------- modal basis
+
+def noll_nm(j: int):
+    """Noll index -> (n, m) by enumerating each radial order's azimuthal orders
+    (|m| ascending, m != 0 twice); even j carries cos (m > 0), odd j sin."""
+    count, n = 0, 0
+    while True:
+        for mabs in range(n % 2, n + 1, 2):
+            for _ in range(1 if mabs == 0 else 2):
+                count += 1
+                if count == j:
+                    return n, (0 if mabs == 0 else (mabs if j % 2 == 0 else -mabs))
+        n += 1
+
+
+def radial_jacobi(n: int, m: int, rho: np.ndarray) -> np.ndarray:
+    """R_n^m(rho) = (-1)^((n-m)/2) rho^m P_((n-m)/2)^(m,0)(1 - 2 rho^2)."""
+    from scipy.special import eval_jacobi
+    k = (n - m) // 2
+    return (-1) ** k * rho ** m * eval_jacobi(k, m, 0, 1.0 - 2.0 * rho * rho)
+
+
+def zernike_basis(Np: int, pupil_flat_idx: np.ndarray, n_modes: int) -> np.ndarray:
+    """(n_pix, n_modes) float64, Noll j = 2..n_modes+1, orthonormalised on the
+    pupil pixels (modified Gram-Schmidt twice, column order kept) and scaled to
+    1 nm RMS per unit coefficient."""
+    i, jj = np.divmod(pupil_flat_idx.astype(np.int64), Np)
+    x = (i - (Np - 1) / 2.0) / (Np / 2.0)
+    y = (jj - (Np - 1) / 2.0) / (Np / 2.0)
+    rho = np.hypot(x, y)
+    th = np.arctan2(y, x)
+    Z = np.empty((rho.size, n_modes))
+    for c, j in enumerate(range(2, n_modes + 2)):
+        n, m = noll_nm(j)
+        r = radial_jacobi(n, abs(m), rho)
+        if m == 0:
+            Z[:, c] = math.sqrt(n + 1) * r
+        elif m > 0:
+            Z[:, c] = math.sqrt(2 * (n + 1)) * r * np.cos(m * th)
+        else:
+            Z[:, c] = math.sqrt(2 * (n + 1)) * r * np.sin(-m * th)
+    npix = Z.shape[0]
+    Q = Z.copy()
+    for _ in range(2):
+        for c in range(n_modes):
+            v = Q[:, c]
+            if c:
+                v -= Q[:, :c] @ (Q[:, :c].T @ v)
+            Q[:, c] = v / np.linalg.norm(v)
+    # sign convention: positive overlap with the raw polynomial
+    sgn = np.sign(np.einsum("pc,pc->c", Q, Z))
+    sgn[sgn == 0] = 1.0
+    return Q * sgn * math.sqrt(npix)
+
+
+def pseudo_inverse(IM: np.ndarray, rcond: float = 1e-3) -> np.ndarray:
+    """FP64 SVD pseudo-inverse, singular values below rcond * max dropped."""
+    U, s, Vt = np.linalg.svd(np.asarray(IM, dtype=np.float64), full_matrices=False)
+    keep = s >= rcond * s.max()
+    return (Vt[keep].T * (1.0 / s[keep])) @ U[:, keep].T

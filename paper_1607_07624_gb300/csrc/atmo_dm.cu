@@ -1,0 +1,283 @@
+// Atmosphere propagation (wind-shifted layers summed on the pupil) and the modal DM
+// (influence-function multiplication) with the residual seen by the sensor
+// (Table 1 atmo / wind_speed / wind_direction / DM; Table 2 get_atmo_propagation,
+// add_layer_to_layer_list(dm.out_layer); Sec. GPU acceleration, "wavefront
+// propagation through phase screens" and "influence function multiplication").
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "atmo_dm.cuh"
+#include "internal.h"
+
+namespace pas {
+
+// Per-layer integer shift and float32 bilinear weights at `step`:
+// sample position of pupil pixel i is i - step*v = i + n + f, n = floor(-step*v).
+__device__ inline void layer_shift(double v, long long step, int S, int* n_mod, float* f) {
+  const double d = -(double)step * v;
+  const double n = floor(d);
+  *f = (float)(d - n);
+  long long ni = (long long)n % S;
+  if (ni < 0) ni += S;
+  *n_mod = (int)ni;
+}
+
+__device__ inline float atmo_sample(const AtmoArgs& a, const int* six, const int* siy,
+                                    const float* sfx, const float* sfy, int i, int j) {
+  float acc = 0.f;
+  const int S = a.S;
+  for (int l = 0; l < a.L; ++l) {
+    int i0 = i + six[l];
+    if (i0 >= S) i0 -= S;
+    int j0 = j + siy[l];
+    if (j0 >= S) j0 -= S;
+    const int i1 = (i0 + 1 == S) ? 0 : i0 + 1;
+    const int j1 = (j0 + 1 == S) ? 0 : j0 + 1;
+    const float* sc = a.screens + (size_t)l * S * S;
+    const float fx = sfx[l], fy = sfy[l];
+    const float v00 = __ldg(sc + (size_t)i0 * S + j0), v10 = __ldg(sc + (size_t)i1 * S + j0);
+    const float v01 = __ldg(sc + (size_t)i0 * S + j1), v11 = __ldg(sc + (size_t)i1 * S + j1);
+    acc += (1.f - fx) * (1.f - fy) * v00 + fx * (1.f - fy) * v10 + (1.f - fx) * fy * v01 + fx * fy * v11;
+  }
+  return acc;
+}
+
+__global__ void atmo_kernel(AtmoArgs a, const long long* d_step, long long h_step, float* out) {
+  __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
+  __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
+  const long long step = d_step ? *d_step : h_step;
+  if (threadIdx.x < a.L) {
+    layer_shift(a.vx[threadIdx.x], step, a.S, &six[threadIdx.x], &sfx[threadIdx.x]);
+    layer_shift(a.vy[threadIdx.x], step, a.S, &siy[threadIdx.x], &sfy[threadIdx.x]);
+  }
+  __syncthreads();
+  const int n = a.Np * a.Np;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int i = p / a.Np, j = p - i * a.Np;
+    out[p] = atmo_sample(a, six, siy, sfx, sfy, i, j);
+  }
+}
+
+// Residual over the pupil pixel list: out[pix] = atm - dm_sign * (M c).
+// CTA: 256 threads = 8 warps over one tile of 128 pixels; each lane owns 4
+// consecutive pixels (one 16-byte load per mode) and warp w the modes m = w mod 8.
+__global__ void __launch_bounds__(256) residual_kernel(ResArgs a) {
+  extern __shared__ float c_s[];                  // [n_m]
+  __shared__ float red[8][128];
+  __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
+  __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
+  __shared__ double wred[2][8];
+  const long long step = a.d_step ? *a.d_step : a.h_step;
+  const float* cmd = a.cmd;
+  if (a.cmd_ring) cmd = a.cmd_ring + (size_t)(step % a.delay) * a.n_m;
+  for (int m = threadIdx.x; m < a.n_m; m += blockDim.x) c_s[m] = cmd[m];
+  if (threadIdx.x < a.atmo.L) {
+    layer_shift(a.atmo.vx[threadIdx.x], step, a.atmo.S, &six[threadIdx.x], &sfx[threadIdx.x]);
+    layer_shift(a.atmo.vy[threadIdx.x], step, a.atmo.S, &siy[threadIdx.x], &sfy[threadIdx.x]);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int base = blockIdx.x * 128;
+  if (a.MT && a.n_m > 0) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4* col = reinterpret_cast<const float4*>(a.MT + base) + lane;
+    const size_t stride4 = (size_t)a.n_pad / 4;
+#pragma unroll 4
+    for (int m = warp; m < a.n_m; m += 8) {
+      const float4 v = __ldg(col + (size_t)m * stride4);
+      const float c = c_s[m];
+      acc.x = fmaf(c, v.x, acc.x);
+      acc.y = fmaf(c, v.y, acc.y);
+      acc.z = fmaf(c, v.z, acc.z);
+      acc.w = fmaf(c, v.w, acc.w);
+    }
+    red[warp][4 * lane + 0] = acc.x;
+    red[warp][4 * lane + 1] = acc.y;
+    red[warp][4 * lane + 2] = acc.z;
+    red[warp][4 * lane + 3] = acc.w;
+  }
+  __syncthreads();
+  double s1 = 0.0, s2 = 0.0;
+  if (threadIdx.x < 128) {
+    const int p = base + threadIdx.x;
+    if (p < a.n_pix) {
+      float dm = 0.f;
+      if (a.MT && a.n_m > 0) {
+#pragma unroll
+        for (int w = 0; w < 8; ++w) dm += red[w][threadIdx.x];
+      }
+      const int flat = a.pix[p];
+      const int i = flat / a.Np, j = flat - i * a.Np;
+      float atm = 0.f;
+      if (a.atmo.L > 0) atm = atmo_sample(a.atmo, six, siy, sfx, sfy, i, j);
+      else if (a.opd_atm) atm = a.opd_atm[flat];
+      const float r = atm - a.dm_sign * dm;
+      a.out[flat] = r;
+      s1 = r;
+      s2 = (double)r * r;
+    }
+  }
+  if (a.wfe_part) {
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_down_sync(0xffffffffu, s1, o);
+      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+      wred[0][warp] = s1;
+      wred[1][warp] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t1 = 0.0, t2 = 0.0;
+      for (int w = 0; w < 8; ++w) {
+        t1 += wred[0][w];
+        t2 += wred[1][w];
+      }
+      a.wfe_part[blockIdx.x] = make_double2(t1, t2);
+    }
+  }
+}
+
+// Zero the pixels of an Np x Np map outside the pupil.
+__global__ void zero_outside_kernel(float* out, int Np, long long T) {
+  const int n = Np * Np;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int i = p / Np, j = p - i * Np;
+    const long long ai = 2LL * i - Np + 1, bj = 2LL * j - Np + 1;
+    const long long d2 = ai * ai + bj * bj;
+    if (!(d2 <= (long long)Np * Np && d2 >= T)) out[p] = 0.f;
+  }
+}
+
+__global__ void integrate_kernel(float* cmd, const float* dmodes, const float* gain, int n) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < n) cmd[m] += (gain ? gain[m] : 1.0f) * dmodes[m];
+}
+
+pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st) {
+  const int tiles = (a.n_pix + 127) / 128;
+  if (tiles == 0) return PAS_OK;
+  const size_t smem = sizeof(float) * (size_t)std::max(a.n_m, 1);
+  residual_kernel<<<tiles, 256, smem, st>>>(a);
+  return check_launch(ctx, "residual kernel launch");
+}
+
+}  // namespace pas
+
+// ------------------------------------------------------------------ objects
+
+extern "C" {
+
+pas_status pas_atmo_create(pas_ctx_t ctx, const pas_atmo_params* p, const float* d_screens,
+                           pas_atmo_t* out) {
+  if (!ctx || !p || !d_screens || !out) return pas::set_global_error(PAS_EINVAL, "pas_atmo_create: NULL argument");
+  *out = nullptr;
+  PAS_CHECK_ARG(ctx, p->n_layers >= 1 && p->n_layers <= PAS_MAX_LAYERS, "pas_atmo_create: 1..16 layers");
+  PAS_CHECK_ARG(ctx, p->Np > 0 && p->S >= p->Np + 2, "pas_atmo_create: need S >= Np + 2");
+  PAS_CHECK_ARG(ctx, p->vx && p->vy, "pas_atmo_create: NULL velocity arrays");
+  pas_atmo_t a = new pas_atmo_s();
+  a->ctx = ctx;
+  a->args.screens = d_screens;
+  a->args.L = p->n_layers;
+  a->args.S = p->S;
+  a->args.Np = p->Np;
+  for (int l = 0; l < PAS_MAX_LAYERS; ++l) {
+    a->args.vx[l] = l < p->n_layers ? p->vx[l] : 0.0;
+    a->args.vy[l] = l < p->n_layers ? p->vy[l] : 0.0;
+  }
+  *out = a;
+  return PAS_OK;
+}
+
+pas_status pas_atmo_advance(pas_atmo_t a, int64_t step, float* d_opd) {
+  if (!a || !d_opd) return pas::set_global_error(PAS_EINVAL, "pas_atmo_advance: NULL argument");
+  PAS_CHECK_ARG(a->ctx, step >= 0, "pas_atmo_advance: negative step");
+  const int n = a->args.Np * a->args.Np;
+  const int blocks = std::min((n + 255) / 256, 4 * std::max(a->ctx->sm_count, 1));
+  pas::atmo_kernel<<<blocks, 256, 0, a->ctx->stream>>>(a->args, nullptr, step, d_opd);
+  return pas::check_launch(a->ctx, "pas_atmo_advance launch");
+}
+
+void pas_atmo_destroy(pas_atmo_t a) { delete a; }
+
+void pas_dm_destroy(pas_dm_t d) {
+  if (!d) return;
+  pas::dev_free(d->d_MT);
+  pas::dev_free(d->d_pix);
+  delete d;
+}
+
+pas_status pas_dm_create(pas_ctx_t ctx, const float* h_M, int32_t n_pix, int32_t n_modes, int32_t Np,
+                         double obs, pas_precision prec, pas_dm_t* out) {
+  if (!ctx || !h_M || !out) return pas::set_global_error(PAS_EINVAL, "pas_dm_create: NULL argument");
+  *out = nullptr;
+  PAS_CHECK_ARG(ctx, n_modes >= 1 && Np > 0, "pas_dm_create: bad sizes");
+  PAS_CHECK_ARG(ctx, prec == PAS_FP32, "pas_dm_create: only PAS_FP32 DM bases are supported");
+  int32_t npx = 0;
+  if (pas_pupil_pixels(Np, obs, nullptr, 0, &npx) != PAS_OK || npx != n_pix)
+    return pas::set_error(ctx, PAS_EINVAL, "pas_dm_create: n_pix=%d does not match the pupil (%d)", n_pix, npx);
+  std::vector<int32_t> pix(n_pix);
+  pas_pupil_pixels(Np, obs, pix.data(), n_pix, &npx);
+  pas_dm_t d = new pas_dm_s();
+  d->ctx = ctx;
+  d->n_pix = n_pix;
+  d->n_modes = n_modes;
+  d->Np = Np;
+  d->n_pad = ((n_pix + 127) / 128) * 128;
+  d->T_obs = pas::obstruction_threshold(Np, obs);
+  std::vector<float> MT((size_t)n_modes * d->n_pad, 0.f);
+  for (int p = 0; p < n_pix; ++p)
+    for (int m = 0; m < n_modes; ++m) MT[(size_t)m * d->n_pad + p] = h_M[(size_t)p * n_modes + m];
+  pas_status st = pas::dev_alloc(ctx, (void**)&d->d_MT, sizeof(float) * MT.size());
+  if (st == PAS_OK) st = pas::dev_alloc(ctx, (void**)&d->d_pix, sizeof(int32_t) * n_pix);
+  if (st != PAS_OK) {
+    pas_dm_destroy(d);
+    return st;
+  }
+  cudaError_t e = cudaMemcpy(d->d_MT, MT.data(), sizeof(float) * MT.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d->d_pix, pix.data(), sizeof(int32_t) * n_pix, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    pas_dm_destroy(d);
+    return pas::set_error(ctx, PAS_ECUDA, "pas_dm_create: %s", cudaGetErrorString(e));
+  }
+  *out = d;
+  return PAS_OK;
+}
+
+pas_status pas_dm_update(pas_dm_t d, const float* d_dmodes, const float* d_gain, float* d_cmd,
+                         float* d_opd_dm) {
+  if (!d || !d_cmd) return pas::set_global_error(PAS_EINVAL, "pas_dm_update: NULL argument");
+  cudaStream_t st = d->ctx->stream;
+  if (d_dmodes) {
+    pas::integrate_kernel<<<(d->n_modes + 255) / 256, 256, 0, st>>>(d_cmd, d_dmodes, d_gain, d->n_modes);
+    pas_status s = pas::check_launch(d->ctx, "pas_dm_update integrate launch");
+    if (s != PAS_OK) return s;
+  }
+  if (d_opd_dm) {
+    pas::ResArgs a = pas::make_res_args(d);
+    a.cmd = d_cmd;
+    a.out = d_opd_dm;
+    a.dm_sign = -1.0f;  // out = 0 - (-1) M c = M c
+    pas::zero_outside_kernel<<<(d->Np * d->Np + 255) / 256, 256, 0, st>>>(d_opd_dm, d->Np, d->T_obs);
+    return pas::residual_launch(d->ctx, a, st);
+  }
+  return PAS_OK;
+}
+
+pas_status pas_dm_residual(pas_dm_t d, const float* d_opd_atm, const float* d_cmd, float* d_opd_res) {
+  if (!d || !d_opd_atm || !d_cmd || !d_opd_res)
+    return pas::set_global_error(PAS_EINVAL, "pas_dm_residual: NULL argument");
+  cudaStream_t st = d->ctx->stream;
+  pas::ResArgs a = pas::make_res_args(d);
+  a.opd_atm = d_opd_atm;
+  a.cmd = d_cmd;
+  a.out = d_opd_res;
+  a.dm_sign = 1.0f;
+  pas_status s = pas::residual_launch(d->ctx, a, st);
+  if (s != PAS_OK) return s;
+  pas::zero_outside_kernel<<<(d->Np * d->Np + 255) / 256, 256, 0, st>>>(d_opd_res, d->Np, d->T_obs);
+  return pas::check_launch(d->ctx, "pas_dm_residual zero launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// Shared declarations of the atmosphere / DM objects and their kernels.
+#pragma once
+#include "internal.h"
+
+namespace pas {
+
+struct AtmoArgs {
+  const float* screens = nullptr;  // [L][S][S]
+  int L = 0, S = 0, Np = 0;
+  double vx[PAS_MAX_LAYERS] = {};
+  double vy[PAS_MAX_LAYERS] = {};
+};
+
+struct ResArgs {
+  AtmoArgs atmo;                   // L = 0: take opd_atm instead
+  const float* opd_atm = nullptr;  // [Np][Np] or null (zero atmosphere)
+  const float* MT = nullptr;       // [n_m][n_pad] mode-major basis
+  const int* pix = nullptr;        // [n_pix] flat pupil pixel indices
+  int n_pix = 0, n_pad = 0, n_m = 0, Np = 0;
+  const float* cmd = nullptr;      // [n_m] command
+  const float* cmd_ring = nullptr; // [delay][n_m]: slot step % delay used instead
+  int delay = 1;
+  const long long* d_step = nullptr;
+  long long h_step = 0;
+  float dm_sign = 1.0f;            // out = atm - dm_sign * M c
+  float* out = nullptr;            // [Np][Np], pupil pixels written
+  double2* wfe_part = nullptr;     // per-CTA (sum r, sum r^2) or null
+};
+
+pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st);
+
+}  // namespace pas
+
+struct pas_atmo_s {
+  pas_ctx_t ctx = nullptr;
+  pas::AtmoArgs args;
+};
+
+struct pas_dm_s {
+  pas_ctx_t ctx = nullptr;
+  int n_pix = 0, n_modes = 0, Np = 0, n_pad = 0;
+  int64_t T_obs = 0;
+  float* d_MT = nullptr;
+  int32_t* d_pix = nullptr;
+};
+
+namespace pas {
+inline ResArgs make_res_args(pas_dm_t d) {
+  ResArgs a;
+  a.MT = d->d_MT;
+  a.pix = d->d_pix;
+  a.n_pix = d->n_pix;
+  a.n_pad = d->n_pad;
+  a.n_m = d->n_modes;
+  a.Np = d->Np;
+  return a;
+}
+}  // namespace pas

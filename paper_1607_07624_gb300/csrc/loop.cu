@@ -1,0 +1,286 @@
+// Loop control (Sec. Structure: the loop control object triggers every processing
+// object once per simulation step; Table 2: loop.add in run order, loop.run).
+// One step on the device, in the order atmo -> prop (residual with the DM layer)
+// -> pyr -> ccd -> slopec -> modalrec -> control; the DM layer of step t carries the
+// command of step t - delay. The step is captured once as a CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "atmo_dm.cuh"
+#include "internal.h"
+#include "pyr.cuh"
+#include "recon.cuh"
+
+namespace pas {
+__global__ void step_increment_kernel(long long* step) { *step += 1; }
+}  // namespace pas
+
+struct pas_loop_s {
+  pas_ctx_t ctx = nullptr;
+  pas_atmo_t atmo = nullptr;
+  pas_pyr_t pyr = nullptr;
+  pas_recon_t rec = nullptr;
+  pas_dm_t dm = nullptr;
+  int delay = 1, hist = 1, n_m = 0, n_slopes = 0, nd = 0, Np = 0, n_tiles = 0;
+  float* d_opd = nullptr;
+  float* d_frame = nullptr;
+  float* d_slopes = nullptr;
+  float* d_dmodes = nullptr;
+  float* d_ring = nullptr;
+  float* d_cmd = nullptr;
+  float* d_gain = nullptr;
+  double* d_wfe = nullptr;
+  double2* d_wfe_part = nullptr;
+  long long* d_step = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+// ev (optional): PAS_LOOP_KERNELS + 1 events recorded before each kernel and
+// after the last one.
+static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = nullptr) {
+  pas::ResArgs ra = pas::make_res_args(L->dm);
+  ra.atmo = L->atmo->args;
+  ra.cmd_ring = L->d_ring;
+  ra.delay = L->delay;
+  ra.d_step = L->d_step;
+  ra.dm_sign = 1.0f;
+  ra.out = L->d_opd;
+  ra.wfe_part = L->d_wfe_part;
+  if (ev) cudaEventRecord(ev[0], st);
+  pas_status s = pas::residual_launch(L->ctx, ra, st);
+  if (s != PAS_OK) return s;
+  pas::FrameArgs fa;
+  std::memset(&fa, 0, sizeof(fa));
+  fa.frame_ctr = L->d_step;
+  fa.wfe_part = L->d_wfe_part;
+  fa.n_wfe_part = L->n_tiles;
+  fa.inv_npix = 1.0 / (double)L->dm->n_pix;
+  fa.wfe_hist = L->d_wfe;
+  fa.wfe_hist_len = L->hist;
+  fa.step = L->d_step;
+  s = pas::pyr_launch(L->pyr, L->d_opd, L->d_frame, L->d_slopes, st, &fa, false, ev ? ev + 1 : nullptr);
+  if (s != PAS_OK) return s;
+  pas::ReconArgs rc;
+  rc.s = L->d_slopes;
+  rc.dmodes = L->d_dmodes;
+  rc.gain = L->d_gain;
+  rc.ring = L->d_ring;
+  rc.delay = L->delay;
+  rc.step = L->d_step;
+  rc.cmd_last = L->d_cmd;
+  if (ev) cudaEventRecord(ev[4], st);
+  s = pas::recon_launch(L->rec, rc, st);
+  if (s != PAS_OK) return s;
+  if (ev) cudaEventRecord(ev[5], st);
+  pas::step_increment_kernel<<<1, 1, 0, st>>>(L->d_step);
+  if (ev) cudaEventRecord(ev[6], st);
+  return pas::check_launch(L->ctx, "step counter launch");
+}
+
+extern "C" {
+
+void pas_loop_destroy(pas_loop_t L) {
+  if (!L) return;
+  if (L->exec) cudaGraphExecDestroy(L->exec);
+  if (L->graph) cudaGraphDestroy(L->graph);
+  pas::dev_free(L->d_opd);
+  pas::dev_free(L->d_frame);
+  pas::dev_free(L->d_slopes);
+  pas::dev_free(L->d_dmodes);
+  pas::dev_free(L->d_ring);
+  pas::dev_free(L->d_cmd);
+  pas::dev_free(L->d_gain);
+  pas::dev_free(L->d_wfe);
+  pas::dev_free(L->d_wfe_part);
+  pas::dev_free(L->d_step);
+  delete L;
+}
+
+pas_status pas_loop_create(pas_ctx_t ctx, pas_atmo_t atmo, pas_pyr_t pyr, pas_recon_t rec, pas_dm_t dm,
+                           const float* d_gain, int32_t delay, int32_t wfe_history, pas_loop_t* out) {
+  if (!ctx || !atmo || !pyr || !rec || !dm || !d_gain || !out)
+    return pas::set_global_error(PAS_EINVAL, "pas_loop_create: NULL argument");
+  *out = nullptr;
+  PAS_CHECK_ARG(ctx, delay >= 1 && delay <= 64 && wfe_history >= 1, "pas_loop_create: bad delay or history");
+  PAS_CHECK_ARG(ctx, atmo->args.Np == dm->Np, "pas_loop_create: atmosphere and DM pupil sizes differ");
+  PAS_CHECK_ARG(ctx, rec->n_modes == dm->n_modes, "pas_loop_create: reconstructor and DM mode counts differ");
+  PAS_CHECK_ARG(ctx, rec->n_slopes == 2 * pas_pyr_n_valid(pyr), "pas_loop_create: reconstructor slopes != 2 n_valid");
+  pas_loop_t L = new pas_loop_s();
+  L->ctx = ctx;
+  L->atmo = atmo;
+  L->pyr = pyr;
+  L->rec = rec;
+  L->dm = dm;
+  L->delay = delay;
+  L->hist = wfe_history;
+  L->n_m = dm->n_modes;
+  L->n_slopes = rec->n_slopes;
+  L->nd = pas::pyr_nd(pyr);
+  L->Np = dm->Np;
+  L->n_tiles = (dm->n_pix + 127) / 128;
+  pas_status st = PAS_OK;
+  auto A = [&](void** p, size_t bytes) {
+    if (st == PAS_OK) st = pas::dev_alloc(ctx, p, bytes);
+  };
+  A((void**)&L->d_opd, sizeof(float) * L->Np * L->Np);
+  A((void**)&L->d_frame, sizeof(float) * L->nd * L->nd);
+  A((void**)&L->d_slopes, sizeof(float) * L->n_slopes);
+  A((void**)&L->d_dmodes, sizeof(float) * L->n_m);
+  A((void**)&L->d_ring, sizeof(float) * L->n_m * delay);
+  A((void**)&L->d_cmd, sizeof(float) * L->n_m);
+  A((void**)&L->d_gain, sizeof(float) * L->n_m);
+  A((void**)&L->d_wfe, sizeof(double) * wfe_history);
+  A((void**)&L->d_wfe_part, sizeof(double2) * L->n_tiles);
+  A((void**)&L->d_step, sizeof(long long));
+  if (st != PAS_OK) {
+    pas_loop_destroy(L);
+    return st;
+  }
+  cudaError_t e = cudaMemset(L->d_opd, 0, sizeof(float) * L->Np * L->Np);
+  if (e == cudaSuccess) e = cudaMemset(L->d_ring, 0, sizeof(float) * L->n_m * delay);
+  if (e == cudaSuccess) e = cudaMemset(L->d_cmd, 0, sizeof(float) * L->n_m);
+  if (e == cudaSuccess) e = cudaMemset(L->d_wfe, 0, sizeof(double) * wfe_history);
+  if (e == cudaSuccess) e = cudaMemset(L->d_step, 0, sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemcpy(L->d_gain, d_gain, sizeof(float) * L->n_m, cudaMemcpyDeviceToDevice);
+  if (e != cudaSuccess) {
+    pas_loop_destroy(L);
+    return pas::set_error(ctx, PAS_ECUDA, "pas_loop_create: %s", cudaGetErrorString(e));
+  }
+  *out = L;
+  return PAS_OK;
+}
+
+static pas_status loop_capture(pas_loop_t L) {
+  pas_ctx_t ctx = L->ctx;
+  // the capture stream must see everything queued before on the context stream
+  PAS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  PAS_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+  pas_status s = loop_enqueue(L, ctx->capture_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &g);
+  if (s != PAS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return pas::set_error(ctx, PAS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&L->exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return pas::set_error(ctx, PAS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  L->graph = g;
+  return PAS_OK;
+}
+
+static pas_status loop_stats(pas_loop_t L, pas_loop_stats* h) {
+  pas_ctx_t ctx = L->ctx;
+  long long step = 0;
+  PAS_CUDA_TRY(ctx, cudaMemcpyAsync(&step, L->d_step, sizeof(step), cudaMemcpyDeviceToHost, ctx->stream));
+  PAS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  h->step = step;
+  h->wfe_nm = 0.0;
+  if (step > 0) {
+    PAS_CUDA_TRY(ctx, cudaMemcpy(&h->wfe_nm, L->d_wfe + (step - 1) % L->hist, sizeof(double),
+                                 cudaMemcpyDeviceToHost));
+  }
+  return PAS_OK;
+}
+
+pas_status pas_loop_step(pas_loop_t L, int32_t n_steps, pas_loop_stats* h_stats) {
+  if (!L) return pas::set_global_error(PAS_EINVAL, "pas_loop_step: NULL loop");
+  PAS_CHECK_ARG(L->ctx, n_steps >= 0, "pas_loop_step: negative step count");
+  if (!L->exec && n_steps > 0) {
+    pas_status s = loop_capture(L);
+    if (s != PAS_OK) return s;
+  }
+  for (int t = 0; t < n_steps; ++t) PAS_CUDA_TRY(L->ctx, cudaGraphLaunch(L->exec, L->ctx->stream));
+  if (h_stats) return loop_stats(L, h_stats);
+  return PAS_OK;
+}
+
+pas_status pas_loop_step_eager(pas_loop_t L, int32_t n_steps) {
+  if (!L) return pas::set_global_error(PAS_EINVAL, "pas_loop_step_eager: NULL loop");
+  PAS_CHECK_ARG(L->ctx, n_steps >= 0, "pas_loop_step_eager: negative step count");
+  for (int t = 0; t < n_steps; ++t) {
+    pas_status s = loop_enqueue(L, L->ctx->stream);
+    if (s != PAS_OK) return s;
+  }
+  return PAS_OK;
+}
+
+pas_status pas_loop_profile(pas_loop_t L, int32_t n_steps, float* h_ms, int32_t cap, int32_t* n_kernels) {
+  if (!L || !h_ms) return pas::set_global_error(PAS_EINVAL, "pas_loop_profile: NULL argument");
+  PAS_CHECK_ARG(L->ctx, n_steps >= 1 && cap >= PAS_LOOP_KERNELS, "pas_loop_profile: bad n_steps or cap");
+  cudaEvent_t ev[PAS_LOOP_KERNELS + 1];
+  for (int i = 0; i <= PAS_LOOP_KERNELS; ++i) PAS_CUDA_TRY(L->ctx, cudaEventCreate(&ev[i]));
+  double acc[PAS_LOOP_KERNELS] = {0};
+  pas_status s = PAS_OK;
+  for (int t = 0; t < n_steps && s == PAS_OK; ++t) {
+    s = loop_enqueue(L, L->ctx->stream, ev);
+    if (s != PAS_OK) break;
+    cudaError_t e = cudaEventSynchronize(ev[PAS_LOOP_KERNELS]);
+    if (e != cudaSuccess) {
+      s = pas::set_error(L->ctx, PAS_ECUDA, "pas_loop_profile: %s", cudaGetErrorString(e));
+      break;
+    }
+    for (int k = 0; k < PAS_LOOP_KERNELS; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      acc[k] += ms;
+    }
+  }
+  for (int i = 0; i <= PAS_LOOP_KERNELS; ++i) cudaEventDestroy(ev[i]);
+  if (s != PAS_OK) return s;
+  for (int k = 0; k < PAS_LOOP_KERNELS; ++k) h_ms[k] = (float)(acc[k] / n_steps);
+  if (n_kernels) *n_kernels = PAS_LOOP_KERNELS;
+  return PAS_OK;
+}
+
+const char* pas_loop_kernel_name(int32_t idx) {
+  static const char* names[PAS_LOOP_KERNELS] = {"residual_kernel", "pyr_rows_kernel", "pyr_cols_kernel",
+                                                "frame_slopes_kernel", "recon_kernel", "step_increment_kernel"};
+  return (idx >= 0 && idx < PAS_LOOP_KERNELS) ? names[idx] : nullptr;
+}
+
+pas_status pas_loop_buffers(pas_loop_t L, float** opd_res, float** frame, float** slopes, float** dmodes,
+                            float** cmd, double** wfe) {
+  if (!L) return pas::set_global_error(PAS_EINVAL, "pas_loop_buffers: NULL loop");
+  if (opd_res) *opd_res = L->d_opd;
+  if (frame) *frame = L->d_frame;
+  if (slopes) *slopes = L->d_slopes;
+  if (dmodes) *dmodes = L->d_dmodes;
+  if (cmd) *cmd = L->d_cmd;
+  if (wfe) *wfe = L->d_wfe;
+  return PAS_OK;
+}
+
+pas_status pas_loop_get_state(pas_loop_t L, int64_t* step, float* h_cmd_ring) {
+  if (!L || !step) return pas::set_global_error(PAS_EINVAL, "pas_loop_get_state: NULL argument");
+  long long s = 0;
+  PAS_CUDA_TRY(L->ctx, cudaStreamSynchronize(L->ctx->stream));
+  PAS_CUDA_TRY(L->ctx, cudaMemcpy(&s, L->d_step, sizeof(s), cudaMemcpyDeviceToHost));
+  *step = s;
+  if (h_cmd_ring)
+    PAS_CUDA_TRY(L->ctx, cudaMemcpy(h_cmd_ring, L->d_ring, sizeof(float) * L->n_m * L->delay,
+                                    cudaMemcpyDeviceToHost));
+  return PAS_OK;
+}
+
+pas_status pas_loop_set_state(pas_loop_t L, int64_t step, const float* h_cmd_ring) {
+  if (!L || !h_cmd_ring) return pas::set_global_error(PAS_EINVAL, "pas_loop_set_state: NULL argument");
+  PAS_CHECK_ARG(L->ctx, step >= 0, "pas_loop_set_state: negative step");
+  long long s = step;
+  PAS_CUDA_TRY(L->ctx, cudaStreamSynchronize(L->ctx->stream));
+  PAS_CUDA_TRY(L->ctx, cudaMemcpy(L->d_step, &s, sizeof(s), cudaMemcpyHostToDevice));
+  PAS_CUDA_TRY(L->ctx, cudaMemcpy(L->d_ring, h_cmd_ring, sizeof(float) * L->n_m * L->delay,
+                                  cudaMemcpyHostToDevice));
+  // the last command is the ring slot of step - 1
+  const int slot = (int)(((step - 1) % L->delay + L->delay) % L->delay);
+  PAS_CUDA_TRY(L->ctx, cudaMemcpy(L->d_cmd, L->d_ring + (size_t)slot * L->n_m, sizeof(float) * L->n_m,
+                                  cudaMemcpyDeviceToDevice));
+  return PAS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,625 @@
+// Modulated four-face pyramid WFS, CCD binning/noise and slope computer
+// (Table 1 pyramid / detector / slopec; Sec. GPU acceleration, "pyramid
+// propagation from wavefront to detector plane").
+//
+// The centred DFT, the pyramid mask |u~| + |v~| and the modulation tilt are all
+// separable, so for modulation point k the pupil-plane field after the pyramid is
+//   g_k = A diag(tx_k) E0 diag(ty_k) A^T,   A = IDFT diag(p) DFT  (1-D, N x N),
+// with E0 the embedded pupil field. Two passes compute it:
+//   rows pass: for each pupil row i and each distinct sin(theta_k):
+//              phasor * tilt_y -> FFT -> p(u)/N -> IFFT  => H_s[y][i] (transposed);
+//   cols pass: for each column y and each k: H_s(k)[y][:] * tilt_x -> FFT -> p/N ->
+//              IFFT -> |.|^2, accumulated over the CTA's k and binned b x b.
+// The centring ramps of the DFT reduce to (-1)^x exp(-i pi x / N) on the input
+// and a unit-modulus ramp on the output; the output ramp of each pass is a
+// per-row/column constant of the next pass and vanishes in |.|^2, so only the
+// input ramp is kept (merged into the tilt phases alpha_k, beta_s).
+// Modulation points with equal sin(theta) (theta and pi - theta) share a rows pass.
+#include <cmath>
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "fft.cuh"
+#include "internal.h"
+#include "noise.cuh"
+#include "pyr.cuh"
+
+namespace pas {
+
+constexpr int ROWS_PER_CTA = 8;
+
+struct RowArgs {
+  const float* opd;     // [Np][Np]
+  const float2* tw;     // [N]
+  const float2* mask;   // [N] digit-reversed
+  const float* beta;    // [n_s] cycles per pixel (tilt_y + input ramp)
+  float2* H;            // [n_s][N][Np]
+  int Np, off;
+  int T_obs;            // obstruction threshold (integer)
+  float inv_hi, inv_lo; // 1/lambda split in two floats
+};
+
+struct ColArgs {
+  const float2* H;
+  const float2* tw;
+  const float2* mask;
+  const float* alpha;   // [K] cycles per pixel (tilt_x + input ramp)
+  const int* kmap;      // [K] -> rows-pass index
+  float* part;          // [G][nd][nd]
+  int Np, off, K, kper, nd, b;
+};
+
+
+
+template <int N>
+__global__ void __launch_bounds__(ROWS_PER_CTA * 32)
+pyr_rows_kernel(RowArgs a) {
+  extern __shared__ float2 smem[];
+  float2* tw_s = smem;
+  float2* mk_s = smem + N;
+  float2* bufs = smem + 2 * N;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    tw_s[t] = a.tw[t];
+    mk_s[t] = a.mask[t];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * ROWS_PER_CTA;
+  const int i = i0 + warp;
+  const int s = blockIdx.y;
+  float2* buf = bufs + warp * (N + 1);
+  if (i < a.Np) {
+    const float beta = a.beta[s];
+    const float* orow = a.opd + (size_t)i * a.Np;
+    const int Np = a.Np, off = a.off;
+    const int ai = 2 * i - Np + 1;
+    const int ai2 = ai * ai;
+    const float cj = 0.5f * (float)(Np - 1);
+    auto load = [&](int x) -> float2 {
+      const int j = x - off;
+      if ((unsigned)j < (unsigned)Np) {
+        const int bj = 2 * j - Np + 1;
+        const int d2 = ai2 + bj * bj;
+        if (d2 <= Np * Np && d2 >= a.T_obs) {
+          const float o = __ldg(orow + j);
+          // opd / lambda in cycles, reduced to [-1/2, 1/2] with an exact split
+          const float hi = o * a.inv_hi;
+          const float err = fmaf(o, a.inv_hi, -hi);
+          const float lo = fmaf(o, a.inv_lo, err);
+          const float cyc = (hi - rintf(hi)) + lo + ((float)j - cj) * beta;
+          float sn, cs;
+          sincospif(2.0f * cyc, &sn, &cs);
+          return (j & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
+        }
+      }
+      return make_float2(0.f, 0.f);
+    };
+    auto store = [&](int, int, int x, float2 v) { buf[x] = v; };
+    fft_mask_ifft<N>(buf, tw_s, mk_s, lane, load, store);
+  }
+  __syncthreads();
+  // transposed, coalesced write: H[s][y][i0 + r]
+  float2* Hs = a.H + (size_t)s * N * a.Np;
+  const int nr = min(ROWS_PER_CTA, a.Np - i0);
+  for (int idx = threadIdx.x; idx < N * ROWS_PER_CTA; idx += blockDim.x) {
+    const int r = idx % ROWS_PER_CTA, y = idx / ROWS_PER_CTA;
+    if (r < nr) Hs[(size_t)y * a.Np + i0 + r] = bufs[r * (N + 1) + y];
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(512)
+pyr_cols_kernel(ColArgs a) {
+  extern __shared__ float2 smem[];
+  float2* tw_s = smem;
+  float2* mk_s = smem + N;
+  float2* tilt_s = smem + 2 * N;                  // [kper][Np]
+  float2* bufs = tilt_s + a.kper * a.Np;          // [b][N + 1]
+  const int Np = a.Np;
+  const int q = blockIdx.x;                       // detector column
+  const int g = blockIdx.y;                       // modulation group
+  const int k0 = g * a.kper;
+  const int kc = min(a.kper, a.K - k0);
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    tw_s[t] = a.tw[t];
+    mk_s[t] = a.mask[t];
+  }
+  const float ci = 0.5f * (float)(Np - 1);
+  for (int t = threadIdx.x; t < kc * Np; t += blockDim.x) {
+    const int kk = t / Np, i = t - kk * Np;
+    float sn, cs;
+    sincospif(2.0f * ((float)i - ci) * a.alpha[k0 + kk], &sn, &cs);
+    tilt_s[t] = (i & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int y = q * a.b + warp;
+  float2* buf = bufs + warp * (N + 1);
+  using OS = OutShape<N>;
+  float acc[OS::PER_LANE];
+#pragma unroll
+  for (int t = 0; t < OS::PER_LANE; ++t) acc[t] = 0.f;
+  for (int kk = 0; kk < kc; ++kk) {
+    const float2* Hcol = a.H + ((size_t)a.kmap[k0 + kk] * N + y) * Np;
+    const float2* tl = tilt_s + kk * Np;
+    const int off = a.off;
+    auto load = [&](int x) -> float2 {
+      const int i = x - off;
+      if ((unsigned)i < (unsigned)Np) return cmul(__ldg(Hcol + i), tl[i]);
+      return make_float2(0.f, 0.f);
+    };
+    auto store = [&](int jb, int k, int, float2 v) {
+      acc[jb * OS::R0 + k] = fmaf(v.x, v.x, fmaf(v.y, v.y, acc[jb * OS::R0 + k]));
+    };
+    fft_mask_ifft<N>(buf, tw_s, mk_s, lane, load, store);
+    __syncwarp();
+  }
+  // stage |g|^2 of this column, then bin b x b across the CTA's b columns
+  float* accw = reinterpret_cast<float*>(buf);
+#pragma unroll
+  for (int jb = 0; jb < OS::NJ0; ++jb) {
+    const int bb = lane + 32 * jb;
+    if (OS::NB0 % 32 == 0 || bb < OS::NB0) {
+#pragma unroll
+      for (int k = 0; k < OS::R0; ++k) accw[bb + k * OS::NB0] = acc[jb * OS::R0 + k];
+    }
+  }
+  __syncthreads();
+  const int nd = a.nd, b = a.b;
+  float* out = a.part + (size_t)g * nd * nd;
+  for (int p = threadIdx.x; p < nd; p += blockDim.x) {
+    float sum = 0.f;
+    for (int w = 0; w < b; ++w) {
+      const float* col = reinterpret_cast<const float*>(bufs + w * (N + 1));
+      for (int xx = 0; xx < b; ++xx) sum += col[p * b + xx];
+    }
+    out[(size_t)p * nd + q] = sum;
+  }
+}
+
+__device__ inline double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (warp == 0) {
+    r = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    if (lane == 0) red[0] = r;
+  }
+  __syncthreads();
+  r = red[0];
+  return r;
+}
+
+__global__ void __launch_bounds__(1024) frame_slopes_kernel(FrameArgs a) {
+  __shared__ double red[32];
+  const int np = a.nd * a.nd;
+  const long long fidx = a.frame_ctr ? *a.frame_ctr : 0;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    float v = 0.f;
+    for (int gg = 0; gg < a.G; ++gg) v += a.part[(size_t)gg * np + p];
+    v *= a.invK;
+    if (a.photon_scale > 0.0) {
+      double e = poisson_draw((double)v * a.photon_scale, a.seed, (uint32_t)p, (uint64_t)fidx);
+      if (a.ron > 0.0) e += a.ron * gaussian_draw(a.seed, (uint32_t)p, (uint64_t)fidx);
+      v = (float)e;
+    }
+    a.frame[p] = v;
+  }
+  __syncthreads();
+  const int ns = a.n_sub, nd = a.nd;
+  double tsum = 0.0;
+  for (int j = threadIdx.x; j < a.nv; j += blockDim.x) {
+    const int v = a.valid[j], r = v / ns, c = v - r * ns;
+    tsum += (double)a.frame[r * nd + c] + (double)a.frame[r * nd + ns + c] +
+            (double)a.frame[(ns + r) * nd + c] + (double)a.frame[(ns + r) * nd + ns + c];
+  }
+  const double F = block_sum(tsum, red) / (double)a.nv;
+  if (a.slopes) {
+    for (int j = threadIdx.x; j < a.nv; j += blockDim.x) {
+      const int v = a.valid[j], r = v / ns, c = v - r * ns;
+      const float q00 = a.frame[r * nd + c], q01 = a.frame[r * nd + ns + c];
+      const float q10 = a.frame[(ns + r) * nd + c], q11 = a.frame[(ns + r) * nd + ns + c];
+      const float den = a.local_norm ? (q00 + q01 + q10 + q11) : (float)F;
+      const float inv = 1.0f / den;
+      float sx = ((q10 + q11) - (q00 + q01)) * inv;
+      float sy = ((q01 + q11) - (q00 + q10)) * inv;
+      if (a.sn) {
+        sx -= a.sn[j];
+        sy -= a.sn[a.nv + j];
+      }
+      a.slopes[j] = sx;
+      a.slopes[a.nv + j] = sy;
+    }
+  }
+  if (a.wfe_part) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int t = threadIdx.x; t < a.n_wfe_part; t += blockDim.x) {
+      s1 += a.wfe_part[t].x;
+      s2 += a.wfe_part[t].y;
+    }
+    s1 = block_sum(s1, red);
+    s2 = block_sum(s2, red);
+    if (threadIdx.x == 0) {
+      const double m = s1 * a.inv_npix;
+      const double var = fmax(s2 * a.inv_npix - m * m, 0.0);
+      a.wfe_hist[(*a.step) % a.wfe_hist_len] = sqrt(var);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && a.ctr_increment && a.frame_ctr) *a.frame_ctr = fidx + 1;
+}
+
+__global__ void ccd_noise_kernel(const float* in, float* out, int n, double scale, double ron,
+                                 unsigned long long seed, long long fidx) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    double v = in[p];
+    double e = scale > 0.0 ? poisson_draw(v * scale, seed, (uint32_t)p, (uint64_t)fidx) : v;
+    if (ron > 0.0 && scale > 0.0) e += ron * gaussian_draw(seed, (uint32_t)p, (uint64_t)fidx);
+    out[p] = (float)e;
+  }
+}
+
+// ------------------------------------------------------------------ dispatch
+
+struct PyrKernels {
+  void (*rows)(RowArgs);
+  void (*cols)(ColArgs);
+  int per_lane;
+};
+
+template <int N>
+PyrKernels kernels_for() {
+  return PyrKernels{pyr_rows_kernel<N>, pyr_cols_kernel<N>, OutShape<N>::PER_LANE};
+}
+
+#define PAS_PYR_SIZES(X) X(16) X(24) X(32) X(40) X(48) X(64) X(80) X(96) X(120) X(128) X(160) \
+  X(192) X(240) X(256) X(320) X(480) X(512) X(640) X(960)
+
+static bool lookup_kernels(int N, PyrKernels* k) {
+  switch (N) {
+#define PAS_CASE(n) \
+  case n:           \
+    *k = kernels_for<n>(); \
+    return true;
+    PAS_PYR_SIZES(PAS_CASE)
+#undef PAS_CASE
+    default:
+      return false;
+  }
+}
+
+// Digit-reversed frequency of in-place position p for the radix list of N.
+static int digit_reversed_freq(int N, int p) {
+  const int M = radix_count(N);
+  int rem = p, L = N, mult = 1, u = 0;
+  for (int i = 0; i < M; ++i) {
+    const int R = radix_at(N, i), S = L / R;
+    const int k = rem / S;
+    rem -= k * S;
+    u += k * mult;
+    mult *= R;
+    L = S;
+  }
+  return u;
+}
+
+}  // namespace pas
+
+struct pas_pyr_s {
+  pas_ctx_t ctx = nullptr;
+  pas_pyr_params p{};
+  pas::PyrKernels kern{};
+  int b = 0, nd = 0, n_s = 0, G = 0, kper = 0, n_valid = 0, n_pupil = 0;
+  int64_t T_obs = 0;
+  float inv_hi = 0.f, inv_lo = 0.f;
+  size_t smem_rows = 0, smem_cols = 0;
+  int32_t* d_valid = nullptr;
+  float* d_sn = nullptr;
+  float2* d_tw = nullptr;
+  float2* d_mask = nullptr;
+  float* d_alpha = nullptr;
+  float* d_beta = nullptr;
+  int* d_kmap = nullptr;
+  float2* d_H = nullptr;
+  float* d_part = nullptr;
+  float* d_frame = nullptr;
+  long long* d_frame_ctr = nullptr;
+  double photon_scale = 0.0, ron = 0.0;
+  unsigned long long seed = 0;
+  bool has_sn = false;
+};
+
+namespace pas {
+
+// Launch the three pyramid kernels. wfe fields of `fa` may be filled by the loop.
+pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes,
+                      cudaStream_t st, FrameArgs* fa_extra, bool increment_ctr, cudaEvent_t* ev) {
+  const pas_pyr_params& p = y->p;
+  RowArgs ra;
+  ra.opd = d_opd;
+  ra.tw = y->d_tw;
+  ra.mask = y->d_mask;
+  ra.beta = y->d_beta;
+  ra.H = y->d_H;
+  ra.Np = p.Np;
+  ra.off = (p.N - p.Np) / 2;
+  ra.T_obs = (int)y->T_obs;
+  ra.inv_hi = y->inv_hi;
+  ra.inv_lo = y->inv_lo;
+  dim3 gr((p.Np + ROWS_PER_CTA - 1) / ROWS_PER_CTA, y->n_s);
+  if (ev) cudaEventRecord(ev[0], st);
+  y->kern.rows<<<gr, ROWS_PER_CTA * 32, y->smem_rows, st>>>(ra);
+  ColArgs ca;
+  ca.H = y->d_H;
+  ca.tw = y->d_tw;
+  ca.mask = y->d_mask;
+  ca.alpha = y->d_alpha;
+  ca.kmap = y->d_kmap;
+  ca.part = y->d_part;
+  ca.Np = p.Np;
+  ca.off = (p.N - p.Np) / 2;
+  ca.K = p.K;
+  ca.kper = y->kper;
+  ca.nd = y->nd;
+  ca.b = y->b;
+  dim3 gc(y->nd, y->G);
+  if (ev) cudaEventRecord(ev[1], st);
+  y->kern.cols<<<gc, y->b * 32, y->smem_cols, st>>>(ca);
+  FrameArgs fa;
+  if (fa_extra) fa = *fa_extra;
+  else {
+    memset(&fa, 0, sizeof(fa));
+  }
+  fa.part = y->d_part;
+  fa.frame = d_frame ? d_frame : y->d_frame;
+  fa.valid = y->d_valid;
+  fa.sn = y->has_sn ? y->d_sn : nullptr;
+  fa.slopes = d_slopes;
+  fa.G = y->G;
+  fa.nd = y->nd;
+  fa.n_sub = p.n_sub;
+  fa.nv = y->n_valid;
+  fa.local_norm = p.local_norm;
+  fa.invK = 1.0f / (float)p.K;
+  fa.photon_scale = y->photon_scale;
+  fa.ron = y->ron;
+  fa.seed = y->seed;
+  if (!fa_extra) fa.frame_ctr = y->d_frame_ctr;
+  fa.ctr_increment = increment_ctr ? 1 : 0;
+  if (ev) cudaEventRecord(ev[2], st);
+  frame_slopes_kernel<<<1, 1024, 0, st>>>(fa);
+  return check_launch(y->ctx, "pas_pyr_measure launch");
+}
+
+int pyr_n_pupil(pas_pyr_t y) { return y->n_pupil; }
+int pyr_nd(pas_pyr_t y) { return y->nd; }
+
+}  // namespace pas
+
+extern "C" {
+
+int pas_pyr_supported(int N) {
+  pas::PyrKernels k;
+  return pas::lookup_kernels(N, &k) ? 1 : 0;
+}
+
+void pas_pyr_destroy(pas_pyr_t y) {
+  if (!y) return;
+  pas::dev_free(y->d_valid);
+  pas::dev_free(y->d_sn);
+  pas::dev_free(y->d_tw);
+  pas::dev_free(y->d_mask);
+  pas::dev_free(y->d_alpha);
+  pas::dev_free(y->d_beta);
+  pas::dev_free(y->d_kmap);
+  pas::dev_free(y->d_H);
+  pas::dev_free(y->d_part);
+  pas::dev_free(y->d_frame);
+  pas::dev_free(y->d_frame_ctr);
+  delete y;
+}
+
+pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t* h_valid,
+                          int32_t n_valid, pas_pyr_t* out) {
+  if (!ctx || !pp || !out) return pas::set_global_error(PAS_EINVAL, "pas_pyr_create: NULL argument");
+  *out = nullptr;
+  const pas_pyr_params p = *pp;
+  PAS_CHECK_ARG(ctx, p.Np > 0 && p.N == 2 * p.Np, "pas_pyr_create: N must equal 2*Np");
+  PAS_CHECK_ARG(ctx, p.n_sub > 0 && p.N % (2 * p.n_sub) == 0, "pas_pyr_create: N must be a multiple of 2*n_sub");
+  PAS_CHECK_ARG(ctx, p.K >= 1 && p.K <= 4096, "pas_pyr_create: K out of range");
+  PAS_CHECK_ARG(ctx, p.wavelength_nm > 0 && p.mod_radius >= 0 && p.obs >= 0 && p.obs < 1,
+                "pas_pyr_create: bad wavelength, modulation radius or obstruction");
+  pas::PyrKernels kern;
+  if (!pas::lookup_kernels(p.N, &kern))
+    return pas::set_error(ctx, PAS_EINVAL, "pas_pyr_create: FFT size N=%d not supported", p.N);
+  const int b = p.N / (2 * p.n_sub);
+  PAS_CHECK_ARG(ctx, b <= 16, "pas_pyr_create: more than 16 fine pixels per detector pixel");
+
+  pas_pyr_t y = new pas_pyr_s();
+  y->ctx = ctx;
+  y->p = p;
+  y->kern = kern;
+  y->b = b;
+  y->nd = 2 * p.n_sub;
+  y->T_obs = pas::obstruction_threshold(p.Np, p.obs);
+  {
+    int32_t n = 0;
+    pas_pupil_mask(p.Np, p.obs, nullptr, &n);
+    y->n_pupil = n;
+  }
+  // valid sub-apertures
+  std::vector<int32_t> valid;
+  if (h_valid) {
+    if (n_valid <= 0) {
+      delete y;
+      return pas::set_error(ctx, PAS_EINVAL, "pas_pyr_create: n_valid must be > 0");
+    }
+    valid.assign(h_valid, h_valid + n_valid);
+    for (int j = 0; j < n_valid; ++j)
+      if (valid[j] < 0 || valid[j] >= p.n_sub * p.n_sub || (j > 0 && valid[j] <= valid[j - 1])) {
+        delete y;
+        return pas::set_error(ctx, PAS_EINVAL, "pas_pyr_create: valid indices must be ascending in [0, n_sub^2)");
+      }
+  } else {
+    int32_t nv = 0;
+    if (p.Np % p.n_sub != 0) {
+      delete y;
+      return pas::set_error(ctx, PAS_EINVAL, "pas_pyr_create: geometric rule needs Np multiple of n_sub");
+    }
+    pas_valid_subaps(p.Np, p.obs, p.n_sub, nullptr, 0, &nv);
+    valid.resize(nv);
+    pas_valid_subaps(p.Np, p.obs, p.n_sub, valid.data(), nv, &nv);
+  }
+  y->n_valid = (int)valid.size();
+
+  // modulation: distinct sin(theta) rows passes; theta and pi - theta share one
+  std::vector<int> kmap(p.K), rep_of_s;
+  for (int k = 0; k < p.K; ++k) {
+    int rep = k;
+    if (p.K % 2 == 0) {
+      int partner = ((p.K / 2 - k) % p.K + p.K) % p.K;
+      rep = std::min(k, partner);
+    }
+    int s = -1;
+    for (size_t t = 0; t < rep_of_s.size(); ++t)
+      if (rep_of_s[t] == rep) s = (int)t;
+    if (s < 0) {
+      s = (int)rep_of_s.size();
+      rep_of_s.push_back(rep);
+    }
+    kmap[k] = s;
+  }
+  y->n_s = (int)rep_of_s.size();
+  std::vector<float> alpha(p.K), beta(y->n_s);
+  const double ramp = 1.0 / (2.0 * p.N);
+  for (int k = 0; k < p.K; ++k) {
+    double th = 2.0 * M_PI * (double)k / (double)p.K;
+    alpha[k] = (float)(p.mod_radius * std::cos(th) / p.Np - ramp);
+  }
+  for (int s = 0; s < y->n_s; ++s) {
+    double th = 2.0 * M_PI * (double)rep_of_s[s] / (double)p.K;
+    beta[s] = (float)(p.mod_radius * std::sin(th) / p.Np - ramp);
+  }
+  // twiddles and digit-reversed pyramid mask (delta = N/4): phase = (pi/2)|u~|
+  std::vector<float2> tw(p.N), mk(p.N);
+  for (int j = 0; j < p.N; ++j) {
+    double a = -2.0 * M_PI * (double)j / (double)p.N;
+    tw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    int u = pas::digit_reversed_freq(p.N, j);
+    double ut = std::fabs((double)u - 0.5 * (p.N - 1));
+    double ph = 0.5 * M_PI * ut;
+    mk[j] = make_float2((float)(std::cos(ph) / p.N), (float)(std::sin(ph) / p.N));
+  }
+  double inv = 1.0 / p.wavelength_nm;
+  y->inv_hi = (float)inv;
+  y->inv_lo = (float)(inv - (double)y->inv_hi);
+
+  // launch geometry
+  {
+    int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
+    int G = (4 * sms + y->nd - 1) / y->nd;
+    G = std::max(1, std::min(G, p.K));
+    y->kper = (p.K + G - 1) / G;
+    y->G = (p.K + y->kper - 1) / y->kper;
+  }
+  y->smem_rows = sizeof(float2) * (2 * (size_t)p.N + (size_t)pas::ROWS_PER_CTA * (p.N + 1));
+  y->smem_cols = sizeof(float2) * (2 * (size_t)p.N + (size_t)y->kper * p.Np + (size_t)b * (p.N + 1));
+
+  pas_status st = PAS_OK;
+  auto A = [&](void** ptr, size_t bytes) {
+    if (st == PAS_OK) st = pas::dev_alloc(ctx, ptr, bytes);
+  };
+  A((void**)&y->d_valid, sizeof(int32_t) * y->n_valid);
+  A((void**)&y->d_sn, sizeof(float) * 2 * y->n_valid);
+  A((void**)&y->d_tw, sizeof(float2) * p.N);
+  A((void**)&y->d_mask, sizeof(float2) * p.N);
+  A((void**)&y->d_alpha, sizeof(float) * p.K);
+  A((void**)&y->d_beta, sizeof(float) * y->n_s);
+  A((void**)&y->d_kmap, sizeof(int) * p.K);
+  A((void**)&y->d_H, sizeof(float2) * (size_t)y->n_s * p.N * p.Np);
+  A((void**)&y->d_part, sizeof(float) * (size_t)y->G * y->nd * y->nd);
+  A((void**)&y->d_frame, sizeof(float) * y->nd * y->nd);
+  A((void**)&y->d_frame_ctr, sizeof(long long));
+  if (st != PAS_OK) {
+    pas_pyr_destroy(y);
+    return st;
+  }
+  cudaError_t e = cudaSuccess;
+  auto C = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  C(y->d_valid, valid.data(), sizeof(int32_t) * y->n_valid);
+  C(y->d_tw, tw.data(), sizeof(float2) * p.N);
+  C(y->d_mask, mk.data(), sizeof(float2) * p.N);
+  C(y->d_alpha, alpha.data(), sizeof(float) * p.K);
+  C(y->d_beta, beta.data(), sizeof(float) * y->n_s);
+  C(y->d_kmap, kmap.data(), sizeof(int) * p.K);
+  if (e == cudaSuccess) e = cudaMemset(y->d_sn, 0, sizeof(float) * 2 * y->n_valid);
+  if (e == cudaSuccess) e = cudaMemset(y->d_frame_ctr, 0, sizeof(long long));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern.rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)y->smem_rows);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern.cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)y->smem_cols);
+  if (e != cudaSuccess) {
+    pas_pyr_destroy(y);
+    return pas::set_error(ctx, PAS_ECUDA, "pas_pyr_create: %s", cudaGetErrorString(e));
+  }
+  *out = y;
+  return PAS_OK;
+}
+
+int32_t pas_pyr_n_valid(pas_pyr_t y) { return y ? y->n_valid : -1; }
+
+pas_status pas_pyr_get_valid(pas_pyr_t y, int32_t* h_valid, int32_t cap) {
+  if (!y || !h_valid) return pas::set_global_error(PAS_EINVAL, "pas_pyr_get_valid: NULL argument");
+  PAS_CHECK_ARG(y->ctx, cap >= y->n_valid, "pas_pyr_get_valid: cap too small");
+  PAS_CUDA_TRY(y->ctx, cudaMemcpy(h_valid, y->d_valid, sizeof(int32_t) * y->n_valid, cudaMemcpyDeviceToHost));
+  return PAS_OK;
+}
+
+pas_status pas_pyr_set_reference(pas_pyr_t y, const float* d_sn) {
+  if (!y) return pas::set_global_error(PAS_EINVAL, "pas_pyr_set_reference: NULL pyramid");
+  if (!d_sn) {
+    y->has_sn = false;
+    return PAS_OK;
+  }
+  PAS_CUDA_TRY(y->ctx, cudaMemcpyAsync(y->d_sn, d_sn, sizeof(float) * 2 * y->n_valid,
+                                       cudaMemcpyDeviceToDevice, y->ctx->stream));
+  y->has_sn = true;
+  return PAS_OK;
+}
+
+pas_status pas_pyr_set_noise(pas_pyr_t y, double photons, double ron, uint64_t seed, int64_t frame_index) {
+  if (!y) return pas::set_global_error(PAS_EINVAL, "pas_pyr_set_noise: NULL pyramid");
+  PAS_CHECK_ARG(y->ctx, ron >= 0.0 && frame_index >= 0, "pas_pyr_set_noise: bad read noise or frame index");
+  y->photon_scale = photons > 0.0 ? photons / (double)y->n_pupil : 0.0;
+  y->ron = ron;
+  y->seed = seed;
+  long long f = frame_index;
+  PAS_CUDA_TRY(y->ctx, cudaMemcpyAsync(y->d_frame_ctr, &f, sizeof(f), cudaMemcpyHostToDevice, y->ctx->stream));
+  PAS_CUDA_TRY(y->ctx, cudaStreamSynchronize(y->ctx->stream));
+  return PAS_OK;
+}
+
+pas_status pas_pyr_measure(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes) {
+  if (!y || !d_opd) return pas::set_global_error(PAS_EINVAL, "pas_pyr_measure: NULL argument");
+  return pas::pyr_launch(y, d_opd, d_frame, d_slopes, y->ctx->stream, nullptr, true);
+}
+
+pas_status pas_ccd_noise(pas_ctx_t ctx, const float* d_in, float* d_out, int32_t n, double photons,
+                         int32_t n_pupil_pixels, double ron, uint64_t seed, int64_t frame_index) {
+  if (!ctx || !d_in || !d_out) return pas::set_global_error(PAS_EINVAL, "pas_ccd_noise: NULL argument");
+  PAS_CHECK_ARG(ctx, n >= 0 && n_pupil_pixels > 0 && ron >= 0 && frame_index >= 0, "pas_ccd_noise: bad argument");
+  if (n == 0) return PAS_OK;
+  double scale = photons > 0.0 ? photons / (double)n_pupil_pixels : 0.0;
+  int threads = 256, blocks = (n + threads - 1) / threads;
+  pas::ccd_noise_kernel<<<blocks, threads, 0, ctx->stream>>>(d_in, d_out, n, scale, ron, seed, frame_index);
+  return pas::check_launch(ctx, "pas_ccd_noise launch");
+}
+
+}  // extern "C"

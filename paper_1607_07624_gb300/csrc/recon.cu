@@ -1,0 +1,165 @@
+// Modal reconstructor dmodes = R * slopes (Table 1 modalrec.recmat_tag) and the
+// integrator control c_t = c_{t-1} + g * dmodes (Table 1 control, type 'INT'),
+// fused into one kernel for the loop.
+//
+// The matrix-vector product reads every element of R once per step: it is bound
+// by memory bandwidth, so it runs on CUDA cores with 16-byte loads, one warp per
+// mode row, the slope vector staged in shared memory. PAS_BF16 stores R as
+// bfloat16 scaled per row (row max |R| = 1) with float32 accumulation.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "recon.cuh"
+
+namespace pas {
+
+__device__ inline float dot4(float4 a, float4 b, float acc) {
+  acc = fmaf(a.x, b.x, acc);
+  acc = fmaf(a.y, b.y, acc);
+  acc = fmaf(a.z, b.z, acc);
+  return fmaf(a.w, b.w, acc);
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(256) recon_kernel(ReconArgs a) {
+  extern __shared__ float4 s4[];  // [n_s_pad / 4]
+  float* s_s = reinterpret_cast<float*>(s4);
+  for (int t = threadIdx.x; t < a.n_s_pad; t += blockDim.x) s_s[t] = t < a.n_s ? a.s[t] : 0.f;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = blockIdx.x * 8 + warp;
+  if (m >= a.n_m) return;
+  float acc = 0.f;
+  if (BF16) {
+    const uint4* row = reinterpret_cast<const uint4*>(a.Rb + (size_t)m * a.n_s_pad);
+    const int nc = a.n_s_pad / 8;
+#pragma unroll 4
+    for (int c = lane; c < nc; c += 32) {
+      const uint4 u = __ldg(row + c);
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+      const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
+      const float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
+      acc = dot4(make_float4(f0.x, f0.y, f1.x, f1.y), s4[2 * c], acc);
+      acc = dot4(make_float4(f2.x, f2.y, f3.x, f3.y), s4[2 * c + 1], acc);
+    }
+  } else {
+    const float4* row = reinterpret_cast<const float4*>(a.R + (size_t)m * a.n_s_pad);
+    const int nc = a.n_s_pad / 4;
+#pragma unroll 4
+    for (int c = lane; c < nc; c += 32) acc = dot4(__ldg(row + c), s4[c], acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    const float dm = BF16 ? acc * a.scale[m] : acc;
+    if (a.dmodes) a.dmodes[m] = dm;
+    if (a.ring) {
+      const long long t = *a.step;
+      const float prev = a.ring[(size_t)((t - 1 + a.delay) % a.delay) * a.n_m + m];
+      const float c = fmaf(a.gain ? a.gain[m] : 1.0f, dm, prev);
+      a.ring[(size_t)(t % a.delay) * a.n_m + m] = c;
+      if (a.cmd_last) a.cmd_last[m] = c;
+    }
+  }
+}
+
+static uint16_t f32_to_bf16_rne(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  return (uint16_t)(u >> 16);
+}
+
+pas_status recon_launch(pas_recon_t r, ReconArgs a, cudaStream_t st) {
+  a.R = r->d_R;
+  a.Rb = r->d_Rb;
+  a.scale = r->d_scale;
+  a.n_m = r->n_modes;
+  a.n_s = r->n_slopes;
+  a.n_s_pad = r->n_s_pad;
+  const size_t smem = sizeof(float) * (size_t)r->n_s_pad;
+  const int grid = (r->n_modes + 7) / 8;
+  if (r->prec == PAS_BF16) recon_kernel<true><<<grid, 256, smem, st>>>(a);
+  else recon_kernel<false><<<grid, 256, smem, st>>>(a);
+  return check_launch(r->ctx, "reconstructor launch");
+}
+
+}  // namespace pas
+
+extern "C" {
+
+void pas_recon_destroy(pas_recon_t r) {
+  if (!r) return;
+  pas::dev_free(r->d_R);
+  pas::dev_free(r->d_Rb);
+  pas::dev_free(r->d_scale);
+  delete r;
+}
+
+pas_status pas_recon_create(pas_ctx_t ctx, const float* h_R, int32_t n_modes, int32_t n_slopes,
+                            pas_precision prec, pas_recon_t* out) {
+  if (!ctx || !h_R || !out) return pas::set_global_error(PAS_EINVAL, "pas_recon_create: NULL argument");
+  *out = nullptr;
+  PAS_CHECK_ARG(ctx, n_modes >= 1 && n_slopes >= 1, "pas_recon_create: bad sizes");
+  PAS_CHECK_ARG(ctx, prec == PAS_FP32 || prec == PAS_BF16, "pas_recon_create: bad precision");
+  pas_recon_t r = new pas_recon_s();
+  r->ctx = ctx;
+  r->n_modes = n_modes;
+  r->n_slopes = n_slopes;
+  r->n_s_pad = ((n_slopes + 7) / 8) * 8;
+  r->prec = prec;
+  const size_t smem = sizeof(float) * (size_t)r->n_s_pad;
+  pas_status st = PAS_OK;
+  cudaError_t e = cudaSuccess;
+  if (prec == PAS_FP32) {
+    std::vector<float> R((size_t)n_modes * r->n_s_pad, 0.f);
+    for (int m = 0; m < n_modes; ++m)
+      std::memcpy(&R[(size_t)m * r->n_s_pad], h_R + (size_t)m * n_slopes, sizeof(float) * n_slopes);
+    st = pas::dev_alloc(ctx, (void**)&r->d_R, sizeof(float) * R.size());
+    if (st == PAS_OK) e = cudaMemcpy(r->d_R, R.data(), sizeof(float) * R.size(), cudaMemcpyHostToDevice);
+    if (st == PAS_OK && e == cudaSuccess)
+      e = cudaFuncSetAttribute(pas::recon_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  } else {
+    std::vector<uint16_t> Rb((size_t)n_modes * r->n_s_pad, 0);
+    std::vector<float> scale(n_modes, 1.f);
+    for (int m = 0; m < n_modes; ++m) {
+      float mx = 0.f;
+      for (int j = 0; j < n_slopes; ++j) mx = std::max(mx, std::fabs(h_R[(size_t)m * n_slopes + j]));
+      scale[m] = mx > 0.f ? mx : 1.f;
+      for (int j = 0; j < n_slopes; ++j)
+        Rb[(size_t)m * r->n_s_pad + j] = pas::f32_to_bf16_rne(h_R[(size_t)m * n_slopes + j] / scale[m]);
+    }
+    st = pas::dev_alloc(ctx, (void**)&r->d_Rb, sizeof(uint16_t) * Rb.size());
+    if (st == PAS_OK) st = pas::dev_alloc(ctx, (void**)&r->d_scale, sizeof(float) * n_modes);
+    if (st == PAS_OK) e = cudaMemcpy(r->d_Rb, Rb.data(), sizeof(uint16_t) * Rb.size(), cudaMemcpyHostToDevice);
+    if (st == PAS_OK && e == cudaSuccess)
+      e = cudaMemcpy(r->d_scale, scale.data(), sizeof(float) * n_modes, cudaMemcpyHostToDevice);
+    if (st == PAS_OK && e == cudaSuccess)
+      e = cudaFuncSetAttribute(pas::recon_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  if (st != PAS_OK) {
+    pas_recon_destroy(r);
+    return st;
+  }
+  if (e != cudaSuccess) {
+    pas_recon_destroy(r);
+    return pas::set_error(ctx, PAS_ECUDA, "pas_recon_create: %s", cudaGetErrorString(e));
+  }
+  *out = r;
+  return PAS_OK;
+}
+
+pas_status pas_recon_apply(pas_recon_t r, const float* d_slopes, float* d_dmodes) {
+  if (!r || !d_slopes || !d_dmodes) return pas::set_global_error(PAS_EINVAL, "pas_recon_apply: NULL argument");
+  pas::ReconArgs a;
+  a.s = d_slopes;
+  a.dmodes = d_dmodes;
+  return pas::recon_launch(r, a, r->ctx->stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,339 @@
+"""Thin ctypes binding of libpas.so (include/pas.h): argument marshalling only.
+
+Every function keeps the C name; device buffers are passed as torch CUDA tensors
+(their data_ptr), host buffers as numpy arrays. A non-zero status raises
+PasError with the library's message. There is no fallback: if the library is not
+built, importing this module raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libpas.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+
+_lib = C.CDLL(LIB_PATH)
+
+PAS_OK, PAS_EINVAL, PAS_ENOMEM, PAS_ECUDA, PAS_ETIMEOUT, PAS_ESTATE = range(6)
+PAS_FP32, PAS_BF16 = 0, 1
+STATUS_NAMES = {0: "PAS_OK", 1: "PAS_EINVAL", 2: "PAS_ENOMEM", 3: "PAS_ECUDA", 4: "PAS_ETIMEOUT",
+                5: "PAS_ESTATE"}
+
+
+class PasError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pas_atmo_params(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("S", C.c_int32), ("Np", C.c_int32),
+                ("vx", C.POINTER(C.c_double)), ("vy", C.POINTER(C.c_double))]
+
+
+class pas_pyr_params(C.Structure):
+    _fields_ = [("Np", C.c_int32), ("N", C.c_int32), ("K", C.c_int32), ("n_sub", C.c_int32),
+                ("mod_radius", C.c_double), ("wavelength_nm", C.c_double), ("obs", C.c_double),
+                ("local_norm", C.c_int32)]
+
+
+class pas_loop_stats(C.Structure):
+    _fields_ = [("step", C.c_int64), ("wfe_nm", C.c_double)]
+
+
+vp = C.c_void_p
+i32 = C.c_int32
+i64 = C.c_int64
+f64 = C.c_double
+P = C.POINTER
+
+_SIGS = {
+    "pas_version": (C.c_int, []),
+    "pas_ctx_create": (C.c_int, [vp, P(vp)]),
+    "pas_ctx_destroy": (None, [vp]),
+    "pas_ctx_set_stream": (C.c_int, [vp, vp]),
+    "pas_ctx_synchronize": (C.c_int, [vp]),
+    "pas_last_error": (C.c_char_p, [vp]),
+    "pas_global_error": (C.c_char_p, []),
+    "pas_debug_fail_alloc_after": (None, [C.c_int]),
+    "pas_pupil_mask": (C.c_int, [C.c_int, f64, vp, P(i32)]),
+    "pas_pupil_pixels": (C.c_int, [C.c_int, f64, vp, i32, P(i32)]),
+    "pas_valid_subaps": (C.c_int, [C.c_int, f64, C.c_int, vp, i32, P(i32)]),
+    "pas_atmo_create": (C.c_int, [vp, P(pas_atmo_params), vp, P(vp)]),
+    "pas_atmo_advance": (C.c_int, [vp, i64, vp]),
+    "pas_atmo_destroy": (None, [vp]),
+    "pas_pyr_supported": (C.c_int, [C.c_int]),
+    "pas_pyr_create": (C.c_int, [vp, P(pas_pyr_params), vp, i32, P(vp)]),
+    "pas_pyr_n_valid": (i32, [vp]),
+    "pas_pyr_get_valid": (C.c_int, [vp, vp, i32]),
+    "pas_pyr_set_reference": (C.c_int, [vp, vp]),
+    "pas_pyr_set_noise": (C.c_int, [vp, f64, f64, C.c_uint64, i64]),
+    "pas_pyr_measure": (C.c_int, [vp, vp, vp, vp]),
+    "pas_ccd_noise": (C.c_int, [vp, vp, vp, i32, f64, i32, f64, C.c_uint64, i64]),
+    "pas_pyr_destroy": (None, [vp]),
+    "pas_recon_create": (C.c_int, [vp, vp, i32, i32, C.c_int, P(vp)]),
+    "pas_recon_apply": (C.c_int, [vp, vp, vp]),
+    "pas_recon_destroy": (None, [vp]),
+    "pas_dm_create": (C.c_int, [vp, vp, i32, i32, i32, f64, C.c_int, P(vp)]),
+    "pas_dm_update": (C.c_int, [vp, vp, vp, vp, vp]),
+    "pas_dm_residual": (C.c_int, [vp, vp, vp, vp]),
+    "pas_dm_destroy": (None, [vp]),
+    "pas_loop_create": (C.c_int, [vp, vp, vp, vp, vp, vp, i32, i32, P(vp)]),
+    "pas_loop_step": (C.c_int, [vp, i32, P(pas_loop_stats)]),
+    "pas_loop_step_eager": (C.c_int, [vp, i32]),
+    "pas_loop_buffers": (C.c_int, [vp, P(vp), P(vp), P(vp), P(vp), P(vp), P(vp)]),
+    "pas_loop_get_state": (C.c_int, [vp, P(i64), vp]),
+    "pas_loop_set_state": (C.c_int, [vp, i64, vp]),
+    "pas_loop_destroy": (None, [vp]),
+    "pas_loop_profile": (C.c_int, [vp, i32, vp, i32, P(i32)]),
+    "pas_loop_kernel_name": (C.c_char_p, [i32]),
+}
+
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor / host pointer of a numpy array / None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return int(x)
+
+
+def _check(st: int, ctx=None):
+    if st != PAS_OK:
+        msg = (_lib.pas_last_error(ctx) if ctx else _lib.pas_global_error()) or b""
+        raise PasError(st, msg.decode(errors="replace"))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ------------------------------------------------------------------ functions
+
+def pas_version() -> int:
+    return _lib.pas_version()
+
+
+def pas_ctx_create(stream=None):
+    h = vp()
+    _check(_lib.pas_ctx_create(_stream_handle(stream), C.byref(h)))
+    return h
+
+
+def pas_ctx_destroy(ctx):
+    _lib.pas_ctx_destroy(ctx)
+
+
+def pas_ctx_set_stream(ctx, stream):
+    _check(_lib.pas_ctx_set_stream(ctx, _stream_handle(stream)), ctx)
+
+
+def pas_ctx_synchronize(ctx):
+    _check(_lib.pas_ctx_synchronize(ctx), ctx)
+
+
+def pas_last_error(ctx) -> str:
+    return (_lib.pas_last_error(ctx) or b"").decode()
+
+
+def pas_debug_fail_alloc_after(n: int):
+    _lib.pas_debug_fail_alloc_after(int(n))
+
+
+def pas_pupil_mask(Np: int, obs: float) -> np.ndarray:
+    m = np.zeros((Np, Np), dtype=np.uint8)
+    n = i32()
+    _check(_lib.pas_pupil_mask(Np, obs, m.ctypes.data, C.byref(n)))
+    return m
+
+
+def pas_pupil_pixels(Np: int, obs: float) -> np.ndarray:
+    n = i32()
+    _check(_lib.pas_pupil_pixels(Np, obs, None, 0, C.byref(n)))
+    out = np.zeros(n.value, dtype=np.int32)
+    _check(_lib.pas_pupil_pixels(Np, obs, out.ctypes.data, n.value, C.byref(n)))
+    return out
+
+
+def pas_valid_subaps(Np: int, obs: float, n_sub: int) -> np.ndarray:
+    n = i32()
+    _check(_lib.pas_valid_subaps(Np, obs, n_sub, None, 0, C.byref(n)))
+    out = np.zeros(n.value, dtype=np.int32)
+    _check(_lib.pas_valid_subaps(Np, obs, n_sub, out.ctypes.data, n.value, C.byref(n)))
+    return out
+
+
+def pas_atmo_create(ctx, n_layers, S, Np, vx, vy, d_screens):
+    vx = np.ascontiguousarray(vx, dtype=np.float64)
+    vy = np.ascontiguousarray(vy, dtype=np.float64)
+    p = pas_atmo_params(n_layers, S, Np, vx.ctypes.data_as(P(C.c_double)), vy.ctypes.data_as(P(C.c_double)))
+    h = vp()
+    _check(_lib.pas_atmo_create(ctx, C.byref(p), _ptr(d_screens), C.byref(h)), ctx)
+    return h
+
+
+def pas_atmo_advance(atmo, ctx, step: int, d_opd):
+    _check(_lib.pas_atmo_advance(atmo, int(step), _ptr(d_opd)), ctx)
+
+
+def pas_atmo_destroy(atmo):
+    _lib.pas_atmo_destroy(atmo)
+
+
+def pas_pyr_supported(N: int) -> bool:
+    return bool(_lib.pas_pyr_supported(N))
+
+
+def pas_pyr_create(ctx, Np, N, K, n_sub, mod_radius, wavelength_nm, obs, valid=None, local_norm=0):
+    p = pas_pyr_params(Np, N, K, n_sub, mod_radius, wavelength_nm, obs, local_norm)
+    h = vp()
+    if valid is not None:
+        valid = np.ascontiguousarray(valid, dtype=np.int32)
+        _check(_lib.pas_pyr_create(ctx, C.byref(p), valid.ctypes.data, valid.size, C.byref(h)), ctx)
+    else:
+        _check(_lib.pas_pyr_create(ctx, C.byref(p), None, 0, C.byref(h)), ctx)
+    return h
+
+
+def pas_pyr_n_valid(pyr) -> int:
+    return _lib.pas_pyr_n_valid(pyr)
+
+
+def pas_pyr_get_valid(pyr, ctx) -> np.ndarray:
+    n = _lib.pas_pyr_n_valid(pyr)
+    out = np.zeros(n, dtype=np.int32)
+    _check(_lib.pas_pyr_get_valid(pyr, out.ctypes.data, n), ctx)
+    return out
+
+
+def pas_pyr_set_reference(pyr, ctx, d_sn):
+    _check(_lib.pas_pyr_set_reference(pyr, _ptr(d_sn)), ctx)
+
+
+def pas_pyr_set_noise(pyr, ctx, photons, read_noise_e, seed, frame_index=0):
+    _check(_lib.pas_pyr_set_noise(pyr, float(photons), float(read_noise_e), int(seed), int(frame_index)), ctx)
+
+
+def pas_pyr_measure(pyr, ctx, d_opd, d_frame=None, d_slopes=None):
+    _check(_lib.pas_pyr_measure(pyr, _ptr(d_opd), _ptr(d_frame), _ptr(d_slopes)), ctx)
+
+
+def pas_ccd_noise(ctx, d_in, d_out, photons, n_pupil_pixels, read_noise_e, seed, frame_index):
+    _check(_lib.pas_ccd_noise(ctx, _ptr(d_in), _ptr(d_out), d_in.numel(), float(photons),
+                              int(n_pupil_pixels), float(read_noise_e), int(seed), int(frame_index)), ctx)
+
+
+def pas_pyr_destroy(pyr):
+    _lib.pas_pyr_destroy(pyr)
+
+
+def pas_recon_create(ctx, R: np.ndarray, precision=PAS_FP32):
+    R = np.ascontiguousarray(R, dtype=np.float32)
+    h = vp()
+    _check(_lib.pas_recon_create(ctx, R.ctypes.data, R.shape[0], R.shape[1], precision, C.byref(h)), ctx)
+    return h
+
+
+def pas_recon_apply(rec, ctx, d_slopes, d_dmodes):
+    _check(_lib.pas_recon_apply(rec, _ptr(d_slopes), _ptr(d_dmodes)), ctx)
+
+
+def pas_recon_destroy(rec):
+    _lib.pas_recon_destroy(rec)
+
+
+def pas_dm_create(ctx, M: np.ndarray, Np: int, obs: float, precision=PAS_FP32):
+    M = np.ascontiguousarray(M, dtype=np.float32)
+    h = vp()
+    _check(_lib.pas_dm_create(ctx, M.ctypes.data, M.shape[0], M.shape[1], Np, obs, precision, C.byref(h)), ctx)
+    return h
+
+
+def pas_dm_update(dm, ctx, d_dmodes, d_gain, d_cmd, d_opd_dm):
+    _check(_lib.pas_dm_update(dm, _ptr(d_dmodes), _ptr(d_gain), _ptr(d_cmd), _ptr(d_opd_dm)), ctx)
+
+
+def pas_dm_residual(dm, ctx, d_opd_atm, d_cmd, d_opd_res):
+    _check(_lib.pas_dm_residual(dm, _ptr(d_opd_atm), _ptr(d_cmd), _ptr(d_opd_res)), ctx)
+
+
+def pas_dm_destroy(dm):
+    _lib.pas_dm_destroy(dm)
+
+
+def pas_loop_create(ctx, atmo, pyr, rec, dm, d_gain, delay=1, wfe_history=1):
+    h = vp()
+    _check(_lib.pas_loop_create(ctx, atmo, pyr, rec, dm, _ptr(d_gain), delay, wfe_history, C.byref(h)), ctx)
+    return h
+
+
+def pas_loop_step(loop, ctx, n_steps=1, stats=False):
+    if stats:
+        s = pas_loop_stats()
+        _check(_lib.pas_loop_step(loop, n_steps, C.byref(s)), ctx)
+        return s.step, s.wfe_nm
+    _check(_lib.pas_loop_step(loop, n_steps, None), ctx)
+    return None
+
+
+def pas_loop_step_eager(loop, ctx, n_steps=1):
+    _check(_lib.pas_loop_step_eager(loop, n_steps), ctx)
+
+
+def pas_loop_buffers(loop, ctx):
+    ptrs = [vp() for _ in range(6)]
+    _check(_lib.pas_loop_buffers(loop, *[C.byref(p) for p in ptrs]), ctx)
+    names = ("opd_res", "frame", "slopes", "dmodes", "cmd", "wfe")
+    return {n: p.value for n, p in zip(names, ptrs)}
+
+
+def pas_loop_get_state(loop, ctx, n_modes: int, delay: int):
+    step = i64()
+    ring = np.zeros((delay, n_modes), dtype=np.float32)
+    _check(_lib.pas_loop_get_state(loop, C.byref(step), ring.ctypes.data), ctx)
+    return step.value, ring
+
+
+def pas_loop_set_state(loop, ctx, step: int, ring: np.ndarray):
+    ring = np.ascontiguousarray(ring, dtype=np.float32)
+    _check(_lib.pas_loop_set_state(loop, int(step), ring.ctypes.data), ctx)
+
+
+def pas_loop_destroy(loop):
+    _lib.pas_loop_destroy(loop)
+
+
+def pas_loop_profile(loop, ctx, n_steps=1):
+    """Mean per-kernel duration [ms] of n_steps eager steps: {kernel name: ms}."""
+    ms = np.zeros(16, dtype=np.float32)
+    n = i32()
+    _check(_lib.pas_loop_profile(loop, int(n_steps), ms.ctypes.data, ms.size, C.byref(n)), ctx)
+    return {_lib.pas_loop_kernel_name(k).decode(): float(ms[k]) for k in range(n.value)}
+
+
+def pas_loop_kernel_name(idx: int):
+    r = _lib.pas_loop_kernel_name(int(idx))
+    return r.decode() if r else None
+
+
+def loaded_library_path() -> str:
+    return LIB_PATH

@@ -1,0 +1,154 @@
+"""SCAO system: the paper's processing-object chain built on libpas.so.
+
+Mirrors the main file of the paper's example (Table 2): build the processing
+objects from the parameters, connect them, calibrate (pupil indices, slope
+reference, reconstruction matrix), then run the loop control. Device memory and
+streams come from PyTorch; every per-step operation runs in libpas.so.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import calib
+from . import pas as P
+
+
+class DevView:
+    """Zero-copy torch view of library-owned device memory."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+    @staticmethod
+    def tensor(ptr, shape, dtype="<f4"):
+        return torch.as_tensor(DevView(ptr, shape, dtype), device="cuda")
+
+
+class SCAOSystem:
+    """Single-conjugate AO loop with a modulated pyramid, for one configuration.
+
+    screens: float32 (L, S, S) OPD [nm] (host numpy or None: generated from the
+    configuration's seeds); basis: float (n_pix, n_modes) (None: Zernike);
+    R: reconstruction matrix (None: calibrated by push-pull on the GPU)."""
+
+    def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32,
+                 noise=None, delay=None, wfe_history=4096, stream=None, build_loop=True):
+        from synth.inputs import layer_seeds, screen_white_noise
+        self.cfg = cfg
+        self.dev = torch.device("cuda")
+        self.stream = stream or torch.cuda.current_stream()
+        self.ctx = P.pas_ctx_create(self.stream)
+        self.pix = P.pas_pupil_pixels(cfg.Np, cfg.obs)
+        self.valid = P.pas_valid_subaps(cfg.Np, cfg.obs, cfg.n_sub)
+        self.n_pix, self.n_valid = self.pix.size, self.valid.size
+        # atmosphere
+        if screens is None:
+            noises = [screen_white_noise(cfg.S, s) for s in layer_seeds(cfg.seed, len(cfg.layers))]
+            screens = calib.layer_screens(cfg, noises)
+        self.d_screens = torch.as_tensor(np.ascontiguousarray(screens, dtype=np.float32)).to(self.dev)
+        vel = np.array(cfg.layer_velocity_px(), dtype=np.float64).reshape(-1, 2)
+        self.atmo = P.pas_atmo_create(self.ctx, len(cfg.layers), cfg.S, cfg.Np, vel[:, 0], vel[:, 1],
+                                      self.d_screens)
+        # pyramid + slope computer
+        self.pyr = P.pas_pyr_create(self.ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius,
+                                    cfg.wavelength_nm, cfg.obs, self.valid)
+        # DM
+        if basis is None:
+            basis = calib.zernike_basis(cfg.Np, self.pix, cfg.n_modes)
+        self.basis = np.ascontiguousarray(basis, dtype=np.float32)
+        self.n_modes = self.basis.shape[1]
+        self.dm = P.pas_dm_create(self.ctx, self.basis, cfg.Np, cfg.obs)
+        # buffers
+        f32 = dict(device=self.dev, dtype=torch.float32)
+        self.d_opd = torch.zeros(cfg.Np, cfg.Np, **f32)
+        self.d_frame = torch.zeros(cfg.n_det, cfg.n_det, **f32)
+        self.d_slopes = torch.zeros(2 * self.n_valid, **f32)
+        self.d_sn = torch.zeros(2 * self.n_valid, **f32)
+        # calibration: slope reference (flat wavefront, noiseless)
+        P.pas_pyr_set_reference(self.pyr, self.ctx, None)
+        self.measure(self.d_opd, reference=True)
+        self.d_sn.copy_(self.d_slopes)
+        P.pas_pyr_set_reference(self.pyr, self.ctx, self.d_sn)
+        if R is None:
+            R = self.calibrate_reconstructor()
+        self.R = np.ascontiguousarray(R, dtype=np.float32)
+        self.rec = P.pas_recon_create(self.ctx, self.R, recon_precision)
+        self.d_gain = torch.full((self.n_modes,), cfg.gain, **f32)
+        if noise is None and cfg.magnitude is not None:
+            noise = (cfg.photons_per_frame(), cfg.read_noise_e, cfg.seed)
+        if noise is not None:
+            P.pas_pyr_set_noise(self.pyr, self.ctx, noise[0], noise[1], noise[2], 0)
+        self.delay = cfg.delay if delay is None else delay
+        self.loop = None
+        if build_loop:
+            self.loop = P.pas_loop_create(self.ctx, self.atmo, self.pyr, self.rec, self.dm, self.d_gain,
+                                          self.delay, wfe_history)
+            b = P.pas_loop_buffers(self.loop, self.ctx)
+            self.wfe_history = wfe_history
+            self.loop_opd = DevView.tensor(b["opd_res"], (cfg.Np, cfg.Np))
+            self.loop_frame = DevView.tensor(b["frame"], (cfg.n_det, cfg.n_det))
+            self.loop_slopes = DevView.tensor(b["slopes"], (2 * self.n_valid,))
+            self.loop_dmodes = DevView.tensor(b["dmodes"], (self.n_modes,))
+            self.loop_cmd = DevView.tensor(b["cmd"], (self.n_modes,))
+            self.loop_wfe = DevView.tensor(b["wfe"], (wfe_history,), "<f8")
+
+    # ---------------------------------------------------------------- steps
+    def measure(self, d_opd, reference=False):
+        """opd -> (frame, slopes) through pas_pyr_measure (device tensors)."""
+        P.pas_pyr_measure(self.pyr, self.ctx, d_opd, self.d_frame, self.d_slopes)
+        return self.d_frame, self.d_slopes
+
+    def calibrate_reconstructor(self, amp_nm=None, rcond=1e-3):
+        """Push-pull interaction matrix measured by the GPU pyramid; FP64 pinv."""
+        amp = self.cfg.pushpull_nm if amp_nm is None else amp_nm
+        cmd = torch.zeros(self.n_modes, device=self.dev, dtype=torch.float32)
+        opd = torch.zeros(self.cfg.Np, self.cfg.Np, device=self.dev, dtype=torch.float32)
+        IM = torch.zeros(2 * self.n_valid, self.n_modes, device=self.dev, dtype=torch.float64)
+        for m in range(self.n_modes):
+            cols = []
+            for sgn in (1.0, -1.0):
+                cmd.zero_()
+                cmd[m] = sgn * amp
+                P.pas_dm_update(self.dm, self.ctx, None, None, cmd, opd)
+                self.measure(opd)
+                cols.append(self.d_slopes.double().clone())
+            IM[:, m] = (cols[0] - cols[1]) / (2.0 * amp)
+        self.IM = IM.cpu().numpy()
+        return calib.pseudo_inverse(self.IM, rcond)
+
+    def step(self, n=1, stats=False):
+        return P.pas_loop_step(self.loop, self.ctx, n, stats)
+
+    def step_eager(self, n=1):
+        P.pas_loop_step_eager(self.loop, self.ctx, n)
+
+    def wfe_nm(self, n_steps):
+        """Per-step residual WFE [nm] of the first n_steps (n_steps <= history)."""
+        torch.cuda.synchronize()
+        return self.loop_wfe[:n_steps].cpu().numpy().copy()
+
+    def get_state(self):
+        return P.pas_loop_get_state(self.loop, self.ctx, self.n_modes, self.delay)
+
+    def set_state(self, step, ring):
+        P.pas_loop_set_state(self.loop, self.ctx, step, ring)
+
+    def close(self):
+        for h, f in ((getattr(self, "loop", None), P.pas_loop_destroy), (getattr(self, "rec", None), P.pas_recon_destroy),
+                     (getattr(self, "dm", None), P.pas_dm_destroy), (getattr(self, "pyr", None), P.pas_pyr_destroy),
+                     (getattr(self, "atmo", None), P.pas_atmo_destroy)):
+            if h:
+                f(h)
+        self.loop = self.rec = self.dm = self.pyr = self.atmo = None
+        if getattr(self, "ctx", None):
+            torch.cuda.synchronize()
+            P.pas_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

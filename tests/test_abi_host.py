@@ -1,0 +1,90 @@
+"""C-ABI library: loads without a GPU, exports every declared symbol, and its
+host-side integer geometry is bit-exact with the oracle. Also the product's host
+setup (screens, modal basis) against the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1607_07624_gb300 import build
+    build.build()
+    from paper_1607_07624_gb300 import pas
+    return pas
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pas.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pas_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import ctypes
+    names = declared_functions()
+    assert len(names) >= 30
+    so = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+    # the binding covers the whole header with the same names
+    assert sorted(lib.EXPORTED) == names
+
+
+def test_version_and_supported_sizes(lib):
+    assert lib.pas_version() >= 100
+    for N in (16, 24, 32, 48, 64, 128, 480, 960):
+        assert lib.pas_pyr_supported(N)
+    assert not lib.pas_pyr_supported(7) and not lib.pas_pyr_supported(1000)
+
+
+@pytest.mark.parametrize("Np,obs,n_sub", [(64, 0.1, 16), (240, 0.1, 30), (480, 0.1, 96),
+                                          (16, 0.1, 4), (24, 0.0, 4), (60, 0.25, 10)])
+def test_geometry_bit_exact_with_oracle(lib, Np, obs, n_sub):
+    from oracle import optics as op
+    m = op.pupil_mask(Np, obs)
+    assert np.array_equal(lib.pas_pupil_mask(Np, obs).astype(bool), m)
+    assert np.array_equal(lib.pas_pupil_pixels(Np, obs), np.flatnonzero(m.ravel()).astype(np.int32))
+    assert np.array_equal(lib.pas_valid_subaps(Np, obs, n_sub), op.valid_subapertures(Np, obs, n_sub))
+
+
+def test_geometry_rejects_bad_arguments(lib):
+    with pytest.raises(lib.PasError) as e:
+        lib.pas_valid_subaps(30, 0.1, 7)
+    assert e.value.status == lib.PAS_EINVAL
+    with pytest.raises(lib.PasError):
+        lib.pas_pupil_mask(16, 1.5)
+
+
+def test_product_screens_match_oracle():
+    from oracle import atmosphere as at
+    from paper_1607_07624_gb300 import calib
+    from synth import get_config
+    from synth.configs import with_
+    from synth.inputs import screen_white_noise
+    cfg = with_(get_config(2), S=256)
+    w = [screen_white_noise(256, 3 + l) for l in range(3)]
+    a = calib.layer_screens(cfg, w).astype(np.float64)
+    b = at.layer_screens_nm(cfg, w)
+    assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b))
+
+
+def test_product_basis_matches_oracle():
+    from oracle import modal as md
+    from oracle import optics as op
+    from paper_1607_07624_gb300 import calib
+    idx = np.flatnonzero(op.pupil_mask(64, 0.1).ravel())
+    assert np.max(np.abs(calib.zernike_basis(64, idx, 100) - md.modal_basis(64, 0.1, 100))) < 1e-9
+    for j in range(1, 300):
+        assert calib.noll_nm(j) == md.noll_to_nm(j)
+
+
+def test_product_pinv_matches_oracle():
+    from oracle import modal as md
+    from paper_1607_07624_gb300 import calib
+    IM = np.random.default_rng(5).standard_normal((80, 30))
+    assert np.max(np.abs(calib.pseudo_inverse(IM) - md.pseudo_inverse(IM))) < 1e-12

@@ -1,0 +1,126 @@
+"""GPU atmosphere, DM, reconstructor and detector noise against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from synth import get_config, tiny_config
+from synth.inputs import random_matrix, random_vector
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_1607_07624_gb300 import pas
+    ctx = pas.pas_ctx_create()
+    yield torch, pas, ctx
+    torch.cuda.synchronize()
+    pas.pas_ctx_destroy(ctx)
+
+
+def test_atmosphere_matches_oracle_and_integer_shift_is_exact(env):
+    torch, pas, ctx = env
+    from oracle import atmosphere as at
+    S, Np = 256, 60
+    scr = np.random.default_rng(3).standard_normal((3, S, S)).astype(np.float32) * 100
+    vel = np.array([[0.37, -0.81], [1.0, 0.0], [-2.0, 3.0]])
+    d_scr = torch.as_tensor(scr).cuda()
+    atmo = pas.pas_atmo_create(ctx, 3, S, Np, vel[:, 0], vel[:, 1], d_scr)
+    out = torch.zeros(Np, Np, device="cuda")
+    try:
+        for step in (0, 1, 7, 123, 1000):
+            pas.pas_atmo_advance(atmo, ctx, step, out)
+            torch.cuda.synchronize()
+            g = out.cpu().numpy().astype(np.float64)
+            o = at.atmo_opd(scr.astype(np.float64), vel, step, Np)
+            assert np.max(np.abs(g - o)) <= 1e-6 * np.max(np.abs(o)), step
+        # integer velocities only: exact copy of the screen sum
+        atmo2 = pas.pas_atmo_create(ctx, 2, S, Np, vel[1:, 0], vel[1:, 1], d_scr[1:])
+        pas.pas_atmo_advance(atmo2, ctx, 77, out)
+        torch.cuda.synchronize()
+        o = at.atmo_opd(scr[1:].astype(np.float64), vel[1:], 77, Np).astype(np.float32)
+        assert np.array_equal(out.cpu().numpy(), o)
+        pas.pas_atmo_destroy(atmo2)
+    finally:
+        pas.pas_atmo_destroy(atmo)
+
+
+@pytest.mark.parametrize("Np,n_modes", [(16, 10), (64, 100), (240, 400)])
+def test_dm_shape_and_residual_match_oracle(env, Np, n_modes):
+    torch, pas, ctx = env
+    from oracle import modal as md
+    from oracle import optics as op
+    M = md.modal_basis(Np, 0.1, n_modes)
+    mask = op.pupil_mask(Np, 0.1)
+    dm = pas.pas_dm_create(ctx, M, Np, 0.1)
+    try:
+        c = random_vector(n_modes, 11, 20.0).astype(np.float32)
+        d_c = torch.as_tensor(c).cuda()
+        opd = torch.zeros(Np, Np, device="cuda")
+        pas.pas_dm_update(dm, ctx, None, None, d_c, opd)
+        atm = (np.random.default_rng(2).standard_normal((Np, Np)) * 50).astype(np.float32)
+        res = torch.as_tensor(atm).cuda()
+        pas.pas_dm_residual(dm, ctx, res, d_c, res)     # in place
+        torch.cuda.synchronize()
+        ref = md.basis_to_grid(M.astype(np.float32).astype(np.float64), c.astype(np.float64), mask)
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(opd.cpu().numpy() - ref)) <= 2e-6 * scale * math.sqrt(n_modes)
+        r_ref = np.where(mask, atm.astype(np.float64) - ref, 0.0)
+        assert np.max(np.abs(res.cpu().numpy() - r_ref)) <= 2e-6 * (scale + 200) * math.sqrt(n_modes)
+        # integrator: cmd += g * dmodes
+        dmodes = torch.as_tensor(random_vector(n_modes, 12).astype(np.float32)).cuda()
+        gain = torch.full((n_modes,), 0.5, device="cuda")
+        c2 = d_c.clone()
+        pas.pas_dm_update(dm, ctx, dmodes, gain, c2, None)
+        torch.cuda.synchronize()
+        assert torch.allclose(c2, d_c + 0.5 * dmodes, rtol=0, atol=1e-6)
+    finally:
+        pas.pas_dm_destroy(dm)
+
+
+@pytest.mark.parametrize("n_m,n_s", [(100, 416), (400, 1424), (37, 13), (4000, 14312)])
+def test_reconstructor_fp32_and_bf16(env, n_m, n_s):
+    torch, pas, ctx = env
+    R = random_matrix(n_m, n_s, 21, 1.0 / math.sqrt(n_s)).astype(np.float32)
+    s = random_vector(n_s, 22, 0.05).astype(np.float32)
+    exact = R.astype(np.float64) @ s.astype(np.float64)
+    d_s = torch.as_tensor(s).cuda()
+    out = torch.zeros(n_m, device="cuda")
+    for prec in (pas.PAS_FP32, pas.PAS_BF16):
+        rec = pas.pas_recon_create(ctx, R, prec)
+        try:
+            pas.pas_recon_apply(rec, ctx, d_s, out)
+            torch.cuda.synchronize()
+            g = out.cpu().numpy().astype(np.float64)
+            if prec == pas.PAS_FP32:
+                tol = 1e-5 * np.max(np.abs(exact)) + 1e-7
+                assert np.max(np.abs(g - exact)) <= tol
+            else:
+                rel = np.sqrt(np.mean((g - exact) ** 2)) / np.sqrt(np.mean(exact ** 2))
+                assert rel <= 0.01, rel
+        finally:
+            pas.pas_recon_destroy(rec)
+
+
+def test_detector_noise_matches_oracle_counts(env):
+    torch, pas, ctx = env
+    from oracle import noise as nz
+    fr = (np.random.default_rng(7).random((60, 60)) * 3.0).astype(np.float32)
+    fr[:5] = 0.0
+    photons, npup, ron, seed = 5.3e4, 2848, 0.5, 1000
+    d_in = torch.as_tensor(fr).cuda()
+    d_out = torch.zeros_like(d_in)
+    for frame_index in (0, 17):
+        pas.pas_ccd_noise(ctx, d_in, d_out, photons, npup, ron, seed, frame_index)
+        torch.cuda.synchronize()
+        g = d_out.cpu().numpy().astype(np.float64)
+        o = nz.apply_noise(fr.astype(np.float64), photons, npup, ron, seed, frame_index)
+        close = np.abs(g - o) <= 1e-4 * np.maximum(1.0, np.abs(o))
+        assert close.mean() >= 0.999, close.mean()
+        # photon counts alone (no read noise): integers equal
+    pas.pas_ccd_noise(ctx, d_in, d_out, photons, npup, 0.0, seed, 3)
+    torch.cuda.synchronize()
+    o = nz.apply_noise(fr.astype(np.float64), photons, npup, 0.0, seed, 3)
+    assert np.mean(d_out.cpu().numpy() == o) >= 0.999

@@ -1,0 +1,151 @@
+"""GPU pyramid (pas_pyr_measure) against the FP64 oracle, element by element.
+
+Inputs are seeded OPD maps in float32; the oracle promotes the same float32 values
+to float64, so the test judges the pyramid path alone. Tolerances (FP32 path):
+  frame:  max |dI| <= 1e-5 * max |I_oracle|
+  slopes: max |ds| <= 1e-5 * max |s_oracle| + 1e-7
+Index maps (valid sub-apertures) are compared bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from synth import get_config, tiny_config
+from synth.configs import with_
+from synth.inputs import random_opd_nm, screen_white_noise
+
+pytestmark = pytest.mark.gpu
+
+FRAME_TOL = 1e-5
+SLOPE_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_1607_07624_gb300 import pas
+    assert torch.cuda.is_available()
+    ctx = pas.pas_ctx_create()
+    yield torch, pas, ctx
+    torch.cuda.synchronize()
+    pas.pas_ctx_destroy(ctx)
+
+
+def open_loop_opd(cfg, seed):
+    """An open-loop atmospheric OPD sample (tens of radians) from an oracle screen."""
+    from oracle import atmosphere as at
+    S = max(64, 1 << (2 * cfg.Np - 1).bit_length())
+    scr = at.phase_screen_rad(S, cfg.dx, cfg.r0_m, cfg.L0_m, screen_white_noise(S, seed))
+    return scr[:cfg.Np, :cfg.Np] * 500.0 / (2 * math.pi)
+
+
+def run_gpu(env, cfg, opd32, valid=None):
+    torch, pas, ctx = env
+    pyr = pas.pas_pyr_create(ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius, cfg.wavelength_nm,
+                             cfg.obs, valid)
+    try:
+        d_opd = torch.as_tensor(opd32).cuda()
+        nv = pas.pas_pyr_n_valid(pyr)
+        fr = torch.zeros(cfg.n_det, cfg.n_det, device="cuda")
+        sl = torch.zeros(2 * nv, device="cuda")
+        pas.pas_pyr_measure(pyr, ctx, d_opd, fr, sl)
+        torch.cuda.synchronize()
+        return fr.cpu().numpy().astype(np.float64), sl.cpu().numpy().astype(np.float64), \
+            pas.pas_pyr_get_valid(pyr, ctx)
+    finally:
+        pas.pas_pyr_destroy(pyr)
+
+
+def oracle_measure(cfg, opd32, valid):
+    from oracle import optics as op
+    I = op.pwfs_intensity(opd32.astype(np.float64), cfg.wavelength_nm, cfg.obs, cfg.N, cfg.K,
+                          cfg.mod_radius, cfg.delta)
+    fr = op.bin_detector(I, cfg.b)
+    return fr, op.pwfs_slopes(fr, valid, cfg.n_sub)
+
+
+def check(cfg, fr_g, sl_g, fr_o, sl_o):
+    ef = np.max(np.abs(fr_g - fr_o)) / np.max(np.abs(fr_o))
+    es = np.max(np.abs(sl_g - sl_o))
+    assert ef <= FRAME_TOL, f"{cfg.name}: frame rel err {ef:.3e}"
+    assert es <= SLOPE_TOL * np.max(np.abs(sl_o)) + 1e-7, f"{cfg.name}: slope err {es:.3e}"
+    return ef, es
+
+
+TINY = [
+    tiny_config(Np=8, N=16, n_sub=2, K=4),          # radices 4,4
+    tiny_config(Np=12, N=24, n_sub=3, K=6),         # 3,8
+    tiny_config(Np=20, N=40, n_sub=5, K=5),         # 5,8, odd K (no shared rows pass)
+    tiny_config(Np=24, N=48, n_sub=4, K=8),         # 3,4,4, b = 6
+    tiny_config(Np=40, N=80, n_sub=10, K=12),       # 5,4,4
+    tiny_config(Np=60, N=120, n_sub=10, K=12, mod_radius=3.0),  # 5,3,8
+    tiny_config(Np=16, N=32, n_sub=4, K=1, mod_radius=0.0),     # unmodulated
+    tiny_config(Np=80, N=160, n_sub=20, K=16, obs=0.3),
+    tiny_config(Np=96, N=192, n_sub=16, K=8),
+    tiny_config(Np=120, N=240, n_sub=24, K=10),
+]
+
+
+@pytest.mark.parametrize("cfg", TINY, ids=lambda c: f"N{c.N}_K{c.K}")
+def test_small_grids_match_oracle(env, cfg):
+    from oracle import optics as op
+    opd = random_opd_nm(cfg.Np, 250.0, seed=cfg.N + cfg.K).astype(np.float32)
+    fr_g, sl_g, valid = run_gpu(env, cfg, opd)
+    assert np.array_equal(valid, op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub))
+    check(cfg, fr_g, sl_g, *oracle_measure(cfg, opd, valid))
+
+
+@pytest.mark.parametrize("idx", [1, 2, 3])
+def test_full_size_configs_open_loop_phase(env, idx):
+    """Full-size N = 128 / 480 / 960 grids on an open-loop screen sample (the phasor
+    sees tens of radians)."""
+    cfg = get_config(idx)
+    opd = open_loop_opd(cfg, 4000 + idx).astype(np.float32)
+    assert np.ptp(opd) * 2 * math.pi / cfg.wavelength_nm > 20.0
+    fr_g, sl_g, valid = run_gpu(env, cfg, opd)
+    check(cfg, fr_g, sl_g, *oracle_measure(cfg, opd, valid))
+
+
+def test_flat_wavefront_and_parseval(env):
+    from oracle import optics as op
+    cfg = get_config(1)
+    fr_g, sl_g, valid = run_gpu(env, cfg, np.zeros((cfg.Np, cfg.Np), np.float32))
+    n = cfg.n_sub
+    tots = [fr_g[:n, :n].sum(), fr_g[:n, n:].sum(), fr_g[n:, :n].sum(), fr_g[n:, n:].sum()]
+    assert np.ptp(tots) / np.mean(tots) < 1e-5
+    assert abs(fr_g.sum() - op.pupil_mask(cfg.Np, cfg.obs).sum()) / fr_g.sum() < 1e-5
+    nv = valid.size
+    assert abs(sl_g[:nv].mean()) < 1e-6 and abs(sl_g[nv:].mean()) < 1e-6
+
+
+def test_reference_subtraction_and_user_valid_list(env):
+    torch, pas, ctx = env
+    from oracle import optics as op
+    cfg = tiny_config(Np=24, N=48, n_sub=4, K=8)
+    valid = np.array([1, 2, 5, 6, 9, 10], dtype=np.int32)
+    opd = random_opd_nm(cfg.Np, 100.0, seed=3).astype(np.float32)
+    pyr = pas.pas_pyr_create(ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius, cfg.wavelength_nm,
+                             cfg.obs, valid)
+    try:
+        sn = torch.linspace(-0.1, 0.1, 2 * valid.size, device="cuda")
+        pas.pas_pyr_set_reference(pyr, ctx, sn)
+        sl = torch.zeros(2 * valid.size, device="cuda")
+        pas.pas_pyr_measure(pyr, ctx, torch.as_tensor(opd).cuda(), None, sl)
+        torch.cuda.synchronize()
+        _, s_o = oracle_measure(cfg, opd, valid)
+        s_o = s_o - sn.cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(sl.cpu().numpy() - s_o)) <= SLOPE_TOL * np.max(np.abs(s_o)) + 1e-7
+    finally:
+        pas.pas_pyr_destroy(pyr)
+
+
+def test_bad_arguments_are_rejected(env):
+    torch, pas, ctx = env
+    with pytest.raises(pas.PasError) as e:
+        pas.pas_pyr_create(ctx, 64, 100, 12, 16, 3.0, 750.0, 0.1)
+    assert e.value.status == pas.PAS_EINVAL
+    with pytest.raises(pas.PasError):
+        pas.pas_pyr_create(ctx, 64, 128, 12, 16, 3.0, 750.0, 0.1, valid=np.array([5, 3], np.int32))
+    with pytest.raises(pas.PasError):
+        pas.pas_pyr_create(ctx, 36, 72, 4, 4, 3.0, 750.0, 0.1)  # 72 = 8*9 unsupported
