@@ -150,7 +150,8 @@ def algorithmic_work(cfg, n_pix, n_valid, n_modes, n_s_rows, recon_bytes_per_el)
                             + 4.0 * L * (Np + 1) ** 2 + 4.0 * n_modes},
         "pyr_rows_kernel": {"bound": "alu", "flops": n_s_rows * Np * (fft_pair + 20.0 * Np)},
         "pyr_cols_kernel": {"bound": "alu", "flops": K * N * (fft_pair + 6.0 * Np + 3.0 * N)},
-        "frame_slopes_kernel": {"bound": "latency", "bytes": 4.0 * (cfg.n_det ** 2) * 2 + 8.0 * 2 * n_valid},
+        "frame_kernel": {"bound": "latency", "bytes": 4.0 * (cfg.n_det ** 2) * 2},
+        "slopes_kernel": {"bound": "latency", "bytes": 16.0 * n_valid + 8.0 * 2 * n_valid},
         "recon_kernel": {"bound": "hbm", "bytes": recon_bytes_per_el * n_modes * 2 * n_valid + 8.0 * n_modes},
     }
 
@@ -335,7 +336,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 4 * sysg.n_modes + 16},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 7 * args.steps,
         "clocks": clocks,
         "residual_wfe_nm_mean": float(np.mean(wfe[len(wfe) // 5:])) if len(wfe) else None,
         "setup_s": t_setup, "wall_timed_s": t_wall,

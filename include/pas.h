@@ -247,8 +247,9 @@ void pas_loop_destroy(pas_loop_t loop);
  * launch on the context stream, synchronise, and write the mean duration in ms of
  * each kernel of the step into h_ms[0 .. *n_kernels-1] (cap >= PAS_LOOP_KERNELS).
  * The step's kernels, in order: residual (atmosphere + DM), pyramid rows pass,
- * pyramid columns pass, frame + slopes, reconstructor + integrator, step counter. */
-#define PAS_LOOP_KERNELS 6
+ * pyramid columns pass, detector frame (+ noise), slopes, reconstructor +
+ * integrator, step counter. */
+#define PAS_LOOP_KERNELS 7
 pas_status pas_loop_profile(pas_loop_t loop, int32_t n_steps, float* h_ms, int32_t cap,
                             int32_t* n_kernels);
 /* Name of kernel `idx` of pas_loop_profile (static string), NULL if out of range. */

@@ -5,15 +5,21 @@ readout_level, quantum_eff, bandw; ``wfs_source.magnitude``). The paper does not
 how noise is drawn. Readings:
 
   * photons per frame = F0 10^(-0.4 mag) (pi/4) D^2 (1 - obs^2) bandwidth QE dt;
-    the expected count of detector pixel p is photons * I_p / n_pupil_pixels (the
-    binned intensity sums to the pupil pixel count, Parseval);
+    the expected count of detector pixel p is lambda_p = I_p * (photons /
+    n_pupil_pixels) (the binned intensity sums to the pupil pixel count, Parseval);
   * counter-based RNG Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key =
     (seed low, seed high), counter = (pixel, frame low, frame high, block);
-    u = (x + 0.5) 2^-32 in FP64;
-  * read noise: Box-Muller on block 0 words 0, 1: sigma sqrt(-2 ln u0) cos(2 pi u1);
-  * photon noise: Poisson by inversion (sequential search) on block 0 word 2 when
-    lambda < 16, else the PTRS transformed rejection of Hoermann (1993) on pairs
-    (word 2, word 3) of blocks 0, 1, 2, ...; all decisions in FP64.
+  * the draws are integer decisions taken from floating point, so they are taken
+    in float32, the precision of the detector kernel, with IEEE float32 products,
+    quotients and sums (numpy float32 scalars here): uniform
+    u = ((x >> 8) + 1/2) 2^-24 (exact in float32);
+  * read noise: Box-Muller on block 0 words 0, 1: sqrt(-2 ln u0) cos(2 pi u1);
+  * photon noise, lambda < 64: inversion by sequential search on block 0 word 2,
+    p0 = exp(-lambda) evaluated in float64 and rounded to float32, then
+    p_k = p_{k-1} * (lambda / k), F_k = F_{k-1} + p_k in float32, the count being
+    the first k with u <= F_k (at most 256 terms);
+    lambda >= 64: the PTRS transformed rejection of Hoermann (1993) in float32 on
+    the pairs (word 2, word 3) of blocks 0, 1, 2, ...
 """
 from __future__ import annotations
 
@@ -26,6 +32,7 @@ M1 = 0xCD9E8D57
 W0 = 0x9E3779B9
 W1 = 0xBB67AE85
 MASK32 = 0xFFFFFFFF
+F32 = np.float32
 
 
 def philox4x32_10(ctr, key):
@@ -44,8 +51,9 @@ def philox4x32_10(ctr, key):
     return c0, c1, c2, c3
 
 
-def u01(x: int) -> float:
-    return (float(x) + 0.5) * 2.0 ** -32
+def u01(x: int) -> np.float32:
+    """Uniform in (0, 1), exact in float32."""
+    return F32((x >> 8) + 0.5) * F32(2.0 ** -24)
 
 
 def _block(seed: int, pixel: int, frame: int, blk: int):
@@ -53,60 +61,65 @@ def _block(seed: int, pixel: int, frame: int, blk: int):
     return philox4x32_10((pixel, frame & MASK32, (frame >> 32) & MASK32, blk), key)
 
 
-def poisson(lam: float, seed: int, pixel: int, frame: int) -> int:
-    """Poisson(lam) drawn from the pixel's counter stream."""
-    if lam <= 0.0:
+def poisson(lam, seed: int, pixel: int, frame: int) -> int:
+    """Poisson(lam) drawn from the pixel's counter stream, decisions in float32."""
+    lam = F32(lam)
+    if not lam > 0:
         return 0
     w = _block(seed, pixel, frame, 0)
-    if lam < 16.0:
+    if lam < F32(64.0):
         u = u01(w[2])
-        k = 0
-        p = math.exp(-lam)
+        p = F32(math.exp(-float(lam)))
         F = p
-        while u > F and k < 1000:
+        k = 0
+        while u > F and k < 256:
             k += 1
-            p *= lam / k
-            F += p
+            p = F32(p * F32(lam / F32(k)))
+            F = F32(F + p)
         return k
-    slam = math.sqrt(lam)
-    loglam = math.log(lam)
-    b = 0.931 + 2.53 * slam
-    a = -0.059 + 0.02483 * b
-    invalpha = 1.1239 + 1.1328 / (b - 3.4)
-    vr = 0.9277 - 3.6224 / (b - 2.0)
+    slam = np.sqrt(lam)
+    loglam = np.log(lam)
+    b = F32(F32(0.931) + F32(2.53) * slam)
+    a = F32(F32(-0.059) + F32(0.02483) * b)
+    invalpha = F32(F32(1.1239) + F32(1.1328) / (b - F32(3.4)))
+    vr = F32(F32(0.9277) - F32(3.6224) / (b - F32(2.0)))
     blk = 0
     while blk < 64:
         if blk > 0:
             w = _block(seed, pixel, frame, blk)
-        U = u01(w[2]) - 0.5
+        U = F32(u01(w[2]) - F32(0.5))
         V = u01(w[3])
         blk += 1
-        us = 0.5 - abs(U)
-        k = math.floor((2.0 * a / us + b) * U + lam + 0.43)
-        if us >= 0.07 and V <= vr:
+        us = F32(F32(0.5) - abs(U))
+        k = np.floor((F32(2.0) * a / us + b) * U + lam + F32(0.43))
+        if us >= F32(0.07) and V <= vr:
             return int(k)
-        if k < 0 or (us < 0.013 and V > us):
+        if k < 0 or (us < F32(0.013) and V > us):
             continue
-        if (math.log(V) + math.log(invalpha) - math.log(a / (us * us) + b)
-                <= -lam + k * loglam - math.lgamma(k + 1.0)):
+        lhs = np.log(V) + np.log(invalpha) - np.log(a / (us * us) + b)
+        rhs = -lam + k * loglam - F32(math.lgamma(float(k) + 1.0))
+        if F32(lhs) <= F32(rhs):
             return int(k)
-    return int(math.floor(lam + 0.5))
+    return int(np.floor(lam + F32(0.5)))
 
 
-def gaussian(seed: int, pixel: int, frame: int) -> float:
+def gaussian(seed: int, pixel: int, frame: int) -> np.float32:
     w = _block(seed, pixel, frame, 0)
-    return math.sqrt(-2.0 * math.log(u01(w[0]))) * math.cos(2.0 * math.pi * u01(w[1]))
+    return F32(np.sqrt(F32(-2.0) * np.log(u01(w[0]))) * np.cos(F32(2.0 * math.pi) * u01(w[1])))
 
 
 def apply_noise(frame_in: np.ndarray, photons_per_frame: float, n_pupil_px: int,
                 read_noise_e: float, seed: int, frame_index: int) -> np.ndarray:
     """Noisy detector frame in photo-electrons (pixels in row-major order)."""
-    flat = np.asarray(frame_in, dtype=np.float64).ravel()
-    scale = photons_per_frame / n_pupil_px
-    out = np.empty_like(flat)
+    flat = np.asarray(frame_in, dtype=np.float32).ravel()
+    scale = F32(photons_per_frame / n_pupil_px)
+    out = np.empty(flat.size, dtype=np.float64)
     for p, v in enumerate(flat):
-        val = float(poisson(v * scale, seed, p, frame_index)) if photons_per_frame > 0 else v * scale
-        if read_noise_e > 0:
-            val += read_noise_e * gaussian(seed, p, frame_index)
+        if photons_per_frame > 0:
+            val = float(poisson(F32(v * scale), seed, p, frame_index))
+            if read_noise_e > 0:
+                val = float(F32(F32(val) + F32(read_noise_e) * gaussian(seed, p, frame_index)))
+        else:
+            val = float(v)
         out[p] = val
     return out.reshape(np.shape(frame_in))

@@ -51,8 +51,7 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   if (ev) cudaEventRecord(ev[0], st);
   pas_status s = pas::residual_launch(L->ctx, ra, st);
   if (s != PAS_OK) return s;
-  pas::FrameArgs fa;
-  std::memset(&fa, 0, sizeof(fa));
+  pas::LoopExtra fa;
   fa.frame_ctr = L->d_step;
   fa.wfe_part = L->d_wfe_part;
   fa.n_wfe_part = L->n_tiles;
@@ -70,12 +69,12 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   rc.delay = L->delay;
   rc.step = L->d_step;
   rc.cmd_last = L->d_cmd;
-  if (ev) cudaEventRecord(ev[4], st);
+  if (ev) cudaEventRecord(ev[5], st);
   s = pas::recon_launch(L->rec, rc, st);
   if (s != PAS_OK) return s;
-  if (ev) cudaEventRecord(ev[5], st);
-  pas::step_increment_kernel<<<1, 1, 0, st>>>(L->d_step);
   if (ev) cudaEventRecord(ev[6], st);
+  pas::step_increment_kernel<<<1, 1, 0, st>>>(L->d_step);
+  if (ev) cudaEventRecord(ev[7], st);
   return pas::check_launch(L->ctx, "step counter launch");
 }
 
@@ -240,7 +239,8 @@ pas_status pas_loop_profile(pas_loop_t L, int32_t n_steps, float* h_ms, int32_t 
 
 const char* pas_loop_kernel_name(int32_t idx) {
   static const char* names[PAS_LOOP_KERNELS] = {"residual_kernel", "pyr_rows_kernel", "pyr_cols_kernel",
-                                                "frame_slopes_kernel", "recon_kernel", "step_increment_kernel"};
+                                                "frame_kernel", "slopes_kernel", "recon_kernel",
+                                                "step_increment_kernel"};
   return (idx >= 0 && idx < PAS_LOOP_KERNELS) ? names[idx] : nullptr;
 }
 

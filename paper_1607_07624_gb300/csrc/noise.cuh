@@ -1,10 +1,13 @@
 // Detector noise for the CCD object (Table 1 detector: photon_noise, readout_noise,
 // readout_level). Counter-based Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11):
-// key = seed, counter = (pixel, frame low, frame high, block). Uniforms
-// u = (x + 0.5) 2^-32 in double. Read noise: Box-Muller on block 0 words 0, 1.
-// Photon noise: Poisson by sequential-search inversion on block 0 word 2 for
-// lambda < 16, else Hoermann's (1993) PTRS transformed rejection on the pairs
-// (word 2, word 3) of blocks 0, 1, 2, ...; every decision in double.
+// key = seed, counter = (pixel, frame low, frame high, block).
+// All decisions in float32 with IEEE products, quotients and sums (no contraction):
+//   uniform u = ((x >> 8) + 1/2) 2^-24 (exact);
+//   read noise: Box-Muller on block 0 words 0, 1;
+//   photons, lambda < 64: sequential-search inversion on block 0 word 2, starting
+//     from exp(-lambda) evaluated in double and rounded to float;
+//   photons, lambda >= 64: Hoermann's (1993) PTRS transformed rejection on the pairs
+//     (word 2, word 3) of blocks 0, 1, 2, ...
 #pragma once
 #include <cstdint>
 
@@ -30,50 +33,62 @@ __host__ __device__ inline u32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
   return o;
 }
 
-__device__ inline double u01(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
+__device__ inline float u01f(uint32_t x) { return ((float)(x >> 8) + 0.5f) * 5.9604644775390625e-8f; }
 
 __device__ inline u32x4 noise_block(uint64_t seed, uint32_t pixel, uint64_t frame, uint32_t blk) {
   return philox4x32_10(pixel, (uint32_t)frame, (uint32_t)(frame >> 32), blk, (uint32_t)seed,
                        (uint32_t)(seed >> 32));
 }
 
-__device__ inline double poisson_draw(double lam, uint64_t seed, uint32_t pixel, uint64_t frame) {
-  if (!(lam > 0.0)) return 0.0;
+__device__ inline float poisson_draw(float lam, uint64_t seed, uint32_t pixel, uint64_t frame) {
+  if (!(lam > 0.f)) return 0.f;
   u32x4 w = noise_block(seed, pixel, frame, 0);
-  if (lam < 16.0) {
-    double u = u01(w.v[2]);
+  if (lam < 64.f) {
+    const float u = u01f(w.v[2]);
+    float p = (float)exp(-(double)lam);
+    float F = p;
     int k = 0;
-    double p = exp(-lam);
-    double F = p;
-    while (u > F && k < 1000) {
+    while (u > F && k < 256) {
       ++k;
-      p *= lam / k;
-      F += p;
+      p = __fmul_rn(p, __fdiv_rn(lam, (float)k));
+      F = __fadd_rn(F, p);
     }
-    return (double)k;
+    return (float)k;
   }
-  double slam = sqrt(lam), loglam = log(lam);
-  double b = 0.931 + 2.53 * slam;
-  double a = -0.059 + 0.02483 * b;
-  double invalpha = 1.1239 + 1.1328 / (b - 3.4);
-  double vr = 0.9277 - 3.6224 / (b - 2.0);
+  const float slam = sqrtf(lam), loglam = logf(lam);
+  const float b = __fadd_rn(0.931f, __fmul_rn(2.53f, slam));
+  const float a = __fadd_rn(-0.059f, __fmul_rn(0.02483f, b));
+  const float invalpha = __fadd_rn(1.1239f, __fdiv_rn(1.1328f, __fsub_rn(b, 3.4f)));
+  const float vr = __fsub_rn(0.9277f, __fdiv_rn(3.6224f, __fsub_rn(b, 2.0f)));
   for (uint32_t blk = 0; blk < 64; ++blk) {
     if (blk > 0) w = noise_block(seed, pixel, frame, blk);
-    double U = u01(w.v[2]) - 0.5;
-    double V = u01(w.v[3]);
-    double us = 0.5 - fabs(U);
-    double k = floor((2.0 * a / us + b) * U + lam + 0.43);
-    if (us >= 0.07 && V <= vr) return k;
-    if (k < 0.0 || (us < 0.013 && V > us)) continue;
-    if (log(V) + log(invalpha) - log(a / (us * us) + b) <= -lam + k * loglam - lgamma(k + 1.0))
-      return k;
+    const float U = __fsub_rn(u01f(w.v[2]), 0.5f);
+    const float V = u01f(w.v[3]);
+    const float us = __fsub_rn(0.5f, fabsf(U));
+    const float k = floorf(__fadd_rn(__fadd_rn(__fmul_rn(__fadd_rn(__fdiv_rn(__fmul_rn(2.0f, a), us), b), U), lam), 0.43f));
+    if (us >= 0.07f && V <= vr) return k;
+    if (k < 0.f || (us < 0.013f && V > us)) continue;
+    const float lhs = __fsub_rn(__fadd_rn(logf(V), logf(invalpha)),
+                                logf(__fadd_rn(__fdiv_rn(a, __fmul_rn(us, us)), b)));
+    const float rhs = __fsub_rn(__fadd_rn(-lam, __fmul_rn(k, loglam)), (float)lgamma((double)k + 1.0));
+    if (lhs <= rhs) return k;
   }
-  return floor(lam + 0.5);
+  return floorf(lam + 0.5f);
 }
 
-__device__ inline double gaussian_draw(uint64_t seed, uint32_t pixel, uint64_t frame) {
+__device__ inline float gaussian_draw(uint64_t seed, uint32_t pixel, uint64_t frame) {
   u32x4 w = noise_block(seed, pixel, frame, 0);
-  return sqrt(-2.0 * log(u01(w.v[0]))) * cospi(2.0 * u01(w.v[1]));
+  return __fmul_rn(sqrtf(__fmul_rn(-2.0f, logf(u01f(w.v[0])))), cospif(__fmul_rn(2.0f, u01f(w.v[1]))));
+}
+
+// Noisy value of one detector pixel: Poisson(v * scale) + ron * N(0, 1) in
+// photo-electrons; scale <= 0 leaves v unchanged.
+__device__ inline float noisy_pixel(float v, float scale, float ron, uint64_t seed, uint32_t pixel,
+                                    uint64_t frame) {
+  if (!(scale > 0.f)) return v;
+  float e = poisson_draw(__fmul_rn(v, scale), seed, pixel, frame);
+  if (ron > 0.f) e = __fadd_rn(e, __fmul_rn(ron, gaussian_draw(seed, pixel, frame)));
+  return e;
 }
 
 }  // namespace pas

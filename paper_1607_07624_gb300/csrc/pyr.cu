@@ -195,73 +195,100 @@ __device__ inline double block_sum(double v, double* red) {
   return r;
 }
 
-__global__ void __launch_bounds__(1024) frame_slopes_kernel(FrameArgs a) {
+struct FrameArgs {
+  const float* part;           // [G][nd*nd]
+  float* frame;                // [nd*nd]
+  const unsigned char* vpix;   // [nd*nd] 1: quadrant pixel of a valid sub-aperture
+  double* flux_part;           // [gridDim.x]
+  const long long* frame_ctr;
+  int G, np;
+  float invK, scale, ron;
+  unsigned long long seed;
+};
+
+struct SlopeArgs {
+  const float* frame;
+  const int* valid;
+  const float* sn;             // [2nv] or null
+  float* slopes;               // [2nv] or null
+  const double* flux_part;
+  int n_flux_part, nv, n_sub, nd, local_norm;
+  long long* frame_ctr;
+  int ctr_increment;
+  LoopExtra wfe;               // wfe.wfe_part null: no WFE
+};
+
+// Detector frame: sum of the modulation groups' partial frames, / K, noise; and
+// the per-CTA partial flux over the valid sub-apertures' pixels.
+__global__ void __launch_bounds__(256) frame_kernel(FrameArgs a) {
   __shared__ double red[32];
-  const int np = a.nd * a.nd;
-  const long long fidx = a.frame_ctr ? *a.frame_ctr : 0;
-  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  double flux = 0.0;
+  if (p < a.np) {
     float v = 0.f;
-    for (int gg = 0; gg < a.G; ++gg) v += a.part[(size_t)gg * np + p];
+    for (int gg = 0; gg < a.G; ++gg) v += a.part[(size_t)gg * a.np + p];
     v *= a.invK;
-    if (a.photon_scale > 0.0) {
-      double e = poisson_draw((double)v * a.photon_scale, a.seed, (uint32_t)p, (uint64_t)fidx);
-      if (a.ron > 0.0) e += a.ron * gaussian_draw(a.seed, (uint32_t)p, (uint64_t)fidx);
-      v = (float)e;
-    }
+    const long long fidx = a.frame_ctr ? *a.frame_ctr : 0;
+    v = noisy_pixel(v, a.scale, a.ron, a.seed, (uint32_t)p, (uint64_t)fidx);
     a.frame[p] = v;
+    if (a.vpix[p]) flux = v;
   }
-  __syncthreads();
-  const int ns = a.n_sub, nd = a.nd;
-  double tsum = 0.0;
-  for (int j = threadIdx.x; j < a.nv; j += blockDim.x) {
-    const int v = a.valid[j], r = v / ns, c = v - r * ns;
-    tsum += (double)a.frame[r * nd + c] + (double)a.frame[r * nd + ns + c] +
-            (double)a.frame[(ns + r) * nd + c] + (double)a.frame[(ns + r) * nd + ns + c];
-  }
-  const double F = block_sum(tsum, red) / (double)a.nv;
-  if (a.slopes) {
-    for (int j = threadIdx.x; j < a.nv; j += blockDim.x) {
-      const int v = a.valid[j], r = v / ns, c = v - r * ns;
-      const float q00 = a.frame[r * nd + c], q01 = a.frame[r * nd + ns + c];
-      const float q10 = a.frame[(ns + r) * nd + c], q11 = a.frame[(ns + r) * nd + ns + c];
-      const float den = a.local_norm ? (q00 + q01 + q10 + q11) : (float)F;
-      const float inv = 1.0f / den;
-      float sx = ((q10 + q11) - (q00 + q01)) * inv;
-      float sy = ((q01 + q11) - (q00 + q10)) * inv;
-      if (a.sn) {
-        sx -= a.sn[j];
-        sy -= a.sn[a.nv + j];
-      }
-      a.slopes[j] = sx;
-      a.slopes[a.nv + j] = sy;
-    }
-  }
-  if (a.wfe_part) {
-    double s1 = 0.0, s2 = 0.0;
-    for (int t = threadIdx.x; t < a.n_wfe_part; t += blockDim.x) {
-      s1 += a.wfe_part[t].x;
-      s2 += a.wfe_part[t].y;
-    }
-    s1 = block_sum(s1, red);
-    s2 = block_sum(s2, red);
-    if (threadIdx.x == 0) {
-      const double m = s1 * a.inv_npix;
-      const double var = fmax(s2 * a.inv_npix - m * m, 0.0);
-      a.wfe_hist[(*a.step) % a.wfe_hist_len] = sqrt(var);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && a.ctr_increment && a.frame_ctr) *a.frame_ctr = fidx + 1;
+  flux = block_sum(flux, red);
+  if (threadIdx.x == 0) a.flux_part[blockIdx.x] = flux;
 }
 
-__global__ void ccd_noise_kernel(const float* in, float* out, int n, double scale, double ron,
-                                 unsigned long long seed, long long fidx) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    double v = in[p];
-    double e = scale > 0.0 ? poisson_draw(v * scale, seed, (uint32_t)p, (uint64_t)fidx) : v;
-    if (ron > 0.0 && scale > 0.0) e += ron * gaussian_draw(seed, (uint32_t)p, (uint64_t)fidx);
-    out[p] = (float)e;
+// Normalised slopes of the valid sub-apertures; CTA 0 also closes the step's
+// residual WFE and advances the noise frame counter.
+__global__ void __launch_bounds__(256) slopes_kernel(SlopeArgs a) {
+  __shared__ double red[32];
+  __shared__ double F_s;
+  if (threadIdx.x == 0) {
+    double f = 0.0;
+    for (int i = 0; i < a.n_flux_part; ++i) f += a.flux_part[i];
+    F_s = f / (double)a.nv;
   }
+  __syncthreads();
+  const float F = (float)F_s;
+  const int ns = a.n_sub, nd = a.nd;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < a.nv && a.slopes) {
+    const int v = a.valid[j], r = v / ns, c = v - r * ns;
+    const float q00 = a.frame[r * nd + c], q01 = a.frame[r * nd + ns + c];
+    const float q10 = a.frame[(ns + r) * nd + c], q11 = a.frame[(ns + r) * nd + ns + c];
+    const float den = a.local_norm ? (q00 + q01 + q10 + q11) : F;
+    const float inv = 1.0f / den;
+    float sx = ((q10 + q11) - (q00 + q01)) * inv;
+    float sy = ((q01 + q11) - (q00 + q10)) * inv;
+    if (a.sn) {
+      sx -= a.sn[j];
+      sy -= a.sn[a.nv + j];
+    }
+    a.slopes[j] = sx;
+    a.slopes[a.nv + j] = sy;
+  }
+  if (blockIdx.x == 0) {
+    if (a.wfe.wfe_part) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int t = threadIdx.x; t < a.wfe.n_wfe_part; t += blockDim.x) {
+        s1 += a.wfe.wfe_part[t].x;
+        s2 += a.wfe.wfe_part[t].y;
+      }
+      s1 = block_sum(s1, red);
+      s2 = block_sum(s2, red);
+      if (threadIdx.x == 0) {
+        const double m = s1 * a.wfe.inv_npix;
+        const double var = fmax(s2 * a.wfe.inv_npix - m * m, 0.0);
+        a.wfe.wfe_hist[(*a.wfe.step) % a.wfe.wfe_hist_len] = sqrt(var);
+      }
+    }
+    if (threadIdx.x == 0 && a.ctr_increment && a.frame_ctr) *a.frame_ctr += 1;
+  }
+}
+
+__global__ void ccd_noise_kernel(const float* in, float* out, int n, float scale, float ron,
+                                 unsigned long long seed, long long fidx) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+    out[p] = noisy_pixel(in[p], scale, ron, seed, (uint32_t)p, (uint64_t)fidx);
 }
 
 // ------------------------------------------------------------------ dispatch
@@ -329,7 +356,10 @@ struct pas_pyr_s {
   float* d_part = nullptr;
   float* d_frame = nullptr;
   long long* d_frame_ctr = nullptr;
-  double photon_scale = 0.0, ron = 0.0;
+  unsigned char* d_vpix = nullptr;
+  double* d_flux_part = nullptr;
+  int n_fb = 0;
+  float photon_scale = 0.f, ron = 0.f;
   unsigned long long seed = 0;
   bool has_sn = false;
 };
@@ -338,7 +368,7 @@ namespace pas {
 
 // Launch the three pyramid kernels. wfe fields of `fa` may be filled by the loop.
 pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes,
-                      cudaStream_t st, FrameArgs* fa_extra, bool increment_ctr, cudaEvent_t* ev) {
+                      cudaStream_t st, const LoopExtra* fa_extra, bool increment_ctr, cudaEvent_t* ev) {
   const pas_pyr_params& p = y->p;
   RowArgs ra;
   ra.opd = d_opd;
@@ -370,29 +400,37 @@ pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_
   dim3 gc(y->nd, y->G);
   if (ev) cudaEventRecord(ev[1], st);
   y->kern.cols<<<gc, y->b * 32, y->smem_cols, st>>>(ca);
+  long long* ctr = fa_extra ? fa_extra->frame_ctr : y->d_frame_ctr;
   FrameArgs fa;
-  if (fa_extra) fa = *fa_extra;
-  else {
-    memset(&fa, 0, sizeof(fa));
-  }
   fa.part = y->d_part;
   fa.frame = d_frame ? d_frame : y->d_frame;
-  fa.valid = y->d_valid;
-  fa.sn = y->has_sn ? y->d_sn : nullptr;
-  fa.slopes = d_slopes;
+  fa.vpix = y->d_vpix;
+  fa.flux_part = y->d_flux_part;
+  fa.frame_ctr = ctr;
   fa.G = y->G;
-  fa.nd = y->nd;
-  fa.n_sub = p.n_sub;
-  fa.nv = y->n_valid;
-  fa.local_norm = p.local_norm;
+  fa.np = y->nd * y->nd;
   fa.invK = 1.0f / (float)p.K;
-  fa.photon_scale = y->photon_scale;
+  fa.scale = y->photon_scale;
   fa.ron = y->ron;
   fa.seed = y->seed;
-  if (!fa_extra) fa.frame_ctr = y->d_frame_ctr;
-  fa.ctr_increment = increment_ctr ? 1 : 0;
   if (ev) cudaEventRecord(ev[2], st);
-  frame_slopes_kernel<<<1, 1024, 0, st>>>(fa);
+  frame_kernel<<<y->n_fb, 256, 0, st>>>(fa);
+  SlopeArgs sa;
+  sa.frame = fa.frame;
+  sa.valid = y->d_valid;
+  sa.sn = y->has_sn ? y->d_sn : nullptr;
+  sa.slopes = d_slopes;
+  sa.flux_part = y->d_flux_part;
+  sa.n_flux_part = y->n_fb;
+  sa.nv = y->n_valid;
+  sa.n_sub = p.n_sub;
+  sa.nd = y->nd;
+  sa.local_norm = p.local_norm;
+  sa.frame_ctr = ctr;
+  sa.ctr_increment = increment_ctr ? 1 : 0;
+  if (fa_extra) sa.wfe = *fa_extra;
+  if (ev) cudaEventRecord(ev[3], st);
+  slopes_kernel<<<(y->n_valid + 255) / 256, 256, 0, st>>>(sa);
   return check_launch(y->ctx, "pas_pyr_measure launch");
 }
 
@@ -421,6 +459,8 @@ void pas_pyr_destroy(pas_pyr_t y) {
   pas::dev_free(y->d_part);
   pas::dev_free(y->d_frame);
   pas::dev_free(y->d_frame_ctr);
+  pas::dev_free(y->d_vpix);
+  pas::dev_free(y->d_flux_part);
   delete y;
 }
 
@@ -545,6 +585,9 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   A((void**)&y->d_part, sizeof(float) * (size_t)y->G * y->nd * y->nd);
   A((void**)&y->d_frame, sizeof(float) * y->nd * y->nd);
   A((void**)&y->d_frame_ctr, sizeof(long long));
+  y->n_fb = (y->nd * y->nd + 255) / 256;
+  A((void**)&y->d_vpix, (size_t)y->nd * y->nd);
+  A((void**)&y->d_flux_part, sizeof(double) * y->n_fb);
   if (st != PAS_OK) {
     pas_pyr_destroy(y);
     return st;
@@ -559,6 +602,14 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   C(y->d_alpha, alpha.data(), sizeof(float) * p.K);
   C(y->d_beta, beta.data(), sizeof(float) * y->n_s);
   C(y->d_kmap, kmap.data(), sizeof(int) * p.K);
+  {
+    std::vector<unsigned char> vpix((size_t)y->nd * y->nd, 0);
+    for (int v : valid) {
+      const int r = v / p.n_sub, c = v % p.n_sub, ns = p.n_sub, nd = y->nd;
+      vpix[r * nd + c] = vpix[r * nd + ns + c] = vpix[(ns + r) * nd + c] = vpix[(ns + r) * nd + ns + c] = 1;
+    }
+    C(y->d_vpix, vpix.data(), vpix.size());
+  }
   if (e == cudaSuccess) e = cudaMemset(y->d_sn, 0, sizeof(float) * 2 * y->n_valid);
   if (e == cudaSuccess) e = cudaMemset(y->d_frame_ctr, 0, sizeof(long long));
   if (e == cudaSuccess)
@@ -597,8 +648,8 @@ pas_status pas_pyr_set_reference(pas_pyr_t y, const float* d_sn) {
 pas_status pas_pyr_set_noise(pas_pyr_t y, double photons, double ron, uint64_t seed, int64_t frame_index) {
   if (!y) return pas::set_global_error(PAS_EINVAL, "pas_pyr_set_noise: NULL pyramid");
   PAS_CHECK_ARG(y->ctx, ron >= 0.0 && frame_index >= 0, "pas_pyr_set_noise: bad read noise or frame index");
-  y->photon_scale = photons > 0.0 ? photons / (double)y->n_pupil : 0.0;
-  y->ron = ron;
+  y->photon_scale = photons > 0.0 ? (float)(photons / (double)y->n_pupil) : 0.f;
+  y->ron = (float)ron;
   y->seed = seed;
   long long f = frame_index;
   PAS_CUDA_TRY(y->ctx, cudaMemcpyAsync(y->d_frame_ctr, &f, sizeof(f), cudaMemcpyHostToDevice, y->ctx->stream));
@@ -616,9 +667,9 @@ pas_status pas_ccd_noise(pas_ctx_t ctx, const float* d_in, float* d_out, int32_t
   if (!ctx || !d_in || !d_out) return pas::set_global_error(PAS_EINVAL, "pas_ccd_noise: NULL argument");
   PAS_CHECK_ARG(ctx, n >= 0 && n_pupil_pixels > 0 && ron >= 0 && frame_index >= 0, "pas_ccd_noise: bad argument");
   if (n == 0) return PAS_OK;
-  double scale = photons > 0.0 ? photons / (double)n_pupil_pixels : 0.0;
+  const float scale = photons > 0.0 ? (float)(photons / (double)n_pupil_pixels) : 0.f;
   int threads = 256, blocks = (n + threads - 1) / threads;
-  pas::ccd_noise_kernel<<<blocks, threads, 0, ctx->stream>>>(d_in, d_out, n, scale, ron, seed, frame_index);
+  pas::ccd_noise_kernel<<<blocks, threads, 0, ctx->stream>>>(d_in, d_out, n, scale, (float)ron, seed, frame_index);
   return pas::check_launch(ctx, "pas_ccd_noise launch");
 }
 

@@ -117,9 +117,10 @@ def test_detector_noise_matches_oracle_counts(env):
         torch.cuda.synchronize()
         g = d_out.cpu().numpy().astype(np.float64)
         o = nz.apply_noise(fr.astype(np.float64), photons, npup, ron, seed, frame_index)
-        close = np.abs(g - o) <= 1e-4 * np.maximum(1.0, np.abs(o))
+        # same float32 decisions on both sides: counts agree; the Gaussian part
+        # differs only by the cosine implementations (a few float32 ulps)
+        close = np.abs(g - o) <= 1e-5 * np.maximum(1.0, np.abs(o))
         assert close.mean() >= 0.999, close.mean()
-        # photon counts alone (no read noise): integers equal
     pas.pas_ccd_noise(ctx, d_in, d_out, photons, npup, 0.0, seed, 3)
     torch.cuda.synchronize()
     o = nz.apply_noise(fr.astype(np.float64), photons, npup, 0.0, seed, 3)
