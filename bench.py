@@ -146,11 +146,10 @@ def algorithmic_work(cfg, n_pix, n_valid, n_modes, n_s_rows, recon_bytes_per_el)
     N, Np, K, L = cfg.N, cfg.Np, cfg.K, len(cfg.layers)
     fft_pair = 2 * 5.0 * N * math.log2(N) + 6.0 * N           # FFT + mask + IFFT
     return {
-        "residual_kernel": {"bound": "hbm", "bytes": 4.0 * n_modes * n_pix + 12.0 * n_pix
-                            + 4.0 * L * (Np + 1) ** 2 + 4.0 * n_modes},
-        "pyr_rows_kernel": {"bound": "alu", "flops": n_s_rows * Np * (fft_pair + 20.0 * Np)},
+        "atmo_pupil_kernel": {"bound": "hbm", "bytes": 4.0 * L * (Np + 1) ** 2 + 8.0 * n_pix},
+        "residual_kernel": {"bound": "hbm", "bytes": 4.0 * n_modes * n_pix + 12.0 * n_pix + 4.0 * n_modes},
+        "pyr_rows_kernel": {"bound": "alu", "flops": n_s_rows * Np * (fft_pair + 6.0 * Np)},
         "pyr_cols_kernel": {"bound": "alu", "flops": K * N * (fft_pair + 6.0 * Np + 3.0 * N)},
-        "frame_kernel": {"bound": "latency", "bytes": 4.0 * (cfg.n_det ** 2) * 2},
         "slopes_kernel": {"bound": "latency", "bytes": 16.0 * n_valid + 8.0 * 2 * n_valid},
         "recon_kernel": {"bound": "hbm", "bytes": recon_bytes_per_el * n_modes * 2 * n_valid + 8.0 * n_modes},
     }
@@ -200,7 +199,20 @@ def main():
     sysg = SCAOSystem(cfg_r, recon_precision=prec, wfe_history=max(4096, args.steps + args.warmup + 64))
     t_setup = time.perf_counter() - t_setup
     stream = torch.cuda.current_stream()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    # L2 flush between timed steps: write 256 MiB (evicts everything), then read
+    # another 256 MiB so that the dirty lines are written back outside the timed
+    # region and the next step starts from a clean, cold L2
+    flush_w = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush_r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush_sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+
+    class _Flush:
+        @staticmethod
+        def zero_():
+            flush_w.zero_()
+            torch.sum(flush_r, dim=0, keepdim=True, out=flush_sink)
+
+    flush = _Flush()
     props = torch.cuda.get_device_properties(local_rank)
     uuid = getattr(props, "uuid", None)
     sampler = ClockSampler(f"GPU-{uuid}" if uuid else None) if rank == 0 else None
@@ -211,11 +223,14 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up (also captures the graph) and a short soak for steady clocks
+    # warm-up (also captures the graph) and a short soak for steady clocks; the
+    # loop state is then reset so that the timed steps start a fresh simulation
     sysg.step(max(3, args.warmup))
     t_end = time.perf_counter() + 1.5
     while time.perf_counter() < t_end:
         sysg.step(50)
+    barrier()
+    sysg.set_state(0, np.zeros((sysg.delay, sysg.n_modes), dtype=np.float32))
     barrier()
 
     def timed(fn, n):
@@ -241,8 +256,10 @@ def main():
     value = steps_total / (ms_total / 1000.0)
     ms_per_step = ms_total / args.steps
 
-    # PWFS frames/s: pas_pyr_measure alone on the loop's residual
-    opd = sysg.loop_opd.clone()
+    # PWFS frames/s: pas_pyr_measure alone on a fixed input, the open-loop
+    # atmospheric OPD of step 0 (pas_atmo_advance)
+    opd = torch.zeros(cfg.Np, cfg.Np, dtype=torch.float32, device="cuda")
+    pas.pas_atmo_advance(sysg.atmo, sysg.ctx, 0, opd)
     n_fr = max(20, min(args.steps, 500))
     ms_fr = timed(lambda: sysg.measure(opd), n_fr)
     frames_per_s = world * n_fr / (ms_fr / 1000.0)
@@ -269,7 +286,7 @@ def main():
     barrier()
     clocks = sampler.stop() if sampler else None
 
-    wfe = sysg.wfe_nm(min(sysg.wfe_history, args.warmup + args.steps))
+    wfe = sysg.wfe_nm(min(sysg.wfe_history, args.steps))
     n_s_rows = cfg.K // 2 + 1 if cfg.K % 2 == 0 else cfg.K
     work = algorithmic_work(cfg, sysg.n_pix, sysg.n_valid, sysg.n_modes, n_s_rows,
                             2.0 if prec == pas.PAS_BF16 else 4.0)
@@ -324,7 +341,8 @@ def main():
                                f"R={cfg.mod_radius} l/D, {sysg.n_modes} modes, mag {cfg.magnitude} + "
                                f"{cfg.read_noise_e} e- RON",
                    "l2": "flushed (256 MiB write) between timed steps", "recon": args.recon,
-                   "parallelism": f"replicas x{world}", "graph": "whole step, CUDA graph"},
+                   "parallelism": f"replicas x{world}", "graph": "whole step, CUDA graph",
+                   "pyramid_tuning": dict(zip(("rows_per_cta", "row_chunks", "col_groups"), sysg.tuning))},
         "pwfs_frames_per_s": frames_per_s,
         "roofline": None if dom is None else {"bound": dom["bound"], "achieved": dom["achieved"],
                                                "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"],
@@ -336,7 +354,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 4 * sysg.n_modes + 16},
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": 6 * args.steps,
         "clocks": clocks,
         "residual_wfe_nm_mean": float(np.mean(wfe[len(wfe) // 5:])) if len(wfe) else None,
         "setup_s": t_setup, "wall_timed_s": t_wall,

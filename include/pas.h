@@ -177,6 +177,26 @@ pas_status pas_ccd_noise(pas_ctx_t ctx, const float* d_in, float* d_out, int32_t
                          double read_noise_e, uint64_t seed, int64_t frame_index);
 void pas_pyr_destroy(pas_pyr_t pyr);
 
+/* Launch geometry of the pyramid kernels: rows pass = pupil rows per CTA and the
+ * number of chunks the distinct sin(theta_k) values are split into (the OPD
+ * phasor of a row is computed once per chunk); columns pass = number of groups
+ * of modulation points (each CTA accumulates |g|^2 over its group). */
+typedef struct {
+    int32_t rows_per_cta;   /* 1, 2, 4 or 8 */
+    int32_t row_chunks;     /* 1 .. number of distinct sin(theta_k) */
+    int32_t col_groups;     /* 1 .. K */
+} pas_pyr_tuning;
+pas_status pas_pyr_get_tuning(pas_pyr_t pyr, pas_pyr_tuning* h_out);
+/* Values are rounded to the nearest realisable split; results do not depend on
+ * the geometry beyond float32 summation order of the modulation groups. */
+pas_status pas_pyr_set_tuning(pas_pyr_t pyr, const pas_pyr_tuning* h_t);
+/* Autotuner: times each candidate geometry (rows_per_cta 2/4/8 x every chunk
+ * count; every column group count) with CUDA events over `iters` launches on
+ * d_opd (device [Np][Np]), keeps the fastest and writes it to h_out (may be
+ * NULL). Synchronous; overwrites the object's internal frame; do not call while
+ * the context stream is being captured. */
+pas_status pas_pyr_autotune(pas_pyr_t pyr, const float* d_opd, int32_t iters, pas_pyr_tuning* h_out);
+
 /* ------------------------------------------------- modal reconstructor
  * Modal reconstructor (Table 1 modalrec.recmat_tag): dmodes = R * slopes.
  * h_R: host float32 [n_modes][n_slopes] row-major, copied. PAS_BF16 stores R in
@@ -243,13 +263,15 @@ pas_status pas_loop_get_state(pas_loop_t loop, int64_t* step, float* h_cmd_ring)
 pas_status pas_loop_set_state(pas_loop_t loop, int64_t step, const float* h_cmd_ring);
 void pas_loop_destroy(pas_loop_t loop);
 
-/* Profiling: run n_steps >= 1 steps kernel by kernel with CUDA events around each
- * launch on the context stream, synchronise, and write the mean duration in ms of
- * each kernel of the step into h_ms[0 .. *n_kernels-1] (cap >= PAS_LOOP_KERNELS).
- * The step's kernels, in order: residual (atmosphere + DM), pyramid rows pass,
- * pyramid columns pass, detector frame (+ noise), slopes, reconstructor +
- * integrator, step counter. */
-#define PAS_LOOP_KERNELS 7
+/* Profiling: run n_steps >= 1 steps, each one launch of a CUDA graph of the step
+ * with event-record nodes between its kernels (GPU-side timing, no host launch
+ * gaps), synchronising after each, and write the mean duration in ms of each
+ * kernel into h_ms[0 .. *n_kernels-1] (cap >= PAS_LOOP_KERNELS). The steps advance
+ * the loop like pas_loop_step.
+ * The step's kernels, in order: atmosphere, residual (- DM shape), pyramid
+ * rows pass, pyramid columns pass (+ detector frame and noise in the last CTA of
+ * each detector column), slopes, reconstructor + integrator (+ step counter). */
+#define PAS_LOOP_KERNELS 6
 pas_status pas_loop_profile(pas_loop_t loop, int32_t n_steps, float* h_ms, int32_t cap,
                             int32_t* n_kernels);
 /* Name of kernel `idx` of pas_loop_profile (static string), NULL if out of range. */

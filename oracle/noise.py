@@ -16,8 +16,9 @@ how noise is drawn. Readings:
   * read noise: Box-Muller on block 0 words 0, 1: sqrt(-2 ln u0) cos(2 pi u1);
   * photon noise, lambda < 64: inversion by sequential search on block 0 word 2,
     p0 = exp(-lambda) evaluated in float64 and rounded to float32, then
-    p_k = p_{k-1} * (lambda / k), F_k = F_{k-1} + p_k in float32, the count being
-    the first k with u <= F_k (at most 256 terms);
+    p_k = p_{k-1} * (lambda * rn(1/k)), F_k = F_{k-1} + p_k in float32 (rn(1/k):
+    the correctly rounded float32 reciprocal), the count being the first k with
+    u <= F_k (at most 256 terms);
     lambda >= 64: the PTRS transformed rejection of Hoermann (1993) in float32 on
     the pairs (word 2, word 3) of blocks 0, 1, 2, ...
 """
@@ -74,7 +75,7 @@ def poisson(lam, seed: int, pixel: int, frame: int) -> int:
         k = 0
         while u > F and k < 256:
             k += 1
-            p = F32(p * F32(lam / F32(k)))
+            p = F32(p * F32(lam * (F32(1.0) / F32(k))))
             F = F32(F + p)
         return k
     slam = np.sqrt(lam)

@@ -43,6 +43,71 @@ __device__ inline float atmo_sample(const AtmoArgs& a, const int* six, const int
   return acc;
 }
 
+// Same sum with the layer count known at compile time: all 4 L taps are issued
+// before the first one is used.
+template <int L>
+__device__ inline float atmo_sample_fixed(const AtmoArgs& a, const int* six, const int* siy,
+                                          const float* sfx, const float* sfy, int i, int j) {
+  const int S = a.S;
+  float v[L][4];
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    int i0 = i + six[l];
+    if (i0 >= S) i0 -= S;
+    int j0 = j + siy[l];
+    if (j0 >= S) j0 -= S;
+    const int i1 = (i0 + 1 == S) ? 0 : i0 + 1;
+    const int j1 = (j0 + 1 == S) ? 0 : j0 + 1;
+    const float* sc = a.screens + (size_t)l * S * S;
+    v[l][0] = __ldg(sc + (size_t)i0 * S + j0);
+    v[l][1] = __ldg(sc + (size_t)i1 * S + j0);
+    v[l][2] = __ldg(sc + (size_t)i0 * S + j1);
+    v[l][3] = __ldg(sc + (size_t)i1 * S + j1);
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    const float fx = sfx[l], fy = sfy[l];
+    acc += (1.f - fx) * (1.f - fy) * v[l][0] + fx * (1.f - fy) * v[l][1] + (1.f - fx) * fy * v[l][2] +
+           fx * fy * v[l][3];
+  }
+  return acc;
+}
+
+__device__ inline float atmo_sample_any(const AtmoArgs& a, const int* six, const int* siy,
+                                        const float* sfx, const float* sfy, int i, int j) {
+  switch (a.L) {
+    case 1: return atmo_sample_fixed<1>(a, six, siy, sfx, sfy, i, j);
+    case 2: return atmo_sample_fixed<2>(a, six, siy, sfx, sfy, i, j);
+    case 3: return atmo_sample_fixed<3>(a, six, siy, sfx, sfy, i, j);
+    case 4: return atmo_sample_fixed<4>(a, six, siy, sfx, sfy, i, j);
+    case 5: return atmo_sample_fixed<5>(a, six, siy, sfx, sfy, i, j);
+    case 6: return atmo_sample_fixed<6>(a, six, siy, sfx, sfy, i, j);
+    default: return atmo_sample(a, six, siy, sfx, sfy, i, j);
+  }
+}
+
+// Atmosphere on the pupil pixels only (the loop's first kernel): one thread per
+// pixel, all 4 L taps issued at once.
+template <int LT>
+__global__ void __launch_bounds__(256) atmo_pupil_kernel(AtmoArgs a, const int* pix, int n_pix,
+                                                         const long long* d_step, float* out) {
+  __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
+  __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
+  const long long step = *d_step;
+  if (threadIdx.x < a.L) {
+    layer_shift(a.vx[threadIdx.x], step, a.S, &six[threadIdx.x], &sfx[threadIdx.x]);
+    layer_shift(a.vy[threadIdx.x], step, a.S, &siy[threadIdx.x], &sfy[threadIdx.x]);
+  }
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pix) return;
+  const int flat = pix[p];
+  const int i = flat / a.Np, j = flat - i * a.Np;
+  out[flat] = LT > 0 ? atmo_sample_fixed<(LT > 0 ? LT : 1)>(a, six, siy, sfx, sfy, i, j)
+                     : atmo_sample(a, six, siy, sfx, sfy, i, j);
+}
+
 __global__ void atmo_kernel(AtmoArgs a, const long long* d_step, long long h_step, float* out) {
   __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
   __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
@@ -55,19 +120,64 @@ __global__ void atmo_kernel(AtmoArgs a, const long long* d_step, long long h_ste
   const int n = a.Np * a.Np;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const int i = p / a.Np, j = p - i * a.Np;
-    out[p] = atmo_sample(a, six, siy, sfx, sfy, i, j);
+    out[p] = atmo_sample_any(a, six, siy, sfx, sfy, i, j);
   }
 }
 
 // Residual over the pupil pixel list: out[pix] = atm - dm_sign * (M c).
-// CTA: 256 threads = 8 warps over one tile of 128 pixels; each lane owns 4
-// consecutive pixels (one 16-byte load per mode) and warp w the modes m = w mod 8.
-__global__ void __launch_bounds__(256) residual_kernel(ResArgs a) {
+// CTA: RES_WARPS warps over one tile of RES_TILE = 64 pixels; each half-warp
+// covers the tile with one 16-byte load per lane and mode, and half-warp g of the
+// CTA takes the modes m = g mod RES_GROUPS. Small tiles keep the SMs evenly
+// loaded; the atmosphere taps are loaded before the GEMV.
+constexpr int RES_WARPS = 16;
+constexpr int RES_TILE = 64;
+constexpr int RES_GROUPS = 2 * RES_WARPS;
+
+// Bilinear taps of L layers for one pixel, loaded before use.
+template <int L> struct Taps {
+  float v[L][4];
+  __device__ __forceinline__ void load(const AtmoArgs& a, const int* six, const int* siy, int i, int j) {
+    const int S = a.S;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      int i0 = i + six[l];
+      if (i0 >= S) i0 -= S;
+      int j0 = j + siy[l];
+      if (j0 >= S) j0 -= S;
+      const int i1 = (i0 + 1 == S) ? 0 : i0 + 1;
+      const int j1 = (j0 + 1 == S) ? 0 : j0 + 1;
+      const float* sc = a.screens + (size_t)l * S * S;
+      v[l][0] = __ldg(sc + (size_t)i0 * S + j0);
+      v[l][1] = __ldg(sc + (size_t)i1 * S + j0);
+      v[l][2] = __ldg(sc + (size_t)i0 * S + j1);
+      v[l][3] = __ldg(sc + (size_t)i1 * S + j1);
+    }
+  }
+  __device__ __forceinline__ float combine(const float* sfx, const float* sfy) const {
+    float acc = 0.f;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      const float fx = sfx[l], fy = sfy[l];
+      acc += (1.f - fx) * (1.f - fy) * v[l][0] + fx * (1.f - fy) * v[l][1] + (1.f - fx) * fy * v[l][2] +
+             fx * fy * v[l][3];
+    }
+    return acc;
+  }
+};
+template <> struct Taps<0> {
+  __device__ __forceinline__ void load(const AtmoArgs&, const int*, const int*, int, int) {}
+  __device__ __forceinline__ float combine(const float*, const float*) const { return 0.f; }
+};
+
+// LT = number of layers (0: the atmosphere comes from opd_atm or is zero; -1:
+// any count, sampled after the GEMV with a runtime loop).
+template <int LT>
+__global__ void __launch_bounds__(RES_WARPS * 32) residual_kernel(ResArgs a) {
   extern __shared__ float c_s[];                  // [n_m]
-  __shared__ float red[8][128];
+  __shared__ float red[RES_GROUPS][RES_TILE];
   __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
   __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
-  __shared__ double wred[2][8];
+  __shared__ double wred[2][RES_WARPS];
   const long long step = a.d_step ? *a.d_step : a.h_step;
   const float* cmd = a.cmd;
   if (a.cmd_ring) cmd = a.cmd_ring + (size_t)(step % a.delay) * a.n_m;
@@ -78,45 +188,57 @@ __global__ void __launch_bounds__(256) residual_kernel(ResArgs a) {
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int base = blockIdx.x * 128;
+  const int base = blockIdx.x * RES_TILE;
+  // the last warps own the tile's pixels: their atmosphere loads are issued
+  // before their share of the GEMV and combined after it
+  const int owner_t = (int)threadIdx.x - (RES_WARPS * 32 - RES_TILE);
+  const int p = base + owner_t;
+  const bool owner = owner_t >= 0 && p < a.n_pix;
+  int flat = 0, pi = 0, pj = 0;
+  Taps<(LT > 0 ? LT : 0)> taps;
+  float atm_in = 0.f;
+  if (owner) {
+    flat = a.pix[p];
+    pi = flat / a.Np;
+    pj = flat - pi * a.Np;
+    if (LT > 0) taps.load(a.atmo, six, siy, pi, pj);
+    else if (LT == 0 && a.opd_atm) atm_in = a.opd_atm[flat];
+  }
   if (a.MT && a.n_m > 0) {
+    const int g = 2 * warp + (lane >> 4), l16 = lane & 15;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4* col = reinterpret_cast<const float4*>(a.MT + base) + lane;
-    const size_t stride4 = (size_t)a.n_pad / 4;
-#pragma unroll 4
-    for (int m = warp; m < a.n_m; m += 8) {
-      const float4 v = __ldg(col + (size_t)m * stride4);
+    // this tile's block of the basis: [n_m][RES_TILE] contiguous
+    const float4* col = reinterpret_cast<const float4*>(a.MT + (size_t)blockIdx.x * a.n_m * RES_TILE) + l16;
+#pragma unroll 8
+    for (int m = g; m < a.n_m; m += RES_GROUPS) {
+      const float4 v = __ldg(col + (size_t)m * (RES_TILE / 4));
       const float c = c_s[m];
       acc.x = fmaf(c, v.x, acc.x);
       acc.y = fmaf(c, v.y, acc.y);
       acc.z = fmaf(c, v.z, acc.z);
       acc.w = fmaf(c, v.w, acc.w);
     }
-    red[warp][4 * lane + 0] = acc.x;
-    red[warp][4 * lane + 1] = acc.y;
-    red[warp][4 * lane + 2] = acc.z;
-    red[warp][4 * lane + 3] = acc.w;
+    red[g][4 * l16 + 0] = acc.x;
+    red[g][4 * l16 + 1] = acc.y;
+    red[g][4 * l16 + 2] = acc.z;
+    red[g][4 * l16 + 3] = acc.w;
   }
   __syncthreads();
   double s1 = 0.0, s2 = 0.0;
-  if (threadIdx.x < 128) {
-    const int p = base + threadIdx.x;
-    if (p < a.n_pix) {
-      float dm = 0.f;
-      if (a.MT && a.n_m > 0) {
+  if (owner) {
+    float atm;
+    if (LT > 0) atm = taps.combine(sfx, sfy);
+    else if (LT == 0) atm = atm_in;
+    else atm = atmo_sample(a.atmo, six, siy, sfx, sfy, pi, pj);
+    float dm = 0.f;
+    if (a.MT && a.n_m > 0) {
 #pragma unroll
-        for (int w = 0; w < 8; ++w) dm += red[w][threadIdx.x];
-      }
-      const int flat = a.pix[p];
-      const int i = flat / a.Np, j = flat - i * a.Np;
-      float atm = 0.f;
-      if (a.atmo.L > 0) atm = atmo_sample(a.atmo, six, siy, sfx, sfy, i, j);
-      else if (a.opd_atm) atm = a.opd_atm[flat];
-      const float r = atm - a.dm_sign * dm;
-      a.out[flat] = r;
-      s1 = r;
-      s2 = (double)r * r;
+      for (int g = 0; g < RES_GROUPS; ++g) dm += red[g][owner_t];
     }
+    const float r = atm - a.dm_sign * dm;
+    a.out[flat] = r;
+    s1 = r;
+    s2 = (double)r * r;
   }
   if (a.wfe_part) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -130,7 +252,7 @@ __global__ void __launch_bounds__(256) residual_kernel(ResArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) {
       double t1 = 0.0, t2 = 0.0;
-      for (int w = 0; w < 8; ++w) {
+      for (int w = 0; w < RES_WARPS; ++w) {
         t1 += wred[0][w];
         t2 += wred[1][w];
       }
@@ -155,11 +277,38 @@ __global__ void integrate_kernel(float* cmd, const float* dmodes, const float* g
   if (m < n) cmd[m] += (gain ? gain[m] : 1.0f) * dmodes[m];
 }
 
+int residual_tiles(int n_pix) { return (n_pix + RES_TILE - 1) / RES_TILE; }
+
+pas_status atmo_pupil_launch(pas_ctx_t ctx, const AtmoArgs& a, const int* pix, int n_pix,
+                             const long long* d_step, float* out, cudaStream_t st) {
+  const int blocks = (n_pix + 255) / 256;
+  switch (a.L) {
+    case 1: atmo_pupil_kernel<1><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
+    case 2: atmo_pupil_kernel<2><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
+    case 3: atmo_pupil_kernel<3><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
+    case 4: atmo_pupil_kernel<4><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
+    case 5: atmo_pupil_kernel<5><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
+    case 6: atmo_pupil_kernel<6><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
+    default: atmo_pupil_kernel<0><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
+  }
+  return check_launch(ctx, "atmosphere kernel launch");
+}
+
 pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st) {
-  const int tiles = (a.n_pix + 127) / 128;
+  const int tiles = residual_tiles(a.n_pix);
   if (tiles == 0) return PAS_OK;
   const size_t smem = sizeof(float) * (size_t)std::max(a.n_m, 1);
-  residual_kernel<<<tiles, 256, smem, st>>>(a);
+  const dim3 g(tiles), blk(RES_WARPS * 32);
+  switch (a.atmo.L) {
+    case 0: residual_kernel<0><<<g, blk, smem, st>>>(a); break;
+    case 1: residual_kernel<1><<<g, blk, smem, st>>>(a); break;
+    case 2: residual_kernel<2><<<g, blk, smem, st>>>(a); break;
+    case 3: residual_kernel<3><<<g, blk, smem, st>>>(a); break;
+    case 4: residual_kernel<4><<<g, blk, smem, st>>>(a); break;
+    case 5: residual_kernel<5><<<g, blk, smem, st>>>(a); break;
+    case 6: residual_kernel<6><<<g, blk, smem, st>>>(a); break;
+    default: residual_kernel<-1><<<g, blk, smem, st>>>(a); break;
+  }
   return check_launch(ctx, "residual kernel launch");
 }
 
@@ -224,11 +373,16 @@ pas_status pas_dm_create(pas_ctx_t ctx, const float* h_M, int32_t n_pix, int32_t
   d->n_pix = n_pix;
   d->n_modes = n_modes;
   d->Np = Np;
-  d->n_pad = ((n_pix + 127) / 128) * 128;
+  // tiled layout: tile t (RES_TILE pixels) holds [n_modes][RES_TILE] contiguously
+  const int tiles = pas::residual_tiles(n_pix);
+  d->n_pad = tiles * pas::RES_TILE;
   d->T_obs = pas::obstruction_threshold(Np, obs);
   std::vector<float> MT((size_t)n_modes * d->n_pad, 0.f);
-  for (int p = 0; p < n_pix; ++p)
-    for (int m = 0; m < n_modes; ++m) MT[(size_t)m * d->n_pad + p] = h_M[(size_t)p * n_modes + m];
+  for (int p = 0; p < n_pix; ++p) {
+    const int t = p / pas::RES_TILE, pl = p % pas::RES_TILE;
+    for (int m = 0; m < n_modes; ++m)
+      MT[((size_t)t * n_modes + m) * pas::RES_TILE + pl] = h_M[(size_t)p * n_modes + m];
+  }
   pas_status st = pas::dev_alloc(ctx, (void**)&d->d_MT, sizeof(float) * MT.size());
   if (st == PAS_OK) st = pas::dev_alloc(ctx, (void**)&d->d_pix, sizeof(int32_t) * n_pix);
   if (st != PAS_OK) {

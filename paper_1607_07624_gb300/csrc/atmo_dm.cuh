@@ -14,7 +14,7 @@ struct AtmoArgs {
 struct ResArgs {
   AtmoArgs atmo;                   // L = 0: take opd_atm instead
   const float* opd_atm = nullptr;  // [Np][Np] or null (zero atmosphere)
-  const float* MT = nullptr;       // [n_m][n_pad] mode-major basis
+  const float* MT = nullptr;       // [tiles][n_m][64] basis, one contiguous block per pixel tile
   const int* pix = nullptr;        // [n_pix] flat pupil pixel indices
   int n_pix = 0, n_pad = 0, n_m = 0, Np = 0;
   const float* cmd = nullptr;      // [n_m] command
@@ -28,6 +28,11 @@ struct ResArgs {
 };
 
 pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st);
+// Number of CTAs (and of residual-WFE partials) of residual_launch for n_pix pixels.
+int residual_tiles(int n_pix);
+// Summed atmosphere at the device step on the listed pupil pixels of out [Np][Np].
+pas_status atmo_pupil_launch(pas_ctx_t ctx, const AtmoArgs& a, const int* pix, int n_pix,
+                             const long long* d_step, float* out, cudaStream_t st);
 
 }  // namespace pas
 

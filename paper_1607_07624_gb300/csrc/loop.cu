@@ -12,10 +12,6 @@
 #include "pyr.cuh"
 #include "recon.cuh"
 
-namespace pas {
-__global__ void step_increment_kernel(long long* step) { *step += 1; }
-}  // namespace pas
-
 struct pas_loop_s {
   pas_ctx_t ctx = nullptr;
   pas_atmo_t atmo = nullptr;
@@ -35,21 +31,30 @@ struct pas_loop_s {
   long long* d_step = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // profiling graph: the same step with event-record nodes between the kernels
+  cudaGraph_t prof_graph = nullptr;
+  cudaGraphExec_t prof_exec = nullptr;
+  cudaEvent_t prof_ev[PAS_LOOP_KERNELS + 1] = {};
 };
 
 // ev (optional): PAS_LOOP_KERNELS + 1 events recorded before each kernel and
 // after the last one.
 static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = nullptr) {
+  // atmosphere into the residual buffer, then residual = atmosphere - M c in place
+  if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+  pas_status s = pas::atmo_pupil_launch(L->ctx, L->atmo->args, L->dm->d_pix, L->dm->n_pix, L->d_step,
+                                        L->d_opd, st);
+  if (s != PAS_OK) return s;
   pas::ResArgs ra = pas::make_res_args(L->dm);
-  ra.atmo = L->atmo->args;
+  ra.opd_atm = L->d_opd;
   ra.cmd_ring = L->d_ring;
   ra.delay = L->delay;
   ra.d_step = L->d_step;
   ra.dm_sign = 1.0f;
   ra.out = L->d_opd;
   ra.wfe_part = L->d_wfe_part;
-  if (ev) cudaEventRecord(ev[0], st);
-  pas_status s = pas::residual_launch(L->ctx, ra, st);
+  if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
+  s = pas::residual_launch(L->ctx, ra, st);
   if (s != PAS_OK) return s;
   pas::LoopExtra fa;
   fa.frame_ctr = L->d_step;
@@ -59,7 +64,7 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   fa.wfe_hist = L->d_wfe;
   fa.wfe_hist_len = L->hist;
   fa.step = L->d_step;
-  s = pas::pyr_launch(L->pyr, L->d_opd, L->d_frame, L->d_slopes, st, &fa, false, ev ? ev + 1 : nullptr);
+  s = pas::pyr_launch(L->pyr, L->d_opd, L->d_frame, L->d_slopes, st, &fa, false, ev ? ev + 2 : nullptr);
   if (s != PAS_OK) return s;
   pas::ReconArgs rc;
   rc.s = L->d_slopes;
@@ -69,13 +74,11 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   rc.delay = L->delay;
   rc.step = L->d_step;
   rc.cmd_last = L->d_cmd;
-  if (ev) cudaEventRecord(ev[5], st);
+  rc.step_inc = L->d_step;
+  if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
   s = pas::recon_launch(L->rec, rc, st);
-  if (s != PAS_OK) return s;
-  if (ev) cudaEventRecord(ev[6], st);
-  pas::step_increment_kernel<<<1, 1, 0, st>>>(L->d_step);
-  if (ev) cudaEventRecord(ev[7], st);
-  return pas::check_launch(L->ctx, "step counter launch");
+  if (ev) cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
+  return s;
 }
 
 extern "C" {
@@ -84,6 +87,10 @@ void pas_loop_destroy(pas_loop_t L) {
   if (!L) return;
   if (L->exec) cudaGraphExecDestroy(L->exec);
   if (L->graph) cudaGraphDestroy(L->graph);
+  if (L->prof_exec) cudaGraphExecDestroy(L->prof_exec);
+  if (L->prof_graph) cudaGraphDestroy(L->prof_graph);
+  for (int i = 0; i <= PAS_LOOP_KERNELS; ++i)
+    if (L->prof_ev[i]) cudaEventDestroy(L->prof_ev[i]);
   pas::dev_free(L->d_opd);
   pas::dev_free(L->d_frame);
   pas::dev_free(L->d_slopes);
@@ -118,7 +125,7 @@ pas_status pas_loop_create(pas_ctx_t ctx, pas_atmo_t atmo, pas_pyr_t pyr, pas_re
   L->n_slopes = rec->n_slopes;
   L->nd = pas::pyr_nd(pyr);
   L->Np = dm->Np;
-  L->n_tiles = (dm->n_pix + 127) / 128;
+  L->n_tiles = pas::residual_tiles(dm->n_pix);
   pas_status st = PAS_OK;
   auto A = [&](void** p, size_t bytes) {
     if (st == PAS_OK) st = pas::dev_alloc(ctx, p, bytes);
@@ -212,35 +219,44 @@ pas_status pas_loop_step_eager(pas_loop_t L, int32_t n_steps) {
 pas_status pas_loop_profile(pas_loop_t L, int32_t n_steps, float* h_ms, int32_t cap, int32_t* n_kernels) {
   if (!L || !h_ms) return pas::set_global_error(PAS_EINVAL, "pas_loop_profile: NULL argument");
   PAS_CHECK_ARG(L->ctx, n_steps >= 1 && cap >= PAS_LOOP_KERNELS, "pas_loop_profile: bad n_steps or cap");
-  cudaEvent_t ev[PAS_LOOP_KERNELS + 1];
-  for (int i = 0; i <= PAS_LOOP_KERNELS; ++i) PAS_CUDA_TRY(L->ctx, cudaEventCreate(&ev[i]));
-  double acc[PAS_LOOP_KERNELS] = {0};
-  pas_status s = PAS_OK;
-  for (int t = 0; t < n_steps && s == PAS_OK; ++t) {
-    s = loop_enqueue(L, L->ctx->stream, ev);
-    if (s != PAS_OK) break;
-    cudaError_t e = cudaEventSynchronize(ev[PAS_LOOP_KERNELS]);
-    if (e != cudaSuccess) {
-      s = pas::set_error(L->ctx, PAS_ECUDA, "pas_loop_profile: %s", cudaGetErrorString(e));
-      break;
+  pas_ctx_t ctx = L->ctx;
+  if (!L->prof_exec) {
+    for (int i = 0; i <= PAS_LOOP_KERNELS; ++i) PAS_CUDA_TRY(ctx, cudaEventCreate(&L->prof_ev[i]));
+    PAS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    PAS_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+    pas_status s = loop_enqueue(L, ctx->capture_stream, L->prof_ev);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &g);
+    if (s != PAS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
     }
+    if (e != cudaSuccess) return pas::set_error(ctx, PAS_ECUDA, "profile capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&L->prof_exec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return pas::set_error(ctx, PAS_ECUDA, "profile instantiate: %s", cudaGetErrorString(e));
+    }
+    L->prof_graph = g;
+  }
+  double acc[PAS_LOOP_KERNELS] = {0};
+  for (int t = 0; t < n_steps; ++t) {
+    PAS_CUDA_TRY(ctx, cudaGraphLaunch(L->prof_exec, ctx->stream));
+    PAS_CUDA_TRY(ctx, cudaEventSynchronize(L->prof_ev[PAS_LOOP_KERNELS]));
     for (int k = 0; k < PAS_LOOP_KERNELS; ++k) {
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      PAS_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, L->prof_ev[k], L->prof_ev[k + 1]));
       acc[k] += ms;
     }
   }
-  for (int i = 0; i <= PAS_LOOP_KERNELS; ++i) cudaEventDestroy(ev[i]);
-  if (s != PAS_OK) return s;
   for (int k = 0; k < PAS_LOOP_KERNELS; ++k) h_ms[k] = (float)(acc[k] / n_steps);
   if (n_kernels) *n_kernels = PAS_LOOP_KERNELS;
   return PAS_OK;
 }
 
 const char* pas_loop_kernel_name(int32_t idx) {
-  static const char* names[PAS_LOOP_KERNELS] = {"residual_kernel", "pyr_rows_kernel", "pyr_cols_kernel",
-                                                "frame_kernel", "slopes_kernel", "recon_kernel",
-                                                "step_increment_kernel"};
+  static const char* names[PAS_LOOP_KERNELS] = {"atmo_pupil_kernel", "residual_kernel", "pyr_rows_kernel",
+                                                "pyr_cols_kernel", "slopes_kernel", "recon_kernel"};
   return (idx >= 0 && idx < PAS_LOOP_KERNELS) ? names[idx] : nullptr;
 }
 

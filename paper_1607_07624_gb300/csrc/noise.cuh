@@ -5,7 +5,8 @@
 //   uniform u = ((x >> 8) + 1/2) 2^-24 (exact);
 //   read noise: Box-Muller on block 0 words 0, 1;
 //   photons, lambda < 64: sequential-search inversion on block 0 word 2, starting
-//     from exp(-lambda) evaluated in double and rounded to float;
+//     from exp(-lambda) evaluated in double and rounded to float, each term
+//     p_k = p_{k-1} (lambda rn(1/k)) with the correctly rounded reciprocal;
 //   photons, lambda >= 64: Hoermann's (1993) PTRS transformed rejection on the pairs
 //     (word 2, word 3) of blocks 0, 1, 2, ...
 #pragma once
@@ -50,7 +51,7 @@ __device__ inline float poisson_draw(float lam, uint64_t seed, uint32_t pixel, u
     int k = 0;
     while (u > F && k < 256) {
       ++k;
-      p = __fmul_rn(p, __fdiv_rn(lam, (float)k));
+      p = __fmul_rn(p, __fmul_rn(lam, __frcp_rn((float)k)));
       F = __fadd_rn(F, p);
     }
     return (float)k;

@@ -27,7 +27,7 @@
 
 namespace pas {
 
-constexpr int ROWS_PER_CTA = 8;
+constexpr int MAX_ROWS_PER_CTA = 8;  // rows pass: one warp per pupil row
 
 struct RowArgs {
   const float* opd;     // [Np][Np]
@@ -36,8 +36,27 @@ struct RowArgs {
   const float* beta;    // [n_s] cycles per pixel (tilt_y + input ramp)
   float2* H;            // [n_s][N][Np]
   int Np, off;
+  int n_s, s_chunk;     // distinct sin values; at most s_chunk per CTA
   int T_obs;            // obstruction threshold (integer)
   float inv_hi, inv_lo; // 1/lambda split in two floats
+};
+
+// Detector frame, noise and slopes, done by the last CTAs of the columns pass.
+struct FrameArgs {
+  float* frame;                // [nd*nd]
+  const unsigned char* vpix;   // [nd*nd] 1: quadrant pixel of a valid sub-aperture
+  double* flux_part;           // [nd] per detector column
+  unsigned int* done_col;      // [nd] CTA completion counters (0 between launches)
+  long long* frame_ctr;
+  int ctr_increment;
+  int G, np;
+  float invK, scale, ron;
+  unsigned long long seed;
+  const int* valid;
+  const float* sn;             // [2nv] or null
+  float* slopes;               // [2nv] or null
+  int nv, n_sub, local_norm;
+  LoopExtra wfe;               // wfe.wfe_part null: no WFE
 };
 
 struct ColArgs {
@@ -48,105 +67,206 @@ struct ColArgs {
   const int* kmap;      // [K] -> rows-pass index
   float* part;          // [G][nd][nd]
   int Np, off, K, kper, nd, b;
+  FrameArgs fin;
 };
 
 
 
 template <int N>
-__global__ void __launch_bounds__(ROWS_PER_CTA * 32)
+__global__ void __launch_bounds__(MAX_ROWS_PER_CTA * 32)
 pyr_rows_kernel(RowArgs a) {
+  constexpr int TWN = tw_size(N), BL = buf_len(N), PITCH = BL | 1;
   extern __shared__ float2 smem[];
   float2* tw_s = smem;
-  float2* mk_s = smem + N;
-  float2* bufs = smem + 2 * N;
-  for (int t = threadIdx.x; t < N; t += blockDim.x) {
-    tw_s[t] = a.tw[t];
-    mk_s[t] = a.mask[t];
+  float2* mk_s = smem + TWN;
+  float2* tilt_s = mk_s + BL;                       // [s_chunk][Np]
+  const int rows = blockDim.x >> 5;
+  float2* phs = tilt_s + a.s_chunk * a.Np;          // [rows][Np]
+  float2* bufs = phs + rows * a.Np;                 // [rows][PITCH]
+  const int Np = a.Np, off = a.off;
+  const int i0 = blockIdx.x * rows;
+  const int s0 = (blockIdx.y * a.n_s) / gridDim.y, s1 = ((blockIdx.y + 1) * a.n_s) / gridDim.y;
+  for (int t = threadIdx.x; t < TWN; t += blockDim.x) tw_s[t] = a.tw[t];
+  for (int t = threadIdx.x; t < BL; t += blockDim.x) mk_s[t] = a.mask[t];
+  // tilt along the row (with the input centring ramp and (-1)^j) per sin value
+  const float cj = 0.5f * (float)(Np - 1);
+  for (int t = threadIdx.x; t < (s1 - s0) * Np; t += blockDim.x) {
+    const int sl = t / Np, j = t - sl * Np;
+    float sn, cs;
+    sincospif(2.0f * ((float)j - cj) * a.beta[s0 + sl], &sn, &cs);
+    tilt_s[t] = (j & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
   }
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i0 = blockIdx.x * ROWS_PER_CTA;
   const int i = i0 + warp;
-  const int s = blockIdx.y;
-  float2* buf = bufs + warp * (N + 1);
-  if (i < a.Np) {
-    const float beta = a.beta[s];
-    const float* orow = a.opd + (size_t)i * a.Np;
-    const int Np = a.Np, off = a.off;
+  float2* buf = bufs + warp * PITCH;
+  // pupil phasor A exp(2 pi i opd / lambda) of this warp's row, kept for all s
+  float2* phrow = phs + warp * Np;
+  {
     const int ai = 2 * i - Np + 1;
     const int ai2 = ai * ai;
-    const float cj = 0.5f * (float)(Np - 1);
-    auto load = [&](int x) -> float2 {
-      const int j = x - off;
-      if ((unsigned)j < (unsigned)Np) {
-        const int bj = 2 * j - Np + 1;
-        const int d2 = ai2 + bj * bj;
-        if (d2 <= Np * Np && d2 >= a.T_obs) {
-          const float o = __ldg(orow + j);
-          // opd / lambda in cycles, reduced to [-1/2, 1/2] with an exact split
-          const float hi = o * a.inv_hi;
-          const float err = fmaf(o, a.inv_hi, -hi);
-          const float lo = fmaf(o, a.inv_lo, err);
-          const float cyc = (hi - rintf(hi)) + lo + ((float)j - cj) * beta;
-          float sn, cs;
-          sincospif(2.0f * cyc, &sn, &cs);
-          return (j & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
-        }
+    const float* orow = a.opd + (size_t)min(i, Np - 1) * Np;
+    for (int j = lane; j < Np; j += 32) {
+      float2 v = make_float2(0.f, 0.f);
+      const int bj = 2 * j - Np + 1;
+      const int d2 = ai2 + bj * bj;
+      if (i < Np && d2 <= Np * Np && d2 >= a.T_obs) {
+        const float o = __ldg(orow + j);
+        // opd / lambda in cycles, reduced to [-1/2, 1/2] with an exact split
+        const float hi = o * a.inv_hi;
+        const float err = fmaf(o, a.inv_hi, -hi);
+        const float lo = fmaf(o, a.inv_lo, err);
+        float sn, cs;
+        sincospif(2.0f * ((hi - rintf(hi)) + lo), &sn, &cs);
+        v = make_float2(cs, sn);
       }
-      return make_float2(0.f, 0.f);
-    };
-    auto store = [&](int, int, int x, float2 v) { buf[x] = v; };
-    fft_mask_ifft<N>(buf, tw_s, mk_s, lane, load, store);
+      phrow[j] = v;
+    }
   }
   __syncthreads();
-  // transposed, coalesced write: H[s][y][i0 + r]
-  float2* Hs = a.H + (size_t)s * N * a.Np;
-  const int nr = min(ROWS_PER_CTA, a.Np - i0);
-  for (int idx = threadIdx.x; idx < N * ROWS_PER_CTA; idx += blockDim.x) {
-    const int r = idx % ROWS_PER_CTA, y = idx / ROWS_PER_CTA;
-    if (r < nr) Hs[(size_t)y * a.Np + i0 + r] = bufs[r * (N + 1) + y];
+  const int nr = min(rows, Np - i0);
+  for (int s = s0; s < s1; ++s) {
+    const float2* tl = tilt_s + (s - s0) * Np;
+    if (i < Np) {
+      auto load = [&](int, int, int x) -> float2 {
+        const int j = x - off;
+        if ((unsigned)j < (unsigned)Np) return cmul(phrow[j], tl[j]);
+        return make_float2(0.f, 0.f);
+      };
+      auto store = [&](int, int, int x, float2 v) { buf[phys(x)] = v; };
+      fft_mask_ifft<N>(buf, tw_s, mk_s, lane, load, store);
+    }
+    __syncthreads();
+    // transposed write: H[s][y][i0 + r], rows x 8 contiguous bytes per y
+    float2* Hs = a.H + (size_t)s * N * Np;
+    for (int idx = threadIdx.x; idx < N * rows; idx += blockDim.x) {
+      const int r = idx % rows, y = idx / rows;
+      if (r < nr) Hs[(size_t)y * Np + i0 + r] = bufs[r * PITCH + phys(y)];
+    }
+    __syncthreads();
+  }
+}
+
+__device__ inline double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (warp == 0) {
+    r = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    if (lane == 0) red[0] = r;
+  }
+  __syncthreads();
+  r = red[0];
+  return r;
+}
+
+// Column q of the detector: sum of the G groups' partials / K, noise, and the
+// column's flux over the valid sub-apertures' pixels (run by the column's last CTA).
+__device__ void finish_column(const FrameArgs& f, const float* part, int q, int nd, double* red) {
+  const long long fidx = f.frame_ctr ? *f.frame_ctr : 0;
+  double flux = 0.0;
+  for (int p = threadIdx.x; p < nd; p += blockDim.x) {
+    const int pix = p * nd + q;
+    float v = 0.f;
+    for (int gg = 0; gg < f.G; ++gg) v += __ldcg(part + (size_t)gg * f.np + pix);
+    v *= f.invK;
+    v = noisy_pixel(v, f.scale, f.ron, f.seed, (uint32_t)pix, (uint64_t)fidx);
+    f.frame[pix] = v;
+    if (f.vpix[pix]) flux += v;
+  }
+  flux = block_sum(flux, red);
+  if (threadIdx.x == 0) {
+    f.flux_part[q] = flux;
+    f.done_col[q] = 0u;
+  }
+}
+
+// Normalised slopes: every CTA forms the global flux from the per-column partials
+// (fixed order) and computes its share of the valid sub-apertures; CTA 0 also
+// closes the loop step's residual WFE and advances the frame counter.
+__global__ void __launch_bounds__(256) slopes_kernel(FrameArgs f, int nd) {
+  __shared__ double red[32];
+  double fl = 0.0;
+  for (int t = threadIdx.x; t < nd; t += blockDim.x) fl += f.flux_part[t];
+  const float F = (float)(block_sum(fl, red) / (double)f.nv);
+  const int ns = f.n_sub;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f.slopes && j < f.nv) {
+    const int v = f.valid[j], r = v / ns, c = v - r * ns;
+    const float q00 = f.frame[r * nd + c], q01 = f.frame[r * nd + ns + c];
+    const float q10 = f.frame[(ns + r) * nd + c], q11 = f.frame[(ns + r) * nd + ns + c];
+    const float den = f.local_norm ? (q00 + q01 + q10 + q11) : F;
+    const float inv = 1.0f / den;
+    float sx = ((q10 + q11) - (q00 + q01)) * inv;
+    float sy = ((q01 + q11) - (q00 + q10)) * inv;
+    if (f.sn) {
+      sx -= f.sn[j];
+      sy -= f.sn[f.nv + j];
+    }
+    f.slopes[j] = sx;
+    f.slopes[f.nv + j] = sy;
+  }
+  if (blockIdx.x == 0) {
+    if (f.wfe.wfe_part) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int t = threadIdx.x; t < f.wfe.n_wfe_part; t += blockDim.x) {
+        const double2 w = f.wfe.wfe_part[t];
+        s1 += w.x;
+        s2 += w.y;
+      }
+      s1 = block_sum(s1, red);
+      s2 = block_sum(s2, red);
+      if (threadIdx.x == 0) {
+        const double m = s1 * f.wfe.inv_npix;
+        const double var = fmax(s2 * f.wfe.inv_npix - m * m, 0.0);
+        f.wfe.wfe_hist[(*f.wfe.step) % f.wfe.wfe_hist_len] = sqrt(var);
+      }
+    }
+    if (threadIdx.x == 0 && f.ctr_increment && f.frame_ctr) *f.frame_ctr += 1;
   }
 }
 
 template <int N>
 __global__ void __launch_bounds__(512)
 pyr_cols_kernel(ColArgs a) {
+  constexpr int TWN = tw_size(N), BL = buf_len(N), PITCH = BL | 1;
   extern __shared__ float2 smem[];
   float2* tw_s = smem;
-  float2* mk_s = smem + N;
-  float2* tilt_s = smem + 2 * N;                  // [kper][Np]
-  float2* bufs = tilt_s + a.kper * a.Np;          // [b][N + 1]
+  float2* mk_s = smem + TWN;
+  float2* tilt_s = mk_s + BL;                     // [Np]: tilt of the current k
+  float2* bufs = tilt_s + a.Np;                   // [b][PITCH]
   const int Np = a.Np;
   const int q = blockIdx.x;                       // detector column
   const int g = blockIdx.y;                       // modulation group
   const int k0 = g * a.kper;
   const int kc = min(a.kper, a.K - k0);
-  for (int t = threadIdx.x; t < N; t += blockDim.x) {
-    tw_s[t] = a.tw[t];
-    mk_s[t] = a.mask[t];
-  }
+  for (int t = threadIdx.x; t < TWN; t += blockDim.x) tw_s[t] = a.tw[t];
+  for (int t = threadIdx.x; t < BL; t += blockDim.x) mk_s[t] = a.mask[t];
   const float ci = 0.5f * (float)(Np - 1);
-  for (int t = threadIdx.x; t < kc * Np; t += blockDim.x) {
-    const int kk = t / Np, i = t - kk * Np;
-    float sn, cs;
-    sincospif(2.0f * ((float)i - ci) * a.alpha[k0 + kk], &sn, &cs);
-    tilt_s[t] = (i & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
-  }
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int y = q * a.b + warp;
-  float2* buf = bufs + warp * (N + 1);
+  float2* buf = bufs + warp * PITCH;
   using OS = OutShape<N>;
   float acc[OS::PER_LANE];
 #pragma unroll
   for (int t = 0; t < OS::PER_LANE; ++t) acc[t] = 0.f;
   for (int kk = 0; kk < kc; ++kk) {
+    __syncthreads();                              // previous k's tilt no longer read
+    const float alpha = a.alpha[k0 + kk];
+    for (int i = threadIdx.x; i < Np; i += blockDim.x) {
+      float sn, cs;
+      sincospif(2.0f * ((float)i - ci) * alpha, &sn, &cs);
+      tilt_s[i] = (i & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
+    }
+    __syncthreads();
     const float2* Hcol = a.H + ((size_t)a.kmap[k0 + kk] * N + y) * Np;
-    const float2* tl = tilt_s + kk * Np;
     const int off = a.off;
-    auto load = [&](int x) -> float2 {
+    auto load = [&](int, int, int x) -> float2 {
       const int i = x - off;
-      if ((unsigned)i < (unsigned)Np) return cmul(__ldg(Hcol + i), tl[i]);
+      if ((unsigned)i < (unsigned)Np) return cmul(__ldg(Hcol + i), tilt_s[i]);
       return make_float2(0.f, 0.f);
     };
     auto store = [&](int jb, int k, int, float2 v) {
@@ -171,119 +291,26 @@ pyr_cols_kernel(ColArgs a) {
   for (int p = threadIdx.x; p < nd; p += blockDim.x) {
     float sum = 0.f;
     for (int w = 0; w < b; ++w) {
-      const float* col = reinterpret_cast<const float*>(bufs + w * (N + 1));
+      const float* col = reinterpret_cast<const float*>(bufs + w * PITCH);
       for (int xx = 0; xx < b; ++xx) sum += col[p * b + xx];
     }
     out[(size_t)p * nd + q] = sum;
   }
-}
-
-__device__ inline double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (warp == 0) {
-    r = lane < nw ? red[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-    if (lane == 0) red[0] = r;
-  }
-  __syncthreads();
-  r = red[0];
-  return r;
-}
-
-struct FrameArgs {
-  const float* part;           // [G][nd*nd]
-  float* frame;                // [nd*nd]
-  const unsigned char* vpix;   // [nd*nd] 1: quadrant pixel of a valid sub-aperture
-  double* flux_part;           // [gridDim.x]
-  const long long* frame_ctr;
-  int G, np;
-  float invK, scale, ron;
-  unsigned long long seed;
-};
-
-struct SlopeArgs {
-  const float* frame;
-  const int* valid;
-  const float* sn;             // [2nv] or null
-  float* slopes;               // [2nv] or null
-  const double* flux_part;
-  int n_flux_part, nv, n_sub, nd, local_norm;
-  long long* frame_ctr;
-  int ctr_increment;
-  LoopExtra wfe;               // wfe.wfe_part null: no WFE
-};
-
-// Detector frame: sum of the modulation groups' partial frames, / K, noise; and
-// the per-CTA partial flux over the valid sub-apertures' pixels.
-__global__ void __launch_bounds__(256) frame_kernel(FrameArgs a) {
+  // the last of the G groups of column q builds that detector column; the CTA
+  // that completes the last column computes the slopes
   __shared__ double red[32];
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  double flux = 0.0;
-  if (p < a.np) {
-    float v = 0.f;
-    for (int gg = 0; gg < a.G; ++gg) v += a.part[(size_t)gg * a.np + p];
-    v *= a.invK;
-    const long long fidx = a.frame_ctr ? *a.frame_ctr : 0;
-    v = noisy_pixel(v, a.scale, a.ron, a.seed, (uint32_t)p, (uint64_t)fidx);
-    a.frame[p] = v;
-    if (a.vpix[p]) flux = v;
-  }
-  flux = block_sum(flux, red);
-  if (threadIdx.x == 0) a.flux_part[blockIdx.x] = flux;
+  __shared__ bool flag;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) flag = atomicAdd(a.fin.done_col + q, 1u) == (unsigned)a.fin.G - 1;
+  __syncthreads();
+  if (!flag) return;
+  __threadfence();
+  finish_column(a.fin, a.part, q, nd, red);
 }
 
-// Normalised slopes of the valid sub-apertures; CTA 0 also closes the step's
-// residual WFE and advances the noise frame counter.
-__global__ void __launch_bounds__(256) slopes_kernel(SlopeArgs a) {
-  __shared__ double red[32];
-  __shared__ double F_s;
-  if (threadIdx.x == 0) {
-    double f = 0.0;
-    for (int i = 0; i < a.n_flux_part; ++i) f += a.flux_part[i];
-    F_s = f / (double)a.nv;
-  }
-  __syncthreads();
-  const float F = (float)F_s;
-  const int ns = a.n_sub, nd = a.nd;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < a.nv && a.slopes) {
-    const int v = a.valid[j], r = v / ns, c = v - r * ns;
-    const float q00 = a.frame[r * nd + c], q01 = a.frame[r * nd + ns + c];
-    const float q10 = a.frame[(ns + r) * nd + c], q11 = a.frame[(ns + r) * nd + ns + c];
-    const float den = a.local_norm ? (q00 + q01 + q10 + q11) : F;
-    const float inv = 1.0f / den;
-    float sx = ((q10 + q11) - (q00 + q01)) * inv;
-    float sy = ((q01 + q11) - (q00 + q10)) * inv;
-    if (a.sn) {
-      sx -= a.sn[j];
-      sy -= a.sn[a.nv + j];
-    }
-    a.slopes[j] = sx;
-    a.slopes[a.nv + j] = sy;
-  }
-  if (blockIdx.x == 0) {
-    if (a.wfe.wfe_part) {
-      double s1 = 0.0, s2 = 0.0;
-      for (int t = threadIdx.x; t < a.wfe.n_wfe_part; t += blockDim.x) {
-        s1 += a.wfe.wfe_part[t].x;
-        s2 += a.wfe.wfe_part[t].y;
-      }
-      s1 = block_sum(s1, red);
-      s2 = block_sum(s2, red);
-      if (threadIdx.x == 0) {
-        const double m = s1 * a.wfe.inv_npix;
-        const double var = fmax(s2 * a.wfe.inv_npix - m * m, 0.0);
-        a.wfe.wfe_hist[(*a.wfe.step) % a.wfe.wfe_hist_len] = sqrt(var);
-      }
-    }
-    if (threadIdx.x == 0 && a.ctr_increment && a.frame_ctr) *a.frame_ctr += 1;
-  }
-}
+
+
 
 __global__ void ccd_noise_kernel(const float* in, float* out, int n, float scale, float ron,
                                  unsigned long long seed, long long fidx) {
@@ -296,12 +323,12 @@ __global__ void ccd_noise_kernel(const float* in, float* out, int n, float scale
 struct PyrKernels {
   void (*rows)(RowArgs);
   void (*cols)(ColArgs);
-  int per_lane;
+  int tw_n, buf_n, pitch;
 };
 
 template <int N>
 PyrKernels kernels_for() {
-  return PyrKernels{pyr_rows_kernel<N>, pyr_cols_kernel<N>, OutShape<N>::PER_LANE};
+  return PyrKernels{pyr_rows_kernel<N>, pyr_cols_kernel<N>, tw_size(N), buf_len(N), buf_len(N) | 1};
 }
 
 #define PAS_PYR_SIZES(X) X(16) X(24) X(32) X(40) X(48) X(64) X(80) X(96) X(120) X(128) X(160) \
@@ -322,10 +349,10 @@ static bool lookup_kernels(int N, PyrKernels* k) {
 
 // Digit-reversed frequency of in-place position p for the radix list of N.
 static int digit_reversed_freq(int N, int p) {
-  const int M = radix_count(N);
+  const int M = plan_count(N);
   int rem = p, L = N, mult = 1, u = 0;
   for (int i = 0; i < M; ++i) {
-    const int R = radix_at(N, i), S = L / R;
+    const int R = plan_radix(N, i), S = L / R;
     const int k = rem / S;
     rem -= k * S;
     u += k * mult;
@@ -342,6 +369,7 @@ struct pas_pyr_s {
   pas_pyr_params p{};
   pas::PyrKernels kern{};
   int b = 0, nd = 0, n_s = 0, G = 0, kper = 0, n_valid = 0, n_pupil = 0;
+  int rows = 4, s_chunk = 1, n_schunks = 1;
   int64_t T_obs = 0;
   float inv_hi = 0.f, inv_lo = 0.f;
   size_t smem_rows = 0, smem_cols = 0;
@@ -357,8 +385,8 @@ struct pas_pyr_s {
   float* d_frame = nullptr;
   long long* d_frame_ctr = nullptr;
   unsigned char* d_vpix = nullptr;
+  unsigned int* d_done_col = nullptr;
   double* d_flux_part = nullptr;
-  int n_fb = 0;
   float photon_scale = 0.f, ron = 0.f;
   unsigned long long seed = 0;
   bool has_sn = false;
@@ -366,9 +394,12 @@ struct pas_pyr_s {
 
 namespace pas {
 
-// Launch the three pyramid kernels. wfe fields of `fa` may be filled by the loop.
-pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes,
-                      cudaStream_t st, const LoopExtra* fa_extra, bool increment_ctr, cudaEvent_t* ev) {
+size_t rows_smem(pas_pyr_t y, int rows, int s_chunk) {
+  return sizeof(float2) * ((size_t)y->kern.tw_n + y->kern.buf_n + (size_t)s_chunk * y->p.Np +
+                           (size_t)rows * (y->p.Np + y->kern.pitch));
+}
+
+static void launch_rows(pas_pyr_t y, const float* d_opd, cudaStream_t st) {
   const pas_pyr_params& p = y->p;
   RowArgs ra;
   ra.opd = d_opd;
@@ -381,9 +412,15 @@ pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_
   ra.T_obs = (int)y->T_obs;
   ra.inv_hi = y->inv_hi;
   ra.inv_lo = y->inv_lo;
-  dim3 gr((p.Np + ROWS_PER_CTA - 1) / ROWS_PER_CTA, y->n_s);
-  if (ev) cudaEventRecord(ev[0], st);
-  y->kern.rows<<<gr, ROWS_PER_CTA * 32, y->smem_rows, st>>>(ra);
+  ra.n_s = y->n_s;
+  ra.s_chunk = y->s_chunk;
+  dim3 gr((p.Np + y->rows - 1) / y->rows, y->n_schunks);
+  y->kern.rows<<<gr, y->rows * 32, rows_smem(y, y->rows, y->s_chunk), st>>>(ra);
+}
+
+static void launch_cols(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream_t st,
+                        const LoopExtra* fa_extra, bool increment_ctr) {
+  const pas_pyr_params& p = y->p;
   ColArgs ca;
   ca.H = y->d_H;
   ca.tw = y->d_tw;
@@ -397,40 +434,58 @@ pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_
   ca.kper = y->kper;
   ca.nd = y->nd;
   ca.b = y->b;
-  dim3 gc(y->nd, y->G);
-  if (ev) cudaEventRecord(ev[1], st);
-  y->kern.cols<<<gc, y->b * 32, y->smem_cols, st>>>(ca);
   long long* ctr = fa_extra ? fa_extra->frame_ctr : y->d_frame_ctr;
-  FrameArgs fa;
-  fa.part = y->d_part;
+  FrameArgs& fa = ca.fin;
   fa.frame = d_frame ? d_frame : y->d_frame;
   fa.vpix = y->d_vpix;
   fa.flux_part = y->d_flux_part;
+  fa.done_col = y->d_done_col;
   fa.frame_ctr = ctr;
+  fa.ctr_increment = increment_ctr ? 1 : 0;
   fa.G = y->G;
   fa.np = y->nd * y->nd;
   fa.invK = 1.0f / (float)p.K;
   fa.scale = y->photon_scale;
   fa.ron = y->ron;
   fa.seed = y->seed;
-  if (ev) cudaEventRecord(ev[2], st);
-  frame_kernel<<<y->n_fb, 256, 0, st>>>(fa);
-  SlopeArgs sa;
-  sa.frame = fa.frame;
-  sa.valid = y->d_valid;
-  sa.sn = y->has_sn ? y->d_sn : nullptr;
-  sa.slopes = d_slopes;
-  sa.flux_part = y->d_flux_part;
-  sa.n_flux_part = y->n_fb;
-  sa.nv = y->n_valid;
-  sa.n_sub = p.n_sub;
-  sa.nd = y->nd;
-  sa.local_norm = p.local_norm;
-  sa.frame_ctr = ctr;
-  sa.ctr_increment = increment_ctr ? 1 : 0;
-  if (fa_extra) sa.wfe = *fa_extra;
-  if (ev) cudaEventRecord(ev[3], st);
-  slopes_kernel<<<(y->n_valid + 255) / 256, 256, 0, st>>>(sa);
+  fa.valid = y->d_valid;
+  fa.sn = y->has_sn ? y->d_sn : nullptr;
+  fa.slopes = d_slopes;
+  fa.nv = y->n_valid;
+  fa.n_sub = p.n_sub;
+  fa.local_norm = p.local_norm;
+  fa.wfe = fa_extra ? *fa_extra : LoopExtra();
+  dim3 gc(y->nd, y->G);
+  y->kern.cols<<<gc, y->b * 32, y->smem_cols, st>>>(ca);
+}
+
+static void launch_slopes(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream_t st,
+                          const LoopExtra* fa_extra, bool increment_ctr) {
+  FrameArgs f{};
+  f.frame = d_frame ? d_frame : y->d_frame;
+  f.flux_part = y->d_flux_part;
+  f.frame_ctr = fa_extra ? fa_extra->frame_ctr : y->d_frame_ctr;
+  f.ctr_increment = increment_ctr ? 1 : 0;
+  f.valid = y->d_valid;
+  f.sn = y->has_sn ? y->d_sn : nullptr;
+  f.slopes = d_slopes;
+  f.nv = y->n_valid;
+  f.n_sub = y->p.n_sub;
+  f.local_norm = y->p.local_norm;
+  f.wfe = fa_extra ? *fa_extra : LoopExtra();
+  slopes_kernel<<<(y->n_valid + 255) / 256, 256, 0, st>>>(f, y->nd);
+}
+
+// Launch the pyramid kernels (rows pass, columns pass with the detector frame,
+// noise and slopes). `fa_extra`: the loop's frame counter and WFE fields.
+pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes,
+                      cudaStream_t st, const LoopExtra* fa_extra, bool increment_ctr, cudaEvent_t* ev) {
+  if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+  launch_rows(y, d_opd, st);
+  if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
+  launch_cols(y, d_frame, d_slopes, st, fa_extra, increment_ctr);
+  if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
+  launch_slopes(y, d_frame, d_slopes, st, fa_extra, increment_ctr);
   return check_launch(y->ctx, "pas_pyr_measure launch");
 }
 
@@ -460,6 +515,7 @@ void pas_pyr_destroy(pas_pyr_t y) {
   pas::dev_free(y->d_frame);
   pas::dev_free(y->d_frame_ctr);
   pas::dev_free(y->d_vpix);
+  pas::dev_free(y->d_done_col);
   pas::dev_free(y->d_flux_part);
   delete y;
 }
@@ -545,30 +601,38 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
     double th = 2.0 * M_PI * (double)rep_of_s[s] / (double)p.K;
     beta[s] = (float)(p.mod_radius * std::sin(th) / p.Np - ramp);
   }
-  // twiddles and digit-reversed pyramid mask (delta = N/4): phase = (pi/2)|u~|
-  std::vector<float2> tw(p.N), mk(p.N);
-  for (int j = 0; j < p.N; ++j) {
-    double a = -2.0 * M_PI * (double)j / (double)p.N;
-    tw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
-    int u = pas::digit_reversed_freq(p.N, j);
-    double ut = std::fabs((double)u - 0.5 * (p.N - 1));
-    double ph = 0.5 * M_PI * ut;
-    mk[j] = make_float2((float)(std::cos(ph) / p.N), (float)(std::sin(ph) / p.N));
+  // per-pass twiddle tables ([k-1][n1] = w_L^{n1 k}) and the digit-reversed
+  // pyramid mask (delta = N/4: phase (pi/2)|u~|, divided by N) in padded layout
+  std::vector<float2> tw(kern.tw_n), mk(kern.buf_n, make_float2(0.f, 0.f));
+  {
+    const int M = pas::plan_count(p.N);
+    for (int pass = 0; pass + 1 < M; ++pass) {
+      const int R = pas::plan_radix(p.N, pass), L = pas::block_len(p.N, pass), S = L / R;
+      const int off = pas::tw_offset(p.N, pass);
+      for (int k = 1; k < R; ++k)
+        for (int n1 = 0; n1 < S; ++n1) {
+          const double a = -2.0 * M_PI * (double)(n1 * k) / (double)L;
+          tw[off + (k - 1) * S + n1] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    }
+    for (int j = 0; j < p.N; ++j) {
+      const int u = pas::digit_reversed_freq(p.N, j);
+      const double ut = std::fabs((double)u - 0.5 * (p.N - 1));
+      const double ph = 0.5 * M_PI * ut;
+      mk[pas::phys(j)] = make_float2((float)(std::cos(ph) / p.N), (float)(std::sin(ph) / p.N));
+    }
   }
   double inv = 1.0 / p.wavelength_nm;
   y->inv_hi = (float)inv;
   y->inv_lo = (float)(inv - (double)y->inv_hi);
 
-  // launch geometry
-  {
-    int sms = ctx->sm_count > 0 ? ctx->sm_count : 148;
-    int G = (4 * sms + y->nd - 1) / y->nd;
-    G = std::max(1, std::min(G, p.K));
-    y->kper = (p.K + G - 1) / G;
-    y->G = (p.K + y->kper - 1) / y->kper;
-  }
-  y->smem_rows = sizeof(float2) * (2 * (size_t)p.N + (size_t)pas::ROWS_PER_CTA * (p.N + 1));
-  y->smem_cols = sizeof(float2) * (2 * (size_t)p.N + (size_t)y->kper * p.Np + (size_t)b * (p.N + 1));
+  // rows pass default: 4 rows per CTA, chunks of about 4 distinct sin values
+  // (pas_pyr_autotune measures the alternatives)
+  y->rows = 4;
+  y->n_schunks = (y->n_s + 3) / 4;
+  y->s_chunk = (y->n_s + y->n_schunks - 1) / y->n_schunks;
+  y->smem_rows = pas::rows_smem(y, pas::MAX_ROWS_PER_CTA, y->n_s);  // largest candidate
+  y->smem_cols = sizeof(float2) * ((size_t)kern.tw_n + kern.buf_n + (size_t)p.Np + (size_t)b * kern.pitch);
 
   pas_status st = PAS_OK;
   auto A = [&](void** ptr, size_t bytes) {
@@ -576,18 +640,18 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   };
   A((void**)&y->d_valid, sizeof(int32_t) * y->n_valid);
   A((void**)&y->d_sn, sizeof(float) * 2 * y->n_valid);
-  A((void**)&y->d_tw, sizeof(float2) * p.N);
-  A((void**)&y->d_mask, sizeof(float2) * p.N);
+  A((void**)&y->d_tw, sizeof(float2) * kern.tw_n);
+  A((void**)&y->d_mask, sizeof(float2) * kern.buf_n);
   A((void**)&y->d_alpha, sizeof(float) * p.K);
   A((void**)&y->d_beta, sizeof(float) * y->n_s);
   A((void**)&y->d_kmap, sizeof(int) * p.K);
   A((void**)&y->d_H, sizeof(float2) * (size_t)y->n_s * p.N * p.Np);
-  A((void**)&y->d_part, sizeof(float) * (size_t)y->G * y->nd * y->nd);
+  A((void**)&y->d_part, sizeof(float) * (size_t)p.K * y->nd * y->nd);  // G <= K groups
   A((void**)&y->d_frame, sizeof(float) * y->nd * y->nd);
   A((void**)&y->d_frame_ctr, sizeof(long long));
-  y->n_fb = (y->nd * y->nd + 255) / 256;
   A((void**)&y->d_vpix, (size_t)y->nd * y->nd);
-  A((void**)&y->d_flux_part, sizeof(double) * y->n_fb);
+  A((void**)&y->d_flux_part, sizeof(double) * y->nd);
+  A((void**)&y->d_done_col, sizeof(unsigned int) * y->nd);
   if (st != PAS_OK) {
     pas_pyr_destroy(y);
     return st;
@@ -597,8 +661,8 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
     if (e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
   };
   C(y->d_valid, valid.data(), sizeof(int32_t) * y->n_valid);
-  C(y->d_tw, tw.data(), sizeof(float2) * p.N);
-  C(y->d_mask, mk.data(), sizeof(float2) * p.N);
+  C(y->d_tw, tw.data(), sizeof(float2) * kern.tw_n);
+  C(y->d_mask, mk.data(), sizeof(float2) * kern.buf_n);
   C(y->d_alpha, alpha.data(), sizeof(float) * p.K);
   C(y->d_beta, beta.data(), sizeof(float) * y->n_s);
   C(y->d_kmap, kmap.data(), sizeof(int) * p.K);
@@ -612,10 +676,30 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   }
   if (e == cudaSuccess) e = cudaMemset(y->d_sn, 0, sizeof(float) * 2 * y->n_valid);
   if (e == cudaSuccess) e = cudaMemset(y->d_frame_ctr, 0, sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemset(y->d_done_col, 0, sizeof(unsigned int) * y->nd);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kern.rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)y->smem_rows);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kern.cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)y->smem_cols);
+  // modulation grouping: the columns pass runs nd x G CTAs of b warps, each warp
+  // doing kper = ceil(K / G) transforms; pick G minimising waves x kper
+  int occ = 1;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern.cols, b * 32, y->smem_cols);
+  if (e == cudaSuccess) {
+    const int slots = std::max(1, occ) * std::max(1, ctx->sm_count);
+    double best = 1e30;
+    for (int G = 1; G <= p.K; ++G) {
+      const int kper = (p.K + G - 1) / G, Gc = (p.K + kper - 1) / kper;
+      const int waves = (y->nd * Gc + slots - 1) / slots;
+      const double cost = (double)waves * kper + 1e-3 * Gc;
+      if (cost < best) {
+        best = cost;
+        y->kper = kper;
+        y->G = Gc;
+      }
+    }
+  }
   if (e != cudaSuccess) {
     pas_pyr_destroy(y);
     return pas::set_error(ctx, PAS_ECUDA, "pas_pyr_create: %s", cudaGetErrorString(e));
@@ -660,6 +744,108 @@ pas_status pas_pyr_set_noise(pas_pyr_t y, double photons, double ron, uint64_t s
 pas_status pas_pyr_measure(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes) {
   if (!y || !d_opd) return pas::set_global_error(PAS_EINVAL, "pas_pyr_measure: NULL argument");
   return pas::pyr_launch(y, d_opd, d_frame, d_slopes, y->ctx->stream, nullptr, true);
+}
+
+pas_status pas_pyr_get_tuning(pas_pyr_t y, pas_pyr_tuning* out) {
+  if (!y || !out) return pas::set_global_error(PAS_EINVAL, "pas_pyr_get_tuning: NULL argument");
+  out->rows_per_cta = y->rows;
+  out->row_chunks = y->n_schunks;
+  out->col_groups = y->G;
+  return PAS_OK;
+}
+
+pas_status pas_pyr_set_tuning(pas_pyr_t y, const pas_pyr_tuning* t) {
+  if (!y || !t) return pas::set_global_error(PAS_EINVAL, "pas_pyr_set_tuning: NULL argument");
+  const int r = t->rows_per_cta;
+  PAS_CHECK_ARG(y->ctx, (r == 1 || r == 2 || r == 4 || r == 8) && t->row_chunks >= 1 &&
+                t->row_chunks <= y->n_s && t->col_groups >= 1 && t->col_groups <= y->p.K,
+                "pas_pyr_set_tuning: rows_per_cta in {1,2,4,8}, 1 <= row_chunks <= distinct sin values, "
+                "1 <= col_groups <= K");
+  y->rows = r;
+  y->s_chunk = (y->n_s + t->row_chunks - 1) / t->row_chunks;
+  y->n_schunks = (y->n_s + y->s_chunk - 1) / y->s_chunk;
+  y->kper = (y->p.K + t->col_groups - 1) / t->col_groups;
+  y->G = (y->p.K + y->kper - 1) / y->kper;
+  return PAS_OK;
+}
+
+pas_status pas_pyr_autotune(pas_pyr_t y, const float* d_opd, int32_t iters, pas_pyr_tuning* out) {
+  if (!y || !d_opd) return pas::set_global_error(PAS_EINVAL, "pas_pyr_autotune: NULL argument");
+  PAS_CHECK_ARG(y->ctx, iters >= 1, "pas_pyr_autotune: iters >= 1");
+  cudaStream_t st = y->ctx->stream;
+  cudaEvent_t e0, e1;
+  PAS_CUDA_TRY(y->ctx, cudaStreamSynchronize(st));
+  PAS_CUDA_TRY(y->ctx, cudaEventCreate(&e0));
+  PAS_CUDA_TRY(y->ctx, cudaEventCreate(&e1));
+  // each candidate: `iters` launches captured in a graph, timed on the GPU
+  // (host launch latency does not enter the measurement)
+  cudaStream_t cs = y->ctx->capture_stream;
+  auto time_it = [&](auto&& launch) -> float {
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return 1e30f;
+    for (int i = 0; i < iters; ++i) launch(cs);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(cs, &g) != cudaSuccess || !g) return 1e30f;
+    cudaGraphExec_t ex = nullptr;
+    float ms = 1e30f;
+    if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+      cudaGraphLaunch(ex, st);
+      cudaEventRecord(e0, st);
+      cudaGraphLaunch(ex, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaGraphExecDestroy(ex);
+    }
+    cudaGraphDestroy(g);
+    return ms;
+  };
+  // rows pass
+  float best = 1e30f;
+  pas_pyr_tuning bt{y->rows, y->n_schunks, y->G};
+  const int rows_c[3] = {2, 4, 8};
+  for (int r : rows_c) {
+    int last_chunk = -1;
+    for (int nc = 1; nc <= y->n_s; ++nc) {
+      const int chunk = (y->n_s + nc - 1) / nc;
+      if (chunk == last_chunk) continue;
+      last_chunk = chunk;
+      y->rows = r;
+      y->s_chunk = chunk;
+      y->n_schunks = (y->n_s + chunk - 1) / chunk;
+      const float ms = time_it([&](cudaStream_t q) { pas::launch_rows(y, d_opd, q); });
+      if (ms < best) {
+        best = ms;
+        bt.rows_per_cta = r;
+        bt.row_chunks = y->n_schunks;
+      }
+    }
+  }
+  pas_pyr_tuning cur = bt;
+  cur.col_groups = y->G;
+  pas_pyr_set_tuning(y, &cur);
+  pas::launch_rows(y, d_opd, st);
+  // columns pass (with the frame/slopes tail, into the internal frame)
+  best = 1e30f;
+  int last_kper = -1;
+  for (int G = 1; G <= y->p.K; ++G) {
+    const int kper = (y->p.K + G - 1) / G;
+    if (kper == last_kper) continue;
+    last_kper = kper;
+    y->kper = kper;
+    y->G = (y->p.K + kper - 1) / kper;
+    const float ms = time_it([&](cudaStream_t q) { pas::launch_cols(y, nullptr, nullptr, q, nullptr, false); });
+    if (ms < best) {
+      best = ms;
+      bt.col_groups = y->G;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pas_status s = pas::check_launch(y->ctx, "pas_pyr_autotune launches");
+  if (s != PAS_OK) return s;
+  pas_pyr_set_tuning(y, &bt);
+  if (out) *out = bt;
+  return PAS_OK;
 }
 
 pas_status pas_ccd_noise(pas_ctx_t ctx, const float* d_in, float* d_out, int32_t n, double photons,

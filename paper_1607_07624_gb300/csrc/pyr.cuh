@@ -18,7 +18,7 @@ struct LoopExtra {
 
 // Launch rows pass, cols pass and frame/slopes on `st`. `extra` (may be null)
 // supplies the loop's frame counter and residual-WFE fields. `ev` (may be null):
-// four events recorded before the rows, cols, frame and slopes kernels.
+// two events recorded before the rows and the columns (+ frame, slopes) kernels.
 pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes,
                       cudaStream_t st, const LoopExtra* extra, bool increment_ctr,
                       cudaEvent_t* ev = nullptr);

@@ -3,7 +3,7 @@
 // fused into one kernel for the loop.
 //
 // The matrix-vector product reads every element of R once per step: it is bound
-// by memory bandwidth, so it runs on CUDA cores with 16-byte loads, one warp per
+// by memory bandwidth, so it runs on CUDA cores with 16-byte loads, four warps per
 // mode row, the slope vector staged in shared memory. PAS_BF16 stores R as
 // bfloat16 scaled per row (row max |R| = 1) with float32 accumulation.
 #include <cuda_bf16.h>
@@ -25,37 +25,54 @@ __device__ inline float dot4(float4 a, float4 b, float acc) {
   return fmaf(a.w, b.w, acc);
 }
 
+// CTA: 256 threads = RECON_ROWS rows x RECON_SPLIT warps per row; the warps of a
+// row take interleaved 16-byte chunks and meet in shared memory. With the
+// integrator active, the last CTA to finish advances the step counter.
+constexpr int RECON_SPLIT = 4;
+constexpr int RECON_ROWS = 8 / RECON_SPLIT;
+
 template <bool BF16>
 __global__ void __launch_bounds__(256) recon_kernel(ReconArgs a) {
   extern __shared__ float4 s4[];  // [n_s_pad / 4]
+  __shared__ float part[8];
+  __shared__ bool is_last;
   float* s_s = reinterpret_cast<float*>(s4);
   for (int t = threadIdx.x; t < a.n_s_pad; t += blockDim.x) s_s[t] = t < a.n_s ? a.s[t] : 0.f;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m = blockIdx.x * 8 + warp;
-  if (m >= a.n_m) return;
+  const int row_local = warp / RECON_SPLIT, part_idx = warp % RECON_SPLIT;
+  const int m = blockIdx.x * RECON_ROWS + row_local;
   float acc = 0.f;
-  if (BF16) {
-    const uint4* row = reinterpret_cast<const uint4*>(a.Rb + (size_t)m * a.n_s_pad);
-    const int nc = a.n_s_pad / 8;
+  if (m < a.n_m) {
+    const int c0 = part_idx * 32 + lane;
+    constexpr int STEP = RECON_SPLIT * 32;
+    if (BF16) {
+      const uint4* row = reinterpret_cast<const uint4*>(a.Rb + (size_t)m * a.n_s_pad);
+      const int nc = a.n_s_pad / 8;
 #pragma unroll 4
-    for (int c = lane; c < nc; c += 32) {
-      const uint4 u = __ldg(row + c);
-      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
-      const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
-      const float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
-      acc = dot4(make_float4(f0.x, f0.y, f1.x, f1.y), s4[2 * c], acc);
-      acc = dot4(make_float4(f2.x, f2.y, f3.x, f3.y), s4[2 * c + 1], acc);
+      for (int c = c0; c < nc; c += STEP) {
+        const uint4 u = __ldg(row + c);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+        const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
+        const float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
+        acc = dot4(make_float4(f0.x, f0.y, f1.x, f1.y), s4[2 * c], acc);
+        acc = dot4(make_float4(f2.x, f2.y, f3.x, f3.y), s4[2 * c + 1], acc);
+      }
+    } else {
+      const float4* row = reinterpret_cast<const float4*>(a.R + (size_t)m * a.n_s_pad);
+      const int nc = a.n_s_pad / 4;
+#pragma unroll 4
+      for (int c = c0; c < nc; c += STEP) acc = dot4(__ldg(row + c), s4[c], acc);
     }
-  } else {
-    const float4* row = reinterpret_cast<const float4*>(a.R + (size_t)m * a.n_s_pad);
-    const int nc = a.n_s_pad / 4;
-#pragma unroll 4
-    for (int c = lane; c < nc; c += 32) acc = dot4(__ldg(row + c), s4[c], acc);
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if (lane == 0) {
-    const float dm = BF16 ? acc * a.scale[m] : acc;
+  if (lane == 0) part[warp] = acc;
+  __syncthreads();
+  if (part_idx == 0 && lane == 0 && m < a.n_m) {
+    float tot = 0.f;
+#pragma unroll
+    for (int q = 0; q < RECON_SPLIT; ++q) tot += part[warp + q];
+    const float dm = BF16 ? tot * a.scale[m] : tot;
     if (a.dmodes) a.dmodes[m] = dm;
     if (a.ring) {
       const long long t = *a.step;
@@ -63,6 +80,18 @@ __global__ void __launch_bounds__(256) recon_kernel(ReconArgs a) {
       const float c = fmaf(a.gain ? a.gain[m] : 1.0f, dm, prev);
       a.ring[(size_t)(t % a.delay) * a.n_m + m] = c;
       if (a.cmd_last) a.cmd_last[m] = c;
+    }
+  }
+  if (a.step_inc) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      is_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (is_last && threadIdx.x == 0) {
+      *a.step_inc += 1;
+      *a.done = 0u;
     }
   }
 }
@@ -82,8 +111,9 @@ pas_status recon_launch(pas_recon_t r, ReconArgs a, cudaStream_t st) {
   a.n_m = r->n_modes;
   a.n_s = r->n_slopes;
   a.n_s_pad = r->n_s_pad;
+  a.done = r->d_done;
   const size_t smem = sizeof(float) * (size_t)r->n_s_pad;
-  const int grid = (r->n_modes + 7) / 8;
+  const int grid = (r->n_modes + RECON_ROWS - 1) / RECON_ROWS;
   if (r->prec == PAS_BF16) recon_kernel<true><<<grid, 256, smem, st>>>(a);
   else recon_kernel<false><<<grid, 256, smem, st>>>(a);
   return check_launch(r->ctx, "reconstructor launch");
@@ -98,6 +128,7 @@ void pas_recon_destroy(pas_recon_t r) {
   pas::dev_free(r->d_R);
   pas::dev_free(r->d_Rb);
   pas::dev_free(r->d_scale);
+  pas::dev_free(r->d_done);
   delete r;
 }
 
@@ -142,6 +173,8 @@ pas_status pas_recon_create(pas_ctx_t ctx, const float* h_R, int32_t n_modes, in
     if (st == PAS_OK && e == cudaSuccess)
       e = cudaFuncSetAttribute(pas::recon_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
+  if (st == PAS_OK) st = pas::dev_alloc(ctx, (void**)&r->d_done, sizeof(unsigned int));
+  if (st == PAS_OK && e == cudaSuccess) e = cudaMemset(r->d_done, 0, sizeof(unsigned int));
   if (st != PAS_OK) {
     pas_recon_destroy(r);
     return st;

@@ -19,6 +19,8 @@ struct ReconArgs {
   int delay = 1;
   const long long* step = nullptr;
   float* cmd_last = nullptr;            // [n_m] copy of the new command
+  long long* step_inc = nullptr;        // advanced by one after the last CTA (or null)
+  unsigned int* done = nullptr;         // CTA completion counter
 };
 
 }  // namespace pas
@@ -30,6 +32,7 @@ struct pas_recon_s {
   float* d_R = nullptr;
   __nv_bfloat16* d_Rb = nullptr;
   float* d_scale = nullptr;
+  unsigned int* d_done = nullptr;
 };
 
 namespace pas {

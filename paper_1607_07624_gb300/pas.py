@@ -43,6 +43,10 @@ class pas_pyr_params(C.Structure):
                 ("local_norm", C.c_int32)]
 
 
+class pas_pyr_tuning(C.Structure):
+    _fields_ = [("rows_per_cta", C.c_int32), ("row_chunks", C.c_int32), ("col_groups", C.c_int32)]
+
+
 class pas_loop_stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("wfe_nm", C.c_double)]
 
@@ -77,6 +81,9 @@ _SIGS = {
     "pas_pyr_measure": (C.c_int, [vp, vp, vp, vp]),
     "pas_ccd_noise": (C.c_int, [vp, vp, vp, i32, f64, i32, f64, C.c_uint64, i64]),
     "pas_pyr_destroy": (None, [vp]),
+    "pas_pyr_get_tuning": (C.c_int, [vp, P(pas_pyr_tuning)]),
+    "pas_pyr_set_tuning": (C.c_int, [vp, P(pas_pyr_tuning)]),
+    "pas_pyr_autotune": (C.c_int, [vp, vp, i32, P(pas_pyr_tuning)]),
     "pas_recon_create": (C.c_int, [vp, vp, i32, i32, C.c_int, P(vp)]),
     "pas_recon_apply": (C.c_int, [vp, vp, vp]),
     "pas_recon_destroy": (None, [vp]),
@@ -244,6 +251,23 @@ def pas_ccd_noise(ctx, d_in, d_out, photons, n_pupil_pixels, read_noise_e, seed,
 
 def pas_pyr_destroy(pyr):
     _lib.pas_pyr_destroy(pyr)
+
+
+def pas_pyr_get_tuning(pyr, ctx):
+    t = pas_pyr_tuning()
+    _check(_lib.pas_pyr_get_tuning(pyr, C.byref(t)), ctx)
+    return (t.rows_per_cta, t.row_chunks, t.col_groups)
+
+
+def pas_pyr_set_tuning(pyr, ctx, rows_per_cta, row_chunks, col_groups):
+    t = pas_pyr_tuning(rows_per_cta, row_chunks, col_groups)
+    _check(_lib.pas_pyr_set_tuning(pyr, C.byref(t)), ctx)
+
+
+def pas_pyr_autotune(pyr, ctx, d_opd, iters=5):
+    t = pas_pyr_tuning()
+    _check(_lib.pas_pyr_autotune(pyr, _ptr(d_opd), int(iters), C.byref(t)), ctx)
+    return (t.rows_per_cta, t.row_chunks, t.col_groups)
 
 
 def pas_recon_create(ctx, R: np.ndarray, precision=PAS_FP32):

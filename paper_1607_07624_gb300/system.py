@@ -34,7 +34,8 @@ class SCAOSystem:
     R: reconstruction matrix (None: calibrated by push-pull on the GPU)."""
 
     def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32,
-                 noise=None, delay=None, wfe_history=4096, stream=None, build_loop=True):
+                 noise=None, delay=None, wfe_history=4096, stream=None, build_loop=True,
+                 autotune=True):
         from synth.inputs import layer_seeds, screen_white_noise
         self.cfg = cfg
         self.dev = torch.device("cuda")
@@ -76,6 +77,12 @@ class SCAOSystem:
         self.R = np.ascontiguousarray(R, dtype=np.float32)
         self.rec = P.pas_recon_create(self.ctx, self.R, recon_precision)
         self.d_gain = torch.full((self.n_modes,), cfg.gain, **f32)
+        # launch geometry of the pyramid kernels, measured on the open-loop OPD
+        self.tuning = P.pas_pyr_get_tuning(self.pyr, self.ctx)
+        if autotune:
+            P.pas_atmo_advance(self.atmo, self.ctx, 0, self.d_opd)
+            self.tuning = P.pas_pyr_autotune(self.pyr, self.ctx, self.d_opd, 5)
+            self.d_opd.zero_()
         if noise is None and cfg.magnitude is not None:
             noise = (cfg.photons_per_frame(), cfg.read_noise_e, cfg.seed)
         if noise is not None:

@@ -149,3 +149,31 @@ def test_bad_arguments_are_rejected(env):
         pas.pas_pyr_create(ctx, 64, 128, 12, 16, 3.0, 750.0, 0.1, valid=np.array([5, 3], np.int32))
     with pytest.raises(pas.PasError):
         pas.pas_pyr_create(ctx, 36, 72, 4, 4, 3.0, 750.0, 0.1)  # 72 = 8*9 unsupported
+
+
+def test_autotune_and_tunings_give_the_same_frame(env):
+    """Every launch geometry computes the same frame (up to the float32 order of
+    the modulation-group sums); the autotuner returns a valid one."""
+    torch, pas, ctx = env
+    cfg = get_config(1)
+    opd = torch.as_tensor(random_opd_nm(cfg.Np, 300.0, seed=9).astype(np.float32)).cuda()
+    pyr = pas.pas_pyr_create(ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius, cfg.wavelength_nm, cfg.obs)
+    try:
+        nv = pas.pas_pyr_n_valid(pyr)
+        frames = []
+        for t in [(1, 1, 1), (2, 3, 4), (8, 7, 12), (4, 2, 5)]:
+            pas.pas_pyr_set_tuning(pyr, ctx, *t)
+            fr = torch.zeros(cfg.n_det, cfg.n_det, device="cuda")
+            sl = torch.zeros(2 * nv, device="cuda")
+            pas.pas_pyr_measure(pyr, ctx, opd, fr, sl)
+            torch.cuda.synchronize()
+            frames.append(fr.cpu().numpy())
+        for f in frames[1:]:
+            assert np.max(np.abs(f - frames[0])) <= 1e-6 * np.max(frames[0])
+        best = pas.pas_pyr_autotune(pyr, ctx, opd, 2)
+        assert best[0] in (2, 4, 8) and 1 <= best[1] and 1 <= best[2] <= cfg.K
+        assert pas.pas_pyr_get_tuning(pyr, ctx) == best
+        with pytest.raises(pas.PasError):
+            pas.pas_pyr_set_tuning(pyr, ctx, 3, 1, 1)
+    finally:
+        pas.pas_pyr_destroy(pyr)
