@@ -24,6 +24,8 @@ pas_status set_global_error(pas_status st, const char* fmt, ...);
 // cudaMalloc with the test fault-injection hook; on failure records PAS_ENOMEM.
 pas_status dev_alloc(pas_ctx_t ctx, void** p, size_t bytes);
 void dev_free(void* p);
+// Raise (never lower) a kernel's dynamic shared-memory limit.
+cudaError_t raise_dyn_smem(const void* func, size_t bytes);
 // Check the last launch; records PAS_ECUDA with `what`.
 pas_status check_launch(pas_ctx_t ctx, const char* what);
 

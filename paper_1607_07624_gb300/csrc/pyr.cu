@@ -394,6 +394,16 @@ struct pas_pyr_s {
 
 namespace pas {
 
+// The dynamic shared-memory limit is a property of the kernel function, shared by
+// every object using it: only ever raise it.
+cudaError_t raise_dyn_smem(const void* func, size_t bytes) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 size_t rows_smem(pas_pyr_t y, int rows, int s_chunk) {
   return sizeof(float2) * ((size_t)y->kern.tw_n + y->kern.buf_n + (size_t)s_chunk * y->p.Np +
                            (size_t)rows * (y->p.Np + y->kern.pitch));
@@ -677,10 +687,8 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   if (e == cudaSuccess) e = cudaMemset(y->d_sn, 0, sizeof(float) * 2 * y->n_valid);
   if (e == cudaSuccess) e = cudaMemset(y->d_frame_ctr, 0, sizeof(long long));
   if (e == cudaSuccess) e = cudaMemset(y->d_done_col, 0, sizeof(unsigned int) * y->nd);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kern.rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)y->smem_rows);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kern.cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)y->smem_cols);
+  if (e == cudaSuccess) e = pas::raise_dyn_smem((const void*)kern.rows, y->smem_rows);
+  if (e == cudaSuccess) e = pas::raise_dyn_smem((const void*)kern.cols, y->smem_cols);
   // modulation grouping: the columns pass runs nd x G CTAs of b warps, each warp
   // doing kper = ceil(K / G) transforms; pick G minimising waves x kper
   int occ = 1;
@@ -860,3 +868,4 @@ pas_status pas_ccd_noise(pas_ctx_t ctx, const float* d_in, float* d_out, int32_t
 }
 
 }  // extern "C"
+

@@ -154,7 +154,7 @@ pas_status pas_recon_create(pas_ctx_t ctx, const float* h_R, int32_t n_modes, in
     st = pas::dev_alloc(ctx, (void**)&r->d_R, sizeof(float) * R.size());
     if (st == PAS_OK) e = cudaMemcpy(r->d_R, R.data(), sizeof(float) * R.size(), cudaMemcpyHostToDevice);
     if (st == PAS_OK && e == cudaSuccess)
-      e = cudaFuncSetAttribute(pas::recon_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = pas::raise_dyn_smem((const void*)pas::recon_kernel<false>, smem);
   } else {
     std::vector<uint16_t> Rb((size_t)n_modes * r->n_s_pad, 0);
     std::vector<float> scale(n_modes, 1.f);
@@ -171,7 +171,7 @@ pas_status pas_recon_create(pas_ctx_t ctx, const float* h_R, int32_t n_modes, in
     if (st == PAS_OK && e == cudaSuccess)
       e = cudaMemcpy(r->d_scale, scale.data(), sizeof(float) * n_modes, cudaMemcpyHostToDevice);
     if (st == PAS_OK && e == cudaSuccess)
-      e = cudaFuncSetAttribute(pas::recon_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = pas::raise_dyn_smem((const void*)pas::recon_kernel<true>, smem);
   }
   if (st == PAS_OK) st = pas::dev_alloc(ctx, (void**)&r->d_done, sizeof(unsigned int));
   if (st == PAS_OK && e == cudaSuccess) e = cudaMemset(r->d_done, 0, sizeof(unsigned int));
