@@ -170,6 +170,30 @@ pas_status pas_pyr_set_noise(pas_pyr_t pyr, double photons_per_frame, double rea
  * ignored). d_frame: device float32 [2n_sub][2n_sub] out (may be NULL).
  * d_slopes: device float32 [2*n_valid] out (may be NULL). */
 pas_status pas_pyr_measure(pas_pyr_t pyr, const float* d_opd, float* d_frame, float* d_slopes);
+/* Allocation-free pyramid measurement (the paper has no counterpart).
+ * For callers that may not allocate device memory once they run (an application
+ * whose allocator forbids cudaMalloc after start-up, code running while another
+ * library owns the device allocator, a moment when an allocation would stall the
+ * device): it computes what pas_pyr_create + pas_pyr_measure compute (noiseless,
+ * default launch geometry) without creating an object and without allocating.
+ * Its intermediates live in one array of PAS_STATIC_SCRATCH_BYTES of device memory
+ * compiled into this library, held by every GPU that loads it until the process
+ * exits. Geometries that need more (e.g. N = 960 with 32 modulation points) are
+ * rejected with PAS_EINVAL and a message giving the bytes needed; also N <= 960,
+ * K <= 256, n_sub <= 128.
+ *   p: as for pas_pyr_create; h_valid (host, ascending) / n_valid or NULL for the
+ *   geometric rule; d_sn: device [2 n_valid] slope reference or NULL;
+ *   d_opd: device [Np][Np] input; d_frame: device [2n_sub]^2 output (required);
+ *   d_slopes: device [2 n_valid] output or NULL; cuda_stream: cudaStream_t or NULL.
+ * The first call on a device (with that device current) looks up the array's
+ * device address once; make that first call before any stream capture. Every call
+ * uses the same array and leaves its contents behind: the call clears what has to
+ * start at zero itself, and calls whose work overlaps on the GPU (other streams,
+ * other threads) race on it. Table set-up copies from host memory on the stream. */
+#define PAS_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+pas_status pas_pyr_measure_static(const pas_pyr_params* p, const int32_t* h_valid, int32_t n_valid,
+                                  const float* d_sn, const float* d_opd, float* d_frame,
+                                  float* d_slopes, void* cuda_stream);
 /* Stand-alone detector noise on a frame (same rule as above; frame counter
  * given explicitly; in-place allowed). n = number of pixels. */
 pas_status pas_ccd_noise(pas_ctx_t ctx, const float* d_in, float* d_out, int32_t n,

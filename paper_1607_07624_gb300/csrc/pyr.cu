@@ -18,6 +18,7 @@
 #include <cmath>
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "fft.cuh"
@@ -869,3 +870,225 @@ pas_status pas_ccd_noise(pas_ctx_t ctx, const float* d_in, float* d_out, int32_t
 
 }  // extern "C"
 
+// ------------------------------------------------------------------------------
+// Allocation-free pyramid measurement.
+//
+// For callers that cannot allocate device memory while they run: a simulation
+// embedded in a host application whose allocator forbids cudaMalloc after start-up,
+// code running while another library owns the device allocator, or a context where
+// a cudaMalloc would synchronise the device at the wrong moment. Everything the
+// measurement needs besides the caller's input and outputs lives in one fixed array
+// of device memory compiled into this library; every GPU that loads the library
+// holds it until the process exits.
+namespace pas {
+
+constexpr int STATIC_MAX_K = 256;      // modulation points
+constexpr int STATIC_MAX_N = 960;      // FFT grid side
+constexpr int STATIC_MAX_NSUB = 128;   // sub-apertures across
+constexpr int STATIC_TABLE = 1024;     // twiddle / mask entries
+constexpr size_t STATIC_SCRATCH_BYTES = (size_t)PAS_STATIC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_pyr_scratch[STATIC_SCRATCH_BYTES];
+
+constexpr int STATIC_MAX_DEVICES = 64;
+static std::mutex g_static_mutex;
+static unsigned char* g_static_ptr[STATIC_MAX_DEVICES] = {};
+static int g_static_sms[STATIC_MAX_DEVICES] = {};
+
+// Device address of the scratch array for the current device (set-up once per
+// device, with that device current).
+static pas_status static_scratch(unsigned char** out, int* sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_global_error(PAS_ECUDA, "pas_pyr_measure_static: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= STATIC_MAX_DEVICES)
+    return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_pyr_scratch);
+    if (e != cudaSuccess || !p)
+      return set_global_error(PAS_ECUDA, "pas_pyr_measure_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return set_global_error(PAS_ECUDA, "pas_pyr_measure_static: %s", cudaGetErrorString(e));
+    g_static_ptr[dev] = static_cast<unsigned char*>(p);
+    g_static_sms[dev] = n;
+  }
+  *out = g_static_ptr[dev];
+  *sms = g_static_sms[dev];
+  return PAS_OK;
+}
+
+}  // namespace pas
+
+extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int32_t* h_valid, int32_t n_valid,
+                                             const float* d_sn, const float* d_opd, float* d_frame,
+                                             float* d_slopes, void* cuda_stream) {
+  using namespace pas;
+  if (!pp || !d_opd || !d_frame)
+    return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: NULL parameters, input or frame");
+  const pas_pyr_params p = *pp;
+  if (!(p.Np > 0 && p.N == 2 * p.Np && p.n_sub > 0 && p.N % (2 * p.n_sub) == 0 && p.K >= 1 &&
+        p.K <= STATIC_MAX_K && p.wavelength_nm > 0 && p.mod_radius >= 0 && p.obs >= 0 && p.obs < 1))
+    return set_global_error(PAS_EINVAL,
+                            "pas_pyr_measure_static: need N = 2 Np, N a multiple of 2 n_sub, 1 <= K <= %d", STATIC_MAX_K);
+  PyrKernels kern;
+  if (!lookup_kernels(p.N, &kern) || p.N > STATIC_MAX_N)
+    return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: FFT size N=%d not supported here (max %d)",
+                            p.N, STATIC_MAX_N);
+  const int b = p.N / (2 * p.n_sub), nd = 2 * p.n_sub;
+  if (b > 16 || p.n_sub > STATIC_MAX_NSUB)
+    return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: at most 16 fine pixels per detector pixel "
+                            "and %d sub-apertures across", STATIC_MAX_NSUB);
+  // valid sub-apertures (host, on the stack)
+  int32_t valid[STATIC_MAX_NSUB * STATIC_MAX_NSUB];
+  int32_t nv = 0;
+  if (h_valid) {
+    if (n_valid <= 0 || n_valid > p.n_sub * p.n_sub)
+      return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: bad n_valid");
+    for (int j = 0; j < n_valid; ++j) {
+      if (h_valid[j] < 0 || h_valid[j] >= p.n_sub * p.n_sub || (j > 0 && h_valid[j] <= h_valid[j - 1]))
+        return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: valid indices must be ascending in [0, n_sub^2)");
+      valid[j] = h_valid[j];
+    }
+    nv = n_valid;
+  } else {
+    if (p.Np % p.n_sub != 0)
+      return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: geometric rule needs Np multiple of n_sub");
+    pas_status s = pas_valid_subaps(p.Np, p.obs, p.n_sub, valid, STATIC_MAX_NSUB * STATIC_MAX_NSUB, &nv);
+    if (s != PAS_OK) return s;
+  }
+  if (d_slopes && nv <= 0) return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: no valid sub-aperture");
+
+  // distinct sin(theta) rows passes, tilts, twiddles and mask (host, on the stack)
+  int kmap[STATIC_MAX_K], rep_of_s[STATIC_MAX_K];
+  int n_s = 0;
+  for (int k = 0; k < p.K; ++k) {
+    int rep = k;
+    if (p.K % 2 == 0) rep = std::min(k, ((p.K / 2 - k) % p.K + p.K) % p.K);
+    int s = -1;
+    for (int t = 0; t < n_s; ++t)
+      if (rep_of_s[t] == rep) s = t;
+    if (s < 0) {
+      s = n_s;
+      rep_of_s[n_s++] = rep;
+    }
+    kmap[k] = s;
+  }
+  float alpha[STATIC_MAX_K], beta[STATIC_MAX_K];
+  const double ramp = 1.0 / (2.0 * p.N);
+  for (int k = 0; k < p.K; ++k)
+    alpha[k] = (float)(p.mod_radius * std::cos(2.0 * M_PI * (double)k / (double)p.K) / p.Np - ramp);
+  for (int s = 0; s < n_s; ++s)
+    beta[s] = (float)(p.mod_radius * std::sin(2.0 * M_PI * (double)rep_of_s[s] / (double)p.K) / p.Np - ramp);
+  float2 tw[STATIC_TABLE], mk[STATIC_TABLE];
+  if (kern.tw_n > STATIC_TABLE || kern.buf_n > STATIC_TABLE)
+    return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: table size");
+  {
+    const int M = plan_count(p.N);
+    for (int pass = 0; pass + 1 < M; ++pass) {
+      const int R = plan_radix(p.N, pass), L = block_len(p.N, pass), S = L / R, off = tw_offset(p.N, pass);
+      for (int k = 1; k < R; ++k)
+        for (int n1 = 0; n1 < S; ++n1) {
+          const double a = -2.0 * M_PI * (double)(n1 * k) / (double)L;
+          tw[off + (k - 1) * S + n1] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    }
+    for (int j = 0; j < kern.buf_n; ++j) mk[j] = make_float2(0.f, 0.f);
+    for (int j = 0; j < p.N; ++j) {
+      const double ut = std::fabs((double)digit_reversed_freq(p.N, j) - 0.5 * (p.N - 1));
+      mk[phys(j)] = make_float2((float)(std::cos(0.5 * M_PI * ut) / p.N), (float)(std::sin(0.5 * M_PI * ut) / p.N));
+    }
+  }
+  unsigned char vpix[(2 * STATIC_MAX_NSUB) * (2 * STATIC_MAX_NSUB)];
+  for (int t = 0; t < nd * nd; ++t) vpix[t] = 0;
+  for (int j = 0; j < nv; ++j) {
+    const int r = valid[j] / p.n_sub, c = valid[j] % p.n_sub, ns = p.n_sub;
+    vpix[r * nd + c] = vpix[r * nd + ns + c] = vpix[(ns + r) * nd + c] = vpix[(ns + r) * nd + ns + c] = 1;
+  }
+
+  // carve the scratch array
+  unsigned char* base = nullptr;
+  int sms = 0;
+  pas_status st0 = static_scratch(&base, &sms);
+  if (st0 != PAS_OK) return st0;
+  size_t off = 0;
+  auto carve = [&](size_t bytes) -> unsigned char* {
+    unsigned char* q = base + off;
+    off += (bytes + 255) / 256 * 256;
+    return q;
+  };
+  pas_pyr_s y;
+  y.p = p;
+  y.kern = kern;
+  y.b = b;
+  y.nd = nd;
+  y.n_s = n_s;
+  y.n_valid = nv;
+  y.T_obs = obstruction_threshold(p.Np, p.obs);
+  const double inv = 1.0 / p.wavelength_nm;
+  y.inv_hi = (float)inv;
+  y.inv_lo = (float)(inv - (double)y.inv_hi);
+  y.rows = 4;
+  y.n_schunks = (n_s + 3) / 4;
+  y.s_chunk = (n_s + y.n_schunks - 1) / y.n_schunks;
+  y.smem_cols = sizeof(float2) * ((size_t)kern.tw_n + kern.buf_n + (size_t)p.Np + (size_t)b * kern.pitch);
+  {
+    const int slots = 2 * std::max(1, sms);
+    int best_G = 1;
+    double best = 1e30;
+    for (int G = 1; G <= p.K; ++G) {
+      const int kper = (p.K + G - 1) / G, Gc = (p.K + kper - 1) / kper;
+      const double cost = (double)((nd * Gc + slots - 1) / slots) * kper + 1e-3 * Gc;
+      if (cost < best) {
+        best = cost;
+        best_G = Gc;
+      }
+    }
+    y.kper = (p.K + best_G - 1) / best_G;
+    y.G = (p.K + y.kper - 1) / y.kper;
+  }
+  y.d_H = reinterpret_cast<float2*>(carve(sizeof(float2) * (size_t)n_s * p.N * p.Np));
+  y.d_part = reinterpret_cast<float*>(carve(sizeof(float) * (size_t)y.G * nd * nd));
+  y.d_tw = reinterpret_cast<float2*>(carve(sizeof(float2) * kern.tw_n));
+  y.d_mask = reinterpret_cast<float2*>(carve(sizeof(float2) * kern.buf_n));
+  y.d_alpha = reinterpret_cast<float*>(carve(sizeof(float) * p.K));
+  y.d_beta = reinterpret_cast<float*>(carve(sizeof(float) * n_s));
+  y.d_kmap = reinterpret_cast<int*>(carve(sizeof(int) * p.K));
+  y.d_valid = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * std::max(nv, 1)));
+  y.d_vpix = carve((size_t)nd * nd);
+  y.d_flux_part = reinterpret_cast<double*>(carve(sizeof(double) * nd));
+  y.d_done_col = reinterpret_cast<unsigned int*>(carve(sizeof(unsigned int) * nd));
+  y.d_frame_ctr = reinterpret_cast<long long*>(carve(sizeof(long long)));
+  y.d_frame = d_frame;
+  if (off > STATIC_SCRATCH_BYTES)
+    return set_global_error(PAS_EINVAL,
+                            "pas_pyr_measure_static: this geometry needs %zu bytes of scratch, the library holds %zu "
+                            "(use pas_pyr_create / pas_pyr_measure)", off, STATIC_SCRATCH_BYTES);
+  y.has_sn = d_sn != nullptr;
+  y.d_sn = const_cast<float*>(d_sn);
+  const size_t smem_rows = rows_smem(&y, y.rows, y.s_chunk);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaError_t e = raise_dyn_smem((const void*)kern.rows, smem_rows);
+  if (e == cudaSuccess) e = raise_dyn_smem((const void*)kern.cols, y.smem_cols);
+  // tables in, counters (and the unused noise frame counter) cleared
+  auto H2D = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  H2D(y.d_tw, tw, sizeof(float2) * kern.tw_n);
+  H2D(y.d_mask, mk, sizeof(float2) * kern.buf_n);
+  H2D(y.d_alpha, alpha, sizeof(float) * p.K);
+  H2D(y.d_beta, beta, sizeof(float) * n_s);
+  H2D(y.d_kmap, kmap, sizeof(int) * p.K);
+  H2D(y.d_valid, valid, sizeof(int32_t) * std::max(nv, 1));
+  H2D(y.d_vpix, vpix, (size_t)nd * nd);
+  if (e == cudaSuccess) e = cudaMemsetAsync(y.d_done_col, 0, sizeof(unsigned int) * nd, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(y.d_frame_ctr, 0, sizeof(long long), st);
+  if (e != cudaSuccess) return set_global_error(PAS_ECUDA, "pas_pyr_measure_static: %s", cudaGetErrorString(e));
+  launch_rows(&y, d_opd, st);
+  launch_cols(&y, d_frame, d_slopes, st, nullptr, false);
+  if (d_slopes) launch_slopes(&y, d_frame, d_slopes, st, nullptr, false);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_global_error(PAS_ECUDA, "pas_pyr_measure_static launch: %s", cudaGetErrorString(e));
+  return PAS_OK;
+}

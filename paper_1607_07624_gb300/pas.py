@@ -80,6 +80,7 @@ _SIGS = {
     "pas_pyr_set_noise": (C.c_int, [vp, f64, f64, C.c_uint64, i64]),
     "pas_pyr_measure": (C.c_int, [vp, vp, vp, vp]),
     "pas_ccd_noise": (C.c_int, [vp, vp, vp, i32, f64, i32, f64, C.c_uint64, i64]),
+    "pas_pyr_measure_static": (C.c_int, [P(pas_pyr_params), vp, i32, vp, vp, vp, vp, vp]),
     "pas_pyr_destroy": (None, [vp]),
     "pas_pyr_get_tuning": (C.c_int, [vp, P(pas_pyr_tuning)]),
     "pas_pyr_set_tuning": (C.c_int, [vp, P(pas_pyr_tuning)]),
@@ -242,6 +243,19 @@ def pas_pyr_set_noise(pyr, ctx, photons, read_noise_e, seed, frame_index=0):
 
 def pas_pyr_measure(pyr, ctx, d_opd, d_frame=None, d_slopes=None):
     _check(_lib.pas_pyr_measure(pyr, _ptr(d_opd), _ptr(d_frame), _ptr(d_slopes)), ctx)
+
+
+def pas_pyr_measure_static(Np, N, K, n_sub, mod_radius, wavelength_nm, obs, d_opd, d_frame, d_slopes=None,
+                           valid=None, d_sn=None, stream=None, local_norm=0):
+    """Allocation-free pyramid measurement (no object, no device allocation)."""
+    p = pas_pyr_params(Np, N, K, n_sub, mod_radius, wavelength_nm, obs, local_norm)
+    if valid is not None:
+        valid = np.ascontiguousarray(valid, dtype=np.int32)
+        vptr, nv = valid.ctypes.data, valid.size
+    else:
+        vptr, nv = None, 0
+    _check(_lib.pas_pyr_measure_static(C.byref(p), vptr, nv, _ptr(d_sn), _ptr(d_opd), _ptr(d_frame),
+                                       _ptr(d_slopes), _stream_handle(stream)))
 
 
 def pas_ccd_noise(ctx, d_in, d_out, photons, n_pupil_pixels, read_noise_e, seed, frame_index):
