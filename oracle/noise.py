@@ -14,13 +14,16 @@ how noise is drawn. Readings:
     quotients and sums (numpy float32 scalars here): uniform
     u = ((x >> 8) + 1/2) 2^-24 (exact in float32);
   * read noise: Box-Muller on block 0 words 0, 1: sqrt(-2 ln u0) cos(2 pi u1);
-  * photon noise, lambda < 64: inversion by sequential search on block 0 word 2,
-    p0 = exp(-lambda) evaluated in float64 and rounded to float32, then
-    p_k = p_{k-1} * (lambda * rn(1/k)), F_k = F_{k-1} + p_k in float32 (rn(1/k):
-    the correctly rounded float32 reciprocal), the count being the first k with
-    u <= F_k (at most 256 terms);
-    lambda >= 64: the PTRS transformed rejection of Hoermann (1993) in float32 on
-    the pairs (word 2, word 3) of blocks 0, 1, 2, ...
+  * photon noise, lambda < 10: inversion by sequential search on block 0 word 2,
+    p0 = exp(-lambda) in float32, then p_k = p_{k-1} * (lambda * rn(1/k)),
+    F_k = F_{k-1} + p_k in float32 (rn(1/k): the correctly rounded float32
+    reciprocal), the count being the first k with u <= F_k (at most 256 terms);
+    lambda >= 10: the PTRS transformed rejection of Hoermann (1993), valid from
+    lambda = 10, in float32 (log-gamma in float32) on the pairs (word 2, word 3) of
+    blocks 0, 1, 2, ...
+    exp, log and log-gamma are float32 library functions on both sides; their
+    implementations may differ by an ulp, which can flip a decision only for draws
+    within that distance of a boundary.
 """
 from __future__ import annotations
 
@@ -68,9 +71,9 @@ def poisson(lam, seed: int, pixel: int, frame: int) -> int:
     if not lam > 0:
         return 0
     w = _block(seed, pixel, frame, 0)
-    if lam < F32(64.0):
+    if lam < F32(10.0):
         u = u01(w[2])
-        p = F32(math.exp(-float(lam)))
+        p = np.exp(-lam)
         F = p
         k = 0
         while u > F and k < 256:
@@ -98,7 +101,7 @@ def poisson(lam, seed: int, pixel: int, frame: int) -> int:
         if k < 0 or (us < F32(0.013) and V > us):
             continue
         lhs = np.log(V) + np.log(invalpha) - np.log(a / (us * us) + b)
-        rhs = -lam + k * loglam - F32(math.lgamma(float(k) + 1.0))
+        rhs = -lam + k * loglam - F32(math.lgamma(float(F32(k) + F32(1.0))))
         if F32(lhs) <= F32(rhs):
             return int(k)
     return int(np.floor(lam + F32(0.5)))

@@ -9,6 +9,7 @@
 
 #include "atmo_dm.cuh"
 #include "internal.h"
+#include "pdl.cuh"
 
 namespace pas {
 
@@ -94,6 +95,8 @@ __global__ void __launch_bounds__(256) atmo_pupil_kernel(AtmoArgs a, const int* 
                                                          const long long* d_step, float* out) {
   __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
   __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
+  pdl_trigger();
+  pdl_wait();
   const long long step = *d_step;
   if (threadIdx.x < a.L) {
     layer_shift(a.vx[threadIdx.x], step, a.S, &six[threadIdx.x], &sfx[threadIdx.x]);
@@ -178,6 +181,15 @@ __global__ void __launch_bounds__(RES_WARPS * 32) residual_kernel(ResArgs a) {
   __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
   __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
   __shared__ double wred[2][RES_WARPS];
+  pdl_trigger();
+  // the basis is constant: stream this tile's block towards L2 while the
+  // predecessor (atmosphere) still runs
+  if (a.MT && a.n_m > 0) {
+    const char* blk = reinterpret_cast<const char*>(a.MT + (size_t)blockIdx.x * a.n_m * RES_TILE);
+    const int lines = a.n_m * RES_TILE * 4 / 128;
+    for (int t = threadIdx.x; t < lines; t += blockDim.x) prefetch_l2(blk + (size_t)t * 128);
+  }
+  pdl_wait();
   const long long step = a.d_step ? *a.d_step : a.h_step;
   const float* cmd = a.cmd;
   if (a.cmd_ring) cmd = a.cmd_ring + (size_t)(step % a.delay) * a.n_m;
@@ -294,11 +306,16 @@ pas_status atmo_pupil_launch(pas_ctx_t ctx, const AtmoArgs& a, const int* pix, i
   return check_launch(ctx, "atmosphere kernel launch");
 }
 
-pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st) {
+pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, bool pdl) {
   const int tiles = residual_tiles(a.n_pix);
   if (tiles == 0) return PAS_OK;
   const size_t smem = sizeof(float) * (size_t)std::max(a.n_m, 1);
   const dim3 g(tiles), blk(RES_WARPS * 32);
+  if (a.atmo.L == 0) {
+    cudaError_t e = launch_k(residual_kernel<0>, g, blk, smem, st, pdl, a);
+    if (e != cudaSuccess) return set_error(ctx, PAS_ECUDA, "residual kernel launch: %s", cudaGetErrorString(e));
+    return PAS_OK;
+  }
   switch (a.atmo.L) {
     case 0: residual_kernel<0><<<g, blk, smem, st>>>(a); break;
     case 1: residual_kernel<1><<<g, blk, smem, st>>>(a); break;

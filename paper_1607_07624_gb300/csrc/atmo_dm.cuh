@@ -27,7 +27,8 @@ struct ResArgs {
   double2* wfe_part = nullptr;     // per-CTA (sum r, sum r^2) or null
 };
 
-pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st);
+// pdl: launch as a programmatic dependent of the preceding kernel in `st`.
+pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, bool pdl = false);
 // Number of CTAs (and of residual-WFE partials) of residual_launch for n_pix pixels.
 int residual_tiles(int n_pix);
 // Summed atmosphere at the device step on the listed pupil pixels of out [Np][Np].

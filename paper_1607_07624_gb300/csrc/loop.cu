@@ -53,8 +53,12 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   ra.dm_sign = 1.0f;
   ra.out = L->d_opd;
   ra.wfe_part = L->d_wfe_part;
+  // inside the step the kernels follow each other programmatically (prologues and
+  // constant-matrix prefetches overlap the predecessor), except when events are
+  // recorded between them for profiling
+  const bool pdl = ev == nullptr;
   if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
-  s = pas::residual_launch(L->ctx, ra, st);
+  s = pas::residual_launch(L->ctx, ra, st, pdl);
   if (s != PAS_OK) return s;
   pas::LoopExtra fa;
   fa.frame_ctr = L->d_step;
@@ -64,7 +68,7 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   fa.wfe_hist = L->d_wfe;
   fa.wfe_hist_len = L->hist;
   fa.step = L->d_step;
-  s = pas::pyr_launch(L->pyr, L->d_opd, L->d_frame, L->d_slopes, st, &fa, false, ev ? ev + 2 : nullptr);
+  s = pas::pyr_launch(L->pyr, L->d_opd, L->d_frame, L->d_slopes, st, &fa, false, ev ? ev + 2 : nullptr, pdl);
   if (s != PAS_OK) return s;
   pas::ReconArgs rc;
   rc.s = L->d_slopes;
@@ -76,7 +80,7 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   rc.cmd_last = L->d_cmd;
   rc.step_inc = L->d_step;
   if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
-  s = pas::recon_launch(L->rec, rc, st);
+  s = pas::recon_launch(L->rec, rc, st, pdl);
   if (ev) cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
   return s;
 }

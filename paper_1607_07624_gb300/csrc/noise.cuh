@@ -4,11 +4,12 @@
 // All decisions in float32 with IEEE products, quotients and sums (no contraction):
 //   uniform u = ((x >> 8) + 1/2) 2^-24 (exact);
 //   read noise: Box-Muller on block 0 words 0, 1;
-//   photons, lambda < 64: sequential-search inversion on block 0 word 2, starting
-//     from exp(-lambda) evaluated in double and rounded to float, each term
-//     p_k = p_{k-1} (lambda rn(1/k)) with the correctly rounded reciprocal;
-//   photons, lambda >= 64: Hoermann's (1993) PTRS transformed rejection on the pairs
-//     (word 2, word 3) of blocks 0, 1, 2, ...
+//   photons, lambda < 10: sequential-search inversion on block 0 word 2, starting
+//     from expf(-lambda), each term p_k = p_{k-1} (lambda rn(1/k)) with the
+//     correctly rounded reciprocal;
+//   photons, lambda >= 10: Hoermann's (1993) PTRS transformed rejection (valid from
+//     lambda = 10, O(1) expected draws) on the pairs (word 2, word 3) of blocks
+//     0, 1, 2, ..., with lgammaf.
 #pragma once
 #include <cstdint>
 
@@ -44,9 +45,9 @@ __device__ inline u32x4 noise_block(uint64_t seed, uint32_t pixel, uint64_t fram
 __device__ inline float poisson_draw(float lam, uint64_t seed, uint32_t pixel, uint64_t frame) {
   if (!(lam > 0.f)) return 0.f;
   u32x4 w = noise_block(seed, pixel, frame, 0);
-  if (lam < 64.f) {
+  if (lam < 10.f) {
     const float u = u01f(w.v[2]);
-    float p = (float)exp(-(double)lam);
+    float p = expf(-lam);
     float F = p;
     int k = 0;
     while (u > F && k < 256) {
@@ -71,7 +72,7 @@ __device__ inline float poisson_draw(float lam, uint64_t seed, uint32_t pixel, u
     if (k < 0.f || (us < 0.013f && V > us)) continue;
     const float lhs = __fsub_rn(__fadd_rn(logf(V), logf(invalpha)),
                                 logf(__fadd_rn(__fdiv_rn(a, __fmul_rn(us, us)), b)));
-    const float rhs = __fsub_rn(__fadd_rn(-lam, __fmul_rn(k, loglam)), (float)lgamma((double)k + 1.0));
+    const float rhs = __fsub_rn(__fadd_rn(-lam, __fmul_rn(k, loglam)), lgammaf(__fadd_rn(k, 1.0f)));
     if (lhs <= rhs) return k;
   }
   return floorf(lam + 0.5f);

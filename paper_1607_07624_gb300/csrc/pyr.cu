@@ -24,6 +24,7 @@
 #include "fft.cuh"
 #include "internal.h"
 #include "noise.cuh"
+#include "pdl.cuh"
 #include "pyr.cuh"
 
 namespace pas {
@@ -87,6 +88,7 @@ pyr_rows_kernel(RowArgs a) {
   const int Np = a.Np, off = a.off;
   const int i0 = blockIdx.x * rows;
   const int s0 = (blockIdx.y * a.n_s) / gridDim.y, s1 = ((blockIdx.y + 1) * a.n_s) / gridDim.y;
+  pdl_trigger();
   for (int t = threadIdx.x; t < TWN; t += blockDim.x) tw_s[t] = a.tw[t];
   for (int t = threadIdx.x; t < BL; t += blockDim.x) mk_s[t] = a.mask[t];
   // tilt along the row (with the input centring ramp and (-1)^j) per sin value
@@ -102,6 +104,7 @@ pyr_rows_kernel(RowArgs a) {
   float2* buf = bufs + warp * PITCH;
   // pupil phasor A exp(2 pi i opd / lambda) of this warp's row, kept for all s
   float2* phrow = phs + warp * Np;
+  pdl_wait();  // the OPD comes from the predecessor
   {
     const int ai = 2 * i - Np + 1;
     const int ai2 = ai * ai;
@@ -190,6 +193,8 @@ __device__ void finish_column(const FrameArgs& f, const float* part, int q, int 
 // closes the loop step's residual WFE and advances the frame counter.
 __global__ void __launch_bounds__(256) slopes_kernel(FrameArgs f, int nd) {
   __shared__ double red[32];
+  pdl_trigger();
+  pdl_wait();
   double fl = 0.0;
   for (int t = threadIdx.x; t < nd; t += blockDim.x) fl += f.flux_part[t];
   const float F = (float)(block_sum(fl, red) / (double)f.nv);
@@ -244,8 +249,10 @@ pyr_cols_kernel(ColArgs a) {
   const int g = blockIdx.y;                       // modulation group
   const int k0 = g * a.kper;
   const int kc = min(a.kper, a.K - k0);
+  pdl_trigger();
   for (int t = threadIdx.x; t < TWN; t += blockDim.x) tw_s[t] = a.tw[t];
   for (int t = threadIdx.x; t < BL; t += blockDim.x) mk_s[t] = a.mask[t];
+  pdl_wait();  // H, the partial frames and the counters belong to the predecessors
   const float ci = 0.5f * (float)(Np - 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int y = q * a.b + warp;
@@ -410,7 +417,7 @@ size_t rows_smem(pas_pyr_t y, int rows, int s_chunk) {
                            (size_t)rows * (y->p.Np + y->kern.pitch));
 }
 
-static void launch_rows(pas_pyr_t y, const float* d_opd, cudaStream_t st) {
+static void launch_rows(pas_pyr_t y, const float* d_opd, cudaStream_t st, bool pdl = false) {
   const pas_pyr_params& p = y->p;
   RowArgs ra;
   ra.opd = d_opd;
@@ -426,11 +433,11 @@ static void launch_rows(pas_pyr_t y, const float* d_opd, cudaStream_t st) {
   ra.n_s = y->n_s;
   ra.s_chunk = y->s_chunk;
   dim3 gr((p.Np + y->rows - 1) / y->rows, y->n_schunks);
-  y->kern.rows<<<gr, y->rows * 32, rows_smem(y, y->rows, y->s_chunk), st>>>(ra);
+  launch_k(y->kern.rows, gr, dim3(y->rows * 32), rows_smem(y, y->rows, y->s_chunk), st, pdl, ra);
 }
 
 static void launch_cols(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream_t st,
-                        const LoopExtra* fa_extra, bool increment_ctr) {
+                        const LoopExtra* fa_extra, bool increment_ctr, bool pdl = false) {
   const pas_pyr_params& p = y->p;
   ColArgs ca;
   ca.H = y->d_H;
@@ -467,11 +474,11 @@ static void launch_cols(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream
   fa.local_norm = p.local_norm;
   fa.wfe = fa_extra ? *fa_extra : LoopExtra();
   dim3 gc(y->nd, y->G);
-  y->kern.cols<<<gc, y->b * 32, y->smem_cols, st>>>(ca);
+  launch_k(y->kern.cols, gc, dim3(y->b * 32), y->smem_cols, st, pdl, ca);
 }
 
 static void launch_slopes(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream_t st,
-                          const LoopExtra* fa_extra, bool increment_ctr) {
+                          const LoopExtra* fa_extra, bool increment_ctr, bool pdl = false) {
   FrameArgs f{};
   f.frame = d_frame ? d_frame : y->d_frame;
   f.flux_part = y->d_flux_part;
@@ -484,19 +491,23 @@ static void launch_slopes(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStre
   f.n_sub = y->p.n_sub;
   f.local_norm = y->p.local_norm;
   f.wfe = fa_extra ? *fa_extra : LoopExtra();
-  slopes_kernel<<<(y->n_valid + 255) / 256, 256, 0, st>>>(f, y->nd);
+  launch_k(slopes_kernel, dim3((y->n_valid + 255) / 256), dim3(256), 0, st, pdl, f, y->nd);
 }
 
 // Launch the pyramid kernels (rows pass, columns pass with the detector frame,
 // noise and slopes). `fa_extra`: the loop's frame counter and WFE fields.
 pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes,
-                      cudaStream_t st, const LoopExtra* fa_extra, bool increment_ctr, cudaEvent_t* ev) {
+                      cudaStream_t st, const LoopExtra* fa_extra, bool increment_ctr, cudaEvent_t* ev,
+                      bool pdl_first) {
+  // the columns and slopes kernels follow the rows pass programmatically unless
+  // events are recorded between the kernels
+  const bool pdl = ev == nullptr;
   if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
-  launch_rows(y, d_opd, st);
+  launch_rows(y, d_opd, st, pdl && pdl_first);
   if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
-  launch_cols(y, d_frame, d_slopes, st, fa_extra, increment_ctr);
+  launch_cols(y, d_frame, d_slopes, st, fa_extra, increment_ctr, pdl);
   if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
-  launch_slopes(y, d_frame, d_slopes, st, fa_extra, increment_ctr);
+  launch_slopes(y, d_frame, d_slopes, st, fa_extra, increment_ctr, pdl);
   return check_launch(y->ctx, "pas_pyr_measure launch");
 }
 

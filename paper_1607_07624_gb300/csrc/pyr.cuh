@@ -18,10 +18,12 @@ struct LoopExtra {
 
 // Launch rows pass, cols pass and frame/slopes on `st`. `extra` (may be null)
 // supplies the loop's frame counter and residual-WFE fields. `ev` (may be null):
-// two events recorded before the rows and the columns (+ frame, slopes) kernels.
+// three events recorded before the rows, columns and slopes kernels (the kernels are
+// then launched without programmatic dependence). pdl_first: the rows pass itself
+// follows a kernel programmatically.
 pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes,
                       cudaStream_t st, const LoopExtra* extra, bool increment_ctr,
-                      cudaEvent_t* ev = nullptr);
+                      cudaEvent_t* ev = nullptr, bool pdl_first = false);
 int pyr_n_pupil(pas_pyr_t y);
 int pyr_nd(pas_pyr_t y);
 

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "pdl.cuh"
 #include "recon.cuh"
 
 namespace pas {
@@ -36,6 +37,17 @@ __global__ void __launch_bounds__(256) recon_kernel(ReconArgs a) {
   extern __shared__ float4 s4[];  // [n_s_pad / 4]
   __shared__ float part[8];
   __shared__ bool is_last;
+  pdl_trigger();
+  {
+    // the reconstructor is constant: start its rows towards L2 before waiting
+    const int m0 = blockIdx.x * RECON_ROWS;
+    const size_t row_bytes = (size_t)a.n_s_pad * (BF16 ? 2 : 4);
+    const char* base = BF16 ? reinterpret_cast<const char*>(a.Rb) : reinterpret_cast<const char*>(a.R);
+    const int nrow = min(RECON_ROWS, a.n_m - m0);
+    const int lines = (int)((row_bytes * nrow + 127) / 128);
+    for (int t = threadIdx.x; t < lines; t += blockDim.x) prefetch_l2(base + row_bytes * m0 + (size_t)t * 128);
+  }
+  pdl_wait();
   float* s_s = reinterpret_cast<float*>(s4);
   for (int t = threadIdx.x; t < a.n_s_pad; t += blockDim.x) s_s[t] = t < a.n_s ? a.s[t] : 0.f;
   __syncthreads();
@@ -104,7 +116,7 @@ static uint16_t f32_to_bf16_rne(float f) {
   return (uint16_t)(u >> 16);
 }
 
-pas_status recon_launch(pas_recon_t r, ReconArgs a, cudaStream_t st) {
+pas_status recon_launch(pas_recon_t r, ReconArgs a, cudaStream_t st, bool pdl) {
   a.R = r->d_R;
   a.Rb = r->d_Rb;
   a.scale = r->d_scale;
@@ -114,9 +126,10 @@ pas_status recon_launch(pas_recon_t r, ReconArgs a, cudaStream_t st) {
   a.done = r->d_done;
   const size_t smem = sizeof(float) * (size_t)r->n_s_pad;
   const int grid = (r->n_modes + RECON_ROWS - 1) / RECON_ROWS;
-  if (r->prec == PAS_BF16) recon_kernel<true><<<grid, 256, smem, st>>>(a);
-  else recon_kernel<false><<<grid, 256, smem, st>>>(a);
-  return check_launch(r->ctx, "reconstructor launch");
+  cudaError_t e = r->prec == PAS_BF16 ? launch_k(recon_kernel<true>, dim3(grid), dim3(256), smem, st, pdl, a)
+                                       : launch_k(recon_kernel<false>, dim3(grid), dim3(256), smem, st, pdl, a);
+  if (e != cudaSuccess) return set_error(r->ctx, PAS_ECUDA, "reconstructor launch: %s", cudaGetErrorString(e));
+  return PAS_OK;
 }
 
 }  // namespace pas

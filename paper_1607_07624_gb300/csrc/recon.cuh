@@ -36,5 +36,5 @@ struct pas_recon_s {
 };
 
 namespace pas {
-pas_status recon_launch(pas_recon_t r, ReconArgs a, cudaStream_t st);
+pas_status recon_launch(pas_recon_t r, ReconArgs a, cudaStream_t st, bool pdl = false);
 }
