@@ -127,126 +127,84 @@ __global__ void atmo_kernel(AtmoArgs a, const long long* d_step, long long h_ste
   }
 }
 
-// Residual over the pupil pixel list: out[pix] = atm - dm_sign * (M c).
-// CTA: RES_WARPS warps over one tile of RES_TILE = 64 pixels; each half-warp
-// covers the tile with one 16-byte load per lane and mode, and half-warp g of the
-// CTA takes the modes m = g mod RES_GROUPS. Small tiles keep the SMs evenly
-// loaded; the atmosphere taps are loaded before the GEMV.
-constexpr int RES_WARPS = 16;
-constexpr int RES_TILE = 64;
-constexpr int RES_GROUPS = 2 * RES_WARPS;
+constexpr int RES_TILE = 64;        // pixels per CTA (one contiguous basis block)
+constexpr int RES_THREADS = 256;
+constexpr int RES_CHUNK = 32;       // modes per pipeline stage: 32 x 64 x 4 B = 8 KB
+constexpr int RES_STAGES = 4;
+constexpr int RES_GROUPS = RES_THREADS / RES_TILE;
 
-// Bilinear taps of L layers for one pixel, loaded before use.
-template <int L> struct Taps {
-  float v[L][4];
-  __device__ __forceinline__ void load(const AtmoArgs& a, const int* six, const int* siy, int i, int j) {
-    const int S = a.S;
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-      int i0 = i + six[l];
-      if (i0 >= S) i0 -= S;
-      int j0 = j + siy[l];
-      if (j0 >= S) j0 -= S;
-      const int i1 = (i0 + 1 == S) ? 0 : i0 + 1;
-      const int j1 = (j0 + 1 == S) ? 0 : j0 + 1;
-      const float* sc = a.screens + (size_t)l * S * S;
-      v[l][0] = __ldg(sc + (size_t)i0 * S + j0);
-      v[l][1] = __ldg(sc + (size_t)i1 * S + j0);
-      v[l][2] = __ldg(sc + (size_t)i0 * S + j1);
-      v[l][3] = __ldg(sc + (size_t)i1 * S + j1);
-    }
-  }
-  __device__ __forceinline__ float combine(const float* sfx, const float* sfy) const {
-    float acc = 0.f;
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-      const float fx = sfx[l], fy = sfy[l];
-      acc += (1.f - fx) * (1.f - fy) * v[l][0] + fx * (1.f - fy) * v[l][1] + (1.f - fx) * fy * v[l][2] +
-             fx * fy * v[l][3];
-    }
-    return acc;
-  }
-};
-template <> struct Taps<0> {
-  __device__ __forceinline__ void load(const AtmoArgs&, const int*, const int*, int, int) {}
-  __device__ __forceinline__ float combine(const float*, const float*) const { return 0.f; }
-};
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// LT = number of layers (0: the atmosphere comes from opd_atm or is zero; -1:
-// any count, sampled after the GEMV with a runtime loop).
-template <int LT>
-__global__ void __launch_bounds__(RES_WARPS * 32) residual_kernel(ResArgs a) {
-  extern __shared__ float c_s[];                  // [n_m]
+// Residual over the pupil pixel list: out[pix] = atm - dm_sign * (M c), atm read
+// from opd_atm (or zero). CTA: one 64-pixel tile whose basis block [n_m][64] is
+// streamed through shared memory by a RES_STAGES-deep cp.async pipeline (16-byte
+// copies, L1 bypassed); thread t accumulates pixel t % 64 over the modes
+// m = t / 64 mod 4 of each stage. The basis is constant, so the first stages are
+// issued before the programmatic wait and overlap the predecessor kernel.
+__global__ void __launch_bounds__(RES_THREADS) residual_kernel(ResArgs a) {
+  extern __shared__ float4 res_smem[];
+  float4* stage = res_smem;                                            // [S][CHUNK*TILE/4]
+  float* c_s = reinterpret_cast<float*>(res_smem + RES_STAGES * RES_CHUNK * RES_TILE / 4);  // [n_m]
   __shared__ float red[RES_GROUPS][RES_TILE];
-  __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
-  __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
-  __shared__ double wred[2][RES_WARPS];
+  __shared__ double wred[2][RES_THREADS / 32];
+  const int tid = threadIdx.x;
+  const int n_m = a.MT ? a.n_m : 0;
+  const int nchunks = (n_m + RES_CHUNK - 1) / RES_CHUNK;
+  const float4* blk = reinterpret_cast<const float4*>(a.MT + (size_t)blockIdx.x * n_m * RES_TILE);
+  constexpr int V4 = RES_CHUNK * RES_TILE / 4;   // float4 per full stage (512)
+  auto issue = [&](int c) {
+    if (c < nchunks) {
+      const int rows = min(RES_CHUNK, n_m - c * RES_CHUNK);
+      const int nv4 = rows * RES_TILE / 4;
+      float4* dst = stage + (c % RES_STAGES) * V4;
+      const float4* src = blk + (size_t)c * V4;
+      for (int v = tid; v < nv4; v += RES_THREADS) cp_async16(dst + v, src + v);
+    }
+    cp_async_commit();
+  };
   pdl_trigger();
-  // the basis is constant: stream this tile's block towards L2 while the
-  // predecessor (atmosphere) still runs
-  if (a.MT && a.n_m > 0) {
-    const char* blk = reinterpret_cast<const char*>(a.MT + (size_t)blockIdx.x * a.n_m * RES_TILE);
-    const int lines = a.n_m * RES_TILE * 4 / 128;
-    for (int t = threadIdx.x; t < lines; t += blockDim.x) prefetch_l2(blk + (size_t)t * 128);
-  }
+#pragma unroll
+  for (int c = 0; c < RES_STAGES - 1; ++c) issue(c);
   pdl_wait();
   const long long step = a.d_step ? *a.d_step : a.h_step;
   const float* cmd = a.cmd;
   if (a.cmd_ring) cmd = a.cmd_ring + (size_t)(step % a.delay) * a.n_m;
-  for (int m = threadIdx.x; m < a.n_m; m += blockDim.x) c_s[m] = cmd[m];
-  if (threadIdx.x < a.atmo.L) {
-    layer_shift(a.atmo.vx[threadIdx.x], step, a.atmo.S, &six[threadIdx.x], &sfx[threadIdx.x]);
-    layer_shift(a.atmo.vy[threadIdx.x], step, a.atmo.S, &siy[threadIdx.x], &sfy[threadIdx.x]);
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int m = tid; m < n_m; m += RES_THREADS) c_s[m] = cmd[m];
   const int base = blockIdx.x * RES_TILE;
-  // the last warps own the tile's pixels: their atmosphere loads are issued
-  // before their share of the GEMV and combined after it
-  const int owner_t = (int)threadIdx.x - (RES_WARPS * 32 - RES_TILE);
-  const int p = base + owner_t;
-  const bool owner = owner_t >= 0 && p < a.n_pix;
-  int flat = 0, pi = 0, pj = 0;
-  Taps<(LT > 0 ? LT : 0)> taps;
-  float atm_in = 0.f;
+  const int px = tid % RES_TILE, grp = tid / RES_TILE;
+  const int p = base + px;
+  const bool owner = grp == 0 && p < a.n_pix;
+  int flat = 0;
+  float atm = 0.f;
   if (owner) {
     flat = a.pix[p];
-    pi = flat / a.Np;
-    pj = flat - pi * a.Np;
-    if (LT > 0) taps.load(a.atmo, six, siy, pi, pj);
-    else if (LT == 0 && a.opd_atm) atm_in = a.opd_atm[flat];
+    if (a.opd_atm) atm = a.opd_atm[flat];
   }
-  if (a.MT && a.n_m > 0) {
-    const int g = 2 * warp + (lane >> 4), l16 = lane & 15;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    // this tile's block of the basis: [n_m][RES_TILE] contiguous
-    const float4* col = reinterpret_cast<const float4*>(a.MT + (size_t)blockIdx.x * a.n_m * RES_TILE) + l16;
+  float acc = 0.f;
+  for (int c = 0; c < nchunks; ++c) {
+    issue(c + RES_STAGES - 1);
+    cp_async_wait<RES_STAGES - 1>();
+    __syncthreads();
+    const float* sb = reinterpret_cast<const float*>(stage + (c % RES_STAGES) * V4);
+    const int rows = min(RES_CHUNK, n_m - c * RES_CHUNK);
+    const float* cc = c_s + c * RES_CHUNK;
 #pragma unroll 8
-    for (int m = g; m < a.n_m; m += RES_GROUPS) {
-      const float4 v = __ldg(col + (size_t)m * (RES_TILE / 4));
-      const float c = c_s[m];
-      acc.x = fmaf(c, v.x, acc.x);
-      acc.y = fmaf(c, v.y, acc.y);
-      acc.z = fmaf(c, v.z, acc.z);
-      acc.w = fmaf(c, v.w, acc.w);
-    }
-    red[g][4 * l16 + 0] = acc.x;
-    red[g][4 * l16 + 1] = acc.y;
-    red[g][4 * l16 + 2] = acc.z;
-    red[g][4 * l16 + 3] = acc.w;
+    for (int r = grp; r < rows; r += RES_GROUPS) acc = fmaf(cc[r], sb[r * RES_TILE + px], acc);
+    __syncthreads();
   }
+  red[grp][px] = acc;
   __syncthreads();
   double s1 = 0.0, s2 = 0.0;
   if (owner) {
-    float atm;
-    if (LT > 0) atm = taps.combine(sfx, sfy);
-    else if (LT == 0) atm = atm_in;
-    else atm = atmo_sample(a.atmo, six, siy, sfx, sfy, pi, pj);
     float dm = 0.f;
-    if (a.MT && a.n_m > 0) {
 #pragma unroll
-      for (int g = 0; g < RES_GROUPS; ++g) dm += red[g][owner_t];
-    }
+    for (int g = 0; g < RES_GROUPS; ++g) dm += red[g][px];
     const float r = atm - a.dm_sign * dm;
     a.out[flat] = r;
     s1 = r;
@@ -257,14 +215,15 @@ __global__ void __launch_bounds__(RES_WARPS * 32) residual_kernel(ResArgs a) {
       s1 += __shfl_down_sync(0xffffffffu, s1, o);
       s2 += __shfl_down_sync(0xffffffffu, s2, o);
     }
+    const int warp = tid >> 5, lane = tid & 31;
     if (lane == 0) {
       wred[0][warp] = s1;
       wred[1][warp] = s2;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       double t1 = 0.0, t2 = 0.0;
-      for (int w = 0; w < RES_WARPS; ++w) {
+      for (int w = 0; w < RES_THREADS / 32; ++w) {
         t1 += wred[0][w];
         t2 += wred[1][w];
       }
@@ -309,24 +268,12 @@ pas_status atmo_pupil_launch(pas_ctx_t ctx, const AtmoArgs& a, const int* pix, i
 pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, bool pdl) {
   const int tiles = residual_tiles(a.n_pix);
   if (tiles == 0) return PAS_OK;
-  const size_t smem = sizeof(float) * (size_t)std::max(a.n_m, 1);
-  const dim3 g(tiles), blk(RES_WARPS * 32);
-  if (a.atmo.L == 0) {
-    cudaError_t e = launch_k(residual_kernel<0>, g, blk, smem, st, pdl, a);
-    if (e != cudaSuccess) return set_error(ctx, PAS_ECUDA, "residual kernel launch: %s", cudaGetErrorString(e));
-    return PAS_OK;
-  }
-  switch (a.atmo.L) {
-    case 0: residual_kernel<0><<<g, blk, smem, st>>>(a); break;
-    case 1: residual_kernel<1><<<g, blk, smem, st>>>(a); break;
-    case 2: residual_kernel<2><<<g, blk, smem, st>>>(a); break;
-    case 3: residual_kernel<3><<<g, blk, smem, st>>>(a); break;
-    case 4: residual_kernel<4><<<g, blk, smem, st>>>(a); break;
-    case 5: residual_kernel<5><<<g, blk, smem, st>>>(a); break;
-    case 6: residual_kernel<6><<<g, blk, smem, st>>>(a); break;
-    default: residual_kernel<-1><<<g, blk, smem, st>>>(a); break;
-  }
-  return check_launch(ctx, "residual kernel launch");
+  if (a.atmo.L != 0) return set_error(ctx, PAS_EINVAL, "residual kernel: the atmosphere comes from opd_atm");
+  const size_t smem = sizeof(float4) * RES_STAGES * RES_CHUNK * RES_TILE / 4 + sizeof(float) * (size_t)std::max(a.n_m, 1);
+  cudaError_t e = raise_dyn_smem((const void*)residual_kernel, smem);
+  if (e == cudaSuccess) e = launch_k(residual_kernel, dim3(tiles), dim3(RES_THREADS), smem, st, pdl, a);
+  if (e != cudaSuccess) return set_error(ctx, PAS_ECUDA, "residual kernel launch: %s", cudaGetErrorString(e));
+  return PAS_OK;
 }
 
 }  // namespace pas
