@@ -199,3 +199,54 @@ def test_gaussian_moments_and_frame_noise_shape():
     c = nz.apply_noise(fr, 1000.0, 36 * 2, 0.5, 9, 1)
     assert np.array_equal(a, b) and not np.array_equal(a, c)
     assert abs(a.mean() - 2.0 * 1000 / 72) < 5
+
+
+# ---------------------------------------------------------------- MLP reconstructor
+
+def test_mlp_gradient_matches_central_differences():
+    from oracle import mlp
+    g = np.random.default_rng(4)
+    sizes = mlp.layer_sizes(7, 6, 3, 5)
+    params = mlp.init_params(sizes, g)
+    for i in range(1, len(params), 2):
+        params[i] = g.standard_normal(params[i].shape) * 0.1
+    x = g.standard_normal((4, 7))
+    y = g.standard_normal((4, 5))
+    out, cache = mlp.forward(params, x)
+    grads = mlp.flatten(mlp.backward(params, cache, out, y))
+    vec = mlp.flatten(params)
+    h = 1e-6
+    num = np.empty_like(vec)
+    for k in range(vec.size):
+        vp, vm = vec.copy(), vec.copy()
+        vp[k] += h
+        vm[k] -= h
+        lp = mlp.loss(mlp.forward(mlp.unflatten(vp, sizes), x)[0], y)
+        lm = mlp.loss(mlp.forward(mlp.unflatten(vm, sizes), x)[0], y)
+        num[k] = (lp - lm) / (2 * h)
+    assert np.max(np.abs(num - grads)) < 1e-7 * max(1.0, np.max(np.abs(grads)))
+
+
+def test_gelu_closed_form_points_and_derivative():
+    from oracle import mlp
+    from scipy.stats import norm
+    z = np.array([-3.0, -1.0, 0.0, 0.5, 2.0])
+    assert np.allclose(mlp.gelu(z), z * norm.cdf(z), rtol=0, atol=1e-15)
+    h = 1e-6
+    assert np.allclose(mlp.gelu_grad(z), (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h), atol=1e-8)
+
+
+def test_mlp_adam_overfits_a_tiny_batch():
+    from oracle import mlp
+    g = np.random.default_rng(5)
+    sizes = mlp.layer_sizes(6, 16, 2, 3)
+    params = mlp.init_params(sizes, g)
+    x = g.standard_normal((8, 6))
+    y = g.standard_normal((8, 3))
+    m = [np.zeros_like(p) for p in params]
+    v = [np.zeros_like(p) for p in params]
+    l0 = mlp.loss(mlp.forward(params, x)[0], y)
+    for t in range(1, 1501):
+        out, cache = mlp.forward(params, x)
+        mlp.adam_update(params, mlp.backward(params, cache, out, y), m, v, t, 1e-2)
+    assert mlp.loss(mlp.forward(params, x)[0], y) < 1e-4 * l0
