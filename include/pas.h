@@ -53,6 +53,7 @@ typedef struct pas_pyr_s*   pas_pyr_t;
 typedef struct pas_recon_s* pas_recon_t;
 typedef struct pas_dm_s*    pas_dm_t;
 typedef struct pas_loop_s*  pas_loop_t;
+typedef struct pas_mlp_s*   pas_mlp_t;
 
 /* ------------------------------------------------------------------ context */
 
@@ -294,12 +295,91 @@ void pas_loop_destroy(pas_loop_t loop);
  * the loop like pas_loop_step.
  * The step's kernels, in order: atmosphere, residual (- DM shape), pyramid
  * rows pass, pyramid columns pass (+ detector frame and noise in the last CTA of
- * each detector column), slopes, reconstructor + integrator (+ step counter). */
+ * each detector column), slopes, reconstructor + integrator (+ step counter);
+ * with a learned reconstructor attached the last entry spans its layer kernels. */
 #define PAS_LOOP_KERNELS 6
 pas_status pas_loop_profile(pas_loop_t loop, int32_t n_steps, float* h_ms, int32_t cap,
                             int32_t* n_kernels);
 /* Name of kernel `idx` of pas_loop_profile (static string), NULL if out of range. */
 const char* pas_loop_kernel_name(int32_t idx);
+
+/* -------------------------------------------------- learned reconstructor
+ * A multilayer perceptron from slopes to modal coefficients, used by the loop
+ * in place of the linear modal reconstructor (Table 1 modalrec). The paper's
+ * reconstructor is linear; this network is an extension of it:
+ *   x = (s - mean) * inv_std                      (per slope, set by set_norm)
+ *   h_l = gelu(W_l h_{l-1} + b_l), l < L - 1      gelu(z) = z * Phi(z) (erf form)
+ *   out = W_{L-1} h_{L-2} + b_{L-1}
+ * trained on the mean squared error mean_{b,o} (out - y)^2 with Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).
+ * Parameters travel as one packed float32 vector: W_0 ([sizes[1]][sizes[0]]
+ * row-major), b_0, W_1, b_1, ... (pas_mlp_n_params floats). The object keeps
+ * float32 master weights and bf16 working copies: batched passes (forward,
+ * gradients, training) run as bf16 tensor-core GEMMs with float32 accumulation;
+ * single-vector inference (apply, the loop) reads the bf16 weights with float32
+ * activations. */
+
+/* n_layers in [1, 8] weight layers; sizes: host int32 [n_layers + 1] widths
+ * (sizes[0] = slopes, sizes[n_layers] = modes); max_batch >= 1 bounds the batch
+ * of forward / gradients / train. Parameters start at zero, mean 0, inv_std 1. */
+pas_status pas_mlp_create(pas_ctx_t ctx, int32_t n_layers, const int32_t* sizes, int32_t max_batch,
+                          pas_mlp_t* out);
+void pas_mlp_destroy(pas_mlp_t mlp);
+/* Number of parameters (packed), -1 for a NULL handle. Host only. */
+int64_t pas_mlp_n_params(pas_mlp_t mlp);
+/* h_params: host float32 [n_params] packed. set resets the Adam state.
+ * Both synchronise. */
+pas_status pas_mlp_set_params(pas_mlp_t mlp, const float* h_params);
+pas_status pas_mlp_get_params(pas_mlp_t mlp, float* h_params);
+/* Input standardisation, host float32 [sizes[0]] each; synchronous. */
+pas_status pas_mlp_set_norm(pas_mlp_t mlp, const float* h_mean, const float* h_inv_std);
+/* Single vector: d_slopes device float32 [sizes[0]] -> d_out [sizes[L]]. */
+pas_status pas_mlp_apply(pas_mlp_t mlp, const float* d_slopes, float* d_out);
+/* Batch (tensor cores): d_S device float32 [batch][sizes[0]] raw slopes ->
+ * d_out [batch][sizes[L]]. */
+pas_status pas_mlp_forward(pas_mlp_t mlp, int32_t batch, const float* d_S, float* d_out);
+/* Loss gradient of the batch (d_S as above, d_Y [batch][sizes[L]] targets):
+ * d_grad device float32 [n_params] packed; h_loss (may be NULL) receives the
+ * loss, which makes the call synchronous. Parameters are not changed. */
+pas_status pas_mlp_gradients(pas_mlp_t mlp, int32_t batch, const float* d_S, const float* d_Y,
+                             float* d_grad, float* h_loss);
+/* n_steps Adam steps over a device-resident data set d_S [n_data][sizes[0]],
+ * d_Y [n_data][sizes[L]]: step t uses the samples d_idx[t*batch .. t*batch +
+ * batch - 1] (int32 in [0, n_data)) and learning rate d_lr[t], and writes its
+ * loss (before the update) to d_loss[t]. All device arrays are caller-owned
+ * and must stay valid; the step is captured once as a CUDA graph per (arrays,
+ * batch) and replayed. Out-of-range indices read sample 0 and are reported by
+ * pas_mlp_check. */
+pas_status pas_mlp_train(pas_mlp_t mlp, const float* d_S, const float* d_Y, int32_t n_data,
+                         int32_t batch, const int32_t* d_idx, const float* d_lr, int32_t n_steps,
+                         float* d_loss);
+/* Synchronise, then report and clear the device flags: PAS_ETIMEOUT if a
+ * tensor-core pipeline wait gave up, PAS_EINVAL for an out-of-range sample
+ * index; *h_fault (may be NULL) = 1 if the loop's last layer produced a
+ * non-finite coefficient since the last check (that coefficient's update was
+ * replaced by 0). */
+pas_status pas_mlp_check(pas_mlp_t mlp, uint32_t* h_fault);
+/* One training pair from a residual OPD: opd = amp * d_opd (device float32
+ * [Np][Np]); d_slopes [2 n_valid] = pyramid slopes of opd (reference slopes
+ * subtracted, no noise); d_coeffs [n_modes] = (1/n_pix) M^T opd, the modal
+ * projection for a basis with M^T M = n_pix I. d_work: device float32 scratch
+ * of Np*Np + (2 n_sub)^2 elements. */
+pas_status pas_mlp_pair(pas_pyr_t pyr, pas_dm_t dm, const float* d_opd, float amp, float* d_work,
+                        float* d_slopes, float* d_coeffs);
+/* Use `mlp` (NULL: the linear reconstructor again) as the loop's reconstructor
+ * from the next step on; sizes must be [2 n_valid, ..., n_modes]. The loop's
+ * graph is captured again at the next step. */
+pas_status pas_loop_set_mlp(pas_loop_t loop, pas_mlp_t mlp);
+
+/* BF16 tensor-core GEMM (the kernel behind the batched network passes):
+ * C[M][N] = A[M][K] * B[N][K]^T, A and B device bf16 (raw uint16 bits)
+ * row-major with leading dimensions lda, ldb (multiples of 8, base 16-byte
+ * aligned), C device float32 with leading dimension ldc; float32 accumulation.
+ * tile_n: output tile width 64, 128 or 256, 0 = automatic. d_err: device
+ * uint32 that receives a nonzero code if a pipeline wait timed out. */
+pas_status pas_gemm_bf16(pas_ctx_t ctx, int32_t M, int32_t N, int32_t K, const uint16_t* d_A,
+                         int32_t lda, const uint16_t* d_B, int32_t ldb, float* d_C, int32_t ldc,
+                         int32_t tile_n, uint32_t* d_err);
 
 #ifdef __cplusplus
 }

@@ -9,6 +9,7 @@
 
 #include "atmo_dm.cuh"
 #include "internal.h"
+#include "mlp.cuh"
 #include "pyr.cuh"
 #include "recon.cuh"
 
@@ -18,6 +19,7 @@ struct pas_loop_s {
   pas_pyr_t pyr = nullptr;
   pas_recon_t rec = nullptr;
   pas_dm_t dm = nullptr;
+  pas_mlp_t mlp = nullptr;  // learned reconstructor in place of rec (optional)
   int delay = 1, hist = 1, n_m = 0, n_slopes = 0, nd = 0, Np = 0, n_tiles = 0;
   float* d_opd = nullptr;
   float* d_frame = nullptr;
@@ -80,7 +82,7 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   rc.cmd_last = L->d_cmd;
   rc.step_inc = L->d_step;
   if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
-  s = pas::recon_launch(L->rec, rc, st, pdl);
+  s = L->mlp ? pas::mlp_loop_launch(L->mlp, rc, st, pdl) : pas::recon_launch(L->rec, rc, st, pdl);
   if (ev) cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
   return s;
 }
@@ -255,6 +257,24 @@ pas_status pas_loop_profile(pas_loop_t L, int32_t n_steps, float* h_ms, int32_t 
   }
   for (int k = 0; k < PAS_LOOP_KERNELS; ++k) h_ms[k] = (float)(acc[k] / n_steps);
   if (n_kernels) *n_kernels = PAS_LOOP_KERNELS;
+  return PAS_OK;
+}
+
+pas_status pas_loop_set_mlp(pas_loop_t L, pas_mlp_t m) {
+  if (!L) return pas::set_global_error(PAS_EINVAL, "pas_loop_set_mlp: NULL loop");
+  if (m)
+    PAS_CHECK_ARG(L->ctx, m->sz[0] == L->n_slopes && m->sz[m->L] == L->n_m,
+                  "pas_loop_set_mlp: network sizes must be [2 n_valid, ..., n_modes]");
+  PAS_CUDA_TRY(L->ctx, cudaStreamSynchronize(L->ctx->stream));
+  if (L->exec) cudaGraphExecDestroy(L->exec);
+  if (L->graph) cudaGraphDestroy(L->graph);
+  if (L->prof_exec) cudaGraphExecDestroy(L->prof_exec);
+  if (L->prof_graph) cudaGraphDestroy(L->prof_graph);
+  L->exec = nullptr;
+  L->graph = nullptr;
+  L->prof_exec = nullptr;
+  L->prof_graph = nullptr;
+  L->mlp = m;
   return PAS_OK;
 }
 

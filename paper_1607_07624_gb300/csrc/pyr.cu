@@ -513,6 +513,7 @@ pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_
 
 int pyr_n_pupil(pas_pyr_t y) { return y->n_pupil; }
 int pyr_nd(pas_pyr_t y) { return y->nd; }
+int pyr_np(pas_pyr_t y) { return y->p.Np; }
 
 }  // namespace pas
 

@@ -26,5 +26,6 @@ pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_
                       cudaEvent_t* ev = nullptr, bool pdl_first = false);
 int pyr_n_pupil(pas_pyr_t y);
 int pyr_nd(pas_pyr_t y);
+int pyr_np(pas_pyr_t y);
 
 }  // namespace pas

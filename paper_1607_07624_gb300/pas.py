@@ -101,6 +101,20 @@ _SIGS = {
     "pas_loop_destroy": (None, [vp]),
     "pas_loop_profile": (C.c_int, [vp, i32, vp, i32, P(i32)]),
     "pas_loop_kernel_name": (C.c_char_p, [i32]),
+    "pas_mlp_create": (C.c_int, [vp, i32, vp, i32, P(vp)]),
+    "pas_mlp_destroy": (None, [vp]),
+    "pas_mlp_n_params": (i64, [vp]),
+    "pas_mlp_set_params": (C.c_int, [vp, vp]),
+    "pas_mlp_get_params": (C.c_int, [vp, vp]),
+    "pas_mlp_set_norm": (C.c_int, [vp, vp, vp]),
+    "pas_mlp_apply": (C.c_int, [vp, vp, vp]),
+    "pas_mlp_forward": (C.c_int, [vp, i32, vp, vp]),
+    "pas_mlp_gradients": (C.c_int, [vp, i32, vp, vp, vp, vp]),
+    "pas_mlp_train": (C.c_int, [vp, vp, vp, i32, i32, vp, vp, i32, vp]),
+    "pas_mlp_check": (C.c_int, [vp, P(C.c_uint32)]),
+    "pas_mlp_pair": (C.c_int, [vp, vp, vp, C.c_float, vp, vp, vp]),
+    "pas_loop_set_mlp": (C.c_int, [vp, vp]),
+    "pas_gemm_bf16": (C.c_int, [vp, i32, i32, i32, vp, i32, vp, i32, vp, i32, i32, vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -371,6 +385,78 @@ def pas_loop_profile(loop, ctx, n_steps=1):
 def pas_loop_kernel_name(idx: int):
     r = _lib.pas_loop_kernel_name(int(idx))
     return r.decode() if r else None
+
+
+def pas_mlp_create(ctx, sizes, max_batch: int):
+    sz = np.ascontiguousarray(sizes, dtype=np.int32)
+    h = vp()
+    _check(_lib.pas_mlp_create(ctx, sz.size - 1, sz.ctypes.data, int(max_batch), C.byref(h)), ctx)
+    return h
+
+
+def pas_mlp_destroy(mlp):
+    _lib.pas_mlp_destroy(mlp)
+
+
+def pas_mlp_n_params(mlp) -> int:
+    return int(_lib.pas_mlp_n_params(mlp))
+
+
+def pas_mlp_set_params(mlp, ctx, params: np.ndarray):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != pas_mlp_n_params(mlp):
+        raise ValueError(f"expected {pas_mlp_n_params(mlp)} parameters, got {p.size}")
+    _check(_lib.pas_mlp_set_params(mlp, p.ctypes.data), ctx)
+
+
+def pas_mlp_get_params(mlp, ctx) -> np.ndarray:
+    p = np.zeros(pas_mlp_n_params(mlp), dtype=np.float32)
+    _check(_lib.pas_mlp_get_params(mlp, p.ctypes.data), ctx)
+    return p
+
+
+def pas_mlp_set_norm(mlp, ctx, mean: np.ndarray, inv_std: np.ndarray):
+    m = np.ascontiguousarray(mean, dtype=np.float32)
+    s = np.ascontiguousarray(inv_std, dtype=np.float32)
+    _check(_lib.pas_mlp_set_norm(mlp, m.ctypes.data, s.ctypes.data), ctx)
+
+
+def pas_mlp_apply(mlp, ctx, d_slopes, d_out):
+    _check(_lib.pas_mlp_apply(mlp, _ptr(d_slopes), _ptr(d_out)), ctx)
+
+
+def pas_mlp_forward(mlp, ctx, batch: int, d_S, d_out):
+    _check(_lib.pas_mlp_forward(mlp, int(batch), _ptr(d_S), _ptr(d_out)), ctx)
+
+
+def pas_mlp_gradients(mlp, ctx, batch: int, d_S, d_Y, d_grad) -> float:
+    loss = C.c_float()
+    _check(_lib.pas_mlp_gradients(mlp, int(batch), _ptr(d_S), _ptr(d_Y), _ptr(d_grad), C.byref(loss)), ctx)
+    return float(loss.value)
+
+
+def pas_mlp_train(mlp, ctx, d_S, d_Y, n_data: int, batch: int, d_idx, d_lr, n_steps: int, d_loss):
+    _check(_lib.pas_mlp_train(mlp, _ptr(d_S), _ptr(d_Y), int(n_data), int(batch), _ptr(d_idx), _ptr(d_lr),
+                              int(n_steps), _ptr(d_loss)), ctx)
+
+
+def pas_mlp_check(mlp, ctx) -> int:
+    f = C.c_uint32()
+    _check(_lib.pas_mlp_check(mlp, C.byref(f)), ctx)
+    return int(f.value)
+
+
+def pas_mlp_pair(pyr, dm, ctx, d_opd, amp: float, d_work, d_slopes, d_coeffs):
+    _check(_lib.pas_mlp_pair(pyr, dm, _ptr(d_opd), float(amp), _ptr(d_work), _ptr(d_slopes), _ptr(d_coeffs)), ctx)
+
+
+def pas_loop_set_mlp(loop, ctx, mlp):
+    _check(_lib.pas_loop_set_mlp(loop, mlp), ctx)
+
+
+def pas_gemm_bf16(ctx, M, N, K, d_A, lda, d_B, ldb, d_C, ldc, d_err, tile_n=0):
+    _check(_lib.pas_gemm_bf16(ctx, int(M), int(N), int(K), _ptr(d_A), int(lda), _ptr(d_B), int(ldb), _ptr(d_C),
+                              int(ldc), int(tile_n), _ptr(d_err)), ctx)
 
 
 def loaded_library_path() -> str:
