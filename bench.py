@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--recon", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-mlp", action="store_true", help="skip the learned-reconstructor measurements")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-budget-s", type=float, default=20.0)
     return ap.parse_args()
@@ -153,6 +154,90 @@ def algorithmic_work(cfg, n_pix, n_valid, n_modes, n_s_rows, recon_bytes_per_el)
         "slopes_kernel": {"bound": "latency", "bytes": 16.0 * n_valid + 8.0 * 2 * n_valid},
         "recon_kernel": {"bound": "hbm", "bytes": recon_bytes_per_el * n_modes * 2 * n_valid + 8.0 * n_modes},
     }
+
+
+def bench_mlp(sysg, peaks, timed, n_train=50, batch=1024):
+    """Learned reconstructor on this system's sizes (2 n_valid -> 1024^3 -> n_modes):
+    training throughput (Adam steps on a device-resident synthetic set larger than
+    L2, one CUDA-graph replay per step, timed back to back), a large standalone
+    tensor-core GEMM against the measured bf16 peak with cuBLAS beside it, and the
+    loop with the network as its reconstructor."""
+    import numpy as np
+    import torch
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.learned import MLPReconstructor, he_normal_params
+    ctx = sysg.ctx
+    sizes = [2 * sysg.n_valid, 1024, 1024, 1024, sysg.n_modes]
+    mlp = MLPReconstructor(ctx, sizes, max_batch=batch, seed=7)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    n_data = 65536
+    S = torch.randn(n_data, sizes[0], device="cuda", generator=gen)
+    Y = torch.randn(n_data, sizes[-1], device="cuda", generator=gen)
+    idx = torch.randint(0, n_data, (n_train * batch,), device="cuda", generator=gen, dtype=torch.int32)
+    lr = torch.full((n_train,), 1e-4, device="cuda")
+    loss = torch.zeros(n_train, device="cuda")
+    pas.pas_mlp_train(mlp.h, ctx, S, Y, n_data, batch, idx, lr, 5, loss)  # captures the step graph
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    pas.pas_mlp_train(mlp.h, ctx, S, Y, n_data, batch, idx, lr, n_train, loss)
+    e1.record()
+    torch.cuda.synchronize()
+    pas.pas_mlp_check(mlp.h, ctx)
+    ms = e0.elapsed_time(e1) / n_train
+    mac = sum(a * b for a, b in zip(sizes[:-1], sizes[1:]))
+    flops = 2.0 * batch * (2 * mac + (mac - sizes[0] * sizes[1]))  # forward, weight and input gradients
+    bf16_sus = peaks.get("bf16_tflops_sustained", 1700.0)
+    bf16_burst = peaks.get("bf16_tflops", 1900.0)
+    train = {"batch": batch, "ms_per_step": ms, "samples_per_s": batch / (ms * 1e-3),
+             "flops_per_step": flops, "tflops": flops / (ms * 1e-3) / 1e12,
+             "frac_of_bf16_sustained": flops / (ms * 1e-3) / 1e12 / bf16_sus,
+             "note": "whole Adam step (GEMMs + input, loss, bias-gradient and Adam kernels), one graph replay"}
+    del S, Y
+    # standalone GEMM C = A B^T, 8192^3, operands 2 x 128 MiB (larger than L2), back to back
+    n = 8192
+    A = torch.randn(n, n, device="cuda", generator=gen).to(torch.bfloat16)
+    B = torch.randn(n, n, device="cuda", generator=gen).to(torch.bfloat16)
+    C = torch.empty(n, n, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        pas.pas_gemm_bf16(ctx, n, n, n, A, n, B, n, C, n, err)
+    torch.cuda.synchronize()
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        pas.pas_gemm_bf16(ctx, n, n, n, A, n, B, n, C, n, err)
+    e1.record()
+    torch.cuda.synchronize()
+    ours = 2.0 * n ** 3 / (e0.elapsed_time(e1) / reps * 1e-3) / 1e12
+    for _ in range(3):
+        torch.matmul(A, B.t())
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        torch.matmul(A, B.t())
+    e1.record()
+    torch.cuda.synchronize()
+    cub = 2.0 * n ** 3 / (e0.elapsed_time(e1) / reps * 1e-3) / 1e12
+    gemm = {"shape": [n, n, n], "tflops": ours, "peak": bf16_burst, "frac": ours / bf16_burst,
+            "timeout_flag": int(err.item()), "cublas_bf16_tflops": cub,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured, burst)"}
+    del A, B, C
+    # loop with the network (hidden layers He-initialised, output layer zero: same work, bounded state)
+    p = he_normal_params(sizes, 7)
+    p[-(sizes[-1] * sizes[-2] + sizes[-1]):] = 0.0
+    mlp.set_params(p)
+    pas.pas_loop_set_mlp(sysg.loop, ctx, mlp.h)
+    sysg.set_state(0, np.zeros((sysg.delay, sysg.n_modes), dtype=np.float32))
+    sysg.step(20)
+    n_loop = 200
+    ms_loop = timed(lambda: sysg.step(1), n_loop)
+    chain = pas.pas_loop_profile(sysg.loop, ctx, 20).get("recon_kernel")
+    pas.pas_loop_set_mlp(sysg.loop, ctx, None)
+    mlp.close()
+    return {"sizes": sizes, "train": train, "gemm": gemm,
+            "loop_steps_per_s_with_network": n_loop / (ms_loop * 1e-3),
+            "network_chain_ms_in_loop": chain}
 
 
 def main():
@@ -317,6 +402,13 @@ def main():
     except (OSError, ValueError):
         pass
 
+    mlp_info = None
+    if not args.no_mlp:
+        try:
+            mlp_info = bench_mlp(sysg, peaks, timed)
+        except Exception as e:  # reported, never fatal for the headline number
+            mlp_info = {"error": str(e)}
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -356,6 +448,7 @@ def main():
                 "d2h_bytes_per_step": 4 * sysg.n_modes + 16},
         "gpu_launches": 6 * args.steps,
         "clocks": clocks,
+        "learned_reconstructor": mlp_info,
         "residual_wfe_nm_mean": float(np.mean(wfe[len(wfe) // 5:])) if len(wfe) else None,
         "setup_s": t_setup, "wall_timed_s": t_wall,
     }

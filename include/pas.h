@@ -250,6 +250,11 @@ pas_status pas_dm_update(pas_dm_t dm, const float* d_dmodes, const float* d_gain
  * d_opd_atm, d_opd_res: device float32 [Np][Np] (may alias); d_cmd [n_modes]. */
 pas_status pas_dm_residual(pas_dm_t dm, const float* d_opd_atm, const float* d_cmd,
                            float* d_opd_res);
+/* Modal projection (modal analysis of an OPD on the DM basis):
+ * coeffs = (1/n_pix) M^T opd over the pupil pixels, the least-squares
+ * coefficients when M^T M = n_pix I (orthonormalised basis, nm RMS).
+ * d_opd: device float32 [Np][Np]; d_coeffs: device float32 [n_modes] out. */
+pas_status pas_dm_project(pas_dm_t dm, const float* d_opd, float* d_coeffs);
 void pas_dm_destroy(pas_dm_t dm);
 
 /* ------------------------------------------------------------------ loop

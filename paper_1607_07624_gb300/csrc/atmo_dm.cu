@@ -276,6 +276,32 @@ pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, boo
   return PAS_OK;
 }
 
+// Modal projection c_j = (1/n_pix) sum_p M[p][j] opd[pix[p]]: the least-squares
+// modal coefficients for a basis with M^T M = n_pix I (the orthonormalised
+// bases of the DM). One CTA per mode streams that mode's column of the tiled
+// matrix; the OPD gather stays in L2 across CTAs.
+__global__ void __launch_bounds__(256) dm_project_kernel(const float* MT, const int32_t* pix, int n_pix, int n_m,
+                                                         const float* opd, float* c) {
+  __shared__ float red[8];
+  const int j = blockIdx.x;
+  float acc = 0.f;
+  for (int p = threadIdx.x; p < n_pix; p += blockDim.x)
+    acc = fmaf(MT[((size_t)(p >> 6) * n_m + j) * 64 + (p & 63)], opd[pix[p]], acc);
+  for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int i = 0; i < 8; ++i) t += red[i];
+    c[j] = t / (float)n_pix;
+  }
+}
+
+pas_status dm_project_launch(pas_dm_t dm, const float* opd, float* coeffs, cudaStream_t st) {
+  dm_project_kernel<<<dm->n_modes, 256, 0, st>>>(dm->d_MT, dm->d_pix, dm->n_pix, dm->n_modes, opd, coeffs);
+  return check_launch(dm->ctx, "modal projection launch");
+}
+
 }  // namespace pas
 
 // ------------------------------------------------------------------ objects
@@ -396,6 +422,11 @@ pas_status pas_dm_residual(pas_dm_t d, const float* d_opd_atm, const float* d_cm
   if (s != PAS_OK) return s;
   pas::zero_outside_kernel<<<(d->Np * d->Np + 255) / 256, 256, 0, st>>>(d_opd_res, d->Np, d->T_obs);
   return pas::check_launch(d->ctx, "pas_dm_residual zero launch");
+}
+
+pas_status pas_dm_project(pas_dm_t d, const float* d_opd, float* d_coeffs) {
+  if (!d || !d_opd || !d_coeffs) return pas::set_global_error(PAS_EINVAL, "pas_dm_project: NULL argument");
+  return pas::dm_project_launch(d, d_opd, d_coeffs, d->ctx->stream);
 }
 
 }  // extern "C"

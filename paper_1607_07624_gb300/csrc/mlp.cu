@@ -668,24 +668,6 @@ __global__ void scale_kernel(const float* in, float amp, float* out, int n) {
   if (i < n) out[i] = amp * in[i];
 }
 
-// c_j = (1/n_pix) sum_p M[p][j] opd[pix[p]] (projection on a basis with M^T M = n_pix I)
-__global__ void __launch_bounds__(256) dm_project_kernel(const float* MT, const int32_t* pix, int n_pix, int n_m,
-                                                         const float* opd, float* c) {
-  __shared__ float red[8];
-  const int j = blockIdx.x;
-  float acc = 0.f;
-  for (int p = threadIdx.x; p < n_pix; p += blockDim.x)
-    acc = fmaf(MT[((size_t)(p >> 6) * n_m + j) * 64 + (p & 63)], opd[pix[p]], acc);
-  for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float t = 0.f;
-    for (int i = 0; i < 8; ++i) t += red[i];
-    c[j] = t / (float)n_pix;
-  }
-}
-
 }  // namespace pas
 
 // ================================================================ C ABI
@@ -977,9 +959,7 @@ pas_status pas_mlp_pair(pas_pyr_t pyr, pas_dm_t dm, const float* d_opd, float am
   PAS_CUDA_TRY(ctx, cudaGetLastError());
   pas_status s = pas::pyr_launch(pyr, d_work, d_work + n, d_slopes, st, nullptr, true);
   if (s != PAS_OK) return s;
-  pas::dm_project_kernel<<<dm->n_modes, 256, 0, st>>>(dm->d_MT, dm->d_pix, dm->n_pix, dm->n_modes, d_work, d_coeffs);
-  PAS_CUDA_TRY(ctx, cudaGetLastError());
-  return PAS_OK;
+  return pas::dm_project_launch(dm, d_work, d_coeffs, st);
 }
 
 pas_status pas_gemm_bf16(pas_ctx_t ctx, int32_t M, int32_t N, int32_t K, const uint16_t* d_A, int32_t lda,

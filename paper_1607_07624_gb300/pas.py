@@ -91,6 +91,7 @@ _SIGS = {
     "pas_dm_create": (C.c_int, [vp, vp, i32, i32, i32, f64, C.c_int, P(vp)]),
     "pas_dm_update": (C.c_int, [vp, vp, vp, vp, vp]),
     "pas_dm_residual": (C.c_int, [vp, vp, vp, vp]),
+    "pas_dm_project": (C.c_int, [vp, vp, vp]),
     "pas_dm_destroy": (None, [vp]),
     "pas_loop_create": (C.c_int, [vp, vp, vp, vp, vp, vp, i32, i32, P(vp)]),
     "pas_loop_step": (C.c_int, [vp, i32, P(pas_loop_stats)]),
@@ -326,6 +327,10 @@ def pas_dm_update(dm, ctx, d_dmodes, d_gain, d_cmd, d_opd_dm):
 
 def pas_dm_residual(dm, ctx, d_opd_atm, d_cmd, d_opd_res):
     _check(_lib.pas_dm_residual(dm, _ptr(d_opd_atm), _ptr(d_cmd), _ptr(d_opd_res)), ctx)
+
+
+def pas_dm_project(dm, ctx, d_opd, d_coeffs):
+    _check(_lib.pas_dm_project(dm, _ptr(d_opd), _ptr(d_coeffs)), ctx)
 
 
 def pas_dm_destroy(dm):
