@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--recon", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-reconstructor measurements")
+    ap.add_argument("--soak", type=float, default=1.5, help="seconds of untimed steps before timing")
+    ap.add_argument("--tuning", default=None,
+                    help="pyramid launch geometry rows_per_cta,row_chunks,col_groups (default: autotuned)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-budget-s", type=float, default=20.0)
     return ap.parse_args()
@@ -179,9 +182,11 @@ def bench_mlp(sysg, peaks, timed, n_train=50, batch=1024):
     pas.pas_mlp_train(mlp.h, ctx, S, Y, n_data, batch, idx, lr, 5, loss)  # captures the step graph
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("train")
     e0.record()
     pas.pas_mlp_train(mlp.h, ctx, S, Y, n_data, batch, idx, lr, n_train, loss)
     e1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     pas.pas_mlp_check(mlp.h, ctx)
     ms = e0.elapsed_time(e1) / n_train
@@ -193,6 +198,21 @@ def bench_mlp(sysg, peaks, timed, n_train=50, batch=1024):
              "flops_per_step": flops, "tflops": flops / (ms * 1e-3) / 1e12,
              "frac_of_bf16_sustained": flops / (ms * 1e-3) / 1e12 / bf16_sus,
              "note": "whole Adam step (GEMMs + input, loss, bias-gradient and Adam kernels), one graph replay"}
+    # the same step at batch 4096 (four times the GEMM work per step)
+    mlp4 = MLPReconstructor(ctx, sizes, max_batch=4 * batch, seed=7)
+    n4 = max(1, n_train // 4)
+    idx4 = torch.randint(0, n_data, (n4 * 4 * batch,), device="cuda", generator=gen, dtype=torch.int32)
+    pas.pas_mlp_train(mlp4.h, ctx, S, Y, n_data, 4 * batch, idx4, lr, 2, loss)
+    torch.cuda.synchronize()
+    e0.record()
+    pas.pas_mlp_train(mlp4.h, ctx, S, Y, n_data, 4 * batch, idx4, lr, n4, loss)
+    e1.record()
+    torch.cuda.synchronize()
+    pas.pas_mlp_check(mlp4.h, ctx)
+    mlp4.close()
+    ms4 = e0.elapsed_time(e1) / n4
+    train["batch_4096"] = {"ms_per_step": ms4, "samples_per_s": 4 * batch / (ms4 * 1e-3),
+                           "tflops": 4 * flops / (ms4 * 1e-3) / 1e12}
     del S, Y
     # standalone GEMM C = A B^T, 8192^3, operands 2 x 128 MiB (larger than L2), back to back
     n = 8192
@@ -204,10 +224,12 @@ def bench_mlp(sysg, peaks, timed, n_train=50, batch=1024):
         pas.pas_gemm_bf16(ctx, n, n, n, A, n, B, n, C, n, err)
     torch.cuda.synchronize()
     reps = 10
+    torch.cuda.nvtx.range_push("gemm")
     e0.record()
     for _ in range(reps):
         pas.pas_gemm_bf16(ctx, n, n, n, A, n, B, n, C, n, err)
     e1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ours = 2.0 * n ** 3 / (e0.elapsed_time(e1) / reps * 1e-3) / 1e12
     for _ in range(3):
@@ -231,7 +253,9 @@ def bench_mlp(sysg, peaks, timed, n_train=50, batch=1024):
     sysg.set_state(0, np.zeros((sysg.delay, sysg.n_modes), dtype=np.float32))
     sysg.step(20)
     n_loop = 200
+    torch.cuda.nvtx.range_push("timed_network")
     ms_loop = timed(lambda: sysg.step(1), n_loop)
+    torch.cuda.nvtx.range_pop()
     chain = pas.pas_loop_profile(sysg.loop, ctx, 20).get("recon_kernel")
     pas.pas_loop_set_mlp(sysg.loop, ctx, None)
     mlp.close()
@@ -281,7 +305,9 @@ def main():
     cfg_r = with_(cfg, seed=cfg.seed + 1000 * rank)
     prec = pas.PAS_BF16 if args.recon == "bf16" else pas.PAS_FP32
     t_setup = time.perf_counter()
-    sysg = SCAOSystem(cfg_r, recon_precision=prec, wfe_history=max(4096, args.steps + args.warmup + 64))
+    tuning = tuple(int(v) for v in args.tuning.split(",")) if args.tuning else True
+    sysg = SCAOSystem(cfg_r, recon_precision=prec, wfe_history=max(4096, args.steps + args.warmup + 64),
+                      autotune=tuning)
     t_setup = time.perf_counter() - t_setup
     stream = torch.cuda.current_stream()
     # L2 flush between timed steps: write 256 MiB (evicts everything), then read
@@ -311,7 +337,7 @@ def main():
     # warm-up (also captures the graph) and a short soak for steady clocks; the
     # loop state is then reset so that the timed steps start a fresh simulation
     sysg.step(max(3, args.warmup))
-    t_end = time.perf_counter() + 1.5
+    t_end = time.perf_counter() + args.soak
     while time.perf_counter() < t_end:
         sysg.step(50)
     barrier()
@@ -330,7 +356,9 @@ def main():
 
     barrier()
     t_wall = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")
     ms_total = timed(lambda: sysg.step(1), args.steps)
+    torch.cuda.nvtx.range_pop()
     barrier()
     t_wall = time.perf_counter() - t_wall
     if dist is not None:

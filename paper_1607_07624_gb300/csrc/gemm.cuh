@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 
 #include "internal.h"
+#include "pdl.cuh"
 #include "tc.cuh"
 
 namespace pas {
@@ -65,6 +66,10 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
+  // launched programmatically after the producer of A, B or the epilogue inputs:
+  // the set-up above overlaps its tail; nothing it wrote is touched before this
+  pdl_trigger();
+  pdl_wait();
 
   // last round issued per slot (for the drain after a timeout); producer only
   int last_round[STAGES];
@@ -159,26 +164,27 @@ int gemm_pick_bn(int M, int N, int sms);
 bool gemm_prepare(GemmOp* op, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                   int sms);
 
+// pdl: launch with programmatic stream serialization (the kernel waits for its
+// predecessor after its set-up).
 template <int BN, int STAGES, class Epi>
-cudaError_t gemm_launch_bn(const GemmOp& op, const Epi& epi, cudaStream_t st, unsigned* err) {
+cudaError_t gemm_launch_bn(const GemmOp& op, const Epi& epi, cudaStream_t st, unsigned* err, bool pdl) {
   using C = GemmCfg<BN, STAGES>;
   auto kern = gemm_bf16_tc_kernel<BN, STAGES, Epi>;
   cudaError_t e = raise_dyn_smem((const void*)kern, C::SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid((op.N + BN - 1) / BN, (op.M + 127) / 128);
-  kern<<<grid, 128, C::SMEM, st>>>(op.a, op.b, op.M, op.N, op.K, epi, err);
-  return cudaGetLastError();
+  return launch_k(kern, grid, dim3(128), C::SMEM, st, pdl, op.a, op.b, op.M, op.N, op.K, epi, err);
 }
 
 template <class Epi>
-cudaError_t gemm_launch(const GemmOp& op, const Epi& epi, cudaStream_t st, unsigned* err) {
+cudaError_t gemm_launch(const GemmOp& op, const Epi& epi, cudaStream_t st, unsigned* err, bool pdl = false) {
   switch (op.bn) {
     case 64:
-      return gemm_launch_bn<64, 6>(op, epi, st, err);
+      return gemm_launch_bn<64, 6>(op, epi, st, err, pdl);
     case 256:
-      return gemm_launch_bn<256, 4>(op, epi, st, err);
+      return gemm_launch_bn<256, 4>(op, epi, st, err, pdl);
     default:
-      return gemm_launch_bn<128, 5>(op, epi, st, err);
+      return gemm_launch_bn<128, 5>(op, epi, st, err, pdl);
   }
 }
 

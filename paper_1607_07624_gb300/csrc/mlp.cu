@@ -204,6 +204,8 @@ __global__ void mlp_input_kernel(const float* S, int n_data, const int* idx, con
                                  const float* mean, const float* istd, __nv_bfloat16* X, int ldx,
                                  __nv_bfloat16* Xt, int ldt, unsigned* err) {
   __shared__ float tile[32][33];
+  pdl_trigger();
+  pdl_wait();
   const int i0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
   const int* id = idx ? idx + (size_t)(*iter) * B : nullptr;
   const int tx = threadIdx.x;
@@ -236,6 +238,8 @@ __global__ void mlp_loss_kernel(const float* out, int ldo, const float* Y, int n
   __shared__ float tile[32][33];
   __shared__ float red[8];
   __shared__ bool is_last;
+  pdl_trigger();
+  pdl_wait();
   const int o0 = blockIdx.x * 32, b0 = blockIdx.y * 32, tx = threadIdx.x;
   const int* id = idx ? idx + (size_t)(*iter) * B : nullptr;
   const float gs = 2.0f / ((float)B * (float)n_out);
@@ -270,13 +274,21 @@ __global__ void mlp_loss_kernel(const float* out, int ldo, const float* Y, int n
     __threadfence();
     is_last = atomicAdd(done, 1u) == (unsigned)nblk - 1;
   }
-  __syncthreads();
-  if (is_last && threadIdx.y == 0 && tx == 0) {
+  __syncthreads();  // also orders the reads of red above before its reuse below
+  if (is_last) {  // fixed-order reduction of the block partials by the whole last block
     __threadfence();
-    double t = 0.0;
-    for (int i = 0; i < nblk; ++i) t += (double)part[i];
-    loss[*iter] = (float)(t / ((double)B * (double)n_out));
-    *done = 0u;
+    const int tid = threadIdx.y * 32 + tx;
+    float t = 0.f;
+    for (int i = tid; i < nblk; i += 256) t += part[i];
+    for (int s = 16; s > 0; s >>= 1) t += __shfl_down_sync(0xffffffffu, t, s);
+    if ((tx & 31) == 0) red[tid >> 5] = t;
+    __syncthreads();
+    if (tid == 0) {
+      float tot = 0.f;
+      for (int i = 0; i < 8; ++i) tot += red[i];
+      loss[*iter] = tot / ((float)B * (float)n_out);
+      *done = 0u;
+    }
   }
 }
 
@@ -290,6 +302,8 @@ struct BiasGradArgs {
 
 // db_l[o] = sum_b dZ_l[b][o]: one warp per bias element, reading a row of dZ^T.
 __global__ void mlp_bias_grad_kernel(BiasGradArgs a) {
+  pdl_trigger();
+  pdl_wait();
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (w >= a.start[a.L]) return;
   int l = 0;
@@ -340,6 +354,8 @@ __device__ __forceinline__ float adam_one(const AdamArgs& a, size_t k, float lr,
 __global__ void __launch_bounds__(256) mlp_adam_kernel(AdamArgs a) {
   __shared__ float tile[32][33];
   __shared__ bool is_last;
+  pdl_trigger();
+  pdl_wait();
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   float lr = 0.f, c1 = 1.f, c2 = 1.f;
   if (a.update) {
@@ -543,9 +559,9 @@ static pas_status mlp_forward_enqueue(pas_mlp_t m, int B, const float* S, int n_
                                       const int* iter, cudaStream_t st) {
   const int n_in = m->sz[0];
   dim3 tb(32, 8);
-  mlp_input_kernel<<<dim3((n_in + 31) / 32, (B + 31) / 32), tb, 0, st>>>(
-      S, n_data, idx, iter, B, n_in, m->d_mean, m->d_istd, m->d_X, m->ld[0], m->d_Xt, m->ldb, m->d_err);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_k(mlp_input_kernel, dim3((n_in + 31) / 32, (B + 31) / 32), tb, 0, st, false, S, n_data, idx,
+                           iter, B, n_in, (const float*)m->d_mean, (const float*)m->d_istd, m->d_X, m->ld[0], m->d_Xt,
+                           m->ldb, m->d_err);
   if (e != cudaSuccess) return gemm_err(m, "MLP input", e);
   for (int l = 0; l < m->L; ++l) {
     const __nv_bfloat16* A = l == 0 ? m->d_X : m->d_H[l - 1];
@@ -554,10 +570,10 @@ static pas_status mlp_forward_enqueue(pas_mlp_t m, int B, const float* S, int n_
       return set_error(m->ctx, PAS_ECUDA, "MLP forward layer %d: tensor map rejected", l);
     if (l < m->L - 1) {
       EpiHidden ep{m->d_p + m->offb[l], m->d_Z[l], m->d_H[l], m->d_Ht[l], m->ld[l + 1], m->ldb, m->sz[l + 1]};
-      e = gemm_launch(op, ep, st, m->d_err);
+      e = gemm_launch(op, ep, st, m->d_err, true);
     } else {
       EpiOut ep{m->d_p + m->offb[l], m->d_out, m->ld[l + 1], m->sz[l + 1]};
-      e = gemm_launch(op, ep, st, m->d_err);
+      e = gemm_launch(op, ep, st, m->d_err, true);
     }
     if (e != cudaSuccess) return gemm_err(m, "MLP forward GEMM", e);
   }
@@ -570,9 +586,9 @@ static pas_status mlp_backward_enqueue(pas_mlp_t m, int B, const float* Y, int n
   const int L = m->L, n_out = m->sz[L];
   dim3 tb(32, 8);
   dim3 lg((n_out + 31) / 32, (B + 31) / 32);
-  mlp_loss_kernel<<<lg, tb, 0, st>>>(m->d_out, m->ld[L], Y, n_data, idx, iter, B, n_out, m->d_dZ[L - 1],
-                                     m->ld[L], m->d_dZt[L - 1], m->ldb, m->d_loss_part, m->d_done, loss);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_k(mlp_loss_kernel, lg, tb, 0, st, true, (const float*)m->d_out, m->ld[L], Y, n_data, idx,
+                           iter, B, n_out, m->d_dZ[L - 1], m->ld[L], m->d_dZt[L - 1], m->ldb, m->d_loss_part,
+                           m->d_done, loss);
   if (e != cudaSuccess) return gemm_err(m, "MLP loss", e);
   for (int l = L - 1; l >= 0; --l) {
     // weight gradient dW_l = dZ_l^T H_{l-1}: M = out, N = in, K = B
@@ -581,7 +597,7 @@ static pas_status mlp_backward_enqueue(pas_mlp_t m, int B, const float* Y, int n
     if (!gemm_prepare(&op, m->d_dZt[l], m->ldb, Ht, m->ldb, m->sz[l + 1], m->sz[l], B, m->ctx->sm_count))
       return set_error(m->ctx, PAS_ECUDA, "MLP weight-gradient layer %d: tensor map rejected", l);
     EpiF32 eg{m->d_g + m->offW[l], m->sz[l], m->sz[l]};
-    e = gemm_launch(op, eg, st, m->d_err);
+    e = gemm_launch(op, eg, st, m->d_err, true);
     if (e != cudaSuccess) return gemm_err(m, "MLP weight-gradient GEMM", e);
     if (l == 0) break;
     // input gradient dH_{l-1} = dZ_l W_l, times gelu'(Z_{l-1}): M = B, N = in, K = out
@@ -590,7 +606,7 @@ static pas_status mlp_backward_enqueue(pas_mlp_t m, int B, const float* Y, int n
                       m->ctx->sm_count))
       return set_error(m->ctx, PAS_ECUDA, "MLP input-gradient layer %d: tensor map rejected", l);
     EpiBack eb{m->d_Z[l - 1], m->d_dZ[l - 1], m->d_dZt[l - 1], m->ld[l], m->ldb, m->sz[l]};
-    e = gemm_launch(ob, eb, st, m->d_err);
+    e = gemm_launch(ob, eb, st, m->d_err, true);
     if (e != cudaSuccess) return gemm_err(m, "MLP input-gradient GEMM", e);
   }
   BiasGradArgs ba = {};
@@ -605,8 +621,7 @@ static pas_status mlp_backward_enqueue(pas_mlp_t m, int B, const float* Y, int n
     ba.start[l + 1] = ba.start[l] + m->sz[l + 1];
   }
   const int warps = ba.start[L];
-  mlp_bias_grad_kernel<<<(warps * 32 + 255) / 256, 256, 0, st>>>(ba);
-  e = cudaGetLastError();
+  e = launch_k(mlp_bias_grad_kernel, dim3((warps * 32 + 255) / 256), dim3(256), 0, st, true, ba);
   if (e != cudaSuccess) return gemm_err(m, "MLP bias gradient", e);
   return PAS_OK;
 }
@@ -641,10 +656,9 @@ static AdamArgs adam_args(pas_mlp_t m, int update) {
   return a;
 }
 
-static pas_status adam_launch(pas_mlp_t m, const AdamArgs& a, cudaStream_t st) {
+static pas_status adam_launch(pas_mlp_t m, const AdamArgs& a, cudaStream_t st, bool pdl = false) {
   const int blocks = a.tile_start[a.L] + (a.update ? (a.bias_start[a.L] + 255) / 256 : 0);
-  mlp_adam_kernel<<<blocks, dim3(32, 8), 0, st>>>(a);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_k(mlp_adam_kernel, dim3(blocks), dim3(32, 8), 0, st, pdl, a);
   if (e != cudaSuccess) return gemm_err(m, "MLP Adam", e);
   return PAS_OK;
 }
@@ -658,7 +672,7 @@ static pas_status mlp_train_enqueue(pas_mlp_t m, int B, const float* S, const fl
   a.lr = lr;
   a.iter = m->d_iter;
   a.iter_inc = m->d_iter;
-  return adam_launch(m, a, st);
+  return adam_launch(m, a, st, true);
 }
 
 // ---------------------------------------------------------------- training pairs

@@ -31,7 +31,9 @@ class SCAOSystem:
 
     screens: float32 (L, S, S) OPD [nm] (host numpy or None: generated from the
     configuration's seeds); basis: float (n_pix, n_modes) (None: Zernike);
-    R: reconstruction matrix (None: calibrated by push-pull on the GPU)."""
+    R: reconstruction matrix (None: calibrated by push-pull on the GPU);
+    autotune: True (time the pyramid launch geometries on the GPU), False (library
+    default) or (rows_per_cta, row_chunks, col_groups) to set one."""
 
     def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32,
                  noise=None, delay=None, wfe_history=4096, stream=None, build_loop=True,
@@ -79,7 +81,10 @@ class SCAOSystem:
         self.d_gain = torch.full((self.n_modes,), cfg.gain, **f32)
         # launch geometry of the pyramid kernels, measured on the open-loop OPD
         self.tuning = P.pas_pyr_get_tuning(self.pyr, self.ctx)
-        if autotune:
+        if isinstance(autotune, (tuple, list)):
+            P.pas_pyr_set_tuning(self.pyr, self.ctx, *autotune)
+            self.tuning = P.pas_pyr_get_tuning(self.pyr, self.ctx)
+        elif autotune:
             P.pas_atmo_advance(self.atmo, self.ctx, 0, self.d_opd)
             self.tuning = P.pas_pyr_autotune(self.pyr, self.ctx, self.d_opd, 5)
             self.d_opd.zero_()
