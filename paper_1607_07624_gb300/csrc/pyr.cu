@@ -65,7 +65,7 @@ struct ColArgs {
   const float2* H;
   const float2* tw;
   const float2* mask;
-  const float* alpha;   // [K] cycles per pixel (tilt_x + input ramp)
+  const float2* tilt;   // [K][Np] (-1)^i exp(2 pi i (i - ci) alpha_k): tilt_x + input ramp
   const int* kmap;      // [K] -> rows-pass index
   float* part;          // [G][nd][nd]
   int Np, off, K, kper, nd, b;
@@ -74,8 +74,14 @@ struct ColArgs {
 
 
 
+// Register caps per transform length: 72 for N = 480 compiles without spills and
+// lets 3 columns-pass CTAs of 8 warps (and 7 rows-pass CTAs of 4 warps) share an SM
+// instead of 2 (4); other lengths keep the compiler's choice.
+constexpr int rows_max_regs(int N) { return N == 480 ? 72 : 128; }
+constexpr int cols_max_regs(int N) { return N == 480 ? 72 : 128; }
+
 template <int N>
-__global__ void __launch_bounds__(MAX_ROWS_PER_CTA * 32)
+__global__ void __maxnreg__(rows_max_regs(N))
 pyr_rows_kernel(RowArgs a) {
   constexpr int TWN = tw_size(N), BL = buf_len(N), PITCH = BL | 1;
   extern __shared__ float2 smem[];
@@ -235,15 +241,29 @@ __global__ void __launch_bounds__(256) slopes_kernel(FrameArgs f, int nd) {
   }
 }
 
+// Column tilt phasors of the modulation points, [K][Np]: (-1)^i e^{2 pi i (i - ci) alpha_k}
+// (tilt along axis 0 with the input centring ramp). Constant for a geometry: built
+// once at creation, in the same float arithmetic the columns pass used inline.
+__global__ void tilt_table_kernel(const float* alpha, int K, int Np, float2* tilt) {
+  const int k = blockIdx.x;
+  if (k >= K) return;
+  const float ci = 0.5f * (float)(Np - 1);
+  const float al = alpha[k];
+  for (int i = threadIdx.x; i < Np; i += blockDim.x) {
+    float sn, cs;
+    sincospif(2.0f * ((float)i - ci) * al, &sn, &cs);
+    tilt[(size_t)k * Np + i] = (i & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
+  }
+}
+
 template <int N>
-__global__ void __launch_bounds__(512)
+__global__ void __maxnreg__(cols_max_regs(N))
 pyr_cols_kernel(ColArgs a) {
   constexpr int TWN = tw_size(N), BL = buf_len(N), PITCH = BL | 1;
   extern __shared__ float2 smem[];
   float2* tw_s = smem;
   float2* mk_s = smem + TWN;
-  float2* tilt_s = mk_s + BL;                     // [Np]: tilt of the current k
-  float2* bufs = tilt_s + a.Np;                   // [b][PITCH]
+  float2* bufs = mk_s + BL;                       // [b][PITCH]
   const int Np = a.Np;
   const int q = blockIdx.x;                       // detector column
   const int g = blockIdx.y;                       // modulation group
@@ -253,7 +273,7 @@ pyr_cols_kernel(ColArgs a) {
   for (int t = threadIdx.x; t < TWN; t += blockDim.x) tw_s[t] = a.tw[t];
   for (int t = threadIdx.x; t < BL; t += blockDim.x) mk_s[t] = a.mask[t];
   pdl_wait();  // H, the partial frames and the counters belong to the predecessors
-  const float ci = 0.5f * (float)(Np - 1);
+  __syncthreads();  // twiddles and mask staged
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int y = q * a.b + warp;
   float2* buf = bufs + warp * PITCH;
@@ -262,19 +282,13 @@ pyr_cols_kernel(ColArgs a) {
 #pragma unroll
   for (int t = 0; t < OS::PER_LANE; ++t) acc[t] = 0.f;
   for (int kk = 0; kk < kc; ++kk) {
-    __syncthreads();                              // previous k's tilt no longer read
-    const float alpha = a.alpha[k0 + kk];
-    for (int i = threadIdx.x; i < Np; i += blockDim.x) {
-      float sn, cs;
-      sincospif(2.0f * ((float)i - ci) * alpha, &sn, &cs);
-      tilt_s[i] = (i & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
-    }
-    __syncthreads();
+    // the tilt row of this k is shared by the CTA's warps through L1; no barrier
     const float2* Hcol = a.H + ((size_t)a.kmap[k0 + kk] * N + y) * Np;
+    const float2* tk = a.tilt + (size_t)(k0 + kk) * Np;
     const int off = a.off;
     auto load = [&](int, int, int x) -> float2 {
       const int i = x - off;
-      if ((unsigned)i < (unsigned)Np) return cmul(__ldg(Hcol + i), tilt_s[i]);
+      if ((unsigned)i < (unsigned)Np) return cmul(__ldg(Hcol + i), __ldg(tk + i));
       return make_float2(0.f, 0.f);
     };
     auto store = [&](int jb, int k, int, float2 v) {
@@ -386,6 +400,7 @@ struct pas_pyr_s {
   float2* d_tw = nullptr;
   float2* d_mask = nullptr;
   float* d_alpha = nullptr;
+  float2* d_tilt = nullptr;
   float* d_beta = nullptr;
   int* d_kmap = nullptr;
   float2* d_H = nullptr;
@@ -437,13 +452,13 @@ static void launch_rows(pas_pyr_t y, const float* d_opd, cudaStream_t st, bool p
 }
 
 static void launch_cols(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream_t st,
-                        const LoopExtra* fa_extra, bool increment_ctr, bool pdl = false) {
+                        const LoopExtra* fa_extra, bool increment_ctr) {
   const pas_pyr_params& p = y->p;
   ColArgs ca;
   ca.H = y->d_H;
   ca.tw = y->d_tw;
   ca.mask = y->d_mask;
-  ca.alpha = y->d_alpha;
+  ca.tilt = y->d_tilt;
   ca.kmap = y->d_kmap;
   ca.part = y->d_part;
   ca.Np = p.Np;
@@ -474,7 +489,11 @@ static void launch_cols(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream
   fa.local_norm = p.local_norm;
   fa.wfe = fa_extra ? *fa_extra : LoopExtra();
   dim3 gc(y->nd, y->G);
-  launch_k(y->kern.cols, gc, dim3(y->b * 32), y->smem_cols, st, pdl, ca);
+  // the columns pass starts after the rows pass has finished: launched early, its
+  // CTAs (up to 3 per SM) wait on the SMs while the rows pass runs and slow it
+  // (measured on the 480 grid: 84 us per loop step this way, 89-99 us with the
+  // early launch)
+  launch_k(y->kern.cols, gc, dim3(y->b * 32), y->smem_cols, st, false, ca);
 }
 
 static void launch_slopes(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream_t st,
@@ -499,13 +518,13 @@ static void launch_slopes(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStre
 pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes,
                       cudaStream_t st, const LoopExtra* fa_extra, bool increment_ctr, cudaEvent_t* ev,
                       bool pdl_first) {
-  // the columns and slopes kernels follow the rows pass programmatically unless
-  // events are recorded between the kernels
+  // the slopes kernel follows the columns pass programmatically (and the rows pass
+  // its predecessor when pdl_first) unless events are recorded between the kernels
   const bool pdl = ev == nullptr;
   if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
   launch_rows(y, d_opd, st, pdl && pdl_first);
   if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
-  launch_cols(y, d_frame, d_slopes, st, fa_extra, increment_ctr, pdl);
+  launch_cols(y, d_frame, d_slopes, st, fa_extra, increment_ctr);
   if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
   launch_slopes(y, d_frame, d_slopes, st, fa_extra, increment_ctr, pdl);
   return check_launch(y->ctx, "pas_pyr_measure launch");
@@ -531,6 +550,7 @@ void pas_pyr_destroy(pas_pyr_t y) {
   pas::dev_free(y->d_tw);
   pas::dev_free(y->d_mask);
   pas::dev_free(y->d_alpha);
+  pas::dev_free(y->d_tilt);
   pas::dev_free(y->d_beta);
   pas::dev_free(y->d_kmap);
   pas::dev_free(y->d_H);
@@ -655,7 +675,7 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   y->n_schunks = (y->n_s + 3) / 4;
   y->s_chunk = (y->n_s + y->n_schunks - 1) / y->n_schunks;
   y->smem_rows = pas::rows_smem(y, pas::MAX_ROWS_PER_CTA, y->n_s);  // largest candidate
-  y->smem_cols = sizeof(float2) * ((size_t)kern.tw_n + kern.buf_n + (size_t)p.Np + (size_t)b * kern.pitch);
+  y->smem_cols = sizeof(float2) * ((size_t)kern.tw_n + kern.buf_n + (size_t)b * kern.pitch);
 
   pas_status st = PAS_OK;
   auto A = [&](void** ptr, size_t bytes) {
@@ -666,6 +686,7 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   A((void**)&y->d_tw, sizeof(float2) * kern.tw_n);
   A((void**)&y->d_mask, sizeof(float2) * kern.buf_n);
   A((void**)&y->d_alpha, sizeof(float) * p.K);
+  A((void**)&y->d_tilt, sizeof(float2) * (size_t)p.K * p.Np);
   A((void**)&y->d_beta, sizeof(float) * y->n_s);
   A((void**)&y->d_kmap, sizeof(int) * p.K);
   A((void**)&y->d_H, sizeof(float2) * (size_t)y->n_s * p.N * p.Np);
@@ -687,6 +708,11 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   C(y->d_tw, tw.data(), sizeof(float2) * kern.tw_n);
   C(y->d_mask, mk.data(), sizeof(float2) * kern.buf_n);
   C(y->d_alpha, alpha.data(), sizeof(float) * p.K);
+  if (e == cudaSuccess) {
+    pas::tilt_table_kernel<<<p.K, 256>>>(y->d_alpha, p.K, p.Np, y->d_tilt);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
   C(y->d_beta, beta.data(), sizeof(float) * y->n_s);
   C(y->d_kmap, kmap.data(), sizeof(int) * p.K);
   {
@@ -1044,7 +1070,7 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
   y.rows = 4;
   y.n_schunks = (n_s + 3) / 4;
   y.s_chunk = (n_s + y.n_schunks - 1) / y.n_schunks;
-  y.smem_cols = sizeof(float2) * ((size_t)kern.tw_n + kern.buf_n + (size_t)p.Np + (size_t)b * kern.pitch);
+  y.smem_cols = sizeof(float2) * ((size_t)kern.tw_n + kern.buf_n + (size_t)b * kern.pitch);
   {
     const int slots = 2 * std::max(1, sms);
     int best_G = 1;
@@ -1065,6 +1091,7 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
   y.d_tw = reinterpret_cast<float2*>(carve(sizeof(float2) * kern.tw_n));
   y.d_mask = reinterpret_cast<float2*>(carve(sizeof(float2) * kern.buf_n));
   y.d_alpha = reinterpret_cast<float*>(carve(sizeof(float) * p.K));
+  y.d_tilt = reinterpret_cast<float2*>(carve(sizeof(float2) * (size_t)p.K * p.Np));
   y.d_beta = reinterpret_cast<float*>(carve(sizeof(float) * n_s));
   y.d_kmap = reinterpret_cast<int*>(carve(sizeof(int) * p.K));
   y.d_valid = reinterpret_cast<int32_t*>(carve(sizeof(int32_t) * std::max(nv, 1)));
@@ -1090,6 +1117,10 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
   H2D(y.d_tw, tw, sizeof(float2) * kern.tw_n);
   H2D(y.d_mask, mk, sizeof(float2) * kern.buf_n);
   H2D(y.d_alpha, alpha, sizeof(float) * p.K);
+  if (e == cudaSuccess) {
+    tilt_table_kernel<<<p.K, 256, 0, st>>>(y.d_alpha, p.K, p.Np, y.d_tilt);
+    e = cudaGetLastError();
+  }
   H2D(y.d_beta, beta, sizeof(float) * n_s);
   H2D(y.d_kmap, kmap, sizeof(int) * p.K);
   H2D(y.d_valid, valid, sizeof(int32_t) * std::max(nv, 1));
