@@ -127,84 +127,78 @@ __global__ void atmo_kernel(AtmoArgs a, const long long* d_step, long long h_ste
   }
 }
 
+// Residual over the pupil pixel list: out[pix] = atm - dm_sign * (M c), atm read
+// from opd_atm (or zero). CTA: one 64-pixel tile, whose basis block [n_m][64] is
+// one contiguous stretch of memory. Thread t owns the 4 pixels 4 (t % 16) .. +3 and
+// the modes m = t / 16 + 16 j: it streams those 16-byte rows straight from global
+// memory (a warp reads two whole 256-byte mode rows per load) with RES_U loads in
+// flight, and the 16 partial sums per pixel meet once in shared memory at the end.
+// The basis is constant, so the first loads are issued before the programmatic
+// wait and overlap the predecessor kernel.
 constexpr int RES_TILE = 64;        // pixels per CTA (one contiguous basis block)
 constexpr int RES_THREADS = 256;
-constexpr int RES_CHUNK = 32;       // modes per pipeline stage: 32 x 64 x 4 B = 8 KB
-constexpr int RES_STAGES = 4;
-constexpr int RES_GROUPS = RES_THREADS / RES_TILE;
+constexpr int RES_COLS = RES_TILE / 4;             // float4 columns of a mode row
+constexpr int RES_ROWS = RES_THREADS / RES_COLS;   // modes read per CTA-wide load
+constexpr int RES_U = 5;                           // loads in flight per thread
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+__device__ __forceinline__ float4 ld_stream4(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Residual over the pupil pixel list: out[pix] = atm - dm_sign * (M c), atm read
-// from opd_atm (or zero). CTA: one 64-pixel tile whose basis block [n_m][64] is
-// streamed through shared memory by a RES_STAGES-deep cp.async pipeline (16-byte
-// copies, L1 bypassed); thread t accumulates pixel t % 64 over the modes
-// m = t / 64 mod 4 of each stage. The basis is constant, so the first stages are
-// issued before the programmatic wait and overlap the predecessor kernel.
 __global__ void __launch_bounds__(RES_THREADS) residual_kernel(ResArgs a) {
-  extern __shared__ float4 res_smem[];
-  float4* stage = res_smem;                                            // [S][CHUNK*TILE/4]
-  float* c_s = reinterpret_cast<float*>(res_smem + RES_STAGES * RES_CHUNK * RES_TILE / 4);  // [n_m]
-  __shared__ float red[RES_GROUPS][RES_TILE];
+  extern __shared__ float c_s[];                       // [n_m]
+  __shared__ float4 red[RES_ROWS][RES_COLS];
   __shared__ double wred[2][RES_THREADS / 32];
   const int tid = threadIdx.x;
   const int n_m = a.MT ? a.n_m : 0;
-  const int nchunks = (n_m + RES_CHUNK - 1) / RES_CHUNK;
-  const float4* blk = reinterpret_cast<const float4*>(a.MT + (size_t)blockIdx.x * n_m * RES_TILE);
-  constexpr int V4 = RES_CHUNK * RES_TILE / 4;   // float4 per full stage (512)
-  auto issue = [&](int c) {
-    if (c < nchunks) {
-      const int rows = min(RES_CHUNK, n_m - c * RES_CHUNK);
-      const int nv4 = rows * RES_TILE / 4;
-      float4* dst = stage + (c % RES_STAGES) * V4;
-      const float4* src = blk + (size_t)c * V4;
-      for (int v = tid; v < nv4; v += RES_THREADS) cp_async16(dst + v, src + v);
-    }
-    cp_async_commit();
-  };
-  pdl_trigger();
+  const int col = tid % RES_COLS, row = tid / RES_COLS;
+  const float4* blk = reinterpret_cast<const float4*>(a.MT + (size_t)blockIdx.x * n_m * RES_TILE) + col;
+  float4 v[RES_U];
 #pragma unroll
-  for (int c = 0; c < RES_STAGES - 1; ++c) issue(c);
+  for (int u = 0; u < RES_U; ++u) {
+    const int m = row + RES_ROWS * u;
+    v[u] = m < n_m ? ld_stream4(blk + (size_t)m * RES_COLS) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  pdl_trigger();
   pdl_wait();
   const long long step = a.d_step ? *a.d_step : a.h_step;
   const float* cmd = a.cmd;
   if (a.cmd_ring) cmd = a.cmd_ring + (size_t)(step % a.delay) * a.n_m;
   for (int m = tid; m < n_m; m += RES_THREADS) c_s[m] = cmd[m];
-  const int base = blockIdx.x * RES_TILE;
-  const int px = tid % RES_TILE, grp = tid / RES_TILE;
-  const int p = base + px;
-  const bool owner = grp == 0 && p < a.n_pix;
-  int flat = 0;
-  float atm = 0.f;
-  if (owner) {
-    flat = a.pix[p];
-    if (a.opd_atm) atm = a.opd_atm[flat];
-  }
-  float acc = 0.f;
-  for (int c = 0; c < nchunks; ++c) {
-    issue(c + RES_STAGES - 1);
-    cp_async_wait<RES_STAGES - 1>();
-    __syncthreads();
-    const float* sb = reinterpret_cast<const float*>(stage + (c % RES_STAGES) * V4);
-    const int rows = min(RES_CHUNK, n_m - c * RES_CHUNK);
-    const float* cc = c_s + c * RES_CHUNK;
-#pragma unroll 8
-    for (int r = grp; r < rows; r += RES_GROUPS) acc = fmaf(cc[r], sb[r * RES_TILE + px], acc);
-    __syncthreads();
-  }
-  red[grp][px] = acc;
   __syncthreads();
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int mb = row; mb < n_m; mb += RES_ROWS * RES_U) {
+#pragma unroll
+    for (int u = 0; u < RES_U; ++u) {
+      const int m = mb + RES_ROWS * u;
+      if (m < n_m) {
+        const float cm = c_s[m];
+        acc.x = fmaf(cm, v[u].x, acc.x);
+        acc.y = fmaf(cm, v[u].y, acc.y);
+        acc.z = fmaf(cm, v[u].z, acc.z);
+        acc.w = fmaf(cm, v[u].w, acc.w);
+      }
+      const int mn = m + RES_ROWS * RES_U;
+      if (mn < n_m) v[u] = ld_stream4(blk + (size_t)mn * RES_COLS);
+    }
+  }
+  red[row][col] = acc;
+  __syncthreads();
+  const int base = blockIdx.x * RES_TILE;
+  const int px = tid;
+  const int p = base + px;
   double s1 = 0.0, s2 = 0.0;
-  if (owner) {
+  if (px < RES_TILE && p < a.n_pix) {
+    const float* rf = reinterpret_cast<const float*>(&red[0][0]);
     float dm = 0.f;
 #pragma unroll
-    for (int g = 0; g < RES_GROUPS; ++g) dm += red[g][px];
+    for (int r = 0; r < RES_ROWS; ++r) dm += rf[r * RES_TILE + px];
+    const int flat = a.pix[p];
+    const float atm = a.opd_atm ? a.opd_atm[flat] : 0.f;
     const float r = atm - a.dm_sign * dm;
     a.out[flat] = r;
     s1 = r;
@@ -269,7 +263,7 @@ pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, boo
   const int tiles = residual_tiles(a.n_pix);
   if (tiles == 0) return PAS_OK;
   if (a.atmo.L != 0) return set_error(ctx, PAS_EINVAL, "residual kernel: the atmosphere comes from opd_atm");
-  const size_t smem = sizeof(float4) * RES_STAGES * RES_CHUNK * RES_TILE / 4 + sizeof(float) * (size_t)std::max(a.n_m, 1);
+  const size_t smem = sizeof(float) * (size_t)std::max(a.n_m, 1);
   cudaError_t e = raise_dyn_smem((const void*)residual_kernel, smem);
   if (e == cudaSuccess) e = launch_k(residual_kernel, dim3(tiles), dim3(RES_THREADS), smem, st, pdl, a);
   if (e != cudaSuccess) return set_error(ctx, PAS_ECUDA, "residual kernel launch: %s", cudaGetErrorString(e));
