@@ -159,6 +159,26 @@ def algorithmic_work(cfg, n_pix, n_valid, n_modes, n_s_rows, recon_bytes_per_el)
     }
 
 
+def replica_seed(seed: int, rank: int) -> int:
+    """Each replica simulates its own atmosphere (weak scaling, no data exchange)."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's value (the job ends when every replica has finished)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(steps_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job steps/s: the steps of all replicas over the slowest rank's time."""
+    return steps_per_rank * world / (ms_max / 1000.0)
+
+
 def bench_mlp(sysg, peaks, timed, n_train=50, batch=1024):
     """Learned reconstructor on this system's sizes (2 n_valid -> 1024^3 -> n_modes):
     training throughput (Adam steps on a device-resident synthetic set larger than
@@ -302,7 +322,7 @@ def main():
     from paper_1607_07624_gb300.system import SCAOSystem
     from synth.configs import with_
 
-    cfg_r = with_(cfg, seed=cfg.seed + 1000 * rank)
+    cfg_r = with_(cfg, seed=replica_seed(cfg.seed, rank))
     prec = pas.PAS_BF16 if args.recon == "bf16" else pas.PAS_FP32
     t_setup = time.perf_counter()
     tuning = tuple(int(v) for v in args.tuning.split(",")) if args.tuning else True
@@ -361,12 +381,8 @@ def main():
     torch.cuda.nvtx.range_pop()
     barrier()
     t_wall = time.perf_counter() - t_wall
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    steps_total = args.steps * world
-    value = steps_total / (ms_total / 1000.0)
+    ms_total = max_over_ranks(ms_total, dist, "cuda")
+    value = job_throughput(args.steps, world, ms_total)
     ms_per_step = ms_total / args.steps
 
     # PWFS frames/s: pas_pyr_measure alone on a fixed input, the open-loop
