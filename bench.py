@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--recon", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-reconstructor measurements")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the BF16 loop and the other workloads (64 px, ELT-scale)")
     ap.add_argument("--soak", type=float, default=1.5, help="seconds of untimed steps before timing")
     ap.add_argument("--tuning", default=None,
                     help="pyramid launch geometry rows_per_cta,row_chunks,col_groups (default: autotuned)")
@@ -177,6 +179,96 @@ def max_over_ranks(x: float, dist, device) -> float:
 def job_throughput(steps_per_rank: int, world: int, ms_max: float) -> float:
     """Whole-job steps/s: the steps of all replicas over the slowest rank's time."""
     return steps_per_rank * world / (ms_max / 1000.0)
+
+
+def timed_loop(sysg, timed, n_steps, warmup=20):
+    """Reset the loop, warm it, reset again, time n_steps single-step graph launches
+    (L2 flushed between steps by `timed`); returns (steps/s, per-step WFE)."""
+    import numpy as np
+    zeros = np.zeros((sysg.delay, sysg.n_modes), dtype=np.float32)
+    sysg.set_state(0, zeros)
+    sysg.step(warmup)
+    sysg.set_state(0, zeros)
+    ms = timed(lambda: sysg.step(1), n_steps)
+    return n_steps / (ms * 1e-3), sysg.wfe_nm(min(n_steps, sysg.wfe_history))
+
+
+def bench_bf16_loop(cfg_r, timed, n_steps, wfe_fp32):
+    """The same loop (same seeds) with the DM basis and the reconstructor in bfloat16
+    (float32 sums and integrator): steps/s and the residual WFE against the FP32 loop."""
+    import numpy as np
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    sysb = SCAOSystem(cfg_r, recon_precision=pas.PAS_BF16, dm_precision=pas.PAS_BF16,
+                      wfe_history=max(4096, n_steps + 64))
+    try:
+        sps, wfe = timed_loop(sysb, timed, n_steps)
+    finally:
+        sysb.close()
+    n = min(len(wfe), len(wfe_fp32))
+    burn = n // 5
+    d = wfe[burn:n] - wfe_fp32[burn:n]
+    d10 = wfe[:min(10, n)] - wfe_fp32[:min(10, n)]
+    return {"steps_per_s": sps, "dm_basis": "bf16", "reconstructor": "bf16 (per-row scale)",
+            "wfe_diff_nm_rms_first_10_steps": float(np.sqrt(np.mean(d10 * d10))),
+            "wfe_nm_mean": float(np.mean(wfe[burn:n])), "wfe_nm_mean_fp32": float(np.mean(wfe_fp32[burn:n])),
+            "wfe_diff_nm_rms": float(np.sqrt(np.mean(d * d))), "wfe_diff_nm_max": float(np.max(np.abs(d))),
+            "steps_compared": n - burn}
+
+
+def bench_other_workloads(timed, peaks, n_steps=200):
+    """Loop steps/s and PWFS frames/s of the 64 px workload (calibrated as the
+    headline one) and of the ELT-scale workload. The ELT loop uses random screens,
+    a random 4000-mode basis and a random reconstructor of the right shapes: its
+    cost is that of the real loop, its wavefront error is not meaningful."""
+    import numpy as np
+    import torch
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    from synth import get_config
+    out = {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    cfg1 = get_config(1)
+    s1 = SCAOSystem(cfg1, wfe_history=max(4096, n_steps + 64))
+    try:
+        sps, _ = timed_loop(s1, timed, n_steps)
+        opd = torch.zeros(cfg1.Np, cfg1.Np, device="cuda")
+        pas.pas_atmo_advance(s1.atmo, s1.ctx, 0, opd)
+        fr = n_steps / (timed(lambda: s1.measure(opd), n_steps) * 1e-3)
+        out[cfg1.name] = {"loop_steps_per_s": sps, "pwfs_frames_per_s": fr, "tuning": list(s1.tuning)}
+    finally:
+        s1.close()
+    cfg3 = get_config(3)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    pix = pas.pas_pupil_pixels(cfg3.Np, cfg3.obs)
+    valid = pas.pas_valid_subaps(cfg3.Np, cfg3.obs, cfg3.n_sub)
+    screens = (torch.randn(len(cfg3.layers), cfg3.S, cfg3.S, device="cuda", generator=gen) * 300.0).cpu().numpy()
+    basis = torch.randn(pix.size, cfg3.n_modes, device="cuda", generator=gen).cpu().numpy()
+    R = (torch.randn(cfg3.n_modes, 2 * valid.size, device="cuda", generator=gen) * 1e-3).cpu().numpy()
+    s3 = SCAOSystem(cfg3, screens=screens, basis=basis, R=R, recon_precision=pas.PAS_BF16,
+                    wfe_history=max(4096, n_steps + 64))
+    del screens, basis, R
+    try:
+        n3 = max(20, n_steps // 4)
+        sps, _ = timed_loop(s3, timed, n3)
+        opd = torch.zeros(cfg3.Np, cfg3.Np, device="cuda")
+        pas.pas_atmo_advance(s3.atmo, s3.ctx, 0, opd)
+        fr = n3 / (timed(lambda: s3.measure(opd), n3) * 1e-3)
+        prof = {}
+        for _ in range(10):
+            for k, v in pas.pas_loop_profile(s3.loop, s3.ctx, 1).items():
+                prof[k] = prof.get(k, 0.0) + v / 10
+        res_bytes = 4.0 * cfg3.n_modes * pix.size + 12.0 * pix.size
+        res_gbs = res_bytes / (prof["residual_kernel"] * 1e-3) / 1e9
+        out[cfg3.name] = {"loop_steps_per_s": sps, "pwfs_frames_per_s": fr, "tuning": list(s3.tuning),
+                          "kernel_ms": prof,
+                          "residual_roofline": {"bound": "hbm", "achieved": res_gbs, "peak": hbm, "unit": "GB/s",
+                                                "frac": res_gbs / hbm, "bytes_per_launch": res_bytes},
+                          "note": "random screens, basis and reconstructor of the workload's shapes "
+                                  "(timing only); reconstructor bf16 4000 x 14312"}
+    finally:
+        s3.close()
+    return out
 
 
 def bench_mlp(sysg, peaks, timed, n_train=50, batch=1024):
@@ -446,6 +538,17 @@ def main():
     except (OSError, ValueError):
         pass
 
+    extra = {}
+    if not args.no_extra:
+        try:
+            extra["loop_bf16"] = bench_bf16_loop(cfg_r, timed, args.steps, wfe)
+        except Exception as e:
+            extra["loop_bf16"] = {"error": str(e)}
+        try:
+            extra["other_workloads"] = bench_other_workloads(timed, peaks)
+        except Exception as e:
+            extra["other_workloads"] = {"error": str(e)}
+
     mlp_info = None
     if not args.no_mlp:
         try:
@@ -493,6 +596,7 @@ def main():
         "gpu_launches": 6 * args.steps,
         "clocks": clocks,
         "learned_reconstructor": mlp_info,
+        **extra,
         "residual_wfe_nm_mean": float(np.mean(wfe[len(wfe) // 5:])) if len(wfe) else None,
         "setup_s": t_setup, "wall_timed_s": t_wall,
     }

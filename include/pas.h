@@ -237,7 +237,10 @@ void pas_recon_destroy(pas_recon_t rec);
  * Integrator control and modal DM (Table 1 control: type 'INT', int_gain;
  * Table 1 DM; Sec. GPU acceleration, "influence function multiplication").
  * h_M: host float32 [n_pix][n_modes] modal basis over the pupil pixels listed
- * (row-major order) by pas_pupil_pixels(Np, obs); copied (stored mode-major). */
+ * (row-major order) by pas_pupil_pixels(Np, obs); copied (stored mode-major).
+ * prec: PAS_FP32 keeps the basis in float32; PAS_BF16 rounds it to bfloat16
+ * (nearest even; half the bytes the residual streams every step). Products and
+ * sums are float32 in both cases. */
 pas_status pas_dm_create(pas_ctx_t ctx, const float* h_M, int32_t n_pix, int32_t n_modes,
                          int32_t Np, double obs, pas_precision prec, pas_dm_t* out);
 /* Integrator then DM shape:

@@ -129,39 +129,62 @@ __global__ void atmo_kernel(AtmoArgs a, const long long* d_step, long long h_ste
 
 // Residual over the pupil pixel list: out[pix] = atm - dm_sign * (M c), atm read
 // from opd_atm (or zero). CTA: one 64-pixel tile, whose basis block [n_m][64] is
-// one contiguous stretch of memory. Thread t owns the 4 pixels 4 (t % 16) .. +3 and
-// the modes m = t / 16 + 16 j: it streams those 16-byte rows straight from global
-// memory (a warp reads two whole 256-byte mode rows per load) with RES_U loads in
-// flight, and the 16 partial sums per pixel meet once in shared memory at the end.
-// The basis is constant, so the first loads are issued before the programmatic
-// wait and overlap the predecessor kernel.
+// one contiguous stretch of memory. Each thread owns VEC consecutive pixels (one
+// 16-byte load: 4 float or 8 bfloat16 values) and every ROWS-th mode: it streams
+// those rows straight from global memory (a warp reads whole 256-byte or 128-byte
+// mode rows per load) with RES_U loads in flight, accumulating in float32; the
+// ROWS partial sums per pixel meet once in shared memory at the end. The basis is
+// constant, so the first loads are issued before the programmatic wait and
+// overlap the predecessor kernel.
 constexpr int RES_TILE = 64;        // pixels per CTA (one contiguous basis block)
 constexpr int RES_THREADS = 256;
-constexpr int RES_COLS = RES_TILE / 4;             // float4 columns of a mode row
-constexpr int RES_ROWS = RES_THREADS / RES_COLS;   // modes read per CTA-wide load
-constexpr int RES_U = 5;                           // loads in flight per thread
+constexpr int RES_U = 5;            // loads in flight per thread
 
-__device__ __forceinline__ float4 ld_stream4(const float4* p) {
-  float4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+__device__ __forceinline__ uint4 ld_stream16(const void* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                : "l"(p));
   return v;
 }
 
+template <typename T>
+__device__ __forceinline__ void unpack16(const uint4& u, float* f) {
+  if constexpr (sizeof(T) == 4) {
+    f[0] = __uint_as_float(u.x);
+    f[1] = __uint_as_float(u.y);
+    f[2] = __uint_as_float(u.z);
+    f[3] = __uint_as_float(u.w);
+  } else {  // bfloat16: the value is the upper half of a float32
+    const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      f[2 * i] = __uint_as_float(w[i] << 16);
+      f[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+  }
+}
+
+template <typename T>
 __global__ void __launch_bounds__(RES_THREADS) residual_kernel(ResArgs a) {
-  extern __shared__ float c_s[];                       // [n_m]
-  __shared__ float4 red[RES_ROWS][RES_COLS];
+  constexpr int VEC = 16 / (int)sizeof(T);         // pixels per 16-byte load
+  constexpr int COLS = RES_TILE / VEC;              // loads per mode row
+  constexpr int ROWS = RES_THREADS / COLS;          // modes per CTA-wide load
+  extern __shared__ float c_s[];                    // [n_m]
+  __shared__ float red[ROWS][RES_TILE];
   __shared__ double wred[2][RES_THREADS / 32];
   const int tid = threadIdx.x;
-  const int n_m = a.MT ? a.n_m : 0;
-  const int col = tid % RES_COLS, row = tid / RES_COLS;
-  const float4* blk = reinterpret_cast<const float4*>(a.MT + (size_t)blockIdx.x * n_m * RES_TILE) + col;
-  float4 v[RES_U];
+  const T* MT = nullptr;
+  if constexpr (sizeof(T) == 4) MT = a.MT;
+  else MT = a.MTb;
+  const int n_m = MT ? a.n_m : 0;
+  const int col = tid % COLS, row = tid / COLS;
+  const T* blk = MT + (size_t)blockIdx.x * n_m * RES_TILE + col * VEC;
+  uint4 v[RES_U];
 #pragma unroll
   for (int u = 0; u < RES_U; ++u) {
-    const int m = row + RES_ROWS * u;
-    v[u] = m < n_m ? ld_stream4(blk + (size_t)m * RES_COLS) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int m = row + ROWS * u;
+    v[u] = m < n_m ? ld_stream16(blk + (size_t)m * RES_TILE) : make_uint4(0u, 0u, 0u, 0u);
   }
   pdl_trigger();
   pdl_wait();
@@ -170,33 +193,35 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(ResArgs a) {
   if (a.cmd_ring) cmd = a.cmd_ring + (size_t)(step % a.delay) * a.n_m;
   for (int m = tid; m < n_m; m += RES_THREADS) c_s[m] = cmd[m];
   __syncthreads();
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int mb = row; mb < n_m; mb += RES_ROWS * RES_U) {
+  float acc[VEC];
+#pragma unroll
+  for (int i = 0; i < VEC; ++i) acc[i] = 0.f;
+  for (int mb = row; mb < n_m; mb += ROWS * RES_U) {
 #pragma unroll
     for (int u = 0; u < RES_U; ++u) {
-      const int m = mb + RES_ROWS * u;
+      const int m = mb + ROWS * u;
       if (m < n_m) {
         const float cm = c_s[m];
-        acc.x = fmaf(cm, v[u].x, acc.x);
-        acc.y = fmaf(cm, v[u].y, acc.y);
-        acc.z = fmaf(cm, v[u].z, acc.z);
-        acc.w = fmaf(cm, v[u].w, acc.w);
+        float f[VEC];
+        unpack16<T>(v[u], f);
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) acc[i] = fmaf(cm, f[i], acc[i]);
       }
-      const int mn = m + RES_ROWS * RES_U;
-      if (mn < n_m) v[u] = ld_stream4(blk + (size_t)mn * RES_COLS);
+      const int mn = m + ROWS * RES_U;
+      if (mn < n_m) v[u] = ld_stream16(blk + (size_t)mn * RES_TILE);
     }
   }
-  red[row][col] = acc;
+#pragma unroll
+  for (int i = 0; i < VEC; ++i) red[row][col * VEC + i] = acc[i];
   __syncthreads();
   const int base = blockIdx.x * RES_TILE;
   const int px = tid;
   const int p = base + px;
   double s1 = 0.0, s2 = 0.0;
   if (px < RES_TILE && p < a.n_pix) {
-    const float* rf = reinterpret_cast<const float*>(&red[0][0]);
     float dm = 0.f;
 #pragma unroll
-    for (int r = 0; r < RES_ROWS; ++r) dm += rf[r * RES_TILE + px];
+    for (int r = 0; r < ROWS; ++r) dm += red[r][px];
     const int flat = a.pix[p];
     const float atm = a.opd_atm ? a.opd_atm[flat] : 0.f;
     const float r = atm - a.dm_sign * dm;
@@ -264,8 +289,14 @@ pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, boo
   if (tiles == 0) return PAS_OK;
   if (a.atmo.L != 0) return set_error(ctx, PAS_EINVAL, "residual kernel: the atmosphere comes from opd_atm");
   const size_t smem = sizeof(float) * (size_t)std::max(a.n_m, 1);
-  cudaError_t e = raise_dyn_smem((const void*)residual_kernel, smem);
-  if (e == cudaSuccess) e = launch_k(residual_kernel, dim3(tiles), dim3(RES_THREADS), smem, st, pdl, a);
+  cudaError_t e;
+  if (a.MTb) {
+    e = raise_dyn_smem((const void*)residual_kernel<__nv_bfloat16>, smem);
+    if (e == cudaSuccess) e = launch_k(residual_kernel<__nv_bfloat16>, dim3(tiles), dim3(RES_THREADS), smem, st, pdl, a);
+  } else {
+    e = raise_dyn_smem((const void*)residual_kernel<float>, smem);
+    if (e == cudaSuccess) e = launch_k(residual_kernel<float>, dim3(tiles), dim3(RES_THREADS), smem, st, pdl, a);
+  }
   if (e != cudaSuccess) return set_error(ctx, PAS_ECUDA, "residual kernel launch: %s", cudaGetErrorString(e));
   return PAS_OK;
 }
@@ -274,13 +305,18 @@ pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, boo
 // modal coefficients for a basis with M^T M = n_pix I (the orthonormalised
 // bases of the DM). One CTA per mode streams that mode's column of the tiled
 // matrix; the OPD gather stays in L2 across CTAs.
-__global__ void __launch_bounds__(256) dm_project_kernel(const float* MT, const int32_t* pix, int n_pix, int n_m,
+template <typename T>
+__global__ void __launch_bounds__(256) dm_project_kernel(const T* MT, const int32_t* pix, int n_pix, int n_m,
                                                          const float* opd, float* c) {
   __shared__ float red[8];
   const int j = blockIdx.x;
   float acc = 0.f;
-  for (int p = threadIdx.x; p < n_pix; p += blockDim.x)
-    acc = fmaf(MT[((size_t)(p >> 6) * n_m + j) * 64 + (p & 63)], opd[pix[p]], acc);
+  for (int p = threadIdx.x; p < n_pix; p += blockDim.x) {
+    float m;
+    if constexpr (sizeof(T) == 4) m = MT[((size_t)(p >> 6) * n_m + j) * 64 + (p & 63)];
+    else m = __bfloat162float(MT[((size_t)(p >> 6) * n_m + j) * 64 + (p & 63)]);
+    acc = fmaf(m, opd[pix[p]], acc);
+  }
   for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -292,7 +328,10 @@ __global__ void __launch_bounds__(256) dm_project_kernel(const float* MT, const 
 }
 
 pas_status dm_project_launch(pas_dm_t dm, const float* opd, float* coeffs, cudaStream_t st) {
-  dm_project_kernel<<<dm->n_modes, 256, 0, st>>>(dm->d_MT, dm->d_pix, dm->n_pix, dm->n_modes, opd, coeffs);
+  if (dm->d_MTb)
+    dm_project_kernel<<<dm->n_modes, 256, 0, st>>>(dm->d_MTb, dm->d_pix, dm->n_pix, dm->n_modes, opd, coeffs);
+  else
+    dm_project_kernel<<<dm->n_modes, 256, 0, st>>>(dm->d_MT, dm->d_pix, dm->n_pix, dm->n_modes, opd, coeffs);
   return check_launch(dm->ctx, "modal projection launch");
 }
 
@@ -337,6 +376,7 @@ void pas_atmo_destroy(pas_atmo_t a) { delete a; }
 void pas_dm_destroy(pas_dm_t d) {
   if (!d) return;
   pas::dev_free(d->d_MT);
+  pas::dev_free(d->d_MTb);
   pas::dev_free(d->d_pix);
   delete d;
 }
@@ -346,7 +386,7 @@ pas_status pas_dm_create(pas_ctx_t ctx, const float* h_M, int32_t n_pix, int32_t
   if (!ctx || !h_M || !out) return pas::set_global_error(PAS_EINVAL, "pas_dm_create: NULL argument");
   *out = nullptr;
   PAS_CHECK_ARG(ctx, n_modes >= 1 && Np > 0, "pas_dm_create: bad sizes");
-  PAS_CHECK_ARG(ctx, prec == PAS_FP32, "pas_dm_create: only PAS_FP32 DM bases are supported");
+  PAS_CHECK_ARG(ctx, prec == PAS_FP32 || prec == PAS_BF16, "pas_dm_create: precision PAS_FP32 or PAS_BF16");
   int32_t npx = 0;
   if (pas_pupil_pixels(Np, obs, nullptr, 0, &npx) != PAS_OK || npx != n_pix)
     return pas::set_error(ctx, PAS_EINVAL, "pas_dm_create: n_pix=%d does not match the pupil (%d)", n_pix, npx);
@@ -367,13 +407,29 @@ pas_status pas_dm_create(pas_ctx_t ctx, const float* h_M, int32_t n_pix, int32_t
     for (int m = 0; m < n_modes; ++m)
       MT[((size_t)t * n_modes + m) * pas::RES_TILE + pl] = h_M[(size_t)p * n_modes + m];
   }
-  pas_status st = pas::dev_alloc(ctx, (void**)&d->d_MT, sizeof(float) * MT.size());
-  if (st == PAS_OK) st = pas::dev_alloc(ctx, (void**)&d->d_pix, sizeof(int32_t) * n_pix);
-  if (st != PAS_OK) {
-    pas_dm_destroy(d);
-    return st;
+  d->prec = prec;
+  pas_status st = PAS_OK;
+  cudaError_t e = cudaSuccess;
+  if (prec == PAS_BF16) {
+    // round to nearest even; the pad pixels stay zero
+    std::vector<__nv_bfloat16> MTb(MT.size());
+    for (size_t i = 0; i < MT.size(); ++i) MTb[i] = __float2bfloat16_rn(MT[i]);
+    st = pas::dev_alloc(ctx, (void**)&d->d_MTb, sizeof(__nv_bfloat16) * MTb.size());
+    if (st == PAS_OK) st = pas::dev_alloc(ctx, (void**)&d->d_pix, sizeof(int32_t) * n_pix);
+    if (st != PAS_OK) {
+      pas_dm_destroy(d);
+      return st;
+    }
+    e = cudaMemcpy(d->d_MTb, MTb.data(), sizeof(__nv_bfloat16) * MTb.size(), cudaMemcpyHostToDevice);
+  } else {
+    st = pas::dev_alloc(ctx, (void**)&d->d_MT, sizeof(float) * MT.size());
+    if (st == PAS_OK) st = pas::dev_alloc(ctx, (void**)&d->d_pix, sizeof(int32_t) * n_pix);
+    if (st != PAS_OK) {
+      pas_dm_destroy(d);
+      return st;
+    }
+    e = cudaMemcpy(d->d_MT, MT.data(), sizeof(float) * MT.size(), cudaMemcpyHostToDevice);
   }
-  cudaError_t e = cudaMemcpy(d->d_MT, MT.data(), sizeof(float) * MT.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d->d_pix, pix.data(), sizeof(int32_t) * n_pix, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     pas_dm_destroy(d);

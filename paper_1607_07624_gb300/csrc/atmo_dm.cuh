@@ -1,5 +1,6 @@
 // Shared declarations of the atmosphere / DM objects and their kernels.
 #pragma once
+#include <cuda_bf16.h>
 #include "internal.h"
 
 namespace pas {
@@ -15,6 +16,7 @@ struct ResArgs {
   AtmoArgs atmo;                   // L = 0: take opd_atm instead
   const float* opd_atm = nullptr;  // [Np][Np] or null (zero atmosphere)
   const float* MT = nullptr;       // [tiles][n_m][64] basis, one contiguous block per pixel tile
+  const __nv_bfloat16* MTb = nullptr;  // the same in bfloat16 (a PAS_BF16 DM); MT then null
   const int* pix = nullptr;        // [n_pix] flat pupil pixel indices
   int n_pix = 0, n_pad = 0, n_m = 0, Np = 0;
   const float* cmd = nullptr;      // [n_m] command
@@ -48,7 +50,9 @@ struct pas_dm_s {
   pas_ctx_t ctx = nullptr;
   int n_pix = 0, n_modes = 0, Np = 0, n_pad = 0;
   int64_t T_obs = 0;
-  float* d_MT = nullptr;
+  float* d_MT = nullptr;            // PAS_FP32 basis
+  __nv_bfloat16* d_MTb = nullptr;   // PAS_BF16 basis
+  pas_precision prec = PAS_FP32;
   int32_t* d_pix = nullptr;
 };
 
@@ -56,6 +60,7 @@ namespace pas {
 inline ResArgs make_res_args(pas_dm_t d) {
   ResArgs a;
   a.MT = d->d_MT;
+  a.MTb = d->d_MTb;
   a.pix = d->d_pix;
   a.n_pix = d->n_pix;
   a.n_pad = d->n_pad;

@@ -35,7 +35,7 @@ class SCAOSystem:
     autotune: True (time the pyramid launch geometries on the GPU), False (library
     default) or (rows_per_cta, row_chunks, col_groups) to set one."""
 
-    def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32,
+    def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32, dm_precision=P.PAS_FP32,
                  noise=None, delay=None, wfe_history=4096, stream=None, build_loop=True,
                  autotune=True):
         from synth.inputs import layer_seeds, screen_white_noise
@@ -62,7 +62,7 @@ class SCAOSystem:
             basis = calib.zernike_basis(cfg.Np, self.pix, cfg.n_modes)
         self.basis = np.ascontiguousarray(basis, dtype=np.float32)
         self.n_modes = self.basis.shape[1]
-        self.dm = P.pas_dm_create(self.ctx, self.basis, cfg.Np, cfg.obs)
+        self.dm = P.pas_dm_create(self.ctx, self.basis, cfg.Np, cfg.obs, dm_precision)
         # buffers
         f32 = dict(device=self.dev, dtype=torch.float32)
         self.d_opd = torch.zeros(cfg.Np, cfg.Np, **f32)

@@ -80,6 +80,47 @@ def test_dm_shape_and_residual_match_oracle(env, Np, n_modes):
         pas.pas_dm_destroy(dm)
 
 
+@pytest.mark.parametrize("Np,n_modes", [(16, 10), (240, 400)])
+def test_bf16_dm_basis_within_rounding_of_oracle(env, Np, n_modes):
+    """A PAS_BF16 DM: shape and residual equal the oracle's with the basis rounded to
+    bfloat16 (float32 sums), and stay within the rounding's statistical error of the
+    exact float64 shape."""
+    torch, pas, ctx = env
+    from oracle import modal as md
+    from oracle import optics as op
+    M = md.modal_basis(Np, 0.1, n_modes)
+    mask = op.pupil_mask(Np, 0.1)
+    dm = pas.pas_dm_create(ctx, M, Np, 0.1, pas.PAS_BF16)
+    try:
+        c = random_vector(n_modes, 31, 20.0).astype(np.float32)
+        d_c = torch.as_tensor(c).cuda()
+        opd = torch.zeros(Np, Np, device="cuda")
+        pas.pas_dm_update(dm, ctx, None, None, d_c, opd)
+        atm = (np.random.default_rng(3).standard_normal((Np, Np)) * 50).astype(np.float32)
+        res = torch.as_tensor(atm).cuda()
+        pas.pas_dm_residual(dm, ctx, res, d_c, res)
+        coeffs = torch.zeros(n_modes, device="cuda")
+        pas.pas_dm_project(dm, ctx, opd, coeffs)
+        torch.cuda.synchronize()
+        Mb = torch.as_tensor(M.astype(np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+        ref_b = md.basis_to_grid(Mb, c.astype(np.float64), mask)
+        ref = md.basis_to_grid(M, c.astype(np.float64), mask)
+        scale = np.max(np.abs(ref_b))
+        got = opd.cpu().numpy()
+        assert np.max(np.abs(got - ref_b)) <= 2e-6 * scale * math.sqrt(n_modes)
+        r = ref[mask]
+        err = got[mask] - r
+        # bf16 rounding: relative 2^-9 per element, independent across modes
+        assert np.sqrt(np.mean(err ** 2)) <= 2.0 * 2.0 ** -9 * np.sqrt(np.mean(r ** 2))
+        r_ref = np.where(mask, atm.astype(np.float64) - ref_b, 0.0)
+        assert np.max(np.abs(res.cpu().numpy() - r_ref)) <= 2e-6 * (scale + 200) * math.sqrt(n_modes)
+        # projection with the rounded basis
+        pref = Mb.T @ got.astype(np.float64)[mask] / mask.sum()
+        assert np.max(np.abs(coeffs.cpu().numpy() - pref)) <= 1e-4 * np.max(np.abs(pref))
+    finally:
+        pas.pas_dm_destroy(dm)
+
+
 @pytest.mark.parametrize("n_m,n_s", [(100, 416), (400, 1424), (37, 13), (4000, 14312)])
 def test_reconstructor_fp32_and_bf16(env, n_m, n_s):
     torch, pas, ctx = env
