@@ -271,6 +271,39 @@ def bench_other_workloads(timed, peaks, n_steps=200):
     return out
 
 
+def bench_batch(timed, n_loops=64, n_steps=100):
+    """Monte-Carlo batch: n_loops realisations of the 64 px workload (own screens
+    each; basis, reconstructor and launch geometry shared) stepped by one graph
+    launch per step. Returns the whole batch's loop-steps/s next to one loop's."""
+    import numpy as np
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    from synth import get_config
+    from synth.configs import with_
+    cfg = get_config(1)
+    systems = [SCAOSystem(cfg, wfe_history=max(256, n_steps + 64))]
+    batch = None
+    try:
+        for i in range(1, n_loops):
+            systems.append(SCAOSystem(with_(cfg, seed=cfg.seed + 7919 * i), basis=systems[0].basis, R=systems[0].R,
+                                      autotune=tuple(systems[0].tuning), wfe_history=max(256, n_steps + 64)))
+        batch = pas.pas_batch_create(systems[0].ctx, [s.loop for s in systems])
+        pas.pas_batch_step(batch, systems[0].ctx, 5)
+        for s in systems:
+            s.set_state(0, np.zeros((s.delay, s.n_modes), np.float32))
+        ms = timed(lambda: pas.pas_batch_step(batch, systems[0].ctx, 1), n_steps)
+        wfe = np.array([s.wfe_nm(n_steps) for s in systems])
+        return {"workload": f"{n_loops} realisations of {cfg.name} (own screens each)",
+                "loop_steps_per_s": n_loops * n_steps / (ms * 1e-3), "batch_steps_per_s": n_steps / (ms * 1e-3),
+                "graph_launches_per_step": 1, "kernels_per_step": 6 * n_loops,
+                "wfe_nm_mean_over_realisations": float(wfe[:, n_steps // 5:].mean())}
+    finally:
+        if batch is not None:
+            pas.pas_batch_destroy(batch)
+        for s in systems:
+            s.close()
+
+
 def bench_mlp(sysg, peaks, timed, n_train=50, batch=1024):
     """Learned reconstructor on this system's sizes (2 n_valid -> 1024^3 -> n_modes):
     training throughput (Adam steps on a device-resident synthetic set larger than
@@ -548,6 +581,10 @@ def main():
             extra["other_workloads"] = bench_other_workloads(timed, peaks)
         except Exception as e:
             extra["other_workloads"] = {"error": str(e)}
+        try:
+            extra["monte_carlo_batch"] = bench_batch(timed)
+        except Exception as e:
+            extra["monte_carlo_batch"] = {"error": str(e)}
 
     mlp_info = None
     if not args.no_mlp:

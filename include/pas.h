@@ -54,6 +54,7 @@ typedef struct pas_recon_s* pas_recon_t;
 typedef struct pas_dm_s*    pas_dm_t;
 typedef struct pas_loop_s*  pas_loop_t;
 typedef struct pas_mlp_s*   pas_mlp_t;
+typedef struct pas_batch_s* pas_batch_t;
 
 /* ------------------------------------------------------------------ context */
 
@@ -310,6 +311,22 @@ pas_status pas_loop_profile(pas_loop_t loop, int32_t n_steps, float* h_ms, int32
                             int32_t* n_kernels);
 /* Name of kernel `idx` of pas_loop_profile (static string), NULL if out of range. */
 const char* pas_loop_kernel_name(int32_t idx);
+
+/* ----------------------------------------------------------------- batches
+ * Many independent loops (Monte-Carlo realisations, of equal or different
+ * sizes) stepped by one CUDA-graph launch per step: the graph holds every loop's
+ * step as a parallel branch (the paper runs its Monte-Carlo cases as separate
+ * simulations; this is the GPU-side batching of them). The loops keep their own
+ * state, buffers and statistics (pas_loop_step(loop, 0, &stats) reads them) and
+ * must not be stepped, re-configured (pas_loop_set_mlp) or destroyed while the
+ * batch exists. Creation synchronises every loop's stream and captures the graph
+ * on `ctx`'s private stream; steps run on `ctx`'s stream. */
+pas_status pas_batch_create(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, pas_batch_t* out);
+/* n_steps >= 0 steps of every loop of the batch, asynchronous. */
+pas_status pas_batch_step(pas_batch_t batch, int32_t n_steps);
+/* Number of loops, -1 for a NULL handle. Host only. */
+int32_t pas_batch_size(pas_batch_t batch);
+void pas_batch_destroy(pas_batch_t batch);
 
 /* -------------------------------------------------- learned reconstructor
  * A multilayer perceptron from slopes to modal coefficients, used by the loop

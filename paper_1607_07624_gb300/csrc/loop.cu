@@ -323,4 +323,92 @@ pas_status pas_loop_set_state(pas_loop_t L, int64_t step, const float* h_cmd_rin
   return PAS_OK;
 }
 
+// ---------------------------------------------------------------- batches
+
+struct pas_batch_s {
+  pas_ctx_t ctx = nullptr;
+  std::vector<pas_loop_t> loops;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+void pas_batch_destroy(pas_batch_t b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaStream_t s : b->streams)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
+
+pas_status pas_batch_create(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, pas_batch_t* out) {
+  if (!ctx || !loops || !out) return pas::set_global_error(PAS_EINVAL, "pas_batch_create: NULL argument");
+  *out = nullptr;
+  PAS_CHECK_ARG(ctx, n_loops >= 1 && n_loops <= 4096, "pas_batch_create: 1 <= n_loops <= 4096");
+  for (int i = 0; i < n_loops; ++i) {
+    PAS_CHECK_ARG(ctx, loops[i] != nullptr, "pas_batch_create: NULL loop");
+    for (int j = 0; j < i; ++j) PAS_CHECK_ARG(ctx, loops[j] != loops[i], "pas_batch_create: a loop appears twice");
+  }
+  pas_batch_t b = new pas_batch_s();
+  b->ctx = ctx;
+  b->loops.assign(loops, loops + n_loops);
+  b->streams.assign(n_loops, nullptr);
+  b->join.assign(n_loops, nullptr);
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < n_loops && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    pas_batch_destroy(b);
+    return pas::set_error(ctx, PAS_ECUDA, "pas_batch_create: %s", cudaGetErrorString(e));
+  }
+  // one graph per step: every loop's step is a branch of its own (fork on the
+  // context's capture stream, one stream per loop, join back)
+  for (pas_loop_t L : b->loops) {
+    cudaError_t s0 = cudaStreamSynchronize(L->ctx->stream);
+    if (s0 != cudaSuccess) {
+      pas_batch_destroy(b);
+      return pas::set_error(ctx, PAS_ECUDA, "pas_batch_create: %s", cudaGetErrorString(s0));
+    }
+  }
+  cudaStream_t cs = ctx->capture_stream;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  pas_status st = PAS_OK;
+  if (e == cudaSuccess) e = cudaEventRecord(b->fork, cs);
+  for (int i = 0; i < n_loops && e == cudaSuccess && st == PAS_OK; ++i) {
+    e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+    if (e == cudaSuccess) st = loop_enqueue(b->loops[i], b->streams[i]);
+    if (e == cudaSuccess && st == PAS_OK) e = cudaEventRecord(b->join[i], b->streams[i]);
+    if (e == cudaSuccess && st == PAS_OK) e = cudaStreamWaitEvent(cs, b->join[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  if (e == cudaSuccess) e = e2;
+  if (st == PAS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+  b->graph = g;
+  if (st != PAS_OK || e != cudaSuccess) {
+    pas_batch_destroy(b);
+    if (st != PAS_OK) return st;
+    return pas::set_error(ctx, PAS_ECUDA, "pas_batch_create capture: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return PAS_OK;
+}
+
+pas_status pas_batch_step(pas_batch_t b, int32_t n_steps) {
+  if (!b) return pas::set_global_error(PAS_EINVAL, "pas_batch_step: NULL batch");
+  PAS_CHECK_ARG(b->ctx, n_steps >= 0, "pas_batch_step: negative step count");
+  for (int t = 0; t < n_steps; ++t) PAS_CUDA_TRY(b->ctx, cudaGraphLaunch(b->exec, b->ctx->stream));
+  return PAS_OK;
+}
+
+int32_t pas_batch_size(pas_batch_t b) { return b ? (int32_t)b->loops.size() : -1; }
+
 }  // extern "C"

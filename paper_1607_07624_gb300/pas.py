@@ -116,6 +116,10 @@ _SIGS = {
     "pas_mlp_pair": (C.c_int, [vp, vp, vp, C.c_float, vp, vp, vp]),
     "pas_loop_set_mlp": (C.c_int, [vp, vp]),
     "pas_gemm_bf16": (C.c_int, [vp, i32, i32, i32, vp, i32, vp, i32, vp, i32, i32, vp]),
+    "pas_batch_create": (C.c_int, [vp, vp, i32, P(vp)]),
+    "pas_batch_step": (C.c_int, [vp, i32]),
+    "pas_batch_size": (i32, [vp]),
+    "pas_batch_destroy": (None, [vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -462,6 +466,25 @@ def pas_loop_set_mlp(loop, ctx, mlp):
 def pas_gemm_bf16(ctx, M, N, K, d_A, lda, d_B, ldb, d_C, ldc, d_err, tile_n=0):
     _check(_lib.pas_gemm_bf16(ctx, int(M), int(N), int(K), _ptr(d_A), int(lda), _ptr(d_B), int(ldb), _ptr(d_C),
                               int(ldc), int(tile_n), _ptr(d_err)), ctx)
+
+
+def pas_batch_create(ctx, loops):
+    arr = (vp * len(loops))(*[l.value if isinstance(l, vp) else l for l in loops])
+    h = vp()
+    _check(_lib.pas_batch_create(ctx, arr, len(loops), C.byref(h)), ctx)
+    return h
+
+
+def pas_batch_step(batch, ctx, n_steps=1):
+    _check(_lib.pas_batch_step(batch, int(n_steps)), ctx)
+
+
+def pas_batch_size(batch) -> int:
+    return int(_lib.pas_batch_size(batch))
+
+
+def pas_batch_destroy(batch):
+    _lib.pas_batch_destroy(batch)
 
 
 def loaded_library_path() -> str:
