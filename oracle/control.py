@@ -21,7 +21,7 @@ import numpy as np
 
 from .atmosphere import atmo_opd
 from .modal import basis_to_grid
-from .optics import pupil_mask, pwfs_intensity, bin_detector, pwfs_slopes
+from .optics import pupil_mask, pwfs_intensity, detector_frame, pwfs_slopes
 
 
 def integrator_step(c: np.ndarray, dc: np.ndarray, gain) -> np.ndarray:
@@ -58,7 +58,7 @@ def closed_loop(cfg, screens_nm, M, R, sn, valid, n_steps, gain=None, delay=None
         wfe[t] = residual_wfe_nm(opd_res, mask)
         I = pwfs_intensity(opd_res, cfg.wavelength_nm, cfg.obs, cfg.N, cfg.K,
                            cfg.mod_radius, cfg.delta, use_fft=use_fft)
-        frame = bin_detector(I, cfg.b)
+        frame = detector_frame(I, cfg.n_sub)
         if noise is not None:
             frame = noise(frame, t)
         s = pwfs_slopes(frame, valid, cfg.n_sub, sn)

@@ -161,6 +161,45 @@ def bin_detector(I: np.ndarray, b: int) -> np.ndarray:
     return I.reshape(n, b, n, b).sum(axis=(1, 3))
 
 
+def overlap_units(n_fine: int, n_coarse: int) -> np.ndarray:
+    """O[s, i] = length of fine pixel [i, i+1) inside coarse pixel s (which spans
+    [s n_fine / n_coarse, (s+1) n_fine / n_coarse)), in units of 1/n_coarse: an
+    integer in [0, n_coarse]. Scaling both intervals by n_coarse makes the ends
+    integers: [i n_coarse, (i+1) n_coarse) and [s n_fine, (s+1) n_fine)."""
+    i = np.arange(n_fine, dtype=np.int64)[None, :]
+    s = np.arange(n_coarse, dtype=np.int64)[:, None]
+    lo = np.maximum(i * n_coarse, s * n_fine)
+    hi = np.minimum((i + 1) * n_coarse, (s + 1) * n_fine)
+    return np.maximum(hi - lo, 0)
+
+
+def rebin(I: np.ndarray, nd: int) -> np.ndarray:
+    """Area-weighted rebinning of the N x N intensity onto nd x nd detector pixels of
+    side b = N / nd fine pixels, b not necessarily an integer (the detector of the
+    batched workload: 20 sub-apertures on 128 pupil pixels, 60 on 320). Each fine
+    pixel splits its value among the detector pixels it overlaps in proportion to
+    the overlap area, so the frame keeps the total; integer b gives block sums."""
+    N = I.shape[0]
+    W = overlap_units(N, nd).astype(np.float64) / nd
+    return W @ np.asarray(I, dtype=np.float64) @ W.T
+
+
+def detector_frame(I: np.ndarray, n_sub: int) -> np.ndarray:
+    """The (2 n_sub)^2 detector frame of an N x N intensity: block sums when
+    N / (2 n_sub) is an integer, area-weighted rebinning otherwise."""
+    N = I.shape[0]
+    if N % (2 * n_sub) == 0:
+        return bin_detector(I, N // (2 * n_sub))
+    return rebin(I, 2 * n_sub)
+
+
+def subaperture_area_units(mask: np.ndarray, n_sub: int) -> np.ndarray:
+    """Pupil area inside each sub-aperture in units of 1/n_sub^2 fine pixels
+    (integers): A = O mask O^T with O = overlap_units(Np, n_sub)."""
+    O = overlap_units(mask.shape[0], n_sub)
+    return O @ mask.astype(np.int64) @ O.T
+
+
 def subaperture_counts(mask: np.ndarray, n_sub: int) -> np.ndarray:
     """Number of pupil pixels in each b x b sub-aperture block (integer b)."""
     Np = mask.shape[0]
@@ -170,12 +209,13 @@ def subaperture_counts(mask: np.ndarray, n_sub: int) -> np.ndarray:
 
 
 def valid_subapertures(Np: int, obs: float, n_sub: int) -> np.ndarray:
-    """Valid sub-apertures: 2 * (pupil pixels in the block) >= b^2 (geometric rule).
+    """Valid sub-apertures: 2 * (pupil area in the sub-aperture) >= b^2 (geometric
+    rule, b = Np / n_sub). In the integer units of subaperture_area_units the rule
+    reads 2 A >= Np^2; for integer b it is 2 * (pupil pixels in the block) >= b^2.
     Returns int32 flat indices r*n_sub + c in row-major order (the pupil index data
     of the slope computer, Table 1 slopec.pupdata_tag, Table 3)."""
-    cnt = subaperture_counts(pupil_mask(Np, obs), n_sub)
-    b = Np // n_sub
-    return np.flatnonzero((2 * cnt).ravel() >= b * b).astype(np.int32)
+    A = subaperture_area_units(pupil_mask(Np, obs), n_sub)
+    return np.flatnonzero((2 * A).ravel() >= Np * Np).astype(np.int32)
 
 
 def valid_subapertures_threshold(frame: np.ndarray, n_sub: int, thr: float) -> np.ndarray:
@@ -217,7 +257,7 @@ def pwfs_measure(opd_nm, cfg, valid=None, sn=None, use_fft=True):
     """opd -> (frame, slopes) for a configuration (noiseless)."""
     I = pwfs_intensity(opd_nm, cfg.wavelength_nm, cfg.obs, cfg.N, cfg.K, cfg.mod_radius,
                        cfg.delta, use_fft=use_fft)
-    frame = bin_detector(I, cfg.b)
+    frame = detector_frame(I, cfg.n_sub)
     if valid is None:
         valid = valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
     return frame, pwfs_slopes(frame, valid, cfg.n_sub, sn)

@@ -225,3 +225,39 @@ def test_threshold_acquisition_agrees_with_geometric_rule():
     geo = set(op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub).tolist())
     thr = set(op.valid_subapertures_threshold(frame, cfg.n_sub, 0.5).tolist())
     assert len(geo ^ thr) <= 0.1 * len(geo)
+
+
+# ---------------------------------------------------------------- fractional binning
+
+def test_rebin_is_block_sum_for_integer_binning():
+    I = np.random.default_rng(41).random((48, 48))
+    assert np.max(np.abs(op.rebin(I, 12) - op.bin_detector(I, 4))) < 1e-12
+    assert np.max(np.abs(op.detector_frame(I, 6) - op.bin_detector(I, 4))) == 0.0
+
+
+@pytest.mark.parametrize("N,nd", [(128, 20), (96, 18), (50, 7), (64, 10)])
+def test_rebin_equals_upsampled_block_sum_and_keeps_the_total(N, nd):
+    """Brute force: split every fine pixel into nd x nd equal micro-pixels; a detector
+    pixel is then exactly N x N micro-pixels."""
+    I = np.random.default_rng(N + nd).random((N, N))
+    up = np.kron(I, np.ones((nd, nd))) / (nd * nd)
+    brute = up.reshape(nd, N, nd, N).sum(axis=(1, 3))
+    fr = op.rebin(I, nd)
+    assert np.max(np.abs(fr - brute)) < 1e-10 * I.sum()
+    assert abs(fr.sum() - I.sum()) < 1e-10 * I.sum()
+    O = op.overlap_units(N, nd)
+    assert np.all(O.sum(axis=0) == nd)          # each fine pixel is fully shared out
+    assert np.all(O.sum(axis=1) == N)           # each detector pixel covers b fine pixels
+
+
+@pytest.mark.parametrize("Np,n_sub", [(64, 16), (96, 12), (128, 20), (96, 18), (50, 7)])
+def test_valid_rule_by_micro_pixel_counts(Np, n_sub):
+    mask = op.pupil_mask(Np, 0.1)
+    up = np.kron(mask.astype(np.int64), np.ones((n_sub, n_sub), dtype=np.int64))
+    A_bf = up.reshape(n_sub, Np, n_sub, Np).sum(axis=(1, 3))
+    assert np.array_equal(op.subaperture_area_units(mask, n_sub), A_bf)
+    v = op.valid_subapertures(Np, 0.1, n_sub)
+    assert np.array_equal(v, np.flatnonzero((2 * A_bf).ravel() >= Np * Np))
+    if Np % n_sub == 0:
+        b = Np // n_sub
+        assert np.array_equal(v, np.flatnonzero((2 * op.subaperture_counts(mask, n_sub)).ravel() >= b * b))
