@@ -92,7 +92,9 @@ void pas_debug_fail_alloc_after(int n);
 pas_status pas_pupil_mask(int Np, double obs, uint8_t* mask, int32_t* n_pix);
 /* Flat indices i*Np+j of the pupil pixels in row-major order into idx[cap]. */
 pas_status pas_pupil_pixels(int Np, double obs, int32_t* idx, int32_t cap, int32_t* n_pix);
-/* Flat indices r*n_sub+c of the valid sub-apertures in row-major order. */
+/* Flat indices r*n_sub+c of the valid sub-apertures in row-major order: twice the
+ * pupil area inside the sub-aperture reaches b^2, b = Np / n_sub (not necessarily
+ * an integer; exact integer arithmetic on the pixel overlaps). */
 pas_status pas_valid_subaps(int Np, double obs, int n_sub, int32_t* valid, int32_t cap,
                             int32_t* n_valid);
 

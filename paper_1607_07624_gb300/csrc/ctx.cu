@@ -1,4 +1,5 @@
 // Context, error reporting, device allocation and the host pupil geometry.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -149,17 +150,31 @@ pas_status pas_pupil_pixels(int Np, double obs, int32_t* idx, int32_t cap, int32
 
 pas_status pas_valid_subaps(int Np, double obs, int n_sub, int32_t* valid, int32_t cap,
                             int32_t* n_valid) {
-  if (Np <= 0 || n_sub <= 0 || Np % n_sub != 0 || !(obs >= 0.0 && obs < 1.0))
-    return pas::set_global_error(PAS_EINVAL, "pas_valid_subaps: Np must be a positive multiple of n_sub");
-  int b = Np / n_sub;
+  if (Np <= 0 || n_sub <= 0 || n_sub > Np || !(obs >= 0.0 && obs < 1.0))
+    return pas::set_global_error(PAS_EINVAL, "pas_valid_subaps: need 0 < n_sub <= Np and 0 <= obs < 1");
+  // Sub-aperture (r, c) covers pupil pixels [r b, (r+1) b) x [c b, (c+1) b), b = Np / n_sub
+  // not necessarily an integer. Scaled by n_sub every end is an integer, and the overlap
+  // of pixel i with row r is o(i) = |[i n_sub, (i+1) n_sub) & [r Np, (r+1) Np)| in units of
+  // 1/n_sub. Valid iff 2 * sum over pupil pixels of o_r(i) o_c(j) >= Np^2, i.e. twice the
+  // pupil area reaches b^2 (for integer b: 2 * pixel count >= b^2).
+  auto ovl = [&](int i, int s) -> int64_t {
+    const int64_t lo = std::max((int64_t)i * n_sub, (int64_t)s * Np);
+    const int64_t hi = std::min((int64_t)(i + 1) * n_sub, (int64_t)(s + 1) * Np);
+    return hi > lo ? hi - lo : 0;
+  };
   int64_t T = pas::obstruction_threshold(Np, obs);
   int32_t n = 0;
-  for (int r = 0; r < n_sub; ++r)
+  for (int r = 0; r < n_sub; ++r) {
+    const int i0 = (int)(((int64_t)r * Np) / n_sub), i1 = (int)(((int64_t)(r + 1) * Np + n_sub - 1) / n_sub);
     for (int c = 0; c < n_sub; ++c) {
-      int cnt = 0;
-      for (int i = r * b; i < (r + 1) * b; ++i)
-        for (int j = c * b; j < (c + 1) * b; ++j) cnt += pas::in_pupil(i, j, Np, T);
-      if (2 * cnt >= b * b) {
+      const int j0 = (int)(((int64_t)c * Np) / n_sub), j1 = (int)(((int64_t)(c + 1) * Np + n_sub - 1) / n_sub);
+      int64_t A = 0;
+      for (int i = i0; i < i1; ++i) {
+        const int64_t oi = ovl(i, r);
+        for (int j = j0; j < j1; ++j)
+          if (pas::in_pupil(i, j, Np, T)) A += oi * ovl(j, c);
+      }
+      if (2 * A >= (int64_t)Np * Np) {
         if (valid) {
           if (n >= cap) return pas::set_global_error(PAS_EINVAL, "pas_valid_subaps: cap too small");
           valid[n] = r * n_sub + c;
@@ -167,6 +182,7 @@ pas_status pas_valid_subaps(int Np, double obs, int n_sub, int32_t* valid, int32
         ++n;
       }
     }
+  }
   if (n_valid) *n_valid = n;
   return PAS_OK;
 }

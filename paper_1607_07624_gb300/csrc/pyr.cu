@@ -68,7 +68,8 @@ struct ColArgs {
   const float2* tilt;   // [K][Np] (-1)^i exp(2 pi i (i - ci) alpha_k): tilt_x + input ramp
   const int* kmap;      // [K] -> rows-pass index
   float* part;          // [G][nd][nd]
-  int Np, off, K, kper, nd, b;
+  int Np, off, K, kper, nd, b;  // b: warps per CTA (fine columns of one detector column)
+  int frac;             // detector pixels of N / nd fine pixels, N / nd not an integer
   FrameArgs fin;
 };
 
@@ -275,13 +276,18 @@ pyr_cols_kernel(ColArgs a) {
   pdl_wait();  // H, the partial frames and the counters belong to the predecessors
   __syncthreads();  // twiddles and mask staged
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int y = q * a.b + warp;
+  // the fine columns overlapping detector column q: [q b, (q+1) b) exactly when b is an
+  // integer; [floor(q N/nd), ceil((q+1) N/nd)) otherwise (the edge columns are shared
+  // with the neighbouring detector columns and transformed by both CTAs)
+  const int y0 = a.frac ? (q * N) / a.nd : q * a.b;
+  const int nw = a.frac ? ((q + 1) * N + a.nd - 1) / a.nd - y0 : a.b;
+  const int y = y0 + warp;
   float2* buf = bufs + warp * PITCH;
   using OS = OutShape<N>;
   float acc[OS::PER_LANE];
 #pragma unroll
   for (int t = 0; t < OS::PER_LANE; ++t) acc[t] = 0.f;
-  for (int kk = 0; kk < kc; ++kk) {
+  for (int kk = 0; kk < (warp < nw ? kc : 0); ++kk) {
     // the tilt row of this k is shared by the CTA's warps through L1; no barrier
     const float2* Hcol = a.H + ((size_t)a.kmap[k0 + kk] * N + y) * Np;
     const float2* tk = a.tilt + (size_t)(k0 + kk) * Np;
@@ -310,13 +316,35 @@ pyr_cols_kernel(ColArgs a) {
   __syncthreads();
   const int nd = a.nd, b = a.b;
   float* out = a.part + (size_t)g * nd * nd;
-  for (int p = threadIdx.x; p < nd; p += blockDim.x) {
-    float sum = 0.f;
-    for (int w = 0; w < b; ++w) {
-      const float* col = reinterpret_cast<const float*>(bufs + w * PITCH);
-      for (int xx = 0; xx < b; ++xx) sum += col[p * b + xx];
+  if (!a.frac) {
+    for (int p = threadIdx.x; p < nd; p += blockDim.x) {
+      float sum = 0.f;
+      for (int w = 0; w < b; ++w) {
+        const float* col = reinterpret_cast<const float*>(bufs + w * PITCH);
+        for (int xx = 0; xx < b; ++xx) sum += col[p * b + xx];
+      }
+      out[(size_t)p * nd + q] = sum;
     }
-    out[(size_t)p * nd + q] = sum;
+  } else {
+    // area weights: fine pixel i shares |[i nd, (i+1) nd) & [p N, (p+1) N)| / nd of
+    // itself with detector pixel p (integers, exact in float)
+    const float inv = 1.0f / ((float)nd * (float)nd);
+    for (int p = threadIdx.x; p < nd; p += blockDim.x) {
+      const int x0 = (p * N) / nd, x1 = ((p + 1) * N + nd - 1) / nd;
+      float sum = 0.f;
+      for (int w = 0; w < nw; ++w) {
+        const int yy = y0 + w;
+        const int oy = min((yy + 1) * nd, (q + 1) * N) - max(yy * nd, q * N);
+        const float* col = reinterpret_cast<const float*>(bufs + w * PITCH);
+        float cs = 0.f;
+        for (int i = x0; i < x1; ++i) {
+          const int ox = min((i + 1) * nd, (p + 1) * N) - max(i * nd, p * N);
+          cs = fmaf((float)ox, col[i], cs);
+        }
+        sum = fmaf((float)oy, cs, sum);
+      }
+      out[(size_t)p * nd + q] = sum * inv;
+    }
   }
   // the last of the G groups of column q builds that detector column; the CTA
   // that completes the last column computes the slopes
@@ -391,6 +419,7 @@ struct pas_pyr_s {
   pas_pyr_params p{};
   pas::PyrKernels kern{};
   int b = 0, nd = 0, n_s = 0, G = 0, kper = 0, n_valid = 0, n_pupil = 0;
+  int frac = 0;  // non-integer fine pixels per detector pixel
   int rows = 4, s_chunk = 1, n_schunks = 1;
   int64_t T_obs = 0;
   float inv_hi = 0.f, inv_lo = 0.f;
@@ -467,6 +496,7 @@ static void launch_cols(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream
   ca.kper = y->kper;
   ca.nd = y->nd;
   ca.b = y->b;
+  ca.frac = y->frac;
   long long* ctr = fa_extra ? fa_extra->frame_ctr : y->d_frame_ctr;
   FrameArgs& fa = ca.fin;
   fa.frame = d_frame ? d_frame : y->d_frame;
@@ -569,14 +599,19 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   *out = nullptr;
   const pas_pyr_params p = *pp;
   PAS_CHECK_ARG(ctx, p.Np > 0 && p.N == 2 * p.Np, "pas_pyr_create: N must equal 2*Np");
-  PAS_CHECK_ARG(ctx, p.n_sub > 0 && p.N % (2 * p.n_sub) == 0, "pas_pyr_create: N must be a multiple of 2*n_sub");
+  PAS_CHECK_ARG(ctx, p.n_sub > 0 && 2 * p.n_sub <= p.N, "pas_pyr_create: need 1 <= n_sub <= Np");
   PAS_CHECK_ARG(ctx, p.K >= 1 && p.K <= 4096, "pas_pyr_create: K out of range");
   PAS_CHECK_ARG(ctx, p.wavelength_nm > 0 && p.mod_radius >= 0 && p.obs >= 0 && p.obs < 1,
                 "pas_pyr_create: bad wavelength, modulation radius or obstruction");
   pas::PyrKernels kern;
   if (!pas::lookup_kernels(p.N, &kern))
     return pas::set_error(ctx, PAS_EINVAL, "pas_pyr_create: FFT size N=%d not supported", p.N);
-  const int b = p.N / (2 * p.n_sub);
+  // warps per columns CTA: b fine columns per detector column, or for a non-integer
+  // N / (2 n_sub) the most fine columns any detector column overlaps
+  const int nd_ = 2 * p.n_sub, frac = p.N % nd_ != 0;
+  int b = p.N / nd_;
+  if (frac)
+    for (int q = 0; q < nd_; ++q) b = std::max(b, ((q + 1) * p.N + nd_ - 1) / nd_ - (q * p.N) / nd_);
   PAS_CHECK_ARG(ctx, b <= 16, "pas_pyr_create: more than 16 fine pixels per detector pixel");
 
   pas_pyr_t y = new pas_pyr_s();
@@ -584,6 +619,7 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   y->p = p;
   y->kern = kern;
   y->b = b;
+  y->frac = frac;
   y->nd = 2 * p.n_sub;
   y->T_obs = pas::obstruction_threshold(p.Np, p.obs);
   {
@@ -606,10 +642,6 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
       }
   } else {
     int32_t nv = 0;
-    if (p.Np % p.n_sub != 0) {
-      delete y;
-      return pas::set_error(ctx, PAS_EINVAL, "pas_pyr_create: geometric rule needs Np multiple of n_sub");
-    }
     pas_valid_subaps(p.Np, p.obs, p.n_sub, nullptr, 0, &nv);
     valid.resize(nv);
     pas_valid_subaps(p.Np, p.obs, p.n_sub, valid.data(), nv, &nv);

@@ -54,10 +54,20 @@ def test_geometry_bit_exact_with_oracle(lib, Np, obs, n_sub):
 
 def test_geometry_rejects_bad_arguments(lib):
     with pytest.raises(lib.PasError) as e:
-        lib.pas_valid_subaps(30, 0.1, 7)
+        lib.pas_valid_subaps(30, 0.1, 0)
     assert e.value.status == lib.PAS_EINVAL
     with pytest.raises(lib.PasError):
+        lib.pas_valid_subaps(30, 0.1, 31)
+    with pytest.raises(lib.PasError):
         lib.pas_pupil_mask(16, 1.5)
+
+
+@pytest.mark.parametrize("Np,n_sub", [(30, 7), (128, 20), (320, 60), (50, 7), (64, 16)])
+def test_valid_subaps_non_integer_binning_bit_exact(lib, Np, n_sub):
+    """Sub-apertures of Np / n_sub pixels, not necessarily an integer: the library's
+    integer overlap rule equals the oracle's."""
+    from oracle import optics as op
+    assert np.array_equal(lib.pas_valid_subaps(Np, 0.1, n_sub), op.valid_subapertures(Np, 0.1, n_sub))
 
 
 def test_product_screens_match_oracle():

@@ -61,7 +61,7 @@ def oracle_measure(cfg, opd32, valid):
     from oracle import optics as op
     I = op.pwfs_intensity(opd32.astype(np.float64), cfg.wavelength_nm, cfg.obs, cfg.N, cfg.K,
                           cfg.mod_radius, cfg.delta)
-    fr = op.bin_detector(I, cfg.b)
+    fr = op.detector_frame(I, cfg.n_sub)
     return fr, op.pwfs_slopes(fr, valid, cfg.n_sub)
 
 
@@ -94,6 +94,32 @@ def test_small_grids_match_oracle(env, cfg):
     fr_g, sl_g, valid = run_gpu(env, cfg, opd)
     assert np.array_equal(valid, op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub))
     check(cfg, fr_g, sl_g, *oracle_measure(cfg, opd, valid))
+
+
+FRACTIONAL = [
+    tiny_config(Np=32, N=64, n_sub=5, K=8),                      # 6.4 pixels per sub-aperture
+    tiny_config(Np=64, N=128, n_sub=20, K=12),                   # 3.2
+    tiny_config(Np=24, N=48, n_sub=7, K=5),                      # 3.43, odd K
+    tiny_config(Np=128, N=256, n_sub=20, K=12, mod_radius=3.0),  # 6.4: batched 8 m group
+    tiny_config(Np=320, N=640, n_sub=60, K=24, mod_radius=3.0),  # 5.33: batched 25 m group
+]
+
+
+@pytest.mark.parametrize("cfg", FRACTIONAL, ids=lambda c: f"N{c.N}_nsub{c.n_sub}")
+def test_non_integer_binning_matches_oracle(env, cfg):
+    """Detector pixels of N / (2 n_sub) fine pixels, not an integer: area-weighted
+    rebinning (the oracle's exact rational weights) and the rational valid rule."""
+    from oracle import optics as op
+    assert cfg.N % (2 * cfg.n_sub) != 0
+    opd = random_opd_nm(cfg.Np, 250.0, seed=cfg.N + cfg.n_sub).astype(np.float32)
+    fr_g, sl_g, valid = run_gpu(env, cfg, opd)
+    assert np.array_equal(valid, op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub))
+    fr_o, sl_o = oracle_measure(cfg, opd, valid)
+    check(cfg, fr_g, sl_g, fr_o, sl_o)
+    # the frame keeps the total intensity of the grid
+    I = op.pwfs_intensity(opd.astype(np.float64), cfg.wavelength_nm, cfg.obs, cfg.N, cfg.K, cfg.mod_radius,
+                          cfg.delta)
+    assert abs(fr_g.sum() - I.sum()) <= 1e-5 * I.sum()
 
 
 @pytest.mark.parametrize("idx", [1, 2, 3])
