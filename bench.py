@@ -304,6 +304,61 @@ def bench_batch(timed, n_loops=64, n_steps=100):
             s.close()
 
 
+def bench_batched_workload(timed, n_steps=30):
+    """The batched Monte-Carlo workload: 64 loops of three sizes (32 x 128 px with
+    20x20 sub-apertures, 24 x 320 px with 60x60, 8 x 480 px with 96x96; 6.4, 5.33
+    and 5 pixels per sub-aperture), each with its own screens (seed and r0 drawn
+    in 0.08-0.2 m), stepped by one graph launch per step. Per group one DM object
+    holds a random basis of the group's shape, every loop has a random bf16
+    reconstructor of its shape and the pyramid launch geometry is autotuned once:
+    timing only, the wavefront error is not meaningful."""
+    import numpy as np
+    import torch
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    from synth.configs import batched_workload
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    ctx = pas.pas_ctx_create(torch.cuda.current_stream())
+    systems, shared, batch = [], {}, None
+    try:
+        for gi, cfg in batched_workload():
+            if gi not in shared:
+                pix = pas.pas_pupil_pixels(cfg.Np, cfg.obs)
+                valid = pas.pas_valid_subaps(cfg.Np, cfg.obs, cfg.n_sub)
+                basis = torch.randn(pix.size, cfg.n_modes, device="cuda", generator=gen).cpu().numpy()
+                R = (torch.randn(cfg.n_modes, 2 * valid.size, device="cuda", generator=gen) * 1e-3).cpu().numpy()
+                shared[gi] = {"basis": basis, "R": R, "dm": pas.pas_dm_create(ctx, basis, cfg.Np, cfg.obs),
+                              "tuning": True, "name": cfg.name, "count": 0, "n_valid": int(valid.size),
+                              "n_modes": cfg.n_modes}
+            sh = shared[gi]
+            sysl = SCAOSystem(cfg, basis=sh["basis"], R=sh["R"], dm=sh["dm"], recon_precision=pas.PAS_BF16,
+                              autotune=sh["tuning"], wfe_history=max(256, n_steps + 64))
+            if sh["tuning"] is True:
+                sh["tuning"] = tuple(sysl.tuning)
+            sh["count"] += 1
+            systems.append(sysl)
+        batch = pas.pas_batch_create(ctx, [s.loop for s in systems])
+        pas.pas_batch_step(batch, ctx, 3)
+        for s in systems:
+            s.set_state(0, np.zeros((s.delay, s.n_modes), np.float32))
+        ms = timed(lambda: pas.pas_batch_step(batch, ctx, 1), n_steps)
+        groups = [{k: v for k, v in sh.items() if k in ("name", "count", "n_valid", "n_modes", "tuning")}
+                  for sh in shared.values()]
+        return {"loops": len(systems), "groups": groups, "ms_per_batch_step": ms / n_steps,
+                "loop_steps_per_s": len(systems) * n_steps / (ms * 1e-3), "graph_launches_per_step": 1,
+                "kernels_per_step": 6 * len(systems),
+                "note": "random bases and reconstructors of the workload's shapes: timing only"}
+    finally:
+        if batch is not None:
+            pas.pas_batch_destroy(batch)
+        for s in systems:
+            s.close()
+        torch.cuda.synchronize()
+        for sh in shared.values():
+            pas.pas_dm_destroy(sh["dm"])
+        pas.pas_ctx_destroy(ctx)
+
+
 def bench_mlp(sysg, peaks, timed, n_train=50, batch=1024):
     """Learned reconstructor on this system's sizes (2 n_valid -> 1024^3 -> n_modes):
     training throughput (Adam steps on a device-resident synthetic set larger than
@@ -585,6 +640,10 @@ def main():
             extra["monte_carlo_batch"] = bench_batch(timed)
         except Exception as e:
             extra["monte_carlo_batch"] = {"error": str(e)}
+        try:
+            extra["batched_workload"] = bench_batched_workload(timed)
+        except Exception as e:
+            extra["batched_workload"] = {"error": str(e)}
 
     mlp_info = None
     if not args.no_mlp:

@@ -36,6 +36,7 @@ class SCAOSystem:
     default) or (rows_per_cta, row_chunks, col_groups) to set one."""
 
     def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32, dm_precision=P.PAS_FP32,
+                 dm=None,
                  noise=None, delay=None, wfe_history=4096, stream=None, build_loop=True,
                  autotune=True):
         from synth.inputs import layer_seeds, screen_white_noise
@@ -62,7 +63,9 @@ class SCAOSystem:
             basis = calib.zernike_basis(cfg.Np, self.pix, cfg.n_modes)
         self.basis = np.ascontiguousarray(basis, dtype=np.float32)
         self.n_modes = self.basis.shape[1]
-        self.dm = P.pas_dm_create(self.ctx, self.basis, cfg.Np, cfg.obs, dm_precision)
+        # a DM object holds only the basis: loops of one geometry may share one (dm=)
+        self.own_dm = dm is None
+        self.dm = P.pas_dm_create(self.ctx, self.basis, cfg.Np, cfg.obs, dm_precision) if dm is None else dm
         # buffers
         f32 = dict(device=self.dev, dtype=torch.float32)
         self.d_opd = torch.zeros(cfg.Np, cfg.Np, **f32)
@@ -148,8 +151,9 @@ class SCAOSystem:
         P.pas_loop_set_state(self.loop, self.ctx, step, ring)
 
     def close(self):
+        dm = getattr(self, "dm", None) if getattr(self, "own_dm", True) else None
         for h, f in ((getattr(self, "loop", None), P.pas_loop_destroy), (getattr(self, "rec", None), P.pas_recon_destroy),
-                     (getattr(self, "dm", None), P.pas_dm_destroy), (getattr(self, "pyr", None), P.pas_pyr_destroy),
+                     (dm, P.pas_dm_destroy), (getattr(self, "pyr", None), P.pas_pyr_destroy),
                      (getattr(self, "atmo", None), P.pas_atmo_destroy)):
             if h:
                 f(h)

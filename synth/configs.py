@@ -114,6 +114,35 @@ CFG3 = SCAOConfig(
 
 CONFIGS = {1: CFG1, 2: CFG2, 3: CFG3}
 
+# Batched Monte-Carlo workload: loops of three sizes stepped together. Per group
+# (count, configuration): 8 m / 128 px / 20x20 sub-apertures / 12 points, 25 m /
+# 320 px / 60x60 / 24, 39 m / 480 px / 96x96 / 32. Not stated for this workload and
+# taken here: one von Karman layer per loop (10 m/s), modulation 3 lambda/D, about
+# half as many modes as valid sub-apertures, 1 ms steps, noiseless.
+BATCH_GROUPS = (
+    (32, SCAOConfig(name="batch_8m_128px", D=8.0, Np=128, N=256, obs=0.1, n_sub=20, K=12, mod_radius=3.0,
+                    wavelength_nm=750.0, n_modes=150, basis="zernike", r0_m=0.15, L0_m=25.0,
+                    layers=(LayerSpec(1.0, 0.0, 10.0, 0.0),), S=512, n_steps=200, seed=3000)),
+    (24, SCAOConfig(name="batch_25m_320px", D=25.0, Np=320, N=640, obs=0.1, n_sub=60, K=24, mod_radius=3.0,
+                    wavelength_nm=750.0, n_modes=1400, basis="zernike", r0_m=0.15, L0_m=25.0,
+                    layers=(LayerSpec(1.0, 0.0, 10.0, 0.0),), S=1024, n_steps=200, seed=4000)),
+    (8, SCAOConfig(name="batch_39m_480px", D=39.0, Np=480, N=960, obs=0.1, n_sub=96, K=32, mod_radius=3.0,
+                   wavelength_nm=750.0, n_modes=3578, basis="zernike", r0_m=0.15, L0_m=25.0,
+                   layers=(LayerSpec(1.0, 0.0, 10.0, 0.0),), S=2048, n_steps=200, seed=5000)),
+)
+
+
+def batched_workload(r0_range=(0.08, 0.2), seed: int = 9000):
+    """The 64 loops of the batched workload: [(group index, configuration)] with a
+    seed and an r0 (uniform in r0_range) of their own."""
+    from .inputs import rng
+    g = rng(seed)
+    out = []
+    for gi, (count, cfg) in enumerate(BATCH_GROUPS):
+        for i in range(count):
+            out.append((gi, with_(cfg, seed=cfg.seed + 17 * i, r0_m=float(g.uniform(*r0_range)))))
+    return out
+
 
 def get_config(idx: int) -> SCAOConfig:
     return CONFIGS[idx]
