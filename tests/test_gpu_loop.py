@@ -72,7 +72,10 @@ def test_graph_and_eager_steps_are_identical_and_resume_is_exact(cfg1_setup):
     from paper_1607_07624_gb300.system import SCAOSystem
     cfg, screens, M, valid, sn, IM, R = cfg1_setup
     a = SCAOSystem(cfg, screens=screens.astype(np.float32), basis=M, R=R, wfe_history=64)
-    b = SCAOSystem(cfg, screens=screens.astype(np.float32), basis=M, R=R, wfe_history=64)
+    # the same launch geometry: another geometry sums the modulation groups in
+    # another order, which is a different (equally valid) rounding of the frame
+    b = SCAOSystem(cfg, screens=screens.astype(np.float32), basis=M, R=R, wfe_history=64,
+                   autotune=tuple(a.tuning))
     try:
         a.step(25)
         b.step_eager(25)
