@@ -201,45 +201,59 @@ __device__ void finish_column(const FrameArgs& f, const float* part, int q, int 
 __global__ void __launch_bounds__(256) slopes_kernel(FrameArgs f, int nd) {
   __shared__ double red[32];
   pdl_trigger();
-  pdl_wait();
-  double fl = 0.0;
-  for (int t = threadIdx.x; t < nd; t += blockDim.x) fl += f.flux_part[t];
-  const float F = (float)(block_sum(fl, red) / (double)f.nv);
+  // Before the wait for the columns pass: the constants of this thread's slope and
+  // the step's residual WFE, whose partials the residual kernel wrote before the
+  // rows pass started (that kernel has completed).
   const int ns = f.n_sub;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f.slopes && j < f.nv) {
+  const bool mine = f.slopes && j < f.nv;
+  int i00 = 0, i01 = 0, i10 = 0, i11 = 0;
+  float snx = 0.f, sny = 0.f;
+  if (mine) {
     const int v = f.valid[j], r = v / ns, c = v - r * ns;
-    const float q00 = f.frame[r * nd + c], q01 = f.frame[r * nd + ns + c];
-    const float q10 = f.frame[(ns + r) * nd + c], q11 = f.frame[(ns + r) * nd + ns + c];
+    i00 = r * nd + c;
+    i01 = r * nd + ns + c;
+    i10 = (ns + r) * nd + c;
+    i11 = (ns + r) * nd + ns + c;
+    if (f.sn) {
+      snx = f.sn[j];
+      sny = f.sn[f.nv + j];
+    }
+  }
+  if (blockIdx.x == 0 && f.wfe.wfe_part) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int t = threadIdx.x; t < f.wfe.n_wfe_part; t += blockDim.x) {
+      const double2 w = f.wfe.wfe_part[t];
+      s1 += w.x;
+      s2 += w.y;
+    }
+    s1 = block_sum(s1, red);
+    s2 = block_sum(s2, red);
+    if (threadIdx.x == 0) {
+      const double m = s1 * f.wfe.inv_npix;
+      const double var = fmax(s2 * f.wfe.inv_npix - m * m, 0.0);
+      f.wfe.wfe_hist[(*f.wfe.step) % f.wfe.wfe_hist_len] = sqrt(var);
+    }
+  }
+  pdl_wait();
+  // the frame and the column fluxes: all loads in one round
+  double fl = 0.0;
+  for (int t = threadIdx.x; t < nd; t += blockDim.x) fl += f.flux_part[t];
+  float q00 = 0.f, q01 = 0.f, q10 = 0.f, q11 = 0.f;
+  if (mine) {
+    q00 = f.frame[i00];
+    q01 = f.frame[i01];
+    q10 = f.frame[i10];
+    q11 = f.frame[i11];
+  }
+  const float F = (float)(block_sum(fl, red) / (double)f.nv);
+  if (mine) {
     const float den = f.local_norm ? (q00 + q01 + q10 + q11) : F;
     const float inv = 1.0f / den;
-    float sx = ((q10 + q11) - (q00 + q01)) * inv;
-    float sy = ((q01 + q11) - (q00 + q10)) * inv;
-    if (f.sn) {
-      sx -= f.sn[j];
-      sy -= f.sn[f.nv + j];
-    }
-    f.slopes[j] = sx;
-    f.slopes[f.nv + j] = sy;
+    f.slopes[j] = ((q10 + q11) - (q00 + q01)) * inv - snx;
+    f.slopes[f.nv + j] = ((q01 + q11) - (q00 + q10)) * inv - sny;
   }
-  if (blockIdx.x == 0) {
-    if (f.wfe.wfe_part) {
-      double s1 = 0.0, s2 = 0.0;
-      for (int t = threadIdx.x; t < f.wfe.n_wfe_part; t += blockDim.x) {
-        const double2 w = f.wfe.wfe_part[t];
-        s1 += w.x;
-        s2 += w.y;
-      }
-      s1 = block_sum(s1, red);
-      s2 = block_sum(s2, red);
-      if (threadIdx.x == 0) {
-        const double m = s1 * f.wfe.inv_npix;
-        const double var = fmax(s2 * f.wfe.inv_npix - m * m, 0.0);
-        f.wfe.wfe_hist[(*f.wfe.step) % f.wfe.wfe_hist_len] = sqrt(var);
-      }
-    }
-    if (threadIdx.x == 0 && f.ctr_increment && f.frame_ctr) *f.frame_ctr += 1;
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && f.ctr_increment && f.frame_ctr) *f.frame_ctr += 1;
 }
 
 // Column tilt phasors of the modulation points, [K][Np]: (-1)^i e^{2 pi i (i - ci) alpha_k}
