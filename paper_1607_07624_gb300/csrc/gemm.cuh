@@ -24,6 +24,7 @@
 namespace pas {
 
 constexpr unsigned GEMM_ERR_PRODUCER = 1u, GEMM_ERR_MMA = 2u, GEMM_ERR_EPILOGUE = 4u, GEMM_ERR_DRAIN = 8u;
+constexpr int GEMM_GROUP = 8;  // column tiles per band of the grouped tile order
 
 template <int BN, int STAGES>
 struct GemmCfg {
@@ -47,7 +48,21 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * 128;
+  // grouped tile order: CTAs are dispatched in linear order; consecutive ones sweep
+  // a band of GEMM_GROUP column tiles row by row, so a wave reads a band of B (which
+  // stays in L2 while the band is swept) instead of all of it
+  int n_tile, m_tile;
+  {
+    const int tn = gridDim.x, tm = gridDim.y;
+    const int lin = blockIdx.y * tn + blockIdx.x;
+    const int band = lin / (GEMM_GROUP * tm);
+    const int first = band * GEMM_GROUP;
+    const int width = min(GEMM_GROUP, tn - first);
+    const int in_band = lin - band * GEMM_GROUP * tm;
+    n_tile = first + in_band % width;
+    m_tile = in_band / width;
+  }
+  const int n0 = n_tile * BN, m0 = m_tile * 128;
   const int nk = (K + 63) / 64;
 
   if (threadIdx.x == 0) {

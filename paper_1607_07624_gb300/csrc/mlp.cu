@@ -989,7 +989,7 @@ pas_status pas_gemm_bf16(pas_ctx_t ctx, int32_t M, int32_t N, int32_t K, const u
   if (!pas::gemm_prepare(&op, reinterpret_cast<const __nv_bfloat16*>(d_A), lda,
                          reinterpret_cast<const __nv_bfloat16*>(d_B), ldb, M, N, K, ctx->sm_count))
     return pas::set_error(ctx, PAS_EINVAL, "pas_gemm_bf16: tensor map rejected (16-byte alignment)");
-  if (tile_n) {
+  if (tile_n) {  // a fixed tile width
     op.bn = tile_n;
     if (!pas::make_tmap_bf16(&op.b, d_B, (uint64_t)N, (uint64_t)K, (uint64_t)ldb, (uint32_t)tile_n))
       return pas::set_error(ctx, PAS_EINVAL, "pas_gemm_bf16: tensor map rejected");
