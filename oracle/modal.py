@@ -21,6 +21,7 @@ import math
 
 import numpy as np
 
+from .atmosphere import von_karman_psd
 from .optics import pupil_mask
 
 
@@ -112,3 +113,46 @@ def pseudo_inverse(IM: np.ndarray, rcond: float = 1e-3) -> np.ndarray:
     U, s, Vt = np.linalg.svd(IM, full_matrices=False)
     keep = s >= rcond * s[0]
     return (Vt[keep].T / s[keep][None, :]) @ U[:, keep].T
+
+
+def modal_covariance(M: np.ndarray, mask: np.ndarray, dx: float, r0: float, L0: float,
+                     pad: int = 2) -> np.ndarray:
+    """Covariance [rad^2 at 500 nm] of the modal coefficients a = (1/n_pix) M^T phi of
+    a stationary phase phi with the von Karman PSD (Kolmogorov for L0 = inf):
+
+        C_ij = (1/n_pix^2) sum_f PSD(f) conj(Mhat_i(f)) Mhat_j(f) df^2,
+        Mhat_i(f) = sum_x m_i(x) exp(-2 pi i f . x),
+
+    over the frequencies of a (pad Np)^2 zero-padded discrete transform, df = 1 /
+    (pad Np dx); for L0 = inf the f = 0 term (infinite PSD) is left out. The
+    reading of the KL basis of the 240 px and ELT workloads (the paper names KL
+    modes without defining them)."""
+    Np = mask.shape[0]
+    P = pad * Np
+    n = int(mask.sum())
+    f = np.fft.fftfreq(P, d=dx)
+    fm = np.sqrt(f[:, None] ** 2 + f[None, :] ** 2)
+    with np.errstate(divide="ignore"):
+        psd = von_karman_psd(fm, r0, L0)
+    if math.isinf(L0):
+        psd[0, 0] = 0.0
+    w = psd.ravel() * (1.0 / (P * dx)) ** 2
+    F = np.empty((M.shape[1], P * P), dtype=np.complex128)
+    for i in range(M.shape[1]):
+        g = np.zeros((P, P))
+        g[:Np, :Np][mask] = M[:, i]
+        F[i] = np.fft.fft2(g).ravel()
+    return ((F.conj() * w) @ F.T).real / (n * n)
+
+
+def kl_basis(M: np.ndarray, C: np.ndarray):
+    """Karhunen-Loeve modes within the span of the orthonormal basis M: M U with
+    C = U diag(w) U^T, w decreasing (the coefficient variances). Sign: each mode
+    is positive at its largest-magnitude pixel (first such pixel), a convention
+    that does not depend on the signs of M. Returns (M U, w)."""
+    w, U = np.linalg.eigh(C)
+    order = np.argsort(-w, kind="stable")
+    w, U = w[order], U[:, order]
+    K = M @ U
+    idx = np.argmax(np.abs(K), axis=0)
+    return K * np.sign(K[idx, np.arange(K.shape[1])]), w

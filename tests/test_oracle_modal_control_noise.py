@@ -250,3 +250,72 @@ def test_mlp_adam_overfits_a_tiny_batch():
         out, cache = mlp.forward(params, x)
         mlp.adam_update(params, mlp.backward(params, cache, out, y), m, v, t, 1e-2)
     assert mlp.loss(mlp.forward(params, x)[0], y) < 1e-4 * l0
+
+
+# ---------------------------------------------------------------- KL basis
+
+def _piston_free(M):
+    M = M - M.mean(axis=0)
+    Q, R = np.linalg.qr(M)
+    return Q * np.sign(np.diag(R)) * math.sqrt(M.shape[0])
+
+
+@pytest.mark.parametrize("Np,D,r0,L0,pad", [(24, 2.0, 0.1, 1.0, 8), (32, 4.0, 0.2, 2.0, 6)])
+def test_modal_covariance_equals_spatial_double_sum(Np, D, r0, L0, pad):
+    """Independent route: C = -(1/2 n^2) M^T D(|x - x'|) M with the closed-form von
+    Karman structure function (zero-mean modes), against the frequency-domain sum."""
+    dx = D / Np
+    mask = op.pupil_mask(Np, 0.1)
+    M = _piston_free(md.modal_basis(Np, 0.1, 12))
+    C = md.modal_covariance(M, mask, dx, r0, L0, pad)
+    X, Y = np.nonzero(mask)
+    P = np.stack([X, Y], 1) * dx
+    r = np.sqrt(((P[:, None, :] - P[None, :, :]) ** 2).sum(-1))
+    Cs = -0.5 * M.T @ at.structure_function_von_karman(r, r0, L0) @ M / mask.sum() ** 2
+    assert np.max(np.abs(C - Cs)) <= 1e-2 * np.max(np.diag(Cs))
+
+
+def _noll_covariance(j, jp, D_r0):
+    """Kolmogorov covariance of Zernike coefficients on a disc (Noll 1976):
+    2.2698 (-1)^((n+n'-2m)/2) sqrt((n+1)(n'+1)) Gamma((n+n'-5/3)/2) (D/r0)^(5/3) /
+    [Gamma((n-n'+17/3)/2) Gamma((n'-n+17/3)/2) Gamma((n+n'+23/3)/2)], zero unless m = m'
+    (and j, j' of equal parity for m != 0)."""
+    from scipy.special import gamma
+    n, m = md.noll_to_nm(j)
+    n2, m2 = md.noll_to_nm(jp)
+    if abs(m) != abs(m2) or (m != 0 and j % 2 != jp % 2):
+        return 0.0
+    K = 2.2698 * (-1) ** ((n + n2 - 2 * abs(m)) // 2) * math.sqrt((n + 1) * (n2 + 1))
+    return K * gamma((n + n2 - 5 / 3) / 2) / (gamma((n - n2 + 17 / 3) / 2) * gamma((n2 - n + 17 / 3) / 2)
+                                              * gamma((n + n2 + 23 / 3) / 2)) * D_r0 ** (5 / 3)
+
+
+def test_modal_covariance_kolmogorov_zernike_variances():
+    """Radial orders 2 and 3 (j = 4 .. 10) and spherical (j = 11) against Noll's
+    closed form. (Tip and tilt are left out: their integrand is singular at f = 0,
+    which a discrete frequency grid undersamples.)"""
+    Np, D, r0 = 64, 8.0, 0.5
+    mask = op.pupil_mask(Np, 0.0)
+    M = _piston_free(md.modal_basis(Np, 0.0, 10))           # j = 2 .. 11
+    C = md.modal_covariance(M, mask, D / Np, r0, math.inf, 8)
+    for k, j in enumerate(range(2, 12)):
+        if j >= 4:
+            assert abs(C[k, k] / _noll_covariance(j, j, D / r0) - 1) < 0.03, j
+    # the closed form itself against Noll's tabulated variances: tilt 0.449, focus 0.0232
+    assert abs(_noll_covariance(2, 2, 1.0) - 0.449) < 0.01
+    assert abs(_noll_covariance(4, 4, 1.0) - 0.0232) < 0.0005
+
+
+def test_kl_basis_diagonalises_and_spans_the_zernike_space():
+    Np = 32
+    mask = op.pupil_mask(Np, 0.1)
+    M = md.modal_basis(Np, 0.1, 20)
+    C = md.modal_covariance(M, mask, 8.0 / Np, 0.15, 25.0, 4)
+    K, w = md.kl_basis(M, C)
+    n = mask.sum()
+    assert np.max(np.abs(K.T @ K / n - np.eye(20))) < 1e-10          # orthonormal
+    assert np.all(np.diff(w) <= 0) and w[-1] > 0                     # decreasing variances
+    Ck = (K.T @ M / n) @ C @ (M.T @ K / n)                           # covariance of KL coefficients
+    assert np.max(np.abs(Ck - np.diag(w))) < 1e-9 * w[0]
+    assert np.max(np.abs(K @ K.T - M @ M.T)) / n < 1e-10             # same span
+    assert np.all(K[np.argmax(np.abs(K), axis=0), np.arange(20)] > 0)
