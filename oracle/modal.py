@@ -148,11 +148,17 @@ def modal_covariance(M: np.ndarray, mask: np.ndarray, dx: float, r0: float, L0: 
 def kl_basis(M: np.ndarray, C: np.ndarray):
     """Karhunen-Loeve modes within the span of the orthonormal basis M: M U with
     C = U diag(w) U^T, w decreasing (the coefficient variances). Sign: each mode
-    is positive at its largest-magnitude pixel (first such pixel), a convention
-    that does not depend on the signs of M. Returns (M U, w)."""
+    has a positive inner product with sign_pattern (a fixed pattern without the
+    pupil's symmetries), a convention independent of the signs of M. Returns
+    (M U, w); M's rows are the pupil pixels of `mask` in row-major order."""
     w, U = np.linalg.eigh(C)
     order = np.argsort(-w, kind="stable")
     w, U = w[order], U[:, order]
     K = M @ U
-    idx = np.argmax(np.abs(K), axis=0)
-    return K * np.sign(K[idx, np.arange(K.shape[1])]), w
+    return K * np.sign(sign_pattern(M.shape[0]) @ K), w
+
+
+def sign_pattern(n_pix: int) -> np.ndarray:
+    """cos(0.73 p + 0.11 + 1.37 sin(0.29 p)) over the pixel list index p."""
+    p = np.arange(n_pix, dtype=np.float64)
+    return np.cos(0.73 * p + 0.11 + 1.37 * np.sin(0.29 * p))

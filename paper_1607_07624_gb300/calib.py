@@ -103,6 +103,68 @@ def zernike_basis(Np: int, pupil_flat_idx: np.ndarray, n_modes: int) -> np.ndarr
     return Q * sgn * math.sqrt(npix)
 
 
+def modal_covariance(basis: np.ndarray, pix: np.ndarray, Np: int, pitch_m: float, r0_m: float, L0_m: float,
+                     pad: int = 2, chunk: int = 64) -> np.ndarray:
+    """Covariance [rad^2 at the r0 wavelength] of the coefficients a = (1/n) B^T phi
+    of von Karman turbulence on the basis B (n pupil pixels x modes):
+    (1/n^2) sum over the (pad Np)^2 frequency lattice of PSD(f) df^2 Re(conj(Bhat_i) Bhat_j).
+    Real mode maps have Hermitian spectra, so only the half spectrum of rfft2 is
+    formed, each column other than 0 and the Nyquist one counted twice, and the
+    complex sum splits into two real matrix products."""
+    P = pad * Np
+    n, nm = basis.shape
+    df = 1.0 / (P * pitch_m)
+    fy = np.fft.fftfreq(P, d=pitch_m)
+    fx = np.fft.rfftfreq(P, d=pitch_m)
+    f2 = np.add.outer(fy * fy, fx * fx)
+    outer = 0.0 if math.isinf(L0_m) else (1.0 / L0_m) ** 2
+    with np.errstate(divide="ignore"):
+        psd = _psd_scale() * r0_m ** (-5.0 / 3.0) * (f2 + outer) ** (-11.0 / 6.0)
+    if math.isinf(L0_m):
+        psd[0, 0] = 0.0
+    mult = np.full(fx.size, 2.0)
+    mult[0] = 1.0
+    if P % 2 == 0:
+        mult[-1] = 1.0
+    w = (psd * mult[None, :] * df * df).ravel()
+    rows, cols = np.divmod(np.asarray(pix, dtype=np.int64), Np)
+    re = np.empty((nm, w.size))
+    im = np.empty((nm, w.size))
+    for c0 in range(0, nm, chunk):
+        c1 = min(nm, c0 + chunk)
+        g = np.zeros((c1 - c0, P, P))
+        g[:, rows, cols] = basis[:, c0:c1].T
+        spec = np.fft.rfft2(g).reshape(c1 - c0, -1)
+        re[c0:c1] = spec.real
+        im[c0:c1] = spec.imag
+    C = (re * w) @ re.T + (im * w) @ im.T
+    return C / (float(n) * n)
+
+
+_KL_CACHE: dict = {}
+
+
+def kl_basis(Np: int, pix: np.ndarray, n_modes: int, pitch_m: float, r0_m: float, L0_m: float,
+             pad: int = 2) -> np.ndarray:
+    """Karhunen-Loeve modes of von Karman turbulence within the span of the first
+    n_modes Zernike modes: eigenvectors of their coefficient covariance, variances
+    decreasing, each mode with a positive inner product with the fixed pattern
+    cos(0.73 p + 0.11 + 1.37 sin(0.29 p)) over the pixel index p (a sign that does
+    not depend on the Zernike signs); float64 (n pixels x n_modes), orthonormal
+    (B^T B = n I). Cached per geometry."""
+    key = (Np, hash(np.asarray(pix).tobytes()), n_modes, pitch_m, r0_m, L0_m, pad)
+    if key not in _KL_CACHE:
+        Z = zernike_basis(Np, pix, n_modes)
+        C = modal_covariance(Z, pix, Np, pitch_m, r0_m, L0_m, pad)
+        w, U = np.linalg.eigh(0.5 * (C + C.T))
+        U = U[:, np.argsort(-w, kind="stable")]
+        K = Z @ U
+        q = np.arange(K.shape[0], dtype=np.float64)
+        K *= np.sign(np.cos(0.73 * q + 0.11 + 1.37 * np.sin(0.29 * q)) @ K)
+        _KL_CACHE[key] = K
+    return _KL_CACHE[key]
+
+
 def pseudo_inverse(IM: np.ndarray, rcond: float = 1e-3) -> np.ndarray:
     """FP64 SVD pseudo-inverse, singular values below rcond * max dropped."""
     U, s, Vt = np.linalg.svd(np.asarray(IM, dtype=np.float64), full_matrices=False)

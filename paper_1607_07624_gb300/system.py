@@ -30,7 +30,8 @@ class SCAOSystem:
     """Single-conjugate AO loop with a modulated pyramid, for one configuration.
 
     screens: float32 (L, S, S) OPD [nm] (host numpy or None: generated from the
-    configuration's seeds); basis: float (n_pix, n_modes) (None: Zernike);
+    configuration's seeds); basis: float (n_pix, n_modes) (None: the configuration's
+    basis, Zernike or KL);
     R: reconstruction matrix (None: calibrated by push-pull on the GPU);
     autotune: True (time the pyramid launch geometries on the GPU), False (library
     default) or (rows_per_cta, row_chunks, col_groups) to set one."""
@@ -60,7 +61,10 @@ class SCAOSystem:
                                     cfg.wavelength_nm, cfg.obs, self.valid)
         # DM
         if basis is None:
-            basis = calib.zernike_basis(cfg.Np, self.pix, cfg.n_modes)
+            if cfg.basis == "kl":
+                basis = calib.kl_basis(cfg.Np, self.pix, cfg.n_modes, cfg.dx, cfg.r0_m, cfg.L0_m)
+            else:
+                basis = calib.zernike_basis(cfg.Np, self.pix, cfg.n_modes)
         self.basis = np.ascontiguousarray(basis, dtype=np.float32)
         self.n_modes = self.basis.shape[1]
         # a DM object holds only the basis: loops of one geometry may share one (dm=)

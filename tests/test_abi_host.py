@@ -98,3 +98,32 @@ def test_product_pinv_matches_oracle():
     from paper_1607_07624_gb300 import calib
     IM = np.random.default_rng(5).standard_normal((80, 30))
     assert np.max(np.abs(calib.pseudo_inverse(IM) - md.pseudo_inverse(IM))) < 1e-12
+
+
+def test_product_kl_basis_matches_oracle():
+    """calib.kl_basis (half-spectrum real products, MGS Zernikes) against the oracle's
+    (full complex spectrum, QR Zernikes): equal variances, and equal modes up to the
+    rotation inside groups of equal variance (cos/sin pairs)."""
+    from oracle import modal as md
+    from oracle import optics as op
+    from paper_1607_07624_gb300 import calib
+    Np, nm, dx, r0, L0 = 32, 20, 8.0 / 32, 0.15, 25.0
+    mask = op.pupil_mask(Np, 0.1)
+    pix = np.flatnonzero(mask.ravel())
+    K = calib.kl_basis(Np, pix, nm, dx, r0, L0, pad=4)
+    M = md.modal_basis(Np, 0.1, nm)
+    Ko, w = md.kl_basis(M, md.modal_covariance(M, mask, dx, r0, L0, 4))
+    n = pix.size
+    Cp = calib.modal_covariance(K, pix, Np, dx, r0, L0, pad=4)
+    assert np.max(np.abs(np.diag(Cp) - w)) <= 1e-8 * w[0]
+    i = 0
+    while i < nm:                                   # groups of (nearly) equal variance
+        j = i + 1
+        while j < nm and abs(w[j] - w[i]) <= 1e-6 * w[i]:
+            j += 1
+        Pp = K[:, i:j] @ K[:, i:j].T / n
+        Po = Ko[:, i:j] @ Ko[:, i:j].T / n
+        assert np.max(np.abs(Pp - Po)) < 1e-7, (i, j)
+        if j - i == 1:
+            assert np.max(np.abs(K[:, i] - Ko[:, i])) < 1e-6
+        i = j
