@@ -152,8 +152,9 @@ def algorithmic_work(cfg, n_pix, n_valid, n_modes, n_s_rows, recon_bytes_per_el)
     N, Np, K, L = cfg.N, cfg.Np, cfg.K, len(cfg.layers)
     fft_pair = 2 * 5.0 * N * math.log2(N) + 6.0 * N           # FFT + mask + IFFT
     return {
-        "atmo_pupil_kernel": {"bound": "hbm", "bytes": 4.0 * L * (Np + 1) ** 2 + 8.0 * n_pix},
-        "residual_kernel": {"bound": "hbm", "bytes": 4.0 * n_modes * n_pix + 12.0 * n_pix + 4.0 * n_modes},
+        # basis block, pixel list and output, command, the layers' pupil footprints
+        "residual_kernel": {"bound": "hbm", "bytes": 4.0 * n_modes * n_pix + 8.0 * n_pix + 4.0 * n_modes
+                            + 4.0 * L * (Np + 1) ** 2},
         "pyr_rows_kernel": {"bound": "alu", "flops": n_s_rows * Np * (fft_pair + 6.0 * Np)},
         "pyr_cols_kernel": {"bound": "alu", "flops": K * N * (fft_pair + 6.0 * Np + 3.0 * N)},
         "slopes_kernel": {"bound": "latency", "bytes": 16.0 * n_valid + 8.0 * 2 * n_valid},
@@ -258,7 +259,8 @@ def bench_other_workloads(timed, peaks, n_steps=200):
         for _ in range(10):
             for k, v in pas.pas_loop_profile(s3.loop, s3.ctx, 1).items():
                 prof[k] = prof.get(k, 0.0) + v / 10
-        res_bytes = 4.0 * cfg3.n_modes * pix.size + 12.0 * pix.size
+        res_bytes = (4.0 * cfg3.n_modes * pix.size + 8.0 * pix.size + 4.0 * cfg3.n_modes
+                     + 4.0 * len(cfg3.layers) * (cfg3.Np + 1) ** 2)
         res_gbs = res_bytes / (prof["residual_kernel"] * 1e-3) / 1e9
         out[cfg3.name] = {"loop_steps_per_s": sps, "pwfs_frames_per_s": fr, "tuning": list(s3.tuning),
                           "kernel_ms": prof,
@@ -295,7 +297,7 @@ def bench_batch(timed, n_loops=64, n_steps=100):
         wfe = np.array([s.wfe_nm(n_steps) for s in systems])
         return {"workload": f"{n_loops} realisations of {cfg.name} (own screens each)",
                 "loop_steps_per_s": n_loops * n_steps / (ms * 1e-3), "batch_steps_per_s": n_steps / (ms * 1e-3),
-                "graph_launches_per_step": 1, "kernels_per_step": 6 * n_loops,
+                "graph_launches_per_step": 1, "kernels_per_step": pas.PAS_LOOP_KERNELS * n_loops,
                 "wfe_nm_mean_over_realisations": float(wfe[:, n_steps // 5:].mean())}
     finally:
         if batch is not None:
@@ -346,7 +348,7 @@ def bench_batched_workload(timed, n_steps=30):
                   for sh in shared.values()]
         return {"loops": len(systems), "groups": groups, "ms_per_batch_step": ms / n_steps,
                 "loop_steps_per_s": len(systems) * n_steps / (ms * 1e-3), "graph_launches_per_step": 1,
-                "kernels_per_step": 6 * len(systems),
+                "kernels_per_step": pas.PAS_LOOP_KERNELS * len(systems),
                 "note": "random bases and reconstructors of the workload's shapes: timing only"}
     finally:
         if batch is not None:
@@ -694,7 +696,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 4 * sysg.n_modes + 8},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": pas.PAS_LOOP_KERNELS * args.steps,
         "clocks": clocks,
         "learned_reconstructor": mlp_info,
         **extra,

@@ -304,11 +304,11 @@ void pas_loop_destroy(pas_loop_t loop);
  * gaps), synchronising after each, and write the mean duration in ms of each
  * kernel into h_ms[0 .. *n_kernels-1] (cap >= PAS_LOOP_KERNELS). The steps advance
  * the loop like pas_loop_step.
- * The step's kernels, in order: atmosphere, residual (- DM shape), pyramid
- * rows pass, pyramid columns pass (+ detector frame and noise in the last CTA of
- * each detector column), slopes, reconstructor + integrator (+ step counter);
+ * The step's kernels, in order: residual (wind-shifted layers sampled at the
+ * pupil pixels, - DM shape), pyramid rows pass, pyramid columns pass (+ detector
+ * frame and noise in the last CTA of each detector column), slopes, reconstructor + integrator (+ step counter);
  * with a learned reconstructor attached the last entry spans its layer kernels. */
-#define PAS_LOOP_KERNELS 6
+#define PAS_LOOP_KERNELS 5
 pas_status pas_loop_profile(pas_loop_t loop, int32_t n_steps, float* h_ms, int32_t cap,
                             int32_t* n_kernels);
 /* Name of kernel `idx` of pas_loop_profile (static string), NULL if out of range. */

@@ -88,29 +88,6 @@ __device__ inline float atmo_sample_any(const AtmoArgs& a, const int* six, const
   }
 }
 
-// Atmosphere on the pupil pixels only (the loop's first kernel): one thread per
-// pixel, all 4 L taps issued at once.
-template <int LT>
-__global__ void __launch_bounds__(256) atmo_pupil_kernel(AtmoArgs a, const int* pix, int n_pix,
-                                                         const long long* d_step, float* out) {
-  __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
-  __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
-  pdl_trigger();
-  pdl_wait();
-  const long long step = *d_step;
-  if (threadIdx.x < a.L) {
-    layer_shift(a.vx[threadIdx.x], step, a.S, &six[threadIdx.x], &sfx[threadIdx.x]);
-    layer_shift(a.vy[threadIdx.x], step, a.S, &siy[threadIdx.x], &sfy[threadIdx.x]);
-  }
-  __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n_pix) return;
-  const int flat = pix[p];
-  const int i = flat / a.Np, j = flat - i * a.Np;
-  out[flat] = LT > 0 ? atmo_sample_fixed<(LT > 0 ? LT : 1)>(a, six, siy, sfx, sfy, i, j)
-                     : atmo_sample(a, six, siy, sfx, sfy, i, j);
-}
-
 __global__ void atmo_kernel(AtmoArgs a, const long long* d_step, long long h_step, float* out) {
   __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
   __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
@@ -127,8 +104,8 @@ __global__ void atmo_kernel(AtmoArgs a, const long long* d_step, long long h_ste
   }
 }
 
-// Residual over the pupil pixel list: out[pix] = atm - dm_sign * (M c), atm read
-// from opd_atm (or zero). CTA: one 64-pixel tile, whose basis block [n_m][64] is
+// Residual over the pupil pixel list: out[pix] = atm - dm_sign * (M c), atm the
+// layers sampled at the step (a.atmo.L > 0), else read from opd_atm (or zero). CTA: one 64-pixel tile, whose basis block [n_m][64] is
 // one contiguous stretch of memory. Each thread owns VEC consecutive pixels (one
 // 16-byte load: 4 float or 8 bfloat16 values) and every ROWS-th mode: it streams
 // those rows straight from global memory (a warp reads whole 256-byte or 128-byte
@@ -165,6 +142,10 @@ __device__ __forceinline__ void unpack16(const uint4& u, float* f) {
   }
 }
 
+// With a.atmo.L > 0 the atmosphere is sampled here (the loop's step: layers
+// shifted by the wind of the device step, bilinear taps at the tile's pupil
+// pixels) by the tile's first 64 threads, while the other warps already stream
+// the basis; otherwise it is read from opd_atm (or zero).
 template <typename T>
 __global__ void __launch_bounds__(RES_THREADS) residual_kernel(ResArgs a) {
   constexpr int VEC = 16 / (int)sizeof(T);         // pixels per 16-byte load
@@ -173,6 +154,8 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(ResArgs a) {
   extern __shared__ float c_s[];                    // [n_m]
   __shared__ float red[ROWS][RES_TILE];
   __shared__ double wred[2][RES_THREADS / 32];
+  __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
+  __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
   const int tid = threadIdx.x;
   const T* MT = nullptr;
   if constexpr (sizeof(T) == 4) MT = a.MT;
@@ -191,8 +174,24 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(ResArgs a) {
   const long long step = a.d_step ? *a.d_step : a.h_step;
   const float* cmd = a.cmd;
   if (a.cmd_ring) cmd = a.cmd_ring + (size_t)(step % a.delay) * a.n_m;
+  if (tid < a.atmo.L) {
+    layer_shift(a.atmo.vx[tid], step, a.atmo.S, &six[tid], &sfx[tid]);
+    layer_shift(a.atmo.vy[tid], step, a.atmo.S, &siy[tid], &sfy[tid]);
+  }
   for (int m = tid; m < n_m; m += RES_THREADS) c_s[m] = cmd[m];
   __syncthreads();
+  const int base = blockIdx.x * RES_TILE;
+  float atm = 0.f;  // meaningful in the output threads tid < RES_TILE
+  int flat = 0;
+  if (tid < RES_TILE && base + tid < a.n_pix) {
+    flat = a.pix[base + tid];
+    if (a.atmo.L > 0) {
+      const int i = flat / a.atmo.Np, j = flat - i * a.atmo.Np;
+      atm = atmo_sample(a.atmo, six, siy, sfx, sfy, i, j);
+    } else if (a.opd_atm) {
+      atm = a.opd_atm[flat];
+    }
+  }
   float acc[VEC];
 #pragma unroll
   for (int i = 0; i < VEC; ++i) acc[i] = 0.f;
@@ -214,7 +213,6 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(ResArgs a) {
 #pragma unroll
   for (int i = 0; i < VEC; ++i) red[row][col * VEC + i] = acc[i];
   __syncthreads();
-  const int base = blockIdx.x * RES_TILE;
   const int px = tid;
   const int p = base + px;
   double s1 = 0.0, s2 = 0.0;
@@ -222,8 +220,6 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(ResArgs a) {
     float dm = 0.f;
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) dm += red[r][px];
-    const int flat = a.pix[p];
-    const float atm = a.opd_atm ? a.opd_atm[flat] : 0.f;
     const float r = atm - a.dm_sign * dm;
     a.out[flat] = r;
     s1 = r;
@@ -269,25 +265,11 @@ __global__ void integrate_kernel(float* cmd, const float* dmodes, const float* g
 
 int residual_tiles(int n_pix) { return (n_pix + RES_TILE - 1) / RES_TILE; }
 
-pas_status atmo_pupil_launch(pas_ctx_t ctx, const AtmoArgs& a, const int* pix, int n_pix,
-                             const long long* d_step, float* out, cudaStream_t st) {
-  const int blocks = (n_pix + 255) / 256;
-  switch (a.L) {
-    case 1: atmo_pupil_kernel<1><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
-    case 2: atmo_pupil_kernel<2><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
-    case 3: atmo_pupil_kernel<3><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
-    case 4: atmo_pupil_kernel<4><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
-    case 5: atmo_pupil_kernel<5><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
-    case 6: atmo_pupil_kernel<6><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
-    default: atmo_pupil_kernel<0><<<blocks, 256, 0, st>>>(a, pix, n_pix, d_step, out); break;
-  }
-  return check_launch(ctx, "atmosphere kernel launch");
-}
-
 pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, bool pdl) {
   const int tiles = residual_tiles(a.n_pix);
   if (tiles == 0) return PAS_OK;
-  if (a.atmo.L != 0) return set_error(ctx, PAS_EINVAL, "residual kernel: the atmosphere comes from opd_atm");
+  if (a.atmo.L < 0 || a.atmo.L > PAS_MAX_LAYERS)
+    return set_error(ctx, PAS_EINVAL, "residual kernel: 0 <= layers <= %d", PAS_MAX_LAYERS);
   const size_t smem = sizeof(float) * (size_t)std::max(a.n_m, 1);
   cudaError_t e;
   if (a.MTb) {

@@ -35,9 +35,6 @@ pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, boo
 int residual_tiles(int n_pix);
 // coeffs = (1/n_pix) M^T opd over the pupil pixels (one CTA per mode).
 pas_status dm_project_launch(pas_dm_t dm, const float* opd, float* coeffs, cudaStream_t st);
-// Summed atmosphere at the device step on the listed pupil pixels of out [Np][Np].
-pas_status atmo_pupil_launch(pas_ctx_t ctx, const AtmoArgs& a, const int* pix, int n_pix,
-                             const long long* d_step, float* out, cudaStream_t st);
 
 }  // namespace pas
 

@@ -42,13 +42,12 @@ struct pas_loop_s {
 // ev (optional): PAS_LOOP_KERNELS + 1 events recorded before each kernel and
 // after the last one.
 static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = nullptr) {
-  // atmosphere into the residual buffer, then residual = atmosphere - M c in place
-  if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
-  pas_status s = pas::atmo_pupil_launch(L->ctx, L->atmo->args, L->dm->d_pix, L->dm->n_pix, L->d_step,
-                                        L->d_opd, st);
-  if (s != PAS_OK) return s;
+  // residual = atmosphere - M c: the residual kernel samples the wind-shifted
+  // layers at its pupil pixels while its other warps stream the basis
+  pas_status s = PAS_OK;
   pas::ResArgs ra = pas::make_res_args(L->dm);
-  ra.opd_atm = L->d_opd;
+  ra.atmo = L->atmo->args;
+  ra.opd_atm = nullptr;
   ra.cmd_ring = L->d_ring;
   ra.delay = L->delay;
   ra.d_step = L->d_step;
@@ -59,8 +58,8 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   // constant-matrix prefetches overlap the predecessor), except when events are
   // recorded between them for profiling
   const bool pdl = ev == nullptr;
-  if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
-  s = pas::residual_launch(L->ctx, ra, st, pdl);
+  if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+  s = pas::residual_launch(L->ctx, ra, st, false);  // the step's first kernel
   if (s != PAS_OK) return s;
   pas::LoopExtra fa;
   fa.frame_ctr = L->d_step;
@@ -70,7 +69,7 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   fa.wfe_hist = L->d_wfe;
   fa.wfe_hist_len = L->hist;
   fa.step = L->d_step;
-  s = pas::pyr_launch(L->pyr, L->d_opd, L->d_frame, L->d_slopes, st, &fa, false, ev ? ev + 2 : nullptr, pdl);
+  s = pas::pyr_launch(L->pyr, L->d_opd, L->d_frame, L->d_slopes, st, &fa, false, ev ? ev + 1 : nullptr, pdl);
   if (s != PAS_OK) return s;
   pas::ReconArgs rc;
   rc.s = L->d_slopes;
@@ -81,9 +80,9 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   rc.step = L->d_step;
   rc.cmd_last = L->d_cmd;
   rc.step_inc = L->d_step;
-  if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
+  if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
   s = L->mlp ? pas::mlp_loop_launch(L->mlp, rc, st, pdl) : pas::recon_launch(L->rec, rc, st, pdl);
-  if (ev) cudaEventRecordWithFlags(ev[6], st, cudaEventRecordExternal);
+  if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
   return s;
 }
 
@@ -279,8 +278,8 @@ pas_status pas_loop_set_mlp(pas_loop_t L, pas_mlp_t m) {
 }
 
 const char* pas_loop_kernel_name(int32_t idx) {
-  static const char* names[PAS_LOOP_KERNELS] = {"atmo_pupil_kernel", "residual_kernel", "pyr_rows_kernel",
-                                                "pyr_cols_kernel", "slopes_kernel", "recon_kernel"};
+  static const char* names[PAS_LOOP_KERNELS] = {"residual_kernel", "pyr_rows_kernel", "pyr_cols_kernel",
+                                                "slopes_kernel", "recon_kernel"};
   return (idx >= 0 && idx < PAS_LOOP_KERNELS) ? names[idx] : nullptr;
 }
 

@@ -22,6 +22,7 @@ _lib = C.CDLL(LIB_PATH)
 
 PAS_OK, PAS_EINVAL, PAS_ENOMEM, PAS_ECUDA, PAS_ETIMEOUT, PAS_ESTATE = range(6)
 PAS_FP32, PAS_BF16 = 0, 1
+PAS_LOOP_KERNELS = 5          # kernels of one loop step (the header's define)
 STATUS_NAMES = {0: "PAS_OK", 1: "PAS_EINVAL", 2: "PAS_ENOMEM", 3: "PAS_ECUDA", 4: "PAS_ETIMEOUT",
                 5: "PAS_ESTATE"}
 

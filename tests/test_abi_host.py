@@ -35,6 +35,14 @@ def test_every_declared_symbol_is_exported(lib):
     assert sorted(lib.EXPORTED) == names
 
 
+def test_loop_kernel_count_matches_header(lib):
+    src = open(os.path.join(ROOT, "include", "pas.h")).read()
+    n = int(re.search(r"#define PAS_LOOP_KERNELS (\d+)", src).group(1))
+    assert lib.PAS_LOOP_KERNELS == n
+    names = [lib.pas_loop_kernel_name(k) for k in range(n)]
+    assert all(names) and lib.pas_loop_kernel_name(n) is None
+
+
 def test_version_and_supported_sizes(lib):
     assert lib.pas_version() >= 100
     for N in (16, 24, 32, 48, 64, 128, 480, 960):
