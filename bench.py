@@ -48,7 +48,8 @@ def parse():
                     help="skip the BF16 loop and the other workloads (64 px, ELT-scale)")
     ap.add_argument("--soak", type=float, default=1.5, help="seconds of untimed steps before timing")
     ap.add_argument("--tuning", default=None,
-                    help="pyramid launch geometry rows_per_cta,row_chunks,col_groups (default: autotuned)")
+                    help="pyramid launch geometry rows_per_cta,row_chunks,col_groups[,col_split] "
+                         "(default: autotuned)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-budget-s", type=float, default=20.0)
     return ap.parse_args()
@@ -684,7 +685,8 @@ def main():
                                f"{cfg.read_noise_e} e- RON",
                    "l2": "flushed (256 MiB write) between timed steps", "recon": args.recon,
                    "parallelism": f"replicas x{world}", "graph": "whole step, CUDA graph",
-                   "pyramid_tuning": dict(zip(("rows_per_cta", "row_chunks", "col_groups"), sysg.tuning))},
+                   "pyramid_tuning": dict(zip(("rows_per_cta", "row_chunks", "col_groups", "col_split"),
+                                             sysg.tuning))},
         "pwfs_frames_per_s": frames_per_s,
         "roofline": None if dom is None else {"bound": dom["bound"], "achieved": dom["achieved"],
                                                "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"],

@@ -208,20 +208,23 @@ void pas_pyr_destroy(pas_pyr_t pyr);
 /* Launch geometry of the pyramid kernels: rows pass = pupil rows per CTA and the
  * number of chunks the distinct sin(theta_k) values are split into (the OPD
  * phasor of a row is computed once per chunk); columns pass = number of groups
- * of modulation points (each CTA accumulates |g|^2 over its group). */
+ * of modulation points (each CTA accumulates |g|^2 over its group) and the
+ * number of CTAs sharing one detector column's b = N / (2 n_sub) fine columns
+ * (smaller CTAs, more of them resident per SM). */
 typedef struct {
     int32_t rows_per_cta;   /* 1, 2, 4 or 8 */
     int32_t row_chunks;     /* 1 .. number of distinct sin(theta_k) */
     int32_t col_groups;     /* 1 .. K */
+    int32_t col_split;      /* 1, or a divisor <= 8 of b when b is an integer */
 } pas_pyr_tuning;
 pas_status pas_pyr_get_tuning(pas_pyr_t pyr, pas_pyr_tuning* h_out);
 /* Values are rounded to the nearest realisable split; results do not depend on
  * the geometry beyond float32 summation order of the modulation groups. */
 pas_status pas_pyr_set_tuning(pas_pyr_t pyr, const pas_pyr_tuning* h_t);
 /* Autotuner: times each candidate geometry (rows_per_cta 2/4/8 x every chunk
- * count; every column group count) with CUDA events over `iters` launches on
- * d_opd (device [Np][Np]), keeps the fastest and writes it to h_out (may be
- * NULL). Synchronous; overwrites the object's internal frame; do not call while
+ * count; every column group count x every column split) with CUDA events over
+ * `iters` launches on d_opd (device [Np][Np]), keeps the fastest and writes it
+ * to h_out (may be NULL). Synchronous; overwrites the object's internal frame; do not call while
  * the context stream is being captured. */
 pas_status pas_pyr_autotune(pas_pyr_t pyr, const float* d_opd, int32_t iters, pas_pyr_tuning* h_out);
 

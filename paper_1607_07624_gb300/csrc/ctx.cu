@@ -73,7 +73,7 @@ int64_t obstruction_threshold(int Np, double obs) {
 
 extern "C" {
 
-int pas_version(void) { return 100; }
+int pas_version(void) { return 101; }
 
 pas_status pas_ctx_create(void* cuda_stream, pas_ctx_t* out) {
   if (!out) return pas::set_global_error(PAS_EINVAL, "pas_ctx_create: out is NULL");

@@ -42,40 +42,99 @@ __device__ inline u32x4 noise_block(uint64_t seed, uint32_t pixel, uint64_t fram
                        (uint32_t)(seed >> 32));
 }
 
-__device__ inline float poisson_draw(float lam, uint64_t seed, uint32_t pixel, uint64_t frame) {
-  if (!(lam > 0.f)) return 0.f;
-  u32x4 w = noise_block(seed, pixel, frame, 0);
-  if (lam < 10.f) {
-    const float u = u01f(w.v[2]);
-    float p = expf(-lam);
-    float F = p;
-    int k = 0;
-    while (u > F && k < 256) {
-      ++k;
-      p = __fmul_rn(p, __fmul_rn(lam, __frcp_rn((float)k)));
-      F = __fadd_rn(F, p);
-    }
-    return (float)k;
+// Inversion by sequential search (lambda < 10) on block 0 word 2.
+__device__ inline float poisson_small(float lam, const u32x4& w0) {
+  const float u = u01f(w0.v[2]);
+  float p = expf(-lam);
+  float F = p;
+  int k = 0;
+  while (u > F && k < 256) {
+    ++k;
+    p = __fmul_rn(p, __fmul_rn(lam, __frcp_rn((float)k)));
+    F = __fadd_rn(F, p);
   }
-  const float slam = sqrtf(lam), loglam = logf(lam);
-  const float b = __fadd_rn(0.931f, __fmul_rn(2.53f, slam));
-  const float a = __fadd_rn(-0.059f, __fmul_rn(0.02483f, b));
-  const float invalpha = __fadd_rn(1.1239f, __fdiv_rn(1.1328f, __fsub_rn(b, 3.4f)));
-  const float vr = __fsub_rn(0.9277f, __fdiv_rn(3.6224f, __fsub_rn(b, 2.0f)));
-  for (uint32_t blk = 0; blk < 64; ++blk) {
-    if (blk > 0) w = noise_block(seed, pixel, frame, blk);
+  return (float)k;
+}
+
+// Constants of the PTRS rejection for one lambda >= 10.
+struct Ptrs {
+  float lam, loglam, b, a, invalpha, vr;
+  __device__ explicit Ptrs(float l) : lam(l) {
+    const float slam = sqrtf(lam);
+    loglam = logf(lam);
+    b = __fadd_rn(0.931f, __fmul_rn(2.53f, slam));
+    a = __fadd_rn(-0.059f, __fmul_rn(0.02483f, b));
+    invalpha = __fadd_rn(1.1239f, __fdiv_rn(1.1328f, __fsub_rn(b, 3.4f)));
+    vr = __fsub_rn(0.9277f, __fdiv_rn(3.6224f, __fsub_rn(b, 2.0f)));
+  }
+  // One candidate from the words (2, 3) of a counter block: true with *k if accepted.
+  __device__ bool attempt(const u32x4& w, float* k_out) const {
     const float U = __fsub_rn(u01f(w.v[2]), 0.5f);
     const float V = u01f(w.v[3]);
     const float us = __fsub_rn(0.5f, fabsf(U));
     const float k = floorf(__fadd_rn(__fadd_rn(__fmul_rn(__fadd_rn(__fdiv_rn(__fmul_rn(2.0f, a), us), b), U), lam), 0.43f));
-    if (us >= 0.07f && V <= vr) return k;
-    if (k < 0.f || (us < 0.013f && V > us)) continue;
+    *k_out = k;
+    if (us >= 0.07f && V <= vr) return true;
+    if (k < 0.f || (us < 0.013f && V > us)) return false;
     const float lhs = __fsub_rn(__fadd_rn(logf(V), logf(invalpha)),
                                 logf(__fadd_rn(__fdiv_rn(a, __fmul_rn(us, us)), b)));
     const float rhs = __fsub_rn(__fadd_rn(-lam, __fmul_rn(k, loglam)), lgammaf(__fadd_rn(k, 1.0f)));
-    if (lhs <= rhs) return k;
+    return lhs <= rhs;
+  }
+};
+
+constexpr uint32_t PTRS_MAX_BLOCKS = 64;  // candidates before the rounded-mean fallback
+
+__device__ inline float poisson_draw(float lam, uint64_t seed, uint32_t pixel, uint64_t frame) {
+  if (!(lam > 0.f)) return 0.f;
+  u32x4 w = noise_block(seed, pixel, frame, 0);
+  if (lam < 10.f) return poisson_small(lam, w);
+  const Ptrs P(lam);
+  for (uint32_t blk = 0; blk < PTRS_MAX_BLOCKS; ++blk) {
+    if (blk > 0) w = noise_block(seed, pixel, frame, blk);
+    float k;
+    if (P.attempt(w, &k)) return k;
   }
   return floorf(lam + 0.5f);
+}
+
+// The same draw by a group of g adjacent lanes (g = 1, 2, 4 or 8, groups aligned in
+// the warp; lane `sub` of its group): in round r the lanes try the candidates of
+// blocks r g + sub side by side and the group keeps the first accepted one in block
+// order, which is the candidate the sequential search accepts, so the result equals
+// poisson_draw's. Every lane of the warp must call it (warp-wide votes); `active`
+// false for lanes without a pixel. Returned to every lane of the group.
+__device__ inline float poisson_draw_group(float lam, uint64_t seed, uint32_t pixel, uint64_t frame, int sub,
+                                           int g, bool active) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, gbase = lane - sub;
+  const unsigned gmask = (g == 32 ? FULL : ((1u << g) - 1u)) << gbase;
+  bool done = !active || !(lam > 0.f);
+  float result = 0.f;
+  if (!done && lam < 10.f) {
+    if (sub == 0) result = poisson_small(lam, noise_block(seed, pixel, frame, 0));
+    done = true;
+  }
+  // the small-lambda result lives in the group's first lane
+  const float small = __shfl_sync(FULL, result, gbase);
+  if (active && lam > 0.f && lam < 10.f) result = small;
+  const Ptrs P(done ? 10.f : lam);
+  for (uint32_t r = 0; r < PTRS_MAX_BLOCKS; r += (uint32_t)g) {
+    if (!__any_sync(FULL, !done)) break;
+    const uint32_t blk = r + (uint32_t)sub;
+    bool acc = false;
+    float k = 0.f;
+    if (!done && blk < PTRS_MAX_BLOCKS) acc = P.attempt(noise_block(seed, pixel, frame, blk), &k);
+    const unsigned m = __ballot_sync(FULL, acc) & gmask;
+    const int first = m ? __ffs(m) - 1 : lane;
+    const float kf = __shfl_sync(FULL, k, first);
+    if (!done && m) {
+      result = kf;
+      done = true;
+    }
+  }
+  if (!done) result = floorf(lam + 0.5f);
+  return result;
 }
 
 __device__ inline float gaussian_draw(uint64_t seed, uint32_t pixel, uint64_t frame) {
@@ -90,6 +149,16 @@ __device__ inline float noisy_pixel(float v, float scale, float ron, uint64_t se
   if (!(scale > 0.f)) return v;
   float e = poisson_draw(__fmul_rn(v, scale), seed, pixel, frame);
   if (ron > 0.f) e = __fadd_rn(e, __fmul_rn(ron, gaussian_draw(seed, pixel, frame)));
+  return e;
+}
+
+// noisy_pixel by a group of g adjacent lanes (poisson_draw_group's contract; scale
+// and ron uniform across the warp). Same value as noisy_pixel, in every lane.
+__device__ inline float noisy_pixel_group(float v, float scale, float ron, uint64_t seed, uint32_t pixel,
+                                          uint64_t frame, int sub, int g, bool active) {
+  if (!(scale > 0.f)) return v;
+  float e = poisson_draw_group(__fmul_rn(v, scale), seed, pixel, frame, sub, g, active);
+  if (ron > 0.f && active) e = __fadd_rn(e, __fmul_rn(ron, gaussian_draw(seed, pixel, frame)));
   return e;
 }
 

@@ -68,7 +68,8 @@ struct ColArgs {
   const float2* tilt;   // [K][Np] (-1)^i exp(2 pi i (i - ci) alpha_k): tilt_x + input ramp
   const int* kmap;      // [K] -> rows-pass index
   float* part;          // [G][nd][nd]
-  int Np, off, K, kper, nd, b;  // b: warps per CTA (fine columns of one detector column)
+  int Np, off, K, kper, nd, b;  // b: fine columns of one detector column (integer binning)
+  int split;            // CTAs per detector column and group, each b / split fine columns
   int frac;             // detector pixels of N / nd fine pixels, N / nd not an integer
   FrameArgs fin;
 };
@@ -175,18 +176,38 @@ __device__ inline double block_sum(double v, double* red) {
 }
 
 // Column q of the detector: sum of the G groups' partials / K, noise, and the
-// column's flux over the valid sub-apertures' pixels (run by the column's last CTA).
-__device__ void finish_column(const FrameArgs& f, const float* part, int q, int nd, double* red) {
-  const long long fidx = f.frame_ctr ? *f.frame_ctr : 0;
+// column's flux over the valid sub-apertures' pixels (run by the column's last CTA,
+// on the step's critical path: the partials are fetched 8 at a time and summed in
+// group order; g lanes per pixel share the photon-noise rejection loop).
+// fidx: the frame counter, read by the caller before the handshake.
+__device__ __noinline__ void finish_column(const FrameArgs& f, const float* part, int q, int nd, double* red,
+                              long long fidx) {
+  constexpr int BATCH = 8;
+  int g = 1;
+  while (g < 8 && nd * g * 2 <= (int)blockDim.x) g *= 2;
   double flux = 0.0;
-  for (int p = threadIdx.x; p < nd; p += blockDim.x) {
-    const int pix = p * nd + q;
+  for (int t0 = 0; t0 < nd * g; t0 += blockDim.x) {  // the same trip count in every thread
+    const int t = t0 + threadIdx.x;
+    const int p = t / g, sub = t - p * g;
+    const bool active = p < nd;
+    const int pix = (active ? p : 0) * nd + q;
+    const bool valid_pix = active && f.vpix[pix] != 0;
     float v = 0.f;
-    for (int gg = 0; gg < f.G; ++gg) v += __ldcg(part + (size_t)gg * f.np + pix);
+    if (active) {
+      for (int g0 = 0; g0 < f.G; g0 += BATCH) {
+        float tv[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) tv[u] = g0 + u < f.G ? __ldcg(part + (size_t)(g0 + u) * f.np + pix) : 0.f;
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) v += tv[u];  // + 0 leaves the partial sums unchanged
+      }
+    }
     v *= f.invK;
-    v = noisy_pixel(v, f.scale, f.ron, f.seed, (uint32_t)pix, (uint64_t)fidx);
-    f.frame[pix] = v;
-    if (f.vpix[pix]) flux += v;
+    v = noisy_pixel_group(v, f.scale, f.ron, f.seed, (uint32_t)pix, (uint64_t)fidx, sub, g, active);
+    if (active && sub == 0) {
+      f.frame[pix] = v;
+      if (valid_pix) flux += v;
+    }
   }
   flux = block_sum(flux, red);
   if (threadIdx.x == 0) {
@@ -281,7 +302,8 @@ pyr_cols_kernel(ColArgs a) {
   float2* bufs = mk_s + BL;                       // [b][PITCH]
   const int Np = a.Np;
   const int q = blockIdx.x;                       // detector column
-  const int g = blockIdx.y;                       // modulation group
+  const int gh = blockIdx.y;                      // modulation group x column part
+  const int g = gh / a.split, h = gh - g * a.split;
   const int k0 = g * a.kper;
   const int kc = min(a.kper, a.K - k0);
   pdl_trigger();
@@ -291,10 +313,12 @@ pyr_cols_kernel(ColArgs a) {
   __syncthreads();  // twiddles and mask staged
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // the fine columns overlapping detector column q: [q b, (q+1) b) exactly when b is an
-  // integer; [floor(q N/nd), ceil((q+1) N/nd)) otherwise (the edge columns are shared
-  // with the neighbouring detector columns and transformed by both CTAs)
-  const int y0 = a.frac ? (q * N) / a.nd : q * a.b;
-  const int nw = a.frac ? ((q + 1) * N + a.nd - 1) / a.nd - y0 : a.b;
+  // integer, of which this CTA takes part h of `split`; [floor(q N/nd), ceil((q+1) N/nd))
+  // otherwise (the edge columns are shared with the neighbouring detector columns and
+  // transformed by both CTAs)
+  const int bw = blockDim.x >> 5;
+  const int y0 = a.frac ? (q * N) / a.nd : q * a.b + h * bw;
+  const int nw = a.frac ? ((q + 1) * N + a.nd - 1) / a.nd - y0 : bw;
   const int y = y0 + warp;
   float2* buf = bufs + warp * PITCH;
   using OS = OutShape<N>;
@@ -317,7 +341,7 @@ pyr_cols_kernel(ColArgs a) {
     fft_mask_ifft<N>(buf, tw_s, mk_s, lane, load, store);
     __syncwarp();
   }
-  // stage |g|^2 of this column, then bin b x b across the CTA's b columns
+  // stage |g|^2 of this column, then bin b x b over the CTA's columns
   float* accw = reinterpret_cast<float*>(buf);
 #pragma unroll
   for (int jb = 0; jb < OS::NJ0; ++jb) {
@@ -329,15 +353,23 @@ pyr_cols_kernel(ColArgs a) {
   }
   __syncthreads();
   const int nd = a.nd, b = a.b;
-  float* out = a.part + (size_t)g * nd * nd;
+  float* out = a.part + (size_t)gh * nd * nd;
   if (!a.frac) {
-    for (int p = threadIdx.x; p < nd; p += blockDim.x) {
+    // gb adjacent lanes per detector pixel, each over every gb-th column, then a
+    // butterfly sum within the lane group
+    int gb = 1;
+    while (gb < 8 && gb < bw && nd * gb * 2 <= (int)blockDim.x) gb *= 2;
+    for (int t0 = 0; t0 < nd * gb; t0 += blockDim.x) {  // the same trip count in every thread
+      const int t = t0 + threadIdx.x;
+      const int p = t / gb, sub = t - p * gb;
       float sum = 0.f;
-      for (int w = 0; w < b; ++w) {
-        const float* col = reinterpret_cast<const float*>(bufs + w * PITCH);
-        for (int xx = 0; xx < b; ++xx) sum += col[p * b + xx];
-      }
-      out[(size_t)p * nd + q] = sum;
+      if (p < nd)
+        for (int w = sub; w < bw; w += gb) {
+          const float* col = reinterpret_cast<const float*>(bufs + w * PITCH) + p * b;
+          for (int xx = 0; xx < b; ++xx) sum += col[xx];
+        }
+      for (int o = 1; o < gb; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (p < nd && sub == 0) out[(size_t)p * nd + q] = sum;
     }
   } else {
     // area weights: fine pixel i shares |[i nd, (i+1) nd) & [p N, (p+1) N)| / nd of
@@ -360,17 +392,19 @@ pyr_cols_kernel(ColArgs a) {
       out[(size_t)p * nd + q] = sum * inv;
     }
   }
-  // the last of the G groups of column q builds that detector column; the CTA
+  // the last of the G x split CTAs of column q builds that detector column; the CTA
   // that completes the last column computes the slopes
   __shared__ double red[32];
   __shared__ bool flag;
+  // written by earlier kernels: fetched now, its latency hidden by the handshake
+  const long long fidx = a.fin.frame_ctr ? *a.fin.frame_ctr : 0;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) flag = atomicAdd(a.fin.done_col + q, 1u) == (unsigned)a.fin.G - 1;
   __syncthreads();
   if (!flag) return;
   __threadfence();
-  finish_column(a.fin, a.part, q, nd, red);
+  finish_column(a.fin, a.part, q, nd, red, fidx);
 }
 
 
@@ -433,6 +467,7 @@ struct pas_pyr_s {
   pas_pyr_params p{};
   pas::PyrKernels kern{};
   int b = 0, nd = 0, n_s = 0, G = 0, kper = 0, n_valid = 0, n_pupil = 0;
+  int H = 1, h_max = 1;  // columns-pass CTAs per detector column and group (divides b)
   int frac = 0;  // non-integer fine pixels per detector pixel
   int rows = 4, s_chunk = 1, n_schunks = 1;
   int64_t T_obs = 0;
@@ -469,6 +504,15 @@ cudaError_t raise_dyn_smem(const void* func, size_t bytes) {
   if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
   return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
+
+// columns pass with `warps` fine columns per CTA
+size_t cols_smem(pas_pyr_t y, int warps) {
+  return sizeof(float2) * ((size_t)y->kern.tw_n + y->kern.buf_n + (size_t)warps * y->kern.pitch);
+}
+
+// Column splits the columns pass accepts: divisors of b up to 8 (1 alone for
+// non-integer binning, whose CTAs cover overlapping column ranges).
+static bool split_ok(pas_pyr_t y, int H) { return H == 1 || (!y->frac && H >= 1 && H <= 8 && y->b % H == 0); }
 
 size_t rows_smem(pas_pyr_t y, int rows, int s_chunk) {
   return sizeof(float2) * ((size_t)y->kern.tw_n + y->kern.buf_n + (size_t)s_chunk * y->p.Np +
@@ -510,6 +554,7 @@ static void launch_cols(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream
   ca.kper = y->kper;
   ca.nd = y->nd;
   ca.b = y->b;
+  ca.split = y->H;
   ca.frac = y->frac;
   long long* ctr = fa_extra ? fa_extra->frame_ctr : y->d_frame_ctr;
   FrameArgs& fa = ca.fin;
@@ -519,7 +564,7 @@ static void launch_cols(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream
   fa.done_col = y->d_done_col;
   fa.frame_ctr = ctr;
   fa.ctr_increment = increment_ctr ? 1 : 0;
-  fa.G = y->G;
+  fa.G = y->G * y->H;
   fa.np = y->nd * y->nd;
   fa.invK = 1.0f / (float)p.K;
   fa.scale = y->photon_scale;
@@ -532,12 +577,13 @@ static void launch_cols(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream
   fa.n_sub = p.n_sub;
   fa.local_norm = p.local_norm;
   fa.wfe = fa_extra ? *fa_extra : LoopExtra();
-  dim3 gc(y->nd, y->G);
+  dim3 gc(y->nd, y->G * y->H);
+  const int warps = y->b / y->H;
   // the columns pass starts after the rows pass has finished: launched early, its
   // CTAs (up to 3 per SM) wait on the SMs while the rows pass runs and slow it
   // (measured on the 480 grid: 84 us per loop step this way, 89-99 us with the
   // early launch)
-  launch_k(y->kern.cols, gc, dim3(y->b * 32), y->smem_cols, st, false, ca);
+  launch_k(y->kern.cols, gc, dim3(warps * 32), cols_smem(y, warps), st, false, ca);
 }
 
 static void launch_slopes(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream_t st,
@@ -721,7 +767,9 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   y->n_schunks = (y->n_s + 3) / 4;
   y->s_chunk = (y->n_s + y->n_schunks - 1) / y->n_schunks;
   y->smem_rows = pas::rows_smem(y, pas::MAX_ROWS_PER_CTA, y->n_s);  // largest candidate
-  y->smem_cols = sizeof(float2) * ((size_t)kern.tw_n + kern.buf_n + (size_t)b * kern.pitch);
+  y->smem_cols = pas::cols_smem(y, b);  // largest: one CTA per detector column and group
+  for (int H = 2; H <= 8; ++H)
+    if (pas::split_ok(y, H)) y->h_max = H;
 
   pas_status st = PAS_OK;
   auto A = [&](void** ptr, size_t bytes) {
@@ -736,7 +784,7 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   A((void**)&y->d_beta, sizeof(float) * y->n_s);
   A((void**)&y->d_kmap, sizeof(int) * p.K);
   A((void**)&y->d_H, sizeof(float2) * (size_t)y->n_s * p.N * p.Np);
-  A((void**)&y->d_part, sizeof(float) * (size_t)p.K * y->nd * y->nd);  // G <= K groups
+  A((void**)&y->d_part, sizeof(float) * (size_t)p.K * y->h_max * y->nd * y->nd);  // G <= K groups x split
   A((void**)&y->d_frame, sizeof(float) * y->nd * y->nd);
   A((void**)&y->d_frame_ctr, sizeof(long long));
   A((void**)&y->d_vpix, (size_t)y->nd * y->nd);
@@ -844,6 +892,7 @@ pas_status pas_pyr_get_tuning(pas_pyr_t y, pas_pyr_tuning* out) {
   out->rows_per_cta = y->rows;
   out->row_chunks = y->n_schunks;
   out->col_groups = y->G;
+  out->col_split = y->H;
   return PAS_OK;
 }
 
@@ -851,14 +900,16 @@ pas_status pas_pyr_set_tuning(pas_pyr_t y, const pas_pyr_tuning* t) {
   if (!y || !t) return pas::set_global_error(PAS_EINVAL, "pas_pyr_set_tuning: NULL argument");
   const int r = t->rows_per_cta;
   PAS_CHECK_ARG(y->ctx, (r == 1 || r == 2 || r == 4 || r == 8) && t->row_chunks >= 1 &&
-                t->row_chunks <= y->n_s && t->col_groups >= 1 && t->col_groups <= y->p.K,
+                t->row_chunks <= y->n_s && t->col_groups >= 1 && t->col_groups <= y->p.K &&
+                pas::split_ok(y, t->col_split),
                 "pas_pyr_set_tuning: rows_per_cta in {1,2,4,8}, 1 <= row_chunks <= distinct sin values, "
-                "1 <= col_groups <= K");
+                "1 <= col_groups <= K, col_split 1 or a divisor <= 8 of the fine pixels per detector pixel");
   y->rows = r;
   y->s_chunk = (y->n_s + t->row_chunks - 1) / t->row_chunks;
   y->n_schunks = (y->n_s + y->s_chunk - 1) / y->s_chunk;
   y->kper = (y->p.K + t->col_groups - 1) / t->col_groups;
   y->G = (y->p.K + y->kper - 1) / y->kper;
+  y->H = t->col_split;
   return PAS_OK;
 }
 
@@ -894,7 +945,7 @@ pas_status pas_pyr_autotune(pas_pyr_t y, const float* d_opd, int32_t iters, pas_
   };
   // rows pass
   float best = 1e30f;
-  pas_pyr_tuning bt{y->rows, y->n_schunks, y->G};
+  pas_pyr_tuning bt{y->rows, y->n_schunks, y->G, y->H};
   const int rows_c[3] = {2, 4, 8};
   for (int r : rows_c) {
     int last_chunk = -1;
@@ -915,21 +966,27 @@ pas_status pas_pyr_autotune(pas_pyr_t y, const float* d_opd, int32_t iters, pas_
   }
   pas_pyr_tuning cur = bt;
   cur.col_groups = y->G;
+  cur.col_split = y->H;
   pas_pyr_set_tuning(y, &cur);
   pas::launch_rows(y, d_opd, st);
   // columns pass (with the frame/slopes tail, into the internal frame)
   best = 1e30f;
-  int last_kper = -1;
-  for (int G = 1; G <= y->p.K; ++G) {
-    const int kper = (y->p.K + G - 1) / G;
-    if (kper == last_kper) continue;
-    last_kper = kper;
-    y->kper = kper;
-    y->G = (y->p.K + kper - 1) / kper;
-    const float ms = time_it([&](cudaStream_t q) { pas::launch_cols(y, nullptr, nullptr, q, nullptr, false); });
-    if (ms < best) {
-      best = ms;
-      bt.col_groups = y->G;
+  for (int H = 1; H <= y->h_max; ++H) {
+    if (!pas::split_ok(y, H)) continue;
+    y->H = H;
+    int last_kper = -1;
+    for (int G = 1; G <= y->p.K; ++G) {
+      const int kper = (y->p.K + G - 1) / G;
+      if (kper == last_kper) continue;
+      last_kper = kper;
+      y->kper = kper;
+      y->G = (y->p.K + kper - 1) / kper;
+      const float ms = time_it([&](cudaStream_t q) { pas::launch_cols(y, nullptr, nullptr, q, nullptr, false); });
+      if (ms < best) {
+        best = ms;
+        bt.col_groups = y->G;
+        bt.col_split = H;
+      }
     }
   }
   cudaEventDestroy(e0);

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -34,63 +35,91 @@ constexpr int RECON_ROWS = 8 / RECON_SPLIT;
 
 template <bool BF16>
 __global__ void __launch_bounds__(256) recon_kernel(ReconArgs a) {
+  using Chunk = typename std::conditional<BF16, uint4, float4>::type;  // one 16-byte load
+  constexpr int PRE = 4;                                               // chunks loaded before the wait
+  constexpr int STEP = RECON_SPLIT * 32;
   extern __shared__ float4 s4[];  // [n_s_pad / 4]
   __shared__ float part[8];
   __shared__ bool is_last;
   pdl_trigger();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row_local = warp / RECON_SPLIT, part_idx = warp % RECON_SPLIT;
+  const int m = blockIdx.x * RECON_ROWS + row_local;
+  const int c0 = part_idx * 32 + lane;
+  const int nc = a.n_s_pad / (BF16 ? 8 : 4);
+  const Chunk* row = nullptr;
+  if (m < a.n_m) {
+    if constexpr (BF16) row = reinterpret_cast<const uint4*>(a.Rb + (size_t)m * a.n_s_pad);
+    else row = reinterpret_cast<const float4*>(a.R + (size_t)m * a.n_s_pad);
+  }
+  // Before the wait for the slopes: everything else this CTA reads is final. The
+  // reconstructor is constant (its first PRE chunks per thread go to registers,
+  // the rest of the CTA's rows towards L2); the step counter and the previous
+  // command were written by the previous step's reconstructor, which has completed.
+  Chunk pre[PRE];
+#pragma unroll
+  for (int u = 0; u < PRE; ++u) {
+    const int c = c0 + u * STEP;
+    pre[u] = (row && c < nc) ? __ldg(row + c) : Chunk{};
+  }
   {
-    // the reconstructor is constant: start its rows towards L2 before waiting
     const int m0 = blockIdx.x * RECON_ROWS;
     const size_t row_bytes = (size_t)a.n_s_pad * (BF16 ? 2 : 4);
     const char* base = BF16 ? reinterpret_cast<const char*>(a.Rb) : reinterpret_cast<const char*>(a.R);
     const int nrow = min(RECON_ROWS, a.n_m - m0);
-    const int lines = (int)((row_bytes * nrow + 127) / 128);
-    for (int t = threadIdx.x; t < lines; t += blockDim.x) prefetch_l2(base + row_bytes * m0 + (size_t)t * 128);
+    const size_t skip = (size_t)PRE * STEP * 16;  // bytes of a row already in registers
+    if (row_bytes > skip) {
+      const int lines = (int)((row_bytes - skip + 127) / 128);
+      for (int t = threadIdx.x; t < lines * nrow; t += blockDim.x) {
+        const int r = t / lines, l = t - r * lines;
+        prefetch_l2(base + row_bytes * (m0 + r) + skip + (size_t)l * 128);
+      }
+    }
+  }
+  const bool writer = part_idx == 0 && lane == 0 && m < a.n_m;
+  long long t_step = 0;
+  float prev = 0.f;
+  if (writer && a.ring) {
+    t_step = *a.step;
+    prev = a.ring[(size_t)((t_step - 1 + a.delay) % a.delay) * a.n_m + m];
   }
   pdl_wait();
   float* s_s = reinterpret_cast<float*>(s4);
   for (int t = threadIdx.x; t < a.n_s_pad; t += blockDim.x) s_s[t] = t < a.n_s ? a.s[t] : 0.f;
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row_local = warp / RECON_SPLIT, part_idx = warp % RECON_SPLIT;
-  const int m = blockIdx.x * RECON_ROWS + row_local;
   float acc = 0.f;
-  if (m < a.n_m) {
-    const int c0 = part_idx * 32 + lane;
-    constexpr int STEP = RECON_SPLIT * 32;
-    if (BF16) {
-      const uint4* row = reinterpret_cast<const uint4*>(a.Rb + (size_t)m * a.n_s_pad);
-      const int nc = a.n_s_pad / 8;
-#pragma unroll 4
-      for (int c = c0; c < nc; c += STEP) {
-        const uint4 u = __ldg(row + c);
+  if (row) {
+    auto fma_chunk = [&](const Chunk& u, int c) {
+      if constexpr (BF16) {
         const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
         const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
         const float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
         acc = dot4(make_float4(f0.x, f0.y, f1.x, f1.y), s4[2 * c], acc);
         acc = dot4(make_float4(f2.x, f2.y, f3.x, f3.y), s4[2 * c + 1], acc);
+      } else {
+        acc = dot4(u, s4[c], acc);
       }
-    } else {
-      const float4* row = reinterpret_cast<const float4*>(a.R + (size_t)m * a.n_s_pad);
-      const int nc = a.n_s_pad / 4;
-#pragma unroll 4
-      for (int c = c0; c < nc; c += STEP) acc = dot4(__ldg(row + c), s4[c], acc);
+    };
+#pragma unroll
+    for (int u = 0; u < PRE; ++u) {
+      const int c = c0 + u * STEP;
+      if (c < nc) fma_chunk(pre[u], c);
     }
+#pragma unroll 4
+    for (int c = c0 + PRE * STEP; c < nc; c += STEP) fma_chunk(__ldg(row + c), c);
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) part[warp] = acc;
   __syncthreads();
-  if (part_idx == 0 && lane == 0 && m < a.n_m) {
+  if (writer) {
     float tot = 0.f;
 #pragma unroll
     for (int q = 0; q < RECON_SPLIT; ++q) tot += part[warp + q];
     const float dm = BF16 ? tot * a.scale[m] : tot;
     if (a.dmodes) a.dmodes[m] = dm;
     if (a.ring) {
-      const long long t = *a.step;
-      const float prev = a.ring[(size_t)((t - 1 + a.delay) % a.delay) * a.n_m + m];
       const float c = fmaf(a.gain ? a.gain[m] : 1.0f, dm, prev);
-      a.ring[(size_t)(t % a.delay) * a.n_m + m] = c;
+      a.ring[(size_t)(t_step % a.delay) * a.n_m + m] = c;
       if (a.cmd_last) a.cmd_last[m] = c;
     }
   }

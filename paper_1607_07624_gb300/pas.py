@@ -45,7 +45,8 @@ class pas_pyr_params(C.Structure):
 
 
 class pas_pyr_tuning(C.Structure):
-    _fields_ = [("rows_per_cta", C.c_int32), ("row_chunks", C.c_int32), ("col_groups", C.c_int32)]
+    _fields_ = [("rows_per_cta", C.c_int32), ("row_chunks", C.c_int32), ("col_groups", C.c_int32),
+                ("col_split", C.c_int32)]
 
 
 class pas_loop_stats(C.Structure):
@@ -287,21 +288,26 @@ def pas_pyr_destroy(pyr):
     _lib.pas_pyr_destroy(pyr)
 
 
+def _tuning_tuple(t):
+    return (t.rows_per_cta, t.row_chunks, t.col_groups, t.col_split)
+
+
 def pas_pyr_get_tuning(pyr, ctx):
+    """(rows_per_cta, row_chunks, col_groups, col_split)."""
     t = pas_pyr_tuning()
     _check(_lib.pas_pyr_get_tuning(pyr, C.byref(t)), ctx)
-    return (t.rows_per_cta, t.row_chunks, t.col_groups)
+    return _tuning_tuple(t)
 
 
-def pas_pyr_set_tuning(pyr, ctx, rows_per_cta, row_chunks, col_groups):
-    t = pas_pyr_tuning(rows_per_cta, row_chunks, col_groups)
+def pas_pyr_set_tuning(pyr, ctx, rows_per_cta, row_chunks, col_groups, col_split=1):
+    t = pas_pyr_tuning(rows_per_cta, row_chunks, col_groups, col_split)
     _check(_lib.pas_pyr_set_tuning(pyr, C.byref(t)), ctx)
 
 
 def pas_pyr_autotune(pyr, ctx, d_opd, iters=5):
     t = pas_pyr_tuning()
     _check(_lib.pas_pyr_autotune(pyr, _ptr(d_opd), int(iters), C.byref(t)), ctx)
-    return (t.rows_per_cta, t.row_chunks, t.col_groups)
+    return _tuning_tuple(t)
 
 
 def pas_recon_create(ctx, R: np.ndarray, precision=PAS_FP32):

@@ -34,7 +34,7 @@ class SCAOSystem:
     basis, Zernike or KL);
     R: reconstruction matrix (None: calibrated by push-pull on the GPU);
     autotune: True (time the pyramid launch geometries on the GPU), False (library
-    default) or (rows_per_cta, row_chunks, col_groups) to set one."""
+    default) or (rows_per_cta, row_chunks, col_groups[, col_split]) to set one."""
 
     def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32, dm_precision=P.PAS_FP32,
                  dm=None,

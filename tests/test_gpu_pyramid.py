@@ -187,7 +187,7 @@ def test_autotune_and_tunings_give_the_same_frame(env):
     try:
         nv = pas.pas_pyr_n_valid(pyr)
         frames = []
-        for t in [(1, 1, 1), (2, 3, 4), (8, 7, 12), (4, 2, 5)]:
+        for t in [(1, 1, 1), (2, 3, 4), (8, 7, 12), (4, 2, 5), (2, 3, 4, 2), (4, 2, 6, 4), (8, 1, 12, 4)]:
             pas.pas_pyr_set_tuning(pyr, ctx, *t)
             fr = torch.zeros(cfg.n_det, cfg.n_det, device="cuda")
             sl = torch.zeros(2 * nv, device="cuda")
@@ -198,8 +198,51 @@ def test_autotune_and_tunings_give_the_same_frame(env):
             assert np.max(np.abs(f - frames[0])) <= 1e-6 * np.max(frames[0])
         best = pas.pas_pyr_autotune(pyr, ctx, opd, 2)
         assert best[0] in (2, 4, 8) and 1 <= best[1] and 1 <= best[2] <= cfg.K
+        b = cfg.N // cfg.n_det
+        assert best[3] >= 1 and b % best[3] == 0
         assert pas.pas_pyr_get_tuning(pyr, ctx) == best
         with pytest.raises(pas.PasError):
             pas.pas_pyr_set_tuning(pyr, ctx, 3, 1, 1)
+        with pytest.raises(pas.PasError):
+            pas.pas_pyr_set_tuning(pyr, ctx, 4, 1, 1, 3)    # 3 does not divide b = 4
+    finally:
+        pas.pas_pyr_destroy(pyr)
+
+
+@pytest.mark.parametrize("cfg_idx,tunings", [(1, [None, (2, 1, 3, 2), (2, 1, 3, 4)]), (2, [None])])
+def test_noise_inside_the_pyramid_matches_oracle_counts(env, cfg_idx, tunings):
+    """Photon and read noise drawn by the columns pass (the last CTA of each detector
+    column; lanes of a group share a pixel's rejection loop) against the oracle's
+    draw on the same noiseless float32 frame. The column splits put 4, 2 and 1 lanes
+    on each pixel of the 64 px case."""
+    torch, pas, ctx = env
+    from oracle import noise as nz
+    cfg = get_config(cfg_idx)
+    opd = torch.as_tensor(open_loop_opd(cfg, 21).astype(np.float32)).cuda()
+    n_pupil = int(pas.pas_pupil_pixels(cfg.Np, cfg.obs).size)
+    photons, ron, seed = 40.0 * n_pupil, 0.5, 1234
+    pyr = pas.pas_pyr_create(ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius, cfg.wavelength_nm, cfg.obs)
+    try:
+        fr = torch.zeros(cfg.n_det, cfg.n_det, device="cuda")
+        for t in tunings:
+            if t is not None:
+                pas.pas_pyr_set_tuning(pyr, ctx, *t)
+            pas.pas_pyr_set_noise(pyr, ctx, 0.0, 0.0, 0, 0)
+            pas.pas_pyr_measure(pyr, ctx, opd, fr)
+            torch.cuda.synchronize()
+            clean = fr.cpu().numpy()
+            lam = clean.astype(np.float64) * photons / n_pupil
+            assert (lam < 10).any() and (lam >= 10).any()          # both Poisson branches
+            for fi, r in ((5, ron), (6, 0.0)):
+                pas.pas_pyr_set_noise(pyr, ctx, photons, r, seed, fi)
+                pas.pas_pyr_measure(pyr, ctx, opd, fr)
+                torch.cuda.synchronize()
+                g = fr.cpu().numpy().astype(np.float64)
+                o = nz.apply_noise(clean.astype(np.float64), photons, n_pupil, r, seed, fi)
+                if r > 0:
+                    close = np.abs(g - o) <= 1e-5 * np.maximum(1.0, np.abs(o))
+                    assert close.mean() >= 0.999, (t, close.mean())
+                else:
+                    assert np.mean(g == o) >= 0.999, (t, np.mean(g == o))
     finally:
         pas.pas_pyr_destroy(pyr)
