@@ -24,22 +24,40 @@ __device__ inline void layer_shift(double v, long long step, int S, int* n_mod, 
   *n_mod = (int)ni;
 }
 
+// Bilinear interpolation of one layer from its four taps, with explicit float32
+// rounding (the same value in every kernel that samples the atmosphere).
+__device__ __forceinline__ float bilinear(float fx, float fy, float v00, float v10, float v01, float v11) {
+  const float gx = __fsub_rn(1.f, fx), gy = __fsub_rn(1.f, fy);
+  float s = __fmul_rn(__fmul_rn(gx, gy), v00);
+  s = __fmaf_rn(__fmul_rn(fx, gy), v10, s);
+  s = __fmaf_rn(__fmul_rn(gx, fy), v01, s);
+  return __fmaf_rn(__fmul_rn(fx, fy), v11, s);
+}
+
+// Offsets of the four taps (00, 10, 01, 11) of pupil pixel (i, j) in one layer.
+__device__ __forceinline__ void tap_offsets(int i, int j, int shift_i, int shift_j, int S, size_t off[4]) {
+  int i0 = i + shift_i;
+  if (i0 >= S) i0 -= S;
+  int j0 = j + shift_j;
+  if (j0 >= S) j0 -= S;
+  const int i1 = (i0 + 1 == S) ? 0 : i0 + 1;
+  const int j1 = (j0 + 1 == S) ? 0 : j0 + 1;
+  off[0] = (size_t)i0 * S + j0;
+  off[1] = (size_t)i1 * S + j0;
+  off[2] = (size_t)i0 * S + j1;
+  off[3] = (size_t)i1 * S + j1;
+}
+
 __device__ inline float atmo_sample(const AtmoArgs& a, const int* six, const int* siy,
                                     const float* sfx, const float* sfy, int i, int j) {
   float acc = 0.f;
   const int S = a.S;
   for (int l = 0; l < a.L; ++l) {
-    int i0 = i + six[l];
-    if (i0 >= S) i0 -= S;
-    int j0 = j + siy[l];
-    if (j0 >= S) j0 -= S;
-    const int i1 = (i0 + 1 == S) ? 0 : i0 + 1;
-    const int j1 = (j0 + 1 == S) ? 0 : j0 + 1;
+    size_t o[4];
+    tap_offsets(i, j, six[l], siy[l], S, o);
     const float* sc = a.screens + (size_t)l * S * S;
-    const float fx = sfx[l], fy = sfy[l];
-    const float v00 = __ldg(sc + (size_t)i0 * S + j0), v10 = __ldg(sc + (size_t)i1 * S + j0);
-    const float v01 = __ldg(sc + (size_t)i0 * S + j1), v11 = __ldg(sc + (size_t)i1 * S + j1);
-    acc += (1.f - fx) * (1.f - fy) * v00 + fx * (1.f - fy) * v10 + (1.f - fx) * fy * v01 + fx * fy * v11;
+    acc = __fadd_rn(acc, bilinear(sfx[l], sfy[l], __ldg(sc + o[0]), __ldg(sc + o[1]), __ldg(sc + o[2]),
+                                  __ldg(sc + o[3])));
   }
   return acc;
 }
@@ -53,25 +71,15 @@ __device__ inline float atmo_sample_fixed(const AtmoArgs& a, const int* six, con
   float v[L][4];
 #pragma unroll
   for (int l = 0; l < L; ++l) {
-    int i0 = i + six[l];
-    if (i0 >= S) i0 -= S;
-    int j0 = j + siy[l];
-    if (j0 >= S) j0 -= S;
-    const int i1 = (i0 + 1 == S) ? 0 : i0 + 1;
-    const int j1 = (j0 + 1 == S) ? 0 : j0 + 1;
+    size_t o[4];
+    tap_offsets(i, j, six[l], siy[l], S, o);
     const float* sc = a.screens + (size_t)l * S * S;
-    v[l][0] = __ldg(sc + (size_t)i0 * S + j0);
-    v[l][1] = __ldg(sc + (size_t)i1 * S + j0);
-    v[l][2] = __ldg(sc + (size_t)i0 * S + j1);
-    v[l][3] = __ldg(sc + (size_t)i1 * S + j1);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) v[l][t] = __ldg(sc + o[t]);
   }
   float acc = 0.f;
 #pragma unroll
-  for (int l = 0; l < L; ++l) {
-    const float fx = sfx[l], fy = sfy[l];
-    acc += (1.f - fx) * (1.f - fy) * v[l][0] + fx * (1.f - fy) * v[l][1] + (1.f - fx) * fy * v[l][2] +
-           fx * fy * v[l][3];
-  }
+  for (int l = 0; l < L; ++l) acc = __fadd_rn(acc, bilinear(sfx[l], sfy[l], v[l][0], v[l][1], v[l][2], v[l][3]));
   return acc;
 }
 
@@ -142,17 +150,28 @@ __device__ __forceinline__ void unpack16(const uint4& u, float* f) {
   }
 }
 
+// 4-byte asynchronous global -> shared copy (no register holds the value in flight).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // With a.atmo.L > 0 the atmosphere is sampled here (the loop's step: layers
 // shifted by the wind of the device step, bilinear taps at the tile's pupil
-// pixels) by the tile's first 64 threads, while the other warps already stream
-// the basis; otherwise it is read from opd_atm (or zero).
+// pixels): the 4 L taps of the tile's pixels are copied to shared memory
+// asynchronously before the basis stream and combined after it, so their latency
+// hides under the stream; otherwise the atmosphere is read from opd_atm (or zero).
 template <typename T>
-__global__ void __launch_bounds__(RES_THREADS) residual_kernel(ResArgs a) {
+__global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(ResArgs a) {
   constexpr int VEC = 16 / (int)sizeof(T);         // pixels per 16-byte load
   constexpr int COLS = RES_TILE / VEC;              // loads per mode row
   constexpr int ROWS = RES_THREADS / COLS;          // modes per CTA-wide load
-  extern __shared__ float c_s[];                    // [n_m]
+  extern __shared__ float c_s[];                    // [n_m], then the taps [L][4][RES_TILE]
   __shared__ float red[ROWS][RES_TILE];
+  __shared__ int s_flat[RES_TILE];
   __shared__ double wred[2][RES_THREADS / 32];
   __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
   __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
@@ -169,28 +188,36 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(ResArgs a) {
     const int m = row + ROWS * u;
     v[u] = m < n_m ? ld_stream16(blk + (size_t)m * RES_TILE) : make_uint4(0u, 0u, 0u, 0u);
   }
+  const int base = blockIdx.x * RES_TILE;
+  const int L = a.atmo.L;
+  if (tid < RES_TILE) s_flat[tid] = base + tid < a.n_pix ? a.pix[base + tid] : 0;  // constant
   pdl_trigger();
   pdl_wait();
   const long long step = a.d_step ? *a.d_step : a.h_step;
   const float* cmd = a.cmd;
   if (a.cmd_ring) cmd = a.cmd_ring + (size_t)(step % a.delay) * a.n_m;
-  if (tid < a.atmo.L) {
+  if (tid < L) {
     layer_shift(a.atmo.vx[tid], step, a.atmo.S, &six[tid], &sfx[tid]);
     layer_shift(a.atmo.vy[tid], step, a.atmo.S, &siy[tid], &sfy[tid]);
   }
   for (int m = tid; m < n_m; m += RES_THREADS) c_s[m] = cmd[m];
   __syncthreads();
-  const int base = blockIdx.x * RES_TILE;
-  float atm = 0.f;  // meaningful in the output threads tid < RES_TILE
-  int flat = 0;
-  if (tid < RES_TILE && base + tid < a.n_pix) {
-    flat = a.pix[base + tid];
-    if (a.atmo.L > 0) {
-      const int i = flat / a.atmo.Np, j = flat - i * a.atmo.Np;
-      atm = atmo_sample(a.atmo, six, siy, sfx, sfy, i, j);
-    } else if (a.opd_atm) {
-      atm = a.opd_atm[flat];
+  float* taps = c_s + max(a.n_m, 1);
+  if (L > 0) {
+    const int S = a.atmo.S;
+    for (int t = tid; t < L * RES_TILE; t += RES_THREADS) {
+      const int l = t / RES_TILE, q = t - l * RES_TILE;
+      if (base + q < a.n_pix) {
+        const int flat = s_flat[q];
+        const int i = flat / a.atmo.Np, j = flat - i * a.atmo.Np;
+        size_t o[4];
+        tap_offsets(i, j, six[l], siy[l], S, o);
+        const float* sc = a.atmo.screens + (size_t)l * S * S;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cp_async4(taps + (l * 4 + k) * RES_TILE + q, sc + o[k]);
+      }
     }
+    cp_async_commit();
   }
   float acc[VEC];
 #pragma unroll
@@ -212,11 +239,28 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(ResArgs a) {
   }
 #pragma unroll
   for (int i = 0; i < VEC; ++i) red[row][col * VEC + i] = acc[i];
+  if (L > 0) {
+    // each (layer, pixel) pair's bilinear value replaces its first tap
+    cp_async_wait_all();
+    __syncthreads();
+    for (int t = tid; t < L * RES_TILE; t += RES_THREADS) {
+      const int l = t / RES_TILE, q = t - l * RES_TILE;
+      float* tp = taps + l * 4 * RES_TILE + q;
+      if (base + q < a.n_pix) tp[0] = bilinear(sfx[l], sfy[l], tp[0], tp[RES_TILE], tp[2 * RES_TILE], tp[3 * RES_TILE]);
+    }
+  }
   __syncthreads();
   const int px = tid;
   const int p = base + px;
   double s1 = 0.0, s2 = 0.0;
   if (px < RES_TILE && p < a.n_pix) {
+    const int flat = s_flat[px];
+    float atm = 0.f;
+    if (L > 0) {
+      for (int l = 0; l < L; ++l) atm = __fadd_rn(atm, taps[l * 4 * RES_TILE + px]);
+    } else if (a.opd_atm) {
+      atm = a.opd_atm[flat];
+    }
     float dm = 0.f;
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) dm += red[r][px];
@@ -265,18 +309,32 @@ __global__ void integrate_kernel(float* cmd, const float* dmodes, const float* g
 
 int residual_tiles(int n_pix) { return (n_pix + RES_TILE - 1) / RES_TILE; }
 
+// The residual kernel streams its basis through registers, not the L1 cache: its
+// launch bounds (at most 51 registers) and a shared-memory carveout preference keep
+// five CTAs resident per SM (one wave for the 700 tiles of a 240 px pupil).
+template <typename T>
+static cudaError_t residual_prepare(size_t smem) {
+  static bool carveout_set = false;
+  cudaError_t e = raise_dyn_smem((const void*)residual_kernel<T>, smem);
+  if (e == cudaSuccess && !carveout_set) {
+    e = cudaFuncSetAttribute((const void*)residual_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
+    carveout_set = e == cudaSuccess;
+  }
+  return e;
+}
+
 pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, bool pdl) {
   const int tiles = residual_tiles(a.n_pix);
   if (tiles == 0) return PAS_OK;
   if (a.atmo.L < 0 || a.atmo.L > PAS_MAX_LAYERS)
     return set_error(ctx, PAS_EINVAL, "residual kernel: 0 <= layers <= %d", PAS_MAX_LAYERS);
-  const size_t smem = sizeof(float) * (size_t)std::max(a.n_m, 1);
+  const size_t smem = sizeof(float) * ((size_t)std::max(a.n_m, 1) + (size_t)a.atmo.L * 4 * RES_TILE);
   cudaError_t e;
   if (a.MTb) {
-    e = raise_dyn_smem((const void*)residual_kernel<__nv_bfloat16>, smem);
+    e = residual_prepare<__nv_bfloat16>(smem);
     if (e == cudaSuccess) e = launch_k(residual_kernel<__nv_bfloat16>, dim3(tiles), dim3(RES_THREADS), smem, st, pdl, a);
   } else {
-    e = raise_dyn_smem((const void*)residual_kernel<float>, smem);
+    e = residual_prepare<float>(smem);
     if (e == cudaSuccess) e = launch_k(residual_kernel<float>, dim3(tiles), dim3(RES_THREADS), smem, st, pdl, a);
   }
   if (e != cudaSuccess) return set_error(ctx, PAS_ECUDA, "residual kernel launch: %s", cudaGetErrorString(e));

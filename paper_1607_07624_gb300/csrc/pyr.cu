@@ -25,6 +25,7 @@
 #include "internal.h"
 #include "noise.cuh"
 #include "pdl.cuh"
+#include "phasor.cuh"
 #include "pyr.cuh"
 
 namespace pas {
@@ -121,16 +122,7 @@ pyr_rows_kernel(RowArgs a) {
       float2 v = make_float2(0.f, 0.f);
       const int bj = 2 * j - Np + 1;
       const int d2 = ai2 + bj * bj;
-      if (i < Np && d2 <= Np * Np && d2 >= a.T_obs) {
-        const float o = __ldg(orow + j);
-        // opd / lambda in cycles, reduced to [-1/2, 1/2] with an exact split
-        const float hi = o * a.inv_hi;
-        const float err = fmaf(o, a.inv_hi, -hi);
-        const float lo = fmaf(o, a.inv_lo, err);
-        float sn, cs;
-        sincospif(2.0f * ((hi - rintf(hi)) + lo), &sn, &cs);
-        v = make_float2(cs, sn);
-      }
+      if (i < Np && d2 <= Np * Np && d2 >= a.T_obs) v = opd_phasor(__ldg(orow + j), a.inv_hi, a.inv_lo);
       phrow[j] = v;
     }
   }
