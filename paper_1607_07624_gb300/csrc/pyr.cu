@@ -140,10 +140,12 @@ pyr_rows_kernel(RowArgs a) {
       fft_mask_ifft<N>(buf, tw_s, mk_s, lane, load, store);
     }
     __syncthreads();
-    // transposed write: H[s][y][i0 + r], rows x 8 contiguous bytes per y
+    // transposed write: H[s][y][i0 + r], rows x 8 contiguous bytes per y (rows is a
+    // power of two: index split by shift and mask)
     float2* Hs = a.H + (size_t)s * N * Np;
+    const int lg = __ffs(rows) - 1;
     for (int idx = threadIdx.x; idx < N * rows; idx += blockDim.x) {
-      const int r = idx % rows, y = idx / rows;
+      const int r = idx & (rows - 1), y = idx >> lg;
       if (r < nr) Hs[(size_t)y * Np + i0 + r] = bufs[r * PITCH + phys(y)];
     }
     __syncthreads();
