@@ -274,6 +274,44 @@ def bench_other_workloads(timed, peaks, n_steps=200):
     return out
 
 
+def bench_psf(timed, n_frames=100):
+    """PSF camera on the LBT-class optics at the paper's camera settings (1650 nm,
+    padding 8: a 1920 x 1920 grid), integrating every frame into a long-exposure PSF:
+    frames/s and the FP32 roofline of its two FFT passes. The residual is a smooth
+    closed-loop-like OPD of 150 nm RMS."""
+    import numpy as np
+    import torch
+    from paper_1607_07624_gb300 import pas
+    from synth import get_config
+    from synth.inputs import random_opd_nm
+    cfg = get_config(2)
+    Np, nd = cfg.Np, 8
+    ctx = pas.pas_ctx_create(torch.cuda.current_stream())
+    h = pas.pas_psf_create(ctx, Np, nd, 1650.0, cfg.obs)
+    try:
+        N = pas.pas_psf_size(h)
+        opd = torch.as_tensor(random_opd_nm(Np, 150.0, seed=3).astype(np.float32)).cuda()
+        acc = torch.zeros(N, N, device="cuda")
+        sr = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(5):
+            pas.pas_psf_compute(h, ctx, opd, acc, True, sr)
+        ms = timed(lambda: pas.pas_psf_compute(h, ctx, opd, acc, True, sr), n_frames)
+        torch.cuda.synchronize()
+        per = ms / n_frames * 1e-3
+        # FFTs of the Np pupil columns and the N frequency rows, |.|^2 and the sum
+        flops = (Np + N) * 5.0 * N * math.log2(N) + 4.0 * N * N
+        bytes_ = 8.0 * N * N + 4.0 * Np * Np + 2 * 8.0 * N * Np   # PSF read+write, OPD, intermediate
+        ach = flops / per / 1e12
+        return {"workload": f"PSF {N}x{N} (Np {Np}, nd {nd}, 1650 nm), integrated each frame",
+                "frames_per_s": n_frames / (ms * 1e-3), "us_per_frame": per * 1e6,
+                "strehl": float(sr.item()), "flops_per_frame": flops, "bytes_per_frame": bytes_,
+                "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": ach / FP32_PEAK_TFLOPS}}
+    finally:
+        pas.pas_psf_destroy(h)
+        pas.pas_ctx_destroy(ctx)
+
+
 def bench_batch(timed, n_loops=64, n_steps=100):
     """Monte-Carlo batch: n_loops realisations of the 64 px workload (own screens
     each; basis, reconstructor and launch geometry shared) stepped by one graph
@@ -644,6 +682,10 @@ def main():
             extra["other_workloads"] = bench_other_workloads(timed, peaks)
         except Exception as e:
             extra["other_workloads"] = {"error": str(e)}
+        try:
+            extra["psf_camera"] = bench_psf(timed)
+        except Exception as e:
+            extra["psf_camera"] = {"error": str(e)}
         try:
             extra["monte_carlo_batch"] = bench_batch(timed)
         except Exception as e:

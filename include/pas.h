@@ -55,6 +55,7 @@ typedef struct pas_dm_s*    pas_dm_t;
 typedef struct pas_loop_s*  pas_loop_t;
 typedef struct pas_mlp_s*   pas_mlp_t;
 typedef struct pas_batch_s* pas_batch_t;
+typedef struct pas_psf_s*   pas_psf_t;
 
 /* ------------------------------------------------------------------ context */
 
@@ -332,6 +333,32 @@ pas_status pas_batch_step(pas_batch_t batch, int32_t n_steps);
 /* Number of loops, -1 for a NULL handle. Host only. */
 int32_t pas_batch_size(pas_batch_t batch);
 void pas_batch_destroy(pas_batch_t batch);
+
+/* -------------------------------------------------------------- PSF camera
+ * Point-spread function and Strehl ratio of the residual field (Table 1 camera:
+ * wavelengthInNm, nd = "padding coefficient for PSF computation"; Table 2
+ * psf.in_ef, psf.out_sr, psf.out_int_psf; Sec. GPU acceleration, "PSF generation
+ * from residual wavefront"). E = A exp(2 pi i opd / lambda) on the Np x Np pupil
+ * (A = pas_pupil_mask), zero-padded to N = nd Np;
+ *   PSF(p, q) = |sum_ij E(i,j) exp(-2 pi i ((p - N/2) i + (q - N/2) j) / N)|^2 / (sum A)^2,
+ * so the zero frequency sits at (N/2, N/2), a diffraction-limited pupil peaks at 1
+ * there and one pixel is lambda / (nd D). The Strehl ratio is the PSF value at
+ * (N/2, N/2) = |sum A exp(i phi)|^2 / (sum A)^2. The integrated PSF is the sum of
+ * the per-step PSFs from a start step on (accumulate = 1 from that step).
+ * Supported pupils Np = 48, 64, 120, 128, 240, 256, 480 and padding 1 <= nd <= 16
+ * (PAS_EINVAL otherwise). The object owns its tables and an N x Np complex
+ * intermediate. */
+pas_status pas_psf_create(pas_ctx_t ctx, int32_t Np, int32_t nd, double wavelength_nm, double obs,
+                          pas_psf_t* out);
+/* N = nd Np, or -1 for a NULL handle. Host only. */
+int32_t pas_psf_size(pas_psf_t psf);
+/* d_opd: device float32 [Np][Np] residual OPD in nm (values outside the pupil are
+ * ignored); d_psf: device float32 [N][N], written (accumulate = 0) or added to
+ * (accumulate = 1); d_strehl: device float64 scalar or NULL, the Strehl ratio.
+ * Asynchronous on the context stream; allocates nothing (graph-capturable). */
+pas_status pas_psf_compute(pas_psf_t psf, const float* d_opd, float* d_psf, int32_t accumulate,
+                           double* d_strehl);
+void pas_psf_destroy(pas_psf_t psf);
 
 /* -------------------------------------------------- learned reconstructor
  * A multilayer perceptron from slopes to modal coefficients, used by the loop

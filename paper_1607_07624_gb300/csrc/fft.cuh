@@ -341,6 +341,32 @@ __device__ __forceinline__ void fft_mask_ifft(float2* buf, const float2* tw, con
   dit_passes<N, M - 2>(buf, tw, lane, store);
 }
 
+// Forward FFT of one length-N vector by one warp, without mask or inverse: pass 0
+// reads through `load` as in fft_mask_ifft; on return buf[phys(p)] holds the
+// frequency fft_freq_at(N, p) (digit-reversed order, fft_host.h).
+template <int N, class Load>
+__device__ __forceinline__ void fft_forward(float2* buf, const float2* tw, int lane, Load& load) {
+  constexpr int M = plan_count(N);
+  static_assert(M >= 2, "transform needs at least two radix passes");
+  dif_passes<N, 0>(buf, tw, lane, load);
+  constexpr int R = plan_radix(N, M - 1);
+  constexpr int NB = N / R;
+  constexpr int NJ = (NB + 31) / 32;
+#pragma unroll
+  for (int jb = 0; jb < NJ; ++jb) {
+    const int b = lane + 32 * jb;
+    if (NB % 32 == 0 || b < NB) {
+      float2 v[R];
+#pragma unroll
+      for (int k = 0; k < R; ++k) v[k] = buf[phys(b * R + k)];
+      Bfly<R, false>::run(v);
+#pragma unroll
+      for (int k = 0; k < R; ++k) buf[phys(b * R + k)] = v[k];
+    }
+  }
+  __syncwarp();
+}
+
 // Outputs a lane receives from the last inverse pass: NJ0 butterflies x R0 values.
 template <int N> struct OutShape {
   static constexpr int R0 = plan_radix(N, 0);

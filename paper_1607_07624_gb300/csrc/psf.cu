@@ -1,0 +1,261 @@
+// PSF camera: point-spread function and Strehl ratio of the residual field (Table 1
+// camera: wavelengthInNm, nd "padding coefficient for PSF computation"; Table 2
+// psf.in_ef, psf.out_sr, psf.out_int_psf; Sec. GPU acceleration, "PSF generation from
+// residual wavefront").
+//
+// E = A exp(2 pi i opd / lambda) on the Np x Np pupil, zero-padded to N = nd Np, and
+// PSF(p, q) = |F(p, q)|^2 / (sum A)^2 with F the 2-D DFT of E (-1)^(i+j): the sign
+// moves the zero frequency to (N/2, N/2), where a diffraction-limited pupil peaks at
+// exactly 1 and where the Strehl ratio is read.
+//
+// The padding is used, not transformed: a length-N DFT of a sequence that is zero
+// beyond Np samples gives at frequency k = nd m + r the length-Np DFT of
+// x[n] exp(-2 pi i r n / N) at m. So each padded 1-D transform is nd warp FFTs of
+// length Np (fft.cuh), one per residue r: first along axis 0 for the Np pupil
+// columns (spectrum written transposed, H[p][j]), then along axis 1 for the N
+// frequency rows, whose nd residues meet in shared memory and leave as one
+// coalesced row of |F|^2.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "fft.cuh"
+#include "fft_host.h"
+#include "internal.h"
+#include "pdl.cuh"
+#include "phasor.cuh"
+
+namespace pas {
+
+constexpr int PSF_COLS_WARPS = 8;  // pupil columns per CTA of the first pass (a power of two)
+constexpr int PSF_MAX_ND = 16;
+
+struct PsfArgs {
+  const float* opd;     // [Np][Np] nm
+  const float2* tw;     // per-pass twiddles of the length-Np FFT
+  const int* pos;       // [Np] buffer position holding frequency m after fft_forward
+  const float2* rot;    // [nd][Np] exp(-2 pi i r n / N)
+  float2* H;            // [N][Np] spectra of the pupil columns along axis 0
+  float* psf;           // [N][N]
+  double* strehl;       // scalar or null
+  int nd, T_obs, accumulate;
+  float inv_hi, inv_lo;  // 1/lambda split in two floats
+  float norm;            // 1 / (sum A)^2
+};
+
+template <int NP>
+__device__ __forceinline__ void psf_stage_tables(const PsfArgs& a, float2* tw_s, int* pos_s) {
+  for (int t = threadIdx.x; t < tw_size(NP); t += blockDim.x) tw_s[t] = a.tw[t];
+  for (int t = threadIdx.x; t < NP; t += blockDim.x) pos_s[t] = a.pos[t];
+}
+
+// Pass 1: CTA (column block, residue r), one warp per pupil column j, transform
+// along axis 0 of A e^{i phi} (-1)^(i+j) e^{-2 pi i r i / N}.
+template <int NP>
+__global__ void __launch_bounds__(PSF_COLS_WARPS * 32) psf_cols_kernel(PsfArgs a) {
+  constexpr int TWN = tw_size(NP), PITCH = buf_len(NP) | 1;
+  extern __shared__ float2 smem[];
+  float2* tw_s = smem;
+  int* pos_s = reinterpret_cast<int*>(smem + TWN);
+  float2* bufs = smem + TWN + (NP + 1) / 2;  // after pos_s (NP ints)
+  pdl_trigger();
+  psf_stage_tables<NP>(a, tw_s, pos_s);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.y, nd = a.nd;
+  const int j0 = blockIdx.x * PSF_COLS_WARPS, j = j0 + warp;
+  float2* buf = bufs + warp * PITCH;
+  const float2* rot = a.rot + (size_t)r * NP;
+  if (j < NP) {
+    const int bj = 2 * j - NP + 1;
+    auto load = [&](int, int, int x) -> float2 {
+      const int ai = 2 * x - NP + 1;
+      const int d2 = ai * ai + bj * bj;
+      if (d2 > NP * NP || d2 < a.T_obs) return make_float2(0.f, 0.f);
+      float2 v = opd_phasor(__ldg(a.opd + (size_t)x * NP + j), a.inv_hi, a.inv_lo);
+      if ((x + j) & 1) v = make_float2(-v.x, -v.y);
+      return cmul(v, __ldg(rot + x));
+    };
+    fft_forward<NP>(buf, tw_s, lane, load);
+  }
+  __syncthreads();
+  // transposed write H[nd m + r][j0 + w]: 8 x 8 contiguous bytes per frequency
+  constexpr int LG = PSF_COLS_WARPS == 8 ? 3 : PSF_COLS_WARPS == 4 ? 2 : PSF_COLS_WARPS == 2 ? 1 : 0;
+  static_assert((1 << LG) == PSF_COLS_WARPS, "PSF_COLS_WARPS must be 1, 2, 4 or 8");
+  for (int idx = threadIdx.x; idx < NP * PSF_COLS_WARPS; idx += blockDim.x) {
+    const int w = idx & (PSF_COLS_WARPS - 1), m = idx >> LG;
+    if (j0 + w < NP) a.H[((size_t)nd * m + r) * NP + j0 + w] = bufs[w * PITCH + phys(pos_s[m])];
+  }
+}
+
+// Pass 2: CTA = one frequency row p, warp r = residue; |F|^2 (sum A)^-2 gathered in
+// shared memory at q = nd m + r and written (or added) as one row.
+template <int NP>
+__global__ void psf_rows_kernel(PsfArgs a) {
+  constexpr int TWN = tw_size(NP), PITCH = buf_len(NP) | 1;
+  extern __shared__ float2 smem[];
+  float2* tw_s = smem;
+  int* pos_s = reinterpret_cast<int*>(smem + TWN);
+  float2* bufs = smem + TWN + (NP + 1) / 2;
+  const int nd = a.nd, N = nd * NP;
+  float* row = reinterpret_cast<float*>(bufs + nd * PITCH);  // [N]
+  psf_stage_tables<NP>(a, tw_s, pos_s);
+  pdl_wait();  // H comes from the first pass
+  __syncthreads();
+  const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x;
+  float2* buf = bufs + r * PITCH;
+  const float2* Hrow = a.H + (size_t)p * NP;
+  const float2* rot = a.rot + (size_t)r * NP;
+  auto load = [&](int, int, int x) -> float2 { return cmul(__ldg(Hrow + x), __ldg(rot + x)); };
+  fft_forward<NP>(buf, tw_s, lane, load);
+  for (int m = lane; m < NP; m += 32) {
+    const float2 v = buf[phys(pos_s[m])];
+    row[nd * m + r] = __fmul_rn(__fmaf_rn(v.x, v.x, __fmul_rn(v.y, v.y)), a.norm);
+  }
+  __syncthreads();
+  float* out = a.psf + (size_t)p * N;
+  for (int q = threadIdx.x; q < N; q += blockDim.x) {
+    const float val = row[q];
+    out[q] = a.accumulate ? __fadd_rn(out[q], val) : val;
+  }
+  if (a.strehl && p == N / 2 && threadIdx.x == 0) *a.strehl = (double)row[N / 2];
+}
+
+struct PsfKernels {
+  void (*cols)(PsfArgs);
+  void (*rows)(PsfArgs);
+  int tw_n, pitch;
+};
+
+#define PAS_PSF_PUPILS(X) X(48) X(64) X(120) X(128) X(240) X(256) X(480)
+
+static bool lookup_psf_kernels(int Np, PsfKernels* k) {
+  switch (Np) {
+#define PAS_CASE(n)                                                                      \
+  case n:                                                                                \
+    *k = PsfKernels{psf_cols_kernel<n>, psf_rows_kernel<n>, tw_size(n), buf_len(n) | 1}; \
+    return true;
+    PAS_PSF_PUPILS(PAS_CASE)
+#undef PAS_CASE
+    default:
+      return false;
+  }
+}
+
+}  // namespace pas
+
+struct pas_psf_s {
+  pas_ctx_t ctx = nullptr;
+  int Np = 0, nd = 0, N = 0, T_obs = 0;
+  float inv_hi = 0.f, inv_lo = 0.f, norm = 0.f;
+  pas::PsfKernels kern{};
+  size_t smem_cols = 0, smem_rows = 0;
+  float2* d_tw = nullptr;
+  int* d_pos = nullptr;
+  float2* d_rot = nullptr;
+  float2* d_H = nullptr;
+};
+
+extern "C" {
+
+void pas_psf_destroy(pas_psf_t P) {
+  if (!P) return;
+  pas::dev_free(P->d_tw);
+  pas::dev_free(P->d_pos);
+  pas::dev_free(P->d_rot);
+  pas::dev_free(P->d_H);
+  delete P;
+}
+
+pas_status pas_psf_create(pas_ctx_t ctx, int32_t Np, int32_t nd, double wavelength_nm, double obs,
+                          pas_psf_t* out) {
+  if (!ctx || !out) return pas::set_global_error(PAS_EINVAL, "pas_psf_create: NULL argument");
+  *out = nullptr;
+  PAS_CHECK_ARG(ctx, Np > 0 && nd >= 1 && nd <= pas::PSF_MAX_ND && wavelength_nm > 0 && obs >= 0 && obs < 1,
+                "pas_psf_create: need Np > 0, 1 <= nd <= 16, wavelength > 0, 0 <= obs < 1");
+  pas::PsfKernels kern;
+  if (!pas::lookup_psf_kernels(Np, &kern))
+    return pas::set_error(ctx, PAS_EINVAL, "pas_psf_create: pupil of %d px not supported", Np);
+  int32_t n_pup = 0;
+  pas_pupil_mask(Np, obs, nullptr, &n_pup);
+  PAS_CHECK_ARG(ctx, n_pup > 0, "pas_psf_create: empty pupil");
+  const int N = Np * nd;
+
+  pas_psf_t P = new pas_psf_s();
+  P->ctx = ctx;
+  P->Np = Np;
+  P->nd = nd;
+  P->N = N;
+  P->kern = kern;
+  P->T_obs = (int)pas::obstruction_threshold(Np, obs);
+  const double inv = 1.0 / wavelength_nm;
+  P->inv_hi = (float)inv;
+  P->inv_lo = (float)(inv - (double)P->inv_hi);
+  P->norm = (float)(1.0 / ((double)n_pup * (double)n_pup));
+  const size_t tables = sizeof(float2) * ((size_t)kern.tw_n + (size_t)(Np + 1) / 2);
+  P->smem_cols = tables + sizeof(float2) * (size_t)pas::PSF_COLS_WARPS * kern.pitch;
+  P->smem_rows = tables + sizeof(float2) * ((size_t)nd * kern.pitch + (size_t)(N + 1) / 2);
+
+  std::vector<float2> tw = pas::fft_twiddles(Np);
+  std::vector<int> pos(Np);
+  for (int p = 0; p < Np; ++p) pos[pas::fft_freq_at(Np, p)] = p;
+  std::vector<float2> rot((size_t)nd * Np);
+  for (int r = 0; r < nd; ++r)
+    for (int n = 0; n < Np; ++n) {
+      const double a = -2.0 * M_PI * (double)((long long)r * n % N) / (double)N;
+      rot[(size_t)r * Np + n] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+  pas_status st = PAS_OK;
+  auto A = [&](void** ptr, size_t bytes) {
+    if (st == PAS_OK) st = pas::dev_alloc(ctx, ptr, bytes);
+  };
+  A((void**)&P->d_tw, sizeof(float2) * tw.size());
+  A((void**)&P->d_pos, sizeof(int) * Np);
+  A((void**)&P->d_rot, sizeof(float2) * rot.size());
+  A((void**)&P->d_H, sizeof(float2) * (size_t)N * Np);
+  if (st != PAS_OK) {
+    pas_psf_destroy(P);
+    return st;
+  }
+  cudaError_t e = cudaMemcpy(P->d_tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(P->d_pos, pos.data(), sizeof(int) * Np, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(P->d_rot, rot.data(), sizeof(float2) * rot.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = pas::raise_dyn_smem((const void*)kern.cols, P->smem_cols);
+  if (e == cudaSuccess) e = pas::raise_dyn_smem((const void*)kern.rows, P->smem_rows);
+  if (e != cudaSuccess) {
+    pas_psf_destroy(P);
+    return pas::set_error(ctx, PAS_ECUDA, "pas_psf_create: %s", cudaGetErrorString(e));
+  }
+  *out = P;
+  return PAS_OK;
+}
+
+int32_t pas_psf_size(pas_psf_t P) { return P ? P->N : -1; }
+
+pas_status pas_psf_compute(pas_psf_t P, const float* d_opd, float* d_psf, int32_t accumulate, double* d_strehl) {
+  if (!P || !d_opd || !d_psf) return pas::set_global_error(PAS_EINVAL, "pas_psf_compute: NULL argument");
+  pas::PsfArgs a;
+  a.opd = d_opd;
+  a.tw = P->d_tw;
+  a.pos = P->d_pos;
+  a.rot = P->d_rot;
+  a.H = P->d_H;
+  a.psf = d_psf;
+  a.strehl = d_strehl;
+  a.nd = P->nd;
+  a.T_obs = P->T_obs;
+  a.accumulate = accumulate ? 1 : 0;
+  a.inv_hi = P->inv_hi;
+  a.inv_lo = P->inv_lo;
+  a.norm = P->norm;
+  cudaStream_t st = P->ctx->stream;
+  cudaError_t e = pas::launch_k(P->kern.cols, dim3((P->Np + pas::PSF_COLS_WARPS - 1) / pas::PSF_COLS_WARPS, P->nd),
+                                dim3(pas::PSF_COLS_WARPS * 32), P->smem_cols, st, false, a);
+  if (e == cudaSuccess)
+    e = pas::launch_k(P->kern.rows, dim3(P->N), dim3(P->nd * 32), P->smem_rows, st, true, a);
+  if (e != cudaSuccess) return pas::set_error(P->ctx, PAS_ECUDA, "pas_psf_compute launch: %s", cudaGetErrorString(e));
+  return PAS_OK;
+}
+
+}  // extern "C"

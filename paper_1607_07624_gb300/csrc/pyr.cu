@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "fft.cuh"
+#include "fft_host.h"
 #include "internal.h"
 #include "noise.cuh"
 #include "pdl.cuh"
@@ -440,20 +441,6 @@ static bool lookup_kernels(int N, PyrKernels* k) {
 }
 
 // Digit-reversed frequency of in-place position p for the radix list of N.
-static int digit_reversed_freq(int N, int p) {
-  const int M = plan_count(N);
-  int rem = p, L = N, mult = 1, u = 0;
-  for (int i = 0; i < M; ++i) {
-    const int R = plan_radix(N, i), S = L / R;
-    const int k = rem / S;
-    rem -= k * S;
-    u += k * mult;
-    mult *= R;
-    L = S;
-  }
-  return u;
-}
-
 }  // namespace pas
 
 struct pas_pyr_s {
@@ -732,20 +719,10 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   }
   // per-pass twiddle tables ([k-1][n1] = w_L^{n1 k}) and the digit-reversed
   // pyramid mask (delta = N/4: phase (pi/2)|u~|, divided by N) in padded layout
-  std::vector<float2> tw(kern.tw_n), mk(kern.buf_n, make_float2(0.f, 0.f));
+  std::vector<float2> tw = pas::fft_twiddles(p.N), mk(kern.buf_n, make_float2(0.f, 0.f));
   {
-    const int M = pas::plan_count(p.N);
-    for (int pass = 0; pass + 1 < M; ++pass) {
-      const int R = pas::plan_radix(p.N, pass), L = pas::block_len(p.N, pass), S = L / R;
-      const int off = pas::tw_offset(p.N, pass);
-      for (int k = 1; k < R; ++k)
-        for (int n1 = 0; n1 < S; ++n1) {
-          const double a = -2.0 * M_PI * (double)(n1 * k) / (double)L;
-          tw[off + (k - 1) * S + n1] = make_float2((float)std::cos(a), (float)std::sin(a));
-        }
-    }
     for (int j = 0; j < p.N; ++j) {
-      const int u = pas::digit_reversed_freq(p.N, j);
+      const int u = pas::fft_freq_at(p.N, j);
       const double ut = std::fabs((double)u - 0.5 * (p.N - 1));
       const double ph = 0.5 * M_PI * ut;
       mk[pas::phys(j)] = make_float2((float)(std::cos(ph) / p.N), (float)(std::sin(ph) / p.N));
@@ -1131,7 +1108,7 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
     }
     for (int j = 0; j < kern.buf_n; ++j) mk[j] = make_float2(0.f, 0.f);
     for (int j = 0; j < p.N; ++j) {
-      const double ut = std::fabs((double)digit_reversed_freq(p.N, j) - 0.5 * (p.N - 1));
+      const double ut = std::fabs((double)fft_freq_at(p.N, j) - 0.5 * (p.N - 1));
       mk[phys(j)] = make_float2((float)(std::cos(0.5 * M_PI * ut) / p.N), (float)(std::sin(0.5 * M_PI * ut) / p.N));
     }
   }

@@ -122,6 +122,10 @@ _SIGS = {
     "pas_batch_step": (C.c_int, [vp, i32]),
     "pas_batch_size": (i32, [vp]),
     "pas_batch_destroy": (None, [vp]),
+    "pas_psf_create": (C.c_int, [vp, i32, i32, C.c_double, C.c_double, P(vp)]),
+    "pas_psf_size": (i32, [vp]),
+    "pas_psf_compute": (C.c_int, [vp, vp, vp, i32, vp]),
+    "pas_psf_destroy": (None, [vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -496,3 +500,25 @@ def pas_batch_destroy(batch):
 
 def loaded_library_path() -> str:
     return LIB_PATH
+
+
+# ------------------------------------------------------------------ PSF camera
+
+def pas_psf_create(ctx, Np, nd, wavelength_nm, obs):
+    h = vp()
+    _check(_lib.pas_psf_create(ctx, int(Np), int(nd), float(wavelength_nm), float(obs), C.byref(h)), ctx)
+    return h
+
+
+def pas_psf_size(psf):
+    return int(_lib.pas_psf_size(psf))
+
+
+def pas_psf_compute(psf, ctx, d_opd, d_psf, accumulate=False, d_strehl=None):
+    """PSF of the residual OPD d_opd into d_psf [N][N] (added when accumulate); the
+    Strehl ratio into the float64 scalar d_strehl when given."""
+    _check(_lib.pas_psf_compute(psf, _ptr(d_opd), _ptr(d_psf), 1 if accumulate else 0, _ptr(d_strehl)), ctx)
+
+
+def pas_psf_destroy(psf):
+    _lib.pas_psf_destroy(psf)
