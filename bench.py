@@ -274,7 +274,7 @@ def bench_other_workloads(timed, peaks, n_steps=200):
     return out
 
 
-def bench_psf(timed, n_frames=100):
+def bench_psf(timed, sysg=None, n_frames=100):
     """PSF camera on the LBT-class optics at the paper's camera settings (1650 nm,
     padding 8: a 1920 x 1920 grid), integrating every frame into a long-exposure PSF:
     frames/s and the FP32 roofline of its two FFT passes. The residual is a smooth
@@ -302,11 +302,28 @@ def bench_psf(timed, n_frames=100):
         flops = (Np + N) * 5.0 * N * math.log2(N) + 4.0 * N * N
         bytes_ = 8.0 * N * N + 4.0 * Np * Np + 2 * 8.0 * N * Np   # PSF read+write, OPD, intermediate
         ach = flops / per / 1e12
-        return {"workload": f"PSF {N}x{N} (Np {Np}, nd {nd}, 1650 nm), integrated each frame",
-                "frames_per_s": n_frames / (ms * 1e-3), "us_per_frame": per * 1e6,
-                "strehl": float(sr.item()), "flops_per_frame": flops, "bytes_per_frame": bytes_,
-                "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": ach / FP32_PEAK_TFLOPS}}
+        out = {"workload": f"PSF {N}x{N} (Np {Np}, nd {nd}, 1650 nm), integrated each frame",
+               "frames_per_s": n_frames / (ms * 1e-3), "us_per_frame": per * 1e6,
+               "strehl": float(sr.item()), "flops_per_frame": flops, "bytes_per_frame": bytes_,
+               "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": ach / FP32_PEAK_TFLOPS}}
+        if sysg is not None:
+            # the headline loop with the camera integrating every step (graph launch +
+            # the camera's two kernels per step), then the loop state is restored
+            zeros = np.zeros((sysg.delay, sysg.n_modes), dtype=np.float32)
+            sysg.attach_camera(nd=nd, wavelength_nm=1650.0, start_step=0)
+            try:
+                sysg.set_state(0, zeros)
+                sysg.step(5)
+                sysg.set_state(0, zeros)
+                ms_l = timed(lambda: sysg.step(1), n_frames)
+                torch.cuda.synchronize()
+                out["loop_with_camera_steps_per_s"] = n_frames / (ms_l * 1e-3)
+                out["loop_with_camera_mean_strehl"] = float(sysg.sr[:n_frames].mean().item())
+            finally:
+                sysg.detach_camera()
+                sysg.set_state(0, zeros)
+        return out
     finally:
         pas.pas_psf_destroy(h)
         pas.pas_ctx_destroy(ctx)
@@ -683,7 +700,7 @@ def main():
         except Exception as e:
             extra["other_workloads"] = {"error": str(e)}
         try:
-            extra["psf_camera"] = bench_psf(timed)
+            extra["psf_camera"] = bench_psf(timed, sysg)
         except Exception as e:
             extra["psf_camera"] = {"error": str(e)}
         try:

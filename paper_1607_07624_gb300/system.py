@@ -138,10 +138,49 @@ class SCAOSystem:
         return calib.pseudo_inverse(self.IM, rcond)
 
     def step(self, n=1, stats=False):
-        return P.pas_loop_step(self.loop, self.ctx, n, stats)
+        cam = getattr(self, "camera", None)
+        if cam is None:
+            out = P.pas_loop_step(self.loop, self.ctx, n, stats)
+            self._t = getattr(self, "_t", 0) + n
+            return out
+        # with a camera: after each loop step from its start step on, the PSF of that
+        # step's residual is added to int_psf and its Strehl ratio written to sr[t mod len]
+        t = getattr(self, "_t", 0)
+        for _ in range(n):
+            P.pas_loop_step(self.loop, self.ctx, 1, False)
+            if t >= self.camera_start:
+                slot = self.sr.data_ptr() + 8 * (t % self.sr.numel())
+                P.pas_psf_compute(cam, self.ctx, self.loop_opd, self.int_psf, True, slot)
+            t += 1
+        self._t = t
+        return P.pas_loop_step(self.loop, self.ctx, 0, True) if stats else None
+
+    # ---------------------------------------------------------------- camera
+    def attach_camera(self, nd=8, wavelength_nm=1650.0, start_step=0, sr_history=None):
+        """PSF camera on the loop's residual (Table 1 camera: imaging wavelength,
+        padding nd, integration start): from loop step `start_step` on, every step's
+        PSF ([N][N], N = nd Np, peak 1 for a flat wavefront at (N/2, N/2)) is added to
+        `int_psf` and its Strehl ratio written to `sr` (float64 ring; entry t mod its
+        length belongs to step t). Returns N."""
+        self.detach_camera()
+        self.camera = P.pas_psf_create(self.ctx, self.cfg.Np, nd, wavelength_nm, self.cfg.obs)
+        N = P.pas_psf_size(self.camera)
+        self.int_psf = torch.zeros(N, N, device=self.dev, dtype=torch.float32)
+        self.sr = torch.zeros(sr_history or getattr(self, "wfe_history", 1024), device=self.dev,
+                              dtype=torch.float64)
+        self.camera_start = int(start_step)
+        return N
+
+    def detach_camera(self):
+        cam = getattr(self, "camera", None)
+        if cam is not None:
+            torch.cuda.synchronize()
+            P.pas_psf_destroy(cam)
+        self.camera = None
 
     def step_eager(self, n=1):
         P.pas_loop_step_eager(self.loop, self.ctx, n)
+        self._t = getattr(self, "_t", 0) + n
 
     def wfe_nm(self, n_steps):
         """Per-step residual WFE [nm] of the first n_steps (n_steps <= history)."""
@@ -153,8 +192,11 @@ class SCAOSystem:
 
     def set_state(self, step, ring):
         P.pas_loop_set_state(self.loop, self.ctx, step, ring)
+        self._t = int(step)
 
     def close(self):
+        if getattr(self, "ctx", None):
+            self.detach_camera()
         dm = getattr(self, "dm", None) if getattr(self, "own_dm", True) else None
         for h, f in ((getattr(self, "loop", None), P.pas_loop_destroy), (getattr(self, "rec", None), P.pas_recon_destroy),
                      (dm, P.pas_dm_destroy), (getattr(self, "pyr", None), P.pas_pyr_destroy),

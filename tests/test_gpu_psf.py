@@ -103,3 +103,33 @@ def test_bad_arguments_are_rejected(env):
             pas.pas_psf_compute(h, ctx, None, torch.zeros(256, 256, device="cuda"))
     finally:
         pas.pas_psf_destroy(h)
+
+
+def test_camera_in_the_closed_loop_matches_oracle(env):
+    """SCAOSystem.attach_camera: from the start step on, each step's PSF of the loop's
+    residual is integrated and its Strehl ratio recorded (against the oracle on the
+    same float32 residuals, copied after every step)."""
+    torch, pas, ctx = env
+    from oracle import psf as ps
+    from paper_1607_07624_gb300.system import SCAOSystem
+    cfg = get_config(1)
+    s = SCAOSystem(cfg, wfe_history=64)
+    try:
+        N = s.attach_camera(nd=4, wavelength_nm=LAM, start_step=2)
+        assert N == 4 * cfg.Np
+        opds = []
+        for _ in range(6):
+            s.step(1)
+            torch.cuda.synchronize()
+            opds.append(s.loop_opd.cpu().numpy().astype(np.float64))
+        ref = ps.integrated_psf(opds, LAM, cfg.obs, 4, start=2)
+        P = s.int_psf.cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(P - ref)) <= 1e-5 * ref.max()
+        sr = s.sr.cpu().numpy()
+        for t in range(6):
+            want = ps.strehl(opds[t], LAM, cfg.obs) if t >= 2 else 0.0
+            assert abs(sr[t] - want) <= 1e-5, (t, sr[t], want)
+        s.detach_camera()
+        s.step(2)                       # without the camera the loop runs on
+    finally:
+        s.close()
