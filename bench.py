@@ -329,6 +329,43 @@ def bench_psf(timed, sysg=None, n_frames=100):
         pas.pas_ctx_destroy(ctx)
 
 
+def bench_sh(timed, n_frames=200):
+    """Shack-Hartmann sensor on the LBT-class geometry (240 px pupil, 30 x 30 lenslets of
+    8 px, Nyquist spots of 16 x 16 px, 750 nm): frame + slopes per measurement,
+    frames/s, and the FP32 roofline of the lenslet DFTs (two dense products per
+    lenslet: b M b + M M b complex multiply-adds)."""
+    import numpy as np
+    import torch
+    from paper_1607_07624_gb300 import pas
+    from synth import get_config
+    from synth.inputs import random_opd_nm
+    cfg = get_config(2)
+    Np, n_sub, ovs = cfg.Np, cfg.n_sub, 2
+    ctx = pas.pas_ctx_create(torch.cuda.current_stream())
+    h = pas.pas_sh_create(ctx, Np, n_sub, ovs, cfg.wavelength_nm, cfg.obs)
+    try:
+        side, nv = pas.pas_sh_frame_side(h), pas.pas_sh_n_valid(h)
+        opd = torch.as_tensor(random_opd_nm(Np, 150.0, seed=3).astype(np.float32)).cuda()
+        fr = torch.zeros(side, side, device="cuda")
+        sl = torch.zeros(2 * nv, device="cuda")
+        for _ in range(5):
+            pas.pas_sh_measure(h, ctx, opd, fr, sl)
+        ms = timed(lambda: pas.pas_sh_measure(h, ctx, opd, fr, sl), n_frames)
+        torch.cuda.synchronize()
+        b = Np // n_sub
+        M = ovs * b
+        flops = n_sub * n_sub * 8.0 * (b * M * b + M * M * b)
+        per = ms / n_frames * 1e-3
+        ach = flops / per / 1e12
+        return {"workload": f"Shack-Hartmann {n_sub}x{n_sub} lenslets of {b} px, {M}x{M} spots, {nv} valid",
+                "frames_per_s": n_frames / (ms * 1e-3), "us_per_frame": per * 1e6, "flops_per_frame": flops,
+                "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": ach / FP32_PEAK_TFLOPS}}
+    finally:
+        pas.pas_sh_destroy(h)
+        pas.pas_ctx_destroy(ctx)
+
+
 def bench_batch(timed, n_loops=64, n_steps=100):
     """Monte-Carlo batch: n_loops realisations of the 64 px workload (own screens
     each; basis, reconstructor and launch geometry shared) stepped by one graph
@@ -703,6 +740,10 @@ def main():
             extra["psf_camera"] = bench_psf(timed, sysg)
         except Exception as e:
             extra["psf_camera"] = {"error": str(e)}
+        try:
+            extra["shack_hartmann"] = bench_sh(timed)
+        except Exception as e:
+            extra["shack_hartmann"] = {"error": str(e)}
         try:
             extra["monte_carlo_batch"] = bench_batch(timed)
         except Exception as e:

@@ -56,6 +56,7 @@ typedef struct pas_loop_s*  pas_loop_t;
 typedef struct pas_mlp_s*   pas_mlp_t;
 typedef struct pas_batch_s* pas_batch_t;
 typedef struct pas_psf_s*   pas_psf_t;
+typedef struct pas_sh_s*    pas_sh_t;
 
 /* ------------------------------------------------------------------ context */
 
@@ -359,6 +360,34 @@ int32_t pas_psf_size(pas_psf_t psf);
 pas_status pas_psf_compute(pas_psf_t psf, const float* d_opd, float* d_psf, int32_t accumulate,
                            double* d_strehl);
 void pas_psf_destroy(pas_psf_t psf);
+
+/* ------------------------------------------------------ Shack-Hartmann WFS
+ * The framework's second sensor type (Sec. GPU acceleration, "Pyramid and Shack
+ * Hartmann propagation (from wavefront to detector plane)"; the paper gives no
+ * parameters). An n_sub x n_sub lenslet array on the Np x Np pupil, b = Np / n_sub
+ * pupil pixels per lenslet (integer); lenslet (r, c)'s field E = A exp(2 pi i opd /
+ * lambda) zero-padded to M x M, M = ovs b (even, <= 32), gives the spot
+ *   I(k, l) = |sum_ij E(i, j) exp(-2 pi i ((k - M/2) i + (l - M/2) j) / M)|^2 / M^2
+ * (zero frequency at pixel (M/2, M/2); one pixel = lambda / (ovs d); a spot sums to
+ * its lenslet's lit pupil pixels). Spots tile the frame [(n_sub M)][(n_sub M)], lenslet
+ * (r, c) at rows r M .. r M + M - 1, columns c M .. c M + M - 1. Slopes: centre of
+ * gravity about (M/2, M/2) in pixels, x along axis 0, layout [x; y] over the valid
+ * lenslets (ascending r n_sub + c; NULL h_valid: the pyramid's geometric rule, see
+ * pas_valid_subaps), minus the reference (pas_sh_set_reference). */
+pas_status pas_sh_create(pas_ctx_t ctx, int32_t Np, int32_t n_sub, int32_t ovs, double wavelength_nm,
+                         double obs, const int32_t* h_valid, int32_t n_valid, pas_sh_t* out);
+/* Number of valid lenslets; side of the frame (n_sub M); -1 for a NULL handle. Host only. */
+int32_t pas_sh_n_valid(pas_sh_t sh);
+int32_t pas_sh_frame_side(pas_sh_t sh);
+/* Copy the valid lenslet indices to host memory (cap >= n_valid). Synchronous. */
+pas_status pas_sh_get_valid(pas_sh_t sh, int32_t* h_valid, int32_t cap);
+/* d_ref: device float32 [2 n_valid] reference slopes (copied), NULL to clear. */
+pas_status pas_sh_set_reference(pas_sh_t sh, const float* d_ref);
+/* d_opd: device float32 [Np][Np] (nm); d_frame (may be NULL): device float32
+ * [(n_sub M)^2]; d_slopes (may be NULL): device float32 [2 n_valid]. Asynchronous on
+ * the context stream; allocates nothing. */
+pas_status pas_sh_measure(pas_sh_t sh, const float* d_opd, float* d_frame, float* d_slopes);
+void pas_sh_destroy(pas_sh_t sh);
 
 /* -------------------------------------------------- learned reconstructor
  * A multilayer perceptron from slopes to modal coefficients, used by the loop

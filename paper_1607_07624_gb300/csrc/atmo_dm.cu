@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(ResArgs a) {
   __syncthreads();
   const int px = tid;
   const int p = base + px;
-  double s1 = 0.0, s2 = 0.0;
+  float s1 = 0.f, s2 = 0.f;
   if (px < RES_TILE && p < a.n_pix) {
     const int flat = s_flat[px];
     float atm = 0.f;
@@ -267,22 +267,28 @@ __global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(ResArgs a) {
     const float r = atm - a.dm_sign * dm;
     a.out[flat] = r;
     s1 = r;
-    s2 = (double)r * r;
+    s2 = r * r;
   }
   if (a.wfe_part) {
-    for (int o = 16; o > 0; o >>= 1) {
-      s1 += __shfl_down_sync(0xffffffffu, s1, o);
-      s2 += __shfl_down_sync(0xffffffffu, s2, o);
-    }
+    // the tile's (sum r, sum r^2): float within each of the output warps (FP64 is a
+    // slow pipe here), the warps' sums added in double by thread 0
+    constexpr int OUT_WARPS = RES_TILE / 32;
     const int warp = tid >> 5, lane = tid & 31;
-    if (lane == 0) {
-      wred[0][warp] = s1;
-      wred[1][warp] = s2;
+    if (warp < OUT_WARPS) {
+      float f1 = (float)s1, f2 = (float)s2;
+      for (int o = 16; o > 0; o >>= 1) {
+        f1 += __shfl_down_sync(0xffffffffu, f1, o);
+        f2 += __shfl_down_sync(0xffffffffu, f2, o);
+      }
+      if (lane == 0) {
+        wred[0][warp] = f1;
+        wred[1][warp] = f2;
+      }
     }
     __syncthreads();
     if (tid == 0) {
       double t1 = 0.0, t2 = 0.0;
-      for (int w = 0; w < RES_THREADS / 32; ++w) {
+      for (int w = 0; w < OUT_WARPS; ++w) {
         t1 += wred[0][w];
         t2 += wred[1][w];
       }

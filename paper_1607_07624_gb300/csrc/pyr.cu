@@ -170,6 +170,24 @@ __device__ inline double block_sum(double v, double* red) {
   return r;
 }
 
+// Block sum of one float per thread: float within each warp (fixed shuffle tree),
+// the warps' sums added in double in warp order (FP64 is a slow pipe on this GPU,
+// so it is kept out of the per-thread work). Result in every thread.
+__device__ inline double block_sum_f(float v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = (double)v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    red[0] = t;
+  }
+  __syncthreads();
+  return red[0];
+}
+
 // Column q of the detector: sum of the G groups' partials / K, noise, and the
 // column's flux over the valid sub-apertures' pixels (run by the column's last CTA,
 // on the step's critical path: the partials are fetched 8 at a time and summed in
@@ -180,7 +198,7 @@ __device__ __noinline__ void finish_column(const FrameArgs& f, const float* part
   constexpr int BATCH = 8;
   int g = 1;
   while (g < 8 && nd * g * 2 <= (int)blockDim.x) g *= 2;
-  double flux = 0.0;
+  float flux = 0.f;
   for (int t0 = 0; t0 < nd * g; t0 += blockDim.x) {  // the same trip count in every thread
     const int t = t0 + threadIdx.x;
     const int p = t / g, sub = t - p * g;
@@ -204,9 +222,9 @@ __device__ __noinline__ void finish_column(const FrameArgs& f, const float* part
       if (valid_pix) flux += v;
     }
   }
-  flux = block_sum(flux, red);
+  const double col_flux = block_sum_f(flux, red);
   if (threadIdx.x == 0) {
-    f.flux_part[q] = flux;
+    f.flux_part[q] = col_flux;
     f.done_col[q] = 0u;
   }
 }
@@ -262,7 +280,7 @@ __global__ void __launch_bounds__(256) slopes_kernel(FrameArgs f, int nd) {
     q10 = f.frame[i10];
     q11 = f.frame[i11];
   }
-  const float F = (float)(block_sum(fl, red) / (double)f.nv);
+  const float F = (float)(block_sum_f((float)fl, red) / (double)f.nv);
   if (mine) {
     const float den = f.local_norm ? (q00 + q01 + q10 + q11) : F;
     const float inv = 1.0f / den;

@@ -126,6 +126,13 @@ _SIGS = {
     "pas_psf_size": (i32, [vp]),
     "pas_psf_compute": (C.c_int, [vp, vp, vp, i32, vp]),
     "pas_psf_destroy": (None, [vp]),
+    "pas_sh_create": (C.c_int, [vp, i32, i32, i32, C.c_double, C.c_double, vp, i32, P(vp)]),
+    "pas_sh_n_valid": (i32, [vp]),
+    "pas_sh_frame_side": (i32, [vp]),
+    "pas_sh_get_valid": (C.c_int, [vp, vp, i32]),
+    "pas_sh_set_reference": (C.c_int, [vp, vp]),
+    "pas_sh_measure": (C.c_int, [vp, vp, vp, vp]),
+    "pas_sh_destroy": (None, [vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -522,3 +529,39 @@ def pas_psf_compute(psf, ctx, d_opd, d_psf, accumulate=False, d_strehl=None):
 
 def pas_psf_destroy(psf):
     _lib.pas_psf_destroy(psf)
+
+
+# ------------------------------------------------------ Shack-Hartmann WFS
+
+def pas_sh_create(ctx, Np, n_sub, ovs, wavelength_nm, obs, valid=None):
+    h = vp()
+    v = None if valid is None else np.ascontiguousarray(valid, dtype=np.int32)
+    _check(_lib.pas_sh_create(ctx, int(Np), int(n_sub), int(ovs), float(wavelength_nm), float(obs),
+                              None if v is None else v.ctypes.data, 0 if v is None else int(v.size), C.byref(h)), ctx)
+    return h
+
+
+def pas_sh_n_valid(sh):
+    return int(_lib.pas_sh_n_valid(sh))
+
+
+def pas_sh_frame_side(sh):
+    return int(_lib.pas_sh_frame_side(sh))
+
+
+def pas_sh_get_valid(sh, ctx):
+    out = np.zeros(pas_sh_n_valid(sh), dtype=np.int32)
+    _check(_lib.pas_sh_get_valid(sh, out.ctypes.data, out.size), ctx)
+    return out
+
+
+def pas_sh_set_reference(sh, ctx, d_ref):
+    _check(_lib.pas_sh_set_reference(sh, _ptr(d_ref)), ctx)
+
+
+def pas_sh_measure(sh, ctx, d_opd, d_frame=None, d_slopes=None):
+    _check(_lib.pas_sh_measure(sh, _ptr(d_opd), _ptr(d_frame), _ptr(d_slopes)), ctx)
+
+
+def pas_sh_destroy(sh):
+    _lib.pas_sh_destroy(sh)

@@ -1,0 +1,92 @@
+"""GPU Shack-Hartmann sensor (pas_sh_*) against the FP64 oracle, element by element.
+
+Tolerances (FP32 path): frame max |dI| <= 1e-5 max I_oracle; slopes max |ds| <=
+1e-5 max |s_oracle| + 2e-5 pixel. The valid lenslet map is compared bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from synth.inputs import random_opd_nm, screen_white_noise
+
+pytestmark = pytest.mark.gpu
+
+LAM = 750.0
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_1607_07624_gb300 import pas
+    assert torch.cuda.is_available()
+    ctx = pas.pas_ctx_create()
+    yield torch, pas, ctx
+    torch.cuda.synchronize()
+    pas.pas_ctx_destroy(ctx)
+
+
+def open_loop_opd(Np, dx, seed):
+    from oracle import atmosphere as at
+    S = max(64, 1 << (2 * Np - 1).bit_length())
+    scr = at.phase_screen_rad(S, dx, 0.15, 25.0, screen_white_noise(S, seed))
+    return (scr[:Np, :Np] * 500.0 / (2 * math.pi)).astype(np.float32)
+
+
+def run_sh(env, Np, n_sub, ovs, obs, opd32, ref=None):
+    torch, pas, ctx = env
+    h = pas.pas_sh_create(ctx, Np, n_sub, ovs, LAM, obs)
+    try:
+        side = pas.pas_sh_frame_side(h)
+        nv = pas.pas_sh_n_valid(h)
+        fr = torch.zeros(side, side, device="cuda")
+        sl = torch.zeros(2 * nv, device="cuda")
+        if ref is not None:
+            pas.pas_sh_set_reference(h, ctx, torch.as_tensor(ref).cuda())
+        pas.pas_sh_measure(h, ctx, torch.as_tensor(opd32).cuda(), fr, sl)
+        torch.cuda.synchronize()
+        return fr.cpu().numpy().astype(np.float64), sl.cpu().numpy().astype(np.float64), pas.pas_sh_get_valid(h, ctx)
+    finally:
+        pas.pas_sh_destroy(h)
+
+
+@pytest.mark.parametrize("Np,n_sub,ovs,obs,kind", [
+    (64, 16, 2, 0.1, "small"), (64, 8, 2, 0.1, "open"), (48, 16, 2, 0.1, "open"), (120, 10, 2, 0.0, "small"),
+    (64, 4, 2, 0.1, "small"), (240, 30, 2, 0.1, "small"), (240, 30, 2, 0.1, "open"), (96, 12, 3, 0.2, "open")])
+def test_sh_matches_oracle(env, Np, n_sub, ovs, obs, kind):
+    from oracle import optics as op
+    from oracle import shack_hartmann as sh
+    opd = random_opd_nm(Np, 60.0, seed=Np + n_sub).astype(np.float32) if kind == "small" \
+        else open_loop_opd(Np, 8.4 / Np, Np + 7 * n_sub)
+    fr, sl, valid = run_sh(env, Np, n_sub, ovs, obs, opd)
+    assert np.array_equal(valid, op.valid_subapertures(Np, obs, n_sub))
+    fo, so = sh.sh_measure(opd.astype(np.float64), LAM, obs, n_sub, ovs)
+    assert np.max(np.abs(fr - fo)) <= 1e-5 * fo.max()
+    assert np.max(np.abs(sl - so)) <= 1e-5 * np.max(np.abs(so)) + 2e-5
+
+
+def test_reference_cancels_and_tilt_sign(env):
+    torch, pas, ctx = env
+    Np, n_sub, ovs = 64, 8, 2
+    flat = np.zeros((Np, Np), np.float32)
+    _, ref, _ = run_sh(env, Np, n_sub, ovs, 0.1, flat)
+    _, s0, _ = run_sh(env, Np, n_sub, ovs, 0.1, flat, ref=ref.astype(np.float32))
+    assert np.max(np.abs(s0)) == 0.0
+    # a small tilt along axis 0 moves every x centroid the same positive way
+    b = Np // n_sub
+    tilt = np.repeat((0.05 * LAM * np.arange(Np) / b)[:, None], Np, 1).astype(np.float32)
+    _, st, _ = run_sh(env, Np, n_sub, ovs, 0.1, tilt, ref=ref.astype(np.float32))
+    nv = st.size // 2
+    assert np.all(st[:nv] > 0.05) and np.max(np.abs(st[nv:])) < 1e-4
+
+
+def test_bad_arguments_are_rejected(env):
+    torch, pas, ctx = env
+    with pytest.raises(pas.PasError):
+        pas.pas_sh_create(ctx, 64, 10, 2, LAM, 0.1)     # 10 does not divide 64
+    with pytest.raises(pas.PasError):
+        pas.pas_sh_create(ctx, 60, 20, 1, LAM, 0.1)     # spot side 3 is odd
+    with pytest.raises(pas.PasError):
+        pas.pas_sh_create(ctx, 64, 2, 2, LAM, 0.1)      # spot side 64 > 32
+    with pytest.raises(pas.PasError):
+        pas.pas_sh_create(ctx, 64, 8, 2, LAM, 0.1, valid=np.array([3, 2], np.int32))
