@@ -357,13 +357,24 @@ def bench_sh(timed, n_frames=200):
         flops = n_sub * n_sub * 8.0 * (b * M * b + M * M * b)
         per = ms / n_frames * 1e-3
         ach = flops / per / 1e12
-        return {"workload": f"Shack-Hartmann {n_sub}x{n_sub} lenslets of {b} px, {M}x{M} spots, {nv} valid",
-                "frames_per_s": n_frames / (ms * 1e-3), "us_per_frame": per * 1e6, "flops_per_frame": flops,
-                "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": ach / FP32_PEAK_TFLOPS}}
+        out = {"workload": f"Shack-Hartmann {n_sub}x{n_sub} lenslets of {b} px, {M}x{M} spots, {nv} valid",
+               "frames_per_s": n_frames / (ms * 1e-3), "us_per_frame": per * 1e6, "flops_per_frame": flops,
+               "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": ach / FP32_PEAK_TFLOPS}}
     finally:
         pas.pas_sh_destroy(h)
         pas.pas_ctx_destroy(ctx)
+    # the closed loop with this sensor in place of the pyramid (noiseless; same
+    # atmosphere, KL basis and integrator; calibrated by push-pull through the sensor)
+    from paper_1607_07624_gb300.system import SCAOSystem
+    s = SCAOSystem(cfg, sensor="sh", sh_ovs=ovs, wfe_history=max(4096, n_frames + 64))
+    try:
+        sps, wfe = timed_loop(s, timed, n_frames)
+        out["loop_steps_per_s"] = sps
+        out["loop_wfe_nm_first_steps"] = [float(x) for x in wfe[:5]]
+    finally:
+        s.close()
+    return out
 
 
 def bench_batch(timed, n_loops=64, n_steps=100):

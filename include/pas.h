@@ -287,6 +287,14 @@ typedef struct {
 pas_status pas_loop_create(pas_ctx_t ctx, pas_atmo_t atmo, pas_pyr_t pyr, pas_recon_t rec,
                            pas_dm_t dm, const float* d_gain, int32_t delay,
                            int32_t wfe_history, pas_loop_t* out);
+/* The same loop with a Shack-Hartmann sensor (pas_sh_*) in place of the pyramid:
+ * a step is residual -> lenslet spots and centroid slopes -> reconstructor and
+ * integrator (noiseless; the frame of pas_loop_buffers is the sensor's). Everything
+ * else (steps, state, buffers, learned reconstructor, batches) works the same;
+ * pas_loop_profile answers PAS_ESTATE (its kernel list is the pyramid loop's). */
+pas_status pas_loop_create_sh(pas_ctx_t ctx, pas_atmo_t atmo, pas_sh_t sh, pas_recon_t rec,
+                              pas_dm_t dm, const float* d_gain, int32_t delay,
+                              int32_t wfe_history, pas_loop_t* out);
 /* Run n_steps >= 0 steps. If h_stats != NULL the call synchronises and fills it. */
 pas_status pas_loop_step(pas_loop_t loop, int32_t n_steps, pas_loop_stats* h_stats);
 /* Same step launched kernel by kernel without the graph (for comparison). */

@@ -41,9 +41,11 @@ def residual_opd(opd_atm: np.ndarray, M: np.ndarray, c: np.ndarray, mask: np.nda
 
 
 def closed_loop(cfg, screens_nm, M, R, sn, valid, n_steps, gain=None, delay=None,
-                noise=None, use_fft=True, record=False):
+                noise=None, use_fft=True, record=False, sensor=None):
     """Run the SCAO loop for n_steps; returns dict with per-step WFE [nm] and the
-    final command (and per-step slopes/commands if record)."""
+    final command (and per-step slopes/commands if record). sensor: None for the
+    modulated pyramid of cfg, else a callable (opd_res, t) -> (frame, slopes)
+    already referenced (e.g. the Shack-Hartmann oracle)."""
     gain = cfg.gain if gain is None else gain
     delay = cfg.delay if delay is None else delay
     mask = pupil_mask(cfg.Np, cfg.obs)
@@ -56,12 +58,15 @@ def closed_loop(cfg, screens_nm, M, R, sn, valid, n_steps, gain=None, delay=None
     for t in range(n_steps):
         opd_res = residual_opd(atmo_opd(screens_nm, vel, t, cfg.Np), M, applied[0], mask)
         wfe[t] = residual_wfe_nm(opd_res, mask)
-        I = pwfs_intensity(opd_res, cfg.wavelength_nm, cfg.obs, cfg.N, cfg.K,
-                           cfg.mod_radius, cfg.delta, use_fft=use_fft)
-        frame = detector_frame(I, cfg.n_sub)
-        if noise is not None:
-            frame = noise(frame, t)
-        s = pwfs_slopes(frame, valid, cfg.n_sub, sn)
+        if sensor is None:
+            I = pwfs_intensity(opd_res, cfg.wavelength_nm, cfg.obs, cfg.N, cfg.K,
+                               cfg.mod_radius, cfg.delta, use_fft=use_fft)
+            frame = detector_frame(I, cfg.n_sub)
+            if noise is not None:
+                frame = noise(frame, t)
+            s = pwfs_slopes(frame, valid, cfg.n_sub, sn)
+        else:
+            frame, s = sensor(opd_res, t)
         c = integrator_step(c, R @ s, gain)
         applied.append(c.copy())
         if record:

@@ -12,11 +12,13 @@
 #include "mlp.cuh"
 #include "pyr.cuh"
 #include "recon.cuh"
+#include "sh.cuh"
 
 struct pas_loop_s {
   pas_ctx_t ctx = nullptr;
   pas_atmo_t atmo = nullptr;
   pas_pyr_t pyr = nullptr;
+  pas_sh_t sh = nullptr;    // a Shack-Hartmann loop: the sensor in place of the pyramid
   pas_recon_t rec = nullptr;
   pas_dm_t dm = nullptr;
   pas_mlp_t mlp = nullptr;  // learned reconstructor in place of rec (optional)
@@ -69,7 +71,10 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   fa.wfe_hist = L->d_wfe;
   fa.wfe_hist_len = L->hist;
   fa.step = L->d_step;
-  s = pas::pyr_launch(L->pyr, L->d_opd, L->d_frame, L->d_slopes, st, &fa, false, ev ? ev + 1 : nullptr, pdl);
+  if (L->sh)
+    s = pas::sh_launch(L->sh, L->d_opd, L->d_frame, L->d_slopes, st, &fa, pdl);
+  else
+    s = pas::pyr_launch(L->pyr, L->d_opd, L->d_frame, L->d_slopes, st, &fa, false, ev ? ev + 1 : nullptr, pdl);
   if (s != PAS_OK) return s;
   pas::ReconArgs rc;
   rc.s = L->d_slopes;
@@ -109,26 +114,31 @@ void pas_loop_destroy(pas_loop_t L) {
   delete L;
 }
 
-pas_status pas_loop_create(pas_ctx_t ctx, pas_atmo_t atmo, pas_pyr_t pyr, pas_recon_t rec, pas_dm_t dm,
-                           const float* d_gain, int32_t delay, int32_t wfe_history, pas_loop_t* out) {
-  if (!ctx || !atmo || !pyr || !rec || !dm || !d_gain || !out)
+// One sensor, pyramid or Shack-Hartmann, is given.
+static pas_status loop_create(pas_ctx_t ctx, pas_atmo_t atmo, pas_pyr_t pyr, pas_sh_t sh, pas_recon_t rec,
+                              pas_dm_t dm, const float* d_gain, int32_t delay, int32_t wfe_history,
+                              pas_loop_t* out) {
+  if (!ctx || !atmo || !(pyr || sh) || !rec || !dm || !d_gain || !out)
     return pas::set_global_error(PAS_EINVAL, "pas_loop_create: NULL argument");
   *out = nullptr;
   PAS_CHECK_ARG(ctx, delay >= 1 && delay <= 64 && wfe_history >= 1, "pas_loop_create: bad delay or history");
   PAS_CHECK_ARG(ctx, atmo->args.Np == dm->Np, "pas_loop_create: atmosphere and DM pupil sizes differ");
   PAS_CHECK_ARG(ctx, rec->n_modes == dm->n_modes, "pas_loop_create: reconstructor and DM mode counts differ");
-  PAS_CHECK_ARG(ctx, rec->n_slopes == 2 * pas_pyr_n_valid(pyr), "pas_loop_create: reconstructor slopes != 2 n_valid");
+  const int n_slopes = sh ? pas::sh_n_slopes(sh) : 2 * pas_pyr_n_valid(pyr);
+  PAS_CHECK_ARG(ctx, rec->n_slopes == n_slopes, "pas_loop_create: reconstructor slopes != 2 n_valid");
+  PAS_CHECK_ARG(ctx, !sh || pas::sh_np(sh) == dm->Np, "pas_loop_create: sensor and DM pupil sizes differ");
   pas_loop_t L = new pas_loop_s();
   L->ctx = ctx;
   L->atmo = atmo;
   L->pyr = pyr;
+  L->sh = sh;
   L->rec = rec;
   L->dm = dm;
   L->delay = delay;
   L->hist = wfe_history;
   L->n_m = dm->n_modes;
   L->n_slopes = rec->n_slopes;
-  L->nd = pas::pyr_nd(pyr);
+  L->nd = sh ? pas::sh_frame_side(sh) : pas::pyr_nd(pyr);  // side of the detector frame
   L->Np = dm->Np;
   L->n_tiles = pas::residual_tiles(dm->n_pix);
   pas_status st = PAS_OK;
@@ -161,6 +171,18 @@ pas_status pas_loop_create(pas_ctx_t ctx, pas_atmo_t atmo, pas_pyr_t pyr, pas_re
   }
   *out = L;
   return PAS_OK;
+}
+
+pas_status pas_loop_create(pas_ctx_t ctx, pas_atmo_t atmo, pas_pyr_t pyr, pas_recon_t rec, pas_dm_t dm,
+                           const float* d_gain, int32_t delay, int32_t wfe_history, pas_loop_t* out) {
+  if (!pyr) return pas::set_global_error(PAS_EINVAL, "pas_loop_create: NULL pyramid");
+  return loop_create(ctx, atmo, pyr, nullptr, rec, dm, d_gain, delay, wfe_history, out);
+}
+
+pas_status pas_loop_create_sh(pas_ctx_t ctx, pas_atmo_t atmo, pas_sh_t sh, pas_recon_t rec, pas_dm_t dm,
+                              const float* d_gain, int32_t delay, int32_t wfe_history, pas_loop_t* out) {
+  if (!sh) return pas::set_global_error(PAS_EINVAL, "pas_loop_create_sh: NULL sensor");
+  return loop_create(ctx, atmo, nullptr, sh, rec, dm, d_gain, delay, wfe_history, out);
 }
 
 static pas_status loop_capture(pas_loop_t L) {
@@ -224,6 +246,7 @@ pas_status pas_loop_step_eager(pas_loop_t L, int32_t n_steps) {
 pas_status pas_loop_profile(pas_loop_t L, int32_t n_steps, float* h_ms, int32_t cap, int32_t* n_kernels) {
   if (!L || !h_ms) return pas::set_global_error(PAS_EINVAL, "pas_loop_profile: NULL argument");
   PAS_CHECK_ARG(L->ctx, n_steps >= 1 && cap >= PAS_LOOP_KERNELS, "pas_loop_profile: bad n_steps or cap");
+  if (L->sh) return pas::set_error(L->ctx, PAS_ESTATE, "pas_loop_profile: the kernel list is the pyramid loop's");
   pas_ctx_t ctx = L->ctx;
   if (!L->prof_exec) {
     for (int i = 0; i <= PAS_LOOP_KERNELS; ++i) PAS_CUDA_TRY(ctx, cudaEventCreate(&L->prof_ev[i]));

@@ -28,6 +28,7 @@
 #include "pdl.cuh"
 #include "phasor.cuh"
 #include "pyr.cuh"
+#include "wfe.cuh"
 
 namespace pas {
 
@@ -153,23 +154,6 @@ pyr_rows_kernel(RowArgs a) {
   }
 }
 
-__device__ inline double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (warp == 0) {
-    r = lane < nw ? red[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-    if (lane == 0) red[0] = r;
-  }
-  __syncthreads();
-  r = red[0];
-  return r;
-}
-
 // Block sum of one float per thread: float within each warp (fixed shuffle tree),
 // the warps' sums added in double in warp order (FP64 is a slow pipe on this GPU,
 // so it is kept out of the per-thread work). Result in every thread.
@@ -254,21 +238,7 @@ __global__ void __launch_bounds__(256) slopes_kernel(FrameArgs f, int nd) {
       sny = f.sn[f.nv + j];
     }
   }
-  if (blockIdx.x == 0 && f.wfe.wfe_part) {
-    double s1 = 0.0, s2 = 0.0;
-    for (int t = threadIdx.x; t < f.wfe.n_wfe_part; t += blockDim.x) {
-      const double2 w = f.wfe.wfe_part[t];
-      s1 += w.x;
-      s2 += w.y;
-    }
-    s1 = block_sum(s1, red);
-    s2 = block_sum(s2, red);
-    if (threadIdx.x == 0) {
-      const double m = s1 * f.wfe.inv_npix;
-      const double var = fmax(s2 * f.wfe.inv_npix - m * m, 0.0);
-      f.wfe.wfe_hist[(*f.wfe.step) % f.wfe.wfe_hist_len] = sqrt(var);
-    }
-  }
+  if (blockIdx.x == 0 && f.wfe.wfe_part) wfe_finalize(f.wfe, red);
   pdl_wait();
   // the frame and the column fluxes: all loads in one round
   double fl = 0.0;

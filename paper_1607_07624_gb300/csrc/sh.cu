@@ -23,6 +23,8 @@
 #include "internal.h"
 #include "pdl.cuh"
 #include "phasor.cuh"
+#include "sh.cuh"
+#include "wfe.cuh"
 
 namespace pas {
 
@@ -35,6 +37,7 @@ struct ShArgs {
   float* slopes;         // [2 nv] or null
   int Np, n_sub, b, M, nv, T_obs;
   float inv_hi, inv_lo, inv_M2;
+  LoopExtra wfe;         // in a loop: the step's residual WFE, closed by CTA 0
 };
 
 __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
@@ -44,6 +47,7 @@ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
 __global__ void __launch_bounds__(1024) sh_kernel(ShArgs a) {
   extern __shared__ float2 sh_smem[];
   __shared__ float3 red[32];
+  __shared__ double dred[32];
   const int b = a.b, M = a.M;
   float2* W_s = sh_smem;          // [M][b]
   float2* E_s = W_s + M * b;      // [b][b]
@@ -52,7 +56,8 @@ __global__ void __launch_bounds__(1024) sh_kernel(ShArgs a) {
   const int tid = threadIdx.x;
   pdl_trigger();
   for (int t = tid; t < M * b; t += blockDim.x) W_s[t] = a.W[t];
-  pdl_wait();  // the OPD may come from the preceding kernel
+  pdl_wait();  // the OPD (and the WFE partials) may come from the preceding kernel
+  if (blockIdx.x == 0 && a.wfe.wfe_part) wfe_finalize(a.wfe, dred);
   const int Np = a.Np;
   for (int t = tid; t < b * b; t += blockDim.x) {
     const int i = t / b, j = t - i * b;
@@ -125,6 +130,40 @@ struct pas_sh_s {
   int32_t* d_valid = nullptr;
   float* d_ref = nullptr;
 };
+
+namespace pas {
+
+pas_status sh_launch(pas_sh_t S, const float* d_opd, float* d_frame, float* d_slopes, cudaStream_t st,
+                     const LoopExtra* extra, bool pdl) {
+  ShArgs a;
+  a.opd = d_opd;
+  a.W = S->d_W;
+  a.slope_of = S->d_slope_of;
+  a.ref = S->has_ref ? S->d_ref : nullptr;
+  a.frame = d_frame;
+  a.slopes = d_slopes;
+  a.Np = S->Np;
+  a.n_sub = S->n_sub;
+  a.b = S->b;
+  a.M = S->M;
+  a.nv = S->nv;
+  a.T_obs = S->T_obs;
+  a.inv_hi = S->inv_hi;
+  a.inv_lo = S->inv_lo;
+  a.inv_M2 = S->inv_M2;
+  a.wfe = extra ? *extra : LoopExtra();
+  const size_t smem = sizeof(float2) * ((size_t)2 * S->M * S->b + (size_t)S->b * S->b);
+  const int threads = (S->M * S->M + 31) / 32 * 32;
+  cudaError_t e = launch_k(sh_kernel, dim3(S->n_sub * S->n_sub), dim3(threads), smem, st, pdl, a);
+  if (e != cudaSuccess) return set_error(S->ctx, PAS_ECUDA, "Shack-Hartmann launch: %s", cudaGetErrorString(e));
+  return PAS_OK;
+}
+
+int sh_n_slopes(pas_sh_t S) { return 2 * S->nv; }
+int sh_frame_side(pas_sh_t S) { return S->n_sub * S->M; }
+int sh_np(pas_sh_t S) { return S->Np; }
+
+}  // namespace pas
 
 extern "C" {
 
@@ -231,28 +270,7 @@ pas_status pas_sh_set_reference(pas_sh_t S, const float* d_ref) {
 
 pas_status pas_sh_measure(pas_sh_t S, const float* d_opd, float* d_frame, float* d_slopes) {
   if (!S || !d_opd) return pas::set_global_error(PAS_EINVAL, "pas_sh_measure: NULL argument");
-  pas::ShArgs a;
-  a.opd = d_opd;
-  a.W = S->d_W;
-  a.slope_of = S->d_slope_of;
-  a.ref = S->has_ref ? S->d_ref : nullptr;
-  a.frame = d_frame;
-  a.slopes = d_slopes;
-  a.Np = S->Np;
-  a.n_sub = S->n_sub;
-  a.b = S->b;
-  a.M = S->M;
-  a.nv = S->nv;
-  a.T_obs = S->T_obs;
-  a.inv_hi = S->inv_hi;
-  a.inv_lo = S->inv_lo;
-  a.inv_M2 = S->inv_M2;
-  const size_t smem = sizeof(float2) * ((size_t)2 * S->M * S->b + (size_t)S->b * S->b);
-  const int threads = (S->M * S->M + 31) / 32 * 32;
-  cudaError_t e = pas::launch_k(pas::sh_kernel, dim3(S->n_sub * S->n_sub), dim3(threads), smem,
-                                S->ctx->stream, false, a);
-  if (e != cudaSuccess) return pas::set_error(S->ctx, PAS_ECUDA, "pas_sh_measure launch: %s", cudaGetErrorString(e));
-  return PAS_OK;
+  return pas::sh_launch(S, d_opd, d_frame, d_slopes, S->ctx->stream, nullptr, false);
 }
 
 }  // extern "C"

@@ -96,6 +96,7 @@ _SIGS = {
     "pas_dm_project": (C.c_int, [vp, vp, vp]),
     "pas_dm_destroy": (None, [vp]),
     "pas_loop_create": (C.c_int, [vp, vp, vp, vp, vp, vp, i32, i32, P(vp)]),
+    "pas_loop_create_sh": (C.c_int, [vp, vp, vp, vp, vp, vp, i32, i32, P(vp)]),
     "pas_loop_step": (C.c_int, [vp, i32, P(pas_loop_stats)]),
     "pas_loop_step_eager": (C.c_int, [vp, i32]),
     "pas_loop_buffers": (C.c_int, [vp, P(vp), P(vp), P(vp), P(vp), P(vp), P(vp)]),
@@ -362,6 +363,12 @@ def pas_dm_destroy(dm):
 def pas_loop_create(ctx, atmo, pyr, rec, dm, d_gain, delay=1, wfe_history=1):
     h = vp()
     _check(_lib.pas_loop_create(ctx, atmo, pyr, rec, dm, _ptr(d_gain), delay, wfe_history, C.byref(h)), ctx)
+    return h
+
+
+def pas_loop_create_sh(ctx, atmo, sh, rec, dm, d_gain, delay=1, wfe_history=1):
+    h = vp()
+    _check(_lib.pas_loop_create_sh(ctx, atmo, sh, rec, dm, _ptr(d_gain), delay, wfe_history, C.byref(h)), ctx)
     return h
 
 

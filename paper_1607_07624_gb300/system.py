@@ -34,12 +34,15 @@ class SCAOSystem:
     basis, Zernike or KL);
     R: reconstruction matrix (None: calibrated by push-pull on the GPU);
     autotune: True (time the pyramid launch geometries on the GPU), False (library
-    default) or (rows_per_cta, row_chunks, col_groups[, col_split]) to set one."""
+    default) or (rows_per_cta, row_chunks, col_groups[, col_split]) to set one;
+    sensor: "pyramid" (the configuration's modulated pyramid) or "sh" (a noiseless
+    Shack-Hartmann sensor with the configuration's n_sub lenslets and spots of
+    sh_ovs x the lenslet size, at the configuration's wavelength)."""
 
     def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32, dm_precision=P.PAS_FP32,
                  dm=None,
                  noise=None, delay=None, wfe_history=4096, stream=None, build_loop=True,
-                 autotune=True):
+                 autotune=True, sensor="pyramid", sh_ovs=2):
         from synth.inputs import layer_seeds, screen_white_noise
         self.cfg = cfg
         self.dev = torch.device("cuda")
@@ -56,9 +59,18 @@ class SCAOSystem:
         vel = np.array(cfg.layer_velocity_px(), dtype=np.float64).reshape(-1, 2)
         self.atmo = P.pas_atmo_create(self.ctx, len(cfg.layers), cfg.S, cfg.Np, vel[:, 0], vel[:, 1],
                                       self.d_screens)
-        # pyramid + slope computer
-        self.pyr = P.pas_pyr_create(self.ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius,
-                                    cfg.wavelength_nm, cfg.obs, self.valid)
+        # sensor + slope computer
+        if sensor not in ("pyramid", "sh"):
+            raise ValueError(f"sensor must be 'pyramid' or 'sh', not {sensor!r}")
+        self.sensor = sensor
+        self.pyr = self.sh = None
+        if sensor == "sh":
+            self.sh = P.pas_sh_create(self.ctx, cfg.Np, cfg.n_sub, sh_ovs, cfg.wavelength_nm, cfg.obs, self.valid)
+            frame_side = P.pas_sh_frame_side(self.sh)
+        else:
+            self.pyr = P.pas_pyr_create(self.ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius,
+                                        cfg.wavelength_nm, cfg.obs, self.valid)
+            frame_side = cfg.n_det
         # DM
         if basis is None:
             if cfg.basis == "kl":
@@ -73,41 +85,50 @@ class SCAOSystem:
         # buffers
         f32 = dict(device=self.dev, dtype=torch.float32)
         self.d_opd = torch.zeros(cfg.Np, cfg.Np, **f32)
-        self.d_frame = torch.zeros(cfg.n_det, cfg.n_det, **f32)
+        self.d_frame = torch.zeros(frame_side, frame_side, **f32)
         self.d_slopes = torch.zeros(2 * self.n_valid, **f32)
         self.d_sn = torch.zeros(2 * self.n_valid, **f32)
         # calibration: slope reference (flat wavefront, noiseless)
-        P.pas_pyr_set_reference(self.pyr, self.ctx, None)
+        set_ref = P.pas_sh_set_reference if self.sh else P.pas_pyr_set_reference
+        set_ref(self.sh or self.pyr, self.ctx, None)
         self.measure(self.d_opd, reference=True)
         self.d_sn.copy_(self.d_slopes)
-        P.pas_pyr_set_reference(self.pyr, self.ctx, self.d_sn)
+        set_ref(self.sh or self.pyr, self.ctx, self.d_sn)
         if R is None:
             R = self.calibrate_reconstructor()
         self.R = np.ascontiguousarray(R, dtype=np.float32)
         self.rec = P.pas_recon_create(self.ctx, self.R, recon_precision)
         self.d_gain = torch.full((self.n_modes,), cfg.gain, **f32)
         # launch geometry of the pyramid kernels, measured on the open-loop OPD
-        self.tuning = P.pas_pyr_get_tuning(self.pyr, self.ctx)
-        if isinstance(autotune, (tuple, list)):
+        self.tuning = P.pas_pyr_get_tuning(self.pyr, self.ctx) if self.pyr else None
+        if self.sh:
+            pass
+        elif isinstance(autotune, (tuple, list)):
             P.pas_pyr_set_tuning(self.pyr, self.ctx, *autotune)
             self.tuning = P.pas_pyr_get_tuning(self.pyr, self.ctx)
         elif autotune:
             P.pas_atmo_advance(self.atmo, self.ctx, 0, self.d_opd)
             self.tuning = P.pas_pyr_autotune(self.pyr, self.ctx, self.d_opd, 5)
             self.d_opd.zero_()
-        if noise is None and cfg.magnitude is not None:
+        if noise is None and cfg.magnitude is not None and self.pyr:
             noise = (cfg.photons_per_frame(), cfg.read_noise_e, cfg.seed)
         if noise is not None:
+            if not self.pyr:
+                raise ValueError("the Shack-Hartmann loop is noiseless")
             P.pas_pyr_set_noise(self.pyr, self.ctx, noise[0], noise[1], noise[2], 0)
         self.delay = cfg.delay if delay is None else delay
         self.loop = None
         if build_loop:
-            self.loop = P.pas_loop_create(self.ctx, self.atmo, self.pyr, self.rec, self.dm, self.d_gain,
-                                          self.delay, wfe_history)
+            if self.sh:
+                self.loop = P.pas_loop_create_sh(self.ctx, self.atmo, self.sh, self.rec, self.dm, self.d_gain,
+                                                 self.delay, wfe_history)
+            else:
+                self.loop = P.pas_loop_create(self.ctx, self.atmo, self.pyr, self.rec, self.dm, self.d_gain,
+                                              self.delay, wfe_history)
             b = P.pas_loop_buffers(self.loop, self.ctx)
             self.wfe_history = wfe_history
             self.loop_opd = DevView.tensor(b["opd_res"], (cfg.Np, cfg.Np))
-            self.loop_frame = DevView.tensor(b["frame"], (cfg.n_det, cfg.n_det))
+            self.loop_frame = DevView.tensor(b["frame"], (frame_side, frame_side))
             self.loop_slopes = DevView.tensor(b["slopes"], (2 * self.n_valid,))
             self.loop_dmodes = DevView.tensor(b["dmodes"], (self.n_modes,))
             self.loop_cmd = DevView.tensor(b["cmd"], (self.n_modes,))
@@ -115,12 +136,15 @@ class SCAOSystem:
 
     # ---------------------------------------------------------------- steps
     def measure(self, d_opd, reference=False):
-        """opd -> (frame, slopes) through pas_pyr_measure (device tensors)."""
-        P.pas_pyr_measure(self.pyr, self.ctx, d_opd, self.d_frame, self.d_slopes)
+        """opd -> (frame, slopes) through the sensor (device tensors)."""
+        if self.sh:
+            P.pas_sh_measure(self.sh, self.ctx, d_opd, self.d_frame, self.d_slopes)
+        else:
+            P.pas_pyr_measure(self.pyr, self.ctx, d_opd, self.d_frame, self.d_slopes)
         return self.d_frame, self.d_slopes
 
     def calibrate_reconstructor(self, amp_nm=None, rcond=1e-3):
-        """Push-pull interaction matrix measured by the GPU pyramid; FP64 pinv."""
+        """Push-pull interaction matrix measured by the GPU sensor; FP64 pinv."""
         amp = self.cfg.pushpull_nm if amp_nm is None else amp_nm
         cmd = torch.zeros(self.n_modes, device=self.dev, dtype=torch.float32)
         opd = torch.zeros(self.cfg.Np, self.cfg.Np, device=self.dev, dtype=torch.float32)
@@ -200,10 +224,11 @@ class SCAOSystem:
         dm = getattr(self, "dm", None) if getattr(self, "own_dm", True) else None
         for h, f in ((getattr(self, "loop", None), P.pas_loop_destroy), (getattr(self, "rec", None), P.pas_recon_destroy),
                      (dm, P.pas_dm_destroy), (getattr(self, "pyr", None), P.pas_pyr_destroy),
+                     (getattr(self, "sh", None), P.pas_sh_destroy),
                      (getattr(self, "atmo", None), P.pas_atmo_destroy)):
             if h:
                 f(h)
-        self.loop = self.rec = self.dm = self.pyr = self.atmo = None
+        self.loop = self.rec = self.dm = self.pyr = self.sh = self.atmo = None
         if getattr(self, "ctx", None):
             torch.cuda.synchronize()
             P.pas_ctx_destroy(self.ctx)

@@ -90,3 +90,43 @@ def test_bad_arguments_are_rejected(env):
         pas.pas_sh_create(ctx, 64, 2, 2, LAM, 0.1)      # spot side 64 > 32
     with pytest.raises(pas.PasError):
         pas.pas_sh_create(ctx, 64, 8, 2, LAM, 0.1, valid=np.array([3, 2], np.int32))
+
+
+def test_sh_closed_loop_matches_oracle(env):
+    """The loop with the Shack-Hartmann sensor (pas_loop_create_sh through
+    SCAOSystem(sensor="sh")) against the oracle's closed loop with the oracle sensor:
+    calibration, then per-step residual WFE."""
+    from oracle import atmosphere as at
+    from oracle import control as ct
+    from oracle import modal as md
+    from oracle import optics as op
+    from oracle import shack_hartmann as shm
+    from paper_1607_07624_gb300.system import SCAOSystem
+    from synth import get_config
+    from synth.inputs import layer_seeds
+    cfg = get_config(1)
+    ovs = 2
+    noises = [screen_white_noise(cfg.S, s) for s in layer_seeds(cfg.seed, len(cfg.layers))]
+    screens = at.layer_screens_nm(cfg, noises)
+    M = md.modal_basis(cfg.Np, cfg.obs, cfg.n_modes)
+    valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
+    mask = op.pupil_mask(cfg.Np, cfg.obs)
+    meas = lambda o, ref=None: shm.sh_measure(o, cfg.wavelength_nm, cfg.obs, cfg.n_sub, ovs, valid, ref)
+    sn = meas(np.zeros((cfg.Np, cfg.Np)))[1]
+    IM = md.interaction_matrix(lambda o: meas(o, sn)[1], M, mask, cfg.pushpull_nm)
+    R = md.pseudo_inverse(IM)
+    n = 100
+    wo = ct.closed_loop(cfg, screens, M, R, sn, valid, n, sensor=lambda o, t: meas(o, sn))["wfe"]
+    s = SCAOSystem(cfg, screens=screens.astype(np.float32), basis=M, R=R, wfe_history=n, sensor="sh", sh_ovs=ovs)
+    try:
+        assert np.max(np.abs(s.d_sn.cpu().numpy() - sn)) <= 1e-5 * np.max(np.abs(sn)) + 2e-5
+        s.calibrate_reconstructor()
+        assert np.max(np.abs(s.IM - IM)) <= 1e-3 * np.max(np.abs(IM))
+        step, last = s.step(n, stats=True)
+        assert step == n
+        wg = s.wfe_nm(n)
+        assert abs(last - wg[-1]) == 0.0
+        assert np.max(np.abs(wg - wo)) <= 2.0, np.max(np.abs(wg - wo))
+        assert wg[10:].min() < 0.5 * wg[0]
+    finally:
+        s.close()
