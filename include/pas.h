@@ -288,8 +288,9 @@ pas_status pas_loop_create(pas_ctx_t ctx, pas_atmo_t atmo, pas_pyr_t pyr, pas_re
                            pas_dm_t dm, const float* d_gain, int32_t delay,
                            int32_t wfe_history, pas_loop_t* out);
 /* The same loop with a Shack-Hartmann sensor (pas_sh_*) in place of the pyramid:
- * a step is residual -> lenslet spots and centroid slopes -> reconstructor and
- * integrator (noiseless; the frame of pas_loop_buffers is the sensor's). Everything
+ * a step is residual -> lenslet spots (with the sensor's detector noise, the step
+ * as frame index) and centroid slopes -> reconstructor and integrator (the frame of
+ * pas_loop_buffers is the sensor's). Everything
  * else (steps, state, buffers, learned reconstructor, batches) works the same;
  * pas_loop_profile answers PAS_ESTATE (its kernel list is the pyramid loop's). */
 pas_status pas_loop_create_sh(pas_ctx_t ctx, pas_atmo_t atmo, pas_sh_t sh, pas_recon_t rec,
@@ -391,6 +392,14 @@ int32_t pas_sh_frame_side(pas_sh_t sh);
 pas_status pas_sh_get_valid(pas_sh_t sh, int32_t* h_valid, int32_t cap);
 /* d_ref: device float32 [2 n_valid] reference slopes (copied), NULL to clear. */
 pas_status pas_sh_set_reference(pas_sh_t sh, const float* d_ref);
+/* Detector noise on the frame, as pas_pyr_set_noise: photons_per_frame <= 0 keeps the
+ * frame in intensity units (no noise); otherwise pix_p = Poisson(photons * I_p /
+ * n_pupil_pixels) + read_noise_e * N(0,1) from Philox-4x32-10 (key = seed, counter =
+ * (p, frame, block), p the frame pixel), and the slopes are the noisy frame's
+ * centroids. `frame_index` is the counter of the next standalone measurement (each
+ * increments it); in a loop the loop's step is the frame index. Synchronous. */
+pas_status pas_sh_set_noise(pas_sh_t sh, double photons_per_frame, double read_noise_e,
+                            uint64_t seed, int64_t frame_index);
 /* d_opd: device float32 [Np][Np] (nm); d_frame (may be NULL): device float32
  * [(n_sub M)^2]; d_slopes (may be NULL): device float32 [2 n_valid]. Asynchronous on
  * the context stream; allocates nothing. */

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "noise.cuh"
 #include "pdl.cuh"
 #include "phasor.cuh"
 #include "sh.cuh"
@@ -37,13 +38,18 @@ struct ShArgs {
   float* slopes;         // [2 nv] or null
   int Np, n_sub, b, M, nv, T_obs;
   float inv_hi, inv_lo, inv_M2;
-  LoopExtra wfe;         // in a loop: the step's residual WFE, closed by CTA 0
+  float scale, ron;            // detector noise: photons per intensity unit (<= 0: none), read noise
+  unsigned long long seed;
+  const long long* frame_ctr;  // the frame's noise counter (the loop's step in a loop)
+  LoopExtra wfe;               // in a loop: the step's residual WFE, closed by CTA 0
 };
 
 __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
   return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
 }
 
+// NOISE: the detector-noise variant (its sampler needs more registers).
+template <bool NOISE>
 __global__ void __launch_bounds__(1024) sh_kernel(ShArgs a) {
   extern __shared__ float2 sh_smem[];
   __shared__ float3 red[32];
@@ -85,7 +91,9 @@ __global__ void __launch_bounds__(1024) sh_kernel(ShArgs a) {
     float2 f = make_float2(0.f, 0.f);
     for (int i = 0; i < b; ++i) f = cfma(W_s[k * b + i], T_s[i * M + l], f);
     I = __fmul_rn(__fmaf_rn(f.x, f.x, __fmul_rn(f.y, f.y)), a.inv_M2);
-    if (a.frame) a.frame[((size_t)r * M + k) * ((size_t)a.n_sub * M) + (size_t)c * M + l] = I;
+    const size_t px = ((size_t)r * M + k) * ((size_t)a.n_sub * M) + (size_t)c * M + l;
+    if constexpr (NOISE) I = noisy_pixel(I, a.scale, a.ron, a.seed, (uint32_t)px, (uint64_t)*a.frame_ctr);
+    if (a.frame) a.frame[px] = I;
   }
   const int s = a.slope_of[lens];
   if (s >= 0 && a.slopes) {  // uniform across the CTA
@@ -125,6 +133,10 @@ struct pas_sh_s {
   int Np = 0, n_sub = 0, b = 0, M = 0, nv = 0, T_obs = 0;
   float inv_hi = 0.f, inv_lo = 0.f, inv_M2 = 0.f;
   bool has_ref = false;
+  int n_pupil = 0;
+  float photon_scale = 0.f, ron = 0.f;
+  unsigned long long seed = 0;
+  long long* d_frame_ctr = nullptr;  // noise counter of standalone measurements
   float2* d_W = nullptr;
   int* d_slope_of = nullptr;
   int32_t* d_valid = nullptr;
@@ -132,6 +144,8 @@ struct pas_sh_s {
 };
 
 namespace pas {
+
+__global__ void sh_count_frame(long long* ctr) { *ctr += 1; }
 
 pas_status sh_launch(pas_sh_t S, const float* d_opd, float* d_frame, float* d_slopes, cudaStream_t st,
                      const LoopExtra* extra, bool pdl) {
@@ -151,10 +165,15 @@ pas_status sh_launch(pas_sh_t S, const float* d_opd, float* d_frame, float* d_sl
   a.inv_hi = S->inv_hi;
   a.inv_lo = S->inv_lo;
   a.inv_M2 = S->inv_M2;
+  a.scale = S->photon_scale;
+  a.ron = S->ron;
+  a.seed = S->seed;
+  a.frame_ctr = extra && extra->frame_ctr ? extra->frame_ctr : S->d_frame_ctr;
   a.wfe = extra ? *extra : LoopExtra();
   const size_t smem = sizeof(float2) * ((size_t)2 * S->M * S->b + (size_t)S->b * S->b);
   const int threads = (S->M * S->M + 31) / 32 * 32;
-  cudaError_t e = launch_k(sh_kernel, dim3(S->n_sub * S->n_sub), dim3(threads), smem, st, pdl, a);
+  cudaError_t e = a.scale > 0.f ? launch_k(sh_kernel<true>, dim3(S->n_sub * S->n_sub), dim3(threads), smem, st, pdl, a)
+                                 : launch_k(sh_kernel<false>, dim3(S->n_sub * S->n_sub), dim3(threads), smem, st, pdl, a);
   if (e != cudaSuccess) return set_error(S->ctx, PAS_ECUDA, "Shack-Hartmann launch: %s", cudaGetErrorString(e));
   return PAS_OK;
 }
@@ -173,6 +192,7 @@ void pas_sh_destroy(pas_sh_t S) {
   pas::dev_free(S->d_slope_of);
   pas::dev_free(S->d_valid);
   pas::dev_free(S->d_ref);
+  pas::dev_free(S->d_frame_ctr);
   delete S;
 }
 
@@ -221,6 +241,7 @@ pas_status pas_sh_create(pas_ctx_t ctx, int32_t Np, int32_t n_sub, int32_t ovs, 
   S->inv_hi = (float)inv;
   S->inv_lo = (float)(inv - (double)S->inv_hi);
   S->inv_M2 = (float)(1.0 / ((double)M * M));
+  pas_pupil_mask(Np, obs, nullptr, &S->n_pupil);
   pas_status st = PAS_OK;
   auto A = [&](void** p, size_t bytes) {
     if (st == PAS_OK) st = pas::dev_alloc(ctx, p, bytes);
@@ -229,6 +250,7 @@ pas_status pas_sh_create(pas_ctx_t ctx, int32_t Np, int32_t n_sub, int32_t ovs, 
   A((void**)&S->d_slope_of, sizeof(int) * slope_of.size());
   A((void**)&S->d_valid, sizeof(int32_t) * valid.size());
   A((void**)&S->d_ref, sizeof(float) * 2 * valid.size());
+  A((void**)&S->d_frame_ctr, sizeof(long long));
   if (st != PAS_OK) {
     pas_sh_destroy(S);
     return st;
@@ -238,6 +260,7 @@ pas_status pas_sh_create(pas_ctx_t ctx, int32_t Np, int32_t n_sub, int32_t ovs, 
     e = cudaMemcpy(S->d_slope_of, slope_of.data(), sizeof(int) * slope_of.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(S->d_valid, valid.data(), sizeof(int32_t) * valid.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(S->d_frame_ctr, 0, sizeof(long long));
   if (e != cudaSuccess) {
     pas_sh_destroy(S);
     return pas::set_error(ctx, PAS_ECUDA, "pas_sh_create: %s", cudaGetErrorString(e));
@@ -270,7 +293,23 @@ pas_status pas_sh_set_reference(pas_sh_t S, const float* d_ref) {
 
 pas_status pas_sh_measure(pas_sh_t S, const float* d_opd, float* d_frame, float* d_slopes) {
   if (!S || !d_opd) return pas::set_global_error(PAS_EINVAL, "pas_sh_measure: NULL argument");
-  return pas::sh_launch(S, d_opd, d_frame, d_slopes, S->ctx->stream, nullptr, false);
+  pas_status st = pas::sh_launch(S, d_opd, d_frame, d_slopes, S->ctx->stream, nullptr, false);
+  if (st != PAS_OK || !(S->photon_scale > 0.f)) return st;
+  pas::sh_count_frame<<<1, 1, 0, S->ctx->stream>>>(S->d_frame_ctr);  // the next frame's counter
+  return pas::check_launch(S->ctx, "Shack-Hartmann frame counter");
+}
+
+pas_status pas_sh_set_noise(pas_sh_t S, double photons_per_frame, double read_noise_e, uint64_t seed,
+                            int64_t frame_index) {
+  if (!S) return pas::set_global_error(PAS_EINVAL, "pas_sh_set_noise: NULL sensor");
+  PAS_CHECK_ARG(S->ctx, read_noise_e >= 0.0 && frame_index >= 0, "pas_sh_set_noise: bad read noise or frame index");
+  S->photon_scale = photons_per_frame > 0.0 ? (float)(photons_per_frame / (double)S->n_pupil) : 0.f;
+  S->ron = (float)read_noise_e;
+  S->seed = seed;
+  long long f = frame_index;
+  PAS_CUDA_TRY(S->ctx, cudaMemcpyAsync(S->d_frame_ctr, &f, sizeof(f), cudaMemcpyHostToDevice, S->ctx->stream));
+  PAS_CUDA_TRY(S->ctx, cudaStreamSynchronize(S->ctx->stream));
+  return PAS_OK;
 }
 
 }  // extern "C"

@@ -132,6 +132,7 @@ _SIGS = {
     "pas_sh_frame_side": (i32, [vp]),
     "pas_sh_get_valid": (C.c_int, [vp, vp, i32]),
     "pas_sh_set_reference": (C.c_int, [vp, vp]),
+    "pas_sh_set_noise": (C.c_int, [vp, C.c_double, C.c_double, C.c_uint64, i64]),
     "pas_sh_measure": (C.c_int, [vp, vp, vp, vp]),
     "pas_sh_destroy": (None, [vp]),
 }
@@ -564,6 +565,10 @@ def pas_sh_get_valid(sh, ctx):
 
 def pas_sh_set_reference(sh, ctx, d_ref):
     _check(_lib.pas_sh_set_reference(sh, _ptr(d_ref)), ctx)
+
+
+def pas_sh_set_noise(sh, ctx, photons, read_noise_e, seed, frame_index=0):
+    _check(_lib.pas_sh_set_noise(sh, float(photons), float(read_noise_e), int(seed), int(frame_index)), ctx)
 
 
 def pas_sh_measure(sh, ctx, d_opd, d_frame=None, d_slopes=None):

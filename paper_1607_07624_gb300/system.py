@@ -35,9 +35,9 @@ class SCAOSystem:
     R: reconstruction matrix (None: calibrated by push-pull on the GPU);
     autotune: True (time the pyramid launch geometries on the GPU), False (library
     default) or (rows_per_cta, row_chunks, col_groups[, col_split]) to set one;
-    sensor: "pyramid" (the configuration's modulated pyramid) or "sh" (a noiseless
-    Shack-Hartmann sensor with the configuration's n_sub lenslets and spots of
-    sh_ovs x the lenslet size, at the configuration's wavelength)."""
+    sensor: "pyramid" (the configuration's modulated pyramid) or "sh" (a Shack-Hartmann
+    sensor with the configuration's n_sub lenslets and spots of sh_ovs x the lenslet
+    size, at the configuration's wavelength, with the same detector noise)."""
 
     def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32, dm_precision=P.PAS_FP32,
                  dm=None,
@@ -110,12 +110,11 @@ class SCAOSystem:
             P.pas_atmo_advance(self.atmo, self.ctx, 0, self.d_opd)
             self.tuning = P.pas_pyr_autotune(self.pyr, self.ctx, self.d_opd, 5)
             self.d_opd.zero_()
-        if noise is None and cfg.magnitude is not None and self.pyr:
+        if noise is None and cfg.magnitude is not None:
             noise = (cfg.photons_per_frame(), cfg.read_noise_e, cfg.seed)
         if noise is not None:
-            if not self.pyr:
-                raise ValueError("the Shack-Hartmann loop is noiseless")
-            P.pas_pyr_set_noise(self.pyr, self.ctx, noise[0], noise[1], noise[2], 0)
+            set_noise = P.pas_sh_set_noise if self.sh else P.pas_pyr_set_noise
+            set_noise(self.sh or self.pyr, self.ctx, noise[0], noise[1], noise[2], 0)
         self.delay = cfg.delay if delay is None else delay
         self.loop = None
         if build_loop:

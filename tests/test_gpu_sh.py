@@ -130,3 +130,43 @@ def test_sh_closed_loop_matches_oracle(env):
         assert wg[10:].min() < 0.5 * wg[0]
     finally:
         s.close()
+
+
+def test_sh_detector_noise_matches_oracle_counts(env):
+    """Photon and read noise on the Shack-Hartmann frame against the oracle's draw on
+    the same noiseless float32 frame; the slopes are the noisy frame's centroids."""
+    torch, pas, ctx = env
+    from oracle import noise as nz
+    from oracle import shack_hartmann as shm
+    Np, n_sub, ovs, obs = 64, 8, 2, 0.1
+    opd = random_opd_nm(Np, 60.0, seed=5).astype(np.float32)
+    n_pupil = int(pas.pas_pupil_pixels(Np, obs).size)
+    photons, ron, seed = 30.0 * n_pupil, 0.5, 77
+    h = pas.pas_sh_create(ctx, Np, n_sub, ovs, LAM, obs)
+    try:
+        side, nv = pas.pas_sh_frame_side(h), pas.pas_sh_n_valid(h)
+        fr = torch.zeros(side, side, device="cuda")
+        sl = torch.zeros(2 * nv, device="cuda")
+        d_opd = torch.as_tensor(opd).cuda()
+        pas.pas_sh_measure(h, ctx, d_opd, fr)
+        torch.cuda.synchronize()
+        clean = fr.cpu().numpy().astype(np.float64)
+        for fi, r in ((3, ron), (4, 0.0)):
+            pas.pas_sh_set_noise(h, ctx, photons, r, seed, fi)
+            pas.pas_sh_measure(h, ctx, d_opd, fr, sl)
+            torch.cuda.synchronize()
+            g = fr.cpu().numpy().astype(np.float64)
+            o = nz.apply_noise(clean, photons, n_pupil, r, seed, fi)
+            if r > 0:
+                close = np.abs(g - o) <= 1e-5 * np.maximum(1.0, np.abs(o))
+                assert close.mean() >= 0.999, close.mean()
+            else:
+                assert np.mean(g == o) >= 0.999
+            so = shm.sh_slopes(g, pas.pas_sh_get_valid(h, ctx), n_sub)
+            assert np.max(np.abs(sl.cpu().numpy() - so)) <= 1e-5 * np.max(np.abs(so)) + 2e-5
+        # the counter advanced by one per noisy measurement
+        pas.pas_sh_measure(h, ctx, d_opd, fr)
+        torch.cuda.synchronize()
+        assert np.mean(fr.cpu().numpy() == nz.apply_noise(clean, photons, n_pupil, 0.0, seed, 5)) >= 0.999
+    finally:
+        pas.pas_sh_destroy(h)
