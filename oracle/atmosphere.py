@@ -16,7 +16,12 @@ the readings are:
   * on-axis source: the layer's pupil footprint is the pupil itself, shifted by the
     wind: at step t the pupil pixel (i, j) samples the screen at
     (i - t vx, j - t vy), vx, vy in pixels per step (FP64, no running sum),
-    bilinear interpolation with periodic wrap.
+    bilinear interpolation with periodic wrap;
+  * a natural guide star off axis at polar coordinates (rho arcsec, phi degrees
+    counter-clockwise from axis 0; Table 1 wfs_source.polar_coordinate) sees layer l
+    at height h_l through a footprint moved by h_l theta: pixel (i, j) samples
+    (i + ox_l - t vx, j + oy_l - t vy) with (ox_l, oy_l) = h_l theta (cos phi, sin phi)
+    / dx, theta = rho in radians (no footprint scaling: the source is at infinity).
 """
 from __future__ import annotations
 
@@ -81,13 +86,24 @@ def layer_offset(step: int, v: float) -> float:
     return float(step) * v
 
 
-def atmo_opd(screens_nm: np.ndarray, velocities_px, step: int, Np: int) -> np.ndarray:
-    """Sum over layers of the wind-shifted screens on the Np x Np pupil grid [nm]."""
+def footprint_offsets_px(heights_m, rho_arcsec: float, phi_deg: float, dx: float):
+    """Per-layer footprint offsets (ox, oy) [px] for a source at infinity in the
+    direction (rho arcsec, phi degrees from axis 0)."""
+    theta = rho_arcsec * math.pi / (180.0 * 3600.0)
+    c, s = math.cos(math.radians(phi_deg)), math.sin(math.radians(phi_deg))
+    return [(h * theta * c / dx, h * theta * s / dx) for h in heights_m]
+
+
+def atmo_opd(screens_nm: np.ndarray, velocities_px, step: int, Np: int, offsets_px=None) -> np.ndarray:
+    """Sum over layers of the wind-shifted screens on the Np x Np pupil grid [nm],
+    each layer's footprint moved by its (ox, oy) offset [px] when given."""
     i = np.arange(Np, dtype=np.float64)
     I, J = np.meshgrid(i, i, indexing="ij")
     out = np.zeros((Np, Np))
-    for scr, (vx, vy) in zip(screens_nm, velocities_px):
-        out += bilinear_sample(scr, I - layer_offset(step, vx), J - layer_offset(step, vy))
+    if offsets_px is None:
+        offsets_px = [(0.0, 0.0)] * len(velocities_px)
+    for scr, (vx, vy), (ox, oy) in zip(screens_nm, velocities_px, offsets_px):
+        out += bilinear_sample(scr, I + (ox - layer_offset(step, vx)), J + (oy - layer_offset(step, vy)))
     return out
 
 

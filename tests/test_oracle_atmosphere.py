@@ -128,3 +128,31 @@ def test_layer_r0_scaling():
     one = at.layer_screens_nm(with_(cfg, layers=(LayerSpec(1.0, 0, 1.0),)), w)
     quarter = at.layer_screens_nm(with_(cfg, layers=(LayerSpec(0.25, 0, 1.0),)), w)
     assert np.allclose(quarter, 0.5 * one)
+
+
+def test_off_axis_footprint_offsets():
+    """An off-axis source moves each layer's footprint by h theta: an integer offset
+    is an exact copy of the shifted screen, an offset o equals the wind displacement
+    of a step t with t v = -o, and zero offsets leave the on-axis sum unchanged."""
+    import math
+    rng = np.random.default_rng(4)
+    S, Np = 64, 16
+    scr = rng.standard_normal((2, S, S))
+    vel = [(0.3, -0.2), (0.0, 0.7)]
+    on = at.atmo_opd(scr, vel, 5, Np)
+    assert np.array_equal(on, at.atmo_opd(scr, vel, 5, Np, [(0.0, 0.0), (0.0, 0.0)]))
+    # integer offsets at step 0: a plain window of each screen
+    o = at.atmo_opd(scr, [(0.0, 0.0), (0.0, 0.0)], 0, Np, [(3.0, -2.0), (-5.0, 4.0)])
+    ref = sum(np.roll(np.roll(scr[l], -int(dx), 0), -int(dy), 1)[:Np, :Np]
+              for l, (dx, dy) in enumerate([(3, -2), (-5, 4)]))
+    assert np.max(np.abs(o - ref)) < 1e-12
+    # offset = -t v reproduces step t of the on-axis sum (to float64 rounding)
+    t = 7
+    off = [(-t * vx, -t * vy) for vx, vy in vel]
+    assert np.max(np.abs(at.atmo_opd(scr, vel, 0, Np, off) - at.atmo_opd(scr, vel, t, Np))) < 1e-9
+    # geometry: 10 arcsec at 45 degrees, layers at 0 and 8 km, 3.5 cm pixels
+    oo = at.footprint_offsets_px([0.0, 8000.0], 10.0, 45.0, 0.035)
+    theta = 10.0 / 206264.80624709636                    # arcseconds per radian
+    assert oo[0] == (0.0, 0.0)
+    assert abs(oo[1][0] - 8000.0 * theta * math.cos(math.pi / 4) / 0.035) < 1e-9
+    assert abs(oo[1][0] - oo[1][1]) < 1e-9 and oo[1][0] > 0
