@@ -106,7 +106,7 @@ pas_status pas_valid_subaps(int Np, double obs, int n_sub, int32_t* valid, int32
  * get_atmo_container, get_atmo_propagation; Sec. GPU acceleration, "wavefront
  * propagation through phase screens").
  * At step t, pupil pixel (i,j) samples layer l at (i - t*vx[l], j - t*vy[l])
- * (screen pixels, periodic, bilinear). The displacement t*v is one FP64 product
+ * (screen pixels, periodic, bilinear; plus the footprint offsets of a view, below). The displacement t*v is one FP64 product
  * from the integer step; floor gives the integer shift and the remainder,
  * rounded to float32, the interpolation weights. */
 typedef struct {
@@ -124,6 +124,13 @@ pas_status pas_atmo_create(pas_ctx_t ctx, const pas_atmo_params* p, const float*
 /* d_opd: device float32 [Np][Np], the summed OPD of all layers at `step`
  * (every pixel of the square, no pupil mask). */
 pas_status pas_atmo_advance(pas_atmo_t atmo, int64_t step, float* d_opd);
+/* A second atmosphere object on the same screens and winds, seen along another
+ * direction: a natural guide star off axis moves layer l's footprint by h_l theta,
+ * so pupil pixel (i,j) samples (i + ox[l] - t vx[l], j + oy[l] - t vy[l]); h_ox,
+ * h_oy: host [L] offsets in screen pixels (added to base's own), finite. The view
+ * shares base's screens (base's must outlive it); loops and advances use it like
+ * any atmosphere. Host only. */
+pas_status pas_atmo_create_view(pas_atmo_t base, const double* h_ox, const double* h_oy, pas_atmo_t* out);
 void pas_atmo_destroy(pas_atmo_t atmo);
 
 /* ------------------------------------------------------ modulated pyramid

@@ -170,3 +170,13 @@ def pseudo_inverse(IM: np.ndarray, rcond: float = 1e-3) -> np.ndarray:
     U, s, Vt = np.linalg.svd(np.asarray(IM, dtype=np.float64), full_matrices=False)
     keep = s >= rcond * s.max()
     return (Vt[keep].T * (1.0 / s[keep])) @ U[:, keep].T
+
+
+def footprint_offsets_px(heights_m, rho_arcsec: float, phi_deg: float, dx: float):
+    """Per-layer footprint offsets (ox, oy) in screen pixels of a natural guide star
+    off axis at (rho arcsec, phi degrees counter-clockwise from axis 0): layer h is
+    crossed at h * theta from the on-axis footprint (Table 1 wfs_source
+    polar_coordinate; a source at infinity, no footprint scaling)."""
+    theta = math.radians(rho_arcsec / 3600.0)
+    phi = math.radians(phi_deg)
+    return [(h * theta * math.cos(phi) / dx, h * theta * math.sin(phi) / dx) for h in heights_m]

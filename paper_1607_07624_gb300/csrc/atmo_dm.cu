@@ -13,10 +13,11 @@
 
 namespace pas {
 
-// Per-layer integer shift and float32 bilinear weights at `step`:
-// sample position of pupil pixel i is i - step*v = i + n + f, n = floor(-step*v).
-__device__ inline void layer_shift(double v, long long step, int S, int* n_mod, float* f) {
-  const double d = -(double)step * v;
+// Per-layer integer shift and float32 bilinear weights at `step`: sample position of
+// pupil pixel i is i + o - step*v = i + n + f, n = floor(o - step*v) (o: the layer's
+// footprint offset for an off-axis source, 0 on axis).
+__device__ inline void layer_shift(double v, double o, long long step, int S, int* n_mod, float* f) {
+  const double d = o - (double)step * v;
   const double n = floor(d);
   *f = (float)(d - n);
   long long ni = (long long)n % S;
@@ -101,8 +102,8 @@ __global__ void atmo_kernel(AtmoArgs a, const long long* d_step, long long h_ste
   __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
   const long long step = d_step ? *d_step : h_step;
   if (threadIdx.x < a.L) {
-    layer_shift(a.vx[threadIdx.x], step, a.S, &six[threadIdx.x], &sfx[threadIdx.x]);
-    layer_shift(a.vy[threadIdx.x], step, a.S, &siy[threadIdx.x], &sfy[threadIdx.x]);
+    layer_shift(a.vx[threadIdx.x], a.ox[threadIdx.x], step, a.S, &six[threadIdx.x], &sfx[threadIdx.x]);
+    layer_shift(a.vy[threadIdx.x], a.oy[threadIdx.x], step, a.S, &siy[threadIdx.x], &sfy[threadIdx.x]);
   }
   __syncthreads();
   const int n = a.Np * a.Np;
@@ -197,8 +198,8 @@ __global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(ResArgs a) {
   const float* cmd = a.cmd;
   if (a.cmd_ring) cmd = a.cmd_ring + (size_t)(step % a.delay) * a.n_m;
   if (tid < L) {
-    layer_shift(a.atmo.vx[tid], step, a.atmo.S, &six[tid], &sfx[tid]);
-    layer_shift(a.atmo.vy[tid], step, a.atmo.S, &siy[tid], &sfy[tid]);
+    layer_shift(a.atmo.vx[tid], a.atmo.ox[tid], step, a.atmo.S, &six[tid], &sfx[tid]);
+    layer_shift(a.atmo.vy[tid], a.atmo.oy[tid], step, a.atmo.S, &siy[tid], &sfy[tid]);
   }
   for (int m = tid; m < n_m; m += RES_THREADS) c_s[m] = cmd[m];
   __syncthreads();
@@ -415,6 +416,20 @@ pas_status pas_atmo_advance(pas_atmo_t a, int64_t step, float* d_opd) {
   const int blocks = std::min((n + 255) / 256, 4 * std::max(a->ctx->sm_count, 1));
   pas::atmo_kernel<<<blocks, 256, 0, a->ctx->stream>>>(a->args, nullptr, step, d_opd);
   return pas::check_launch(a->ctx, "pas_atmo_advance launch");
+}
+
+pas_status pas_atmo_create_view(pas_atmo_t base, const double* h_ox, const double* h_oy, pas_atmo_t* out) {
+  if (!base || !h_ox || !h_oy || !out) return pas::set_global_error(PAS_EINVAL, "pas_atmo_create_view: NULL argument");
+  *out = nullptr;
+  for (int l = 0; l < base->args.L; ++l)
+    PAS_CHECK_ARG(base->ctx, std::isfinite(h_ox[l]) && std::isfinite(h_oy[l]), "pas_atmo_create_view: offsets not finite");
+  pas_atmo_t a = new pas_atmo_s(*base);
+  for (int l = 0; l < PAS_MAX_LAYERS; ++l) {
+    a->args.ox[l] = l < base->args.L ? base->args.ox[l] + h_ox[l] : 0.0;
+    a->args.oy[l] = l < base->args.L ? base->args.oy[l] + h_oy[l] : 0.0;
+  }
+  *out = a;
+  return PAS_OK;
 }
 
 void pas_atmo_destroy(pas_atmo_t a) { delete a; }

@@ -10,6 +10,8 @@ struct AtmoArgs {
   int L = 0, S = 0, Np = 0;
   double vx[PAS_MAX_LAYERS] = {};
   double vy[PAS_MAX_LAYERS] = {};
+  double ox[PAS_MAX_LAYERS] = {};  // footprint offsets of an off-axis source [px]
+  double oy[PAS_MAX_LAYERS] = {};
 };
 
 struct ResArgs {

@@ -73,6 +73,7 @@ _SIGS = {
     "pas_valid_subaps": (C.c_int, [C.c_int, f64, C.c_int, vp, i32, P(i32)]),
     "pas_atmo_create": (C.c_int, [vp, P(pas_atmo_params), vp, P(vp)]),
     "pas_atmo_advance": (C.c_int, [vp, i64, vp]),
+    "pas_atmo_create_view": (C.c_int, [vp, vp, vp, P(vp)]),
     "pas_atmo_destroy": (None, [vp]),
     "pas_pyr_supported": (C.c_int, [C.c_int]),
     "pas_pyr_create": (C.c_int, [vp, P(pas_pyr_params), vp, i32, P(vp)]),
@@ -235,6 +236,15 @@ def pas_atmo_create(ctx, n_layers, S, Np, vx, vy, d_screens):
 
 def pas_atmo_advance(atmo, ctx, step: int, d_opd):
     _check(_lib.pas_atmo_advance(atmo, int(step), _ptr(d_opd)), ctx)
+
+
+def pas_atmo_create_view(atmo, ctx, ox, oy):
+    """The same layers seen along another direction: per-layer footprint offsets [px]."""
+    ox = np.ascontiguousarray(ox, dtype=np.float64)
+    oy = np.ascontiguousarray(oy, dtype=np.float64)
+    h = vp()
+    _check(_lib.pas_atmo_create_view(atmo, ox.ctypes.data, oy.ctypes.data, C.byref(h)), ctx)
+    return h
 
 
 def pas_atmo_destroy(atmo):

@@ -37,12 +37,15 @@ class SCAOSystem:
     default) or (rows_per_cta, row_chunks, col_groups[, col_split]) to set one;
     sensor: "pyramid" (the configuration's modulated pyramid) or "sh" (a Shack-Hartmann
     sensor with the configuration's n_sub lenslets and spots of sh_ovs x the lenslet
-    size, at the configuration's wavelength, with the same detector noise)."""
+    size, at the configuration's wavelength, with the same detector noise);
+    source: None (on axis) or (rho_arcsec, phi_deg), an off-axis natural guide star:
+    the loop sees each layer through a footprint moved by height x angle
+    (pas_atmo_create_view), while `atmo_base` stays the on-axis atmosphere."""
 
     def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32, dm_precision=P.PAS_FP32,
                  dm=None,
                  noise=None, delay=None, wfe_history=4096, stream=None, build_loop=True,
-                 autotune=True, sensor="pyramid", sh_ovs=2):
+                 autotune=True, sensor="pyramid", sh_ovs=2, source=None):
         from synth.inputs import layer_seeds, screen_white_noise
         self.cfg = cfg
         self.dev = torch.device("cuda")
@@ -57,8 +60,14 @@ class SCAOSystem:
             screens = calib.layer_screens(cfg, noises)
         self.d_screens = torch.as_tensor(np.ascontiguousarray(screens, dtype=np.float32)).to(self.dev)
         vel = np.array(cfg.layer_velocity_px(), dtype=np.float64).reshape(-1, 2)
-        self.atmo = P.pas_atmo_create(self.ctx, len(cfg.layers), cfg.S, cfg.Np, vel[:, 0], vel[:, 1],
-                                      self.d_screens)
+        self.atmo_base = P.pas_atmo_create(self.ctx, len(cfg.layers), cfg.S, cfg.Np, vel[:, 0], vel[:, 1],
+                                           self.d_screens)
+        self.atmo = self.atmo_base
+        self.source = source
+        if source is not None:
+            off = np.array(calib.footprint_offsets_px([ly.height_m for ly in cfg.layers], source[0], source[1],
+                                                      cfg.dx), dtype=np.float64).reshape(-1, 2)
+            self.atmo = P.pas_atmo_create_view(self.atmo_base, self.ctx, off[:, 0], off[:, 1])
         # sensor + slope computer
         if sensor not in ("pyramid", "sh"):
             raise ValueError(f"sensor must be 'pyramid' or 'sh', not {sensor!r}")
@@ -169,23 +178,46 @@ class SCAOSystem:
         # with a camera: after each loop step from its start step on, the PSF of that
         # step's residual is added to int_psf and its Strehl ratio written to sr[t mod len]
         t = getattr(self, "_t", 0)
+        sci = self._cmd_queue is not None
         for _ in range(n):
+            applied = self._cmd_queue.popleft() if sci else None   # command applied at step t
             P.pas_loop_step(self.loop, self.ctx, 1, False)
             if t >= self.camera_start:
+                opd = self.loop_opd
+                if sci:   # on-axis residual: the base atmosphere at t minus the applied DM shape
+                    P.pas_atmo_advance(self.atmo_base, self.ctx, t, self._sci_atm)
+                    P.pas_dm_residual(self.dm, self.ctx, self._sci_atm, applied, self._sci_res)
+                    opd = self._sci_res
                 slot = self.sr.data_ptr() + 8 * (t % self.sr.numel())
-                P.pas_psf_compute(cam, self.ctx, self.loop_opd, self.int_psf, True, slot)
+                P.pas_psf_compute(cam, self.ctx, opd, self.int_psf, True, slot)
+            if sci:
+                self._cmd_queue.append(self.loop_cmd.clone())
             t += 1
         self._t = t
         return P.pas_loop_step(self.loop, self.ctx, 0, True) if stats else None
 
     # ---------------------------------------------------------------- camera
-    def attach_camera(self, nd=8, wavelength_nm=1650.0, start_step=0, sr_history=None):
+    def attach_camera(self, nd=8, wavelength_nm=1650.0, start_step=0, sr_history=None, direction="science"):
         """PSF camera on the loop's residual (Table 1 camera: imaging wavelength,
         padding nd, integration start): from loop step `start_step` on, every step's
         PSF ([N][N], N = nd Np, peak 1 for a flat wavefront at (N/2, N/2)) is added to
         `int_psf` and its Strehl ratio written to `sr` (float64 ring; entry t mod its
-        length belongs to step t). Returns N."""
+        length belongs to step t). direction: "science" (on axis) or "wfs" (the guide
+        star's direction); they differ only with an off-axis source. Returns N."""
+        if direction not in ("science", "wfs"):
+            raise ValueError(f"direction must be 'science' or 'wfs', not {direction!r}")
         self.detach_camera()
+        self._cmd_queue = None
+        if direction == "science" and self.source is not None:
+            from collections import deque
+            f32 = dict(device=self.dev, dtype=torch.float32)
+            self._sci_atm = torch.zeros(self.cfg.Np, self.cfg.Np, **f32)
+            self._sci_res = torch.zeros(self.cfg.Np, self.cfg.Np, **f32)
+            t0, ring = self.get_state()
+            # the command applied at steps t0, t0+1, ...: ring slot (t mod delay) before step t
+            self._cmd_queue = deque(torch.as_tensor(ring[(t0 + k) % self.delay]).to(self.dev)
+                                    for k in range(self.delay))
+            self._t = t0
         self.camera = P.pas_psf_create(self.ctx, self.cfg.Np, nd, wavelength_nm, self.cfg.obs)
         N = P.pas_psf_size(self.camera)
         self.int_psf = torch.zeros(N, N, device=self.dev, dtype=torch.float32)
@@ -200,6 +232,7 @@ class SCAOSystem:
             torch.cuda.synchronize()
             P.pas_psf_destroy(cam)
         self.camera = None
+        self._cmd_queue = None
 
     def step_eager(self, n=1):
         P.pas_loop_step_eager(self.loop, self.ctx, n)
@@ -224,10 +257,12 @@ class SCAOSystem:
         for h, f in ((getattr(self, "loop", None), P.pas_loop_destroy), (getattr(self, "rec", None), P.pas_recon_destroy),
                      (dm, P.pas_dm_destroy), (getattr(self, "pyr", None), P.pas_pyr_destroy),
                      (getattr(self, "sh", None), P.pas_sh_destroy),
-                     (getattr(self, "atmo", None), P.pas_atmo_destroy)):
+                     (getattr(self, "atmo", None) if getattr(self, "source", None) is not None else None,
+                      P.pas_atmo_destroy),
+                     (getattr(self, "atmo_base", None), P.pas_atmo_destroy)):
             if h:
                 f(h)
-        self.loop = self.rec = self.dm = self.pyr = self.sh = self.atmo = None
+        self.loop = self.rec = self.dm = self.pyr = self.sh = self.atmo = self.atmo_base = None
         if getattr(self, "ctx", None):
             torch.cuda.synchronize()
             P.pas_ctx_destroy(self.ctx)

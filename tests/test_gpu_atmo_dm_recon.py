@@ -47,6 +47,32 @@ def test_atmosphere_matches_oracle_and_integer_shift_is_exact(env):
         pas.pas_atmo_destroy(atmo)
 
 
+def test_atmosphere_view_of_an_off_axis_source(env):
+    """pas_atmo_create_view: the same screens through footprints moved by per-layer
+    offsets (non-integer, as an off-axis source gives), against the oracle."""
+    torch, pas, ctx = env
+    from oracle import atmosphere as at
+    S, Np = 256, 60
+    scr = np.random.default_rng(8).standard_normal((3, S, S)).astype(np.float32) * 100
+    vel = np.array([[0.37, -0.81], [1.0, 0.0], [-2.0, 3.0]])
+    off = np.array([[0.0, 0.0], [3.7, -12.25], [-30.5, 41.125]])
+    d_scr = torch.as_tensor(scr).cuda()
+    base = pas.pas_atmo_create(ctx, 3, S, Np, vel[:, 0], vel[:, 1], d_scr)
+    view = pas.pas_atmo_create_view(base, ctx, off[:, 0], off[:, 1])
+    out = torch.zeros(Np, Np, device="cuda")
+    try:
+        for step in (0, 5, 600):
+            pas.pas_atmo_advance(view, ctx, step, out)
+            torch.cuda.synchronize()
+            o = at.atmo_opd(scr.astype(np.float64), vel, step, Np, [tuple(x) for x in off])
+            assert np.max(np.abs(out.cpu().numpy() - o)) <= 1e-6 * np.max(np.abs(o)), step
+        with pytest.raises(pas.PasError):
+            pas.pas_atmo_create_view(base, ctx, np.array([0.0, np.nan, 0.0]), off[:, 1])
+    finally:
+        pas.pas_atmo_destroy(view)
+        pas.pas_atmo_destroy(base)
+
+
 @pytest.mark.parametrize("Np,n_modes", [(16, 10), (64, 100), (240, 400)])
 def test_dm_shape_and_residual_match_oracle(env, Np, n_modes):
     torch, pas, ctx = env
