@@ -21,7 +21,10 @@ the readings are:
     counter-clockwise from axis 0; Table 1 wfs_source.polar_coordinate) sees layer l
     at height h_l through a footprint moved by h_l theta: pixel (i, j) samples
     (i + ox_l - t vx, j + oy_l - t vy) with (ox_l, oy_l) = h_l theta (cos phi, sin phi)
-    / dx, theta = rho in radians (no footprint scaling: the source is at infinity).
+    / dx, theta = rho in radians (no footprint scaling: the source is at infinity);
+  * a source at finite height H (a laser guide star) sees layer l through a footprint
+    shrunk by s_l = 1 - h_l / H about the pupil centre c = (Np - 1) / 2 (the cone
+    effect): pixel i samples c + (i - c) s_l + ox_l - t vx (offsets h_l theta as above).
 """
 from __future__ import annotations
 
@@ -94,16 +97,28 @@ def footprint_offsets_px(heights_m, rho_arcsec: float, phi_deg: float, dx: float
     return [(h * theta * c / dx, h * theta * s / dx) for h in heights_m]
 
 
-def atmo_opd(screens_nm: np.ndarray, velocities_px, step: int, Np: int, offsets_px=None) -> np.ndarray:
+def footprint_scales(heights_m, H_m: float):
+    """Per-layer footprint scale 1 - h / H of a source at height H (cone effect)."""
+    return [1.0 - h / H_m for h in heights_m]
+
+
+def atmo_opd(screens_nm: np.ndarray, velocities_px, step: int, Np: int, offsets_px=None,
+             scales=None) -> np.ndarray:
     """Sum over layers of the wind-shifted screens on the Np x Np pupil grid [nm],
-    each layer's footprint moved by its (ox, oy) offset [px] when given."""
+    each layer's footprint moved by its (ox, oy) offset [px] and shrunk by its scale
+    about the pupil centre when given."""
     i = np.arange(Np, dtype=np.float64)
     I, J = np.meshgrid(i, i, indexing="ij")
+    c = (Np - 1) / 2.0
     out = np.zeros((Np, Np))
     if offsets_px is None:
         offsets_px = [(0.0, 0.0)] * len(velocities_px)
-    for scr, (vx, vy), (ox, oy) in zip(screens_nm, velocities_px, offsets_px):
-        out += bilinear_sample(scr, I + (ox - layer_offset(step, vx)), J + (oy - layer_offset(step, vy)))
+    if scales is None:
+        scales = [1.0] * len(velocities_px)
+    for scr, (vx, vy), (ox, oy), sc in zip(screens_nm, velocities_px, offsets_px, scales):
+        Ii = I if sc == 1.0 else c + (I - c) * sc
+        Jj = J if sc == 1.0 else c + (J - c) * sc
+        out += bilinear_sample(scr, Ii + (ox - layer_offset(step, vx)), Jj + (oy - layer_offset(step, vy)))
     return out
 
 

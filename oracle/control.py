@@ -41,12 +41,13 @@ def residual_opd(opd_atm: np.ndarray, M: np.ndarray, c: np.ndarray, mask: np.nda
 
 
 def closed_loop(cfg, screens_nm, M, R, sn, valid, n_steps, gain=None, delay=None,
-                noise=None, use_fft=True, record=False, sensor=None, offsets_px=None):
+                noise=None, use_fft=True, record=False, sensor=None, offsets_px=None, scales=None):
     """Run the SCAO loop for n_steps; returns dict with per-step WFE [nm] and the
     final command (and per-step slopes/commands if record). sensor: None for the
     modulated pyramid of cfg, else a callable (opd_res, t) -> (frame, slopes)
     already referenced (e.g. the Shack-Hartmann oracle); offsets_px: per-layer
-    footprint offsets of an off-axis source (atmosphere.footprint_offsets_px)."""
+    footprint offsets of an off-axis source (atmosphere.footprint_offsets_px);
+    scales: per-layer footprint scales of a source at finite height."""
     gain = cfg.gain if gain is None else gain
     delay = cfg.delay if delay is None else delay
     mask = pupil_mask(cfg.Np, cfg.obs)
@@ -57,7 +58,7 @@ def closed_loop(cfg, screens_nm, M, R, sn, valid, n_steps, gain=None, delay=None
     wfe = np.empty(n_steps)
     hist = {"slopes": [], "cmd": [], "frame": []}
     for t in range(n_steps):
-        opd_res = residual_opd(atmo_opd(screens_nm, vel, t, cfg.Np, offsets_px), M, applied[0], mask)
+        opd_res = residual_opd(atmo_opd(screens_nm, vel, t, cfg.Np, offsets_px, scales), M, applied[0], mask)
         wfe[t] = residual_wfe_nm(opd_res, mask)
         if sensor is None:
             I = pwfs_intensity(opd_res, cfg.wavelength_nm, cfg.obs, cfg.N, cfg.K,

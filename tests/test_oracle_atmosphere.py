@@ -156,3 +156,31 @@ def test_off_axis_footprint_offsets():
     assert oo[0] == (0.0, 0.0)
     assert abs(oo[1][0] - 8000.0 * theta * math.cos(math.pi / 4) / 0.035) < 1e-9
     assert abs(oo[1][0] - oo[1][1]) < 1e-9 and oo[1][0] > 0
+
+
+def test_cone_effect_scales_a_tilt_layer():
+    """Bilinear interpolation reproduces a linear screen exactly, so a tilt layer at
+    height h seen from a source at height H shows its slope times 1 - h/H (the cone
+    effect reduces the tilt a laser guide star sees), centred on the pupil centre;
+    a scale of one leaves the sum unchanged."""
+    S, Np = 128, 20
+    x = np.arange(S, dtype=np.float64)
+    a, b = 0.75, -1.25                        # nm per pixel along axes 0 and 1
+    tilt = a * x[:, None] + b * x[None, :]
+    scr = np.stack([tilt, np.zeros((S, S))])
+    vel = [(0.0, 0.0), (0.0, 0.0)]
+    H, h = 90000.0, 12000.0
+    sc = at.footprint_scales([h, 0.0], H)
+    assert sc[0] == 1.0 - h / H and sc[1] == 1.0
+    off = [(30.0, 40.0), (0.0, 0.0)]
+    o = at.atmo_opd(scr, vel, 0, Np, off, sc)
+    i = np.arange(Np, dtype=np.float64)
+    c = (Np - 1) / 2.0
+    want = a * (c + 30.0 + (i[:, None] - c) * sc[0]) + b * (c + 40.0 + (i[None, :] - c) * sc[0])
+    assert np.max(np.abs(o - want)) < 1e-9
+    gx = np.diff(o, axis=0).mean()
+    assert abs(gx / a - (1.0 - h / H)) < 1e-12
+    rng = np.random.default_rng(2)
+    scr2 = rng.standard_normal((2, S, S))
+    assert np.array_equal(at.atmo_opd(scr2, [(0.4, 0.1), (0.0, -0.3)], 9, Np, None, [1.0, 1.0]),
+                          at.atmo_opd(scr2, [(0.4, 0.1), (0.0, -0.3)], 9, Np))
