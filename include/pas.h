@@ -131,6 +131,16 @@ pas_status pas_atmo_advance(pas_atmo_t atmo, int64_t step, float* d_opd);
  * shares base's screens (base's must outlive it); loops and advances use it like
  * any atmosphere. Host only. */
 pas_status pas_atmo_create_view(pas_atmo_t base, const double* h_ox, const double* h_oy, pas_atmo_t* out);
+/* The same for a source at finite height H (a laser guide star): layer l at height
+ * h_l is seen through a footprint shrunk by s_l = 1 - h_l/H about the pupil centre
+ * c = (Np - 1)/2 (the cone effect), so pupil pixel (i,j) samples
+ * (c + (i - c) s_l + ox[l] - t vx[l], c + (j - c) s_l + oy[l] - t vy[l]), each
+ * position one FP64 value per (layer, pixel). h_scale: host [L], each in (0, 1], or
+ * NULL (all 1: pas_atmo_create_view). A view of a view composes: the new scale is
+ * s_base s and the new offset o_base + s_base o. Host only; EINVAL on a scale
+ * outside (0, 1] or a non-finite offset. */
+pas_status pas_atmo_create_cone_view(pas_atmo_t base, const double* h_ox, const double* h_oy,
+                                     const double* h_scale, pas_atmo_t* out);
 void pas_atmo_destroy(pas_atmo_t atmo);
 
 /* ------------------------------------------------------ modulated pyramid

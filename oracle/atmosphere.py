@@ -24,7 +24,8 @@ the readings are:
     / dx, theta = rho in radians (no footprint scaling: the source is at infinity);
   * a source at finite height H (a laser guide star) sees layer l through a footprint
     shrunk by s_l = 1 - h_l / H about the pupil centre c = (Np - 1) / 2 (the cone
-    effect): pixel i samples c + (i - c) s_l + ox_l - t vx (offsets h_l theta as above).
+    effect): pixel i samples c + (i - c) s_l + ox_l - t vx (offsets h_l theta as above;
+    sources at finite distance: abstract; LGS SCAO systems: Sec. History/Reference works).
 """
 from __future__ import annotations
 

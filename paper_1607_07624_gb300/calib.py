@@ -180,3 +180,13 @@ def footprint_offsets_px(heights_m, rho_arcsec: float, phi_deg: float, dx: float
     theta = math.radians(rho_arcsec / 3600.0)
     phi = math.radians(phi_deg)
     return [(h * theta * math.cos(phi) / dx, h * theta * math.sin(phi) / dx) for h in heights_m]
+
+
+def footprint_scales(heights_m, H_m: float):
+    """Per-layer footprint scales 1 - h/H of a source at height H (a laser guide
+    star): the cone from the pupil to the source crosses layer h on a disc shrunk by
+    that factor (sources at finite distance, abstract; LGS SCAO systems, Sec.
+    History/Reference works)."""
+    if not H_m > max(heights_m):
+        raise ValueError("the source must lie above every layer")
+    return [1.0 - h / H_m for h in heights_m]

@@ -25,6 +25,22 @@ __device__ inline void layer_shift(double v, double o, long long step, int S, in
   *n_mod = (int)ni;
 }
 
+// Cone effect of a source at finite height: the sample position of pupil pixel i in
+// a layer whose footprint is scaled by s about the pupil centre c = (Np - 1) / 2 is
+// c + (i - c) s + o - step*v, one FP64 value per (layer, pixel) with explicit
+// rounding; n_mod = floor mod S, f = the float32 fraction.
+__device__ inline void cone_shift(int i, int Np, double s, double v, double o, long long step, int S, int* n_mod,
+                                  float* f) {
+  const double c = 0.5 * (double)(Np - 1);
+  const double d = __dadd_rn(__dadd_rn(c, __dmul_rn(__dsub_rn((double)i, c), s)),
+                             __dsub_rn(o, __dmul_rn((double)step, v)));
+  const double n = floor(d);
+  *f = (float)(d - n);
+  long long ni = (long long)n % S;
+  if (ni < 0) ni += S;
+  *n_mod = (int)ni;
+}
+
 // Bilinear interpolation of one layer from its four taps, with explicit float32
 // rounding (the same value in every kernel that samples the atmosphere).
 __device__ __forceinline__ float bilinear(float fx, float fy, float v00, float v10, float v01, float v11) {
@@ -97,6 +113,23 @@ __device__ inline float atmo_sample_any(const AtmoArgs& a, const int* six, const
   }
 }
 
+// The same sum for a source at finite height (per-pixel cone positions).
+__device__ inline float atmo_sample_cone(const AtmoArgs& a, long long step, int i, int j) {
+  float acc = 0.f;
+  const int S = a.S;
+  for (int l = 0; l < a.L; ++l) {
+    int ni, nj;
+    float fx, fy;
+    cone_shift(i, a.Np, a.sc[l], a.vx[l], a.ox[l], step, S, &ni, &fx);
+    cone_shift(j, a.Np, a.sc[l], a.vy[l], a.oy[l], step, S, &nj, &fy);
+    size_t o[4];
+    tap_offsets(0, 0, ni, nj, S, o);
+    const float* sc = a.screens + (size_t)l * S * S;
+    acc = __fadd_rn(acc, bilinear(fx, fy, __ldg(sc + o[0]), __ldg(sc + o[1]), __ldg(sc + o[2]), __ldg(sc + o[3])));
+  }
+  return acc;
+}
+
 __global__ void atmo_kernel(AtmoArgs a, const long long* d_step, long long h_step, float* out) {
   __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
   __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
@@ -109,7 +142,7 @@ __global__ void atmo_kernel(AtmoArgs a, const long long* d_step, long long h_ste
   const int n = a.Np * a.Np;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const int i = p / a.Np, j = p - i * a.Np;
-    out[p] = atmo_sample_any(a, six, siy, sfx, sfy, i, j);
+    out[p] = a.cone ? atmo_sample_cone(a, step, i, j) : atmo_sample_any(a, six, siy, sfx, sfy, i, j);
   }
 }
 
@@ -165,7 +198,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // pixels): the 4 L taps of the tile's pixels are copied to shared memory
 // asynchronously before the basis stream and combined after it, so their latency
 // hides under the stream; otherwise the atmosphere is read from opd_atm (or zero).
-template <typename T>
+// CONE: a source at finite height; each (layer, pixel) has its own taps and
+// weights (cone_shift), the weights kept in shared memory after the taps.
+template <typename T, bool CONE>
 __global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(ResArgs a) {
   constexpr int VEC = 16 / (int)sizeof(T);         // pixels per 16-byte load
   constexpr int COLS = RES_TILE / VEC;              // loads per mode row
@@ -197,13 +232,14 @@ __global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(ResArgs a) {
   const long long step = a.d_step ? *a.d_step : a.h_step;
   const float* cmd = a.cmd;
   if (a.cmd_ring) cmd = a.cmd_ring + (size_t)(step % a.delay) * a.n_m;
-  if (tid < L) {
+  if (!CONE && tid < L) {
     layer_shift(a.atmo.vx[tid], a.atmo.ox[tid], step, a.atmo.S, &six[tid], &sfx[tid]);
     layer_shift(a.atmo.vy[tid], a.atmo.oy[tid], step, a.atmo.S, &siy[tid], &sfy[tid]);
   }
   for (int m = tid; m < n_m; m += RES_THREADS) c_s[m] = cmd[m];
   __syncthreads();
   float* taps = c_s + max(a.n_m, 1);
+  float* wts = taps + L * 4 * RES_TILE;             // CONE: [L][2][RES_TILE] weights
   if (L > 0) {
     const int S = a.atmo.S;
     for (int t = tid; t < L * RES_TILE; t += RES_THREADS) {
@@ -212,7 +248,15 @@ __global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(ResArgs a) {
         const int flat = s_flat[q];
         const int i = flat / a.atmo.Np, j = flat - i * a.atmo.Np;
         size_t o[4];
-        tap_offsets(i, j, six[l], siy[l], S, o);
+        if constexpr (CONE) {
+          int ni, nj;
+          cone_shift(i, a.atmo.Np, a.atmo.sc[l], a.atmo.vx[l], a.atmo.ox[l], step, S, &ni, wts + 2 * l * RES_TILE + q);
+          cone_shift(j, a.atmo.Np, a.atmo.sc[l], a.atmo.vy[l], a.atmo.oy[l], step, S, &nj,
+                     wts + (2 * l + 1) * RES_TILE + q);
+          tap_offsets(0, 0, ni, nj, S, o);
+        } else {
+          tap_offsets(i, j, six[l], siy[l], S, o);
+        }
         const float* sc = a.atmo.screens + (size_t)l * S * S;
 #pragma unroll
         for (int k = 0; k < 4; ++k) cp_async4(taps + (l * 4 + k) * RES_TILE + q, sc + o[k]);
@@ -247,7 +291,17 @@ __global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(ResArgs a) {
     for (int t = tid; t < L * RES_TILE; t += RES_THREADS) {
       const int l = t / RES_TILE, q = t - l * RES_TILE;
       float* tp = taps + l * 4 * RES_TILE + q;
-      if (base + q < a.n_pix) tp[0] = bilinear(sfx[l], sfy[l], tp[0], tp[RES_TILE], tp[2 * RES_TILE], tp[3 * RES_TILE]);
+      if (base + q < a.n_pix) {
+        float fx, fy;
+        if constexpr (CONE) {
+          fx = wts[2 * l * RES_TILE + q];
+          fy = wts[(2 * l + 1) * RES_TILE + q];
+        } else {
+          fx = sfx[l];
+          fy = sfy[l];
+        }
+        tp[0] = bilinear(fx, fy, tp[0], tp[RES_TILE], tp[2 * RES_TILE], tp[3 * RES_TILE]);
+      }
     }
   }
   __syncthreads();
@@ -319,14 +373,22 @@ int residual_tiles(int n_pix) { return (n_pix + RES_TILE - 1) / RES_TILE; }
 // The residual kernel streams its basis through registers, not the L1 cache: its
 // launch bounds (at most 51 registers) and a shared-memory carveout preference keep
 // five CTAs resident per SM (one wave for the 700 tiles of a 240 px pupil).
-template <typename T>
+template <typename T, bool CONE>
 static cudaError_t residual_prepare(size_t smem) {
   static bool carveout_set = false;
-  cudaError_t e = raise_dyn_smem((const void*)residual_kernel<T>, smem);
+  cudaError_t e = raise_dyn_smem((const void*)residual_kernel<T, CONE>, smem);
   if (e == cudaSuccess && !carveout_set) {
-    e = cudaFuncSetAttribute((const void*)residual_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 50);
+    e = cudaFuncSetAttribute((const void*)residual_kernel<T, CONE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             50);
     carveout_set = e == cudaSuccess;
   }
+  return e;
+}
+
+template <typename T, bool CONE>
+static cudaError_t residual_start(const ResArgs& a, int tiles, size_t smem, cudaStream_t st, bool pdl) {
+  cudaError_t e = residual_prepare<T, CONE>(smem);
+  if (e == cudaSuccess) e = launch_k(residual_kernel<T, CONE>, dim3(tiles), dim3(RES_THREADS), smem, st, pdl, a);
   return e;
 }
 
@@ -335,15 +397,16 @@ pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, boo
   if (tiles == 0) return PAS_OK;
   if (a.atmo.L < 0 || a.atmo.L > PAS_MAX_LAYERS)
     return set_error(ctx, PAS_EINVAL, "residual kernel: 0 <= layers <= %d", PAS_MAX_LAYERS);
-  const size_t smem = sizeof(float) * ((size_t)std::max(a.n_m, 1) + (size_t)a.atmo.L * 4 * RES_TILE);
+  const bool cone = a.atmo.L > 0 && a.atmo.cone;
+  const size_t smem =
+      sizeof(float) * ((size_t)std::max(a.n_m, 1) + (size_t)a.atmo.L * (cone ? 6 : 4) * RES_TILE);
   cudaError_t e;
-  if (a.MTb) {
-    e = residual_prepare<__nv_bfloat16>(smem);
-    if (e == cudaSuccess) e = launch_k(residual_kernel<__nv_bfloat16>, dim3(tiles), dim3(RES_THREADS), smem, st, pdl, a);
-  } else {
-    e = residual_prepare<float>(smem);
-    if (e == cudaSuccess) e = launch_k(residual_kernel<float>, dim3(tiles), dim3(RES_THREADS), smem, st, pdl, a);
-  }
+  if (a.MTb)
+    e = cone ? residual_start<__nv_bfloat16, true>(a, tiles, smem, st, pdl)
+             : residual_start<__nv_bfloat16, false>(a, tiles, smem, st, pdl);
+  else
+    e = cone ? residual_start<float, true>(a, tiles, smem, st, pdl)
+             : residual_start<float, false>(a, tiles, smem, st, pdl);
   if (e != cudaSuccess) return set_error(ctx, PAS_ECUDA, "residual kernel launch: %s", cudaGetErrorString(e));
   return PAS_OK;
 }
@@ -418,18 +481,32 @@ pas_status pas_atmo_advance(pas_atmo_t a, int64_t step, float* d_opd) {
   return pas::check_launch(a->ctx, "pas_atmo_advance launch");
 }
 
-pas_status pas_atmo_create_view(pas_atmo_t base, const double* h_ox, const double* h_oy, pas_atmo_t* out) {
+pas_status pas_atmo_create_cone_view(pas_atmo_t base, const double* h_ox, const double* h_oy,
+                                     const double* h_scale, pas_atmo_t* out) {
   if (!base || !h_ox || !h_oy || !out) return pas::set_global_error(PAS_EINVAL, "pas_atmo_create_view: NULL argument");
   *out = nullptr;
-  for (int l = 0; l < base->args.L; ++l)
+  for (int l = 0; l < base->args.L; ++l) {
     PAS_CHECK_ARG(base->ctx, std::isfinite(h_ox[l]) && std::isfinite(h_oy[l]), "pas_atmo_create_view: offsets not finite");
+    if (h_scale)
+      PAS_CHECK_ARG(base->ctx, h_scale[l] > 0.0 && h_scale[l] <= 1.0, "pas_atmo_create_cone_view: scales in (0, 1]");
+  }
   pas_atmo_t a = new pas_atmo_s(*base);
+  a->args.cone = 0;
   for (int l = 0; l < PAS_MAX_LAYERS; ++l) {
-    a->args.ox[l] = l < base->args.L ? base->args.ox[l] + h_ox[l] : 0.0;
-    a->args.oy[l] = l < base->args.L ? base->args.oy[l] + h_oy[l] : 0.0;
+    // the view's pupil position p maps to c + (p - c) s_base + o_base in the base
+    const double sb = base->args.sc[l];
+    const bool in = l < base->args.L;
+    a->args.ox[l] = in ? base->args.ox[l] + sb * h_ox[l] : 0.0;
+    a->args.oy[l] = in ? base->args.oy[l] + sb * h_oy[l] : 0.0;
+    a->args.sc[l] = in ? sb * (h_scale ? h_scale[l] : 1.0) : 1.0;
+    if (a->args.sc[l] != 1.0) a->args.cone = 1;
   }
   *out = a;
   return PAS_OK;
+}
+
+pas_status pas_atmo_create_view(pas_atmo_t base, const double* h_ox, const double* h_oy, pas_atmo_t* out) {
+  return pas_atmo_create_cone_view(base, h_ox, h_oy, nullptr, out);
 }
 
 void pas_atmo_destroy(pas_atmo_t a) { delete a; }

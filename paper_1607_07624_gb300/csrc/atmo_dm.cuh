@@ -12,6 +12,8 @@ struct AtmoArgs {
   double vy[PAS_MAX_LAYERS] = {};
   double ox[PAS_MAX_LAYERS] = {};  // footprint offsets of an off-axis source [px]
   double oy[PAS_MAX_LAYERS] = {};
+  double sc[PAS_MAX_LAYERS] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};  // footprint scales
+  int cone = 0;                    // some scale differs from 1 (a source at finite height)
 };
 
 struct ResArgs {

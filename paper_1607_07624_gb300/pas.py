@@ -74,6 +74,7 @@ _SIGS = {
     "pas_atmo_create": (C.c_int, [vp, P(pas_atmo_params), vp, P(vp)]),
     "pas_atmo_advance": (C.c_int, [vp, i64, vp]),
     "pas_atmo_create_view": (C.c_int, [vp, vp, vp, P(vp)]),
+    "pas_atmo_create_cone_view": (C.c_int, [vp, vp, vp, vp, P(vp)]),
     "pas_atmo_destroy": (None, [vp]),
     "pas_pyr_supported": (C.c_int, [C.c_int]),
     "pas_pyr_create": (C.c_int, [vp, P(pas_pyr_params), vp, i32, P(vp)]),
@@ -244,6 +245,20 @@ def pas_atmo_create_view(atmo, ctx, ox, oy):
     oy = np.ascontiguousarray(oy, dtype=np.float64)
     h = vp()
     _check(_lib.pas_atmo_create_view(atmo, ox.ctypes.data, oy.ctypes.data, C.byref(h)), ctx)
+    return h
+
+
+def pas_atmo_create_cone_view(atmo, ctx, ox, oy, scale=None):
+    """The layers seen from a source at finite height: per-layer footprint offsets
+    [px] and scales 1 - h/H (None: all 1)."""
+    ox = np.ascontiguousarray(ox, dtype=np.float64)
+    oy = np.ascontiguousarray(oy, dtype=np.float64)
+    sp = None
+    if scale is not None:
+        scale = np.ascontiguousarray(scale, dtype=np.float64)
+        sp = scale.ctypes.data
+    h = vp()
+    _check(_lib.pas_atmo_create_cone_view(atmo, ox.ctypes.data, oy.ctypes.data, sp, C.byref(h)), ctx)
     return h
 
 

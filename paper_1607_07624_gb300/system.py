@@ -40,7 +40,10 @@ class SCAOSystem:
     size, at the configuration's wavelength, with the same detector noise);
     source: None (on axis) or (rho_arcsec, phi_deg), an off-axis natural guide star:
     the loop sees each layer through a footprint moved by height x angle
-    (pas_atmo_create_view), while `atmo_base` stays the on-axis atmosphere."""
+    (pas_atmo_create_view), while `atmo_base` stays the on-axis atmosphere;
+    (rho_arcsec, phi_deg, height_m) is a source at that height (a laser guide star):
+    each footprint is also shrunk by 1 - h/H about the pupil centre (the cone
+    effect, pas_atmo_create_cone_view)."""
 
     def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32, dm_precision=P.PAS_FP32,
                  dm=None,
@@ -65,9 +68,11 @@ class SCAOSystem:
         self.atmo = self.atmo_base
         self.source = source
         if source is not None:
-            off = np.array(calib.footprint_offsets_px([ly.height_m for ly in cfg.layers], source[0], source[1],
-                                                      cfg.dx), dtype=np.float64).reshape(-1, 2)
-            self.atmo = P.pas_atmo_create_view(self.atmo_base, self.ctx, off[:, 0], off[:, 1])
+            heights = [ly.height_m for ly in cfg.layers]
+            off = np.array(calib.footprint_offsets_px(heights, source[0], source[1], cfg.dx),
+                           dtype=np.float64).reshape(-1, 2)
+            scale = calib.footprint_scales(heights, source[2]) if len(source) > 2 else None
+            self.atmo = P.pas_atmo_create_cone_view(self.atmo_base, self.ctx, off[:, 0], off[:, 1], scale)
         # sensor + slope computer
         if sensor not in ("pyramid", "sh"):
             raise ValueError(f"sensor must be 'pyramid' or 'sh', not {sensor!r}")

@@ -73,6 +73,36 @@ def test_atmosphere_view_of_an_off_axis_source(env):
         pas.pas_atmo_destroy(base)
 
 
+@pytest.mark.parametrize("Np", [60, 61])
+def test_atmosphere_cone_view_of_a_source_at_finite_height(env, Np):
+    """pas_atmo_create_cone_view: footprints shrunk by 1 - h/H about the pupil centre
+    (odd and even Np put the centre on and between pixels) and moved by offsets,
+    against the oracle; scales outside (0, 1] are rejected."""
+    torch, pas, ctx = env
+    from oracle import atmosphere as at
+    S = 256
+    scr = np.random.default_rng(9).standard_normal((3, S, S)).astype(np.float32) * 100
+    vel = np.array([[0.37, -0.81], [1.0, 0.0], [-2.0, 3.0]])
+    off = np.array([[0.0, 0.0], [3.7, -12.25], [-30.5, 41.125]])
+    sc = at.footprint_scales([0.0, 4000.0, 16000.0], 90000.0)
+    d_scr = torch.as_tensor(scr).cuda()
+    base = pas.pas_atmo_create(ctx, 3, S, Np, vel[:, 0], vel[:, 1], d_scr)
+    view = pas.pas_atmo_create_cone_view(base, ctx, off[:, 0], off[:, 1], sc)
+    out = torch.zeros(Np, Np, device="cuda")
+    try:
+        for step in (0, 7, 1500):
+            pas.pas_atmo_advance(view, ctx, step, out)
+            torch.cuda.synchronize()
+            o = at.atmo_opd(scr.astype(np.float64), vel, step, Np, [tuple(x) for x in off], sc)
+            assert np.max(np.abs(out.cpu().numpy() - o)) <= 1e-6 * np.max(np.abs(o)), step
+        for bad in ([1.0, 0.0, 0.5], [1.0, 1.5, 0.5], [1.0, np.nan, 0.5]):
+            with pytest.raises(pas.PasError):
+                pas.pas_atmo_create_cone_view(base, ctx, off[:, 0], off[:, 1], np.array(bad))
+    finally:
+        pas.pas_atmo_destroy(view)
+        pas.pas_atmo_destroy(base)
+
+
 @pytest.mark.parametrize("Np,n_modes", [(16, 10), (64, 100), (240, 400)])
 def test_dm_shape_and_residual_match_oracle(env, Np, n_modes):
     torch, pas, ctx = env

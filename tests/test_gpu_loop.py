@@ -172,3 +172,38 @@ def test_off_axis_source_loop_and_science_camera(cfg1_setup):
         assert np.max(np.abs(np.array(sr_sci) - np.array(sr_wfs))) > 1e-2   # anisoplanatism shows
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("bf16_dm", [False, True])
+def test_laser_guide_star_loop_with_cone_effect(cfg1_setup, bf16_dm):
+    """A source 90 km high and 10 arcsec off axis with a layer at 8 km: the loop
+    (through pas_atmo_create_cone_view, the residual kernel's per-pixel cone
+    positions) against the oracle loop with the same offsets and footprint scales;
+    the fp32 and bf16 DM instantiations of the kernel."""
+    from oracle import atmosphere as at
+    from oracle import control as ct
+    from paper_1607_07624_gb300 import pas as P
+    from paper_1607_07624_gb300.system import SCAOSystem
+    from synth.configs import LayerSpec
+    cfg0, _, M, valid, sn, IM, R = cfg1_setup
+    cfg = with_(cfg0, layers=(LayerSpec(0.5, 0.0, 8.0, 0.0), LayerSpec(0.5, 8000.0, 15.0, 120.0)))
+    noises = [screen_white_noise(cfg.S, s) for s in layer_seeds(cfg.seed, len(cfg.layers))]
+    screens = at.layer_screens_nm(cfg, noises)
+    H = 90000.0
+    heights = [ly.height_m for ly in cfg.layers]
+    off = at.footprint_offsets_px(heights, 10.0, 30.0, cfg.dx)
+    sc = at.footprint_scales(heights, H)
+    n = 40
+    Mo = M
+    if bf16_dm:
+        import torch
+        Mo = torch.as_tensor(M, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    ref = ct.closed_loop(cfg, screens, Mo, R, sn, valid, n, offsets_px=off, scales=sc)
+    s = SCAOSystem(cfg, screens=screens.astype(np.float32), basis=M, R=R, wfe_history=n, source=(10.0, 30.0, H),
+                   dm_precision=P.PAS_BF16 if bf16_dm else P.PAS_FP32)
+    try:
+        s.step(n)
+        wg = s.wfe_nm(n)
+        assert np.max(np.abs(wg - ref["wfe"])) <= 2.0, np.max(np.abs(wg - ref["wfe"]))
+    finally:
+        s.close()
