@@ -41,13 +41,19 @@ def residual_opd(opd_atm: np.ndarray, M: np.ndarray, c: np.ndarray, mask: np.nda
 
 
 def closed_loop(cfg, screens_nm, M, R, sn, valid, n_steps, gain=None, delay=None,
-                noise=None, use_fft=True, record=False, sensor=None, offsets_px=None, scales=None):
+                noise=None, use_fft=True, record=False, sensor=None, offsets_px=None, scales=None,
+                n_int=1):
     """Run the SCAO loop for n_steps; returns dict with per-step WFE [nm] and the
     final command (and per-step slopes/commands if record). sensor: None for the
     modulated pyramid of cfg, else a callable (opd_res, t) -> (frame, slopes)
     already referenced (e.g. the Shack-Hartmann oracle); offsets_px: per-layer
     footprint offsets of an off-axis source (atmosphere.footprint_offsets_px);
-    scales: per-layer footprint scales of a source at finite height."""
+    scales: per-layer footprint scales of a source at finite height;
+    n_int: steps per detector frame of the pyramid (a detector integrating several
+    simulation steps, Sec. Structure): each step's noiseless frame is added up and
+    read out at the steps t with (t + 1) mod n_int = 0 as the window's mean, then the
+    noise, the slopes and the integrator run; in between the command is held (the
+    downstream objects follow the detector's rate) and the slopes keep their value."""
     gain = cfg.gain if gain is None else gain
     delay = cfg.delay if delay is None else delay
     mask = pupil_mask(cfg.Np, cfg.obs)
@@ -55,21 +61,35 @@ def closed_loop(cfg, screens_nm, M, R, sn, valid, n_steps, gain=None, delay=None
     n_m = M.shape[1]
     c = np.zeros(n_m)
     applied = deque([np.zeros(n_m) for _ in range(delay)], maxlen=delay)
+    assert n_int >= 1 and (n_int == 1 or sensor is None)
     wfe = np.empty(n_steps)
     hist = {"slopes": [], "cmd": [], "frame": []}
+    acc = None
+    s = np.zeros(2 * len(valid))
+    frame = None
     for t in range(n_steps):
         opd_res = residual_opd(atmo_opd(screens_nm, vel, t, cfg.Np, offsets_px, scales), M, applied[0], mask)
         wfe[t] = residual_wfe_nm(opd_res, mask)
+        readout = True
         if sensor is None:
             I = pwfs_intensity(opd_res, cfg.wavelength_nm, cfg.obs, cfg.N, cfg.K,
                                cfg.mod_radius, cfg.delta, use_fft=use_fft)
-            frame = detector_frame(I, cfg.n_sub)
-            if noise is not None:
-                frame = noise(frame, t)
-            s = pwfs_slopes(frame, valid, cfg.n_sub, sn)
+            f_t = detector_frame(I, cfg.n_sub)
+            if frame is None:
+                frame = np.zeros_like(f_t)       # the read-out frame, held between read-outs
+            if n_int > 1:
+                acc = f_t if acc is None else acc + f_t
+                readout = (t + 1) % n_int == 0
+            if readout:
+                frame = f_t if n_int == 1 else acc / n_int
+                acc = None
+                if noise is not None:
+                    frame = noise(frame, t)
+                s = pwfs_slopes(frame, valid, cfg.n_sub, sn)
         else:
             frame, s = sensor(opd_res, t)
-        c = integrator_step(c, R @ s, gain)
+        if readout:
+            c = integrator_step(c, R @ s, gain)
         applied.append(c.copy())
         if record:
             hist["slopes"].append(s)

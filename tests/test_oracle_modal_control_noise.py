@@ -158,6 +158,29 @@ def test_delay_two_lags_one_more_step():
     assert abs(o2["wfe"][1] - o2["wfe"][0]) < 1e-9 and o2["wfe"][2] < 0.7 * o2["wfe"][0]
 
 
+def test_detector_integration_of_a_frozen_atmosphere_subsamples_the_single_rate_loop():
+    """With no wind and delay 1 the command is constant over each detector window, so
+    its n_int frames are identical and their mean is the single-step frame: window k
+    of the multi-rate loop repeats step k of the single-rate loop (same residual, read
+    out at its last step, the command changing only there)."""
+    cfg, mask, M, valid, sn, R = _tiny_loop_setup()
+    screens = at.layer_screens_nm(cfg, [screen_white_noise(cfg.S, 21)])
+    n = 3
+    one = ct.closed_loop(cfg, screens, M, R, sn, valid, 4, delay=1, record=True)
+    mr = ct.closed_loop(cfg, screens, M, R, sn, valid, 4 * n, delay=1, record=True, n_int=n)
+    for k in range(4):
+        for i in range(n):
+            assert abs(mr["wfe"][n * k + i] - one["wfe"][k]) <= 1e-9 * one["wfe"][k]
+            want = one["cmd"][k] if i == n - 1 else (one["cmd"][k - 1] if k > 0 else np.zeros(cfg.n_modes))
+            assert np.max(np.abs(mr["cmd"][n * k + i] - want)) <= 1e-9 * np.max(np.abs(one["cmd"][k]))
+        # the read-out frame is the window's mean, not its sum (the normalised slopes
+        # alone cannot tell them apart)
+        assert np.max(np.abs(mr["frame"][n * k + n - 1] - one["frame"][k])) <= 1e-12 * one["frame"][k].max()
+    assert one["wfe"][1] < 0.8 * one["wfe"][0]
+    base = ct.closed_loop(cfg, screens, M, R, sn, valid, 5)
+    assert np.array_equal(ct.closed_loop(cfg, screens, M, R, sn, valid, 5, n_int=1)["wfe"], base["wfe"])
+
+
 def test_closed_loop_reduces_turbulence_wfe():
     cfg, mask, M, valid, sn, R = _tiny_loop_setup(static=False)
     screens = at.layer_screens_nm(cfg, [screen_white_noise(cfg.S, 77)])
