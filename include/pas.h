@@ -328,6 +328,17 @@ pas_status pas_loop_buffers(pas_loop_t loop, float** opd_res, float** frame, flo
  * on get to query only the step. Synchronous. */
 pas_status pas_loop_get_state(pas_loop_t loop, int64_t* step, float* h_cmd_ring);
 pas_status pas_loop_set_state(pas_loop_t loop, int64_t step, const float* h_cmd_ring);
+/* A detector integrating n_int >= 1 simulation steps per frame (Sec. Structure: a
+ * CCD integrating its input for several steps, the objects using its frames
+ * following its lower rate): the pyramid's noiseless frames of the steps add up and
+ * are read out at each step t with (t + 1) mod n_int = 0 as the window's mean
+ * (windows aligned to the step counter), then noise, slopes, reconstruction and
+ * integrator run; at the other steps the slopes keep their value and the command
+ * is held (the delay still counts steps). n_int = 1 restores one frame per step.
+ * The accumulator starts empty (also after pas_loop_set_state). The next step
+ * captures a new graph. PAS_ESTATE for a Shack-Hartmann loop or one with a
+ * learned reconstructor; PAS_EINVAL outside 1 .. 2^20. Synchronous. */
+pas_status pas_loop_set_integration(pas_loop_t loop, int32_t n_int);
 void pas_loop_destroy(pas_loop_t loop);
 
 /* Profiling: run n_steps >= 1 steps, each one launch of a CUDA graph of the step
@@ -351,7 +362,7 @@ const char* pas_loop_kernel_name(int32_t idx);
  * step as a parallel branch (the paper runs its Monte-Carlo cases as separate
  * simulations; this is the GPU-side batching of them). The loops keep their own
  * state, buffers and statistics (pas_loop_step(loop, 0, &stats) reads them) and
- * must not be stepped, re-configured (pas_loop_set_mlp) or destroyed while the
+ * must not be stepped, re-configured (pas_loop_set_mlp, pas_loop_set_integration) or destroyed while the
  * batch exists. Creation synchronises every loop's stream and captures the graph
  * on `ctx`'s private stream; steps run on `ctx`'s stream. */
 pas_status pas_batch_create(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, pas_batch_t* out);

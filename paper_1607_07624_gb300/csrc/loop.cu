@@ -23,6 +23,8 @@ struct pas_loop_s {
   pas_dm_t dm = nullptr;
   pas_mlp_t mlp = nullptr;  // learned reconstructor in place of rec (optional)
   int delay = 1, hist = 1, n_m = 0, n_slopes = 0, nd = 0, Np = 0, n_tiles = 0;
+  int n_int = 1;            // detector steps per frame (pas_loop_set_integration)
+  float* d_acc = nullptr;   // [nd*nd] the integrating detector's accumulator
   float* d_opd = nullptr;
   float* d_frame = nullptr;
   float* d_slopes = nullptr;
@@ -71,6 +73,8 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   fa.wfe_hist = L->d_wfe;
   fa.wfe_hist_len = L->hist;
   fa.step = L->d_step;
+  fa.acc = L->d_acc;
+  fa.n_int = L->n_int;
   if (L->sh)
     s = pas::sh_launch(L->sh, L->d_opd, L->d_frame, L->d_slopes, st, &fa, pdl);
   else
@@ -85,6 +89,7 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   rc.step = L->d_step;
   rc.cmd_last = L->d_cmd;
   rc.step_inc = L->d_step;
+  rc.n_int = L->n_int;
   if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
   s = L->mlp ? pas::mlp_loop_launch(L->mlp, rc, st, pdl) : pas::recon_launch(L->rec, rc, st, pdl);
   if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
@@ -111,6 +116,7 @@ void pas_loop_destroy(pas_loop_t L) {
   pas::dev_free(L->d_wfe);
   pas::dev_free(L->d_wfe_part);
   pas::dev_free(L->d_step);
+  pas::dev_free(L->d_acc);
   delete L;
 }
 
@@ -282,12 +288,8 @@ pas_status pas_loop_profile(pas_loop_t L, int32_t n_steps, float* h_ms, int32_t 
   return PAS_OK;
 }
 
-pas_status pas_loop_set_mlp(pas_loop_t L, pas_mlp_t m) {
-  if (!L) return pas::set_global_error(PAS_EINVAL, "pas_loop_set_mlp: NULL loop");
-  if (m)
-    PAS_CHECK_ARG(L->ctx, m->sz[0] == L->n_slopes && m->sz[m->L] == L->n_m,
-                  "pas_loop_set_mlp: network sizes must be [2 n_valid, ..., n_modes]");
-  PAS_CUDA_TRY(L->ctx, cudaStreamSynchronize(L->ctx->stream));
+// Drop the captured graphs (the next step captures the new configuration).
+static void loop_drop_graphs(pas_loop_t L) {
   if (L->exec) cudaGraphExecDestroy(L->exec);
   if (L->graph) cudaGraphDestroy(L->graph);
   if (L->prof_exec) cudaGraphExecDestroy(L->prof_exec);
@@ -296,6 +298,34 @@ pas_status pas_loop_set_mlp(pas_loop_t L, pas_mlp_t m) {
   L->graph = nullptr;
   L->prof_exec = nullptr;
   L->prof_graph = nullptr;
+}
+
+pas_status pas_loop_set_integration(pas_loop_t L, int32_t n_int) {
+  if (!L) return pas::set_global_error(PAS_EINVAL, "pas_loop_set_integration: NULL loop");
+  PAS_CHECK_ARG(L->ctx, n_int >= 1 && n_int <= (1 << 20), "pas_loop_set_integration: 1 <= n_int <= 2^20");
+  if (n_int > 1 && (L->sh || L->mlp))
+    return pas::set_error(L->ctx, PAS_ESTATE,
+                          "pas_loop_set_integration: a pyramid loop with the linear reconstructor only");
+  PAS_CUDA_TRY(L->ctx, cudaStreamSynchronize(L->ctx->stream));
+  if (n_int > 1 && !L->d_acc) {
+    pas_status st = pas::dev_alloc(L->ctx, (void**)&L->d_acc, sizeof(float) * L->nd * L->nd);
+    if (st != PAS_OK) return st;
+  }
+  if (L->d_acc) PAS_CUDA_TRY(L->ctx, cudaMemset(L->d_acc, 0, sizeof(float) * L->nd * L->nd));
+  loop_drop_graphs(L);
+  L->n_int = n_int;
+  return PAS_OK;
+}
+
+pas_status pas_loop_set_mlp(pas_loop_t L, pas_mlp_t m) {
+  if (!L) return pas::set_global_error(PAS_EINVAL, "pas_loop_set_mlp: NULL loop");
+  if (m)
+    PAS_CHECK_ARG(L->ctx, m->sz[0] == L->n_slopes && m->sz[m->L] == L->n_m,
+                  "pas_loop_set_mlp: network sizes must be [2 n_valid, ..., n_modes]");
+  if (m && L->n_int > 1)
+    return pas::set_error(L->ctx, PAS_ESTATE, "pas_loop_set_mlp: the loop's detector integrates several steps");
+  PAS_CUDA_TRY(L->ctx, cudaStreamSynchronize(L->ctx->stream));
+  loop_drop_graphs(L);
   L->mlp = m;
   return PAS_OK;
 }
@@ -342,6 +372,8 @@ pas_status pas_loop_set_state(pas_loop_t L, int64_t step, const float* h_cmd_rin
   const int slot = (int)(((step - 1) % L->delay + L->delay) % L->delay);
   PAS_CUDA_TRY(L->ctx, cudaMemcpy(L->d_cmd, L->d_ring + (size_t)slot * L->n_m, sizeof(float) * L->n_m,
                                   cudaMemcpyDeviceToDevice));
+  // an integrating detector starts an empty frame
+  if (L->d_acc) PAS_CUDA_TRY(L->ctx, cudaMemset(L->d_acc, 0, sizeof(float) * L->nd * L->nd));
   return PAS_OK;
 }
 

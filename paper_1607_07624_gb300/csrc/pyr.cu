@@ -200,6 +200,15 @@ __device__ __noinline__ void finish_column(const FrameArgs& f, const float* part
       }
     }
     v *= f.invK;
+    if (f.wfe.n_int > 1) {  // the same branch in every thread of the CTA
+      const float a = active ? __fadd_rn(__ldcg(f.wfe.acc + pix), v) : 0.f;
+      if ((fidx + 1) % f.wfe.n_int != 0) {
+        if (active && sub == 0) f.wfe.acc[pix] = a;
+        continue;
+      }
+      if (active && sub == 0) f.wfe.acc[pix] = 0.f;
+      v = __fdiv_rn(a, (float)f.wfe.n_int);  // the window's mean frame
+    }
     v = noisy_pixel_group(v, f.scale, f.ron, f.seed, (uint32_t)pix, (uint64_t)fidx, sub, g, active);
     if (active && sub == 0) {
       f.frame[pix] = v;
@@ -239,7 +248,11 @@ __global__ void __launch_bounds__(256) slopes_kernel(FrameArgs f, int nd) {
     }
   }
   if (blockIdx.x == 0 && f.wfe.wfe_part) wfe_finalize(f.wfe, red);
+  // a detector integrating several steps: no frame between read-outs, the slopes keep
+  // their value (the step counter was advanced by the previous step's last kernel)
+  const bool hold = f.wfe.n_int > 1 && f.frame_ctr && (*f.frame_ctr + 1) % f.wfe.n_int != 0;
   pdl_wait();
+  if (hold) return;
   // the frame and the column fluxes: all loads in one round
   double fl = 0.0;
   for (int t = threadIdx.x; t < nd; t += blockDim.x) fl += f.flux_part[t];

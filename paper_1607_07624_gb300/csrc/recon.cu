@@ -79,9 +79,11 @@ __global__ void __launch_bounds__(256) recon_kernel(ReconArgs a) {
   const bool writer = part_idx == 0 && lane == 0 && m < a.n_m;
   long long t_step = 0;
   float prev = 0.f;
+  bool hold = false;  // between the read-outs of a detector integrating several steps
   if (writer && a.ring) {
     t_step = *a.step;
     prev = a.ring[(size_t)((t_step - 1 + a.delay) % a.delay) * a.n_m + m];
+    hold = a.n_int > 1 && (t_step + 1) % a.n_int != 0;
   }
   pdl_wait();
   float* s_s = reinterpret_cast<float*>(s4);
@@ -115,10 +117,10 @@ __global__ void __launch_bounds__(256) recon_kernel(ReconArgs a) {
     float tot = 0.f;
 #pragma unroll
     for (int q = 0; q < RECON_SPLIT; ++q) tot += part[warp + q];
-    const float dm = BF16 ? tot * a.scale[m] : tot;
+    const float dm = hold ? 0.f : (BF16 ? tot * a.scale[m] : tot);
     if (a.dmodes) a.dmodes[m] = dm;
     if (a.ring) {
-      const float c = fmaf(a.gain ? a.gain[m] : 1.0f, dm, prev);
+      const float c = hold ? prev : fmaf(a.gain ? a.gain[m] : 1.0f, dm, prev);
       a.ring[(size_t)(t_step % a.delay) * a.n_m + m] = c;
       if (a.cmd_last) a.cmd_last[m] = c;
     }

@@ -21,6 +21,7 @@ struct ReconArgs {
   float* cmd_last = nullptr;            // [n_m] copy of the new command
   long long* step_inc = nullptr;        // advanced by one after the last CTA (or null)
   unsigned int* done = nullptr;         // CTA completion counter
+  int n_int = 1;                        // > 1: new command only when (step + 1) mod n_int = 0
 };
 
 }  // namespace pas

@@ -104,6 +104,7 @@ _SIGS = {
     "pas_loop_buffers": (C.c_int, [vp, P(vp), P(vp), P(vp), P(vp), P(vp), P(vp)]),
     "pas_loop_get_state": (C.c_int, [vp, P(i64), vp]),
     "pas_loop_set_state": (C.c_int, [vp, i64, vp]),
+    "pas_loop_set_integration": (C.c_int, [vp, i32]),
     "pas_loop_destroy": (None, [vp]),
     "pas_loop_profile": (C.c_int, [vp, i32, vp, i32, P(i32)]),
     "pas_loop_kernel_name": (C.c_char_p, [i32]),
@@ -428,6 +429,11 @@ def pas_loop_get_state(loop, ctx, n_modes: int, delay: int):
 def pas_loop_set_state(loop, ctx, step: int, ring: np.ndarray):
     ring = np.ascontiguousarray(ring, dtype=np.float32)
     _check(_lib.pas_loop_set_state(loop, int(step), ring.ctypes.data), ctx)
+
+
+def pas_loop_set_integration(loop, ctx, n_int: int):
+    """Detector steps per frame (1: a frame every step)."""
+    _check(_lib.pas_loop_set_integration(loop, int(n_int)), ctx)
 
 
 def pas_loop_destroy(loop):

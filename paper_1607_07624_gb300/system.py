@@ -43,12 +43,15 @@ class SCAOSystem:
     (pas_atmo_create_view), while `atmo_base` stays the on-axis atmosphere;
     (rho_arcsec, phi_deg, height_m) is a source at that height (a laser guide star):
     each footprint is also shrunk by 1 - h/H about the pupil centre (the cone
-    effect, pas_atmo_create_cone_view)."""
+    effect, pas_atmo_create_cone_view);
+    detector_steps: simulation steps per pyramid detector frame (the detector's
+    integration time over the loop's time step, pas_loop_set_integration): frames are
+    read out, and the command updated, every detector_steps steps."""
 
     def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32, dm_precision=P.PAS_FP32,
                  dm=None,
                  noise=None, delay=None, wfe_history=4096, stream=None, build_loop=True,
-                 autotune=True, sensor="pyramid", sh_ovs=2, source=None):
+                 autotune=True, sensor="pyramid", sh_ovs=2, source=None, detector_steps=1):
         from synth.inputs import layer_seeds, screen_white_noise
         self.cfg = cfg
         self.dev = torch.device("cuda")
@@ -138,6 +141,8 @@ class SCAOSystem:
             else:
                 self.loop = P.pas_loop_create(self.ctx, self.atmo, self.pyr, self.rec, self.dm, self.d_gain,
                                               self.delay, wfe_history)
+            if detector_steps != 1:
+                P.pas_loop_set_integration(self.loop, self.ctx, detector_steps)
             b = P.pas_loop_buffers(self.loop, self.ctx)
             self.wfe_history = wfe_history
             self.loop_opd = DevView.tensor(b["opd_res"], (cfg.Np, cfg.Np))

@@ -207,3 +207,49 @@ def test_laser_guide_star_loop_with_cone_effect(cfg1_setup, bf16_dm):
         assert np.max(np.abs(wg - ref["wfe"])) <= 2.0, np.max(np.abs(wg - ref["wfe"]))
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("n_int,noisy", [(3, False), (4, True)])
+def test_integrating_detector_loop_matches_oracle(cfg1_setup, n_int, noisy):
+    """A pyramid detector integrating n_int steps per frame (pas_loop_set_integration):
+    the loop against the oracle loop with the same integration (mean frame read out
+    at (t + 1) mod n_int = 0, command held in between), with photon and read noise
+    drawn on the read-out frames; commands change only at read-outs."""
+    import torch
+    from oracle import atmosphere as at
+    from oracle import control as ct
+    from oracle import noise as nz
+    from paper_1607_07624_gb300 import pas as P
+    from paper_1607_07624_gb300.system import SCAOSystem
+    cfg, screens, M, valid, sn, IM, R = cfg1_setup
+    n = 36
+    noise = None
+    kw = {}
+    if noisy:
+        n_pupil = int(P.pas_pupil_pixels(cfg.Np, cfg.obs).size)
+        photons, ron, seed = 1.0e5, 0.5, 13
+        noise = lambda fr, t: nz.apply_noise(fr, photons, n_pupil, ron, seed, t)
+        kw["noise"] = (photons, ron, seed)
+    ref = ct.closed_loop(cfg, screens, M, R, sn, valid, n, noise=noise, n_int=n_int, record=True)
+    s = SCAOSystem(cfg, screens=screens.astype(np.float32), basis=M, R=R, wfe_history=n, detector_steps=n_int, **kw)
+    try:
+        cmds = []
+        for t in range(n):
+            s.step(1)
+            cmds.append(s.loop_cmd.cpu().numpy().copy())
+        wg = s.wfe_nm(n)
+        assert np.max(np.abs(wg - ref["wfe"])) <= 2.0, np.max(np.abs(wg - ref["wfe"]))
+        cmds = np.array(cmds)
+        for t in range(1, n):
+            if (t + 1) % n_int != 0:
+                assert np.array_equal(cmds[t], cmds[t - 1]), t
+        # every step's command (record=True: ref["cmd"] is the per-step history)
+        assert np.max(np.abs(cmds - ref["cmd"])) <= 1e-2 * np.max(np.abs(ref["cmd"])), \
+            np.max(np.abs(cmds - ref["cmd"]))
+        # back to a frame per step: the loop re-captures and keeps running
+        P.pas_loop_set_integration(s.loop, s.ctx, 1)
+        s.step(2)
+        with pytest.raises(P.PasError):
+            P.pas_loop_set_integration(s.loop, s.ctx, 0)
+    finally:
+        s.close()
