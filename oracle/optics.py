@@ -150,6 +150,26 @@ def pwfs_intensity(opd_nm: np.ndarray, wavelength_nm: float, obs: float, N: int,
     return I / K
 
 
+def pwfs_intensity_extended(opd_nm: np.ndarray, wavelength_nm: float, obs: float, N: int, K: int, R: float,
+                            ex, ey, w=None, delta: float | None = None, use_fft: bool = True) -> np.ndarray:
+    """Modulated pyramid intensity of an extended incoherent source (Sec. History/
+    Reference works, extended reference sources; Sec. Conclusions, their cost at ELT
+    scale): sum_p w_p I_p with I_p the modulated intensity of point source p, whose
+    wavefront carries the tilt 2 pi (ex_p X + ey_p Y) of its offset (ex_p, ey_p)
+    lambda/D from the source centre (the modulation's own tilt convention); the
+    weights are normalised to sum 1 (None: equal)."""
+    ex = np.atleast_1d(np.asarray(ex, dtype=np.float64))
+    ey = np.atleast_1d(np.asarray(ey, dtype=np.float64))
+    w = np.ones(ex.size) if w is None else np.atleast_1d(np.asarray(w, dtype=np.float64))
+    w = w / w.sum()
+    X, Y = pixel_coords(opd_nm.shape[0])
+    I = np.zeros((N, N))
+    for xp, yp, wp in zip(ex, ey, w):
+        opd_p = np.asarray(opd_nm, dtype=np.float64) + wavelength_nm * (xp * X + yp * Y)
+        I += wp * pwfs_intensity(opd_p, wavelength_nm, obs, N, K, R, delta, use_fft)
+    return I
+
+
 # --------------------------------------------------------------------------- detector
 
 def bin_detector(I: np.ndarray, b: int) -> np.ndarray:
