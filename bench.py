@@ -377,6 +377,45 @@ def bench_sh(timed, n_frames=200):
     return out
 
 
+def bench_extended(timed, n_frames=100):
+    """The LBT-class pyramid looking at an extended source, a 3 x 3 grid of points over
+    2 lambda/D (K x 9 = 216 tilt points, 13 x 3 = 39 rows passes): frames/s, the FP32
+    roofline of its transforms (rows passes plus the 216 column transforms, the
+    point-source formulas with K x 9 points) and the closed loop with this sensor."""
+    import numpy as np
+    import torch
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    from synth import get_config
+    from synth.configs import with_
+    cfg = get_config(2)
+    g = np.linspace(-1.0, 1.0, 3)
+    ex, ey = np.repeat(g, 3), np.tile(g, 3)
+    s = SCAOSystem(cfg, extended_source=(ex, ey), wfe_history=max(4096, n_frames + 64))
+    try:
+        opd = torch.zeros(cfg.Np, cfg.Np, dtype=torch.float32, device="cuda")
+        pas.pas_atmo_advance(s.atmo, s.ctx, 0, opd)
+        for _ in range(3):
+            s.measure(opd)
+        ms = timed(lambda: s.measure(opd), n_frames)
+        n_rows = (cfg.K // 2 + 1 if cfg.K % 2 == 0 else cfg.K) * len(set(ey.tolist()))
+        work = algorithmic_work(with_(cfg, K=cfg.K * ex.size), s.n_pix, s.n_valid, s.n_modes, n_rows, 4.0)
+        flops = work["pyr_rows_kernel"]["flops"] + work["pyr_cols_kernel"]["flops"]
+        per = ms / n_frames * 1e-3
+        ach = flops / per / 1e12
+        out = {"workload": f"pyramid {cfg.Np} px, K {cfg.K}, extended source of {ex.size} points over 2 lambda/D",
+               "frames_per_s": n_frames / (ms * 1e-3), "us_per_frame": per * 1e6, "flops_per_frame": flops,
+               "tilt_points": cfg.K * ex.size, "rows_passes": n_rows, "tuning": list(s.tuning),
+               "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": ach / FP32_PEAK_TFLOPS}}
+        sps, wfe = timed_loop(s, timed, n_frames)
+        out["loop_steps_per_s"] = sps
+        out["loop_wfe_nm_first_steps"] = [float(x) for x in wfe[:5]]
+        return out
+    finally:
+        s.close()
+
+
 def bench_batch(timed, n_loops=64, n_steps=100):
     """Monte-Carlo batch: n_loops realisations of the 64 px workload (own screens
     each; basis, reconstructor and launch geometry shared) stepped by one graph
@@ -755,6 +794,10 @@ def main():
             extra["shack_hartmann"] = bench_sh(timed)
         except Exception as e:
             extra["shack_hartmann"] = {"error": str(e)}
+        try:
+            extra["extended_source"] = bench_extended(timed)
+        except Exception as e:
+            extra["extended_source"] = {"error": str(e)}
         try:
             extra["monte_carlo_batch"] = bench_batch(timed)
         except Exception as e:

@@ -176,6 +176,22 @@ int pas_pyr_supported(int N);
  * reference and noise off. */
 pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* p, const int32_t* h_valid,
                           int32_t n_valid, pas_pyr_t* out);
+/* The same sensor looking at an extended incoherent source (Sec. History/Reference
+ * works: extended, non point-like, reference sources; Sec. Conclusions: the costly
+ * case at ELT scale): n_points >= 1 point sources at offsets (h_ex[q], h_ey[q])
+ * lambda/D from the source centre along axes 0 and 1 (the modulation radius's unit
+ * and sign: a point at (r, 0) tilts the wavefront like the modulation point at
+ * theta = 0), with relative intensities h_w[q] >= 0 (normalised to sum 1; NULL:
+ * equal). Every measurement is sum_q w_q I_q, I_q the modulated intensity of point
+ * q: K n_points FFT pairs, each point q riding on the modulation circle at
+ * (R cos theta_k + ex_q, R sin theta_k + ey_q); points of equal ey and equal
+ * sin theta share one rows pass, and w_q enters as the amplitude sqrt(w_q n_points)
+ * of the point's column tilt. Requires K n_points <= 4096. Everything else is
+ * pas_pyr_create's (reference slopes, noise, measurement, loops). EINVAL on
+ * non-finite offsets, negative or all-zero weights. */
+pas_status pas_pyr_create_extended(pas_ctx_t ctx, const pas_pyr_params* p, const int32_t* h_valid,
+                                   int32_t n_valid, const double* h_ex, const double* h_ey,
+                                   const double* h_w, int32_t n_points, pas_pyr_t* out);
 int32_t pas_pyr_n_valid(pas_pyr_t pyr);
 /* Copy the valid sub-aperture list to host memory (synchronous). */
 pas_status pas_pyr_get_valid(pas_pyr_t pyr, int32_t* h_valid, int32_t cap);

@@ -190,3 +190,15 @@ def footprint_scales(heights_m, H_m: float):
     if not H_m > max(heights_m):
         raise ValueError("the source must lie above every layer")
     return [1.0 - h / H_m for h in heights_m]
+
+
+def disc_source(diameter_lod: float, n_across: int):
+    """A uniform disc of angular diameter `diameter_lod` lambda/D as point sources on an
+    n_across x n_across grid of spacing diameter / n_across (those inside the disc;
+    equal intensities): (ex, ey) for pas_pyr_create_extended (extended reference
+    sources, Sec. History/Reference works)."""
+    h = diameter_lod / n_across
+    c = (np.arange(n_across) - (n_across - 1) / 2.0) * h
+    X, Y = np.meshgrid(c, c, indexing="ij")
+    inside = X ** 2 + Y ** 2 <= (diameter_lod / 2.0) ** 2 + 1e-12
+    return X[inside].copy(), Y[inside].copy()

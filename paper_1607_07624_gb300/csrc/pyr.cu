@@ -33,6 +33,7 @@
 namespace pas {
 
 constexpr int MAX_ROWS_PER_CTA = 8;  // rows pass: one warp per pupil row
+constexpr size_t SMEM_MAX = 227 * 1024;  // opt-in dynamic shared memory of one CTA
 
 struct RowArgs {
   const float* opd;     // [Np][Np]
@@ -276,14 +277,20 @@ __global__ void __launch_bounds__(256) slopes_kernel(FrameArgs f, int nd) {
 // Column tilt phasors of the modulation points, [K][Np]: (-1)^i e^{2 pi i (i - ci) alpha_k}
 // (tilt along axis 0 with the input centring ramp). Constant for a geometry: built
 // once at creation, in the same float arithmetic the columns pass used inline.
-__global__ void tilt_table_kernel(const float* alpha, int K, int Np, float2* tilt) {
+// amp (may be null): per-point amplitudes (an extended source's weights).
+__global__ void tilt_table_kernel(const float* alpha, const float* amp, int K, int Np, float2* tilt) {
   const int k = blockIdx.x;
   if (k >= K) return;
   const float ci = 0.5f * (float)(Np - 1);
   const float al = alpha[k];
+  const float am = amp ? amp[k] : 1.0f;
   for (int i = threadIdx.x; i < Np; i += blockDim.x) {
     float sn, cs;
     sincospif(2.0f * ((float)i - ci) * al, &sn, &cs);
+    if (amp) {
+      cs *= am;
+      sn *= am;
+    }
     tilt[(size_t)k * Np + i] = (i & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
   }
 }
@@ -452,6 +459,8 @@ struct pas_pyr_s {
   int H = 1, h_max = 1;  // columns-pass CTAs per detector column and group (divides b)
   int frac = 0;  // non-integer fine pixels per detector pixel
   int rows = 4, s_chunk = 1, n_schunks = 1;
+  int s_chunk_max = 1;   // largest rows-pass chunk whose shared memory fits a CTA
+  int K_mod = 0, n_src = 1;  // modulation points and source points (p.K = K_mod n_src)
   int64_t T_obs = 0;
   float inv_hi = 0.f, inv_lo = 0.f;
   size_t smem_rows = 0, smem_cols = 0;
@@ -461,6 +470,7 @@ struct pas_pyr_s {
   float2* d_mask = nullptr;
   float* d_alpha = nullptr;
   float2* d_tilt = nullptr;
+  float* d_amp = nullptr;  // [K] column-tilt amplitudes of an extended source
   float* d_beta = nullptr;
   int* d_kmap = nullptr;
   float2* d_H = nullptr;
@@ -623,6 +633,7 @@ void pas_pyr_destroy(pas_pyr_t y) {
   pas::dev_free(y->d_mask);
   pas::dev_free(y->d_alpha);
   pas::dev_free(y->d_tilt);
+  pas::dev_free(y->d_amp);
   pas::dev_free(y->d_beta);
   pas::dev_free(y->d_kmap);
   pas::dev_free(y->d_H);
@@ -635,14 +646,29 @@ void pas_pyr_destroy(pas_pyr_t y) {
   delete y;
 }
 
-pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t* h_valid,
-                          int32_t n_valid, pas_pyr_t* out) {
+// Source: n_src = 0 for a point source, else n_src points at (ex, ey) lambda/D with
+// weights w (null: equal).
+static pas_status pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t* h_valid, int32_t n_valid,
+                             const double* ex, const double* ey, const double* w, int n_src, pas_pyr_t* out) {
   if (!ctx || !pp || !out) return pas::set_global_error(PAS_EINVAL, "pas_pyr_create: NULL argument");
   *out = nullptr;
-  const pas_pyr_params p = *pp;
+  pas_pyr_params p = *pp;
   PAS_CHECK_ARG(ctx, p.Np > 0 && p.N == 2 * p.Np, "pas_pyr_create: N must equal 2*Np");
   PAS_CHECK_ARG(ctx, p.n_sub > 0 && 2 * p.n_sub <= p.N, "pas_pyr_create: need 1 <= n_sub <= Np");
-  PAS_CHECK_ARG(ctx, p.K >= 1 && p.K <= 4096, "pas_pyr_create: K out of range");
+  PAS_CHECK_ARG(ctx, p.K >= 1 && p.K * std::max(n_src, 1) <= 4096, "pas_pyr_create: K (x source points) out of range");
+  const int P = std::max(n_src, 1);
+  std::vector<double> src_w(P, 1.0 / P);
+  if (n_src > 0) {
+    PAS_CHECK_ARG(ctx, ex && ey, "pas_pyr_create_extended: NULL offsets");
+    double tot = 0.0;
+    for (int q = 0; q < P; ++q) {
+      PAS_CHECK_ARG(ctx, std::isfinite(ex[q]) && std::isfinite(ey[q]), "pas_pyr_create_extended: offsets not finite");
+      if (w) PAS_CHECK_ARG(ctx, std::isfinite(w[q]) && w[q] >= 0.0, "pas_pyr_create_extended: weights >= 0");
+      tot += w ? w[q] : 1.0;
+    }
+    PAS_CHECK_ARG(ctx, tot > 0.0, "pas_pyr_create_extended: weights sum to zero");
+    for (int q = 0; q < P; ++q) src_w[q] = (w ? w[q] : 1.0) / tot;
+  }
   PAS_CHECK_ARG(ctx, p.wavelength_nm > 0 && p.mod_radius >= 0 && p.obs >= 0 && p.obs < 1,
                 "pas_pyr_create: bad wavelength, modulation radius or obstruction");
   pas::PyrKernels kern;
@@ -690,34 +716,61 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   }
   y->n_valid = (int)valid.size();
 
-  // modulation: distinct sin(theta) rows passes; theta and pi - theta share one
-  std::vector<int> kmap(p.K), rep_of_s;
-  for (int k = 0; k < p.K; ++k) {
-    int rep = k;
-    if (p.K % 2 == 0) {
-      int partner = ((p.K / 2 - k) % p.K + p.K) % p.K;
-      rep = std::min(k, partner);
-    }
-    int s = -1;
-    for (size_t t = 0; t < rep_of_s.size(); ++t)
-      if (rep_of_s[t] == rep) s = (int)t;
-    if (s < 0) {
-      s = (int)rep_of_s.size();
-      rep_of_s.push_back(rep);
-    }
-    kmap[k] = s;
+  // tilt points: modulation point k of source point q at
+  // (R cos theta_k + ex_q, R sin theta_k + ey_q), index t = q K + k. One rows pass per
+  // distinct (sin theta, ey): theta and pi - theta share one, and so do source points
+  // of equal ey. An extended source's weights become column-tilt amplitudes
+  // sqrt(w_q P): the frame is (1/(K P)) sum_t |E_t|^2 = sum_q w_q (1/K) sum_k |E_qk|^2.
+  const int Km = p.K, Kt = Km * P;
+  y->K_mod = Km;
+  y->n_src = P;
+  std::vector<int> ey_id(P);
+  for (int q = 0; q < P; ++q) {
+    ey_id[q] = q;
+    for (int r = 0; r < q; ++r)
+      if (n_src > 0 && ey[r] == ey[q]) {
+        ey_id[q] = ey_id[r];
+        break;
+      }
   }
-  y->n_s = (int)rep_of_s.size();
-  std::vector<float> alpha(p.K), beta(y->n_s);
+  std::vector<int> kmap(Kt);
+  std::vector<std::pair<int, int>> key_of_s;  // (modulation representative, ey id)
+  for (int q = 0; q < P; ++q)
+    for (int k = 0; k < Km; ++k) {
+      int rep = k;
+      if (Km % 2 == 0) {
+        int partner = ((Km / 2 - k) % Km + Km) % Km;
+        rep = std::min(k, partner);
+      }
+      const std::pair<int, int> key(rep, ey_id[q]);
+      int s = -1;
+      for (size_t t = 0; t < key_of_s.size(); ++t)
+        if (key_of_s[t] == key) s = (int)t;
+      if (s < 0) {
+        s = (int)key_of_s.size();
+        key_of_s.push_back(key);
+      }
+      kmap[q * Km + k] = s;
+    }
+  y->n_s = (int)key_of_s.size();
+  std::vector<float> alpha(Kt), beta(y->n_s), amp(Kt);
   const double ramp = 1.0 / (2.0 * p.N);
-  for (int k = 0; k < p.K; ++k) {
-    double th = 2.0 * M_PI * (double)k / (double)p.K;
-    alpha[k] = (float)(p.mod_radius * std::cos(th) / p.Np - ramp);
+  for (int q = 0; q < P; ++q) {
+    const double oxq = n_src > 0 ? ex[q] : 0.0;
+    for (int k = 0; k < Km; ++k) {
+      double th = 2.0 * M_PI * (double)k / (double)Km;
+      alpha[q * Km + k] = (float)((p.mod_radius * std::cos(th) + oxq) / p.Np - ramp);
+      amp[q * Km + k] = (float)std::sqrt(src_w[q] * P);
+    }
   }
   for (int s = 0; s < y->n_s; ++s) {
-    double th = 2.0 * M_PI * (double)rep_of_s[s] / (double)p.K;
-    beta[s] = (float)(p.mod_radius * std::sin(th) / p.Np - ramp);
+    double th = 2.0 * M_PI * (double)key_of_s[s].first / (double)Km;
+    const double oyq = n_src > 0 ? ey[key_of_s[s].second] : 0.0;
+    beta[s] = (float)((p.mod_radius * std::sin(th) + oyq) / p.Np - ramp);
   }
+  // from here on p.K counts all tilt points
+  p.K = Kt;
+  y->p.K = Kt;
   // per-pass twiddle tables ([k-1][n1] = w_L^{n1 k}) and the digit-reversed
   // pyramid mask (delta = N/4: phase (pi/2)|u~|, divided by N) in padded layout
   std::vector<float2> tw = pas::fft_twiddles(p.N), mk(kern.buf_n, make_float2(0.f, 0.f));
@@ -738,7 +791,10 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   y->rows = 4;
   y->n_schunks = (y->n_s + 3) / 4;
   y->s_chunk = (y->n_s + y->n_schunks - 1) / y->n_schunks;
-  y->smem_rows = pas::rows_smem(y, pas::MAX_ROWS_PER_CTA, y->n_s);  // largest candidate
+  y->s_chunk_max = y->n_s;
+  while (y->s_chunk_max > 1 && pas::rows_smem(y, pas::MAX_ROWS_PER_CTA, y->s_chunk_max) > pas::SMEM_MAX)
+    --y->s_chunk_max;
+  y->smem_rows = pas::rows_smem(y, pas::MAX_ROWS_PER_CTA, y->s_chunk_max);  // largest candidate
   y->smem_cols = pas::cols_smem(y, b);  // largest: one CTA per detector column and group
   for (int H = 2; H <= 8; ++H)
     if (pas::split_ok(y, H)) y->h_max = H;
@@ -753,6 +809,7 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   A((void**)&y->d_mask, sizeof(float2) * kern.buf_n);
   A((void**)&y->d_alpha, sizeof(float) * p.K);
   A((void**)&y->d_tilt, sizeof(float2) * (size_t)p.K * p.Np);
+  if (n_src > 0) A((void**)&y->d_amp, sizeof(float) * p.K);
   A((void**)&y->d_beta, sizeof(float) * y->n_s);
   A((void**)&y->d_kmap, sizeof(int) * p.K);
   A((void**)&y->d_H, sizeof(float2) * (size_t)y->n_s * p.N * p.Np);
@@ -774,8 +831,9 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   C(y->d_tw, tw.data(), sizeof(float2) * kern.tw_n);
   C(y->d_mask, mk.data(), sizeof(float2) * kern.buf_n);
   C(y->d_alpha, alpha.data(), sizeof(float) * p.K);
+  if (y->d_amp) C(y->d_amp, amp.data(), sizeof(float) * p.K);
   if (e == cudaSuccess) {
-    pas::tilt_table_kernel<<<p.K, 256>>>(y->d_alpha, p.K, p.Np, y->d_tilt);
+    pas::tilt_table_kernel<<<p.K, 256>>>(y->d_alpha, y->d_amp, p.K, p.Np, y->d_tilt);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
@@ -819,6 +877,20 @@ pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t
   }
   *out = y;
   return PAS_OK;
+}
+
+pas_status pas_pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t* h_valid, int32_t n_valid,
+                          pas_pyr_t* out) {
+  return pyr_create(ctx, pp, h_valid, n_valid, nullptr, nullptr, nullptr, 0, out);
+}
+
+pas_status pas_pyr_create_extended(pas_ctx_t ctx, const pas_pyr_params* pp, const int32_t* h_valid,
+                                   int32_t n_valid, const double* h_ex, const double* h_ey, const double* h_w,
+                                   int32_t n_points, pas_pyr_t* out) {
+  if (!ctx || !out) return pas::set_global_error(PAS_EINVAL, "pas_pyr_create_extended: NULL argument");
+  *out = nullptr;
+  PAS_CHECK_ARG(ctx, n_points >= 1, "pas_pyr_create_extended: n_points >= 1");
+  return pyr_create(ctx, pp, h_valid, n_valid, h_ex, h_ey, h_w, n_points, out);
 }
 
 int32_t pas_pyr_n_valid(pas_pyr_t y) { return y ? y->n_valid : -1; }
@@ -872,10 +944,11 @@ pas_status pas_pyr_set_tuning(pas_pyr_t y, const pas_pyr_tuning* t) {
   if (!y || !t) return pas::set_global_error(PAS_EINVAL, "pas_pyr_set_tuning: NULL argument");
   const int r = t->rows_per_cta;
   PAS_CHECK_ARG(y->ctx, (r == 1 || r == 2 || r == 4 || r == 8) && t->row_chunks >= 1 &&
-                t->row_chunks <= y->n_s && t->col_groups >= 1 && t->col_groups <= y->p.K &&
-                pas::split_ok(y, t->col_split),
-                "pas_pyr_set_tuning: rows_per_cta in {1,2,4,8}, 1 <= row_chunks <= distinct sin values, "
-                "1 <= col_groups <= K, col_split 1 or a divisor <= 8 of the fine pixels per detector pixel");
+                t->row_chunks <= y->n_s && (y->n_s + t->row_chunks - 1) / t->row_chunks <= y->s_chunk_max &&
+                t->col_groups >= 1 && t->col_groups <= y->p.K && pas::split_ok(y, t->col_split),
+                "pas_pyr_set_tuning: rows_per_cta in {1,2,4,8}, 1 <= row_chunks <= distinct sin values (chunks "
+                "within shared memory), 1 <= col_groups <= K, col_split 1 or a divisor <= 8 of the fine pixels "
+                "per detector pixel");
   y->rows = r;
   y->s_chunk = (y->n_s + t->row_chunks - 1) / t->row_chunks;
   y->n_schunks = (y->n_s + y->s_chunk - 1) / y->s_chunk;
@@ -923,7 +996,7 @@ pas_status pas_pyr_autotune(pas_pyr_t y, const float* d_opd, int32_t iters, pas_
     int last_chunk = -1;
     for (int nc = 1; nc <= y->n_s; ++nc) {
       const int chunk = (y->n_s + nc - 1) / nc;
-      if (chunk == last_chunk) continue;
+      if (chunk == last_chunk || chunk > y->s_chunk_max) continue;
       last_chunk = chunk;
       y->rows = r;
       y->s_chunk = chunk;
@@ -1193,7 +1266,7 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
   H2D(y.d_mask, mk, sizeof(float2) * kern.buf_n);
   H2D(y.d_alpha, alpha, sizeof(float) * p.K);
   if (e == cudaSuccess) {
-    tilt_table_kernel<<<p.K, 256, 0, st>>>(y.d_alpha, p.K, p.Np, y.d_tilt);
+    tilt_table_kernel<<<p.K, 256, 0, st>>>(y.d_alpha, nullptr, p.K, p.Np, y.d_tilt);
     e = cudaGetLastError();
   }
   H2D(y.d_beta, beta, sizeof(float) * n_s);

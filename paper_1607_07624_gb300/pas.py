@@ -78,6 +78,7 @@ _SIGS = {
     "pas_atmo_destroy": (None, [vp]),
     "pas_pyr_supported": (C.c_int, [C.c_int]),
     "pas_pyr_create": (C.c_int, [vp, P(pas_pyr_params), vp, i32, P(vp)]),
+    "pas_pyr_create_extended": (C.c_int, [vp, P(pas_pyr_params), vp, i32, vp, vp, vp, i32, P(vp)]),
     "pas_pyr_n_valid": (i32, [vp]),
     "pas_pyr_get_valid": (C.c_int, [vp, vp, i32]),
     "pas_pyr_set_reference": (C.c_int, [vp, vp]),
@@ -279,6 +280,31 @@ def pas_pyr_create(ctx, Np, N, K, n_sub, mod_radius, wavelength_nm, obs, valid=N
         _check(_lib.pas_pyr_create(ctx, C.byref(p), valid.ctypes.data, valid.size, C.byref(h)), ctx)
     else:
         _check(_lib.pas_pyr_create(ctx, C.byref(p), None, 0, C.byref(h)), ctx)
+    return h
+
+
+def pas_pyr_create_extended(ctx, Np, N, K, n_sub, mod_radius, wavelength_nm, obs, ex, ey, w=None, valid=None,
+                            local_norm=0):
+    """The pyramid looking at an extended source: points at (ex, ey) lambda/D with
+    relative intensities w (None: equal)."""
+    p = pas_pyr_params(Np, N, K, n_sub, mod_radius, wavelength_nm, obs, local_norm)
+    ex = np.ascontiguousarray(ex, dtype=np.float64)
+    ey = np.ascontiguousarray(ey, dtype=np.float64)
+    if ex.shape != ey.shape:
+        raise ValueError("ex and ey differ in length")
+    wp = None
+    if w is not None:
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        if w.shape != ex.shape:
+            raise ValueError("w and ex differ in length")
+        wp = w.ctypes.data
+    h = vp()
+    vptr, nv = (None, 0)
+    if valid is not None:
+        valid = np.ascontiguousarray(valid, dtype=np.int32)
+        vptr, nv = valid.ctypes.data, valid.size
+    _check(_lib.pas_pyr_create_extended(ctx, C.byref(p), vptr, nv, ex.ctypes.data, ey.ctypes.data, wp, ex.size,
+                                        C.byref(h)), ctx)
     return h
 
 

@@ -46,12 +46,16 @@ class SCAOSystem:
     effect, pas_atmo_create_cone_view);
     detector_steps: simulation steps per pyramid detector frame (the detector's
     integration time over the loop's time step, pas_loop_set_integration): frames are
-    read out, and the command updated, every detector_steps steps."""
+    read out, and the command updated, every detector_steps steps;
+    extended_source: None (a point source) or (ex, ey[, w]): the pyramid sees an
+    extended incoherent source of points at (ex, ey) lambda/D with intensities w
+    (pas_pyr_create_extended; calib.disc_source builds a uniform disc)."""
 
     def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32, dm_precision=P.PAS_FP32,
                  dm=None,
                  noise=None, delay=None, wfe_history=4096, stream=None, build_loop=True,
-                 autotune=True, sensor="pyramid", sh_ovs=2, source=None, detector_steps=1):
+                 autotune=True, sensor="pyramid", sh_ovs=2, source=None, detector_steps=1,
+                 extended_source=None):
         from synth.inputs import layer_seeds, screen_white_noise
         self.cfg = cfg
         self.dev = torch.device("cuda")
@@ -85,8 +89,14 @@ class SCAOSystem:
             self.sh = P.pas_sh_create(self.ctx, cfg.Np, cfg.n_sub, sh_ovs, cfg.wavelength_nm, cfg.obs, self.valid)
             frame_side = P.pas_sh_frame_side(self.sh)
         else:
-            self.pyr = P.pas_pyr_create(self.ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius,
-                                        cfg.wavelength_nm, cfg.obs, self.valid)
+            if extended_source is None:
+                self.pyr = P.pas_pyr_create(self.ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius,
+                                            cfg.wavelength_nm, cfg.obs, self.valid)
+            else:
+                ex, ey = extended_source[0], extended_source[1]
+                w = extended_source[2] if len(extended_source) > 2 else None
+                self.pyr = P.pas_pyr_create_extended(self.ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius,
+                                                     cfg.wavelength_nm, cfg.obs, ex, ey, w, self.valid)
             frame_side = cfg.n_det
         # DM
         if basis is None:

@@ -253,3 +253,34 @@ def test_integrating_detector_loop_matches_oracle(cfg1_setup, n_int, noisy):
             P.pas_loop_set_integration(s.loop, s.ctx, 0)
     finally:
         s.close()
+
+
+def test_extended_source_loop_matches_oracle(cfg1_setup):
+    """The loop seeing a 1.5 lambda/D disc (SCAOSystem(extended_source=...)): reference
+    slopes of the extended source and the per-step WFE against the oracle loop whose
+    sensor is the oracle's extended-source pyramid (reconstructor of the point source)."""
+    from oracle import control as ct
+    from oracle import optics as op
+    from paper_1607_07624_gb300 import calib
+    from paper_1607_07624_gb300.system import SCAOSystem
+    cfg, screens, M, valid, sn, IM, R = cfg1_setup
+    ex, ey = calib.disc_source(1.5, 3)
+
+    def sensor(o, t=None, ref=None):
+        I = op.pwfs_intensity_extended(o, cfg.wavelength_nm, cfg.obs, cfg.N, cfg.K, cfg.mod_radius, ex, ey,
+                                       None, cfg.delta)
+        fr = op.detector_frame(I, cfg.n_sub)
+        return fr, op.pwfs_slopes(fr, valid, cfg.n_sub, ref)
+
+    sn_e = sensor(np.zeros((cfg.Np, cfg.Np)))[1]
+    n = 30
+    wo = ct.closed_loop(cfg, screens, M, R, sn_e, valid, n, sensor=lambda o, t: sensor(o, t, sn_e))["wfe"]
+    s = SCAOSystem(cfg, screens=screens.astype(np.float32), basis=M, R=R, wfe_history=n, extended_source=(ex, ey))
+    try:
+        assert np.max(np.abs(s.d_sn.cpu().numpy() - sn_e)) <= 1e-5 * np.max(np.abs(sn_e)) + 1e-7
+        s.step(n)
+        wg = s.wfe_nm(n)
+        assert np.max(np.abs(wg - wo)) <= 2.0, np.max(np.abs(wg - wo))
+        assert wg[10:].min() < 0.5 * wg[0]
+    finally:
+        s.close()

@@ -246,3 +246,81 @@ def test_noise_inside_the_pyramid_matches_oracle_counts(env, cfg_idx, tunings):
                     assert np.mean(g == o) >= 0.999, (t, np.mean(g == o))
     finally:
         pas.pas_pyr_destroy(pyr)
+
+
+EXTENDED = [
+    # (config, ex, ey, w): asymmetric sources, repeated ey values (shared rows passes),
+    # odd K, zero and unequal weights
+    (tiny_config(Np=24, N=48, n_sub=4, K=8), [0.0, 1.5, -0.75, 1.5], [0.5, 0.5, -1.25, 2.0], [1.0, 2.0, 0.5, 0.0]),
+    (tiny_config(Np=20, N=40, n_sub=5, K=5), [0.3], [-0.9], None),
+    (tiny_config(Np=32, N=64, n_sub=8, K=12), None, None, None),   # a 3 lambda/D disc, 5 x 5 grid
+]
+
+
+@pytest.mark.parametrize("case", range(len(EXTENDED)))
+def test_extended_source_matches_oracle(env, case):
+    """pas_pyr_create_extended against the oracle's weighted sum of point sources with
+    their wavefront tilts (the kernels ride the points on the modulation circle and
+    carry the weights in the column tilts' amplitudes)."""
+    torch, pas, ctx = env
+    from oracle import optics as op
+    from paper_1607_07624_gb300 import calib
+    cfg, ex, ey, w = EXTENDED[case]
+    if ex is None:
+        ex, ey = calib.disc_source(3.0, 5)
+    opd = random_opd_nm(cfg.Np, 60.0, seed=40 + case).astype(np.float32)
+    valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
+    pyr = pas.pas_pyr_create_extended(ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius, cfg.wavelength_nm,
+                                      cfg.obs, ex, ey, w)
+    try:
+        nv = pas.pas_pyr_n_valid(pyr)
+        fr = torch.zeros(cfg.n_det, cfg.n_det, device="cuda")
+        sl = torch.zeros(2 * nv, device="cuda")
+        pas.pas_pyr_measure(pyr, ctx, torch.as_tensor(opd).cuda(), fr, sl)
+        torch.cuda.synchronize()
+        I = op.pwfs_intensity_extended(opd.astype(np.float64), cfg.wavelength_nm, cfg.obs, cfg.N, cfg.K,
+                                       cfg.mod_radius, ex, ey, w, cfg.delta)
+        fo = op.detector_frame(I, cfg.n_sub)
+        check(cfg, fr.cpu().numpy().astype(np.float64), sl.cpu().numpy().astype(np.float64), fo,
+              op.pwfs_slopes(fo, valid, cfg.n_sub))
+    finally:
+        pas.pas_pyr_destroy(pyr)
+
+
+def test_extended_source_full_size_sampled_and_point_identity(env):
+    """The 240 px pyramid (K = 24) with a 3 x 3 grid source of 2 lambda/D: frame
+    against the oracle on the same input; a one-point source at the origin is the
+    point-source sensor bit for bit; bad sources are rejected."""
+    torch, pas, ctx = env
+    from oracle import optics as op
+    cfg = get_config(2)
+    g = np.linspace(-1.0, 1.0, 3)
+    ex, ey = [a for a in g for _ in g], [b for _ in g for b in g]
+    opd = open_loop_opd(cfg, 91).astype(np.float32)
+    d_opd = torch.as_tensor(opd).cuda()
+    fr = torch.zeros(cfg.n_det, cfg.n_det, device="cuda")
+    args = (ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius, cfg.wavelength_nm, cfg.obs)
+    pyr = pas.pas_pyr_create_extended(*args, ex, ey)
+    try:
+        pas.pas_pyr_measure(pyr, ctx, d_opd, fr)
+        torch.cuda.synchronize()
+        I = op.pwfs_intensity_extended(opd.astype(np.float64), cfg.wavelength_nm, cfg.obs, cfg.N, cfg.K,
+                                       cfg.mod_radius, ex, ey, None, cfg.delta)
+        fo = op.detector_frame(I, cfg.n_sub)
+        assert np.max(np.abs(fr.cpu().numpy() - fo)) <= FRAME_TOL * fo.max()
+    finally:
+        pas.pas_pyr_destroy(pyr)
+    one = pas.pas_pyr_create_extended(*args, [0.0], [0.0])
+    ref = pas.pas_pyr_create(*args)
+    f1 = torch.zeros_like(fr)
+    try:
+        pas.pas_pyr_measure(one, ctx, d_opd, fr)
+        pas.pas_pyr_measure(ref, ctx, d_opd, f1)
+        torch.cuda.synchronize()
+        assert torch.equal(fr, f1)
+    finally:
+        pas.pas_pyr_destroy(one)
+        pas.pas_pyr_destroy(ref)
+    for bad in (([0.0, np.nan], [0.0, 0.0], None), ([0.0], [0.0], [-1.0]), ([0.0, 1.0], [0.0, 0.0], [0.0, 0.0])):
+        with pytest.raises(pas.PasError):
+            pas.pas_pyr_create_extended(*args, *bad)
