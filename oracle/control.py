@@ -42,7 +42,7 @@ def residual_opd(opd_atm: np.ndarray, M: np.ndarray, c: np.ndarray, mask: np.nda
 
 def closed_loop(cfg, screens_nm, M, R, sn, valid, n_steps, gain=None, delay=None,
                 noise=None, use_fft=True, record=False, sensor=None, offsets_px=None, scales=None,
-                n_int=1):
+                n_int=1, slopes_of=None):
     """Run the SCAO loop for n_steps; returns dict with per-step WFE [nm] and the
     final command (and per-step slopes/commands if record). sensor: None for the
     modulated pyramid of cfg, else a callable (opd_res, t) -> (frame, slopes)
@@ -53,7 +53,9 @@ def closed_loop(cfg, screens_nm, M, R, sn, valid, n_steps, gain=None, delay=None
     simulation steps, Sec. Structure): each step's noiseless frame is added up and
     read out at the steps t with (t + 1) mod n_int = 0 as the window's mean, then the
     noise, the slopes and the integrator run; in between the command is held (the
-    downstream objects follow the detector's rate) and the slopes keep their value."""
+    downstream objects follow the detector's rate) and the slopes keep their value;
+    with a sensor callable, its noiseless frames are integrated and slopes_of(frame)
+    gives the read-out frame's slopes."""
     gain = cfg.gain if gain is None else gain
     delay = cfg.delay if delay is None else delay
     mask = pupil_mask(cfg.Np, cfg.obs)
@@ -61,7 +63,7 @@ def closed_loop(cfg, screens_nm, M, R, sn, valid, n_steps, gain=None, delay=None
     n_m = M.shape[1]
     c = np.zeros(n_m)
     applied = deque([np.zeros(n_m) for _ in range(delay)], maxlen=delay)
-    assert n_int >= 1 and (n_int == 1 or sensor is None)
+    assert n_int >= 1 and (n_int == 1 or sensor is None or slopes_of is not None)
     wfe = np.empty(n_steps)
     hist = {"slopes": [], "cmd": [], "frame": []}
     acc = None
@@ -86,8 +88,20 @@ def closed_loop(cfg, screens_nm, M, R, sn, valid, n_steps, gain=None, delay=None
                 if noise is not None:
                     frame = noise(frame, t)
                 s = pwfs_slopes(frame, valid, cfg.n_sub, sn)
-        else:
+        elif n_int == 1:
             frame, s = sensor(opd_res, t)
+        else:
+            f_t = sensor(opd_res, t)[0]
+            acc = f_t if acc is None else acc + f_t
+            readout = (t + 1) % n_int == 0
+            if frame is None:
+                frame = np.zeros_like(f_t)
+            if readout:
+                frame = acc / n_int
+                acc = None
+                if noise is not None:
+                    frame = noise(frame, t)
+                s = slopes_of(frame)
         if readout:
             c = integrator_step(c, R @ s, gain)
         applied.append(c.copy())

@@ -106,3 +106,36 @@ def test_small_tilt_moves_the_centroid_by_about_ovs_t(t):
     gain = (cx - cx0)[1:3, 1:3] / (ovs * t)
     assert np.all((gain > 0.85) & (gain < 1.0))
     assert np.max(np.abs((cy - cy0)[1:3, 1:3])) < 1e-12
+
+
+def test_integrating_detector_of_a_frozen_atmosphere_subsamples_the_single_rate_loop():
+    """The Shack-Hartmann loop with a detector integrating 3 steps: with no wind and
+    delay 1 every frame of a window is the same, so window k repeats step k of the
+    single-rate loop (WFE, command changing only at the read-out, and the read-out
+    frame equal to the single frame: the mean, not the sum)."""
+    from oracle import atmosphere as at
+    from oracle import control as ct
+    from oracle import modal as md
+    from synth import tiny_config
+    from synth.configs import LayerSpec
+    from synth.inputs import screen_white_noise
+    cfg = tiny_config(Np=16, N=32, n_sub=4, K=8, n_modes=12, mod_radius=2.0, S=64, r0_m=0.5,
+                      layers=(LayerSpec(1.0, 0.0, 0.0),))
+    mask = op.pupil_mask(cfg.Np, cfg.obs)
+    M = md.modal_basis(cfg.Np, cfg.obs, cfg.n_modes)
+    valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
+    meas = lambda o, ref=None: sh.sh_measure(o, LAM, cfg.obs, cfg.n_sub, 2, valid, ref)
+    sn = meas(np.zeros((cfg.Np, cfg.Np)))[1]
+    R = md.pseudo_inverse(md.interaction_matrix(lambda o: meas(o, sn)[1], M, mask, 5.0))
+    screens = at.layer_screens_nm(cfg, [screen_white_noise(cfg.S, 21)])
+    n = 3
+    one = ct.closed_loop(cfg, screens, M, R, sn, valid, 4, delay=1, record=True, sensor=lambda o, t: meas(o, sn))
+    mr = ct.closed_loop(cfg, screens, M, R, sn, valid, 4 * n, delay=1, record=True, n_int=n,
+                        sensor=lambda o, t: meas(o, sn), slopes_of=lambda f: sh.sh_slopes(f, valid, cfg.n_sub, sn))
+    for k in range(4):
+        for i in range(n):
+            assert abs(mr["wfe"][n * k + i] - one["wfe"][k]) <= 1e-9 * one["wfe"][k]
+            want = one["cmd"][k] if i == n - 1 else (one["cmd"][k - 1] if k > 0 else np.zeros(cfg.n_modes))
+            assert np.max(np.abs(mr["cmd"][n * k + i] - want)) <= 1e-9 * np.max(np.abs(one["cmd"][k]))
+        assert np.max(np.abs(mr["frame"][n * k + n - 1] - one["frame"][k])) <= 1e-12 * one["frame"][k].max()
+    assert one["wfe"][1] < 0.9 * one["wfe"][0]
