@@ -346,14 +346,15 @@ pas_status pas_loop_get_state(pas_loop_t loop, int64_t* step, float* h_cmd_ring)
 pas_status pas_loop_set_state(pas_loop_t loop, int64_t step, const float* h_cmd_ring);
 /* A detector integrating n_int >= 1 simulation steps per frame (Sec. Structure: a
  * CCD integrating its input for several steps, the objects using its frames
- * following its lower rate): the pyramid's noiseless frames of the steps add up and
+ * following its lower rate): the sensor's (pyramid or Shack-Hartmann) noiseless
+ * frames of the steps add up and
  * are read out at each step t with (t + 1) mod n_int = 0 as the window's mean
  * (windows aligned to the step counter), then noise, slopes, reconstruction and
  * integrator run; at the other steps the slopes keep their value and the command
  * is held (the delay still counts steps). n_int = 1 restores one frame per step.
  * The accumulator starts empty (also after pas_loop_set_state). The next step
- * captures a new graph. PAS_ESTATE for a Shack-Hartmann loop or one with a
- * learned reconstructor; PAS_EINVAL outside 1 .. 2^20. Synchronous. */
+ * captures a new graph. PAS_ESTATE for a loop with a learned reconstructor;
+ * PAS_EINVAL outside 1 .. 2^20. Synchronous. */
 pas_status pas_loop_set_integration(pas_loop_t loop, int32_t n_int);
 void pas_loop_destroy(pas_loop_t loop);
 

@@ -303,9 +303,8 @@ static void loop_drop_graphs(pas_loop_t L) {
 pas_status pas_loop_set_integration(pas_loop_t L, int32_t n_int) {
   if (!L) return pas::set_global_error(PAS_EINVAL, "pas_loop_set_integration: NULL loop");
   PAS_CHECK_ARG(L->ctx, n_int >= 1 && n_int <= (1 << 20), "pas_loop_set_integration: 1 <= n_int <= 2^20");
-  if (n_int > 1 && (L->sh || L->mlp))
-    return pas::set_error(L->ctx, PAS_ESTATE,
-                          "pas_loop_set_integration: a pyramid loop with the linear reconstructor only");
+  if (n_int > 1 && L->mlp)
+    return pas::set_error(L->ctx, PAS_ESTATE, "pas_loop_set_integration: a loop with the linear reconstructor only");
   PAS_CUDA_TRY(L->ctx, cudaStreamSynchronize(L->ctx->stream));
   if (n_int > 1 && !L->d_acc) {
     pas_status st = pas::dev_alloc(L->ctx, (void**)&L->d_acc, sizeof(float) * L->nd * L->nd);

@@ -14,8 +14,8 @@ struct LoopExtra {
   double* wfe_hist = nullptr;
   int wfe_hist_len = 1;
   const long long* step = nullptr;
-  // a detector integrating n_int steps per frame (n_int > 1, pyramid loops): the
-  // noiseless frames add up in acc [nd*nd] and are read out at the steps t with
+  // a detector integrating n_int steps per frame (n_int > 1, loops): the noiseless
+  // frames add up in acc [frame pixels] and are read out at the steps t with
   // (t + 1) mod n_int = 0 (frame_ctr holds t)
   float* acc = nullptr;
   int n_int = 1;

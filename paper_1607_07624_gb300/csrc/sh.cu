@@ -86,17 +86,28 @@ __global__ void __launch_bounds__(1024) sh_kernel(ShArgs a) {
   // extra threads hold no pixel and add zeros to the sums)
   const int k = tid / M, l = tid - k * M;
   const bool pix = tid < M * M;
+  // a detector integrating n_int steps (loops): the spots add up in wfe.acc and are
+  // read out as the window's mean at the steps t with (t + 1) mod n_int = 0 (frame_ctr
+  // holds t); in between there is no frame and the slopes keep their value
+  const bool hold = a.wfe.n_int > 1 && (*a.frame_ctr + 1) % a.wfe.n_int != 0;  // uniform
   float I = 0.f;
   if (pix) {
     float2 f = make_float2(0.f, 0.f);
     for (int i = 0; i < b; ++i) f = cfma(W_s[k * b + i], T_s[i * M + l], f);
     I = __fmul_rn(__fmaf_rn(f.x, f.x, __fmul_rn(f.y, f.y)), a.inv_M2);
     const size_t px = ((size_t)r * M + k) * ((size_t)a.n_sub * M) + (size_t)c * M + l;
-    if constexpr (NOISE) I = noisy_pixel(I, a.scale, a.ron, a.seed, (uint32_t)px, (uint64_t)*a.frame_ctr);
-    if (a.frame) a.frame[px] = I;
+    if (a.wfe.n_int > 1) {
+      const float acc = __fadd_rn(__ldcg(a.wfe.acc + px), I);
+      a.wfe.acc[px] = hold ? acc : 0.f;
+      I = __fdiv_rn(acc, (float)a.wfe.n_int);
+    }
+    if (!hold) {
+      if constexpr (NOISE) I = noisy_pixel(I, a.scale, a.ron, a.seed, (uint32_t)px, (uint64_t)*a.frame_ctr);
+      if (a.frame) a.frame[px] = I;
+    }
   }
   const int s = a.slope_of[lens];
-  if (s >= 0 && a.slopes) {  // uniform across the CTA
+  if (s >= 0 && a.slopes && !hold) {  // uniform across the CTA
     // the three moments: float within a warp (fixed shuffle tree), the warps' partials
     // added in double in warp order by thread 0
     const float half = 0.5f * (float)M;

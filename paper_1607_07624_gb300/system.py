@@ -44,7 +44,7 @@ class SCAOSystem:
     (rho_arcsec, phi_deg, height_m) is a source at that height (a laser guide star):
     each footprint is also shrunk by 1 - h/H about the pupil centre (the cone
     effect, pas_atmo_create_cone_view);
-    detector_steps: simulation steps per pyramid detector frame (the detector's
+    detector_steps: simulation steps per detector frame of the sensor (the detector's
     integration time over the loop's time step, pas_loop_set_integration): frames are
     read out, and the command updated, every detector_steps steps;
     extended_source: None (a point source) or (ex, ey[, w]): the pyramid sees an

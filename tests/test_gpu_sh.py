@@ -170,3 +170,56 @@ def test_sh_detector_noise_matches_oracle_counts(env):
         assert np.mean(fr.cpu().numpy() == nz.apply_noise(clean, photons, n_pupil, 0.0, seed, 5)) >= 0.999
     finally:
         pas.pas_sh_destroy(h)
+
+
+@pytest.mark.parametrize("n_int,noisy", [(3, False), (2, True)])
+def test_sh_integrating_detector_loop_matches_oracle(env, n_int, noisy):
+    """The Shack-Hartmann loop with a detector integrating n_int steps per frame
+    (pas_loop_set_integration) against the oracle loop integrating the oracle sensor's
+    frames (mean frame at (t + 1) mod n_int = 0, noise on it, command held between)."""
+    from oracle import atmosphere as at
+    from oracle import control as ct
+    from oracle import modal as md
+    from oracle import noise as nz
+    from oracle import optics as op
+    from oracle import shack_hartmann as shm
+    from paper_1607_07624_gb300 import pas as P
+    from paper_1607_07624_gb300.system import SCAOSystem
+    from synth import get_config
+    from synth.inputs import layer_seeds
+    cfg = get_config(1)
+    ovs = 2
+    noises = [screen_white_noise(cfg.S, s) for s in layer_seeds(cfg.seed, len(cfg.layers))]
+    screens = at.layer_screens_nm(cfg, noises)
+    M = md.modal_basis(cfg.Np, cfg.obs, cfg.n_modes)
+    valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
+    mask = op.pupil_mask(cfg.Np, cfg.obs)
+    meas = lambda o, ref=None: shm.sh_measure(o, cfg.wavelength_nm, cfg.obs, cfg.n_sub, ovs, valid, ref)
+    sn = meas(np.zeros((cfg.Np, cfg.Np)))[1]
+    R = md.pseudo_inverse(md.interaction_matrix(lambda o: meas(o, sn)[1], M, mask, cfg.pushpull_nm))
+    noise, kw = None, {}
+    if noisy:
+        n_pupil = int(P.pas_pupil_pixels(cfg.Np, cfg.obs).size)
+        photons, ron, seed = 2.0e5, 0.5, 17
+        noise = lambda fr, t: nz.apply_noise(fr, photons, n_pupil, ron, seed, t)
+        kw["noise"] = (photons, ron, seed)
+    n = 36
+    ref = ct.closed_loop(cfg, screens, M, R, sn, valid, n, noise=noise, n_int=n_int, record=True,
+                         sensor=lambda o, t: meas(o), slopes_of=lambda f: shm.sh_slopes(f, valid, cfg.n_sub, sn))
+    s = SCAOSystem(cfg, screens=screens.astype(np.float32), basis=M, R=R, wfe_history=n, sensor="sh", sh_ovs=ovs,
+                   detector_steps=n_int, **kw)
+    try:
+        cmds = []
+        for t in range(n):
+            s.step(1)
+            cmds.append(s.loop_cmd.cpu().numpy().copy())
+        wg = s.wfe_nm(n)
+        assert np.max(np.abs(wg - ref["wfe"])) <= 2.0, np.max(np.abs(wg - ref["wfe"]))
+        cmds = np.array(cmds)
+        for t in range(1, n):
+            if (t + 1) % n_int != 0:
+                assert np.array_equal(cmds[t], cmds[t - 1]), t
+        assert np.max(np.abs(cmds - ref["cmd"])) <= 1e-2 * np.max(np.abs(ref["cmd"])), \
+            np.max(np.abs(cmds - ref["cmd"]))
+    finally:
+        s.close()
