@@ -135,3 +135,43 @@ def test_product_kl_basis_matches_oracle():
         if j - i == 1:
             assert np.max(np.abs(K[:, i] - Ko[:, i])) < 1e-6
         i = j
+
+
+def test_product_source_geometry_matches_oracle():
+    """calib's footprint offsets and cone scales against the oracle's; a source below
+    a layer is rejected."""
+    from oracle import atmosphere as at
+    from paper_1607_07624_gb300 import calib
+    heights = [0.0, 837.0, 3045.0, 12780.0]
+    for rho, phi, dx in ((10.0, 45.0, 0.035), (30.0, -120.0, 8.4 / 240), (0.0, 0.0, 0.1)):
+        a = np.array(calib.footprint_offsets_px(heights, rho, phi, dx))
+        b = np.array(at.footprint_offsets_px(heights, rho, phi, dx))
+        assert np.max(np.abs(a - b)) <= 1e-12 * max(1.0, np.max(np.abs(b)))
+    assert calib.footprint_scales(heights, 90000.0) == at.footprint_scales(heights, 90000.0)
+    with pytest.raises(ValueError):
+        calib.footprint_scales(heights, 12000.0)
+
+
+@pytest.mark.parametrize("d,n", [(3.0, 5), (2.0, 3), (1.0, 1), (4.0, 8)])
+def test_disc_source_points(d, n):
+    """calib.disc_source: the grid points of spacing d/n inside the disc of diameter d,
+    counted by brute force, symmetric about the centre, equal spacing."""
+    from paper_1607_07624_gb300 import calib
+    ex, ey = calib.disc_source(d, n)
+    h = d / n
+    want = sum(1 for i in range(n) for j in range(n)
+               if ((i - (n - 1) / 2) * h) ** 2 + ((j - (n - 1) / 2) * h) ** 2 <= (d / 2) ** 2 + 1e-12)
+    assert ex.size == ey.size == want
+    assert np.all(ex ** 2 + ey ** 2 <= (d / 2) ** 2 + 1e-9)
+    assert abs(ex.sum()) < 1e-9 and abs(ey.sum()) < 1e-9
+    if n > 1:
+        u = np.unique(np.round(ex / h, 9))
+        assert np.allclose(np.diff(u), 1.0)
+
+
+def test_binding_rejects_mismatched_source_arrays(lib):
+    """The binding checks the source arrays' lengths before calling the library."""
+    with pytest.raises(ValueError):
+        lib.pas_pyr_create_extended(None, 16, 32, 4, 2, 1.0, 750.0, 0.0, [0.0, 1.0], [0.0])
+    with pytest.raises(ValueError):
+        lib.pas_pyr_create_extended(None, 16, 32, 4, 2, 1.0, 750.0, 0.0, [0.0, 1.0], [0.0, 1.0], [1.0])
