@@ -52,6 +52,7 @@ def parse():
                          "(default: autotuned)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-budget-s", type=float, default=20.0)
+    ap.add_argument("--no-cpu-pool", action="store_true", help="skip the all-cores oracle timing")
     return ap.parse_args()
 
 
@@ -100,6 +101,38 @@ def run_oracle_subprocess(cfg_idx: int, budget_s: float, max_steps: int) -> dict
                str(cfg_idx), "--oracle-budget-s", str(budget_s)]
         subprocess.run(cmd, env=env, check=True, stdout=open(f.name, "w"))
         return json.loads(open(f.name).read().strip().splitlines()[-1])
+
+
+def run_oracle_pool(cfg_idx: int, budget_s: float, max_steps: int, n_proc: int) -> dict:
+    """All host cores: n_proc independent copies of the oracle's closed loop (the
+    oracle as it stands, one thread each), started together as fresh processes; the
+    aggregate steps/s is the sum of their rates over their concurrent timed regions."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    outs, procs = [], []
+    try:
+        for _ in range(n_proc):
+            f = tempfile.NamedTemporaryFile("r", suffix=".json")
+            outs.append(f)
+            cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(max_steps), "--config",
+                   str(cfg_idx), "--oracle-budget-s", str(budget_s)]
+            procs.append(subprocess.Popen(cmd, env=env, stdout=open(f.name, "w"), stderr=subprocess.DEVNULL))
+        rates, steps = [], 0
+        for p, f in zip(procs, outs):
+            if p.wait() != 0:
+                raise RuntimeError("an oracle process failed")
+            r = json.loads(open(f.name).read().strip().splitlines()[-1])
+            rates.append(r["value"])
+            steps += r["steps"]
+        return {"value": float(sum(rates)), "steps": steps, "processes": n_proc}
+    finally:
+        for p in procs:
+            if p.poll() is None:
+                p.kill()
+        for f in outs:
+            f.close()
 
 
 # ------------------------------------------------------------------ clocks
@@ -828,6 +861,16 @@ def main():
                              f"1 thread, {r['seconds']:.1f} s (setup untimed; random R)"}
         except Exception as e:  # the baseline is reported, never fatal
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+        if cpu.get("value") and not args.no_cpu_pool:
+            n_proc = max(1, min(os.cpu_count() or 1, 16))
+            try:
+                rp = run_oracle_pool(args.config, args.oracle_budget_s / 2, 50, n_proc)
+                cpu["all_cores"] = {"value": rp["value"], "unit": UNIT, "cores": n_proc, "kind": "oracle",
+                                    "sample": f"{n_proc} independent closed loops of {cfg.name} in {n_proc} "
+                                              f"single-thread processes started together, {rp['steps']} steps "
+                                              f"in all (steps/s summed over the concurrent loops)"}
+            except Exception as e:
+                cpu["all_cores"] = {"value": None, "cores": n_proc, "sample": f"failed: {e}"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -50,3 +50,11 @@ def test_single_process_needs_no_group():
     import bench
     assert bench.max_over_ranks(7.5, None, "cpu") == 7.5
     assert bench.job_throughput(100, 1, 50.0) == pytest.approx(2000.0)
+
+
+def test_all_cores_oracle_pool_sums_concurrent_loops():
+    """The all-cores CPU baseline: independent single-thread oracle loops of the small
+    workload in fresh processes, their rates summed."""
+    import bench
+    r = bench.run_oracle_pool(1, 0.5, 3, 2)
+    assert r["processes"] == 2 and r["steps"] >= 2 and r["value"] > 0
