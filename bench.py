@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", default="scao_lbt_240px",
+                    help="workload: scao_8m_64px, scao_lbt_240px or scao_elt_480px")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--recon", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-mlp", action="store_true", help="skip the learned-reconstructor measurements")
@@ -58,7 +59,7 @@ def parse():
 
 # ------------------------------------------------------------------ CPU oracle
 
-def oracle_sample(cfg_idx: int, budget_s: float, max_steps: int) -> dict:
+def oracle_sample(workload: str, budget_s: float, max_steps: int) -> dict:
     """Time the FP64 oracle's closed-loop step (as it stands) for a bounded number
     of steps. Setup (screens, basis) is untimed; R is a seeded random matrix of
     the right shape (the timing does not depend on its values)."""
@@ -70,7 +71,7 @@ def oracle_sample(cfg_idx: int, budget_s: float, max_steps: int) -> dict:
     from oracle import optics as op
     from synth import get_config
     from synth.inputs import layer_seeds, random_matrix, screen_white_noise
-    cfg = get_config(cfg_idx)
+    cfg = get_config(workload)
     screens = at.layer_screens_nm(cfg, [screen_white_noise(cfg.S, s) for s in layer_seeds(cfg.seed, len(cfg.layers))])
     M = md.modal_basis(cfg.Np, cfg.obs, cfg.n_modes)
     valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
@@ -91,19 +92,19 @@ def oracle_sample(cfg_idx: int, budget_s: float, max_steps: int) -> dict:
     return {"steps": n, "seconds": dt, "value": n / dt}
 
 
-def run_oracle_subprocess(cfg_idx: int, budget_s: float, max_steps: int) -> dict:
+def run_oracle_subprocess(workload: str, budget_s: float, max_steps: int) -> dict:
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
     with tempfile.NamedTemporaryFile("r", suffix=".json") as f:
         cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(max_steps), "--config",
-               str(cfg_idx), "--oracle-budget-s", str(budget_s)]
+               workload, "--oracle-budget-s", str(budget_s)]
         subprocess.run(cmd, env=env, check=True, stdout=open(f.name, "w"))
         return json.loads(open(f.name).read().strip().splitlines()[-1])
 
 
-def run_oracle_pool(cfg_idx: int, budget_s: float, max_steps: int, n_proc: int) -> dict:
+def run_oracle_pool(workload: str, budget_s: float, max_steps: int, n_proc: int) -> dict:
     """All host cores: n_proc independent copies of the oracle's closed loop (the
     oracle as it stands, one thread each), started together as fresh processes; the
     aggregate steps/s is the sum of their rates over their concurrent timed regions."""
@@ -117,7 +118,7 @@ def run_oracle_pool(cfg_idx: int, budget_s: float, max_steps: int, n_proc: int) 
             f = tempfile.NamedTemporaryFile("r", suffix=".json")
             outs.append(f)
             cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(max_steps), "--config",
-                   str(cfg_idx), "--oracle-budget-s", str(budget_s)]
+                   workload, "--oracle-budget-s", str(budget_s)]
             procs.append(subprocess.Popen(cmd, env=env, stdout=open(f.name, "w"), stderr=subprocess.DEVNULL))
         rates, steps = [], 0
         for p, f in zip(procs, outs):
@@ -263,7 +264,7 @@ def bench_other_workloads(timed, peaks, n_steps=200):
     from synth import get_config
     out = {}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    cfg1 = get_config(1)
+    cfg1 = get_config("scao_8m_64px")
     s1 = SCAOSystem(cfg1, wfe_history=max(4096, n_steps + 64))
     try:
         sps, _ = timed_loop(s1, timed, n_steps)
@@ -273,7 +274,7 @@ def bench_other_workloads(timed, peaks, n_steps=200):
         out[cfg1.name] = {"loop_steps_per_s": sps, "pwfs_frames_per_s": fr, "tuning": list(s1.tuning)}
     finally:
         s1.close()
-    cfg3 = get_config(3)
+    cfg3 = get_config("scao_elt_480px")
     gen = torch.Generator(device="cuda").manual_seed(3)
     pix = pas.pas_pupil_pixels(cfg3.Np, cfg3.obs)
     valid = pas.pas_valid_subaps(cfg3.Np, cfg3.obs, cfg3.n_sub)
@@ -317,7 +318,7 @@ def bench_psf(timed, sysg=None, n_frames=100):
     from paper_1607_07624_gb300 import pas
     from synth import get_config
     from synth.inputs import random_opd_nm
-    cfg = get_config(2)
+    cfg = get_config("scao_lbt_240px")
     Np, nd = cfg.Np, 8
     ctx = pas.pas_ctx_create(torch.cuda.current_stream())
     h = pas.pas_psf_create(ctx, Np, nd, 1650.0, cfg.obs)
@@ -372,7 +373,7 @@ def bench_sh(timed, n_frames=200):
     from paper_1607_07624_gb300 import pas
     from synth import get_config
     from synth.inputs import random_opd_nm
-    cfg = get_config(2)
+    cfg = get_config("scao_lbt_240px")
     Np, n_sub, ovs = cfg.Np, cfg.n_sub, 2
     ctx = pas.pas_ctx_create(torch.cuda.current_stream())
     h = pas.pas_sh_create(ctx, Np, n_sub, ovs, cfg.wavelength_nm, cfg.obs)
@@ -421,7 +422,7 @@ def bench_extended(timed, n_frames=100):
     from paper_1607_07624_gb300.system import SCAOSystem
     from synth import get_config
     from synth.configs import with_
-    cfg = get_config(2)
+    cfg = get_config("scao_lbt_240px")
     g = np.linspace(-1.0, 1.0, 3)
     ex, ey = np.repeat(g, 3), np.tile(g, 3)
     s = SCAOSystem(cfg, extended_source=(ex, ey), wfe_history=max(4096, n_frames + 64))
@@ -458,7 +459,7 @@ def bench_batch(timed, n_loops=64, n_steps=100):
     from paper_1607_07624_gb300.system import SCAOSystem
     from synth import get_config
     from synth.configs import with_
-    cfg = get_config(1)
+    cfg = get_config("scao_8m_64px")
     systems = [SCAOSystem(cfg, wfe_history=max(256, n_steps + 64))]
     batch = None
     try:

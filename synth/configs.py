@@ -112,7 +112,7 @@ CFG3 = SCAOConfig(
             LayerSpec(0.10, 10000.0, 20.0, 240.0), LayerSpec(0.08, 15000.0, 12.0, 300.0)),
     S=2048, n_steps=1000, seed=1000)
 
-CONFIGS = {1: CFG1, 2: CFG2, 3: CFG3}
+CONFIGS = {c.name: c for c in (CFG1, CFG2, CFG3)}
 
 # Batched Monte-Carlo workload: loops of three sizes stepped together. Per group
 # (count, configuration): 8 m / 128 px / 20x20 sub-apertures / 12 points, 25 m /
@@ -144,8 +144,9 @@ def batched_workload(r0_range=(0.08, 0.2), seed: int = 9000):
     return out
 
 
-def get_config(idx: int) -> SCAOConfig:
-    return CONFIGS[idx]
+def get_config(name: str) -> SCAOConfig:
+    """A workload by name: scao_8m_64px, scao_lbt_240px or scao_elt_480px."""
+    return CONFIGS[name]
 
 
 def tiny_config(Np: int = 16, N: int | None = None, n_sub: int = 4, K: int = 4,

@@ -84,7 +84,7 @@ def test_product_screens_match_oracle():
     from synth import get_config
     from synth.configs import with_
     from synth.inputs import screen_white_noise
-    cfg = with_(get_config(2), S=256)
+    cfg = with_(get_config("scao_lbt_240px"), S=256)
     w = [screen_white_noise(256, 3 + l) for l in range(3)]
     a = calib.layer_screens(cfg, w).astype(np.float64)
     b = at.layer_screens_nm(cfg, w)

@@ -56,5 +56,5 @@ def test_all_cores_oracle_pool_sums_concurrent_loops():
     """The all-cores CPU baseline: independent single-thread oracle loops of the small
     workload in fresh processes, their rates summed."""
     import bench
-    r = bench.run_oracle_pool(1, 0.5, 3, 2)
+    r = bench.run_oracle_pool("scao_8m_64px", 0.5, 3, 2)
     assert r["processes"] == 2 and r["steps"] >= 2 and r["value"] > 0

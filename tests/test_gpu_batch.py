@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 def _systems():
     from paper_1607_07624_gb300.system import SCAOSystem
-    cfg = get_config(1)
+    cfg = get_config("scao_8m_64px")
     first = SCAOSystem(cfg, autotune=False, wfe_history=256)
     out = [first]
     for seed in (2001, 2002):

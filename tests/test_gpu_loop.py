@@ -15,7 +15,7 @@ def cfg1_setup():
     from oracle import atmosphere as at
     from oracle import modal as md
     from oracle import optics as op
-    cfg = get_config(1)
+    cfg = get_config("scao_8m_64px")
     noises = [screen_white_noise(cfg.S, s) for s in layer_seeds(cfg.seed, len(cfg.layers))]
     screens = at.layer_screens_nm(cfg, noises)
     M = md.modal_basis(cfg.Np, cfg.obs, cfg.n_modes)

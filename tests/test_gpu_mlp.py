@@ -261,7 +261,7 @@ def test_out_of_range_sample_index_is_reported(env):
 def test_training_pair_is_pyramid_slopes_and_modal_projection(env):
     torch, pas, ctx = env
     from oracle import modal as md
-    cfg = get_config(1)
+    cfg = get_config("scao_8m_64px")
     pix = pas.pas_pupil_pixels(cfg.Np, cfg.obs)
     valid = pas.pas_valid_subaps(cfg.Np, cfg.obs, cfg.n_sub)
     M = md.modal_basis(cfg.Np, cfg.obs, cfg.n_modes)
@@ -291,7 +291,7 @@ def test_loop_with_single_layer_network_follows_linear_loop(env):
     a non-finite network output is caught and leaves the command finite."""
     torch, pas, ctx = env
     from paper_1607_07624_gb300.system import SCAOSystem
-    cfg = get_config(1)
+    cfg = get_config("scao_8m_64px")
     sys_lin = SCAOSystem(cfg, autotune=False)
     try:
         sys_lin.step(40)

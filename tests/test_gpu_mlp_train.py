@@ -16,7 +16,7 @@ def trained():
     import torch
     from paper_1607_07624_gb300.system import SCAOSystem
     from paper_1607_07624_gb300.learned import MLPReconstructor, generate_pairs
-    cfg = with_(get_config(2), magnitude=None)
+    cfg = with_(get_config("scao_lbt_240px"), magnitude=None)
     system = SCAOSystem(cfg, autotune=False, wfe_history=8192)
     S, Y = generate_pairs(system, 30000, seed=1)
     S_te, Y_te = generate_pairs(system, 3000, seed=2)

@@ -112,7 +112,7 @@ def test_camera_in_the_closed_loop_matches_oracle(env):
     torch, pas, ctx = env
     from oracle import psf as ps
     from paper_1607_07624_gb300.system import SCAOSystem
-    cfg = get_config(1)
+    cfg = get_config("scao_8m_64px")
     s = SCAOSystem(cfg, wfe_history=64)
     try:
         N = s.attach_camera(nd=4, wavelength_nm=LAM, start_step=2)

@@ -122,12 +122,12 @@ def test_non_integer_binning_matches_oracle(env, cfg):
     assert abs(fr_g.sum() - I.sum()) <= 1e-5 * I.sum()
 
 
-@pytest.mark.parametrize("idx", [1, 2, 3])
-def test_full_size_configs_open_loop_phase(env, idx):
+@pytest.mark.parametrize("name,k", [("scao_8m_64px", 1), ("scao_lbt_240px", 2), ("scao_elt_480px", 3)])
+def test_full_size_configs_open_loop_phase(env, name, k):
     """Full-size N = 128 / 480 / 960 grids on an open-loop screen sample (the phasor
     sees tens of radians)."""
-    cfg = get_config(idx)
-    opd = open_loop_opd(cfg, 4000 + idx).astype(np.float32)
+    cfg = get_config(name)
+    opd = open_loop_opd(cfg, 4000 + k).astype(np.float32)
     assert np.ptp(opd) * 2 * math.pi / cfg.wavelength_nm > 20.0
     fr_g, sl_g, valid = run_gpu(env, cfg, opd)
     check(cfg, fr_g, sl_g, *oracle_measure(cfg, opd, valid))
@@ -135,7 +135,7 @@ def test_full_size_configs_open_loop_phase(env, idx):
 
 def test_flat_wavefront_and_parseval(env):
     from oracle import optics as op
-    cfg = get_config(1)
+    cfg = get_config("scao_8m_64px")
     fr_g, sl_g, valid = run_gpu(env, cfg, np.zeros((cfg.Np, cfg.Np), np.float32))
     n = cfg.n_sub
     tots = [fr_g[:n, :n].sum(), fr_g[:n, n:].sum(), fr_g[n:, :n].sum(), fr_g[n:, n:].sum()]
@@ -181,7 +181,7 @@ def test_autotune_and_tunings_give_the_same_frame(env):
     """Every launch geometry computes the same frame (up to the float32 order of
     the modulation-group sums); the autotuner returns a valid one."""
     torch, pas, ctx = env
-    cfg = get_config(1)
+    cfg = get_config("scao_8m_64px")
     opd = torch.as_tensor(random_opd_nm(cfg.Np, 300.0, seed=9).astype(np.float32)).cuda()
     pyr = pas.pas_pyr_create(ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius, cfg.wavelength_nm, cfg.obs)
     try:
@@ -209,15 +209,16 @@ def test_autotune_and_tunings_give_the_same_frame(env):
         pas.pas_pyr_destroy(pyr)
 
 
-@pytest.mark.parametrize("cfg_idx,tunings", [(1, [None, (2, 1, 3, 2), (2, 1, 3, 4)]), (2, [None])])
-def test_noise_inside_the_pyramid_matches_oracle_counts(env, cfg_idx, tunings):
+@pytest.mark.parametrize("name,tunings", [("scao_8m_64px", [None, (2, 1, 3, 2), (2, 1, 3, 4)]),
+                                          ("scao_lbt_240px", [None])])
+def test_noise_inside_the_pyramid_matches_oracle_counts(env, name, tunings):
     """Photon and read noise drawn by the columns pass (the last CTA of each detector
     column; lanes of a group share a pixel's rejection loop) against the oracle's
     draw on the same noiseless float32 frame. The column splits put 4, 2 and 1 lanes
     on each pixel of the 64 px case."""
     torch, pas, ctx = env
     from oracle import noise as nz
-    cfg = get_config(cfg_idx)
+    cfg = get_config(name)
     opd = torch.as_tensor(open_loop_opd(cfg, 21).astype(np.float32)).cuda()
     n_pupil = int(pas.pas_pupil_pixels(cfg.Np, cfg.obs).size)
     photons, ron, seed = 40.0 * n_pupil, 0.5, 1234
@@ -293,7 +294,7 @@ def test_extended_source_full_size_sampled_and_point_identity(env):
     point-source sensor bit for bit; bad sources are rejected."""
     torch, pas, ctx = env
     from oracle import optics as op
-    cfg = get_config(2)
+    cfg = get_config("scao_lbt_240px")
     g = np.linspace(-1.0, 1.0, 3)
     ex, ey = [a for a in g for _ in g], [b for _ in g for b in g]
     opd = open_loop_opd(cfg, 91).astype(np.float32)

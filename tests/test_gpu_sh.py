@@ -104,7 +104,7 @@ def test_sh_closed_loop_matches_oracle(env):
     from paper_1607_07624_gb300.system import SCAOSystem
     from synth import get_config
     from synth.inputs import layer_seeds
-    cfg = get_config(1)
+    cfg = get_config("scao_8m_64px")
     ovs = 2
     noises = [screen_white_noise(cfg.S, s) for s in layer_seeds(cfg.seed, len(cfg.layers))]
     screens = at.layer_screens_nm(cfg, noises)
@@ -187,7 +187,7 @@ def test_sh_integrating_detector_loop_matches_oracle(env, n_int, noisy):
     from paper_1607_07624_gb300.system import SCAOSystem
     from synth import get_config
     from synth.inputs import layer_seeds
-    cfg = get_config(1)
+    cfg = get_config("scao_8m_64px")
     ovs = 2
     noises = [screen_white_noise(cfg.S, s) for s in layer_seeds(cfg.seed, len(cfg.layers))]
     screens = at.layer_screens_nm(cfg, noises)

@@ -102,7 +102,7 @@ def test_pyramid_mask_structure():
 
 @pytest.mark.parametrize("cfgkind", ["tiny", "cfg1"])
 def test_parseval_through_pyramid_and_binning(cfgkind):
-    cfg = tiny_config() if cfgkind == "tiny" else get_config(1)
+    cfg = tiny_config() if cfgkind == "tiny" else get_config("scao_8m_64px")
     opd = random_opd_nm(cfg.Np, 300.0, seed=11)
     frame, _ = op.pwfs_measure(opd, cfg)
     npix = op.pupil_mask(cfg.Np, cfg.obs).sum()
@@ -110,7 +110,7 @@ def test_parseval_through_pyramid_and_binning(cfgkind):
 
 
 def test_flat_wavefront_symmetries():
-    cfg = get_config(1)
+    cfg = get_config("scao_8m_64px")
     n = cfg.n_sub
     frame, s = op.pwfs_measure(np.zeros((cfg.Np, cfg.Np)), cfg)
     q00, q01, q10, q11 = frame[:n, :n], frame[:n, n:], frame[n:, :n], frame[n:, n:]
@@ -134,7 +134,7 @@ def test_tilt_sign_orthogonality_and_linearity():
     phase exp(+i 2 pi delta u~ / N) shifts its image by -delta, so the low-row
     images brighten and Sx < 0. Sy stays zero by symmetry; the response is odd
     and linear for small a."""
-    cfg = get_config(1)
+    cfg = get_config("scao_8m_64px")
     X, Y = op.pixel_coords(cfg.Np)
     _, s0 = op.pwfs_measure(np.zeros((cfg.Np, cfg.Np)), cfg)
     nv = s0.size // 2
@@ -220,7 +220,7 @@ def test_threshold_acquisition_agrees_with_geometric_rule():
     """Table 3's procedure: a flat frame at 20 lambda/D modulation, thresholded,
     finds (nearly) the geometric valid set."""
     from synth.configs import with_
-    cfg = with_(get_config(1), mod_radius=20.0, K=160)
+    cfg = with_(get_config("scao_8m_64px"), mod_radius=20.0, K=160)
     frame, _ = op.pwfs_measure(np.zeros((cfg.Np, cfg.Np)), cfg)
     geo = set(op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub).tolist())
     thr = set(op.valid_subapertures_threshold(frame, cfg.n_sub, 0.5).tolist())

@@ -19,8 +19,8 @@ FRAME_TOL = 1e-5
 SLOPE_TOL = 1e-5
 
 
-@pytest.mark.parametrize("cfg", [get_config(1), tiny_config(Np=60, N=120, n_sub=10, K=12, mod_radius=3.0),
-                                 get_config(2)], ids=lambda c: c.name)
+@pytest.mark.parametrize("cfg", [get_config("scao_8m_64px"), tiny_config(Np=60, N=120, n_sub=10, K=12, mod_radius=3.0),
+                                 get_config("scao_lbt_240px")], ids=lambda c: c.name)
 def test_static_measure_matches_object_measure_twice(cfg):
     import torch
     from paper_1607_07624_gb300 import pas
@@ -54,7 +54,7 @@ def test_static_measure_matches_object_measure_twice(cfg):
 def test_static_measure_rejects_geometries_beyond_its_array():
     import torch
     from paper_1607_07624_gb300 import pas
-    cfg = get_config(3)
+    cfg = get_config("scao_elt_480px")
     opd = torch.zeros(cfg.Np, cfg.Np, device="cuda")
     fr = torch.zeros(cfg.n_det, cfg.n_det, device="cuda")
     with pytest.raises(pas.PasError) as e:
