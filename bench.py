@@ -80,7 +80,7 @@ def oracle_sample(workload: str, budget_s: float, max_steps: int) -> dict:
     noise = None
     if cfg.magnitude is not None:
         npup = int(op.pupil_mask(cfg.Np, cfg.obs).sum())
-        noise = lambda fr, t: nz.apply_noise(fr, cfg.photons_per_frame(), npup, cfg.read_noise_e, cfg.seed, t)
+        noise = lambda fr, t: nz.apply_noise(fr, nz.photons_per_frame(cfg), npup, cfg.read_noise_e, cfg.seed, t)
     # one step to size the sample
     t0 = time.perf_counter()
     ct.closed_loop(cfg, screens, M, R, sn, valid, 1, noise=noise)

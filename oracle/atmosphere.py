@@ -85,6 +85,20 @@ def bilinear_sample(screen: np.ndarray, px: np.ndarray, py: np.ndarray) -> np.nd
             + (1 - fx) * fy * screen[i0, j1] + fx * fy * screen[i1, j1])
 
 
+def wind_velocity_px(cfg):
+    """Per-layer screen displacement per loop step, in screen pixels along (axis 0,
+    axis 1): speed * time step / pixel pitch, split by the wind direction measured
+    counter-clockwise from axis 0 (Table 1 wind_speed, wind_direction; main
+    time_step; the pitch is D / Np)."""
+    pitch = cfg.D / cfg.Np
+    out = []
+    for ly in cfg.layers:
+        d = ly.wind_mps * cfg.dt_s / pitch
+        ang = ly.wind_dir_deg * math.pi / 180.0
+        out.append((d * math.cos(ang), d * math.sin(ang)))
+    return out
+
+
 def layer_offset(step: int, v: float) -> float:
     """Wind displacement after ``step`` steps [px], one FP64 product."""
     return float(step) * v

@@ -19,7 +19,7 @@ from collections import deque
 
 import numpy as np
 
-from .atmosphere import atmo_opd
+from .atmosphere import atmo_opd, wind_velocity_px
 from .modal import basis_to_grid
 from .optics import pupil_mask, pwfs_intensity, detector_frame, pwfs_slopes
 
@@ -59,7 +59,7 @@ def closed_loop(cfg, screens_nm, M, R, sn, valid, n_steps, gain=None, delay=None
     gain = cfg.gain if gain is None else gain
     delay = cfg.delay if delay is None else delay
     mask = pupil_mask(cfg.Np, cfg.obs)
-    vel = cfg.layer_velocity_px()
+    vel = wind_velocity_px(cfg)
     n_m = M.shape[1]
     c = np.zeros(n_m)
     applied = deque([np.zeros(n_m) for _ in range(delay)], maxlen=delay)

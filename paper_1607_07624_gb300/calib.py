@@ -172,6 +172,29 @@ def pseudo_inverse(IM: np.ndarray, rcond: float = 1e-3) -> np.ndarray:
     return (Vt[keep].T * (1.0 / s[keep])) @ U[:, keep].T
 
 
+def wind_shift_px(cfg) -> np.ndarray:
+    """(L, 2) float64: each layer's screen shift per loop step in pixels along axis 0
+    and axis 1, v dt / dx rotated by the wind direction (counter-clockwise from axis
+    0; Table 1 wind_speed / wind_direction, main time_step)."""
+    out = np.empty((len(cfg.layers), 2))
+    for l, ly in enumerate(cfg.layers):
+        px_per_step = ly.wind_mps * cfg.dt_s * cfg.Np / cfg.D
+        a = math.radians(ly.wind_dir_deg)
+        out[l] = (px_per_step * math.cos(a), px_per_step * math.sin(a))
+    return out
+
+
+def detector_photons(cfg) -> float:
+    """Photons per detector frame for the guide star's magnitude (Table 1
+    wfs_source.magnitude, detector bandw / quantum_eff, time step): zero point x
+    10^(-m/2.5) x (pi/4) D^2 (1 - obs^2) x bandwidth x QE x dt; 0 when noiseless."""
+    if cfg.magnitude is None:
+        return 0.0
+    area_m2 = math.pi * (cfg.D / 2.0) ** 2 - math.pi * (cfg.obs * cfg.D / 2.0) ** 2
+    return (cfg.zero_point_ph_s_m2_nm * 10.0 ** (-cfg.magnitude / 2.5) * area_m2 * cfg.bandwidth_nm * cfg.qe
+            * cfg.dt_s)
+
+
 def footprint_offsets_px(heights_m, rho_arcsec: float, phi_deg: float, dx: float):
     """Per-layer footprint offsets (ox, oy) in screen pixels of a natural guide star
     off axis at (rho arcsec, phi degrees counter-clockwise from axis 0): layer h is

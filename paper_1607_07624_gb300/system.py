@@ -69,7 +69,7 @@ class SCAOSystem:
             noises = [screen_white_noise(cfg.S, s) for s in layer_seeds(cfg.seed, len(cfg.layers))]
             screens = calib.layer_screens(cfg, noises)
         self.d_screens = torch.as_tensor(np.ascontiguousarray(screens, dtype=np.float32)).to(self.dev)
-        vel = np.array(cfg.layer_velocity_px(), dtype=np.float64).reshape(-1, 2)
+        vel = calib.wind_shift_px(cfg)
         self.atmo_base = P.pas_atmo_create(self.ctx, len(cfg.layers), cfg.S, cfg.Np, vel[:, 0], vel[:, 1],
                                            self.d_screens)
         self.atmo = self.atmo_base
@@ -138,7 +138,7 @@ class SCAOSystem:
             self.tuning = P.pas_pyr_autotune(self.pyr, self.ctx, self.d_opd, 5)
             self.d_opd.zero_()
         if noise is None and cfg.magnitude is not None:
-            noise = (cfg.photons_per_frame(), cfg.read_noise_e, cfg.seed)
+            noise = (calib.detector_photons(cfg), cfg.read_noise_e, cfg.seed)
         if noise is not None:
             set_noise = P.pas_sh_set_noise if self.sh else P.pas_pyr_set_noise
             set_noise(self.sh or self.pyr, self.ctx, noise[0], noise[1], noise[2], 0)

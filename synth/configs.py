@@ -9,7 +9,10 @@ them from the other.
 Conventions shared by both sides (readings of the paper, which gives no formulas):
   * array axis 0 is x (rows), axis 1 is y (columns);
   * OPD in nm, phase = 2*pi*OPD/lambda;
-  * layer velocity in screen pixels per loop step along (x, y), FP64.
+  * wind direction counter-clockwise from axis 0.
+
+The arithmetic of the method (wind displacement per step, photon flux) is not
+here: the oracle and the product each compute it from these parameters.
 """
 from __future__ import annotations
 
@@ -74,22 +77,6 @@ class SCAOConfig:
     def delta(self) -> float:
         """Pyramid face phase slope: pupil images centred in the grid quadrants."""
         return self.N / 4.0
-
-    def layer_velocity_px(self) -> Tuple[Tuple[float, float], ...]:
-        """Per-layer screen shift per loop step in pixels along (axis 0, axis 1)."""
-        out = []
-        for ly in self.layers:
-            a = math.radians(ly.wind_dir_deg)
-            v = ly.wind_mps * self.dt_s / self.dx
-            out.append((v * math.cos(a), v * math.sin(a)))
-        return tuple(out)
-
-    def photons_per_frame(self) -> float:
-        if self.magnitude is None:
-            return 0.0
-        area = math.pi / 4.0 * self.D ** 2 * (1.0 - self.obs ** 2)
-        return (self.zero_point_ph_s_m2_nm * 10.0 ** (-0.4 * self.magnitude) * area
-                * self.bandwidth_nm * self.qe * self.dt_s)
 
 
 CFG1 = SCAOConfig(

@@ -160,7 +160,7 @@ def test_off_axis_source_loop_and_science_camera(cfg1_setup):
         assert np.max(np.abs(wg - ref["wfe"])) <= 2.0, np.max(np.abs(wg - ref["wfe"]))
         sr = s.sr[:n].cpu().numpy()
         mask = op.pupil_mask(cfg.Np, cfg.obs)
-        vel = cfg.layer_velocity_px()
+        vel = at.wind_velocity_px(cfg)
         d = cfg.delay
         sr_sci, sr_wfs = [], []
         for t in range(n):
@@ -214,11 +214,12 @@ def test_integrating_detector_loop_matches_oracle(cfg1_setup, n_int, noisy):
     """A pyramid detector integrating n_int steps per frame (pas_loop_set_integration):
     the loop against the oracle loop with the same integration (mean frame read out
     at (t + 1) mod n_int = 0, command held in between), with photon and read noise
-    drawn on the read-out frames; commands change only at read-outs."""
+    drawn on the read-out frames (the oracle loop is fed the kernel model's draws, so
+    that both loops see the same counts); commands change only at read-outs."""
     import torch
     from oracle import atmosphere as at
     from oracle import control as ct
-    from oracle import noise as nz
+    import kernel_noise_model as nz  # the kernel's float32 draws (not the oracle)
     from paper_1607_07624_gb300 import pas as P
     from paper_1607_07624_gb300.system import SCAOSystem
     cfg, screens, M, valid, sn, IM, R = cfg1_setup

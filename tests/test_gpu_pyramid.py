@@ -211,13 +211,14 @@ def test_autotune_and_tunings_give_the_same_frame(env):
 
 @pytest.mark.parametrize("name,tunings", [("scao_8m_64px", [None, (2, 1, 3, 2), (2, 1, 3, 4)]),
                                           ("scao_lbt_240px", [None])])
-def test_noise_inside_the_pyramid_matches_oracle_counts(env, name, tunings):
+def test_noise_inside_the_pyramid_matches_kernel_model_counts(env, name, tunings):
     """Photon and read noise drawn by the columns pass (the last CTA of each detector
-    column; lanes of a group share a pixel's rejection loop) against the oracle's
-    draw on the same noiseless float32 frame. The column splits put 4, 2 and 1 lanes
+    column; lanes of a group share a pixel's rejection loop) against the kernel
+    model's draws (the detector kernel's float32 decisions, not the oracle) on the
+    same noiseless float32 frame: the grouped draw equals the sequential one. The column splits put 4, 2 and 1 lanes
     on each pixel of the 64 px case."""
     torch, pas, ctx = env
-    from oracle import noise as nz
+    import kernel_noise_model as nz  # the kernel's float32 draws (not the oracle)
     cfg = get_config(name)
     opd = torch.as_tensor(open_loop_opd(cfg, 21).astype(np.float32)).cuda()
     n_pupil = int(pas.pas_pupil_pixels(cfg.Np, cfg.obs).size)

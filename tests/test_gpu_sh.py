@@ -132,11 +132,13 @@ def test_sh_closed_loop_matches_oracle(env):
         s.close()
 
 
-def test_sh_detector_noise_matches_oracle_counts(env):
-    """Photon and read noise on the Shack-Hartmann frame against the oracle's draw on
-    the same noiseless float32 frame; the slopes are the noisy frame's centroids."""
+def test_sh_detector_noise_matches_kernel_model_counts(env):
+    """Photon and read noise on the Shack-Hartmann frame against the kernel model's
+    draws (the float32 decisions of the detector kernel, not the oracle) on the same
+    noiseless float32 frame; the slopes are the noisy frame's centroids. The noise
+    law itself is judged against the oracle in test_gpu_noise_statistics."""
     torch, pas, ctx = env
-    from oracle import noise as nz
+    import kernel_noise_model as nz  # the kernel's float32 draws (not the oracle)
     from oracle import shack_hartmann as shm
     Np, n_sub, ovs, obs = 64, 8, 2, 0.1
     opd = random_opd_nm(Np, 60.0, seed=5).astype(np.float32)
@@ -176,11 +178,12 @@ def test_sh_detector_noise_matches_oracle_counts(env):
 def test_sh_integrating_detector_loop_matches_oracle(env, n_int, noisy):
     """The Shack-Hartmann loop with a detector integrating n_int steps per frame
     (pas_loop_set_integration) against the oracle loop integrating the oracle sensor's
-    frames (mean frame at (t + 1) mod n_int = 0, noise on it, command held between)."""
+    frames (mean frame at (t + 1) mod n_int = 0, noise on it, command held between).
+    With noise, the oracle loop is fed the kernel model's draws (same counts)."""
     from oracle import atmosphere as at
     from oracle import control as ct
     from oracle import modal as md
-    from oracle import noise as nz
+    import kernel_noise_model as nz  # the kernel's float32 draws (not the oracle)
     from oracle import optics as op
     from oracle import shack_hartmann as shm
     from paper_1607_07624_gb300 import pas as P
