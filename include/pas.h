@@ -228,7 +228,12 @@ pas_status pas_pyr_measure(pas_pyr_t pyr, const float* d_opd, float* d_frame, fl
  * device address once; make that first call before any stream capture. Every call
  * uses the same array and leaves its contents behind: the call clears what has to
  * start at zero itself, and calls whose work overlaps on the GPU (other streams,
- * other threads) race on it. Table set-up copies from host memory on the stream. */
+ * other threads) race on it. Its small tables (twiddles, mask, tilts, valid map)
+ * are built in host arrays of the library, under a lock held until they have been
+ * copied onto the stream (concurrent host calls take turns; nothing large goes on
+ * the caller's stack). Because those copies read host memory that the next call
+ * reuses, a call on a stream that is being captured is refused with PAS_EINVAL
+ * before anything is enqueued. */
 #define PAS_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
 pas_status pas_pyr_measure_static(const pas_pyr_params* p, const int32_t* h_valid, int32_t n_valid,
                                   const float* d_sn, const float* d_opd, float* d_frame,

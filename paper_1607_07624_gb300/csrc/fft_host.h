@@ -11,9 +11,9 @@
 namespace pas {
 
 // Twiddles of forward passes 0 .. M-2: entry tw_offset(pass) + (k - 1) S + n1 holds
-// w_L^{n1 k} = exp(-2 pi i n1 k / L) of that pass (float32 of the double value).
-inline std::vector<float2> fft_twiddles(int N) {
-  std::vector<float2> tw((size_t)tw_size(N));
+// w_L^{n1 k} = exp(-2 pi i n1 k / L) of that pass (float32 of the double value),
+// written into tw[0 .. tw_size(N)).
+inline void fft_twiddles_into(int N, float2* tw) {
   const int M = plan_count(N);
   for (int pass = 0; pass + 1 < M; ++pass) {
     const int R = plan_radix(N, pass), L = block_len(N, pass), S = L / R, off = tw_offset(N, pass);
@@ -23,6 +23,11 @@ inline std::vector<float2> fft_twiddles(int N) {
         tw[off + (k - 1) * S + n1] = make_float2((float)std::cos(a), (float)std::sin(a));
       }
   }
+}
+
+inline std::vector<float2> fft_twiddles(int N) {
+  std::vector<float2> tw((size_t)tw_size(N));
+  fft_twiddles_into(N, tw.data());
   return tw;
 }
 

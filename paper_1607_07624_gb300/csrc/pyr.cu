@@ -28,6 +28,7 @@
 #include "pdl.cuh"
 #include "phasor.cuh"
 #include "pyr.cuh"
+#include "pyr_host.h"
 #include "wfe.cuh"
 
 namespace pas {
@@ -724,64 +725,18 @@ static pas_status pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int3
   const int Km = p.K, Kt = Km * P;
   y->K_mod = Km;
   y->n_src = P;
-  std::vector<int> ey_id(P);
-  for (int q = 0; q < P; ++q) {
-    ey_id[q] = q;
-    for (int r = 0; r < q; ++r)
-      if (n_src > 0 && ey[r] == ey[q]) {
-        ey_id[q] = ey_id[r];
-        break;
-      }
-  }
-  std::vector<int> kmap(Kt);
-  std::vector<std::pair<int, int>> key_of_s;  // (modulation representative, ey id)
-  for (int q = 0; q < P; ++q)
-    for (int k = 0; k < Km; ++k) {
-      int rep = k;
-      if (Km % 2 == 0) {
-        int partner = ((Km / 2 - k) % Km + Km) % Km;
-        rep = std::min(k, partner);
-      }
-      const std::pair<int, int> key(rep, ey_id[q]);
-      int s = -1;
-      for (size_t t = 0; t < key_of_s.size(); ++t)
-        if (key_of_s[t] == key) s = (int)t;
-      if (s < 0) {
-        s = (int)key_of_s.size();
-        key_of_s.push_back(key);
-      }
-      kmap[q * Km + k] = s;
-    }
-  y->n_s = (int)key_of_s.size();
-  std::vector<float> alpha(Kt), beta(y->n_s), amp(Kt);
-  const double ramp = 1.0 / (2.0 * p.N);
-  for (int q = 0; q < P; ++q) {
-    const double oxq = n_src > 0 ? ex[q] : 0.0;
-    for (int k = 0; k < Km; ++k) {
-      double th = 2.0 * M_PI * (double)k / (double)Km;
-      alpha[q * Km + k] = (float)((p.mod_radius * std::cos(th) + oxq) / p.Np - ramp);
-      amp[q * Km + k] = (float)std::sqrt(src_w[q] * P);
-    }
-  }
-  for (int s = 0; s < y->n_s; ++s) {
-    double th = 2.0 * M_PI * (double)key_of_s[s].first / (double)Km;
-    const double oyq = n_src > 0 ? ey[key_of_s[s].second] : 0.0;
-    beta[s] = (float)((p.mod_radius * std::sin(th) + oyq) / p.Np - ramp);
-  }
+  std::vector<int> kmap(Kt), key_rep(Kt), key_ey(Kt);
+  std::vector<float> alpha(Kt), beta(Kt), amp(Kt);
+  y->n_s = pas::pyr_tilt_tables(p.Np, p.N, Km, p.mod_radius, P, n_src > 0 ? ex : nullptr, n_src > 0 ? ey : nullptr,
+                                src_w.data(), kmap.data(), alpha.data(), amp.data(), beta.data(), key_rep.data(),
+                                key_ey.data());
   // from here on p.K counts all tilt points
   p.K = Kt;
   y->p.K = Kt;
   // per-pass twiddle tables ([k-1][n1] = w_L^{n1 k}) and the digit-reversed
   // pyramid mask (delta = N/4: phase (pi/2)|u~|, divided by N) in padded layout
-  std::vector<float2> tw = pas::fft_twiddles(p.N), mk(kern.buf_n, make_float2(0.f, 0.f));
-  {
-    for (int j = 0; j < p.N; ++j) {
-      const int u = pas::fft_freq_at(p.N, j);
-      const double ut = std::fabs((double)u - 0.5 * (p.N - 1));
-      const double ph = 0.5 * M_PI * ut;
-      mk[pas::phys(j)] = make_float2((float)(std::cos(ph) / p.N), (float)(std::sin(ph) / p.N));
-    }
-  }
+  std::vector<float2> tw = pas::fft_twiddles(p.N), mk(kern.buf_n);
+  pas::pyr_mask_table(p.N, kern.buf_n, mk.data());
   double inv = 1.0 / p.wavelength_nm;
   y->inv_hi = (float)inv;
   y->inv_lo = (float)(inv - (double)y->inv_hi);
@@ -840,11 +795,8 @@ static pas_status pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int3
   C(y->d_beta, beta.data(), sizeof(float) * y->n_s);
   C(y->d_kmap, kmap.data(), sizeof(int) * p.K);
   {
-    std::vector<unsigned char> vpix((size_t)y->nd * y->nd, 0);
-    for (int v : valid) {
-      const int r = v / p.n_sub, c = v % p.n_sub, ns = p.n_sub, nd = y->nd;
-      vpix[r * nd + c] = vpix[r * nd + ns + c] = vpix[(ns + r) * nd + c] = vpix[(ns + r) * nd + ns + c] = 1;
-    }
+    std::vector<unsigned char> vpix((size_t)y->nd * y->nd);
+    pas::quadrant_valid_map(p.n_sub, valid.data(), y->n_valid, vpix.data());
     C(y->d_vpix, vpix.data(), vpix.size());
   }
   if (e == cudaSuccess) e = cudaMemset(y->d_sn, 0, sizeof(float) * 2 * y->n_valid);
@@ -857,20 +809,8 @@ static pas_status pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int3
   int occ = 1;
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern.cols, b * 32, y->smem_cols);
-  if (e == cudaSuccess) {
-    const int slots = std::max(1, occ) * std::max(1, ctx->sm_count);
-    double best = 1e30;
-    for (int G = 1; G <= p.K; ++G) {
-      const int kper = (p.K + G - 1) / G, Gc = (p.K + kper - 1) / kper;
-      const int waves = (y->nd * Gc + slots - 1) / slots;
-      const double cost = (double)waves * kper + 1e-3 * Gc;
-      if (cost < best) {
-        best = cost;
-        y->kper = kper;
-        y->G = Gc;
-      }
-    }
-  }
+  if (e == cudaSuccess)
+    pas::pick_modulation_groups(p.K, y->nd, std::max(1, occ) * std::max(1, ctx->sm_count), &y->kper, &y->G);
   if (e != cudaSuccess) {
     pas_pyr_destroy(y);
     return pas::set_error(ctx, PAS_ECUDA, "pas_pyr_create: %s", cudaGetErrorString(e));
@@ -1080,15 +1020,27 @@ static std::mutex g_static_mutex;
 static unsigned char* g_static_ptr[STATIC_MAX_DEVICES] = {};
 static int g_static_sms[STATIC_MAX_DEVICES] = {};
 
-// Device address of the scratch array for the current device (set-up once per
-// device, with that device current).
-static pas_status static_scratch(unsigned char** out, int* sms) {
+// Host tables of one call, filled under g_static_mutex and copied to the scratch
+// array before the mutex is released (a copy from pageable memory returns once the
+// source has been read), so concurrent callers never share them mid-call and no
+// call puts them on its thread's stack.
+struct StaticTables {
+  int32_t valid[STATIC_MAX_NSUB * STATIC_MAX_NSUB];
+  int kmap[STATIC_MAX_K], key_rep[STATIC_MAX_K], key_ey[STATIC_MAX_K];
+  float alpha[STATIC_MAX_K], beta[STATIC_MAX_K];
+  float2 tw[STATIC_TABLE], mk[STATIC_TABLE];
+  unsigned char vpix[(2 * STATIC_MAX_NSUB) * (2 * STATIC_MAX_NSUB)];
+};
+static StaticTables g_static_tables;
+
+// Device address of the scratch array for the current device (looked up once per
+// device, with that device current). The caller holds g_static_mutex.
+static pas_status static_scratch_locked(unsigned char** out, int* sms) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_global_error(PAS_ECUDA, "pas_pyr_measure_static: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= STATIC_MAX_DEVICES)
     return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: device index %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_static_mutex);
   if (!g_static_ptr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_pyr_scratch);
@@ -1113,6 +1065,19 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
   using namespace pas;
   if (!pp || !d_opd || !d_frame)
     return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: NULL parameters, input or frame");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  {
+    // the table copies below read host memory that is reused by the next call: a
+    // graph recorded from them would replay stale tables, so a capturing stream is
+    // refused before anything is enqueued
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess)
+      return set_global_error(PAS_ECUDA, "pas_pyr_measure_static: %s", cudaGetErrorString(e));
+    if (cap != cudaStreamCaptureStatusNone)
+      return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: the stream is being captured; this call "
+                              "copies host tables and cannot be recorded (use pas_pyr_create / pas_pyr_measure)");
+  }
   const pas_pyr_params p = *pp;
   if (!(p.Np > 0 && p.N == 2 * p.Np && p.n_sub > 0 && p.N % (2 * p.n_sub) == 0 && p.K >= 1 &&
         p.K <= STATIC_MAX_K && p.wavelength_nm > 0 && p.mod_radius >= 0 && p.obs >= 0 && p.obs < 1))
@@ -1126,77 +1091,42 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
   if (b > 16 || p.n_sub > STATIC_MAX_NSUB)
     return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: at most 16 fine pixels per detector pixel "
                             "and %d sub-apertures across", STATIC_MAX_NSUB);
-  // valid sub-apertures (host, on the stack)
-  int32_t valid[STATIC_MAX_NSUB * STATIC_MAX_NSUB];
+  if (kern.tw_n > STATIC_TABLE || kern.buf_n > STATIC_TABLE)
+    return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: table size");
+  if (h_valid && (n_valid <= 0 || n_valid > p.n_sub * p.n_sub))
+    return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: bad n_valid");
+  if (!h_valid && p.Np % p.n_sub != 0)
+    return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: geometric rule needs Np multiple of n_sub");
+
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  StaticTables& T = g_static_tables;
+  // valid sub-apertures
   int32_t nv = 0;
   if (h_valid) {
-    if (n_valid <= 0 || n_valid > p.n_sub * p.n_sub)
-      return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: bad n_valid");
     for (int j = 0; j < n_valid; ++j) {
       if (h_valid[j] < 0 || h_valid[j] >= p.n_sub * p.n_sub || (j > 0 && h_valid[j] <= h_valid[j - 1]))
         return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: valid indices must be ascending in [0, n_sub^2)");
-      valid[j] = h_valid[j];
+      T.valid[j] = h_valid[j];
     }
     nv = n_valid;
   } else {
-    if (p.Np % p.n_sub != 0)
-      return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: geometric rule needs Np multiple of n_sub");
-    pas_status s = pas_valid_subaps(p.Np, p.obs, p.n_sub, valid, STATIC_MAX_NSUB * STATIC_MAX_NSUB, &nv);
+    pas_status s = pas_valid_subaps(p.Np, p.obs, p.n_sub, T.valid, STATIC_MAX_NSUB * STATIC_MAX_NSUB, &nv);
     if (s != PAS_OK) return s;
   }
   if (d_slopes && nv <= 0) return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: no valid sub-aperture");
 
-  // distinct sin(theta) rows passes, tilts, twiddles and mask (host, on the stack)
-  int kmap[STATIC_MAX_K], rep_of_s[STATIC_MAX_K];
-  int n_s = 0;
-  for (int k = 0; k < p.K; ++k) {
-    int rep = k;
-    if (p.K % 2 == 0) rep = std::min(k, ((p.K / 2 - k) % p.K + p.K) % p.K);
-    int s = -1;
-    for (int t = 0; t < n_s; ++t)
-      if (rep_of_s[t] == rep) s = t;
-    if (s < 0) {
-      s = n_s;
-      rep_of_s[n_s++] = rep;
-    }
-    kmap[k] = s;
-  }
-  float alpha[STATIC_MAX_K], beta[STATIC_MAX_K];
-  const double ramp = 1.0 / (2.0 * p.N);
-  for (int k = 0; k < p.K; ++k)
-    alpha[k] = (float)(p.mod_radius * std::cos(2.0 * M_PI * (double)k / (double)p.K) / p.Np - ramp);
-  for (int s = 0; s < n_s; ++s)
-    beta[s] = (float)(p.mod_radius * std::sin(2.0 * M_PI * (double)rep_of_s[s] / (double)p.K) / p.Np - ramp);
-  float2 tw[STATIC_TABLE], mk[STATIC_TABLE];
-  if (kern.tw_n > STATIC_TABLE || kern.buf_n > STATIC_TABLE)
-    return set_global_error(PAS_EINVAL, "pas_pyr_measure_static: table size");
-  {
-    const int M = plan_count(p.N);
-    for (int pass = 0; pass + 1 < M; ++pass) {
-      const int R = plan_radix(p.N, pass), L = block_len(p.N, pass), S = L / R, off = tw_offset(p.N, pass);
-      for (int k = 1; k < R; ++k)
-        for (int n1 = 0; n1 < S; ++n1) {
-          const double a = -2.0 * M_PI * (double)(n1 * k) / (double)L;
-          tw[off + (k - 1) * S + n1] = make_float2((float)std::cos(a), (float)std::sin(a));
-        }
-    }
-    for (int j = 0; j < kern.buf_n; ++j) mk[j] = make_float2(0.f, 0.f);
-    for (int j = 0; j < p.N; ++j) {
-      const double ut = std::fabs((double)fft_freq_at(p.N, j) - 0.5 * (p.N - 1));
-      mk[phys(j)] = make_float2((float)(std::cos(0.5 * M_PI * ut) / p.N), (float)(std::sin(0.5 * M_PI * ut) / p.N));
-    }
-  }
-  unsigned char vpix[(2 * STATIC_MAX_NSUB) * (2 * STATIC_MAX_NSUB)];
-  for (int t = 0; t < nd * nd; ++t) vpix[t] = 0;
-  for (int j = 0; j < nv; ++j) {
-    const int r = valid[j] / p.n_sub, c = valid[j] % p.n_sub, ns = p.n_sub;
-    vpix[r * nd + c] = vpix[r * nd + ns + c] = vpix[(ns + r) * nd + c] = vpix[(ns + r) * nd + ns + c] = 1;
-  }
+  // rows passes, tilts, twiddles, mask and the valid-pixel map: the builders of
+  // pas_pyr_create, written into the file-scope tables
+  const int n_s = pyr_tilt_tables(p.Np, p.N, p.K, p.mod_radius, 1, nullptr, nullptr, nullptr, T.kmap, T.alpha,
+                                  nullptr, T.beta, T.key_rep, T.key_ey);
+  fft_twiddles_into(p.N, T.tw);
+  pyr_mask_table(p.N, kern.buf_n, T.mk);
+  quadrant_valid_map(p.n_sub, T.valid, nv, T.vpix);
 
   // carve the scratch array
   unsigned char* base = nullptr;
   int sms = 0;
-  pas_status st0 = static_scratch(&base, &sms);
+  pas_status st0 = static_scratch_locked(&base, &sms);
   if (st0 != PAS_OK) return st0;
   size_t off = 0;
   auto carve = [&](size_t bytes) -> unsigned char* {
@@ -1219,20 +1149,14 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
   y.n_schunks = (n_s + 3) / 4;
   y.s_chunk = (n_s + y.n_schunks - 1) / y.n_schunks;
   y.smem_cols = sizeof(float2) * ((size_t)kern.tw_n + kern.buf_n + (size_t)b * kern.pitch);
+  cudaError_t e = cudaSuccess;
   {
-    const int slots = 2 * std::max(1, sms);
-    int best_G = 1;
-    double best = 1e30;
-    for (int G = 1; G <= p.K; ++G) {
-      const int kper = (p.K + G - 1) / G, Gc = (p.K + kper - 1) / kper;
-      const double cost = (double)((nd * Gc + slots - 1) / slots) * kper + 1e-3 * Gc;
-      if (cost < best) {
-        best = cost;
-        best_G = Gc;
-      }
-    }
-    y.kper = (p.K + best_G - 1) / best_G;
-    y.G = (p.K + y.kper - 1) / y.kper;
+    // the columns pass's resident CTAs per SM, as pas_pyr_create counts them
+    int occ = 1;
+    e = raise_dyn_smem((const void*)kern.cols, y.smem_cols);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern.cols, b * 32, y.smem_cols);
+    if (e != cudaSuccess) return set_global_error(PAS_ECUDA, "pas_pyr_measure_static: %s", cudaGetErrorString(e));
+    pick_modulation_groups(p.K, nd, std::max(1, occ) * std::max(1, sms), &y.kper, &y.G);
   }
   y.d_H = reinterpret_cast<float2*>(carve(sizeof(float2) * (size_t)n_s * p.N * p.Np));
   y.d_part = reinterpret_cast<float*>(carve(sizeof(float) * (size_t)y.G * nd * nd));
@@ -1255,24 +1179,22 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
   y.has_sn = d_sn != nullptr;
   y.d_sn = const_cast<float*>(d_sn);
   const size_t smem_rows = rows_smem(&y, y.rows, y.s_chunk);
-  cudaStream_t st = (cudaStream_t)cuda_stream;
-  cudaError_t e = raise_dyn_smem((const void*)kern.rows, smem_rows);
-  if (e == cudaSuccess) e = raise_dyn_smem((const void*)kern.cols, y.smem_cols);
+  e = raise_dyn_smem((const void*)kern.rows, smem_rows);
   // tables in, counters (and the unused noise frame counter) cleared
   auto H2D = [&](void* dst, const void* src, size_t bytes) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
   };
-  H2D(y.d_tw, tw, sizeof(float2) * kern.tw_n);
-  H2D(y.d_mask, mk, sizeof(float2) * kern.buf_n);
-  H2D(y.d_alpha, alpha, sizeof(float) * p.K);
+  H2D(y.d_tw, T.tw, sizeof(float2) * kern.tw_n);
+  H2D(y.d_mask, T.mk, sizeof(float2) * kern.buf_n);
+  H2D(y.d_alpha, T.alpha, sizeof(float) * p.K);
   if (e == cudaSuccess) {
     tilt_table_kernel<<<p.K, 256, 0, st>>>(y.d_alpha, nullptr, p.K, p.Np, y.d_tilt);
     e = cudaGetLastError();
   }
-  H2D(y.d_beta, beta, sizeof(float) * n_s);
-  H2D(y.d_kmap, kmap, sizeof(int) * p.K);
-  H2D(y.d_valid, valid, sizeof(int32_t) * std::max(nv, 1));
-  H2D(y.d_vpix, vpix, (size_t)nd * nd);
+  H2D(y.d_beta, T.beta, sizeof(float) * n_s);
+  H2D(y.d_kmap, T.kmap, sizeof(int) * p.K);
+  H2D(y.d_valid, T.valid, sizeof(int32_t) * std::max(nv, 1));
+  H2D(y.d_vpix, T.vpix, (size_t)nd * nd);
   if (e == cudaSuccess) e = cudaMemsetAsync(y.d_done_col, 0, sizeof(unsigned int) * nd, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(y.d_frame_ctr, 0, sizeof(long long), st);
   if (e != cudaSuccess) return set_global_error(PAS_ECUDA, "pas_pyr_measure_static: %s", cudaGetErrorString(e));

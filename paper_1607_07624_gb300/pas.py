@@ -333,13 +333,26 @@ def pas_pyr_measure(pyr, ctx, d_opd, d_frame=None, d_slopes=None):
 
 def pas_pyr_measure_static(Np, N, K, n_sub, mod_radius, wavelength_nm, obs, d_opd, d_frame, d_slopes=None,
                            valid=None, d_sn=None, stream=None, local_norm=0):
-    """Allocation-free pyramid measurement (no object, no device allocation)."""
+    """Allocation-free pyramid measurement (no object, no device allocation).
+    d_opd [Np, Np], d_frame [2 n_sub, 2 n_sub], d_slopes and d_sn [2 n_valid]: float32
+    contiguous CUDA tensors (checked here: the C call cannot see their sizes)."""
     p = pas_pyr_params(Np, N, K, n_sub, mod_radius, wavelength_nm, obs, local_norm)
     if valid is not None:
         valid = np.ascontiguousarray(valid, dtype=np.int32)
         vptr, nv = valid.ctypes.data, valid.size
     else:
-        vptr, nv = None, 0
+        vptr = None
+        nv = pas_valid_subaps(Np, obs, n_sub).size if Np % max(n_sub, 1) == 0 else 0
+    for name, t, n in (("d_opd", d_opd, Np * Np), ("d_frame", d_frame, 4 * n_sub * n_sub),
+                       ("d_slopes", d_slopes, 2 * nv), ("d_sn", d_sn, 2 * nv)):
+        if t is None:
+            continue
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise PasError(PAS_EINVAL, f"pas_pyr_measure_static: {name} must be a contiguous float32 CUDA tensor")
+        if t.numel() != n:
+            raise PasError(PAS_EINVAL, f"pas_pyr_measure_static: {name} has {t.numel()} elements, needs {n}")
+    nv = 0 if valid is None else nv
     _check(_lib.pas_pyr_measure_static(C.byref(p), vptr, nv, _ptr(d_sn), _ptr(d_opd), _ptr(d_frame),
                                        _ptr(d_slopes), _stream_handle(stream)))
 

@@ -175,3 +175,15 @@ def test_binding_rejects_mismatched_source_arrays(lib):
         lib.pas_pyr_create_extended(None, 16, 32, 4, 2, 1.0, 750.0, 0.0, [0.0, 1.0], [0.0])
     with pytest.raises(ValueError):
         lib.pas_pyr_create_extended(None, 16, 32, 4, 2, 1.0, 750.0, 0.0, [0.0, 1.0], [0.0, 1.0], [1.0])
+
+
+def test_static_measure_binding_rejects_wrong_tensors_before_the_call():
+    """The C call sees raw pointers only: the binding checks dtype, device and size."""
+    torch = pytest.importorskip("torch")
+    from paper_1607_07624_gb300 import pas
+    Np, N, K, n_sub = 32, 64, 8, 8
+    opd = torch.zeros(Np, Np)            # host tensor: refused
+    fr = torch.zeros(2 * n_sub, 2 * n_sub)
+    with pytest.raises(pas.PasError) as e:
+        pas.pas_pyr_measure_static(Np, N, K, n_sub, 2.0, 750.0, 0.1, opd, fr)
+    assert e.value.status == pas.PAS_EINVAL and "d_opd" in str(e.value)
