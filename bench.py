@@ -1,15 +1,16 @@
 #!/usr/bin/env python3
 """Benchmark: AO loop steps/s and PWFS frames/s on one GB300 (per rank).
 
-Workload: the LBT-class single-conjugate loop (8.4 m, 240 px pupil, 480^2 FFT
-grid, 3 layers, 30x30 pyramid, 24 modulation points, 400 modes, magnitude-10
-photon noise plus 0.5 e- read noise), FP32. A step is one simulated millisecond:
-atmosphere + DM residual -> modulated pyramid -> detector noise -> slopes ->
-reconstructor -> integrator, replayed as one CUDA graph.
+Headline workload: the ELT-scale single-conjugate loop (39 m, 480 px pupil, 960^2
+FFT grid, 6 layers, 96x96 pyramid, 32 modulation points at 4 lambda/D, 4000 modes,
+noiseless), FP32. A step is one simulated millisecond: atmosphere + DM residual ->
+modulated pyramid -> slopes -> reconstructor -> integrator, replayed as one CUDA
+graph. The same loop with a bfloat16 DM basis and reconstructor, and the LBT-class
+loop (240 px, 3 layers, photon and read noise), are reported beside it.
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on
-the launching stream, the L2 flushed (256 MiB write) between steps outside the
-events; barrier + synchronize around the timed region, max over ranks.
+the launching stream, the L2 flushed (256 MiB write + read) between steps outside
+the events; barrier + synchronize around the timed region, max over ranks.
 Multi-GPU (torchrun): independent replicas (different seeds), weak scaling.
 
 --impl reference times the FP64 CPU oracle on this machine's host cores instead.
@@ -29,9 +30,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "AO loop steps/s (LBT-class SCAO, 1 GB300)"
+METRIC = "AO loop steps/s ({workload}, 1 GB300)"
 UNIT = "steps/s"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+FP32_PEAK_TFLOPS = None   # measured by the FMA probe at start-up (measure_fp32_peak)
+FP32_PEAK_SOURCE = None
 
 
 def parse():
@@ -40,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="scao_lbt_240px",
+    ap.add_argument("--config", default="scao_elt_480px",
                     help="workload: scao_8m_64px, scao_lbt_240px or scao_elt_480px")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--recon", default="fp32", choices=["fp32", "bf16"])
@@ -73,7 +75,12 @@ def oracle_sample(workload: str, budget_s: float, max_steps: int) -> dict:
     from synth.inputs import layer_seeds, random_matrix, screen_white_noise
     cfg = get_config(workload)
     screens = at.layer_screens_nm(cfg, [screen_white_noise(cfg.S, s) for s in layer_seeds(cfg.seed, len(cfg.layers))])
-    M = md.modal_basis(cfg.Np, cfg.obs, cfg.n_modes)
+    if cfg.n_modes > 1000:
+        # a seeded random basis of the workload's shape: the step's cost does not
+        # depend on its values (an orthonormal 4000-mode basis is a long setup)
+        M = random_matrix(int(op.pupil_mask(cfg.Np, cfg.obs).sum()), cfg.n_modes, 4, 1.0)
+    else:
+        M = md.modal_basis(cfg.Np, cfg.obs, cfg.n_modes)
     valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
     R = random_matrix(cfg.n_modes, 2 * valid.size, 5, 1e-3)
     sn = np.zeros(2 * valid.size)
@@ -89,7 +96,10 @@ def oracle_sample(workload: str, budget_s: float, max_steps: int) -> dict:
     t0 = time.perf_counter()
     ct.closed_loop(cfg, screens, M, R, sn, valid, n, noise=noise)
     dt = time.perf_counter() - t0
-    return {"steps": n, "seconds": dt, "value": n / dt}
+    basis = "random basis" if cfg.n_modes > 1000 else "the oracle's basis"
+    return {"steps": n, "seconds": dt, "value": n / dt,
+            "sample": f"{n} closed-loop steps of {cfg.name} after one sizing step, FP64 NumPy oracle, 1 thread, "
+                      f"{dt:.1f} s (setup untimed: screens, {basis}, random R of the right shape)"}
 
 
 def run_oracle_subprocess(workload: str, budget_s: float, max_steps: int) -> dict:
@@ -182,14 +192,16 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ roofline
 
-def algorithmic_work(cfg, n_pix, n_valid, n_modes, n_s_rows, recon_bytes_per_el):
-    """Per-launch algorithmic flops / bytes of each kernel of the step."""
+def algorithmic_work(cfg, n_pix, n_valid, n_modes, n_s_rows, recon_bytes_per_el, basis_bytes_per_el=4.0):
+    """Per-launch algorithmic flops / bytes of each kernel of the step. An FFT of
+    length N counts 5 N log2 N flops, the mask, tilt and |.|^2 work 6 N + 6 Np (+3 N
+    in the columns pass for the binning and the modulation sum)."""
     N, Np, K, L = cfg.N, cfg.Np, cfg.K, len(cfg.layers)
     fft_pair = 2 * 5.0 * N * math.log2(N) + 6.0 * N           # FFT + mask + IFFT
     return {
         # basis block, pixel list and output, command, the layers' pupil footprints
-        "residual_kernel": {"bound": "hbm", "bytes": 4.0 * n_modes * n_pix + 8.0 * n_pix + 4.0 * n_modes
-                            + 4.0 * L * (Np + 1) ** 2},
+        "residual_kernel": {"bound": "hbm", "bytes": basis_bytes_per_el * n_modes * n_pix + 8.0 * n_pix
+                            + 4.0 * n_modes + 4.0 * L * (Np + 1) ** 2},
         "pyr_rows_kernel": {"bound": "alu", "flops": n_s_rows * Np * (fft_pair + 6.0 * Np)},
         "pyr_cols_kernel": {"bound": "alu", "flops": K * N * (fft_pair + 6.0 * Np + 3.0 * N)},
         "slopes_kernel": {"bound": "latency", "bytes": 16.0 * n_valid + 8.0 * 2 * n_valid},
@@ -253,10 +265,8 @@ def bench_bf16_loop(cfg_r, timed, n_steps, wfe_fp32):
 
 
 def bench_other_workloads(timed, peaks, n_steps=200):
-    """Loop steps/s and PWFS frames/s of the 64 px workload (calibrated as the
-    headline one) and of the ELT-scale workload. The ELT loop uses random screens,
-    a random 4000-mode basis and a random reconstructor of the right shapes: its
-    cost is that of the real loop, its wavefront error is not meaningful."""
+    """Loop steps/s and PWFS frames/s of the 64 px workload (Zernike basis,
+    calibrated by push-pull on the GPU)."""
     import numpy as np
     import torch
     from paper_1607_07624_gb300 import pas
@@ -274,38 +284,74 @@ def bench_other_workloads(timed, peaks, n_steps=200):
         out[cfg1.name] = {"loop_steps_per_s": sps, "pwfs_frames_per_s": fr, "tuning": list(s1.tuning)}
     finally:
         s1.close()
-    cfg3 = get_config("scao_elt_480px")
-    gen = torch.Generator(device="cuda").manual_seed(3)
-    pix = pas.pas_pupil_pixels(cfg3.Np, cfg3.obs)
-    valid = pas.pas_valid_subaps(cfg3.Np, cfg3.obs, cfg3.n_sub)
-    screens = (torch.randn(len(cfg3.layers), cfg3.S, cfg3.S, device="cuda", generator=gen) * 300.0).cpu().numpy()
-    basis = torch.randn(pix.size, cfg3.n_modes, device="cuda", generator=gen).cpu().numpy()
-    R = (torch.randn(cfg3.n_modes, 2 * valid.size, device="cuda", generator=gen) * 1e-3).cpu().numpy()
-    s3 = SCAOSystem(cfg3, screens=screens, basis=basis, R=R, recon_precision=pas.PAS_BF16,
-                    wfe_history=max(4096, n_steps + 64))
-    del screens, basis, R
-    try:
-        n3 = max(20, n_steps // 4)
-        sps, _ = timed_loop(s3, timed, n3)
-        opd = torch.zeros(cfg3.Np, cfg3.Np, device="cuda")
-        pas.pas_atmo_advance(s3.atmo, s3.ctx, 0, opd)
-        fr = n3 / (timed(lambda: s3.measure(opd), n3) * 1e-3)
-        prof = {}
-        for _ in range(10):
-            for k, v in pas.pas_loop_profile(s3.loop, s3.ctx, 1).items():
-                prof[k] = prof.get(k, 0.0) + v / 10
-        res_bytes = (4.0 * cfg3.n_modes * pix.size + 8.0 * pix.size + 4.0 * cfg3.n_modes
-                     + 4.0 * len(cfg3.layers) * (cfg3.Np + 1) ** 2)
-        res_gbs = res_bytes / (prof["residual_kernel"] * 1e-3) / 1e9
-        out[cfg3.name] = {"loop_steps_per_s": sps, "pwfs_frames_per_s": fr, "tuning": list(s3.tuning),
-                          "kernel_ms": prof,
-                          "residual_roofline": {"bound": "hbm", "achieved": res_gbs, "peak": hbm, "unit": "GB/s",
-                                                "frac": res_gbs / hbm, "bytes_per_launch": res_bytes},
-                          "note": "random screens, basis and reconstructor of the workload's shapes "
-                                  "(timing only); reconstructor bf16 4000 x 14312"}
-    finally:
-        s3.close()
     return out
+
+
+def bench_lbt(args, timed, barrier, flush, world, dist, peaks, no_mlp=False):
+    """The LBT-class loop (8.4 m, 240 px, 3 layers, 400 KL modes calibrated on the
+    GPU, magnitude-10 photon noise + 0.5 e- read noise), FP32: steps/s, PWFS
+    frames/s, per-kernel rooflines and e2e as for the headline; the BF16 loop's WFE
+    against it; the PSF camera attached to it; the learned reconstructor on its
+    sizes. Returns (loop dict, learned-reconstructor dict or None)."""
+    import numpy as np
+    from paper_1607_07624_gb300 import pas
+    from synth import get_config
+    cfg = get_config("scao_lbt_240px")
+    hist = max(4096, args.steps + args.warmup + 64)
+    s = make_system(cfg, pas.PAS_FP32, pas.PAS_FP32, True, hist)
+    mlp_info = None
+    try:
+        r = measure_loop(s, cfg, args, timed, barrier, flush, world, dist, peaks)
+        wfe = r.pop("wfe")
+        r["residual_wfe_nm_mean"] = float(np.mean(wfe[len(wfe) // 5:])) if len(wfe) else None
+        r["tuning"] = list(s.tuning)
+        r["inputs"] = s.setup_note
+        try:
+            r["loop_bf16"] = bench_bf16_loop(cfg, timed, args.steps, wfe)
+        except Exception as e:
+            r["loop_bf16"] = {"error": str(e)}
+        try:
+            r["psf_camera"] = bench_psf(timed, s)
+        except Exception as e:
+            r["psf_camera"] = {"error": str(e)}
+        if not no_mlp:
+            try:
+                mlp_info = bench_mlp(s, peaks, timed)
+            except Exception as e:  # reported, never fatal for the headline number
+                mlp_info = {"error": str(e)}
+    finally:
+        s.close()
+    return r, mlp_info
+
+
+def cpu_baseline_for(cfg, args):
+    """The FP64 oracle on this host: one thread, and all cores as independent
+    single-thread loops (capped by host memory for the large workloads)."""
+    try:
+        r = run_oracle_subprocess(cfg.name, args.oracle_budget_s, 50)
+        cpu = {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": r["sample"]}
+    except Exception as e:  # the baseline is reported, never fatal
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+    if args.no_cpu_pool:
+        return cpu
+    n_proc = max(1, min(os.cpu_count() or 1, 16))
+    try:
+        phys = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError):
+        phys = None
+    # an ELT-scale oracle process holds a 179 156 x 4000 FP64 basis (5.7 GB) and its copies
+    per_proc = 16e9 if cfg.n_modes > 1000 else 2e9
+    if phys:
+        n_proc = max(1, min(n_proc, int(0.5 * phys // per_proc)))
+    try:
+        rp = run_oracle_pool(cfg.name, args.oracle_budget_s / 2, 50, n_proc)
+        cpu["all_cores"] = {"value": rp["value"], "unit": UNIT, "cores": n_proc, "kind": "oracle",
+                            "sample": f"{n_proc} independent closed loops of {cfg.name} in {n_proc} "
+                                      f"single-thread processes started together, {rp['steps']} steps "
+                                      f"in all (steps/s summed over the concurrent loops)"}
+    except Exception as e:
+        cpu["all_cores"] = {"value": None, "cores": n_proc, "sample": f"failed: {e}"}
+    return cpu
 
 
 def bench_psf(timed, sysg=None, n_frames=100):
@@ -643,7 +689,150 @@ def bench_mlp(sysg, peaks, timed, n_train=50, batch=1024):
             "network_chain_ms_in_loop": chain}
 
 
+def measure_fp32_peak(stream, reps=20, iters=4096, blocks_per_sm=8):
+    """FP32 FMA throughput of this GPU (pas_fp32_fma_probe over every SM, 2048 threads
+    per SM, each with 8 independent FMA chains), timed with CUDA events on the
+    launching stream: median and best of `reps` launches after a warm-up."""
+    import torch
+    from paper_1607_07624_gb300 import pas
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    n_blocks = sms * blocks_per_sm
+    sink = torch.empty(n_blocks * 256, device="cuda")
+    for _ in range(3):
+        flops = pas.pas_fp32_fma_probe(sink, n_blocks, iters, stream)
+    torch.cuda.synchronize()
+    rates = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pas.pas_fp32_fma_probe(sink, n_blocks, iters, stream)
+        b.record(stream)
+        b.synchronize()
+        rates.append(flops / (a.elapsed_time(b) * 1e-3) / 1e12)
+    return {"tflops": statistics.median(rates), "tflops_best": max(rates), "sms": sms,
+            "nominal_at_max_clock": sms * 128 * 2 * 2.070e9 / 1e12,
+            "how": f"pas_fp32_fma_probe: {n_blocks} CTAs x 256 threads x 8 FMA chains x {iters} rounds, "
+                   f"median of {reps} launches (CUDA events)"}
+
+
+def elt_timing_inputs(cfg, pix_n, n_valid, seed=3):
+    """The ELT-scale loop's DM basis and reconstructor as seeded random matrices of
+    the workload's shapes: the per-step cost does not depend on their values."""
+    import torch
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    basis = (torch.randn(pix_n, cfg.n_modes, device="cuda", generator=gen)).cpu().numpy()
+    R = (torch.randn(cfg.n_modes, 2 * n_valid, device="cuda", generator=gen) * 1e-3).cpu().numpy()
+    return basis, R
+
+
+def make_system(cfg, prec, dm_prec, tuning, wfe_history):
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    kw = {}
+    note = "calibrated: push-pull interaction matrix measured on the GPU, FP64 pseudo-inverse"
+    if cfg.n_modes > 1000:
+        pix = pas.pas_pupil_pixels(cfg.Np, cfg.obs)
+        valid = pas.pas_valid_subaps(cfg.Np, cfg.obs, cfg.n_sub)
+        kw["basis"], kw["R"] = elt_timing_inputs(cfg, pix.size, valid.size)
+        note = "von Karman screens of the workload; random basis and reconstructor of its shapes (timing)"
+    sysg = SCAOSystem(cfg, recon_precision=prec, dm_precision=dm_prec, wfe_history=wfe_history, autotune=tuning,
+                      **kw)
+    sysg.setup_note = note
+    return sysg
+
+
+def roofline_rows(cfg, sysg, prof, prec_bytes, peaks):
+    n_s_rows = cfg.K // 2 + 1 if cfg.K % 2 == 0 else cfg.K
+    work = algorithmic_work(cfg, sysg.n_pix, sysg.n_valid, sysg.n_modes, n_s_rows, prec_bytes,
+                            basis_bytes_per_el=sysg.basis_bytes_per_el)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roof = []
+    for k, ms in prof.items():
+        w = work.get(k)
+        if not w or ms <= 0:
+            continue
+        if w["bound"] == "alu":
+            ach = w["flops"] / (ms * 1e-3) / 1e12
+            roof.append({"kernel": k, "ms": ms, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "flops": w["flops"],
+                         "peak_source": FP32_PEAK_SOURCE})
+        else:
+            ach = w["bytes"] / (ms * 1e-3) / 1e9
+            roof.append({"kernel": k, "ms": ms, "bound": w["bound"], "achieved": ach, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": ach / hbm_peak, "bytes": w["bytes"],
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"})
+    return roof
+
+
+def measure_loop(sysg, cfg, args, timed, barrier, flush, world, dist, peaks, e2e=True):
+    """Steps/s of the whole step graph, PWFS frames/s, per-kernel profile and rooflines,
+    and the end-to-end rate through the public API with host copies."""
+    import numpy as np
+    import torch
+    from paper_1607_07624_gb300 import pas
+    stream = torch.cuda.current_stream()
+    sysg.step(max(3, args.warmup))
+    t_end = time.perf_counter() + args.soak
+    while time.perf_counter() < t_end:
+        sysg.step(50)
+    barrier()
+    sysg.set_state(0, np.zeros((sysg.delay, sysg.n_modes), dtype=np.float32))
+    barrier()
+    t_wall = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")
+    ms_total = timed(lambda: sysg.step(1), args.steps)
+    torch.cuda.nvtx.range_pop()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    ms_total = max_over_ranks(ms_total, dist, "cuda")
+    out = {"value": job_throughput(args.steps, world, ms_total), "ms_per_step": ms_total / args.steps,
+           "wall_timed_s": t_wall}
+    # PWFS frames/s: the sensor alone on the open-loop OPD of step 0
+    opd = torch.zeros(cfg.Np, cfg.Np, dtype=torch.float32, device="cuda")
+    pas.pas_atmo_advance(sysg.atmo, sysg.ctx, 0, opd)
+    n_fr = max(20, min(args.steps, 500))
+    out["pwfs_frames_per_s"] = world * n_fr / (timed(lambda: sysg.measure(opd), n_fr) / 1000.0)
+    # per-kernel durations (eager step with events around each kernel, L2 flushed)
+    prof = {}
+    n_prof = max(10, min(args.steps, 100))
+    for _ in range(n_prof):
+        flush.zero_()
+        for k, v in pas.pas_loop_profile(sysg.loop, sysg.ctx, 1).items():
+            prof[k] = prof.get(k, 0.0) + v / n_prof
+    out["kernel_ms"] = prof
+    out["roofline_by_kernel"] = roofline_rows(cfg, sysg, prof, sysg.recon_bytes_per_el, peaks)
+    wfe = sysg.wfe_nm(min(sysg.wfe_history, args.steps))
+    out["wfe"] = wfe
+    if e2e:
+        # end to end through the public API, host buffers: per step one graph launch
+        # (pas_loop_step), then the new modal command and the step's residual WFE are
+        # copied to pinned host memory and the stream is synchronised once
+        n_e2e = max(20, min(args.steps, 300))
+        cmd_host = torch.empty(sysg.n_modes, dtype=torch.float32, pin_memory=True)
+        wfe_host = torch.empty(1, dtype=torch.float64, pin_memory=True)
+        step0, _ = sysg.get_state()
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(n_e2e):
+            sysg.step(1)
+            cmd_host.copy_(sysg.loop_cmd, non_blocking=True)
+            k = (step0 + i) % sysg.wfe_history
+            wfe_host.copy_(sysg.loop_wfe[k:k + 1], non_blocking=True)
+            stream.synchronize()
+        e2e_s = time.perf_counter() - t0
+        barrier()
+        out["e2e"] = {"value": n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                      "d2h_bytes_per_step": 4 * sysg.n_modes + 8,
+                      "inputs": "device-resident loop state: the atmosphere's layers are uploaded once and "
+                                "advanced on the GPU, so a step has no per-step input to copy; each step "
+                                "copies its new modal command and residual WFE to pinned host memory and "
+                                "synchronises once"}
+    return out
+
+
 def main():
+    global FP32_PEAK_TFLOPS, FP32_PEAK_SOURCE
     args = parse()
     if args.oracle_sample:
         print(json.dumps(oracle_sample(args.config, args.oracle_budget_s, args.oracle_sample)))
@@ -660,12 +849,12 @@ def main():
         if rank != 0:
             return
         r = run_oracle_subprocess(args.config, args.oracle_budget_s, max(1, args.steps))
-        line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": args.gpus,
+        line = {"impl": "reference", "metric": METRIC.format(workload=cfg.name), "value": r["value"], "unit": UNIT, "n_gpus": args.gpus,
                 "steps": r["steps"], "warmup": 1, "ms_per_step": 1000.0 / r["value"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": cfg.name, "note": "FP64 NumPy oracle, single thread"},
                 "cpu_baseline": {"kind": "oracle", "cores": 1, "value": r["value"], "unit": UNIT,
-                                 "sample": f"{r['steps']} closed-loop steps of {cfg.name} ({r['seconds']:.1f} s)"},
+                                 "sample": r["sample"]},
                 "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -678,17 +867,28 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     from paper_1607_07624_gb300 import pas
-    from paper_1607_07624_gb300.system import SCAOSystem
     from synth.configs import with_
+
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(local_rank)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid else None) if rank == 0 else None
+    fp32 = measure_fp32_peak(stream)
+    FP32_PEAK_TFLOPS = fp32["tflops"]
+    FP32_PEAK_SOURCE = f"measured: FP32 FMA probe on {fp32['sms']} SMs (median), this run"
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
 
     cfg_r = with_(cfg, seed=replica_seed(cfg.seed, rank))
     prec = pas.PAS_BF16 if args.recon == "bf16" else pas.PAS_FP32
-    t_setup = time.perf_counter()
     tuning = tuple(int(v) for v in args.tuning.split(",")) if args.tuning else True
-    sysg = SCAOSystem(cfg_r, recon_precision=prec, wfe_history=max(4096, args.steps + args.warmup + 64),
-                      autotune=tuning)
+    hist = max(4096, args.steps + args.warmup + 64)
+    t_setup = time.perf_counter()
+    sysg = make_system(cfg_r, prec, pas.PAS_FP32, tuning, hist)
     t_setup = time.perf_counter() - t_setup
-    stream = torch.cuda.current_stream()
     # L2 flush between timed steps: write 256 MiB (evicts everything), then read
     # another 256 MiB so that the dirty lines are written back outside the timed
     # region and the next step starts from a clean, cold L2
@@ -703,25 +903,12 @@ def main():
             torch.sum(flush_r, dim=0, keepdim=True, out=flush_sink)
 
     flush = _Flush()
-    props = torch.cuda.get_device_properties(local_rank)
-    uuid = getattr(props, "uuid", None)
-    sampler = ClockSampler(f"GPU-{uuid}" if uuid else None) if rank == 0 else None
 
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
-
-    # warm-up (also captures the graph) and a short soak for steady clocks; the
-    # loop state is then reset so that the timed steps start a fresh simulation
-    sysg.step(max(3, args.warmup))
-    t_end = time.perf_counter() + args.soak
-    while time.perf_counter() < t_end:
-        sysg.step(50)
-    barrier()
-    sysg.set_state(0, np.zeros((sysg.delay, sysg.n_modes), dtype=np.float32))
-    barrier()
 
     def timed(fn, n):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
@@ -733,97 +920,51 @@ def main():
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in evs)
 
-    barrier()
-    t_wall = time.perf_counter()
-    torch.cuda.nvtx.range_push("timed")
-    ms_total = timed(lambda: sysg.step(1), args.steps)
-    torch.cuda.nvtx.range_pop()
-    barrier()
-    t_wall = time.perf_counter() - t_wall
-    ms_total = max_over_ranks(ms_total, dist, "cuda")
-    value = job_throughput(args.steps, world, ms_total)
-    ms_per_step = ms_total / args.steps
-
-    # PWFS frames/s: pas_pyr_measure alone on a fixed input, the open-loop
-    # atmospheric OPD of step 0 (pas_atmo_advance)
-    opd = torch.zeros(cfg.Np, cfg.Np, dtype=torch.float32, device="cuda")
-    pas.pas_atmo_advance(sysg.atmo, sysg.ctx, 0, opd)
-    n_fr = max(20, min(args.steps, 500))
-    ms_fr = timed(lambda: sysg.measure(opd), n_fr)
-    frames_per_s = world * n_fr / (ms_fr / 1000.0)
-
-    # per-kernel durations (eager step with events around each kernel, L2 flushed)
-    prof = {}
-    n_prof = max(10, min(args.steps, 100))
-    for _ in range(n_prof):
-        flush.zero_()
-        for k, v in pas.pas_loop_profile(sysg.loop, sysg.ctx, 1).items():
-            prof[k] = prof.get(k, 0.0) + v / n_prof
-
-    # end to end through the public API, host buffers: per step one graph launch
-    # (pas_loop_step), then the new modal command and the step's residual WFE are
-    # copied to pinned host memory and the stream is synchronised once
-    n_e2e = max(20, min(args.steps, 300))
-    cmd_host = torch.empty(sysg.n_modes, dtype=torch.float32, pin_memory=True)
-    wfe_host = torch.empty(1, dtype=torch.float64, pin_memory=True)
-    step0, _ = sysg.get_state()
-    barrier()
-    t0 = time.perf_counter()
-    for i in range(n_e2e):
-        sysg.step(1)
-        cmd_host.copy_(sysg.loop_cmd, non_blocking=True)
-        k = (step0 + i) % sysg.wfe_history
-        wfe_host.copy_(sysg.loop_wfe[k:k + 1], non_blocking=True)
-        stream.synchronize()
-    e2e_s = time.perf_counter() - t0
-    barrier()
-    clocks = sampler.stop() if sampler else None
-
-    wfe = sysg.wfe_nm(min(sysg.wfe_history, args.steps))
-    n_s_rows = cfg.K // 2 + 1 if cfg.K % 2 == 0 else cfg.K
-    work = algorithmic_work(cfg, sysg.n_pix, sysg.n_valid, sysg.n_modes, n_s_rows,
-                            2.0 if prec == pas.PAS_BF16 else 4.0)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    roof = []
-    for k, ms in prof.items():
-        w = work.get(k)
-        if not w or ms <= 0:
-            continue
-        if w["bound"] == "alu":
-            ach = w["flops"] / (ms * 1e-3) / 1e12
-            roof.append({"kernel": k, "ms": ms, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS})
-        else:
-            ach = w["bytes"] / (ms * 1e-3) / 1e9
-            roof.append({"kernel": k, "ms": ms, "bound": "hbm" if w["bound"] == "hbm" else w["bound"],
-                         "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak})
+    head = measure_loop(sysg, cfg, args, timed, barrier, flush, world, dist, peaks)
+    roof = head["roofline_by_kernel"]
     dom = max(roof, key=lambda r: r["ms"]) if roof else None
+    pwfs_roof = next((r for r in roof if r["kernel"] == "pyr_cols_kernel"), None)
     traffic = None
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
         traffic = tr.get(cfg.name, {}).get(dom["kernel"]) if dom else None
     except (OSError, ValueError):
         pass
+    setup_note = sysg.setup_note
+    sysg.close()
 
     extra = {}
+    mlp_info = None
+    # the same workload with the DM basis and the reconstructor in bfloat16 (float32
+    # sums and integrator): half the bytes of the dominant stream
+    try:
+        sysb = make_system(cfg_r, pas.PAS_BF16, pas.PAS_BF16, tuning, hist)
+        try:
+            rb = measure_loop(sysb, cfg, args, timed, barrier, flush, world, dist, peaks)
+        finally:
+            sysb.close()
+        rb_wfe = rb.pop("wfe")
+        extra["loop_bf16"] = {"steps_per_s": rb["value"], "ms_per_step": rb["ms_per_step"],
+                              "dm_basis": "bf16", "reconstructor": "bf16 (per-row scale)",
+                              "pwfs_frames_per_s": rb["pwfs_frames_per_s"], "kernel_ms": rb["kernel_ms"],
+                              "roofline_by_kernel": rb["roofline_by_kernel"], "e2e": rb["e2e"],
+                              "speedup_vs_fp32": rb["value"] / head["value"]}
+        n = min(len(rb_wfe), len(head["wfe"]), 10)
+        if "random" not in setup_note and n:
+            d = rb_wfe[:n] - head["wfe"][:n]
+            extra["loop_bf16"]["wfe_diff_nm_rms_first_10_steps"] = float(np.sqrt(np.mean(d * d)))
+    except Exception as e:
+        extra["loop_bf16"] = {"error": str(e)}
     if not args.no_extra:
         try:
-            extra["loop_bf16"] = bench_bf16_loop(cfg_r, timed, args.steps, wfe)
+            extra["scao_lbt_240px"], mlp_info = bench_lbt(args, timed, barrier, flush, world, dist, peaks,
+                                                          no_mlp=args.no_mlp)
         except Exception as e:
-            extra["loop_bf16"] = {"error": str(e)}
+            extra["scao_lbt_240px"] = {"error": str(e)}
         try:
             extra["other_workloads"] = bench_other_workloads(timed, peaks)
         except Exception as e:
             extra["other_workloads"] = {"error": str(e)}
-        try:
-            extra["psf_camera"] = bench_psf(timed, sysg)
-        except Exception as e:
-            extra["psf_camera"] = {"error": str(e)}
         try:
             extra["shack_hartmann"] = bench_sh(timed)
         except Exception as e:
@@ -841,12 +982,7 @@ def main():
         except Exception as e:
             extra["batched_workload"] = {"error": str(e)}
 
-    mlp_info = None
-    if not args.no_mlp:
-        try:
-            mlp_info = bench_mlp(sysg, peaks, timed)
-        except Exception as e:  # reported, never fatal for the headline number
-            mlp_info = {"error": str(e)}
+    clocks = sampler.stop() if sampler else None
 
     if rank != 0:
         if dist is not None:
@@ -855,56 +991,38 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        try:
-            r = run_oracle_subprocess(args.config, args.oracle_budget_s, 50)
-            cpu = {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{r['steps']} closed-loop steps of {cfg.name}, FP64 NumPy oracle, "
-                             f"1 thread, {r['seconds']:.1f} s (setup untimed; random R)"}
-        except Exception as e:  # the baseline is reported, never fatal
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
-        if cpu.get("value") and not args.no_cpu_pool:
-            n_proc = max(1, min(os.cpu_count() or 1, 16))
-            try:
-                rp = run_oracle_pool(args.config, args.oracle_budget_s / 2, 50, n_proc)
-                cpu["all_cores"] = {"value": rp["value"], "unit": UNIT, "cores": n_proc, "kind": "oracle",
-                                    "sample": f"{n_proc} independent closed loops of {cfg.name} in {n_proc} "
-                                              f"single-thread processes started together, {rp['steps']} steps "
-                                              f"in all (steps/s summed over the concurrent loops)"}
-            except Exception as e:
-                cpu["all_cores"] = {"value": None, "cores": n_proc, "sample": f"failed: {e}"}
+        cpu = cpu_baseline_for(cfg, args)
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC.format(workload=cfg.name), "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{cfg.name}: D={cfg.D} m, pupil {cfg.Np}^2 px, FFT {cfg.N}^2, "
                                f"{len(cfg.layers)} layers, {cfg.n_sub}x{cfg.n_sub} subaps, K={cfg.K}, "
-                               f"R={cfg.mod_radius} l/D, {sysg.n_modes} modes, mag {cfg.magnitude} + "
-                               f"{cfg.read_noise_e} e- RON",
-                   "l2": "flushed (256 MiB write) between timed steps", "recon": args.recon,
-                   "parallelism": f"replicas x{world}", "graph": "whole step, CUDA graph",
-                   "pyramid_tuning": dict(zip(("rows_per_cta", "row_chunks", "col_groups", "col_split"),
-                                             sysg.tuning))},
-        "pwfs_frames_per_s": frames_per_s,
+                               f"R={cfg.mod_radius} l/D, {cfg.n_modes} modes, "
+                               + (f"mag {cfg.magnitude} + {cfg.read_noise_e} e- RON" if cfg.magnitude is not None
+                                  else "noiseless"),
+                   "inputs": setup_note,
+                   "l2": "flushed (256 MiB write + read) between timed steps", "recon": args.recon,
+                   "parallelism": f"replicas x{world}", "graph": "whole step, CUDA graph"},
+        "pwfs_frames_per_s": head["pwfs_frames_per_s"],
         "roofline": None if dom is None else {"bound": dom["bound"], "achieved": dom["achieved"],
                                                "peak": dom["peak"], "unit": dom["unit"], "frac": dom["frac"],
                                                "traffic": traffic, "kernel": dom["kernel"],
-                                               "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
-                                                               if dom["bound"] == "alu"
-                                                               else "MEASURED_PEAKS.json hbm_gbs (of measured)")},
+                                               "peak_source": dom["peak_source"]},
+        "roofline_pwfs": pwfs_roof,
         "roofline_by_kernel": roof,
+        "kernel_ms": head["kernel_ms"],
+        "fp32_peak": fp32,
         "cpu_baseline": cpu,
-        "e2e": {"value": n_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 4 * sysg.n_modes + 8},
+        "e2e": head["e2e"],
         "gpu_launches": pas.PAS_LOOP_KERNELS * args.steps,
         "clocks": clocks,
         "learned_reconstructor": mlp_info,
         **extra,
-        "residual_wfe_nm_mean": float(np.mean(wfe[len(wfe) // 5:])) if len(wfe) else None,
-        "setup_s": t_setup, "wall_timed_s": t_wall,
+        "setup_s": t_setup, "wall_timed_s": head["wall_timed_s"],
     }
     print(json.dumps(line))
-    sysg.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -524,6 +524,15 @@ pas_status pas_mlp_pair(pas_pyr_t pyr, pas_dm_t dm, const float* d_opd, float am
  * graph is captured again at the next step. */
 pas_status pas_loop_set_mlp(pas_loop_t loop, pas_mlp_t mlp);
 
+/* FP32 throughput probe (no counterpart in the paper): the denominator of the FP32
+ * roofline quoted for the FFT passes. Launches n_blocks CTAs of 256 threads, each
+ * thread running 8 independent FMA chains for `iters` rounds and writing one float
+ * to d_sink (device float32 [n_blocks * 256], caller-owned); *h_flops receives the
+ * floating-point operations the launch performs (2 per FMA). Asynchronous on
+ * cuda_stream (NULL: the legacy default stream); the caller times it with events. */
+pas_status pas_fp32_fma_probe(void* cuda_stream, float* d_sink, int32_t n_blocks, int32_t iters,
+                              int64_t* h_flops);
+
 /* BF16 tensor-core GEMM (the kernel behind the batched network passes):
  * C[M][N] = A[M][K] * B[N][K]^T, A and B device bf16 (raw uint16 bits)
  * row-major with leading dimensions lda, ldb (multiples of 8, base 16-byte

@@ -139,6 +139,7 @@ _SIGS = {
     "pas_sh_set_noise": (C.c_int, [vp, C.c_double, C.c_double, C.c_uint64, i64]),
     "pas_sh_measure": (C.c_int, [vp, vp, vp, vp]),
     "pas_sh_destroy": (None, [vp]),
+    "pas_fp32_fma_probe": (C.c_int, [vp, vp, i32, i32, C.POINTER(C.c_int64)]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -647,3 +648,13 @@ def pas_sh_measure(sh, ctx, d_opd, d_frame=None, d_slopes=None):
 
 def pas_sh_destroy(sh):
     _lib.pas_sh_destroy(sh)
+
+
+def pas_fp32_fma_probe(d_sink, n_blocks, iters, stream=None) -> int:
+    """Launch the FP32 FMA throughput probe (d_sink: float32 CUDA tensor of
+    n_blocks * 256 elements); returns the launch's floating-point operations."""
+    if d_sink.numel() < n_blocks * 256:
+        raise PasError(PAS_EINVAL, "pas_fp32_fma_probe: d_sink too small")
+    f = C.c_int64()
+    _check(_lib.pas_fp32_fma_probe(_stream_handle(stream), _ptr(d_sink), int(n_blocks), int(iters), C.byref(f)))
+    return int(f.value)

@@ -109,6 +109,8 @@ class SCAOSystem:
         # a DM object holds only the basis: loops of one geometry may share one (dm=)
         self.own_dm = dm is None
         self.dm = P.pas_dm_create(self.ctx, self.basis, cfg.Np, cfg.obs, dm_precision) if dm is None else dm
+        self.basis_bytes_per_el = 2.0 if dm_precision == P.PAS_BF16 else 4.0
+        self.recon_bytes_per_el = 2.0 if recon_precision == P.PAS_BF16 else 4.0
         # buffers
         f32 = dict(device=self.dev, dtype=torch.float32)
         self.d_opd = torch.zeros(cfg.Np, cfg.Np, **f32)
