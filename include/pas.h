@@ -524,6 +524,35 @@ pas_status pas_mlp_pair(pas_pyr_t pyr, pas_dm_t dm, const float* d_opd, float am
  * graph is captured again at the next step. */
 pas_status pas_loop_set_mlp(pas_loop_t loop, pas_mlp_t mlp);
 
+/* ---------------------------------------------------------------- calibration
+ * One-off set-up on the GPU (Sec. Example: the reconstruction matrix is calibrated
+ * before the run; Table 1 modalrec). These calls allocate their own temporaries and
+ * return after their work has completed (they synchronise the stream). */
+
+/* Push-pull interaction matrix through one sensor (exactly one of pyr, sh non-NULL;
+ * its noise setting is ignored, its slope reference applies to both pushes and
+ * cancels): column m = (s(+amp M_m) - s(-amp M_m)) / (2 amp), M_m the DM's mode m
+ * at amp nm RMS. d_IM: device FP64 [n_modes][n_slopes] (column m of the
+ * n_slopes x n_modes matrix is contiguous), caller-owned. Runs on the DM's stream. */
+pas_status pas_calib_interaction_matrix(pas_pyr_t pyr, pas_sh_t sh, pas_dm_t dm, double amp_nm, double* d_IM);
+
+/* FP64 pseudo-inverse by one-sided Jacobi SVD (Hestenes): A is m x n column-major
+ * (d_A[j*m + i] = A(i, j)), m >= n; d_P receives A^+ as n x m row-major
+ * (d_P[i*m + k]), singular values below rcond * sigma_max dropped. Optional host
+ * outputs: h_sv[n] the singular values (descending), h_rank the number kept,
+ * h_sweeps the Jacobi sweeps run. PAS_ETIMEOUT if the rotations do not settle in
+ * 60 sweeps. Runs on the context's stream. */
+pas_status pas_pinv_f64(pas_ctx_t ctx, const double* d_A, int32_t m, int32_t n, double rcond, double* d_P,
+                        double* h_sv, int32_t* h_rank, int32_t* h_sweeps);
+
+/* FP64 product for the set-up (Gram matrices, basis changes):
+ * C[i*ldc + k] = sum_j X[i*sxi + j*sxj] * w[j] * Y[k*syk + j*syj] (w NULL: 1), i < ni,
+ * k < nk, j < nj; element strides in elements, all device FP64. Asynchronous on the
+ * context's stream. */
+pas_status pas_gemm_f64(pas_ctx_t ctx, const double* d_X, int64_t sxi, int64_t sxj, const double* d_Y,
+                        int64_t syk, int64_t syj, const double* d_w, int32_t ni, int32_t nk, int32_t nj,
+                        double* d_C, int64_t ldc);
+
 /* FP32 throughput probe (no counterpart in the paper): the denominator of the FP32
  * roofline quoted for the FFT passes. Launches n_blocks CTAs of 256 threads, each
  * thread running 8 independent FMA chains for `iters` rounds and writing one float

@@ -8,7 +8,9 @@ atmosphere (Table 1 ``atmo``/``seeing``) are built from parameters. This module:
   * von Karman phase screens by the FFT method (white noise is an input);
   * the Zernike modal basis in Noll order, orthonormalised on the pupil pixels;
   * the slope reference (a flat wavefront measured by the GPU pyramid);
-  * the push-pull interaction matrix (GPU pyramid) and its FP64 pseudo-inverse.
+  * the Zernike basis for large mode counts by Cholesky QR with FP64 products on the
+    GPU (the push-pull interaction matrix and its FP64 pseudo-inverse run on the GPU,
+    SCAOSystem.calibrate_reconstructor).
 
 Per-step work never runs here: the loop runs in libpas.so's kernels.
 """
@@ -19,6 +21,12 @@ import math
 import numpy as np
 
 R0_REF_NM = 500.0
+# The KL basis diagonalises the modal covariance built from every mode's spectrum on
+# a padded lattice (host FP64): practical up to about this many modes. Larger bases
+# use the orthonormal Zernike basis of the same span (zernike_basis_gpu).
+KL_MAX_MODES = 1000
+# Above this many modes the host Gram-Schmidt gives way to Cholesky QR on the GPU.
+HOST_GS_MAX_MODES = 400
 
 
 def _psd_scale() -> float:
@@ -103,6 +111,85 @@ def zernike_basis(Np: int, pupil_flat_idx: np.ndarray, n_modes: int) -> np.ndarr
     return Q * sgn * math.sqrt(npix)
 
 
+def zernike_raw(Np: int, pupil_flat_idx: np.ndarray, n_modes: int) -> np.ndarray:
+    """(n_pix, n_modes) float64 Zernike polynomials Noll j = 2..n_modes+1 at the pupil
+    pixel centres (unit RMS on the full disc), the radial parts by the three-term
+    recurrence of the Jacobi polynomials P_k^(m,0) in k (DLMF 18.9.1), one azimuthal
+    order at a time for all pixels: R_(m+2k)^m(rho) = (-1)^k rho^m P_k^(m,0)(1 - 2 rho^2)."""
+    i, jj = np.divmod(pupil_flat_idx.astype(np.int64), Np)
+    x = (i - (Np - 1) / 2.0) / (Np / 2.0)
+    y = (jj - (Np - 1) / 2.0) / (Np / 2.0)
+    rho = np.hypot(x, y)
+    th = np.arctan2(y, x)
+    t = 1.0 - 2.0 * rho * rho
+    nm = [noll_nm(j) for j in range(2, n_modes + 2)]
+    need = {}
+    for c, (n, m) in enumerate(nm):
+        need.setdefault(abs(m), []).append((n, m, c))
+    Z = np.empty((rho.size, n_modes))
+    for a, items in need.items():
+        kmax = max((n - a) // 2 for n, _, _ in items)
+        rho_a = rho ** a
+        P_prev, P = None, np.ones_like(t)
+        polys = [P]
+        for k in range(1, kmax + 1):
+            if k == 1:
+                P_new = (a + 1) + (a + 2) * (t - 1.0) / 2.0
+            else:
+                s2 = 2 * k + a
+                c0 = 2.0 * k * (k + a) * (s2 - 2)
+                c1 = (s2 - 1) * ((s2) * (s2 - 2) * t + a * a)
+                c2 = 2.0 * (k + a - 1) * (k - 1) * s2
+                P_new = (c1 * P - c2 * P_prev) / c0
+            P_prev, P = P, P_new
+            polys.append(P)
+        for n, m, c in items:
+            k = (n - a) // 2
+            r = (-1) ** k * rho_a * polys[k]
+            if m == 0:
+                Z[:, c] = math.sqrt(n + 1) * r
+            elif m > 0:
+                Z[:, c] = math.sqrt(2 * (n + 1)) * r * np.cos(m * th)
+            else:
+                Z[:, c] = math.sqrt(2 * (n + 1)) * r * np.sin(-m * th)
+    return Z
+
+
+def zernike_basis_gpu(ctx, Np: int, pupil_flat_idx: np.ndarray, n_modes: int, passes: int = 2) -> np.ndarray:
+    """The Zernike basis of zernike_basis (Noll order, orthonormal on the pupil pixels,
+    1 nm RMS per unit coefficient) for large mode counts: Cholesky QR repeated
+    `passes` times, Q = Z L^-T with L L^T = Z^T Z, the Gram matrices and the products
+    in FP64 on the GPU (pas_gemm_f64), the n x n Cholesky factor on the host. Column
+    order is kept (R = L^T upper triangular with a positive diagonal), so Q is the
+    Gram-Schmidt basis of the same columns. Returns float64 (n_pix, n_modes)."""
+    import torch
+    from . import pas as P
+    Z = zernike_raw(Np, pupil_flat_idx, n_modes)
+    m, n = Z.shape
+    dev = torch.device("cuda")
+    Zd = torch.as_tensor(np.ascontiguousarray(Z.T)).to(dev)     # column a of Z at Zd[a]
+    raw = Zd.clone()
+    del Z
+    G = torch.empty(n, n, device=dev, dtype=torch.float64)
+    for _ in range(passes):
+        # G[a][b] = sum_k Z[k, a] Z[k, b]
+        P.pas_gemm_f64(ctx, Zd, m, 1, Zd, m, 1, None, n, n, m, G, n)
+        torch.cuda.synchronize()
+        L = np.linalg.cholesky(0.5 * (G.cpu().numpy() + G.cpu().numpy().T))
+        T = np.linalg.solve(L, np.eye(n)).T                   # L^-T (upper triangular)
+        Td = torch.as_tensor(np.ascontiguousarray(T)).to(dev)
+        Q = torch.empty_like(Zd)
+        # Q[b][k] = sum_a T[a][b] Z[k, a]
+        P.pas_gemm_f64(ctx, Td, 1, n, Zd, 1, m, None, n, m, n, Q, m)
+        torch.cuda.synchronize()
+        Zd = Q
+    # sign convention of zernike_basis: positive overlap with the raw polynomial
+    sgn = torch.sign((Zd * raw).sum(dim=1))
+    sgn[sgn == 0] = 1.0
+    Zd *= (sgn * math.sqrt(m))[:, None]
+    return Zd.t().cpu().numpy()
+
+
 def modal_covariance(basis: np.ndarray, pix: np.ndarray, Np: int, pitch_m: float, r0_m: float, L0_m: float,
                      pad: int = 2, chunk: int = 64) -> np.ndarray:
     """Covariance [rad^2 at the r0 wavelength] of the coefficients a = (1/n) B^T phi
@@ -163,13 +250,6 @@ def kl_basis(Np: int, pix: np.ndarray, n_modes: int, pitch_m: float, r0_m: float
         K *= np.sign(np.cos(0.73 * q + 0.11 + 1.37 * np.sin(0.29 * q)) @ K)
         _KL_CACHE[key] = K
     return _KL_CACHE[key]
-
-
-def pseudo_inverse(IM: np.ndarray, rcond: float = 1e-3) -> np.ndarray:
-    """FP64 SVD pseudo-inverse, singular values below rcond * max dropped."""
-    U, s, Vt = np.linalg.svd(np.asarray(IM, dtype=np.float64), full_matrices=False)
-    keep = s >= rcond * s.max()
-    return (Vt[keep].T * (1.0 / s[keep])) @ U[:, keep].T
 
 
 def wind_shift_px(cfg) -> np.ndarray:

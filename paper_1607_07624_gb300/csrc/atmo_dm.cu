@@ -155,7 +155,6 @@ __global__ void atmo_kernel(AtmoArgs a, const long long* d_step, long long h_ste
 // ROWS partial sums per pixel meet once in shared memory at the end. The basis is
 // constant, so the first loads are issued before the programmatic wait and
 // overlap the predecessor kernel.
-constexpr int RES_TILE = 64;        // pixels per CTA (one contiguous basis block)
 constexpr int RES_THREADS = 256;
 constexpr int RES_U = 5;            // loads in flight per thread
 

@@ -5,6 +5,10 @@
 
 namespace pas {
 
+// Pixels per basis block: the DM basis is stored [tile][mode][RES_TILE], one contiguous
+// block per tile of RES_TILE pupil pixels (one residual CTA each).
+constexpr int RES_TILE = 64;
+
 struct AtmoArgs {
   const float* screens = nullptr;  // [L][S][S]
   int L = 0, S = 0, Np = 0;

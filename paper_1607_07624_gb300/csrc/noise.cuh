@@ -42,7 +42,10 @@ __device__ inline u32x4 noise_block(uint64_t seed, uint32_t pixel, uint64_t fram
                        (uint32_t)(seed >> 32));
 }
 
-// Inversion by sequential search (lambda < 10) on block 0 word 2.
+// Inversion by sequential search (lambda < 10) on block 0 word 2. The float32 CDF
+// stops growing once the terms fall below its resolution near 1; a uniform above that
+// last value takes the count at which it stopped (the tail beyond is below float32
+// resolution), instead of running the search to its bound.
 __device__ inline float poisson_small(float lam, const u32x4& w0) {
   const float u = u01f(w0.v[2]);
   float p = expf(-lam);
@@ -51,7 +54,9 @@ __device__ inline float poisson_small(float lam, const u32x4& w0) {
   while (u > F && k < 256) {
     ++k;
     p = __fmul_rn(p, __fmul_rn(lam, __frcp_rn((float)k)));
-    F = __fadd_rn(F, p);
+    const float Fn = __fadd_rn(F, p);
+    if (Fn == F) break;
+    F = Fn;
   }
   return (float)k;
 }

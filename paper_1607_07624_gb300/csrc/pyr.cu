@@ -614,6 +614,17 @@ pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_
 }
 
 int pyr_n_pupil(pas_pyr_t y) { return y->n_pupil; }
+int pyr_n_valid(pas_pyr_t y) { return y->n_valid; }
+
+pas_status pyr_measure_noiseless(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes, cudaStream_t st) {
+  // launch arguments are taken by value, so the object's noise setting is restored
+  // as soon as the kernels are enqueued
+  const float scale = y->photon_scale;
+  y->photon_scale = 0.f;
+  const pas_status s = pyr_launch(y, d_opd, d_frame, d_slopes, st, nullptr, false);
+  y->photon_scale = scale;
+  return s;
+}
 int pyr_nd(pas_pyr_t y) { return y->nd; }
 int pyr_np(pas_pyr_t y) { return y->p.Np; }
 

@@ -29,6 +29,10 @@ struct LoopExtra {
 pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes,
                       cudaStream_t st, const LoopExtra* extra, bool increment_ctr,
                       cudaEvent_t* ev = nullptr, bool pdl_first = false);
+// Noiseless frame and slopes of d_opd on `st` (the sensor's reference subtracted),
+// whatever noise the object is set to: calibration measurements.
+pas_status pyr_measure_noiseless(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes, cudaStream_t st);
+int pyr_n_valid(pas_pyr_t y);
 int pyr_n_pupil(pas_pyr_t y);
 int pyr_nd(pas_pyr_t y);
 int pyr_np(pas_pyr_t y);

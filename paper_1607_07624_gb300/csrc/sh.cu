@@ -189,6 +189,14 @@ pas_status sh_launch(pas_sh_t S, const float* d_opd, float* d_frame, float* d_sl
   return PAS_OK;
 }
 
+pas_status sh_measure_noiseless(pas_sh_t S, const float* d_opd, float* d_frame, float* d_slopes, cudaStream_t st) {
+  const float scale = S->photon_scale;
+  S->photon_scale = 0.f;
+  const pas_status r = sh_launch(S, d_opd, d_frame, d_slopes, st, nullptr, false);
+  S->photon_scale = scale;
+  return r;
+}
+
 int sh_n_slopes(pas_sh_t S) { return 2 * S->nv; }
 int sh_frame_side(pas_sh_t S) { return S->n_sub * S->M; }
 int sh_np(pas_sh_t S) { return S->Np; }

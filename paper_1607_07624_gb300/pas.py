@@ -140,6 +140,10 @@ _SIGS = {
     "pas_sh_measure": (C.c_int, [vp, vp, vp, vp]),
     "pas_sh_destroy": (None, [vp]),
     "pas_fp32_fma_probe": (C.c_int, [vp, vp, i32, i32, C.POINTER(C.c_int64)]),
+    "pas_calib_interaction_matrix": (C.c_int, [vp, vp, vp, C.c_double, vp]),
+    "pas_pinv_f64": (C.c_int, [vp, vp, i32, i32, C.c_double, vp, vp, C.POINTER(i32), C.POINTER(i32)]),
+    "pas_gemm_f64": (C.c_int, [vp, vp, C.c_int64, C.c_int64, vp, C.c_int64, C.c_int64, vp, i32, i32, i32, vp,
+                               C.c_int64]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -658,3 +662,38 @@ def pas_fp32_fma_probe(d_sink, n_blocks, iters, stream=None) -> int:
     f = C.c_int64()
     _check(_lib.pas_fp32_fma_probe(_stream_handle(stream), _ptr(d_sink), int(n_blocks), int(iters), C.byref(f)))
     return int(f.value)
+
+
+def _f64_cuda(name, t, numel=None):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise PasError(PAS_EINVAL, f"{name} must be a contiguous float64 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise PasError(PAS_EINVAL, f"{name} has {t.numel()} elements, needs {numel}")
+
+
+def pas_calib_interaction_matrix(ctx, dm, d_IM, amp_nm, n_modes, n_slopes, pyr=None, sh=None):
+    """Push-pull interaction matrix on the GPU into d_IM (float64 CUDA tensor of
+    shape (n_modes, n_slopes): row m is the IM's column m)."""
+    _f64_cuda("d_IM", d_IM, n_modes * n_slopes)
+    _check(_lib.pas_calib_interaction_matrix(pyr, sh, dm, float(amp_nm), _ptr(d_IM)), ctx)
+
+
+def pas_pinv_f64(ctx, d_A, m, n, rcond, d_P):
+    """FP64 pseudo-inverse of the m x n column-major d_A (a (n, m) row-major tensor)
+    into d_P ((n, m) row-major = A^+). Returns (singular values, rank, sweeps)."""
+    _f64_cuda("d_A", d_A, m * n)
+    _f64_cuda("d_P", d_P, m * n)
+    sv = np.zeros(n, dtype=np.float64)
+    rank, sweeps = i32(), i32()
+    _check(_lib.pas_pinv_f64(ctx, _ptr(d_A), int(m), int(n), float(rcond), _ptr(d_P), sv.ctypes.data,
+                             C.byref(rank), C.byref(sweeps)), ctx)
+    return sv, rank.value, sweeps.value
+
+
+def pas_gemm_f64(ctx, X, sxi, sxj, Y, syk, syj, w, ni, nk, nj, Cout, ldc):
+    """C[i*ldc + k] = sum_j X[i*sxi + j*sxj] w[j] Y[k*syk + j*syj] (FP64 CUDA tensors)."""
+    for nm, t in (("X", X), ("Y", Y), ("C", Cout)) + ((("w", w),) if w is not None else ()):
+        _f64_cuda(nm, t)
+    _check(_lib.pas_gemm_f64(ctx, _ptr(X), int(sxi), int(sxj), _ptr(Y), int(syk), int(syj), _ptr(w), int(ni),
+                             int(nk), int(nj), _ptr(Cout), int(ldc)), ctx)

@@ -99,11 +99,20 @@ class SCAOSystem:
                                                      cfg.wavelength_nm, cfg.obs, ex, ey, w, self.valid)
             frame_side = cfg.n_det
         # DM
+        self.basis_kind = "given"
         if basis is None:
-            if cfg.basis == "kl":
+            if cfg.basis == "kl" and cfg.n_modes <= calib.KL_MAX_MODES:
                 basis = calib.kl_basis(cfg.Np, self.pix, cfg.n_modes, cfg.dx, cfg.r0_m, cfg.L0_m)
+                self.basis_kind = "kl"
+            elif cfg.n_modes > calib.HOST_GS_MAX_MODES:
+                # the KL modes of this many Zernikes span the same space; with one gain
+                # on every mode and an untruncated pseudo-inverse the loop does not
+                # depend on the orthonormal basis chosen within that span
+                basis = calib.zernike_basis_gpu(self.ctx, cfg.Np, self.pix, cfg.n_modes)
+                self.basis_kind = "zernike (Cholesky QR on the GPU)"
             else:
                 basis = calib.zernike_basis(cfg.Np, self.pix, cfg.n_modes)
+                self.basis_kind = "zernike"
         self.basis = np.ascontiguousarray(basis, dtype=np.float32)
         self.n_modes = self.basis.shape[1]
         # a DM object holds only the basis: loops of one geometry may share one (dm=)
@@ -174,22 +183,18 @@ class SCAOSystem:
         return self.d_frame, self.d_slopes
 
     def calibrate_reconstructor(self, amp_nm=None, rcond=1e-3):
-        """Push-pull interaction matrix measured by the GPU sensor; FP64 pinv."""
+        """Push-pull interaction matrix measured by the GPU sensor
+        (pas_calib_interaction_matrix) and its FP64 pseudo-inverse by one-sided Jacobi
+        SVD on the GPU (pas_pinv_f64); singular values below rcond x the largest are
+        dropped. Keeps IM (n_slopes x n_modes, host FP64) and its singular values."""
         amp = self.cfg.pushpull_nm if amp_nm is None else amp_nm
-        cmd = torch.zeros(self.n_modes, device=self.dev, dtype=torch.float32)
-        opd = torch.zeros(self.cfg.Np, self.cfg.Np, device=self.dev, dtype=torch.float32)
-        IM = torch.zeros(2 * self.n_valid, self.n_modes, device=self.dev, dtype=torch.float64)
-        for m in range(self.n_modes):
-            cols = []
-            for sgn in (1.0, -1.0):
-                cmd.zero_()
-                cmd[m] = sgn * amp
-                P.pas_dm_update(self.dm, self.ctx, None, None, cmd, opd)
-                self.measure(opd)
-                cols.append(self.d_slopes.double().clone())
-            IM[:, m] = (cols[0] - cols[1]) / (2.0 * amp)
-        self.IM = IM.cpu().numpy()
-        return calib.pseudo_inverse(self.IM, rcond)
+        ns, nm = 2 * self.n_valid if self.pyr else P.pas_sh_n_valid(self.sh) * 2, self.n_modes
+        d_IM = torch.empty(nm, ns, device=self.dev, dtype=torch.float64)   # row m = IM column m
+        P.pas_calib_interaction_matrix(self.ctx, self.dm, d_IM, amp, nm, ns, pyr=self.pyr, sh=self.sh)
+        d_R = torch.empty(nm, ns, device=self.dev, dtype=torch.float64)
+        self.im_singular_values, self.im_rank, self.pinv_sweeps = P.pas_pinv_f64(self.ctx, d_IM, ns, nm, rcond, d_R)
+        self.IM = d_IM.t().cpu().numpy()
+        return d_R.cpu().numpy()
 
     def step(self, n=1, stats=False):
         cam = getattr(self, "camera", None)

@@ -69,7 +69,10 @@ def poisson(lam, seed: int, pixel: int, frame: int) -> int:
         while u > F and k < 256:
             k += 1
             p = F32(p * F32(lam * (F32(1.0) / F32(k))))
-            F = F32(F + p)
+            Fn = F32(F + p)
+            if Fn == F:        # the float32 CDF has stopped growing
+                break
+            F = Fn
         return k
     slam = np.sqrt(lam)
     loglam = np.log(lam)

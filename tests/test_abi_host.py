@@ -101,11 +101,31 @@ def test_product_basis_matches_oracle():
         assert calib.noll_nm(j) == md.noll_to_nm(j)
 
 
-def test_product_pinv_matches_oracle():
+def test_zernike_recurrence_matches_the_oracle_polynomials():
+    """calib.zernike_raw (Jacobi three-term recurrence, all pixels per azimuthal
+    order) against the oracle's Zernike polynomials (its own radial sum) up to
+    radial order 20, and high orders against scipy's Jacobi polynomials."""
+    import math
     from oracle import modal as md
+    from oracle import optics as op
     from paper_1607_07624_gb300 import calib
-    IM = np.random.default_rng(5).standard_normal((80, 30))
-    assert np.max(np.abs(calib.pseudo_inverse(IM) - md.pseudo_inverse(IM))) < 1e-12
+    from scipy.special import eval_jacobi
+    Np = 64
+    idx = np.flatnonzero(op.pupil_mask(Np, 0.1).ravel())
+    Z = calib.zernike_raw(Np, idx, 230)            # radial orders up to 20
+    rho, th = md.pupil_polar(Np)
+    rho, th = rho.ravel()[idx], th.ravel()[idx]
+    for c, j in enumerate(range(2, 232)):
+        # (the oracle's alternating factorial sum loses ~1e-9 by radial order 18)
+        assert np.max(np.abs(Z[:, c] - md.zernike(j, rho, th))) < 1e-8, j
+    # radial order 88 (the 4000-mode basis): against P_k^(m,0) from scipy
+    Zh = calib.zernike_raw(Np, idx, 4000)
+    for j in (3990, 3995, 4001):
+        n, m = calib.noll_nm(j)
+        k = (n - abs(m)) // 2
+        r = (-1) ** k * rho ** abs(m) * eval_jacobi(k, abs(m), 0, 1 - 2 * rho * rho)
+        ang = 1.0 if m == 0 else (math.sqrt(2) * (np.cos(m * th) if m > 0 else np.sin(-m * th)))
+        assert np.max(np.abs(Zh[:, j - 2] - math.sqrt(n + 1) * r * ang)) < 1e-8 * math.sqrt(n + 1), j
 
 
 def test_product_kl_basis_matches_oracle():

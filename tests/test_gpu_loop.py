@@ -59,9 +59,12 @@ def test_closed_loop_wfe_matches_oracle(cfg1_setup):
         burn = n // 5
         assert abs(wg[burn:].mean() - wo[burn:].mean()) <= 0.5
         # the loop corrects: the residual falls well below the open-loop first step.
-        # (It does not settle: with 12 modulation points at 3 lambda/D the pyramid's
-        # Jacobian around the corrected operating point has one slightly negative
-        # mode, so the pure integrator drifts afterwards, in the oracle as here.)
+        # It does not settle at this workload's 12 modulation points: oracle-only runs
+        # (the same loop with 24 points, or with the pupil images apart on a 3 Np or
+        # 4 Np grid) settle near 0.2-0.25 of the first step, while 12 points on a
+        # circle of 3 lambda/D (1.6 lambda/D apart) drift up to ~1 um after step 20 in
+        # the oracle as here; test_loop_settles_with_24_modulation_points checks the
+        # settling case.
         assert wg[10:30].min() < 0.4 * wg[0]
     finally:
         sysg.close()
@@ -99,14 +102,18 @@ def test_graph_and_eager_steps_are_identical_and_resume_is_exact(cfg1_setup):
 
 
 def test_delay_two_and_noisy_loop_run(cfg1_setup):
+    """Delay 2 with magnitude-10 photon and read noise, on the 64 px optics with 24
+    modulation points (the setting whose loop settles; calibrated on the GPU): the
+    loop holds its correction (oracle-only runs of the same setting settle near a
+    quarter of the first step)."""
     from paper_1607_07624_gb300.system import SCAOSystem
     cfg, screens, M, valid, sn, IM, R = cfg1_setup
-    c = with_(cfg, magnitude=10.0, read_noise_e=0.5)
-    s = SCAOSystem(c, screens=screens.astype(np.float32), basis=M, R=R, delay=2, wfe_history=100)
+    c = with_(cfg, K=24, magnitude=10.0, read_noise_e=0.5)
+    s = SCAOSystem(c, screens=screens.astype(np.float32), basis=M, delay=2, wfe_history=100)
     try:
         s.step(100)
         w = s.wfe_nm(100)
-        assert np.all(np.isfinite(w)) and w[10:40].min() < 0.5 * w[0]
+        assert np.all(np.isfinite(w)) and w[50:].mean() < 0.6 * w[0]
         # delay 2: the first two steps see no correction
         assert abs(w[1] - w[0]) < 0.05 * w[0]
     finally:
@@ -283,5 +290,76 @@ def test_extended_source_loop_matches_oracle(cfg1_setup):
         wg = s.wfe_nm(n)
         assert np.max(np.abs(wg - wo)) <= 2.0, np.max(np.abs(wg - wo))
         assert wg[10:].min() < 0.5 * wg[0]
+    finally:
+        s.close()
+
+
+def test_loop_settles_with_24_modulation_points():
+    """The 64 px workload with 24 modulation points instead of 12 (0.8 lambda/D apart
+    on the 3 lambda/D circle): the GPU loop, calibrated on the GPU, follows the
+    oracle loop calibrated by the oracle (per-step WFE within 2 nm) and settles, as
+    oracle-only runs predict: the mean residual after a 20 % burn-in below half the
+    open-loop first step, and no drift over the last 50 steps."""
+    from oracle import atmosphere as at
+    from oracle import control as ct
+    from oracle import modal as md
+    from oracle import optics as op
+    from paper_1607_07624_gb300.system import SCAOSystem
+    cfg = with_(get_config("scao_8m_64px"), K=24)
+    n = cfg.n_steps
+    screens = at.layer_screens_nm(cfg, [screen_white_noise(cfg.S, s) for s in layer_seeds(cfg.seed, len(cfg.layers))])
+    M = md.modal_basis(cfg.Np, cfg.obs, cfg.n_modes)
+    valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
+    mask = op.pupil_mask(cfg.Np, cfg.obs)
+    _, sn = op.pwfs_measure(np.zeros((cfg.Np, cfg.Np)), cfg, valid)
+    IM = md.interaction_matrix(lambda o: op.pwfs_measure(o, cfg, valid, sn)[1], M, mask, cfg.pushpull_nm)
+    wo = ct.closed_loop(cfg, screens, M, md.pseudo_inverse(IM), sn, valid, n)["wfe"]
+    sysg = SCAOSystem(cfg, screens=screens.astype(np.float32), basis=M, wfe_history=n)
+    try:
+        sysg.step(n)
+        wg = sysg.wfe_nm(n)
+        assert np.max(np.abs(wg - wo)) <= 2.0, np.max(np.abs(wg - wo))
+        burn = n // 5
+        assert wg[burn:].mean() < 0.5 * wg[0]
+        assert wg[-50:].mean() < 1.25 * wg[burn:burn + 50].mean()
+        assert wo[burn:].mean() < 0.5 * wo[0]
+    finally:
+        sysg.close()
+
+
+@pytest.mark.parametrize("noisy", [False, True], ids=["noiseless", "mag10"])
+def test_lbt_loop_matches_the_oracle_loop(noisy):
+    """The LBT-class workload's loop as the bench runs it (240 px, 3 layers, the
+    product's own 400-mode KL basis and GPU calibration), 20 steps, against the
+    oracle's closed loop fed the same screens, basis and reconstructor (and, with
+    magnitude-10 noise, the kernel model's draws, so both loops see the same counts):
+    per-step WFE within 2 nm, final commands within 1 % of the largest."""
+    import kernel_noise_model as km  # the kernel's float32 draws (not the oracle)
+    from oracle import control as ct
+    from oracle import noise as nz
+    from oracle import optics as op
+    from paper_1607_07624_gb300.system import SCAOSystem
+    cfg = get_config("scao_lbt_240px")
+    if not noisy:
+        cfg = with_(cfg, magnitude=None, read_noise_e=0.0)
+    n = 20
+    s = SCAOSystem(cfg, wfe_history=n)
+    try:
+        M = s.basis.astype(np.float64)
+        R = s.R.astype(np.float64)
+        screens = s.d_screens.cpu().numpy().astype(np.float64)
+        valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
+        assert np.array_equal(valid, s.valid)
+        _, sn = op.pwfs_measure(np.zeros((cfg.Np, cfg.Np)), cfg, valid)
+        noise = None
+        if noisy:
+            photons, npup = nz.photons_per_frame(cfg), int(op.pupil_mask(cfg.Np, cfg.obs).sum())
+            noise = lambda fr, t: km.apply_noise(fr, photons, npup, cfg.read_noise_e, cfg.seed, t)
+        ref = ct.closed_loop(cfg, screens, M, R, sn, valid, n, noise=noise, record=True)
+        s.step(n)
+        wg = s.wfe_nm(n)
+        assert np.max(np.abs(wg - ref["wfe"])) <= 2.0, np.max(np.abs(wg - ref["wfe"]))
+        cmd = s.loop_cmd.cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(cmd - ref["cmd"])) <= 0.01 * np.max(np.abs(ref["cmd"]))
     finally:
         s.close()
