@@ -571,6 +571,17 @@ pas_status pas_fp32_fma_probe(void* cuda_stream, float* d_sink, int32_t n_blocks
 pas_status pas_gemm_bf16(pas_ctx_t ctx, int32_t M, int32_t N, int32_t K, const uint16_t* d_A,
                          int32_t lda, const uint16_t* d_B, int32_t ldb, float* d_C, int32_t ldc,
                          int32_t tile_n, uint32_t* d_err);
+/* pas_gemm_bf16 whose pipeline waits (a TMA slot to fill or drain, the products to
+ * complete) each give up after wait_limit tries of mbarrier.try_wait (0: at once).
+ * A wait that gives up sets bits in *d_err (1 producer, 2 product issue,
+ * 4 epilogue; 8 if the unwinding itself timed out) and the CTA unwinds: it waits,
+ * with the long default bound, for its own copies in flight and the products it
+ * issued, frees its tensor memory and returns; C is then unspecified. The failure
+ * path of the bounded waits, exercised by the tests; pas_gemm_bf16 uses the default
+ * bound (2^22 tries, seconds). */
+pas_status pas_gemm_bf16_waits(pas_ctx_t ctx, int32_t M, int32_t N, int32_t K, const uint16_t* d_A,
+                               int32_t lda, const uint16_t* d_B, int32_t ldb, float* d_C, int32_t ldc,
+                               int32_t tile_n, uint32_t wait_limit, uint32_t* d_err);
 
 #ifdef __cplusplus
 }

@@ -11,8 +11,10 @@
 //                  and hand 16-column pieces to the epilogue functor.
 // Out-of-range rows and columns of the operands are zero-filled by the TMA unit,
 // so M, N and K need no padding; the epilogue skips rows >= M and columns >= N.
-// Every wait is bounded: a timeout sets a bit in *err, the CTA waits (bounded)
-// for its own outstanding copies, frees its tensor memory and returns.
+// Every wait is bounded: a pipeline wait gives up after wait_limit tries, sets a bit
+// in *err and the CTA unwinds: it waits (bounded by tc::WAIT_LIMIT, far longer than
+// any copy or product takes) for its own outstanding TMA copies and for the products
+// it issued, so that nothing is in flight when it frees its tensor memory and exits.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -40,7 +42,7 @@ struct GemmCfg {
 template <int BN, int STAGES, class Epi>
 __global__ void __launch_bounds__(128, 1)
     gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
-                        int N, int K, Epi epi, unsigned int* err) {
+                        int N, int K, Epi epi, unsigned int* err, uint32_t wait_limit) {
   using C = GemmCfg<BN, STAGES>;
   extern __shared__ uint8_t gemm_dsm[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gemm_dsm) + 1023) & ~uintptr_t(1023));
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0 && lane == 0) {
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES, round = kb / STAGES;
-      if (round > 0 && !tc::mbar_wait(&empty[s], (uint32_t)(round - 1) & 1u)) {
+      if (round > 0 && !tc::mbar_wait(&empty[s], (uint32_t)(round - 1) & 1u, wait_limit)) {
         atomicOr(err, GEMM_ERR_PRODUCER);
         abort_flag = 1;
         break;
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(128, 1)
     constexpr uint32_t idesc = tc::idesc_bf16_f32(128, BN);
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
-      if (!tc::mbar_wait(&full[s], (uint32_t)(kb / STAGES) & 1u)) {
+      if (!tc::mbar_wait(&full[s], (uint32_t)(kb / STAGES) & 1u, wait_limit)) {
         atomicOr(err, GEMM_ERR_MMA);
         abort_flag = 1;
         break;
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(128, 1)
   }
   __syncwarp();
 
-  if (!tc::mbar_wait(&done, 0)) {
+  if (!tc::mbar_wait(&done, 0, wait_limit)) {
     atomicOr(err, GEMM_ERR_EPILOGUE);
     abort_flag = 1;
   }
@@ -146,10 +148,13 @@ __global__ void __launch_bounds__(128, 1)
     }
   }
   if (abort_flag && warp == 0 && lane == 0) {
-    // copies still in flight land before the CTA's shared memory is released
+    // copies still in flight land before the CTA's shared memory is released, and
+    // the products issued complete before their tensor memory is freed (the MMA
+    // thread commits `done` after its loop, aborted or not)
     for (int s = 0; s < STAGES; ++s)
       if (last_round[s] >= 0 && !tc::mbar_wait(&full[s], (uint32_t)last_round[s] & 1u))
         atomicOr(err, GEMM_ERR_DRAIN);
+    if (!tc::mbar_wait(&done, 0)) atomicOr(err, GEMM_ERR_DRAIN);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -182,24 +187,27 @@ bool gemm_prepare(GemmOp* op, const __nv_bfloat16* A, int lda, const __nv_bfloat
 // pdl: launch with programmatic stream serialization (the kernel waits for its
 // predecessor after its set-up).
 template <int BN, int STAGES, class Epi>
-cudaError_t gemm_launch_bn(const GemmOp& op, const Epi& epi, cudaStream_t st, unsigned* err, bool pdl) {
+cudaError_t gemm_launch_bn(const GemmOp& op, const Epi& epi, cudaStream_t st, unsigned* err, bool pdl,
+                           uint32_t wait_limit) {
   using C = GemmCfg<BN, STAGES>;
   auto kern = gemm_bf16_tc_kernel<BN, STAGES, Epi>;
   cudaError_t e = raise_dyn_smem((const void*)kern, C::SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid((op.N + BN - 1) / BN, (op.M + 127) / 128);
-  return launch_k(kern, grid, dim3(128), C::SMEM, st, pdl, op.a, op.b, op.M, op.N, op.K, epi, err);
+  return launch_k(kern, grid, dim3(128), C::SMEM, st, pdl, op.a, op.b, op.M, op.N, op.K, epi, err, wait_limit);
 }
 
+// wait_limit: tries of each pipeline wait before it gives up (tc::WAIT_LIMIT by default).
 template <class Epi>
-cudaError_t gemm_launch(const GemmOp& op, const Epi& epi, cudaStream_t st, unsigned* err, bool pdl = false) {
+cudaError_t gemm_launch(const GemmOp& op, const Epi& epi, cudaStream_t st, unsigned* err, bool pdl = false,
+                        uint32_t wait_limit = tc::WAIT_LIMIT) {
   switch (op.bn) {
     case 64:
-      return gemm_launch_bn<64, 6>(op, epi, st, err, pdl);
+      return gemm_launch_bn<64, 6>(op, epi, st, err, pdl, wait_limit);
     case 256:
-      return gemm_launch_bn<256, 4>(op, epi, st, err, pdl);
+      return gemm_launch_bn<256, 4>(op, epi, st, err, pdl, wait_limit);
     default:
-      return gemm_launch_bn<128, 5>(op, epi, st, err, pdl);
+      return gemm_launch_bn<128, 5>(op, epi, st, err, pdl, wait_limit);
   }
 }
 

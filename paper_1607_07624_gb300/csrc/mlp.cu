@@ -979,6 +979,12 @@ pas_status pas_mlp_pair(pas_pyr_t pyr, pas_dm_t dm, const float* d_opd, float am
 pas_status pas_gemm_bf16(pas_ctx_t ctx, int32_t M, int32_t N, int32_t K, const uint16_t* d_A, int32_t lda,
                          const uint16_t* d_B, int32_t ldb, float* d_C, int32_t ldc, int32_t tile_n,
                          uint32_t* d_err) {
+  return pas_gemm_bf16_waits(ctx, M, N, K, d_A, lda, d_B, ldb, d_C, ldc, tile_n, pas::tc::WAIT_LIMIT, d_err);
+}
+
+pas_status pas_gemm_bf16_waits(pas_ctx_t ctx, int32_t M, int32_t N, int32_t K, const uint16_t* d_A, int32_t lda,
+                               const uint16_t* d_B, int32_t ldb, float* d_C, int32_t ldc, int32_t tile_n,
+                               uint32_t wait_limit, uint32_t* d_err) {
   if (!ctx || !d_A || !d_B || !d_C || !d_err) return pas::set_global_error(PAS_EINVAL, "pas_gemm_bf16: NULL argument");
   PAS_CHECK_ARG(ctx, M >= 1 && N >= 1 && K >= 1 && lda >= K && ldb >= K && ldc >= N,
                 "pas_gemm_bf16: M, N, K >= 1, lda, ldb >= K, ldc >= N");
@@ -995,7 +1001,7 @@ pas_status pas_gemm_bf16(pas_ctx_t ctx, int32_t M, int32_t N, int32_t K, const u
       return pas::set_error(ctx, PAS_EINVAL, "pas_gemm_bf16: tensor map rejected");
   }
   pas::EpiF32 ep{d_C, ldc, N};
-  cudaError_t e = pas::gemm_launch(op, ep, ctx->stream, d_err);
+  cudaError_t e = pas::gemm_launch(op, ep, ctx->stream, d_err, false, wait_limit);
   if (e != cudaSuccess) return pas::set_error(ctx, PAS_ECUDA, "pas_gemm_bf16: %s", cudaGetErrorString(e));
   return PAS_OK;
 }

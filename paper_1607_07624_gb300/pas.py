@@ -123,6 +123,7 @@ _SIGS = {
     "pas_mlp_pair": (C.c_int, [vp, vp, vp, C.c_float, vp, vp, vp]),
     "pas_loop_set_mlp": (C.c_int, [vp, vp]),
     "pas_gemm_bf16": (C.c_int, [vp, i32, i32, i32, vp, i32, vp, i32, vp, i32, i32, vp]),
+    "pas_gemm_bf16_waits": (C.c_int, [vp, i32, i32, i32, vp, i32, vp, i32, vp, i32, i32, C.c_uint32, vp]),
     "pas_batch_create": (C.c_int, [vp, vp, i32, P(vp)]),
     "pas_batch_step": (C.c_int, [vp, i32]),
     "pas_batch_size": (i32, [vp]),
@@ -567,6 +568,13 @@ def pas_loop_set_mlp(loop, ctx, mlp):
 def pas_gemm_bf16(ctx, M, N, K, d_A, lda, d_B, ldb, d_C, ldc, d_err, tile_n=0):
     _check(_lib.pas_gemm_bf16(ctx, int(M), int(N), int(K), _ptr(d_A), int(lda), _ptr(d_B), int(ldb), _ptr(d_C),
                               int(ldc), int(tile_n), _ptr(d_err)), ctx)
+
+
+def pas_gemm_bf16_waits(ctx, M, N, K, d_A, lda, d_B, ldb, d_C, ldc, d_err, wait_limit, tile_n=0):
+    """pas_gemm_bf16 whose pipeline waits give up after wait_limit tries (0: at once);
+    the bits of d_err (uint32 CUDA tensor) say which waits gave up."""
+    _check(_lib.pas_gemm_bf16_waits(ctx, int(M), int(N), int(K), _ptr(d_A), int(lda), _ptr(d_B), int(ldb), _ptr(d_C),
+                                    int(ldc), int(tile_n), int(wait_limit), _ptr(d_err)), ctx)
 
 
 def pas_batch_create(ctx, loops):

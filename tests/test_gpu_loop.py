@@ -360,6 +360,7 @@ def test_lbt_loop_matches_the_oracle_loop(noisy):
         wg = s.wfe_nm(n)
         assert np.max(np.abs(wg - ref["wfe"])) <= 2.0, np.max(np.abs(wg - ref["wfe"]))
         cmd = s.loop_cmd.cpu().numpy().astype(np.float64)
-        assert np.max(np.abs(cmd - ref["cmd"])) <= 0.01 * np.max(np.abs(ref["cmd"]))
+        last = ref["cmd"][-1]                  # the oracle's command after step n - 1
+        assert np.max(np.abs(cmd - last)) <= 0.01 * np.max(np.abs(last))
     finally:
         s.close()

@@ -90,6 +90,34 @@ def test_gemm_bf16_matches_fp64(env, M, N, K, tile):
     assert np.all(np.abs(got - ref) <= 1e-5 * (np.abs(a) @ np.abs(b).T) + 1e-30)
 
 
+def test_gemm_wait_that_gives_up_unwinds_and_reports(env):
+    """Every pipeline wait of the tensor-core GEMM made to give up at once (wait
+    limit 0, a barrier no copy has reached yet): the product-issue and epilogue bits
+    are set, the unwinding (copies in flight drained, products completed, tensor
+    memory freed) finishes within its own bound, and the context stays usable: the
+    same GEMM with the default bound is then exact."""
+    torch, pas, ctx = env
+    g = rng(77)
+    M, N, K = 256, 384, 1024
+    A = torch.as_tensor(g.standard_normal((M, K)).astype(np.float32)).to(torch.bfloat16).cuda()
+    B = torch.as_tensor(g.standard_normal((N, K)).astype(np.float32)).to(torch.bfloat16).cuda()
+    C = torch.zeros(M, N, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    pas.pas_gemm_bf16_waits(ctx, M, N, K, A, K, B, K, C, N, err, 0)
+    torch.cuda.synchronize()
+    e = int(err.item())
+    assert e & 2 and e & 4, e         # product issue and epilogue gave up
+    assert not e & 8, e               # the unwinding completed
+    err.zero_()
+    C.fill_(float("nan"))
+    pas.pas_gemm_bf16(ctx, M, N, K, A, K, B, K, C, N, err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    a = A.float().cpu().numpy().astype(np.float64)
+    b = B.float().cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(C.cpu().numpy() - a @ b.T) <= 1e-5 * (np.abs(a) @ np.abs(b).T))
+
+
 def test_gemm_rejects_unaligned_leading_dimension(env):
     torch, pas, ctx = env
     A = torch.zeros(128, 100, dtype=torch.bfloat16, device="cuda")

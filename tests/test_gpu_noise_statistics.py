@@ -80,7 +80,10 @@ def test_photon_noise_law_matches_fp64_poisson():
     assert np.max(np.abs(z_mean)) < 6.0, np.max(np.abs(z_mean))
     assert np.max(np.abs(z_var)) < 6.0, np.max(np.abs(z_var))
     for level in LEVELS[1:]:
-        stat, p, nb = _chi2_against_pmf(x[:, lam == level].ravel(), level)
+        lv = float(np.float32(level))            # the float32 value the kernel received
+        sel = lam == lv
+        assert sel.sum() == 512
+        stat, p, nb = _chi2_against_pmf(x[:, sel].ravel(), lv)
         assert p > 1e-6, (level, stat, nb, p)
 
 
