@@ -277,6 +277,11 @@ pas_status pas_recon_create(pas_ctx_t ctx, const float* h_R, int32_t n_modes, in
                             pas_precision prec, pas_recon_t* out);
 /* d_slopes: device float32 [n_slopes]; d_dmodes: device float32 [n_modes] out. */
 pas_status pas_recon_apply(pas_recon_t rec, const float* d_slopes, float* d_dmodes);
+/* Synchronous check of the reconstructor's bounded waits (long slope vectors stream
+ * R through bulk copies whose waits give up after a bound): PAS_ETIMEOUT if one gave
+ * up since the last check (the flag is then cleared); h_fault (optional) receives
+ * the flag bits. */
+pas_status pas_recon_check(pas_recon_t rec, uint32_t* h_fault);
 void pas_recon_destroy(pas_recon_t rec);
 
 /* ------------------------------------------------------------- modal DM

@@ -4,8 +4,9 @@
 //
 // The matrix-vector product reads every element of R once per step: it is bound
 // by memory bandwidth, so it runs on CUDA cores with 16-byte loads: four warps per
-// mode row and the slope vector staged in shared memory for short vectors, two warps
-// per row and slopes read through L1 for long ones (recon_stream_kernel). PAS_BF16 stores R as
+// mode row and the slope vector staged in shared memory for short vectors, one warp
+// per row fed by bulk copies and slopes read through L1 for long ones
+// (recon_bulk_kernel). PAS_BF16 stores R as
 // bfloat16 scaled per row (row max |R| = 1) with float32 accumulation.
 #include <cuda_bf16.h>
 
@@ -141,21 +142,52 @@ __global__ void __launch_bounds__(256) recon_kernel(ReconArgs a) {
   }
 }
 
-// The same product for long slope vectors (n_s >= RECON_STREAM_MIN_NS): staging the
-// whole vector in shared memory per CTA would move as many bytes from L2 as R itself
-// and cap the CTAs per SM, so here the slopes are read through L1 (every CTA of an SM
-// shares one copy) and each warp keeps RECON_STREAM_U 16-byte chunks of R in flight.
-// CTA: 256 threads = 4 rows x RECON_STREAM_SPLIT (2) warps; the first chunks of R
-// are loaded before the programmatic wait (R is constant). Slopes must be 16-byte
-// aligned (checked by the launcher).
-constexpr int RECON_STREAM_SPLIT = 2;
-constexpr int RECON_STREAM_ROWS = 8 / RECON_STREAM_SPLIT;
-constexpr int RECON_STREAM_U = 8;
-constexpr int RECON_STREAM_MIN_NS = 4096;
+// The same product for long slope vectors (n_s >= RECON_BULK_MIN_NS): each warp owns
+// one mode row and streams it through a ring of RB_NS shared-memory slots filled by
+// 1-D bulk copies (cp.async.bulk, the TMA engine, completion on one mbarrier per slot),
+// so the bytes in flight do not depend on registers; the slopes are read through L1
+// (every CTA of an SM shares one copy). The first slots are requested before the
+// programmatic wait (R is constant). Every wait is bounded: a slot that does not fill
+// sets *err, and the warp waits (with the long bound) for the copies it still has in
+// flight before it leaves.
+constexpr int RB_WARPS = 4;            // rows (warps) per CTA
+constexpr int RB_NS = 4;               // slots per warp
+constexpr int RB_CH = 2048;            // bytes per slot (a multiple of 512: 16 bytes per lane per step)
+constexpr int RECON_BULK_MIN_NS = 4096;
+constexpr size_t RB_SMEM = (size_t)RB_WARPS * RB_NS * RB_CH;
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Slopes of the 16-byte chunk c of an R row (8 bf16 or 4 float32 columns) from
+// global memory through L1; columns at or beyond n_s (row padding) read as 0.
 template <bool BF16>
 __device__ __forceinline__ void slope_chunk(const float* s, int n_s, int c, float4* lo, float4* hi) {
-  constexpr int W = BF16 ? 8 : 4;  // slopes per 16-byte chunk of R
+  constexpr int W = BF16 ? 8 : 4;
   const int j0 = c * W;
   if (j0 + W <= n_s) {
     *lo = __ldg(reinterpret_cast<const float4*>(s + j0));
@@ -169,31 +201,37 @@ __device__ __forceinline__ void slope_chunk(const float* s, int n_s, int c, floa
   }
 }
 
+constexpr uint32_t RB_WAIT_LIMIT = 1u << 22;  // tries of one wait (seconds, far beyond a copy)
+
 template <bool BF16>
-__global__ void __launch_bounds__(256) recon_stream_kernel(ReconArgs a) {
-  using Chunk = typename std::conditional<BF16, uint4, float4>::type;
-  constexpr int STEP = RECON_STREAM_SPLIT * 32;
-  constexpr int U = RECON_STREAM_U;
-  __shared__ float part[8];
+__global__ void __launch_bounds__(RB_WARPS * 32) recon_bulk_kernel(ReconArgs a) {
+  extern __shared__ __align__(128) unsigned char rb_ring[];  // [warp][slot][RB_CH]
+  __shared__ __align__(8) uint64_t bar[RB_WARPS][RB_NS];
   __shared__ bool is_last;
   pdl_trigger();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row_local = warp / RECON_STREAM_SPLIT, part_idx = warp % RECON_STREAM_SPLIT;
-  const int m = blockIdx.x * RECON_STREAM_ROWS + row_local;
-  const int c0 = part_idx * 32 + lane;
-  const int nc = a.n_s_pad / (BF16 ? 8 : 4);
-  const Chunk* row = nullptr;
-  if (m < a.n_m) {
-    if constexpr (BF16) row = reinterpret_cast<const uint4*>(a.Rb + (size_t)m * a.n_s_pad);
-    else row = reinterpret_cast<const float4*>(a.R + (size_t)m * a.n_s_pad);
+  const int m = blockIdx.x * RB_WARPS + warp;
+  constexpr int ES = BF16 ? 2 : 4;  // bytes per element of R
+  const int row_bytes = a.n_s_pad * ES;
+  const int nch = (row_bytes + RB_CH - 1) / RB_CH;
+  const char* src = nullptr;
+  if (m < a.n_m) src = (BF16 ? reinterpret_cast<const char*>(a.Rb) : reinterpret_cast<const char*>(a.R)) +
+                       (size_t)m * row_bytes;
+  unsigned char* ring = rb_ring + (size_t)warp * RB_NS * RB_CH;
+  if (lane == 0) {
+    for (int s = 0; s < RB_NS; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[warp][s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  Chunk buf[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int c = c0 + u * STEP;
-    buf[u] = (row && c < nc) ? __ldcs(row + c) : Chunk{};
-  }
-  const bool writer = part_idx == 0 && lane == 0 && m < a.n_m;
+  __syncwarp();
+  auto issue = [&](int c) {
+    const int bytes = min(RB_CH, row_bytes - c * RB_CH);
+    bulk_copy_g2s(ring + (size_t)(c % RB_NS) * RB_CH, src + (size_t)c * RB_CH, (uint32_t)bytes,
+                  &bar[warp][c % RB_NS]);
+  };
+  if (lane == 0 && src)
+    for (int c = 0; c < min(RB_NS, nch); ++c) issue(c);
+  const bool writer = lane == 0 && m < a.n_m;
   long long t_step = 0;
   float prev = 0.f;
   bool hold = false;
@@ -204,50 +242,60 @@ __global__ void __launch_bounds__(256) recon_stream_kernel(ReconArgs a) {
   }
   pdl_wait();
   float acc = 0.f;
-  if (row) {
-    auto fma_chunk = [&](const Chunk& u, int c) {
-      float4 lo, hi;
-      slope_chunk<BF16>(a.s, a.n_s, c, &lo, &hi);
-      if constexpr (BF16) {
-        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
-        const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
-        const float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
-        acc = dot4(make_float4(f0.x, f0.y, f1.x, f1.y), lo, acc);
-        acc = dot4(make_float4(f2.x, f2.y, f3.x, f3.y), hi, acc);
-      } else {
-        acc = dot4(u, lo, acc);
+  int c = 0;
+  bool ok = true;
+  if (src) {
+    for (; c < nch; ++c) {
+      const int s = c % RB_NS;
+      // every lane observes the slot's phase; the decision to go on is the warp's
+      const bool got = bar_wait(&bar[warp][s], (uint32_t)(c / RB_NS) & 1u, RB_WAIT_LIMIT);
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
       }
-    };
-    for (int cb = c0; cb < nc; cb += U * STEP) {
-      // the batch in buf is being consumed; the next one is requested first
-      Chunk nxt[U];
+      const int bytes = min(RB_CH, row_bytes - c * RB_CH);
+      const unsigned char* slot = ring + (size_t)s * RB_CH;
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int c = cb + (U + u) * STEP;
-        nxt[u] = c < nc ? __ldcs(row + c) : Chunk{};
+      for (int q = 0; q < RB_CH / 512; ++q) {
+        const int off = q * 512 + lane * 16;
+        if (off < bytes) {
+          const uint4 u = *reinterpret_cast<const uint4*>(slot + off);
+          const int chunk = (c * RB_CH + off) / 16;  // index of this 16-byte chunk in the row
+          float4 lo, hi;
+          slope_chunk<BF16>(a.s, a.n_s, chunk, &lo, &hi);
+          if constexpr (BF16) {
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+            const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
+            const float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
+            acc = dot4(make_float4(f0.x, f0.y, f1.x, f1.y), lo, acc);
+            acc = dot4(make_float4(f2.x, f2.y, f3.x, f3.y), hi, acc);
+          } else {
+            acc = dot4(*reinterpret_cast<const float4*>(&u), lo, acc);
+          }
+        }
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int c = cb + u * STEP;
-        if (c < nc) fma_chunk(buf[u], c);
+      __syncwarp();  // every lane has read slot s
+      if (lane == 0 && c + RB_NS < nch) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads before the copy's writes
+        issue(c + RB_NS);
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u) buf[u] = nxt[u];
     }
   }
+  if (!ok && lane == 0) {
+    // a slot did not fill: record it, then let the copies still in flight land
+    atomicOr(a.err, 1u);
+    for (int d = c; d < min(nch, c + RB_NS); ++d)
+      if (!bar_wait(&bar[warp][d % RB_NS], (uint32_t)(d / RB_NS) & 1u, RB_WAIT_LIMIT)) atomicOr(a.err, 2u);
+  }
+  __syncwarp();
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if (lane == 0) part[warp] = acc;
-  __syncthreads();
   if (writer) {
-    float tot = 0.f;
-#pragma unroll
-    for (int q = 0; q < RECON_STREAM_SPLIT; ++q) tot += part[warp + q];
-    const float dm = hold ? 0.f : (BF16 ? tot * a.scale[m] : tot);
+    const float dm = hold ? 0.f : (BF16 ? acc * a.scale[m] : acc);
     if (a.dmodes) a.dmodes[m] = dm;
     if (a.ring) {
-      const float c = hold ? prev : fmaf(a.gain ? a.gain[m] : 1.0f, dm, prev);
-      a.ring[(size_t)(t_step % a.delay) * a.n_m + m] = c;
-      if (a.cmd_last) a.cmd_last[m] = c;
+      const float cnew = hold ? prev : fmaf(a.gain ? a.gain[m] : 1.0f, dm, prev);
+      a.ring[(size_t)(t_step % a.delay) * a.n_m + m] = cnew;
+      if (a.cmd_last) a.cmd_last[m] = cnew;
     }
   }
   if (a.step_inc) {
@@ -280,11 +328,12 @@ pas_status recon_launch(pas_recon_t r, ReconArgs a, cudaStream_t st, bool pdl) {
   a.n_s = r->n_slopes;
   a.n_s_pad = r->n_s_pad;
   a.done = r->d_done;
+  a.err = r->d_err;
   cudaError_t e;
-  if (r->n_slopes >= RECON_STREAM_MIN_NS && (reinterpret_cast<uintptr_t>(a.s) & 15u) == 0) {
-    const int grid = (r->n_modes + RECON_STREAM_ROWS - 1) / RECON_STREAM_ROWS;
-    e = r->prec == PAS_BF16 ? launch_k(recon_stream_kernel<true>, dim3(grid), dim3(256), 0, st, pdl, a)
-                            : launch_k(recon_stream_kernel<false>, dim3(grid), dim3(256), 0, st, pdl, a);
+  if (r->n_slopes >= RECON_BULK_MIN_NS && (reinterpret_cast<uintptr_t>(a.s) & 15u) == 0) {
+    const int grid = (r->n_modes + RB_WARPS - 1) / RB_WARPS;
+    e = r->prec == PAS_BF16 ? launch_k(recon_bulk_kernel<true>, dim3(grid), dim3(RB_WARPS * 32), RB_SMEM, st, pdl, a)
+                            : launch_k(recon_bulk_kernel<false>, dim3(grid), dim3(RB_WARPS * 32), RB_SMEM, st, pdl, a);
   } else {
     const size_t smem = sizeof(float) * (size_t)r->n_s_pad;
     const int grid = (r->n_modes + RECON_ROWS - 1) / RECON_ROWS;
@@ -305,6 +354,7 @@ void pas_recon_destroy(pas_recon_t r) {
   pas::dev_free(r->d_Rb);
   pas::dev_free(r->d_scale);
   pas::dev_free(r->d_done);
+  pas::dev_free(r->d_err);
   delete r;
 }
 
@@ -350,7 +400,12 @@ pas_status pas_recon_create(pas_ctx_t ctx, const float* h_R, int32_t n_modes, in
       e = pas::raise_dyn_smem((const void*)pas::recon_kernel<true>, smem);
   }
   if (st == PAS_OK) st = pas::dev_alloc(ctx, (void**)&r->d_done, sizeof(unsigned int));
+  if (st == PAS_OK) st = pas::dev_alloc(ctx, (void**)&r->d_err, sizeof(unsigned int));
   if (st == PAS_OK && e == cudaSuccess) e = cudaMemset(r->d_done, 0, sizeof(unsigned int));
+  if (st == PAS_OK && e == cudaSuccess) e = cudaMemset(r->d_err, 0, sizeof(unsigned int));
+  if (st == PAS_OK && e == cudaSuccess)
+    e = prec == PAS_BF16 ? pas::raise_dyn_smem((const void*)pas::recon_bulk_kernel<true>, pas::RB_SMEM)
+                         : pas::raise_dyn_smem((const void*)pas::recon_bulk_kernel<false>, pas::RB_SMEM);
   if (st != PAS_OK) {
     pas_recon_destroy(r);
     return st;
@@ -360,6 +415,18 @@ pas_status pas_recon_create(pas_ctx_t ctx, const float* h_R, int32_t n_modes, in
     return pas::set_error(ctx, PAS_ECUDA, "pas_recon_create: %s", cudaGetErrorString(e));
   }
   *out = r;
+  return PAS_OK;
+}
+
+pas_status pas_recon_check(pas_recon_t r, uint32_t* h_fault) {
+  if (!r) return pas::set_global_error(PAS_EINVAL, "pas_recon_check: NULL argument");
+  unsigned int f = 0;
+  PAS_CUDA_TRY(r->ctx, cudaMemcpy(&f, r->d_err, sizeof(f), cudaMemcpyDeviceToHost));
+  if (h_fault) *h_fault = f;
+  if (f) {
+    PAS_CUDA_TRY(r->ctx, cudaMemset(r->d_err, 0, sizeof(unsigned int)));
+    return pas::set_error(r->ctx, PAS_ETIMEOUT, "reconstructor: a bulk-copy wait gave up (code %u)", f);
+  }
   return PAS_OK;
 }
 

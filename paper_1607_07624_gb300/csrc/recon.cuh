@@ -22,6 +22,7 @@ struct ReconArgs {
   long long* step_inc = nullptr;        // advanced by one after the last CTA (or null)
   unsigned int* done = nullptr;         // CTA completion counter
   int n_int = 1;                        // > 1: new command only when (step + 1) mod n_int = 0
+  unsigned int* err = nullptr;          // wait-timeout flags (bulk-copy kernel)
 };
 
 }  // namespace pas
@@ -34,6 +35,7 @@ struct pas_recon_s {
   __nv_bfloat16* d_Rb = nullptr;
   float* d_scale = nullptr;
   unsigned int* d_done = nullptr;
+  unsigned int* d_err = nullptr;
 };
 
 namespace pas {

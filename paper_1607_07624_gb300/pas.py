@@ -141,6 +141,7 @@ _SIGS = {
     "pas_sh_measure": (C.c_int, [vp, vp, vp, vp]),
     "pas_sh_destroy": (None, [vp]),
     "pas_fp32_fma_probe": (C.c_int, [vp, vp, i32, i32, C.POINTER(C.c_int64)]),
+    "pas_recon_check": (C.c_int, [vp, C.POINTER(C.c_uint32)]),
     "pas_calib_interaction_matrix": (C.c_int, [vp, vp, vp, C.c_double, vp]),
     "pas_pinv_f64": (C.c_int, [vp, vp, i32, i32, C.c_double, vp, vp, C.POINTER(i32), C.POINTER(i32)]),
     "pas_gemm_f64": (C.c_int, [vp, vp, C.c_int64, C.c_int64, vp, C.c_int64, C.c_int64, vp, i32, i32, i32, vp,
@@ -705,3 +706,10 @@ def pas_gemm_f64(ctx, X, sxi, sxj, Y, syk, syj, w, ni, nk, nj, Cout, ldc):
         _f64_cuda(nm, t)
     _check(_lib.pas_gemm_f64(ctx, _ptr(X), int(sxi), int(sxj), _ptr(Y), int(syk), int(syj), _ptr(w), int(ni),
                              int(nk), int(nj), _ptr(Cout), int(ldc)), ctx)
+
+
+def pas_recon_check(rec, ctx):
+    """Raise PasError(PAS_ETIMEOUT) if a bounded wait of the reconstructor gave up."""
+    f = C.c_uint32()
+    _check(_lib.pas_recon_check(rec, C.byref(f)), ctx)
+    return f.value

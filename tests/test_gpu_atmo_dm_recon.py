@@ -177,7 +177,10 @@ def test_bf16_dm_basis_within_rounding_of_oracle(env, Np, n_modes):
         pas.pas_dm_destroy(dm)
 
 
-@pytest.mark.parametrize("n_m,n_s", [(100, 416), (400, 1424), (37, 13), (4000, 14312)])
+@pytest.mark.parametrize("n_m,n_s", [(100, 416), (400, 1424), (37, 13), (4000, 14312),
+                                     # long slope vectors (bulk-copy rows): ragged rows and
+                                     # row counts, a last slot shorter than the others
+                                     (1001, 5001), (3, 4100), (257, 8192)])
 def test_reconstructor_fp32_and_bf16(env, n_m, n_s):
     torch, pas, ctx = env
     R = random_matrix(n_m, n_s, 21, 1.0 / math.sqrt(n_s)).astype(np.float32)
@@ -190,6 +193,7 @@ def test_reconstructor_fp32_and_bf16(env, n_m, n_s):
         try:
             pas.pas_recon_apply(rec, ctx, d_s, out)
             torch.cuda.synchronize()
+            assert pas.pas_recon_check(rec, ctx) == 0
             g = out.cpu().numpy().astype(np.float64)
             if prec == pas.PAS_FP32:
                 tol = 1e-5 * np.max(np.abs(exact)) + 1e-7
