@@ -1,0 +1,154 @@
+// Four-step FFT -> mask -> inverse FFT inside one warp, for the pyramid's transform
+// lengths N = 32 Q with Q = 15 (N = 480, two transforms per warp) or Q = 30 (N = 960,
+// one transform per warp). With n = n1 + 32 n2 and k = Q k1 + k2:
+//
+//   X[Q k1 + k2] = sum_n1 W_32^(n1 k1) W_N^(n1 k2) [sum_n2 x[n1 + 32 n2] W_Q^(n2 k2)]
+//
+// so lane n1 takes the Q-point DFT of its own elements in registers, multiplies by
+// W_N^(n1 k2), and one shared-memory transpose hands column k2 to lane k2 (30 columns
+// per warp: 2 x 15 or 1 x 30), which does the 32-point DFT over n1, the pyramid mask of
+// frequency Q k1 + k2, and the 32-point inverse DFT in registers; the transpose back
+// and the conjugate steps in reverse give x'[n1 + 32 n2] in lane n1. Against the
+// pass-by-pass engine (fft.cuh) each element crosses shared memory twice per direction
+// pair instead of once per radix pass, and the 32-point stage runs with no twiddle
+// loads.
+//
+// Shared memory of a warp: T[30][33] float2 (column c at c*33: both transposes are
+// free of bank conflicts). Tables shared by the CTA: tw4[(k2-1)*32 + n1] = W_N^(n1 k2)
+// for k2 = 1..Q-1, mk4[k2*33 + k1] = mask(Q k1 + k2) (the mask at natural frequency u,
+// divided by N).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+
+namespace pas {
+
+constexpr int F4_PITCH = 33;     // float2 per column of the transpose buffer
+constexpr int F4_COLS = 30;      // columns per warp
+constexpr int F4_BUF = F4_COLS * F4_PITCH;
+
+__host__ __device__ constexpr bool four_step_ok(int N) { return N == 480 || N == 960; }
+__host__ __device__ constexpr int four_q(int N) { return N / 32; }
+__host__ __device__ constexpr int four_tpw(int N) { return N == 480 ? 2 : 1; }  // transforms per warp
+__host__ __device__ constexpr int four_tw_size(int N) { return (four_q(N) - 1) * 32; }
+__host__ __device__ constexpr int four_mask_size(int N) { return four_q(N) * F4_PITCH; }
+
+// cos and sin of 2 pi k / 32, k = 0..15
+__device__ __forceinline__ float2 w32(int k) {
+  const float c[16] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f, 0.83146961230254523708f,
+                       0.70710678118654752440f, 0.55557023301960222474f, 0.38268343236508977173f,
+                       0.19509032201612826785f, 0.0f, -0.19509032201612826785f, -0.38268343236508977173f,
+                       -0.55557023301960222474f, -0.70710678118654752440f, -0.83146961230254523708f,
+                       -0.92387953251128675613f, -0.98078528040323044913f};
+  const float s[16] = {0.0f, 0.19509032201612826785f, 0.38268343236508977173f, 0.55557023301960222474f,
+                       0.70710678118654752440f, 0.83146961230254523708f, 0.92387953251128675613f,
+                       0.98078528040323044913f, 1.0f, 0.98078528040323044913f, 0.92387953251128675613f,
+                       0.83146961230254523708f, 0.70710678118654752440f, 0.55557023301960222474f,
+                       0.38268343236508977173f, 0.19509032201612826785f};
+  return make_float2(c[k], s[k]);
+}
+
+// 32-point DFT in registers, natural order in and out: even and odd halves by
+// 16-point transforms, then X[k] = E[k] + w O[k], X[k+16] = E[k] - w O[k] with
+// w = exp(-+ 2 pi i k / 32).
+template <bool INV>
+__device__ __forceinline__ void dft32(float2* x) {
+  float2 e[16], o[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    e[j] = x[2 * j];
+    o[j] = x[2 * j + 1];
+  }
+  Bfly<16, INV>::run(e);
+  Bfly<16, INV>::run(o);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float2 w = w32(k);
+    const float2 t = INV ? cmul(o[k], w) : cmulc(o[k], w);
+    x[k] = cadd(e[k], t);
+    x[k + 16] = csub(e[k], t);
+  }
+}
+
+// 30-point DFT in registers by the prime-factor mapping 30 = 2 x 15: inputs
+// n = (15 n1 + 2 n2) mod 30, outputs k = (15 k1 + 16 k2) mod 30, no twiddles.
+template <bool INV>
+__device__ __forceinline__ void dft30(float2* x) {
+  float2 y0[15], y1[15];
+#pragma unroll
+  for (int n2 = 0; n2 < 15; ++n2) {
+    y0[n2] = x[(2 * n2) % 30];
+    y1[n2] = x[(15 + 2 * n2) % 30];
+  }
+  Bfly<15, INV>::run(y0);
+  Bfly<15, INV>::run(y1);
+#pragma unroll
+  for (int k2 = 0; k2 < 15; ++k2) {
+    x[(16 * k2) % 30] = cadd(y0[k2], y1[k2]);
+    x[(15 + 16 * k2) % 30] = csub(y0[k2], y1[k2]);
+  }
+}
+
+template <int Q, bool INV>
+__device__ __forceinline__ void dft_q(float2* x) {
+  if constexpr (Q == 15) Bfly<15, INV>::run(x);
+  else dft30<INV>(x);
+}
+
+// FFT -> mask -> inverse FFT of four_tpw(N) length-N vectors by one warp.
+// load(t, j): element lane + 32 j of transform t; store(t, j, v): output element
+// lane + 32 j of transform t (t and j are compile-time constants in the unrolled calls).
+// T: this warp's F4_BUF float2 of shared memory; tw4, mk4: the CTA's tables.
+template <int N, class Load, class Store>
+__device__ __forceinline__ void four_step_mask(float2* T, const float2* tw4, const float2* mk4, int lane, Load& load,
+                                               Store& store) {
+  constexpr int Q = four_q(N), TPW = four_tpw(N);
+  static_assert(Q * TPW == F4_COLS, "30 columns per warp");
+  {
+    float2 v[F4_COLS];
+#pragma unroll
+    for (int t = 0; t < TPW; ++t)
+#pragma unroll
+      for (int n2 = 0; n2 < Q; ++n2) v[t * Q + n2] = load(t, n2);
+#pragma unroll
+    for (int t = 0; t < TPW; ++t) {
+      dft_q<Q, false>(v + t * Q);
+#pragma unroll
+      for (int k2 = 1; k2 < Q; ++k2) v[t * Q + k2] = cmul(v[t * Q + k2], tw4[(k2 - 1) * 32 + lane]);
+    }
+#pragma unroll
+    for (int c = 0; c < F4_COLS; ++c) T[c * F4_PITCH + lane] = v[c];
+  }
+  __syncwarp();
+  if (lane < F4_COLS) {
+    const int k2 = lane % Q;
+    float2* col = T + lane * F4_PITCH;
+    float2 w[32];
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) w[n1] = col[n1];
+    dft32<false>(w);
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) w[k1] = cmul(w[k1], mk4[k2 * F4_PITCH + k1]);
+    dft32<true>(w);
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) col[n1] = w[n1];
+  }
+  __syncwarp();
+  {
+    float2 v[F4_COLS];
+#pragma unroll
+    for (int c = 0; c < F4_COLS; ++c) v[c] = T[c * F4_PITCH + lane];
+#pragma unroll
+    for (int t = 0; t < TPW; ++t) {
+#pragma unroll
+      for (int k2 = 1; k2 < Q; ++k2) v[t * Q + k2] = cmulc(v[t * Q + k2], tw4[(k2 - 1) * 32 + lane]);
+      dft_q<Q, true>(v + t * Q);
+#pragma unroll
+      for (int n2 = 0; n2 < Q; ++n2) store(t, n2, v[t * Q + n2]);
+    }
+  }
+  __syncwarp();  // T is reused by the next call
+}
+
+}  // namespace pas

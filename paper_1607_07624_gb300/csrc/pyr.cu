@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "fft.cuh"
+#include "fft4.cuh"
 #include "fft_host.h"
 #include "internal.h"
 #include "noise.cuh"
@@ -70,6 +71,8 @@ struct ColArgs {
   const float2* H;
   const float2* tw;
   const float2* mask;
+  const float2* tw4;    // four-step engine (N = 480, 960): W_N^(n1 k2) [(Q-1)][32]
+  const float2* mk4;    // and the mask by natural frequency [Q][33]
   const float2* tilt;   // [K][Np] (-1)^i exp(2 pi i (i - ci) alpha_k): tilt_x + input ramp
   const int* kmap;      // [K] -> rows-pass index
   float* part;          // [G][nd][nd]
@@ -85,7 +88,7 @@ struct ColArgs {
 // lets 3 columns-pass CTAs of 8 warps (and 7 rows-pass CTAs of 4 warps) share an SM
 // instead of 2 (4); other lengths keep the compiler's choice.
 constexpr int rows_max_regs(int N) { return N == 480 ? 72 : 128; }
-constexpr int cols_max_regs(int N) { return N == 480 ? 72 : 128; }
+constexpr int cols_max_regs(int N) { return 128; }
 
 template <int N>
 __global__ void __maxnreg__(rows_max_regs(N))
@@ -299,11 +302,16 @@ __global__ void tilt_table_kernel(const float* alpha, const float* amp, int K, i
 template <int N>
 __global__ void __maxnreg__(cols_max_regs(N))
 pyr_cols_kernel(ColArgs a) {
-  constexpr int TWN = tw_size(N), BL = buf_len(N), PITCH = BL | 1;
+  // per-warp buffers: one transform's padded buffer (pass-by-pass engine) or the
+  // four-step engine's transpose buffer; both then hold the warp's column of |g|^2
+  constexpr bool FOUR = four_step_ok(N);
+  constexpr int TWN = FOUR ? four_tw_size(N) : tw_size(N);
+  constexpr int MKN = FOUR ? four_mask_size(N) : buf_len(N);
+  constexpr int PITCH = FOUR ? F4_BUF : (buf_len(N) | 1);
   extern __shared__ float2 smem[];
   float2* tw_s = smem;
   float2* mk_s = smem + TWN;
-  float2* bufs = mk_s + BL;                       // [b][PITCH]
+  float2* bufs = mk_s + MKN;                      // [b][PITCH]
   const int Np = a.Np;
   const int q = blockIdx.x;                       // detector column
   const int gh = blockIdx.y;                      // modulation group x column part
@@ -311,8 +319,12 @@ pyr_cols_kernel(ColArgs a) {
   const int k0 = g * a.kper;
   const int kc = min(a.kper, a.K - k0);
   pdl_trigger();
-  for (int t = threadIdx.x; t < TWN; t += blockDim.x) tw_s[t] = a.tw[t];
-  for (int t = threadIdx.x; t < BL; t += blockDim.x) mk_s[t] = a.mask[t];
+  {
+    const float2* twg = FOUR ? a.tw4 : a.tw;
+    const float2* mkg = FOUR ? a.mk4 : a.mask;
+    for (int t = threadIdx.x; t < TWN; t += blockDim.x) tw_s[t] = twg[t];
+    for (int t = threadIdx.x; t < MKN; t += blockDim.x) mk_s[t] = mkg[t];
+  }
   pdl_wait();  // H, the partial frames and the counters belong to the predecessors
   __syncthreads();  // twiddles and mask staged
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -325,34 +337,64 @@ pyr_cols_kernel(ColArgs a) {
   const int nw = a.frac ? ((q + 1) * N + a.nd - 1) / a.nd - y0 : bw;
   const int y = y0 + warp;
   float2* buf = bufs + warp * PITCH;
-  using OS = OutShape<N>;
-  float acc[OS::PER_LANE];
-#pragma unroll
-  for (int t = 0; t < OS::PER_LANE; ++t) acc[t] = 0.f;
-  for (int kk = 0; kk < (warp < nw ? kc : 0); ++kk) {
-    // the tilt row of this k is shared by the CTA's warps through L1; no barrier
-    const float2* Hcol = a.H + ((size_t)a.kmap[k0 + kk] * N + y) * Np;
-    const float2* tk = a.tilt + (size_t)(k0 + kk) * Np;
-    const int off = a.off;
-    auto load = [&](int, int, int x) -> float2 {
-      const int i = x - off;
-      if ((unsigned)i < (unsigned)Np) return cmul(__ldg(Hcol + i), __ldg(tk + i));
-      return make_float2(0.f, 0.f);
-    };
-    auto store = [&](int jb, int k, int, float2 v) {
-      acc[jb * OS::R0 + k] = fmaf(v.x, v.x, fmaf(v.y, v.y, acc[jb * OS::R0 + k]));
-    };
-    fft_mask_ifft<N>(buf, tw_s, mk_s, lane, load, store);
-    __syncwarp();
-  }
-  // stage |g|^2 of this column, then bin b x b over the CTA's columns
   float* accw = reinterpret_cast<float*>(buf);
+  if constexpr (FOUR) {
+    // lane l accumulates |g|^2 of rows l + 32 j; TPW modulation points per call (a
+    // missing second point of an odd count transforms zeros)
+    constexpr int Q = four_q(N), TPW = four_tpw(N);
+    float acc[Q];
 #pragma unroll
-  for (int jb = 0; jb < OS::NJ0; ++jb) {
-    const int bb = lane + 32 * jb;
-    if (OS::NB0 % 32 == 0 || bb < OS::NB0) {
+    for (int t = 0; t < Q; ++t) acc[t] = 0.f;
+    for (int kk = 0; kk < (warp < nw ? kc : 0); kk += TPW) {
+      const float2* Hcol[TPW];
+      const float2* tk[TPW];
 #pragma unroll
-      for (int k = 0; k < OS::R0; ++k) accw[bb + k * OS::NB0] = acc[jb * OS::R0 + k];
+      for (int t = 0; t < TPW; ++t) {
+        const int kt = min(kk + t, kc - 1);
+        Hcol[t] = a.H + ((size_t)a.kmap[k0 + kt] * N + y) * Np;
+        tk[t] = a.tilt + (size_t)(k0 + kt) * Np;
+      }
+      const int off = a.off;
+      auto load = [&](int t, int j) -> float2 {
+        const int i = lane + 32 * j - off;
+        if ((unsigned)i < (unsigned)Np && kk + t < kc) return cmul(__ldg(Hcol[t] + i), __ldg(tk[t] + i));
+        return make_float2(0.f, 0.f);
+      };
+      auto store = [&](int, int j, float2 v) { acc[j] = fmaf(v.x, v.x, fmaf(v.y, v.y, acc[j])); };
+      four_step_mask<N>(buf, tw_s, mk_s, lane, load, store);
+    }
+    // stage |g|^2 of this column in natural order
+#pragma unroll
+    for (int j = 0; j < Q; ++j) accw[lane + 32 * j] = acc[j];
+  } else {
+    using OS = OutShape<N>;
+    float acc[OS::PER_LANE];
+#pragma unroll
+    for (int t = 0; t < OS::PER_LANE; ++t) acc[t] = 0.f;
+    for (int kk = 0; kk < (warp < nw ? kc : 0); ++kk) {
+      // the tilt row of this k is shared by the CTA's warps through L1; no barrier
+      const float2* Hcol = a.H + ((size_t)a.kmap[k0 + kk] * N + y) * Np;
+      const float2* tk = a.tilt + (size_t)(k0 + kk) * Np;
+      const int off = a.off;
+      auto load = [&](int, int, int x) -> float2 {
+        const int i = x - off;
+        if ((unsigned)i < (unsigned)Np) return cmul(__ldg(Hcol + i), __ldg(tk + i));
+        return make_float2(0.f, 0.f);
+      };
+      auto store = [&](int jb, int k, int, float2 v) {
+        acc[jb * OS::R0 + k] = fmaf(v.x, v.x, fmaf(v.y, v.y, acc[jb * OS::R0 + k]));
+      };
+      fft_mask_ifft<N>(buf, tw_s, mk_s, lane, load, store);
+      __syncwarp();
+    }
+    // stage |g|^2 of this column (natural order)
+#pragma unroll
+    for (int jb = 0; jb < OS::NJ0; ++jb) {
+      const int bb = lane + 32 * jb;
+      if (OS::NB0 % 32 == 0 || bb < OS::NB0) {
+#pragma unroll
+        for (int k = 0; k < OS::R0; ++k) accw[bb + k * OS::NB0] = acc[jb * OS::R0 + k];
+      }
     }
   }
   __syncthreads();
@@ -469,6 +511,8 @@ struct pas_pyr_s {
   float* d_sn = nullptr;
   float2* d_tw = nullptr;
   float2* d_mask = nullptr;
+  float2* d_tw4 = nullptr;   // four-step columns pass (N = 480, 960)
+  float2* d_mk4 = nullptr;
   float* d_alpha = nullptr;
   float2* d_tilt = nullptr;
   float* d_amp = nullptr;  // [K] column-tilt amplitudes of an extended source
@@ -500,6 +544,8 @@ cudaError_t raise_dyn_smem(const void* func, size_t bytes) {
 
 // columns pass with `warps` fine columns per CTA
 size_t cols_smem(pas_pyr_t y, int warps) {
+  if (four_step_ok(y->p.N))
+    return sizeof(float2) * ((size_t)four_tw_size(y->p.N) + four_mask_size(y->p.N) + (size_t)warps * F4_BUF);
   return sizeof(float2) * ((size_t)y->kern.tw_n + y->kern.buf_n + (size_t)warps * y->kern.pitch);
 }
 
@@ -538,6 +584,8 @@ static void launch_cols(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream
   ca.H = y->d_H;
   ca.tw = y->d_tw;
   ca.mask = y->d_mask;
+  ca.tw4 = y->d_tw4;
+  ca.mk4 = y->d_mk4;
   ca.tilt = y->d_tilt;
   ca.kmap = y->d_kmap;
   ca.part = y->d_part;
@@ -648,6 +696,8 @@ void pas_pyr_destroy(pas_pyr_t y) {
   pas::dev_free(y->d_amp);
   pas::dev_free(y->d_beta);
   pas::dev_free(y->d_kmap);
+  pas::dev_free(y->d_tw4);
+  pas::dev_free(y->d_mk4);
   pas::dev_free(y->d_H);
   pas::dev_free(y->d_part);
   pas::dev_free(y->d_frame);
@@ -773,6 +823,10 @@ static pas_status pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int3
   A((void**)&y->d_sn, sizeof(float) * 2 * y->n_valid);
   A((void**)&y->d_tw, sizeof(float2) * kern.tw_n);
   A((void**)&y->d_mask, sizeof(float2) * kern.buf_n);
+  if (pas::four_step_ok(p.N)) {
+    A((void**)&y->d_tw4, sizeof(float2) * pas::four_tw_size(p.N));
+    A((void**)&y->d_mk4, sizeof(float2) * pas::four_mask_size(p.N));
+  }
   A((void**)&y->d_alpha, sizeof(float) * p.K);
   A((void**)&y->d_tilt, sizeof(float2) * (size_t)p.K * p.Np);
   if (n_src > 0) A((void**)&y->d_amp, sizeof(float) * p.K);
@@ -796,6 +850,12 @@ static pas_status pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int3
   C(y->d_valid, valid.data(), sizeof(int32_t) * y->n_valid);
   C(y->d_tw, tw.data(), sizeof(float2) * kern.tw_n);
   C(y->d_mask, mk.data(), sizeof(float2) * kern.buf_n);
+  if (pas::four_step_ok(p.N)) {
+    std::vector<float2> tw4(pas::four_tw_size(p.N)), mk4(pas::four_mask_size(p.N));
+    pas::four_step_tables(p.N, tw4.data(), mk4.data());
+    C(y->d_tw4, tw4.data(), sizeof(float2) * tw4.size());
+    C(y->d_mk4, mk4.data(), sizeof(float2) * mk4.size());
+  }
   C(y->d_alpha, alpha.data(), sizeof(float) * p.K);
   if (y->d_amp) C(y->d_amp, amp.data(), sizeof(float) * p.K);
   if (e == cudaSuccess) {
@@ -1040,8 +1100,10 @@ struct StaticTables {
   int kmap[STATIC_MAX_K], key_rep[STATIC_MAX_K], key_ey[STATIC_MAX_K];
   float alpha[STATIC_MAX_K], beta[STATIC_MAX_K];
   float2 tw[STATIC_TABLE], mk[STATIC_TABLE];
+  float2 tw4[STATIC_TABLE], mk4[STATIC_TABLE];
   unsigned char vpix[(2 * STATIC_MAX_NSUB) * (2 * STATIC_MAX_NSUB)];
 };
+static_assert(four_tw_size(960) <= STATIC_TABLE && four_mask_size(960) <= STATIC_TABLE, "four-step tables");
 static StaticTables g_static_tables;
 
 // Device address of the scratch array for the current device (looked up once per
@@ -1133,6 +1195,7 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
   fft_twiddles_into(p.N, T.tw);
   pyr_mask_table(p.N, kern.buf_n, T.mk);
   quadrant_valid_map(p.n_sub, T.valid, nv, T.vpix);
+  if (four_step_ok(p.N)) four_step_tables(p.N, T.tw4, T.mk4);
 
   // carve the scratch array
   unsigned char* base = nullptr;
@@ -1159,7 +1222,7 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
   y.rows = 4;
   y.n_schunks = (n_s + 3) / 4;
   y.s_chunk = (n_s + y.n_schunks - 1) / y.n_schunks;
-  y.smem_cols = sizeof(float2) * ((size_t)kern.tw_n + kern.buf_n + (size_t)b * kern.pitch);
+  y.smem_cols = cols_smem(&y, b);
   cudaError_t e = cudaSuccess;
   {
     // the columns pass's resident CTAs per SM, as pas_pyr_create counts them
@@ -1173,6 +1236,10 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
   y.d_part = reinterpret_cast<float*>(carve(sizeof(float) * (size_t)y.G * nd * nd));
   y.d_tw = reinterpret_cast<float2*>(carve(sizeof(float2) * kern.tw_n));
   y.d_mask = reinterpret_cast<float2*>(carve(sizeof(float2) * kern.buf_n));
+  if (four_step_ok(p.N)) {
+    y.d_tw4 = reinterpret_cast<float2*>(carve(sizeof(float2) * four_tw_size(p.N)));
+    y.d_mk4 = reinterpret_cast<float2*>(carve(sizeof(float2) * four_mask_size(p.N)));
+  }
   y.d_alpha = reinterpret_cast<float*>(carve(sizeof(float) * p.K));
   y.d_tilt = reinterpret_cast<float2*>(carve(sizeof(float2) * (size_t)p.K * p.Np));
   y.d_beta = reinterpret_cast<float*>(carve(sizeof(float) * n_s));
@@ -1197,6 +1264,10 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
   };
   H2D(y.d_tw, T.tw, sizeof(float2) * kern.tw_n);
   H2D(y.d_mask, T.mk, sizeof(float2) * kern.buf_n);
+  if (four_step_ok(p.N)) {
+    H2D(y.d_tw4, T.tw4, sizeof(float2) * four_tw_size(p.N));
+    H2D(y.d_mk4, T.mk4, sizeof(float2) * four_mask_size(p.N));
+  }
   H2D(y.d_alpha, T.alpha, sizeof(float) * p.K);
   if (e == cudaSuccess) {
     tilt_table_kernel<<<p.K, 256, 0, st>>>(y.d_alpha, nullptr, p.K, p.Np, y.d_tilt);

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "fft4.cuh"
 #include "fft_host.h"
 
 namespace pas {
@@ -76,6 +77,24 @@ inline void pyr_mask_table(int N, int buf_n, float2* mk) {
     const double ph = 0.5 * M_PI * ut;
     mk[phys(j)] = make_float2((float)(std::cos(ph) / N), (float)(std::sin(ph) / N));
   }
+}
+
+// Tables of the four-step engine (fft4.cuh) for N = 32 Q: tw4[(k2 - 1) 32 + n1] =
+// exp(-2 pi i n1 k2 / N), k2 = 1..Q-1; mk4[k2 33 + k1] = the pyramid mask at natural
+// frequency u = Q k1 + k2, exp(i (pi/2) |u - (N-1)/2|) / N (pads zero).
+inline void four_step_tables(int N, float2* tw4, float2* mk4) {
+  const int Q = four_q(N);
+  for (int k2 = 1; k2 < Q; ++k2)
+    for (int n1 = 0; n1 < 32; ++n1) {
+      const double a = -2.0 * M_PI * (double)(n1 * k2) / (double)N;
+      tw4[(k2 - 1) * 32 + n1] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+  for (int t = 0; t < four_mask_size(N); ++t) mk4[t] = make_float2(0.f, 0.f);
+  for (int k2 = 0; k2 < Q; ++k2)
+    for (int k1 = 0; k1 < 32; ++k1) {
+      const double ph = 0.5 * M_PI * std::fabs((double)(Q * k1 + k2) - 0.5 * (N - 1));
+      mk4[k2 * F4_PITCH + k1] = make_float2((float)(std::cos(ph) / N), (float)(std::sin(ph) / N));
+    }
 }
 
 // Detector pixels of the valid sub-apertures in all four quadrants (nd = 2 n_sub).

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) recon_kernel(ReconArgs a) {
 // sets *err, and the warp waits (with the long bound) for the copies it still has in
 // flight before it leaves.
 constexpr int RB_WARPS = 4;            // rows (warps) per CTA
-constexpr int RB_NS = 4;               // slots per warp
+constexpr int RB_NS = 3;               // slots per warp (24 KB per CTA: 9 CTAs per SM, one wave of rows)
 constexpr int RB_CH = 2048;            // bytes per slot (a multiple of 512: 16 bytes per lane per step)
 constexpr int RECON_BULK_MIN_NS = 4096;
 constexpr size_t RB_SMEM = (size_t)RB_WARPS * RB_NS * RB_CH;

@@ -84,6 +84,10 @@ TINY = [
     tiny_config(Np=80, N=160, n_sub=20, K=16, obs=0.3),
     tiny_config(Np=96, N=192, n_sub=16, K=8),
     tiny_config(Np=120, N=240, n_sub=24, K=10),
+    # the four-step engine's lengths: two transforms per warp at N = 480 (odd K leaves a
+    # warp's last pair half empty), one at N = 960
+    tiny_config(Np=240, N=480, n_sub=30, K=5, mod_radius=3.0),
+    tiny_config(Np=480, N=960, n_sub=96, K=3, mod_radius=4.0),
 ]
 
 
@@ -131,6 +135,30 @@ def test_full_size_configs_open_loop_phase(env, name, k):
     assert np.ptp(opd) * 2 * math.pi / cfg.wavelength_nm > 20.0
     fr_g, sl_g, valid = run_gpu(env, cfg, opd)
     check(cfg, fr_g, sl_g, *oracle_measure(cfg, opd, valid))
+
+
+def test_four_step_columns_pass_with_odd_and_even_groupings(env):
+    """N = 480 (two modulation points per warp call): modulation groups of 7, 3, 2 and
+    1 points, and two CTAs per detector column, all against the oracle."""
+    torch, pas, ctx = env
+    cfg = tiny_config(Np=240, N=480, n_sub=30, K=7, mod_radius=3.0)
+    opd = random_opd_nm(cfg.Np, 250.0, seed=17).astype(np.float32)
+    from oracle import optics as op
+    valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
+    fr_o, sl_o = oracle_measure(cfg, opd, valid)
+    pyr = pas.pas_pyr_create(ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius, cfg.wavelength_nm, cfg.obs)
+    try:
+        nv = pas.pas_pyr_n_valid(pyr)
+        d_opd = torch.as_tensor(opd).cuda()
+        for t in [(4, 2, 1, 1), (4, 2, 3, 1), (4, 2, 4, 1), (8, 3, 7, 1), (4, 2, 3, 2), (2, 1, 2, 4)]:
+            pas.pas_pyr_set_tuning(pyr, ctx, *t)
+            fr = torch.zeros(cfg.n_det, cfg.n_det, device="cuda")
+            sl = torch.zeros(2 * nv, device="cuda")
+            pas.pas_pyr_measure(pyr, ctx, d_opd, fr, sl)
+            torch.cuda.synchronize()
+            check(cfg, fr.cpu().numpy().astype(np.float64), sl.cpu().numpy().astype(np.float64), fr_o, sl_o)
+    finally:
+        pas.pas_pyr_destroy(pyr)
 
 
 def test_flat_wavefront_and_parseval(env):
