@@ -324,6 +324,45 @@ def bench_lbt(args, timed, barrier, flush, world, dist, peaks, no_mlp=False):
     return r, mlp_info
 
 
+def bench_equal_wfe(timed, n_timed=300):
+    """North-star comparison where the loop settles: the LBT-class optics (240 px, 3
+    layers, magnitude-10 noise) with 200 KL modes (with 400 the linear loop drifts). The
+    FP32 loop and the loop with a bfloat16 DM basis and reconstructor run the
+    workload's 2000 steps from the same start; reported: their steps/s (L2 flushed
+    between timed steps) and mean residual WFE after a 20 % burn-in."""
+    import numpy as np
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    from synth import get_config
+    from synth.configs import with_
+    cfg = with_(get_config("scao_lbt_240px"), n_modes=200)
+    n = cfg.n_steps
+    out = {"workload": f"{cfg.name} with {cfg.n_modes} KL modes, {n} steps, magnitude {cfg.magnitude} noise"}
+    a = SCAOSystem(cfg, wfe_history=n)
+    try:
+        b = SCAOSystem(cfg, basis=a.basis, R=a.R, recon_precision=pas.PAS_BF16, dm_precision=pas.PAS_BF16,
+                       wfe_history=n, autotune=tuple(a.tuning))
+        try:
+            res = {}
+            for label, s in (("fp32", a), ("bf16", b)):
+                zeros = np.zeros((s.delay, s.n_modes), np.float32)
+                s.set_state(0, zeros)
+                s.step(n)
+                w = s.wfe_nm(n)
+                s.set_state(0, zeros)
+                sps = n_timed / (timed(lambda: s.step(1), n_timed) * 1e-3)
+                res[label] = {"steps_per_s": sps, "wfe_nm_mean": float(w[n // 5:].mean()),
+                              "wfe_nm_first_step": float(w[0]), "wfe_nm_last_500_mean": float(w[-500:].mean())}
+            out.update(res)
+            out["wfe_diff_nm"] = res["bf16"]["wfe_nm_mean"] - res["fp32"]["wfe_nm_mean"]
+            out["bf16_speedup"] = res["bf16"]["steps_per_s"] / res["fp32"]["steps_per_s"]
+        finally:
+            b.close()
+    finally:
+        a.close()
+    return out
+
+
 def cpu_baseline_for(cfg, args):
     """The FP64 oracle on this host: one thread, and all cores as independent
     single-thread loops (capped by host memory for the large workloads)."""
@@ -961,6 +1000,10 @@ def main():
                                                           no_mlp=args.no_mlp)
         except Exception as e:
             extra["scao_lbt_240px"] = {"error": str(e)}
+        try:
+            extra["equal_wfe_bf16_vs_fp32"] = bench_equal_wfe(timed)
+        except Exception as e:
+            extra["equal_wfe_bf16_vs_fp32"] = {"error": str(e)}
         try:
             extra["other_workloads"] = bench_other_workloads(timed, peaks)
         except Exception as e:

@@ -139,6 +139,7 @@ __device__ __forceinline__ void four_step_mask(float2* T, const float2* tw4, con
     float2 v[F4_COLS];
 #pragma unroll
     for (int c = 0; c < F4_COLS; ++c) v[c] = T[c * F4_PITCH + lane];
+    __syncwarp();  // T is read: `store` may write into it
 #pragma unroll
     for (int t = 0; t < TPW; ++t) {
 #pragma unroll

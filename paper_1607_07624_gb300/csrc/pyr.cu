@@ -41,6 +41,8 @@ struct RowArgs {
   const float* opd;     // [Np][Np]
   const float2* tw;     // [N]
   const float2* mask;   // [N] digit-reversed
+  const float2* tw4;    // four-step engine tables (N = 480, 960)
+  const float2* mk4;
   const float* beta;    // [n_s] cycles per pixel (tilt_y + input ramp)
   float2* H;            // [n_s][N][Np]
   int Np, off;
@@ -87,17 +89,20 @@ struct ColArgs {
 // Register caps per transform length: 72 for N = 480 compiles without spills and
 // lets 3 columns-pass CTAs of 8 warps (and 7 rows-pass CTAs of 4 warps) share an SM
 // instead of 2 (4); other lengths keep the compiler's choice.
-constexpr int rows_max_regs(int N) { return N == 480 ? 72 : 128; }
+constexpr int rows_max_regs(int N) { return 128; }
 constexpr int cols_max_regs(int N) { return 128; }
 
 template <int N>
 __global__ void __maxnreg__(rows_max_regs(N))
 pyr_rows_kernel(RowArgs a) {
-  constexpr int TWN = tw_size(N), BL = buf_len(N), PITCH = BL | 1;
+  constexpr bool FOUR = four_step_ok(N);
+  constexpr int TWN = FOUR ? four_tw_size(N) : tw_size(N);
+  constexpr int MKN = FOUR ? four_mask_size(N) : buf_len(N);
+  constexpr int PITCH = FOUR ? F4_BUF : (buf_len(N) | 1);
   extern __shared__ float2 smem[];
   float2* tw_s = smem;
   float2* mk_s = smem + TWN;
-  float2* tilt_s = mk_s + BL;                       // [s_chunk][Np]
+  float2* tilt_s = mk_s + MKN;                      // [s_chunk][Np]
   const int rows = blockDim.x >> 5;
   float2* phs = tilt_s + a.s_chunk * a.Np;          // [rows][Np]
   float2* bufs = phs + rows * a.Np;                 // [rows][PITCH]
@@ -105,8 +110,12 @@ pyr_rows_kernel(RowArgs a) {
   const int i0 = blockIdx.x * rows;
   const int s0 = (blockIdx.y * a.n_s) / gridDim.y, s1 = ((blockIdx.y + 1) * a.n_s) / gridDim.y;
   pdl_trigger();
-  for (int t = threadIdx.x; t < TWN; t += blockDim.x) tw_s[t] = a.tw[t];
-  for (int t = threadIdx.x; t < BL; t += blockDim.x) mk_s[t] = a.mask[t];
+  {
+    const float2* twg = FOUR ? a.tw4 : a.tw;
+    const float2* mkg = FOUR ? a.mk4 : a.mask;
+    for (int t = threadIdx.x; t < TWN; t += blockDim.x) tw_s[t] = twg[t];
+    for (int t = threadIdx.x; t < MKN; t += blockDim.x) mk_s[t] = mkg[t];
+  }
   // tilt along the row (with the input centring ramp and (-1)^j) per sin value
   const float cj = 0.5f * (float)(Np - 1);
   for (int t = threadIdx.x; t < (s1 - s0) * Np; t += blockDim.x) {
@@ -135,25 +144,38 @@ pyr_rows_kernel(RowArgs a) {
   }
   __syncthreads();
   const int nr = min(rows, Np - i0);
-  for (int s = s0; s < s1; ++s) {
-    const float2* tl = tilt_s + (s - s0) * Np;
+  const int lg = __ffs(rows) - 1;
+  constexpr int TPW = FOUR ? four_tpw(N) : 1;   // sin values per engine call
+  for (int s = s0; s < s1; s += TPW) {
     if (i < Np) {
-      auto load = [&](int, int, int x) -> float2 {
-        const int j = x - off;
-        if ((unsigned)j < (unsigned)Np) return cmul(phrow[j], tl[j]);
-        return make_float2(0.f, 0.f);
-      };
-      auto store = [&](int, int, int x, float2 v) { buf[phys(x)] = v; };
-      fft_mask_ifft<N>(buf, tw_s, mk_s, lane, load, store);
+      if constexpr (FOUR) {
+        auto load = [&](int t, int jj) -> float2 {
+          const int j = lane + 32 * jj - off;
+          if ((unsigned)j < (unsigned)Np && s + t < s1) return cmul(phrow[j], tilt_s[(s + t - s0) * Np + j]);
+          return make_float2(0.f, 0.f);
+        };
+        auto store = [&](int t, int jj, float2 v) { buf[t * N + lane + 32 * jj] = v; };
+        four_step_mask<N>(buf, tw_s, mk_s, lane, load, store);
+      } else {
+        const float2* tl = tilt_s + (s - s0) * Np;
+        auto load = [&](int, int, int x) -> float2 {
+          const int j = x - off;
+          if ((unsigned)j < (unsigned)Np) return cmul(phrow[j], tl[j]);
+          return make_float2(0.f, 0.f);
+        };
+        auto store = [&](int, int, int x, float2 v) { buf[phys(x)] = v; };
+        fft_mask_ifft<N>(buf, tw_s, mk_s, lane, load, store);
+      }
     }
     __syncthreads();
     // transposed write: H[s][y][i0 + r], rows x 8 contiguous bytes per y (rows is a
     // power of two: index split by shift and mask)
-    float2* Hs = a.H + (size_t)s * N * Np;
-    const int lg = __ffs(rows) - 1;
-    for (int idx = threadIdx.x; idx < N * rows; idx += blockDim.x) {
-      const int r = idx & (rows - 1), y = idx >> lg;
-      if (r < nr) Hs[(size_t)y * Np + i0 + r] = bufs[r * PITCH + phys(y)];
+    for (int t = 0; t < TPW && s + t < s1; ++t) {
+      float2* Hs = a.H + (size_t)(s + t) * N * Np;
+      for (int idx = threadIdx.x; idx < N * rows; idx += blockDim.x) {
+        const int r = idx & (rows - 1), y = idx >> lg;
+        if (r < nr) Hs[(size_t)y * Np + i0 + r] = FOUR ? bufs[r * PITCH + t * N + y] : bufs[r * PITCH + phys(y)];
+      }
     }
     __syncthreads();
   }
@@ -554,6 +576,9 @@ size_t cols_smem(pas_pyr_t y, int warps) {
 static bool split_ok(pas_pyr_t y, int H) { return H == 1 || (!y->frac && H >= 1 && H <= 8 && y->b % H == 0); }
 
 size_t rows_smem(pas_pyr_t y, int rows, int s_chunk) {
+  if (four_step_ok(y->p.N))
+    return sizeof(float2) * ((size_t)four_tw_size(y->p.N) + four_mask_size(y->p.N) + (size_t)s_chunk * y->p.Np +
+                             (size_t)rows * (y->p.Np + F4_BUF));
   return sizeof(float2) * ((size_t)y->kern.tw_n + y->kern.buf_n + (size_t)s_chunk * y->p.Np +
                            (size_t)rows * (y->p.Np + y->kern.pitch));
 }
@@ -564,6 +589,8 @@ static void launch_rows(pas_pyr_t y, const float* d_opd, cudaStream_t st, bool p
   ra.opd = d_opd;
   ra.tw = y->d_tw;
   ra.mask = y->d_mask;
+  ra.tw4 = y->d_tw4;
+  ra.mk4 = y->d_mk4;
   ra.beta = y->d_beta;
   ra.H = y->d_H;
   ra.Np = p.Np;
