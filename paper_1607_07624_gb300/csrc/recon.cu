@@ -312,6 +312,172 @@ __global__ void __launch_bounds__(RB_WARPS * 32) recon_bulk_kernel(ReconArgs a) 
   }
 }
 
+// The product for long slope vectors up to RT_MAX_NS: a TMA pipeline over whole rows.
+// Thread 0 streams the CTA's mode rows, one bulk copy per row (split into pieces of at
+// most 16 KB, all counted on the row slot's "full" mbarrier), into a ring of RT_NS row
+// slots; each of the 8 warps owns the same column groups of every row (group g = u 8 +
+// warp: 32 chunks of 16 bytes, so a warp reads 512 contiguous bytes per step), keeps
+// the slopes of those columns in registers, and arrives on the slot's "empty" barrier
+// when it has read its part; thread 0 refills a slot once all 8 warps have arrived.
+// Per-row, per-warp partial sums meet in shared memory and are added in warp order.
+// Waits are bounded: one that gives up sets *err and a shared abort flag, every warp
+// leaves the row loop, and thread 0 waits (long bound) for its copies still in flight.
+constexpr int RT_WARPS = 8;
+constexpr int RT_MAX_NS = 16384;           // slopes held in registers: 64 per lane
+constexpr int RT_MAX_ROWS = 64;            // rows per CTA (partial-sum table)
+constexpr size_t RT_SLOT_BUDGET = 96 * 1024;  // shared memory for the row slots of one CTA
+
+template <bool BF16>
+__global__ void __launch_bounds__(RT_WARPS * 32) recon_tma_kernel(ReconArgs a, int rows_per_cta, int ns_slots,
+                                                                  int slot_bytes) {
+  constexpr int W = BF16 ? 8 : 4;       // columns per 16-byte chunk
+  constexpr int MAXG = BF16 ? 8 : 16;   // column groups per warp (64 slopes per lane)
+  extern __shared__ __align__(128) unsigned char rt_smem[];  // [ns_slots][slot_bytes]
+  __shared__ __align__(8) uint64_t full[4], empty[4];
+  __shared__ float part[RT_MAX_ROWS][RT_WARPS];
+  __shared__ volatile int abort_flag;
+  __shared__ bool is_last;
+  pdl_trigger();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int ES = BF16 ? 2 : 4;
+  const int row_bytes = a.n_s_pad * ES;
+  const int nc = a.n_s_pad / W;
+  const int r0 = blockIdx.x * rows_per_cta;
+  const int nrow = max(0, min(a.n_m, r0 + rows_per_cta) - r0);
+  const char* Rbase = BF16 ? reinterpret_cast<const char*>(a.Rb) : reinterpret_cast<const char*>(a.R);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ns_slots; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])), "r"(RT_WARPS) : "memory");
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int i) {  // row r0 + i into slot i % ns_slots
+    unsigned char* dst = rt_smem + (size_t)(i % ns_slots) * slot_bytes;
+    const char* src = Rbase + (size_t)(r0 + i) * row_bytes;
+    uint64_t* bar = &full[i % ns_slots];
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(row_bytes)
+                 : "memory");
+    for (int o = 0; o < row_bytes; o += 16384) {
+      const int bytes = min(16384, row_bytes - o);
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_u32(dst + o)),
+                   "l"(src + o), "r"(bytes), "r"(smem_u32(bar))
+                   : "memory");
+    }
+  };
+  int issued = 0;  // thread 0: rows requested so far
+  if (threadIdx.x == 0)
+    for (; issued < min(ns_slots, nrow); ++issued) issue(issued);  // R is constant: before the wait
+  // the writer of row r0 + t is thread t; its integrator state is final before the wait
+  const bool writer = threadIdx.x < nrow;
+  long long t_step = 0;
+  float prev = 0.f;
+  bool hold = false;
+  if (writer && a.ring) {
+    t_step = *a.step;
+    prev = a.ring[(size_t)((t_step - 1 + a.delay) % a.delay) * a.n_m + r0 + threadIdx.x];
+    hold = a.n_int > 1 && (t_step + 1) % a.n_int != 0;
+  }
+  pdl_wait();
+  // slopes of this lane's chunks (columns at or beyond n_s read as 0)
+  float sl[MAXG][W];
+#pragma unroll
+  for (int u = 0; u < MAXG; ++u) {
+    const int c = (u * RT_WARPS + warp) * 32 + lane;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    if (c < nc) slope_chunk<BF16>(a.s, a.n_s, c, &lo, &hi);
+    sl[u][0] = lo.x; sl[u][1] = lo.y; sl[u][2] = lo.z; sl[u][3] = lo.w;
+    if constexpr (BF16) {
+      sl[u][4] = hi.x; sl[u][5] = hi.y; sl[u][6] = hi.z; sl[u][7] = hi.w;
+    }
+  }
+  for (int i = 0; i < nrow; ++i) {
+    const int s = i % ns_slots;
+    const uint32_t par = (uint32_t)(i / ns_slots) & 1u;
+    const bool got = bar_wait(&full[s], par, RB_WAIT_LIMIT);
+    if (!__all_sync(0xffffffffu, got)) {
+      if (lane == 0) {
+        atomicOr(a.err, 1u);
+        abort_flag = 1;
+      }
+    }
+    __syncwarp();
+    if (abort_flag) break;
+    const unsigned char* slot = rt_smem + (size_t)s * slot_bytes;
+    float acc = 0.f;
+#pragma unroll
+    for (int u = 0; u < MAXG; ++u) {
+      const int c = (u * RT_WARPS + warp) * 32 + lane;
+      if (c < nc) {
+        const uint4 q = *reinterpret_cast<const uint4*>(slot + (size_t)c * 16);
+        if constexpr (BF16) {
+          const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+          const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
+          const float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
+          acc = fmaf(f0.x, sl[u][0], acc); acc = fmaf(f0.y, sl[u][1], acc);
+          acc = fmaf(f1.x, sl[u][2], acc); acc = fmaf(f1.y, sl[u][3], acc);
+          acc = fmaf(f2.x, sl[u][4], acc); acc = fmaf(f2.y, sl[u][5], acc);
+          acc = fmaf(f3.x, sl[u][6], acc); acc = fmaf(f3.y, sl[u][7], acc);
+        } else {
+          const float4 f = *reinterpret_cast<const float4*>(&q);
+          acc = fmaf(f.x, sl[u][0], acc); acc = fmaf(f.y, sl[u][1], acc);
+          acc = fmaf(f.z, sl[u][2], acc); acc = fmaf(f.w, sl[u][3], acc);
+        }
+      }
+    }
+    __syncwarp();  // this warp has read its part of the slot
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s])) : "memory");
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) part[i][warp] = acc;
+    if (threadIdx.x == 0 && issued < nrow) {
+      // refill slot s with row `issued` once every warp has read row i
+      if (!bar_wait(&empty[s], par, RB_WAIT_LIMIT)) {
+        atomicOr(a.err, 4u);
+        abort_flag = 1;
+      } else {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(issued);
+        ++issued;
+      }
+    }
+  }
+  if (threadIdx.x == 0 && abort_flag) {
+    // the last requested row of each slot may still be in flight: let those copies land
+    // (an earlier row of a slot completed before the slot was refilled)
+    for (int i = max(0, issued - ns_slots); i < issued; ++i)
+      if (!bar_wait(&full[i % ns_slots], (uint32_t)(i / ns_slots) & 1u, RB_WAIT_LIMIT)) atomicOr(a.err, 2u);
+  }
+  __syncthreads();
+  if (writer && !abort_flag) {
+    const int m = r0 + threadIdx.x;
+    float tot = 0.f;
+#pragma unroll
+    for (int w = 0; w < RT_WARPS; ++w) tot += part[threadIdx.x][w];
+    const float dm = hold ? 0.f : (BF16 ? tot * a.scale[m] : tot);
+    if (a.dmodes) a.dmodes[m] = dm;
+    if (a.ring) {
+      const float cnew = hold ? prev : fmaf(a.gain ? a.gain[m] : 1.0f, dm, prev);
+      a.ring[(size_t)(t_step % a.delay) * a.n_m + m] = cnew;
+      if (a.cmd_last) a.cmd_last[m] = cnew;
+    }
+  }
+  if (a.step_inc) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      is_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (is_last && threadIdx.x == 0) {
+      *a.step_inc += 1;
+      *a.done = 0u;
+    }
+  }
+}
+
 static uint16_t f32_to_bf16_rne(float f) {
   uint32_t u;
   std::memcpy(&u, &f, 4);
@@ -330,7 +496,17 @@ pas_status recon_launch(pas_recon_t r, ReconArgs a, cudaStream_t st, bool pdl) {
   a.done = r->d_done;
   a.err = r->d_err;
   cudaError_t e;
-  if (r->n_slopes >= RECON_BULK_MIN_NS && (reinterpret_cast<uintptr_t>(a.s) & 15u) == 0) {
+  const size_t row_bytes = (size_t)r->n_s_pad * (r->prec == PAS_BF16 ? 2 : 4);
+  const bool aligned = (reinterpret_cast<uintptr_t>(a.s) & 15u) == 0;
+  if (r->rt_rows > 0 && aligned) {
+    const size_t smem = (size_t)r->rt_slots * row_bytes;
+    const int grid = (r->n_modes + r->rt_rows - 1) / r->rt_rows;
+    e = r->prec == PAS_BF16
+            ? launch_k(recon_tma_kernel<true>, dim3(grid), dim3(RT_WARPS * 32), smem, st, pdl, a, r->rt_rows,
+                       r->rt_slots, (int)row_bytes)
+            : launch_k(recon_tma_kernel<false>, dim3(grid), dim3(RT_WARPS * 32), smem, st, pdl, a, r->rt_rows,
+                       r->rt_slots, (int)row_bytes);
+  } else if (r->n_slopes >= RECON_BULK_MIN_NS && aligned) {
     const int grid = (r->n_modes + RB_WARPS - 1) / RB_WARPS;
     e = r->prec == PAS_BF16 ? launch_k(recon_bulk_kernel<true>, dim3(grid), dim3(RB_WARPS * 32), RB_SMEM, st, pdl, a)
                             : launch_k(recon_bulk_kernel<false>, dim3(grid), dim3(RB_WARPS * 32), RB_SMEM, st, pdl, a);
@@ -406,6 +582,22 @@ pas_status pas_recon_create(pas_ctx_t ctx, const float* h_R, int32_t n_modes, in
   if (st == PAS_OK && e == cudaSuccess)
     e = prec == PAS_BF16 ? pas::raise_dyn_smem((const void*)pas::recon_bulk_kernel<true>, pas::RB_SMEM)
                          : pas::raise_dyn_smem((const void*)pas::recon_bulk_kernel<false>, pas::RB_SMEM);
+  if (st == PAS_OK && e == cudaSuccess && n_slopes >= pas::RECON_BULK_MIN_NS && r->n_s_pad <= pas::RT_MAX_NS) {
+    // the TMA row pipeline: 2 to 4 row slots within the budget; rows per CTA so that
+    // every CTA is resident at once (the CTAs per SM the registers and slots allow)
+    const size_t rb = (size_t)r->n_s_pad * (prec == PAS_BF16 ? 2 : 4);
+    r->rt_slots = (int)std::max<size_t>(2, std::min<size_t>(4, pas::RT_SLOT_BUDGET / rb));
+    const void* kern = prec == PAS_BF16 ? (const void*)pas::recon_tma_kernel<true>
+                                        : (const void*)pas::recon_tma_kernel<false>;
+    e = pas::raise_dyn_smem(kern, r->rt_slots * rb);
+    int occ = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, pas::RT_WARPS * 32, r->rt_slots * rb);
+    if (e == cudaSuccess && occ > 0) {
+      const int slots_total = occ * std::max(1, ctx->sm_count);
+      r->rt_rows = std::min(pas::RT_MAX_ROWS, std::max(1, (n_modes + slots_total - 1) / slots_total));
+    }
+  }
   if (st != PAS_OK) {
     pas_recon_destroy(r);
     return st;

@@ -36,6 +36,7 @@ struct pas_recon_s {
   float* d_scale = nullptr;
   unsigned int* d_done = nullptr;
   unsigned int* d_err = nullptr;
+  int rt_rows = 0, rt_slots = 0;        // TMA row pipeline: rows per CTA (0: not used), row slots
 };
 
 namespace pas {

@@ -180,7 +180,10 @@ def test_bf16_dm_basis_within_rounding_of_oracle(env, Np, n_modes):
 @pytest.mark.parametrize("n_m,n_s", [(100, 416), (400, 1424), (37, 13), (4000, 14312),
                                      # long slope vectors (bulk-copy rows): ragged rows and
                                      # row counts, a last slot shorter than the others
-                                     (1001, 5001), (3, 4100), (257, 8192)])
+                                     (1001, 5001), (3, 4100), (257, 8192),
+                                     # beyond the register-held slopes of the row pipeline:
+                                     # the per-warp bulk-copy rings
+                                     (50, 20000)])
 def test_reconstructor_fp32_and_bf16(env, n_m, n_s):
     torch, pas, ctx = env
     R = random_matrix(n_m, n_s, 21, 1.0 / math.sqrt(n_s)).astype(np.float32)
