@@ -572,10 +572,12 @@ def bench_batched_workload(timed, n_steps=30):
     """The batched Monte-Carlo workload: 64 loops of three sizes (32 x 128 px with
     20x20 sub-apertures, 24 x 320 px with 60x60, 8 x 480 px with 96x96; 6.4, 5.33
     and 5 pixels per sub-aperture), each with its own screens (seed and r0 drawn
-    in 0.08-0.2 m), stepped by one graph launch per step. Per group one DM object
-    holds a random basis of the group's shape, every loop has a random bf16
-    reconstructor of its shape and the pyramid launch geometry is autotuned once:
-    timing only, the wavefront error is not meaningful."""
+    in 0.08-0.2 m), stepped by one graph launch per step. The loops of a group are
+    realisations of one system: they share one DM object (a random basis of the
+    group's shape) and one bf16 reconstructor object (random, of its shape), so the
+    batch reconstructs each group with one tensor-core product; the pyramid launch
+    geometry is autotuned once per group: timing only, the wavefront error is not
+    meaningful."""
     import numpy as np
     import torch
     from paper_1607_07624_gb300 import pas
@@ -592,10 +594,12 @@ def bench_batched_workload(timed, n_steps=30):
                 basis = torch.randn(pix.size, cfg.n_modes, device="cuda", generator=gen).cpu().numpy()
                 R = (torch.randn(cfg.n_modes, 2 * valid.size, device="cuda", generator=gen) * 1e-3).cpu().numpy()
                 shared[gi] = {"basis": basis, "R": R, "dm": pas.pas_dm_create(ctx, basis, cfg.Np, cfg.obs),
+                              "rec": pas.pas_recon_create(ctx, np.ascontiguousarray(R, dtype=np.float32),
+                                                          pas.PAS_BF16),
                               "tuning": True, "name": cfg.name, "count": 0, "n_valid": int(valid.size),
                               "n_modes": cfg.n_modes}
             sh = shared[gi]
-            sysl = SCAOSystem(cfg, basis=sh["basis"], R=sh["R"], dm=sh["dm"], recon_precision=pas.PAS_BF16,
+            sysl = SCAOSystem(cfg, basis=sh["basis"], R=sh["R"], dm=sh["dm"], rec=sh["rec"],
                               autotune=sh["tuning"], wfe_history=max(256, n_steps + 64))
             if sh["tuning"] is True:
                 sh["tuning"] = tuple(sysl.tuning)
@@ -608,10 +612,13 @@ def bench_batched_workload(timed, n_steps=30):
         ms = timed(lambda: pas.pas_batch_step(batch, ctx, 1), n_steps)
         groups = [{k: v for k, v in sh.items() if k in ("name", "count", "n_valid", "n_modes", "tuning")}
                   for sh in shared.values()]
+        pas.pas_batch_check(batch, ctx)
         return {"loops": len(systems), "groups": groups, "ms_per_batch_step": ms / n_steps,
                 "loop_steps_per_s": len(systems) * n_steps / (ms * 1e-3), "graph_launches_per_step": 1,
-                "kernels_per_step": pas.PAS_LOOP_KERNELS * len(systems),
-                "note": "random bases and reconstructors of the workload's shapes: timing only"}
+                "kernels_per_step": pas.pas_batch_kernels_per_step(batch),
+                "tensor_core_reconstruction_groups": pas.pas_batch_n_groups(batch),
+                "note": "random bases and reconstructors of the workload's shapes, shared within a group: "
+                        "timing only"}
     finally:
         if batch is not None:
             pas.pas_batch_destroy(batch)
@@ -620,6 +627,7 @@ def bench_batched_workload(timed, n_steps=30):
         torch.cuda.synchronize()
         for sh in shared.values():
             pas.pas_dm_destroy(sh["dm"])
+            pas.pas_recon_destroy(sh["rec"])
         pas.pas_ctx_destroy(ctx)
 
 

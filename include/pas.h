@@ -397,6 +397,17 @@ pas_status pas_batch_create(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, p
 pas_status pas_batch_step(pas_batch_t batch, int32_t n_steps);
 /* Number of loops, -1 for a NULL handle. Host only. */
 int32_t pas_batch_size(pas_batch_t batch);
+/* Loops of the batch that share one PAS_BF16 reconstructor object (one frame per step,
+ * no network) are reconstructed together: their slopes, as bf16, form the columns of S,
+ * and one tensor-core product C = R S^T (float32 accumulation) gives every loop's
+ * modal update, the integrator applied per loop in the product's epilogue (R is read
+ * once per step instead of once per loop). Groups of up to 128 loops, in loop order.
+ * pas_batch_n_groups: how many such groups; pas_batch_kernels_per_step: kernels one
+ * step launches; pas_batch_check: synchronous, PAS_ETIMEOUT if a product's bounded
+ * wait gave up since the last check (h_fault optional: the flag bits). */
+int32_t pas_batch_n_groups(pas_batch_t batch);
+int32_t pas_batch_kernels_per_step(pas_batch_t batch);
+pas_status pas_batch_check(pas_batch_t batch, uint32_t* h_fault);
 void pas_batch_destroy(pas_batch_t batch);
 
 /* -------------------------------------------------------------- PSF camera
@@ -571,7 +582,7 @@ pas_status pas_fp32_fma_probe(void* cuda_stream, float* d_sink, int32_t n_blocks
  * C[M][N] = A[M][K] * B[N][K]^T, A and B device bf16 (raw uint16 bits)
  * row-major with leading dimensions lda, ldb (multiples of 8, base 16-byte
  * aligned), C device float32 with leading dimension ldc; float32 accumulation.
- * tile_n: output tile width 64, 128 or 256, 0 = automatic. d_err: device
+ * tile_n: output tile width 16, 32, 64, 128 or 256, 0 = automatic. d_err: device
  * uint32 that receives a nonzero code if a pipeline wait timed out. */
 pas_status pas_gemm_bf16(pas_ctx_t ctx, int32_t M, int32_t N, int32_t K, const uint16_t* d_A,
                          int32_t lda, const uint16_t* d_B, int32_t ldb, float* d_C, int32_t ldc,

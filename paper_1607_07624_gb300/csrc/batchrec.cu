@@ -1,0 +1,157 @@
+// Batched reconstruction on the tensor cores: the loops of a batch that share one
+// bfloat16 reconstructor R (n_m x n_s, rows scaled to max |R| = 1) get their modal
+// updates from one product C = R S^T, S the B x n_s matrix of their slopes in
+// bfloat16, with float32 accumulation in tensor memory (gemm.cuh). The epilogue applies
+// each loop's integrator (c_t = c_{t-1} + g * scale_m * C[m][b], written into the loop's
+// command ring), so the per-loop matrix-vector products disappear from the step: R is
+// read once per step instead of B times.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "batchrec.cuh"
+#include "gemm.cuh"
+
+namespace pas {
+
+struct BatchRecGroup {
+  pas_ctx_t ctx = nullptr;
+  pas_recon_t rec = nullptr;
+  int B = 0;
+  __nv_bfloat16* d_S = nullptr;  // [B][n_s_pad]
+  void** d_ptrs = nullptr;       // the pointer arrays of BatchRecState, contiguous
+  int* d_delay = nullptr;
+  unsigned int* d_err = nullptr;
+  BatchRecState st;
+  GemmOp op;
+};
+
+// S[b][j] = bf16(s_b[j]) for j < n_s, 0 in the row padding.
+__global__ void gather_slopes_bf16_kernel(const float* const* slopes, int n_s, int n_s_pad, int B,
+                                          __nv_bfloat16* S) {
+  const size_t tot = (size_t)B * n_s_pad;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(t / n_s_pad), j = (int)(t - (size_t)b * n_s_pad);
+    S[t] = __float2bfloat16_rn(j < n_s ? slopes[b][j] : 0.f);
+  }
+}
+
+__global__ void advance_steps_kernel(long long* const* step, int B) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) *step[b] += 1;
+}
+
+// Epilogue: rows are modes, columns are loops.
+struct EpiBatchIntegrate {
+  BatchRecState st;
+  const float* scale;  // [n_m] per-row scale of the bf16 reconstructor
+  int n_m, B;
+  __device__ void store(int m, int col, const float (&v)[16]) const {
+    const float sc = scale[m];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int b = col + j;
+      if (b < B) {
+        const float dm = v[j] * sc;
+        const long long t = *st.step[b];
+        const int d = st.delay[b];
+        float* ring = st.ring[b];
+        const float prev = ring[(size_t)((t - 1 + d) % d) * n_m + m];
+        const float c = fmaf(st.gain[b][m], dm, prev);
+        ring[(size_t)(t % d) * n_m + m] = c;
+        st.cmd[b][m] = c;
+        st.dmodes[b][m] = dm;
+      }
+    }
+  }
+};
+
+static int pick_bn(int B) { return B <= 16 ? 16 : B <= 32 ? 32 : B <= 64 ? 64 : 128; }
+
+pas_status batch_rec_create(pas_ctx_t ctx, pas_recon_t rec, int B, const float* const* slopes, float* const* ring,
+                            const float* const* gain, float* const* cmd, float* const* dmodes,
+                            long long* const* step, const int* delay, BatchRecGroup** out) {
+  *out = nullptr;
+  PAS_CHECK_ARG(ctx, rec && rec->prec == PAS_BF16 && rec->d_Rb, "batched reconstruction: a bf16 reconstructor");
+  PAS_CHECK_ARG(ctx, B >= 1 && B <= 128, "batched reconstruction: 1 to 128 loops per group");
+  BatchRecGroup* g = new BatchRecGroup();
+  g->ctx = ctx;
+  g->rec = rec;
+  g->B = B;
+  pas_status s = dev_alloc(ctx, (void**)&g->d_S, sizeof(__nv_bfloat16) * (size_t)B * rec->n_s_pad);
+  if (s == PAS_OK) s = dev_alloc(ctx, (void**)&g->d_ptrs, sizeof(void*) * 6 * (size_t)B);
+  if (s == PAS_OK) s = dev_alloc(ctx, (void**)&g->d_delay, sizeof(int) * B);
+  if (s == PAS_OK) s = dev_alloc(ctx, (void**)&g->d_err, sizeof(unsigned int));
+  if (s != PAS_OK) {
+    batch_rec_destroy(g);
+    return s;
+  }
+  std::vector<void*> h(6 * (size_t)B);
+  for (int b = 0; b < B; ++b) {
+    h[0 * B + b] = const_cast<float*>(slopes[b]);
+    h[1 * B + b] = ring[b];
+    h[2 * B + b] = const_cast<float*>(gain[b]);
+    h[3 * B + b] = cmd[b];
+    h[4 * B + b] = dmodes[b];
+    h[5 * B + b] = step[b];
+  }
+  cudaError_t e = cudaMemcpy(g->d_ptrs, h.data(), sizeof(void*) * h.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_delay, delay, sizeof(int) * B, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(g->d_err, 0, sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    batch_rec_destroy(g);
+    return set_error(ctx, PAS_ECUDA, "batched reconstruction: %s", cudaGetErrorString(e));
+  }
+  g->st.slopes = reinterpret_cast<const float* const*>(g->d_ptrs);
+  g->st.ring = reinterpret_cast<float* const*>(g->d_ptrs + (size_t)B);
+  g->st.gain = reinterpret_cast<const float* const*>(g->d_ptrs + 2 * (size_t)B);
+  g->st.cmd = reinterpret_cast<float* const*>(g->d_ptrs + 3 * (size_t)B);
+  g->st.dmodes = reinterpret_cast<float* const*>(g->d_ptrs + 4 * (size_t)B);
+  g->st.step = reinterpret_cast<long long* const*>(g->d_ptrs + 5 * (size_t)B);
+  g->st.delay = g->d_delay;
+  // C[n_m][B] = R[n_m][n_s_pad] * S[B][n_s_pad]^T (both K-major, zero row padding)
+  const int K = rec->n_s_pad;
+  g->op.M = rec->n_modes;
+  g->op.N = B;
+  g->op.K = K;
+  g->op.bn = pick_bn(B);
+  if (!make_tmap_bf16(&g->op.a, rec->d_Rb, (uint64_t)rec->n_modes, (uint64_t)K, (uint64_t)K, 128) ||
+      !make_tmap_bf16(&g->op.b, g->d_S, (uint64_t)B, (uint64_t)K, (uint64_t)K, (uint32_t)g->op.bn)) {
+    batch_rec_destroy(g);
+    return set_error(ctx, PAS_EINVAL, "batched reconstruction: tensor map rejected");
+  }
+  *out = g;
+  return PAS_OK;
+}
+
+pas_status batch_rec_launch(BatchRecGroup* g, cudaStream_t st) {
+  const int n_s = g->rec->n_slopes, K = g->rec->n_s_pad;
+  const int blocks = (int)std::min<size_t>(1024, ((size_t)g->B * K + 255) / 256);
+  gather_slopes_bf16_kernel<<<blocks, 256, 0, st>>>(g->st.slopes, n_s, K, g->B, g->d_S);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    EpiBatchIntegrate ep{g->st, g->rec->d_scale, g->rec->n_modes, g->B};
+    e = gemm_launch(g->op, ep, st, g->d_err, false);
+  }
+  if (e == cudaSuccess) {
+    advance_steps_kernel<<<(g->B + 127) / 128, 128, 0, st>>>(g->st.step, g->B);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess)
+    return set_error(g->ctx, PAS_ECUDA, "batched reconstruction launch: %s", cudaGetErrorString(e));
+  return PAS_OK;
+}
+
+unsigned int* batch_rec_err(BatchRecGroup* g) { return g->d_err; }
+
+void batch_rec_destroy(BatchRecGroup* g) {
+  if (!g) return;
+  dev_free(g->d_S);
+  dev_free(g->d_ptrs);
+  dev_free(g->d_delay);
+  dev_free(g->d_err);
+  delete g;
+}
+
+}  // namespace pas

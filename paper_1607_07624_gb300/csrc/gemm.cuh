@@ -202,6 +202,10 @@ template <class Epi>
 cudaError_t gemm_launch(const GemmOp& op, const Epi& epi, cudaStream_t st, unsigned* err, bool pdl = false,
                         uint32_t wait_limit = tc::WAIT_LIMIT) {
   switch (op.bn) {
+    case 16:
+      return gemm_launch_bn<16, 8>(op, epi, st, err, pdl, wait_limit);
+    case 32:
+      return gemm_launch_bn<32, 8>(op, epi, st, err, pdl, wait_limit);
     case 64:
       return gemm_launch_bn<64, 6>(op, epi, st, err, pdl, wait_limit);
     case 256:

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "atmo_dm.cuh"
+#include "batchrec.cuh"
 #include "internal.h"
 #include "mlp.cuh"
 #include "pyr.cuh"
@@ -44,8 +45,9 @@ struct pas_loop_s {
 };
 
 // ev (optional): PAS_LOOP_KERNELS + 1 events recorded before each kernel and
-// after the last one.
-static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = nullptr) {
+// after the last one. skip_recon: stop after the slopes (a batch reconstructs the
+// loops that share a reconstructor together).
+static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = nullptr, bool skip_recon = false) {
   // residual = atmosphere - M c: the residual kernel samples the wind-shifted
   // layers at its pupil pixels while its other warps stream the basis
   pas_status s = PAS_OK;
@@ -80,6 +82,7 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   else
     s = pas::pyr_launch(L->pyr, L->d_opd, L->d_frame, L->d_slopes, st, &fa, false, ev ? ev + 1 : nullptr, pdl);
   if (s != PAS_OK) return s;
+  if (skip_recon) return PAS_OK;
   pas::ReconArgs rc;
   rc.s = L->d_slopes;
   rc.dmodes = L->d_dmodes;
@@ -386,6 +389,12 @@ struct pas_batch_s {
   cudaEvent_t fork = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // loops sharing one bfloat16 reconstructor: one tensor-core product per group
+  std::vector<std::vector<int>> groups;
+  std::vector<pas::BatchRecGroup*> rec_groups;
+  std::vector<cudaStream_t> group_streams;
+  std::vector<cudaEvent_t> group_join;
+  int kernels_per_step = 0;
 };
 
 void pas_batch_destroy(pas_batch_t b) {
@@ -396,6 +405,11 @@ void pas_batch_destroy(pas_batch_t b) {
     if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->join)
     if (e) cudaEventDestroy(e);
+  for (cudaStream_t s : b->group_streams)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->group_join)
+    if (e) cudaEventDestroy(e);
+  for (pas::BatchRecGroup* g : b->rec_groups) pas::batch_rec_destroy(g);
   if (b->fork) cudaEventDestroy(b->fork);
   delete b;
 }
@@ -422,8 +436,67 @@ pas_status pas_batch_create(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, p
     pas_batch_destroy(b);
     return pas::set_error(ctx, PAS_ECUDA, "pas_batch_create: %s", cudaGetErrorString(e));
   }
+  // loops that share a bfloat16 reconstructor (one frame per step, no network) are
+  // reconstructed together: group them by reconstructor, in loop order
+  std::vector<int> group_of(n_loops, -1);
+  for (int i = 0; i < n_loops; ++i) {
+    pas_loop_t L = b->loops[i];
+    if (group_of[i] >= 0 || L->mlp || L->n_int != 1 || L->rec->prec != PAS_BF16) continue;
+    std::vector<int> members{i};
+    for (int j = i + 1; j < n_loops; ++j) {
+      pas_loop_t M = b->loops[j];
+      if (M->rec == L->rec && !M->mlp && M->n_int == 1) members.push_back(j);
+    }
+    if (members.size() < 2) continue;
+    for (size_t q = 0; q < members.size(); q += 128) {  // at most 128 loops per product
+      std::vector<int> part(members.begin() + q, members.begin() + std::min(members.size(), q + 128));
+      if (part.size() < 2) continue;
+      for (int k : part) group_of[k] = (int)b->groups.size();
+      b->groups.push_back(part);
+    }
+  }
+  for (const std::vector<int>& grp : b->groups) {
+    std::vector<const float*> sl;
+    std::vector<float*> ring, cmd, dm;
+    std::vector<const float*> gain;
+    std::vector<long long*> step;
+    std::vector<int> delay;
+    for (int k : grp) {
+      pas_loop_t L = b->loops[k];
+      sl.push_back(L->d_slopes);
+      ring.push_back(L->d_ring);
+      gain.push_back(L->d_gain);
+      cmd.push_back(L->d_cmd);
+      dm.push_back(L->d_dmodes);
+      step.push_back(L->d_step);
+      delay.push_back(L->delay);
+    }
+    pas::BatchRecGroup* g = nullptr;
+    pas_status sg = pas::batch_rec_create(ctx, b->loops[grp[0]]->rec, (int)grp.size(), sl.data(), ring.data(),
+                                          gain.data(), cmd.data(), dm.data(), step.data(), delay.data(), &g);
+    if (sg != PAS_OK) {
+      pas_batch_destroy(b);
+      return sg;
+    }
+    b->rec_groups.push_back(g);
+    cudaStream_t gs = nullptr;
+    cudaEvent_t ge = nullptr;
+    e = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ge, cudaEventDisableTiming);
+    b->group_streams.push_back(gs);
+    b->group_join.push_back(ge);
+    if (e != cudaSuccess) {
+      pas_batch_destroy(b);
+      return pas::set_error(ctx, PAS_ECUDA, "pas_batch_create: %s", cudaGetErrorString(e));
+    }
+  }
+  b->kernels_per_step = 0;
+  for (int i = 0; i < n_loops; ++i)
+    b->kernels_per_step += (b->loops[i]->sh ? 3 : PAS_LOOP_KERNELS) - (group_of[i] >= 0 ? 1 : 0);
+  b->kernels_per_step += 3 * (int)b->groups.size();
   // one graph per step: every loop's step is a branch of its own (fork on the
-  // context's capture stream, one stream per loop, join back)
+  // context's capture stream, one stream per loop, join back); a group's product
+  // follows the slopes of all its loops on a stream of its own
   for (pas_loop_t L : b->loops) {
     cudaError_t s0 = cudaStreamSynchronize(L->ctx->stream);
     if (s0 != cudaSuccess) {
@@ -437,9 +510,17 @@ pas_status pas_batch_create(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, p
   if (e == cudaSuccess) e = cudaEventRecord(b->fork, cs);
   for (int i = 0; i < n_loops && e == cudaSuccess && st == PAS_OK; ++i) {
     e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
-    if (e == cudaSuccess) st = loop_enqueue(b->loops[i], b->streams[i]);
+    if (e == cudaSuccess) st = loop_enqueue(b->loops[i], b->streams[i], nullptr, group_of[i] >= 0);
     if (e == cudaSuccess && st == PAS_OK) e = cudaEventRecord(b->join[i], b->streams[i]);
-    if (e == cudaSuccess && st == PAS_OK) e = cudaStreamWaitEvent(cs, b->join[i], 0);
+    if (e == cudaSuccess && st == PAS_OK && group_of[i] < 0) e = cudaStreamWaitEvent(cs, b->join[i], 0);
+  }
+  for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess && st == PAS_OK; ++gi) {
+    cudaStream_t gs = b->group_streams[gi];
+    for (int k : b->groups[gi])
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(gs, b->join[k], 0);
+    if (e == cudaSuccess) st = pas::batch_rec_launch(b->rec_groups[gi], gs);
+    if (e == cudaSuccess && st == PAS_OK) e = cudaEventRecord(b->group_join[gi], gs);
+    if (e == cudaSuccess && st == PAS_OK) e = cudaStreamWaitEvent(cs, b->group_join[gi], 0);
   }
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(cs, &g);
@@ -463,5 +544,23 @@ pas_status pas_batch_step(pas_batch_t b, int32_t n_steps) {
 }
 
 int32_t pas_batch_size(pas_batch_t b) { return b ? (int32_t)b->loops.size() : -1; }
+
+int32_t pas_batch_kernels_per_step(pas_batch_t b) { return b ? b->kernels_per_step : -1; }
+
+int32_t pas_batch_n_groups(pas_batch_t b) { return b ? (int32_t)b->groups.size() : -1; }
+
+pas_status pas_batch_check(pas_batch_t b, uint32_t* h_fault) {
+  if (!b) return pas::set_global_error(PAS_EINVAL, "pas_batch_check: NULL batch");
+  unsigned int f = 0;
+  for (pas::BatchRecGroup* g : b->rec_groups) {
+    unsigned int x = 0;
+    PAS_CUDA_TRY(b->ctx, cudaMemcpy(&x, pas::batch_rec_err(g), sizeof(x), cudaMemcpyDeviceToHost));
+    f |= x;
+    if (x) PAS_CUDA_TRY(b->ctx, cudaMemset(pas::batch_rec_err(g), 0, sizeof(unsigned int)));
+  }
+  if (h_fault) *h_fault = f;
+  if (f) return pas::set_error(b->ctx, PAS_ETIMEOUT, "batched reconstruction: a product's wait gave up (%u)", f);
+  return PAS_OK;
+}
 
 }  // extern "C"

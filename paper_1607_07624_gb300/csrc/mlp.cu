@@ -989,8 +989,8 @@ pas_status pas_gemm_bf16_waits(pas_ctx_t ctx, int32_t M, int32_t N, int32_t K, c
   PAS_CHECK_ARG(ctx, M >= 1 && N >= 1 && K >= 1 && lda >= K && ldb >= K && ldc >= N,
                 "pas_gemm_bf16: M, N, K >= 1, lda, ldb >= K, ldc >= N");
   PAS_CHECK_ARG(ctx, lda % 8 == 0 && ldb % 8 == 0, "pas_gemm_bf16: lda and ldb must be multiples of 8");
-  PAS_CHECK_ARG(ctx, tile_n == 0 || tile_n == 64 || tile_n == 128 || tile_n == 256,
-                "pas_gemm_bf16: tile_n in {0 (automatic), 64, 128, 256}");
+  PAS_CHECK_ARG(ctx, tile_n == 0 || tile_n == 16 || tile_n == 32 || tile_n == 64 || tile_n == 128 || tile_n == 256,
+                "pas_gemm_bf16: tile_n in {0 (automatic), 16, 32, 64, 128, 256}");
   pas::GemmOp op;
   if (!pas::gemm_prepare(&op, reinterpret_cast<const __nv_bfloat16*>(d_A), lda,
                          reinterpret_cast<const __nv_bfloat16*>(d_B), ldb, M, N, K, ctx->sm_count))

@@ -142,6 +142,9 @@ _SIGS = {
     "pas_sh_destroy": (None, [vp]),
     "pas_fp32_fma_probe": (C.c_int, [vp, vp, i32, i32, C.POINTER(C.c_int64)]),
     "pas_recon_check": (C.c_int, [vp, C.POINTER(C.c_uint32)]),
+    "pas_batch_n_groups": (i32, [vp]),
+    "pas_batch_kernels_per_step": (i32, [vp]),
+    "pas_batch_check": (C.c_int, [vp, C.POINTER(C.c_uint32)]),
     "pas_calib_interaction_matrix": (C.c_int, [vp, vp, vp, C.c_double, vp]),
     "pas_pinv_f64": (C.c_int, [vp, vp, i32, i32, C.c_double, vp, vp, C.POINTER(i32), C.POINTER(i32)]),
     "pas_gemm_f64": (C.c_int, [vp, vp, C.c_int64, C.c_int64, vp, C.c_int64, C.c_int64, vp, i32, i32, i32, vp,
@@ -712,4 +715,19 @@ def pas_recon_check(rec, ctx):
     """Raise PasError(PAS_ETIMEOUT) if a bounded wait of the reconstructor gave up."""
     f = C.c_uint32()
     _check(_lib.pas_recon_check(rec, C.byref(f)), ctx)
+    return f.value
+
+
+def pas_batch_n_groups(batch) -> int:
+    """Groups of loops reconstructed together (shared bf16 reconstructor)."""
+    return int(_lib.pas_batch_n_groups(batch))
+
+
+def pas_batch_kernels_per_step(batch) -> int:
+    return int(_lib.pas_batch_kernels_per_step(batch))
+
+
+def pas_batch_check(batch, ctx):
+    f = C.c_uint32()
+    _check(_lib.pas_batch_check(batch, C.byref(f)), ctx)
     return f.value

@@ -52,7 +52,7 @@ class SCAOSystem:
     (pas_pyr_create_extended; calib.disc_source builds a uniform disc)."""
 
     def __init__(self, cfg, screens=None, basis=None, R=None, recon_precision=P.PAS_FP32, dm_precision=P.PAS_FP32,
-                 dm=None,
+                 dm=None, rec=None,
                  noise=None, delay=None, wfe_history=4096, stream=None, build_loop=True,
                  autotune=True, sensor="pyramid", sh_ovs=2, source=None, detector_steps=1,
                  extended_source=None):
@@ -135,7 +135,10 @@ class SCAOSystem:
         if R is None:
             R = self.calibrate_reconstructor()
         self.R = np.ascontiguousarray(R, dtype=np.float32)
-        self.rec = P.pas_recon_create(self.ctx, self.R, recon_precision)
+        # a reconstructor object holds only R: loops of one system may share one (rec=),
+        # and a batch then reconstructs them together with one tensor-core product
+        self.own_rec = rec is None
+        self.rec = P.pas_recon_create(self.ctx, self.R, recon_precision) if rec is None else rec
         self.d_gain = torch.full((self.n_modes,), cfg.gain, **f32)
         # launch geometry of the pyramid kernels, measured on the open-loop OPD
         self.tuning = P.pas_pyr_get_tuning(self.pyr, self.ctx) if self.pyr else None
@@ -281,7 +284,8 @@ class SCAOSystem:
         if getattr(self, "ctx", None):
             self.detach_camera()
         dm = getattr(self, "dm", None) if getattr(self, "own_dm", True) else None
-        for h, f in ((getattr(self, "loop", None), P.pas_loop_destroy), (getattr(self, "rec", None), P.pas_recon_destroy),
+        rec = getattr(self, "rec", None) if getattr(self, "own_rec", True) else None
+        for h, f in ((getattr(self, "loop", None), P.pas_loop_destroy), (rec, P.pas_recon_destroy),
                      (dm, P.pas_dm_destroy), (getattr(self, "pyr", None), P.pas_pyr_destroy),
                      (getattr(self, "sh", None), P.pas_sh_destroy),
                      (getattr(self, "atmo", None) if getattr(self, "source", None) is not None else None,

@@ -63,3 +63,52 @@ def test_batch_rejects_duplicates_and_null():
             pas.pas_batch_create(s.ctx, [])
     finally:
         s.close()
+
+
+def test_loops_sharing_a_bf16_reconstructor_get_one_tensor_core_product():
+    """Five realisations of the 64 px workload share one bf16 reconstructor object: the
+    batch reconstructs them with one tensor-core product (R S^T, float32 accumulation)
+    and the integrator in its epilogue. After one step each loop's modal update equals
+    R s for its own slopes (FP64, the bf16 reconstructor's rounding: 1 % of the RMS),
+    and over 40 steps the loops follow the same loops stepped alone with their own
+    bf16 matrix-vector product (per-step WFE within 1 nm)."""
+    import torch
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    cfg = with_(get_config("scao_8m_64px"), K=24)   # the 64 px optics in their settling setting
+    first = SCAOSystem(cfg, autotune=False, wfe_history=64, recon_precision=pas.PAS_BF16)
+    systems, alone, batch = [first], [], None
+    try:
+        for seed in (2001, 2002, 2003, 2004):
+            systems.append(SCAOSystem(with_(cfg, seed=seed), basis=first.basis, R=first.R, rec=first.rec,
+                                      autotune=False, wfe_history=64))
+        for s in systems:   # the same loops, each with a reconstructor of its own
+            alone.append(SCAOSystem(s.cfg, basis=first.basis, R=first.R, recon_precision=pas.PAS_BF16,
+                                    autotune=False, wfe_history=64))
+        ctx = first.ctx
+        batch = pas.pas_batch_create(ctx, [s.loop for s in systems])
+        assert pas.pas_batch_n_groups(batch) == 1
+        assert pas.pas_batch_kernels_per_step(batch) == 5 * 4 + 3
+        pas.pas_batch_step(batch, ctx, 1)
+        torch.cuda.synchronize()
+        assert pas.pas_batch_check(batch, ctx) == 0
+        R = first.R.astype(np.float64)
+        for s in systems:
+            st, _ = pas.pas_loop_step(s.loop, s.ctx, 0, stats=True)
+            assert st == 1
+            ref = R @ s.loop_slopes.cpu().numpy().astype(np.float64)
+            got = s.loop_dmodes.cpu().numpy().astype(np.float64)
+            assert np.sqrt(np.mean((got - ref) ** 2)) <= 0.01 * np.sqrt(np.mean(ref ** 2))
+            # the integrator: command = gain x update after one step from zero
+            assert np.allclose(s.loop_cmd.cpu().numpy(), cfg.gain * s.loop_dmodes.cpu().numpy(), rtol=1e-6,
+                               atol=1e-6)
+        pas.pas_batch_step(batch, ctx, 39)
+        torch.cuda.synchronize()
+        for s, a in zip(systems, alone):
+            a.step(40)
+            assert np.max(np.abs(s.wfe_nm(40) - a.wfe_nm(40))) <= 1.0
+    finally:
+        if batch is not None:
+            pas.pas_batch_destroy(batch)
+        for s in alone + systems[1:] + systems[:1]:
+            s.close()

@@ -65,6 +65,8 @@ def slopes_like(n, B, seed):
 @pytest.mark.parametrize("M,N,K,tile", [(128, 128, 64, 0), (128, 64, 64, 64), (200, 72, 100, 0),
                                         (64, 16, 8, 64), (300, 400, 1024, 256), (1024, 1024, 1424, 0),
                                         (513, 1000, 2000, 128),
+                                        # narrow tiles (the batched reconstruction: a few loops)
+                                        (400, 8, 1424, 16), (3578, 24, 14312, 32), (300, 5, 72, 16),
                                         # many waves of 128 x 256 tiles in the grouped order (odd row-tile
                                         # count, ragged N)
                                         (4096, 4096, 512, 0), (4224, 4000, 520, 0)])
