@@ -605,18 +605,26 @@ def bench_batched_workload(timed, n_steps=30):
                 sh["tuning"] = tuple(sysl.tuning)
             sh["count"] += 1
             systems.append(sysl)
-        batch = pas.pas_batch_create(ctx, [s.loop for s in systems])
-        pas.pas_batch_step(batch, ctx, 3)
-        for s in systems:
-            s.set_state(0, np.zeros((s.delay, s.n_modes), np.float32))
-        ms = timed(lambda: pas.pas_batch_step(batch, ctx, 1), n_steps)
+        modes = {}
+        for name, flags in (("graph_branches", 0), ("persistent", pas.PAS_BATCH_PERSISTENT)):
+            batch = pas.pas_batch_create_ex(ctx, [s.loop for s in systems], flags)
+            pas.pas_batch_step(batch, ctx, 3)
+            for s in systems:
+                s.set_state(0, np.zeros((s.delay, s.n_modes), np.float32))
+            ms = timed(lambda: pas.pas_batch_step(batch, ctx, 1), n_steps)
+            pas.pas_batch_check(batch, ctx)
+            modes[name] = {"ms_per_batch_step": ms / n_steps,
+                           "loop_steps_per_s": len(systems) * n_steps / (ms * 1e-3),
+                           "kernels_per_step": pas.pas_batch_kernels_per_step(batch),
+                           "persistent_launches_per_step": pas.pas_batch_n_persistent(batch),
+                           "tensor_core_reconstruction_groups": pas.pas_batch_n_groups(batch)}
+            pas.pas_batch_destroy(batch)
+            batch = None
+        best = max(modes, key=lambda k: modes[k]["loop_steps_per_s"])
         groups = [{k: v for k, v in sh.items() if k in ("name", "count", "n_valid", "n_modes", "tuning")}
                   for sh in shared.values()]
-        pas.pas_batch_check(batch, ctx)
-        return {"loops": len(systems), "groups": groups, "ms_per_batch_step": ms / n_steps,
-                "loop_steps_per_s": len(systems) * n_steps / (ms * 1e-3), "graph_launches_per_step": 1,
-                "kernels_per_step": pas.pas_batch_kernels_per_step(batch),
-                "tensor_core_reconstruction_groups": pas.pas_batch_n_groups(batch),
+        return {"loops": len(systems), "groups": groups, "mode": best, **modes[best],
+                "graph_launches_per_step": 1, "modes": modes,
                 "note": "random bases and reconstructors of the workload's shapes, shared within a group: "
                         "timing only"}
     finally:

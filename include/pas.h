@@ -391,8 +391,29 @@ const char* pas_loop_kernel_name(int32_t idx);
  * state, buffers and statistics (pas_loop_step(loop, 0, &stats) reads them) and
  * must not be stepped, re-configured (pas_loop_set_mlp, pas_loop_set_integration) or destroyed while the
  * batch exists. Creation synchronises every loop's stream and captures the graph
- * on `ctx`'s private stream; steps run on `ctx`'s stream. */
+ * on `ctx`'s private stream; steps run on `ctx`'s stream. Two loops of a batch may
+ * share atmosphere, DM and reconstructor objects but not a sensor object (PAS_EINVAL).
+ * Loops that share one DM object (realisations of one system) and whose sources are at
+ * infinity get their residuals from one pass over the basis per step: the commands of
+ * the group are gathered, then each CTA streams one tile of the basis once for up to
+ * 8 (bf16 basis: 4) loops; each loop's residual and WFE equal those of its own
+ * residual kernel, bit for bit (pas_batch_n_residual_groups). */
 pas_status pas_batch_create(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, pas_batch_t* out);
+/* pas_batch_create with flags. PAS_BATCH_PERSISTENT: the pyramid loops' rows and
+ * columns passes run as one persistent launch per transform length instead of two
+ * launches per loop. Its CTAs (as many as the SMs hold) draw tasks from one queue:
+ * every loop's rows-pass tasks (a group of pupil rows x a chunk of the sin values),
+ * then every loop's columns-pass tasks (a detector column x a group of modulation
+ * points x a column part), each task one CTA of the loop's own launches, so every
+ * frame, slope and command equals that of the loop stepped alone, bit for bit. A
+ * columns task starts once its loop's rows pass is complete; that wait is bounded
+ * (pas_batch_set_wait_limit): when it runs out the task transforms nothing, the
+ * launch still completes and pas_batch_check returns PAS_ETIMEOUT. The residuals run
+ * first (one kernel per loop), the slopes and reconstructions after the launch;
+ * Shack-Hartmann loops are stepped whole beside it. */
+#define PAS_BATCH_PERSISTENT 1u
+pas_status pas_batch_create_ex(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, uint32_t flags,
+                               pas_batch_t* out);
 /* n_steps >= 0 steps of every loop of the batch, asynchronous. */
 pas_status pas_batch_step(pas_batch_t batch, int32_t n_steps);
 /* Number of loops, -1 for a NULL handle. Host only. */
@@ -407,7 +428,25 @@ int32_t pas_batch_size(pas_batch_t batch);
  * wait gave up since the last check (h_fault optional: the flag bits). */
 int32_t pas_batch_n_groups(pas_batch_t batch);
 int32_t pas_batch_kernels_per_step(pas_batch_t batch);
+/* h_fault bit 8 (0x100): a persistent launch's wait gave up; PAS_ETIMEOUT then too. */
 pas_status pas_batch_check(pas_batch_t batch, uint32_t* h_fault);
+/* Persistent launches per step (one per transform length), 0 for a batch created
+ * without PAS_BATCH_PERSISTENT, -1 for a NULL handle. Host only. */
+int32_t pas_batch_n_persistent(pas_batch_t batch);
+/* Groups of loops sharing a DM object whose residuals are computed together; -1 for a
+ * NULL handle. Host only. */
+int32_t pas_batch_n_residual_groups(pas_batch_t batch);
+/* Polls (about 0.3 us each) a columns task makes for its loop's rows pass before it
+ * gives up; default 2^21 (about a second). Synchronises `ctx`'s stream. PAS_EINVAL for
+ * a batch without persistent launches or a negative limit. */
+pas_status pas_batch_set_wait_limit(pas_batch_t batch, int64_t polls);
+/* Diagnostic of those waits: one persistent launch with the rows pass withheld, so that
+ * every columns task waits for a count nothing advances, gives up after the wait limit
+ * and transforms nothing. Synchronous; returns what pas_batch_check returns after it
+ * (PAS_ETIMEOUT, h_fault bit 8). The loops' frames and slopes buffers, and the
+ * accumulated frame of an integrating detector, are left undefined; their step counters,
+ * commands and statistics are untouched. */
+pas_status pas_batch_probe_waits(pas_batch_t batch, uint32_t* h_fault);
 void pas_batch_destroy(pas_batch_t batch);
 
 /* -------------------------------------------------------------- PSF camera

@@ -444,6 +444,272 @@ pas_status dm_project_launch(pas_dm_t dm, const float* opd, float* coeffs, cudaS
   return check_launch(dm->ctx, "modal projection launch");
 }
 
+
+// ------------------------------------------------------------ batched residual
+// The residuals of B loops that share one DM (realisations of one system): one pass
+// over the basis serves them all. CTA (chunk, tile): the tile's basis block is
+// streamed once for BC loops, each thread keeping BC x VEC accumulators; the
+// chunks of a tile are neighbouring CTAs and share the block through L2. Per loop
+// and pixel the arithmetic is that of residual_kernel (the same thread's modes in
+// the same order, the same fused multiply-adds, the same sum over the ROWS partials,
+// the same atmosphere taps and tile WFE sums), so every loop's residual and WFE
+// partials equal those of its own residual kernel, bit for bit.
+constexpr int RB_U = 6;  // basis loads in flight per thread
+
+template <typename T>
+__host__ __device__ constexpr int res_batch_bc() { return sizeof(T) == 4 ? 8 : 4; }  // BC x VEC = 32 accumulators
+
+// cmdg[m][b] = the command that loop b's residual subtracts at its current step
+// (slot step % delay of its ring); 0 in the padding columns.
+__global__ void gather_cmds_kernel(const ResBatchLoop* loops, int B, int Bp, int n_m, float* cmdg) {
+  pdl_trigger();
+  const int tot = n_m * Bp;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
+    const int m = t / Bp, b = t - m * Bp;
+    float c = 0.f;
+    if (b < B) {
+      const ResBatchLoop& L = loops[b];
+      const long long step = *L.d_step;
+      c = L.cmd_ring[(size_t)(step % L.delay) * n_m + m];
+    }
+    cmdg[t] = c;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RES_THREADS, 3) residual_batch_kernel(ResBatchArgs a) {
+  constexpr int VEC = 16 / (int)sizeof(T);
+  constexpr int COLS = RES_TILE / VEC;
+  constexpr int ROWS = RES_THREADS / COLS;
+  constexpr int BC = res_batch_bc<T>();
+  extern __shared__ float taps[];                  // [BC][Lmax][4][RES_TILE]
+  __shared__ float red[BC][ROWS][RES_TILE];
+  __shared__ int s_flat[RES_TILE];
+  __shared__ double wred[BC][2][RES_TILE / 32];
+  __shared__ int six[BC][PAS_MAX_LAYERS], siy[BC][PAS_MAX_LAYERS];
+  __shared__ float sfx[BC][PAS_MAX_LAYERS], sfy[BC][PAS_MAX_LAYERS];
+  __shared__ int s_L[BC];
+  const int tid = threadIdx.x;
+  const T* MT = nullptr;
+  if constexpr (sizeof(T) == 4) MT = a.MT;
+  else MT = a.MTb;
+  const int n_m = a.n_m;
+  const int col = tid % COLS, row = tid / COLS;
+  const int tile = blockIdx.y, b0 = blockIdx.x * BC;
+  const int nb = min(BC, a.B - b0);
+  const T* blk = MT + (size_t)tile * n_m * RES_TILE + col * VEC;
+  uint4 v[RB_U];
+#pragma unroll
+  for (int u = 0; u < RB_U; ++u) {
+    const int m = row + ROWS * u;
+    v[u] = m < n_m ? ld_stream16(blk + (size_t)m * RES_TILE) : make_uint4(0u, 0u, 0u, 0u);
+  }
+  const int base = tile * RES_TILE;
+  if (tid < RES_TILE) s_flat[tid] = base + tid < a.n_pix ? a.pix[base + tid] : 0;
+  pdl_trigger();
+  pdl_wait();  // the gathered commands
+  const int Lmax = a.Lmax;
+  for (int t = tid; t < BC * PAS_MAX_LAYERS; t += RES_THREADS) {
+    const int b = t / PAS_MAX_LAYERS, l = t - b * PAS_MAX_LAYERS;
+    if (b < nb) {
+      const AtmoArgs& at = a.loops[b0 + b].atmo;
+      if (l == 0) s_L[b] = at.L;
+      if (l < at.L) {
+        const long long step = *a.loops[b0 + b].d_step;
+        layer_shift(at.vx[l], at.ox[l], step, at.S, &six[b][l], &sfx[b][l]);
+        layer_shift(at.vy[l], at.oy[l], step, at.S, &siy[b][l], &sfy[b][l]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < nb * Lmax * RES_TILE; t += RES_THREADS) {
+    const int bl = t / RES_TILE, q = t - bl * RES_TILE;
+    const int b = bl / Lmax, l = bl - b * Lmax;
+    if (l < s_L[b] && base + q < a.n_pix) {
+      const AtmoArgs& at = a.loops[b0 + b].atmo;
+      const int flat = s_flat[q];
+      const int i = flat / at.Np, j = flat - i * at.Np;
+      size_t o[4];
+      tap_offsets(i, j, six[b][l], siy[b][l], at.S, o);
+      const float* sc = at.screens + (size_t)l * at.S * at.S;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cp_async4(taps + ((b * Lmax + l) * 4 + k) * RES_TILE + q, sc + o[k]);
+    }
+  }
+  cp_async_commit();
+  float acc[BC][VEC];
+#pragma unroll
+  for (int b = 0; b < BC; ++b)
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) acc[b][i] = 0.f;
+  const float* cg = a.cmdg + b0;
+  for (int mb = row; mb < n_m; mb += ROWS * RB_U) {
+#pragma unroll
+    for (int u = 0; u < RB_U; ++u) {
+      const int m = mb + ROWS * u;
+      if (m < n_m) {
+        float cm[BC];
+#pragma unroll
+        for (int k = 0; k < BC / 4; ++k) {
+          const float4 c4 = __ldg(reinterpret_cast<const float4*>(cg + (size_t)m * a.Bp) + k);
+          cm[4 * k] = c4.x;
+          cm[4 * k + 1] = c4.y;
+          cm[4 * k + 2] = c4.z;
+          cm[4 * k + 3] = c4.w;
+        }
+        float f[VEC];
+        unpack16<T>(v[u], f);
+#pragma unroll
+        for (int b = 0; b < BC; ++b)
+#pragma unroll
+          for (int i = 0; i < VEC; ++i) acc[b][i] = fmaf(cm[b], f[i], acc[b][i]);
+      }
+      const int mn = m + ROWS * RB_U;
+      if (mn < n_m) v[u] = ld_stream16(blk + (size_t)mn * RES_TILE);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < BC; ++b)
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) red[b][row][col * VEC + i] = acc[b][i];
+  cp_async_wait_all();
+  __syncthreads();
+  for (int t = tid; t < nb * Lmax * RES_TILE; t += RES_THREADS) {
+    const int bl = t / RES_TILE, q = t - bl * RES_TILE;
+    const int b = bl / Lmax, l = bl - b * Lmax;
+    if (l < s_L[b] && base + q < a.n_pix) {
+      float* tp = taps + (b * Lmax + l) * 4 * RES_TILE + q;
+      tp[0] = bilinear(sfx[b][l], sfy[b][l], tp[0], tp[RES_TILE], tp[2 * RES_TILE], tp[3 * RES_TILE]);
+    }
+  }
+  __syncthreads();
+  // output: thread t of a round takes loop t / RES_TILE, pixel t % RES_TILE (the
+  // warps of one loop's tile in the order of residual_kernel's output warps)
+  constexpr int PER_ROUND = RES_THREADS / RES_TILE;
+  for (int r0 = 0; r0 < BC; r0 += PER_ROUND) {
+    const int b = r0 + tid / RES_TILE, px = tid % RES_TILE;
+    const int p = base + px;
+    float s1 = 0.f, s2 = 0.f;
+    if (b < nb && p < a.n_pix) {
+      const ResBatchLoop& L = a.loops[b0 + b];
+      const int flat = s_flat[px];
+      float atm = 0.f;
+      for (int l = 0; l < s_L[b]; ++l) atm = __fadd_rn(atm, taps[(b * Lmax + l) * 4 * RES_TILE + px]);
+      float dm = 0.f;
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) dm += red[b][r][px];
+      const float rr = atm - dm;
+      L.out[flat] = rr;
+      s1 = rr;
+      s2 = rr * rr;
+    }
+    const int w = px >> 5, lane = tid & 31;
+    float f1 = s1, f2 = s2;
+    for (int o = 16; o > 0; o >>= 1) {
+      f1 += __shfl_down_sync(0xffffffffu, f1, o);
+      f2 += __shfl_down_sync(0xffffffffu, f2, o);
+    }
+    if (lane == 0 && b < BC) {
+      wred[b][0][w] = f1;
+      wred[b][1][w] = f2;
+    }
+  }
+  __syncthreads();
+  if (tid < nb) {
+    const ResBatchLoop& L = a.loops[b0 + tid];
+    if (L.wfe_part) {
+      double t1 = 0.0, t2 = 0.0;
+      for (int w = 0; w < RES_TILE / 32; ++w) {
+        t1 += wred[tid][0][w];
+        t2 += wred[tid][1][w];
+      }
+      L.wfe_part[tile] = make_double2(t1, t2);
+    }
+  }
+}
+
+struct ResBatch {
+  pas_ctx_t ctx = nullptr;
+  ResBatchArgs args{};
+  ResBatchLoop* d_loops = nullptr;
+  float* d_cmdg = nullptr;
+  int chunks = 0, tiles = 0;
+  size_t smem = 0;
+  bool bf16 = false;
+};
+
+void res_batch_destroy(ResBatch* r) {
+  if (!r) return;
+  dev_free(r->d_loops);
+  dev_free(r->d_cmdg);
+  delete r;
+}
+
+bool res_batch_ok(const AtmoArgs& atmo) { return !atmo.cone && atmo.L >= 0 && atmo.L <= PAS_MAX_LAYERS; }
+
+pas_status res_batch_create(pas_ctx_t ctx, pas_dm_t dm, int B, const ResBatchLoop* loops, ResBatch** out) {
+  *out = nullptr;
+  PAS_CHECK_ARG(ctx, dm && B >= 1, "batched residual: a DM and at least one loop");
+  int Lmax = 0;
+  for (int b = 0; b < B; ++b) {
+    PAS_CHECK_ARG(ctx, res_batch_ok(loops[b].atmo), "batched residual: on-axis or off-axis sources at infinity");
+    PAS_CHECK_ARG(ctx, loops[b].atmo.L == 0 || loops[b].atmo.Np == dm->Np, "batched residual: pupil sizes differ");
+    PAS_CHECK_ARG(ctx, loops[b].cmd_ring && loops[b].d_step && loops[b].out && loops[b].delay >= 1,
+                  "batched residual: loop buffers");
+    Lmax = std::max(Lmax, loops[b].atmo.L);
+  }
+  ResBatch* r = new ResBatch();
+  r->ctx = ctx;
+  r->bf16 = dm->d_MTb != nullptr;
+  const int BC = r->bf16 ? res_batch_bc<__nv_bfloat16>() : res_batch_bc<float>();
+  r->chunks = (B + BC - 1) / BC;
+  r->tiles = residual_tiles(dm->n_pix);
+  const int Bp = r->chunks * BC;
+  pas_status st = dev_alloc(ctx, (void**)&r->d_loops, sizeof(ResBatchLoop) * B);
+  if (st == PAS_OK) st = dev_alloc(ctx, (void**)&r->d_cmdg, sizeof(float) * (size_t)std::max(dm->n_modes, 1) * Bp);
+  if (st != PAS_OK) {
+    res_batch_destroy(r);
+    return st;
+  }
+  cudaError_t e = cudaMemcpy(r->d_loops, loops, sizeof(ResBatchLoop) * B, cudaMemcpyHostToDevice);
+  ResBatchArgs& a = r->args;
+  a.MT = dm->d_MT;
+  a.MTb = dm->d_MTb;
+  a.pix = dm->d_pix;
+  a.n_pix = dm->n_pix;
+  a.n_m = dm->n_modes;
+  a.loops = r->d_loops;
+  a.B = B;
+  a.Bp = Bp;
+  a.cmdg = r->d_cmdg;
+  a.Lmax = Lmax;
+  r->smem = sizeof(float) * (size_t)BC * Lmax * 4 * RES_TILE;
+  if (e == cudaSuccess)
+    e = r->bf16 ? raise_dyn_smem((const void*)residual_batch_kernel<__nv_bfloat16>, r->smem)
+                : raise_dyn_smem((const void*)residual_batch_kernel<float>, r->smem);
+  if (e != cudaSuccess) {
+    res_batch_destroy(r);
+    return set_error(ctx, PAS_ECUDA, "batched residual: %s", cudaGetErrorString(e));
+  }
+  *out = r;
+  return PAS_OK;
+}
+
+pas_status res_batch_launch(ResBatch* r, cudaStream_t st) {
+  if (r->tiles == 0) return PAS_OK;
+  const ResBatchArgs& a = r->args;
+  const int tot = std::max(a.n_m, 1) * a.Bp;
+  cudaError_t e = launch_k(gather_cmds_kernel, dim3(std::min(1024, (tot + 255) / 256)), dim3(256), 0, st, false,
+                           (const ResBatchLoop*)a.loops, a.B, a.Bp, a.n_m, r->d_cmdg);
+  if (e == cudaSuccess) {
+    const dim3 grid(r->chunks, r->tiles);
+    e = r->bf16 ? launch_k(residual_batch_kernel<__nv_bfloat16>, grid, dim3(RES_THREADS), r->smem, st, true, a)
+                : launch_k(residual_batch_kernel<float>, grid, dim3(RES_THREADS), r->smem, st, true, a);
+  }
+  if (e != cudaSuccess) return set_error(r->ctx, PAS_ECUDA, "batched residual launch: %s", cudaGetErrorString(e));
+  return PAS_OK;
+}
+
 }  // namespace pas
 
 // ------------------------------------------------------------------ objects

@@ -37,6 +37,36 @@ struct ResArgs {
   double2* wfe_part = nullptr;     // per-CTA (sum r, sum r^2) or null
 };
 
+// One loop of a batched residual (loops sharing one DM object).
+struct ResBatchLoop {
+  AtmoArgs atmo;                    // on-axis or off-axis source at infinity (no cone)
+  const float* cmd_ring = nullptr;  // [delay][n_m]: slot step % delay is subtracted
+  int delay = 1;
+  const long long* d_step = nullptr;
+  float* out = nullptr;             // [Np][Np], pupil pixels written
+  double2* wfe_part = nullptr;      // [tiles] (sum r, sum r^2) or null
+};
+
+struct ResBatchArgs {
+  const float* MT = nullptr;
+  const __nv_bfloat16* MTb = nullptr;
+  const int* pix = nullptr;
+  int n_pix = 0, n_m = 0;
+  const ResBatchLoop* loops = nullptr;  // [B] device array
+  int B = 0, Bp = 0;                    // loops, padded to whole chunks
+  const float* cmdg = nullptr;          // [n_m][Bp] gathered commands
+  int Lmax = 0;                         // most layers of a loop
+};
+
+// B loops sharing `dm`: residual_j = atm_j - M c_j for all j from one pass over the
+// basis per step (gather of the commands, then one kernel); every loop's residual
+// and tile WFE partials equal those of its own residual kernel, bit for bit.
+struct ResBatch;
+bool res_batch_ok(const AtmoArgs& atmo);  // the loop's atmosphere can join a batched residual
+pas_status res_batch_create(pas_ctx_t ctx, pas_dm_t dm, int B, const ResBatchLoop* loops, ResBatch** out);
+pas_status res_batch_launch(ResBatch* r, cudaStream_t st);
+void res_batch_destroy(ResBatch* r);
+
 // pdl: launch as a programmatic dependent of the preceding kernel in `st`.
 pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, bool pdl = false);
 // Number of CTAs (and of residual-WFE partials) of residual_launch for n_pix pixels.

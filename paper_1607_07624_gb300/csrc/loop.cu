@@ -44,13 +44,9 @@ struct pas_loop_s {
   cudaEvent_t prof_ev[PAS_LOOP_KERNELS + 1] = {};
 };
 
-// ev (optional): PAS_LOOP_KERNELS + 1 events recorded before each kernel and
-// after the last one. skip_recon: stop after the slopes (a batch reconstructs the
-// loops that share a reconstructor together).
-static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = nullptr, bool skip_recon = false) {
-  // residual = atmosphere - M c: the residual kernel samples the wind-shifted
-  // layers at its pupil pixels while its other warps stream the basis
-  pas_status s = PAS_OK;
+// The step's first kernel: residual = atmosphere - M c (the residual kernel samples
+// the wind-shifted layers at its pupil pixels while its other warps stream the basis).
+static pas_status enqueue_residual(pas_loop_t L, cudaStream_t st) {
   pas::ResArgs ra = pas::make_res_args(L->dm);
   ra.atmo = L->atmo->args;
   ra.opd_atm = nullptr;
@@ -60,13 +56,12 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   ra.dm_sign = 1.0f;
   ra.out = L->d_opd;
   ra.wfe_part = L->d_wfe_part;
-  // inside the step the kernels follow each other programmatically (prologues and
-  // constant-matrix prefetches overlap the predecessor), except when events are
-  // recorded between them for profiling
-  const bool pdl = ev == nullptr;
-  if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
-  s = pas::residual_launch(L->ctx, ra, st, false);  // the step's first kernel
-  if (s != PAS_OK) return s;
+  return pas::residual_launch(L->ctx, ra, st, false);
+}
+
+// What the loop adds to its sensor's measurement: the step counter as the noise
+// frame counter, the residual-WFE finalisation, the integrating detector.
+static pas::LoopExtra loop_extra(pas_loop_t L) {
   pas::LoopExtra fa;
   fa.frame_ctr = L->d_step;
   fa.wfe_part = L->d_wfe_part;
@@ -77,12 +72,12 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   fa.step = L->d_step;
   fa.acc = L->d_acc;
   fa.n_int = L->n_int;
-  if (L->sh)
-    s = pas::sh_launch(L->sh, L->d_opd, L->d_frame, L->d_slopes, st, &fa, pdl);
-  else
-    s = pas::pyr_launch(L->pyr, L->d_opd, L->d_frame, L->d_slopes, st, &fa, false, ev ? ev + 1 : nullptr, pdl);
-  if (s != PAS_OK) return s;
-  if (skip_recon) return PAS_OK;
+  return fa;
+}
+
+// The step's last kernel: reconstruction and integrator (the network in place of
+// the matrix when the loop has one); it advances the step counter.
+static pas_status enqueue_recon(pas_loop_t L, cudaStream_t st, bool pdl) {
   pas::ReconArgs rc;
   rc.s = L->d_slopes;
   rc.dmodes = L->d_dmodes;
@@ -93,8 +88,34 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   rc.cmd_last = L->d_cmd;
   rc.step_inc = L->d_step;
   rc.n_int = L->n_int;
+  return L->mlp ? pas::mlp_loop_launch(L->mlp, rc, st, pdl) : pas::recon_launch(L->rec, rc, st, pdl);
+}
+
+// ev (optional): PAS_LOOP_KERNELS + 1 events recorded before each kernel and
+// after the last one. skip_recon: stop after the slopes (a batch reconstructs the
+// loops that share a reconstructor together). skip_residual: the residual is
+// already in the OPD buffer (a batch's shared-DM residual, ordered before by an
+// event); the sensor then starts without programmatic dependence.
+static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = nullptr, bool skip_recon = false,
+                               bool skip_residual = false) {
+  // inside the step the kernels follow each other programmatically (prologues and
+  // constant-matrix prefetches overlap the predecessor), except when events are
+  // recorded between them for profiling
+  const bool pdl = ev == nullptr;
+  if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+  pas_status s = skip_residual ? PAS_OK : enqueue_residual(L, st);
+  if (s != PAS_OK) return s;
+  const pas::LoopExtra fa = loop_extra(L);
+  const bool pdl_sensor = pdl && !skip_residual;
+  if (L->sh)
+    s = pas::sh_launch(L->sh, L->d_opd, L->d_frame, L->d_slopes, st, &fa, pdl_sensor);
+  else
+    s = pas::pyr_launch(L->pyr, L->d_opd, L->d_frame, L->d_slopes, st, &fa, false, ev ? ev + 1 : nullptr,
+                        pdl_sensor);
+  if (s != PAS_OK) return s;
+  if (skip_recon) return PAS_OK;
   if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
-  s = L->mlp ? pas::mlp_loop_launch(L->mlp, rc, st, pdl) : pas::recon_launch(L->rec, rc, st, pdl);
+  s = enqueue_recon(L, st, pdl);
   if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
   return s;
 }
@@ -395,6 +416,18 @@ struct pas_batch_s {
   std::vector<cudaStream_t> group_streams;
   std::vector<cudaEvent_t> group_join;
   int kernels_per_step = 0;
+  // persistent mode: the pyramid loops' rows and columns passes in one launch per
+  // transform length (member[i]: loop i's index in it, -1 for a loop stepped whole)
+  pas::PyrBatch* pyr_batch = nullptr;
+  std::vector<int> member;
+  std::vector<cudaEvent_t> res_join;
+  cudaEvent_t fork2 = nullptr;
+  // loops sharing a DM object: one batched residual per group (one basis pass)
+  std::vector<std::vector<int>> rgroups;
+  std::vector<int> rgroup_of;
+  std::vector<pas::ResBatch*> res_batches;
+  std::vector<cudaStream_t> rstreams;
+  std::vector<cudaEvent_t> rdone;
 };
 
 void pas_batch_destroy(pas_batch_t b) {
@@ -410,17 +443,35 @@ void pas_batch_destroy(pas_batch_t b) {
   for (cudaEvent_t e : b->group_join)
     if (e) cudaEventDestroy(e);
   for (pas::BatchRecGroup* g : b->rec_groups) pas::batch_rec_destroy(g);
+  for (cudaEvent_t e : b->res_join)
+    if (e) cudaEventDestroy(e);
+  if (b->fork2) cudaEventDestroy(b->fork2);
+  pas::pyr_batch_destroy(b->pyr_batch);
+  for (pas::ResBatch* r : b->res_batches) pas::res_batch_destroy(r);
+  for (cudaStream_t s : b->rstreams)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->rdone)
+    if (e) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   delete b;
 }
 
-pas_status pas_batch_create(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, pas_batch_t* out) {
+pas_status pas_batch_create_ex(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, uint32_t flags,
+                               pas_batch_t* out) {
   if (!ctx || !loops || !out) return pas::set_global_error(PAS_EINVAL, "pas_batch_create: NULL argument");
   *out = nullptr;
   PAS_CHECK_ARG(ctx, n_loops >= 1 && n_loops <= 4096, "pas_batch_create: 1 <= n_loops <= 4096");
+  PAS_CHECK_ARG(ctx, (flags & ~(uint32_t)PAS_BATCH_PERSISTENT) == 0, "pas_batch_create: unknown flag");
   for (int i = 0; i < n_loops; ++i) {
     PAS_CHECK_ARG(ctx, loops[i] != nullptr, "pas_batch_create: NULL loop");
-    for (int j = 0; j < i; ++j) PAS_CHECK_ARG(ctx, loops[j] != loops[i], "pas_batch_create: a loop appears twice");
+    for (int j = 0; j < i; ++j) {
+      PAS_CHECK_ARG(ctx, loops[j] != loops[i], "pas_batch_create: a loop appears twice");
+      // a sensor keeps one measurement's intermediates: loops stepped side by side
+      // need one each
+      PAS_CHECK_ARG(ctx, (loops[i]->pyr == nullptr || loops[j]->pyr != loops[i]->pyr) &&
+                             (loops[i]->sh == nullptr || loops[j]->sh != loops[i]->sh),
+                    "pas_batch_create: two loops share a sensor object");
+    }
   }
   pas_batch_t b = new pas_batch_s();
   b->ctx = ctx;
@@ -490,10 +541,89 @@ pas_status pas_batch_create(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, p
       return pas::set_error(ctx, PAS_ECUDA, "pas_batch_create: %s", cudaGetErrorString(e));
     }
   }
+  // loops sharing a DM object whose sources are at infinity: one residual pass over
+  // the basis per group, in loop order
+  b->rgroup_of.assign(n_loops, -1);
+  for (int i = 0; i < n_loops; ++i) {
+    pas_loop_t L = b->loops[i];
+    if (b->rgroup_of[i] >= 0 || !pas::res_batch_ok(L->atmo->args)) continue;
+    std::vector<int> members{i};
+    for (int j = i + 1; j < n_loops; ++j)
+      if (b->loops[j]->dm == L->dm && pas::res_batch_ok(b->loops[j]->atmo->args)) members.push_back(j);
+    if (members.size() < 2) continue;
+    std::vector<pas::ResBatchLoop> rl;
+    for (int k : members) {
+      pas_loop_t M = b->loops[k];
+      pas::ResBatchLoop r;
+      r.atmo = M->atmo->args;
+      r.cmd_ring = M->d_ring;
+      r.delay = M->delay;
+      r.d_step = M->d_step;
+      r.out = M->d_opd;
+      r.wfe_part = M->d_wfe_part;
+      rl.push_back(r);
+    }
+    pas::ResBatch* rb = nullptr;
+    pas_status sr = pas::res_batch_create(ctx, L->dm, (int)rl.size(), rl.data(), &rb);
+    if (sr != PAS_OK) {
+      pas_batch_destroy(b);
+      return sr;
+    }
+    for (int k : members) b->rgroup_of[k] = (int)b->rgroups.size();
+    b->rgroups.push_back(members);
+    b->res_batches.push_back(rb);
+    cudaStream_t rs = nullptr;
+    cudaEvent_t re = nullptr;
+    e = cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&re, cudaEventDisableTiming);
+    b->rstreams.push_back(rs);
+    b->rdone.push_back(re);
+    if (e != cudaSuccess) {
+      pas_batch_destroy(b);
+      return pas::set_error(ctx, PAS_ECUDA, "pas_batch_create: %s", cudaGetErrorString(e));
+    }
+  }
+  b->member.assign(n_loops, -1);
+  if (flags & PAS_BATCH_PERSISTENT) {
+    std::vector<pas_pyr_t> py;
+    std::vector<const float*> opd;
+    std::vector<float*> frame, sl;
+    std::vector<pas::LoopExtra> ex;
+    for (int i = 0; i < n_loops; ++i) {
+      pas_loop_t L = b->loops[i];
+      if (!L->pyr) continue;
+      b->member[i] = (int)py.size();
+      py.push_back(L->pyr);
+      opd.push_back(L->d_opd);
+      frame.push_back(L->d_frame);
+      sl.push_back(L->d_slopes);
+      ex.push_back(loop_extra(L));
+    }
+    if (!py.empty()) {
+      pas_status sp = pas::pyr_batch_create(ctx, (int)py.size(), py.data(), opd.data(), frame.data(), sl.data(),
+                                            ex.data(), &b->pyr_batch);
+      if (sp != PAS_OK) {
+        pas_batch_destroy(b);
+        return sp;
+      }
+    }
+    b->res_join.assign(n_loops, nullptr);
+    e = cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming);
+    for (int i = 0; i < n_loops && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->res_join[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      pas_batch_destroy(b);
+      return pas::set_error(ctx, PAS_ECUDA, "pas_batch_create: %s", cudaGetErrorString(e));
+    }
+  }
   b->kernels_per_step = 0;
-  for (int i = 0; i < n_loops; ++i)
-    b->kernels_per_step += (b->loops[i]->sh ? 3 : PAS_LOOP_KERNELS) - (group_of[i] >= 0 ? 1 : 0);
-  b->kernels_per_step += 3 * (int)b->groups.size();
+  for (int i = 0; i < n_loops; ++i) {
+    // a persistent member launches its residual and slopes kernels (and its
+    // reconstruction unless its group's product does it)
+    const int whole = b->member[i] >= 0 ? 3 : b->loops[i]->sh ? 3 : PAS_LOOP_KERNELS;
+    b->kernels_per_step += whole - (group_of[i] >= 0 ? 1 : 0) - (b->rgroup_of[i] >= 0 ? 1 : 0);
+  }
+  b->kernels_per_step += 3 * (int)b->groups.size() + 2 * (int)b->rgroups.size();
+  if (b->pyr_batch) b->kernels_per_step += pas::pyr_batch_n_groups(b->pyr_batch);
   // one graph per step: every loop's step is a branch of its own (fork on the
   // context's capture stream, one stream per loop, join back); a group's product
   // follows the slopes of all its loops on a stream of its own
@@ -508,11 +638,38 @@ pas_status pas_batch_create(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, p
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   pas_status st = PAS_OK;
   if (e == cudaSuccess) e = cudaEventRecord(b->fork, cs);
+  // the shared-DM residuals first, each on a stream of its own
+  for (size_t g = 0; g < b->rgroups.size() && e == cudaSuccess && st == PAS_OK; ++g) {
+    e = cudaStreamWaitEvent(b->rstreams[g], b->fork, 0);
+    if (e == cudaSuccess) st = pas::res_batch_launch(b->res_batches[g], b->rstreams[g]);
+    if (e == cudaSuccess && st == PAS_OK) e = cudaEventRecord(b->rdone[g], b->rstreams[g]);
+    if (e == cudaSuccess && st == PAS_OK) e = cudaStreamWaitEvent(cs, b->rdone[g], 0);
+  }
   for (int i = 0; i < n_loops && e == cudaSuccess && st == PAS_OK; ++i) {
-    e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
-    if (e == cudaSuccess) st = loop_enqueue(b->loops[i], b->streams[i], nullptr, group_of[i] >= 0);
+    const int rg = b->rgroup_of[i];
+    e = cudaStreamWaitEvent(b->streams[i], rg >= 0 ? b->rdone[rg] : b->fork, 0);
+    if (b->member[i] >= 0) {  // its residual; the persistent launch follows every one
+      if (rg >= 0) continue;
+      if (e == cudaSuccess) st = enqueue_residual(b->loops[i], b->streams[i]);
+      if (e == cudaSuccess && st == PAS_OK) e = cudaEventRecord(b->res_join[i], b->streams[i]);
+      if (e == cudaSuccess && st == PAS_OK) e = cudaStreamWaitEvent(cs, b->res_join[i], 0);
+      continue;
+    }
+    if (e == cudaSuccess) st = loop_enqueue(b->loops[i], b->streams[i], nullptr, group_of[i] >= 0, rg >= 0);
     if (e == cudaSuccess && st == PAS_OK) e = cudaEventRecord(b->join[i], b->streams[i]);
     if (e == cudaSuccess && st == PAS_OK && group_of[i] < 0) e = cudaStreamWaitEvent(cs, b->join[i], 0);
+  }
+  if (b->pyr_batch && e == cudaSuccess && st == PAS_OK) {
+    st = pas::pyr_batch_launch(b->pyr_batch, cs);
+    if (st == PAS_OK) e = cudaEventRecord(b->fork2, cs);
+    for (int i = 0; i < n_loops && e == cudaSuccess && st == PAS_OK; ++i) {
+      if (b->member[i] < 0) continue;
+      e = cudaStreamWaitEvent(b->streams[i], b->fork2, 0);
+      if (e == cudaSuccess) st = pas::pyr_batch_slopes(b->pyr_batch, b->member[i], b->streams[i], false);
+      if (e == cudaSuccess && st == PAS_OK && group_of[i] < 0) st = enqueue_recon(b->loops[i], b->streams[i], true);
+      if (e == cudaSuccess && st == PAS_OK) e = cudaEventRecord(b->join[i], b->streams[i]);
+      if (e == cudaSuccess && st == PAS_OK && group_of[i] < 0) e = cudaStreamWaitEvent(cs, b->join[i], 0);
+    }
   }
   for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess && st == PAS_OK; ++gi) {
     cudaStream_t gs = b->group_streams[gi];
@@ -534,6 +691,10 @@ pas_status pas_batch_create(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, p
   }
   *out = b;
   return PAS_OK;
+}
+
+pas_status pas_batch_create(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops, pas_batch_t* out) {
+  return pas_batch_create_ex(ctx, loops, n_loops, 0u, out);
 }
 
 pas_status pas_batch_step(pas_batch_t b, int32_t n_steps) {
@@ -558,9 +719,43 @@ pas_status pas_batch_check(pas_batch_t b, uint32_t* h_fault) {
     f |= x;
     if (x) PAS_CUDA_TRY(b->ctx, cudaMemset(pas::batch_rec_err(g), 0, sizeof(unsigned int)));
   }
-  if (h_fault) *h_fault = f;
+  unsigned int w = 0;
+  if (b->pyr_batch) {
+    unsigned int* d = pas::pyr_batch_err(b->pyr_batch);
+    PAS_CUDA_TRY(b->ctx, cudaMemcpy(&w, d, sizeof(w), cudaMemcpyDeviceToHost));
+    if (w) PAS_CUDA_TRY(b->ctx, cudaMemset(d, 0, sizeof(unsigned int)));
+  }
+  if (h_fault) *h_fault = f | (w ? 0x100u : 0u);
   if (f) return pas::set_error(b->ctx, PAS_ETIMEOUT, "batched reconstruction: a product's wait gave up (%u)", f);
+  if (w) return pas::set_error(b->ctx, PAS_ETIMEOUT, "persistent pyramid launch: a columns task's wait gave up");
   return PAS_OK;
+}
+
+int32_t pas_batch_n_residual_groups(pas_batch_t b) { return b ? (int32_t)b->rgroups.size() : -1; }
+
+int32_t pas_batch_n_persistent(pas_batch_t b) {
+  return b ? (b->pyr_batch ? pas::pyr_batch_n_groups(b->pyr_batch) : 0) : -1;
+}
+
+pas_status pas_batch_set_wait_limit(pas_batch_t b, int64_t polls) {
+  if (!b) return pas::set_global_error(PAS_EINVAL, "pas_batch_set_wait_limit: NULL batch");
+  PAS_CHECK_ARG(b->ctx, b->pyr_batch != nullptr, "pas_batch_set_wait_limit: not a persistent batch");
+  PAS_CHECK_ARG(b->ctx, polls >= 0, "pas_batch_set_wait_limit: negative limit");
+  const long long v = polls;
+  PAS_CUDA_TRY(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+  PAS_CUDA_TRY(b->ctx, cudaMemcpy(pas::pyr_batch_wait_limit(b->pyr_batch), &v, sizeof(v), cudaMemcpyHostToDevice));
+  return PAS_OK;
+}
+
+pas_status pas_batch_probe_waits(pas_batch_t b, uint32_t* h_fault) {
+  if (!b) return pas::set_global_error(PAS_EINVAL, "pas_batch_probe_waits: NULL batch");
+  PAS_CHECK_ARG(b->ctx, b->pyr_batch != nullptr, "pas_batch_probe_waits: not a persistent batch");
+  cudaStream_t st = b->ctx->stream;
+  PAS_CUDA_TRY(b->ctx, cudaStreamSynchronize(st));
+  pas_status s = pas::pyr_batch_launch(b->pyr_batch, st, true);
+  if (s != PAS_OK) return s;
+  PAS_CUDA_TRY(b->ctx, cudaStreamSynchronize(st));
+  return pas_batch_check(b, h_fault);
 }
 
 }  // extern "C"

@@ -84,6 +84,26 @@ struct ColArgs {
   FrameArgs fin;
 };
 
+// Where one loop's tasks sit in a persistent batched launch's ticket queue, and the
+// geometry of its own two passes.
+struct BatchLoopGeo {
+  int row_base, n_row;  // tickets [row_base, row_base + n_row): rows-pass tasks
+  int nbx, rows;        // rows pass: nbx x (n_row / nbx) CTAs of `rows` warps
+  int col_base, n_col;  // tickets of the columns-pass tasks
+  int nd, bw;           // columns pass: nd x (n_col / nd) CTAs of bw warps
+};
+
+struct BatchPyrArgs {
+  const RowArgs* ra;             // [L]
+  const ColArgs* ca;             // [L]
+  const BatchLoopGeo* geo;       // [L]
+  unsigned int* ticket;          // next ticket, 0 before the launch
+  unsigned int* rows_done;       // [L] completed rows-pass tasks, 0 before the launch
+  unsigned int* err;             // bit 0: a columns-pass task's wait gave up
+  const long long* wait_limit;   // polls (about 0.3 us each) before a wait gives up
+  int n_loops, n_row_tickets, n_tickets, first_ticket;
+};
+
 
 
 // Register caps per transform length: 72 for N = 480 compiles without spills and
@@ -92,9 +112,11 @@ struct ColArgs {
 constexpr int rows_max_regs(int N) { return 128; }
 constexpr int cols_max_regs(int N) { return 128; }
 
+// One rows-pass task: pupil rows [bx rows, (bx + 1) rows) and the bx-th of nby chunks of
+// the distinct sin values, by warps 0 .. rows-1 of the CTA (rows a power of two <= the
+// CTA's warps; further warps take part in the barriers only).
 template <int N>
-__global__ void __maxnreg__(rows_max_regs(N))
-pyr_rows_kernel(RowArgs a) {
+__device__ __forceinline__ void rows_task(const RowArgs& a, int bx, int by, int nby, int rows) {
   constexpr bool FOUR = four_step_ok(N);
   constexpr int TWN = FOUR ? four_tw_size(N) : tw_size(N);
   constexpr int MKN = FOUR ? four_mask_size(N) : buf_len(N);
@@ -103,12 +125,11 @@ pyr_rows_kernel(RowArgs a) {
   float2* tw_s = smem;
   float2* mk_s = smem + TWN;
   float2* tilt_s = mk_s + MKN;                      // [s_chunk][Np]
-  const int rows = blockDim.x >> 5;
   float2* phs = tilt_s + a.s_chunk * a.Np;          // [rows][Np]
   float2* bufs = phs + rows * a.Np;                 // [rows][PITCH]
   const int Np = a.Np, off = a.off;
-  const int i0 = blockIdx.x * rows;
-  const int s0 = (blockIdx.y * a.n_s) / gridDim.y, s1 = ((blockIdx.y + 1) * a.n_s) / gridDim.y;
+  const int i0 = bx * rows;
+  const int s0 = (by * a.n_s) / nby, s1 = ((by + 1) * a.n_s) / nby;
   pdl_trigger();
   {
     const float2* twg = FOUR ? a.tw4 : a.tw;
@@ -124,8 +145,10 @@ pyr_rows_kernel(RowArgs a) {
     sincospif(2.0f * ((float)j - cj) * a.beta[s0 + sl], &sn, &cs);
     tilt_s[t] = (j & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = i0 + warp;
+  const int warp_raw = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool row_warp = warp_raw < rows;
+  const int warp = row_warp ? warp_raw : 0;
+  const int i = row_warp ? i0 + warp : Np;      // a warp beyond `rows` owns no row
   float2* buf = bufs + warp * PITCH;
   // pupil phasor A exp(2 pi i opd / lambda) of this warp's row, kept for all s
   float2* phrow = phs + warp * Np;
@@ -134,7 +157,7 @@ pyr_rows_kernel(RowArgs a) {
     const int ai = 2 * i - Np + 1;
     const int ai2 = ai * ai;
     const float* orow = a.opd + (size_t)min(i, Np - 1) * Np;
-    for (int j = lane; j < Np; j += 32) {
+    for (int j = lane; j < Np && row_warp; j += 32) {
       float2 v = make_float2(0.f, 0.f);
       const int bj = 2 * j - Np + 1;
       const int d2 = ai2 + bj * bj;
@@ -181,6 +204,12 @@ pyr_rows_kernel(RowArgs a) {
   }
 }
 
+template <int N>
+__global__ void __maxnreg__(rows_max_regs(N))
+pyr_rows_kernel(RowArgs a) {
+  rows_task<N>(a, blockIdx.x, blockIdx.y, gridDim.y, blockDim.x >> 5);
+}
+
 // Block sum of one float per thread: float within each warp (fixed shuffle tree),
 // the warps' sums added in double in warp order (FP64 is a slow pipe on this GPU,
 // so it is kept out of the per-thread work). Result in every thread.
@@ -204,16 +233,18 @@ __device__ inline double block_sum_f(float v, double* red) {
 // on the step's critical path: the partials are fetched 8 at a time and summed in
 // group order; g lanes per pixel share the photon-noise rejection loop).
 // fidx: the frame counter, read by the caller before the handshake.
+// nthreads: the threads that take pixels (the CTA's first nthreads, a multiple of 32;
+// the others join the barriers and votes with no pixel).
 __device__ __noinline__ void finish_column(const FrameArgs& f, const float* part, int q, int nd, double* red,
-                              long long fidx) {
+                              long long fidx, int nthreads) {
   constexpr int BATCH = 8;
   int g = 1;
-  while (g < 8 && nd * g * 2 <= (int)blockDim.x) g *= 2;
+  while (g < 8 && nd * g * 2 <= nthreads) g *= 2;
   float flux = 0.f;
-  for (int t0 = 0; t0 < nd * g; t0 += blockDim.x) {  // the same trip count in every thread
+  for (int t0 = 0; t0 < nd * g; t0 += nthreads) {  // the same trip count in every thread
     const int t = t0 + threadIdx.x;
     const int p = t / g, sub = t - p * g;
-    const bool active = p < nd;
+    const bool active = p < nd && (int)threadIdx.x < nthreads;
     const int pix = (active ? p : 0) * nd + q;
     const bool valid_pix = active && f.vpix[pix] != 0;
     float v = 0.f;
@@ -321,9 +352,22 @@ __global__ void tilt_table_kernel(const float* alpha, const float* amp, int K, i
   }
 }
 
-template <int N>
-__global__ void __maxnreg__(cols_max_regs(N))
-pyr_cols_kernel(ColArgs a) {
+// One columns-pass task: detector column q, modulation group x column part gh, by
+// warps 0 .. bw-1 (the fine columns it transforms; further warps take part in the
+// barriers only). skip: transform nothing (a persistent launch whose wait for the
+// rows pass gave up still keeps the column handshake in step).
+// H through the read-only cache (written by an earlier kernel), or through L2 alone
+// (COH: written by other CTAs of the same persistent launch)
+template <bool COH>
+__device__ __forceinline__ float2 ld_h(const float2* p) {
+  if constexpr (COH)
+    return __ldcg(p);
+  else
+    return __ldg(p);
+}
+
+template <int N, bool COH = false>
+__device__ __forceinline__ void cols_task(const ColArgs& a, int q, int gh, int bw, bool skip = false) {
   // per-warp buffers: one transform's padded buffer (pass-by-pass engine) or the
   // four-step engine's transpose buffer; both then hold the warp's column of |g|^2
   constexpr bool FOUR = four_step_ok(N);
@@ -335,11 +379,9 @@ pyr_cols_kernel(ColArgs a) {
   float2* mk_s = smem + TWN;
   float2* bufs = mk_s + MKN;                      // [b][PITCH]
   const int Np = a.Np;
-  const int q = blockIdx.x;                       // detector column
-  const int gh = blockIdx.y;                      // modulation group x column part
   const int g = gh / a.split, h = gh - g * a.split;
   const int k0 = g * a.kper;
-  const int kc = min(a.kper, a.K - k0);
+  const int kc = skip ? 0 : min(a.kper, a.K - k0);
   pdl_trigger();
   {
     const float2* twg = FOUR ? a.tw4 : a.tw;
@@ -354,11 +396,10 @@ pyr_cols_kernel(ColArgs a) {
   // integer, of which this CTA takes part h of `split`; [floor(q N/nd), ceil((q+1) N/nd))
   // otherwise (the edge columns are shared with the neighbouring detector columns and
   // transformed by both CTAs)
-  const int bw = blockDim.x >> 5;
   const int y0 = a.frac ? (q * N) / a.nd : q * a.b + h * bw;
   const int nw = a.frac ? ((q + 1) * N + a.nd - 1) / a.nd - y0 : bw;
   const int y = y0 + warp;
-  float2* buf = bufs + warp * PITCH;
+  float2* buf = bufs + min(warp, bw - 1) * PITCH;  // warps >= bw transform nothing (nw <= bw)
   float* accw = reinterpret_cast<float*>(buf);
   if constexpr (FOUR) {
     // lane l accumulates |g|^2 of rows l + 32 j; TPW modulation points per call (a
@@ -379,15 +420,17 @@ pyr_cols_kernel(ColArgs a) {
       const int off = a.off;
       auto load = [&](int t, int j) -> float2 {
         const int i = lane + 32 * j - off;
-        if ((unsigned)i < (unsigned)Np && kk + t < kc) return cmul(__ldg(Hcol[t] + i), __ldg(tk[t] + i));
+        if ((unsigned)i < (unsigned)Np && kk + t < kc) return cmul(ld_h<COH>(Hcol[t] + i), __ldg(tk[t] + i));
         return make_float2(0.f, 0.f);
       };
       auto store = [&](int, int j, float2 v) { acc[j] = fmaf(v.x, v.x, fmaf(v.y, v.y, acc[j])); };
       four_step_mask<N>(buf, tw_s, mk_s, lane, load, store);
     }
     // stage |g|^2 of this column in natural order
+    if (warp < bw) {
 #pragma unroll
-    for (int j = 0; j < Q; ++j) accw[lane + 32 * j] = acc[j];
+      for (int j = 0; j < Q; ++j) accw[lane + 32 * j] = acc[j];
+    }
   } else {
     using OS = OutShape<N>;
     float acc[OS::PER_LANE];
@@ -400,7 +443,7 @@ pyr_cols_kernel(ColArgs a) {
       const int off = a.off;
       auto load = [&](int, int, int x) -> float2 {
         const int i = x - off;
-        if ((unsigned)i < (unsigned)Np) return cmul(__ldg(Hcol + i), __ldg(tk + i));
+        if ((unsigned)i < (unsigned)Np) return cmul(ld_h<COH>(Hcol + i), __ldg(tk + i));
         return make_float2(0.f, 0.f);
       };
       auto store = [&](int jb, int k, int, float2 v) {
@@ -413,7 +456,7 @@ pyr_cols_kernel(ColArgs a) {
 #pragma unroll
     for (int jb = 0; jb < OS::NJ0; ++jb) {
       const int bb = lane + 32 * jb;
-      if (OS::NB0 % 32 == 0 || bb < OS::NB0) {
+      if (warp < bw && (OS::NB0 % 32 == 0 || bb < OS::NB0)) {
 #pragma unroll
         for (int k = 0; k < OS::R0; ++k) accw[bb + k * OS::NB0] = acc[jb * OS::R0 + k];
       }
@@ -426,7 +469,7 @@ pyr_cols_kernel(ColArgs a) {
     // gb adjacent lanes per detector pixel, each over every gb-th column, then a
     // butterfly sum within the lane group
     int gb = 1;
-    while (gb < 8 && gb < bw && nd * gb * 2 <= (int)blockDim.x) gb *= 2;
+    while (gb < 8 && gb < bw && nd * gb * 2 <= bw * 32) gb *= 2;  // the CTA's own warps decide
     for (int t0 = 0; t0 < nd * gb; t0 += blockDim.x) {  // the same trip count in every thread
       const int t = t0 + threadIdx.x;
       const int p = t / gb, sub = t - p * gb;
@@ -472,11 +515,85 @@ pyr_cols_kernel(ColArgs a) {
   __syncthreads();
   if (!flag) return;
   __threadfence();
-  finish_column(a.fin, a.part, q, nd, red, fidx);
+  finish_column(a.fin, a.part, q, nd, red, fidx, bw * 32);
 }
 
 
 
+
+template <int N>
+__global__ void __maxnreg__(cols_max_regs(N))
+pyr_cols_kernel(ColArgs a) {
+  cols_task<N>(a, blockIdx.x, blockIdx.y, blockDim.x >> 5);
+}
+
+// ------------------------------------------------- persistent batched launch
+// Both passes of several loops' pyramids (one transform length) in one launch: the
+// CTAs draw tickets from one queue, every loop's rows-pass tasks first, then every
+// loop's columns-pass tasks (detector column x modulation group x column part). A
+// task is exactly one CTA of the loop's own launches (its geometry, its warps, its
+// arithmetic), so the frames equal those of the loop measured alone, bit for bit.
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int N>
+__global__ void __maxnreg__(cols_max_regs(N))
+pyr_batch_kernel(BatchPyrArgs a) {
+  __shared__ int s_task, s_loop, s_skip;
+  int cur_r = 0, cur_c = 0;  // thread 0's cursors: a CTA's tickets increase
+  for (;;) {
+    __syncthreads();  // the previous task is done with the shared memory
+    if (threadIdx.x == 0) {
+      const int t = (int)atomicAdd(a.ticket, 1u) + a.first_ticket;
+      int l = -1, skip = 0;
+      if (t < a.n_row_tickets) {
+        while (a.geo[cur_r].row_base + a.geo[cur_r].n_row <= t) ++cur_r;
+        l = cur_r;
+      } else if (t < a.n_tickets) {
+        while (a.geo[cur_c].col_base + a.geo[cur_c].n_col <= t) ++cur_c;
+        l = cur_c;
+        // the loop's rows pass must be complete. Its tasks hold lower tickets, each
+        // claimed by a running CTA that waits for nothing, so the wait ends; a wait
+        // that outlasts the limit flags the launch and the task transforms nothing
+        // (its column handshake still runs, the counters stay consistent)
+        const unsigned int need = (unsigned int)a.geo[l].n_row;
+        const long long limit = *a.wait_limit;
+        for (long long polls = 0; ld_acquire_u32(a.rows_done + l) < need; ++polls) {
+          if (polls >= limit) {
+            atomicOr(a.err, 1u);
+            skip = 1;
+            break;
+          }
+          __nanosleep(256);
+        }
+      }
+      s_task = t;
+      s_loop = l;
+      s_skip = skip;
+    }
+    __syncthreads();
+    const int t = s_task, l = s_loop;
+    if (l < 0) return;  // the queue is empty
+    const BatchLoopGeo g = a.geo[l];
+    if (t < a.n_row_tickets) {
+      const int r = t - g.row_base;
+      const int by = r / g.nbx;
+      rows_task<N>(a.ra[l], r - by * g.nbx, by, g.n_row / g.nbx, g.rows);
+      __threadfence();  // this task's part of H, before the count that publishes it
+      __syncthreads();
+      if (threadIdx.x == 0) atomicAdd(a.rows_done + l, 1u);
+    } else {
+      const int c = t - g.col_base;
+      const int gh = c / g.nd;
+      __threadfence();
+      cols_task<N, true>(a.ca[l], c - gh * g.nd, gh, g.bw, s_skip != 0);
+    }
+  }
+}
 
 __global__ void ccd_noise_kernel(const float* in, float* out, int n, float scale, float ron,
                                  unsigned long long seed, long long fidx) {
@@ -490,11 +607,13 @@ struct PyrKernels {
   void (*rows)(RowArgs);
   void (*cols)(ColArgs);
   int tw_n, buf_n, pitch;
+  void (*batch)(BatchPyrArgs);
 };
 
 template <int N>
 PyrKernels kernels_for() {
-  return PyrKernels{pyr_rows_kernel<N>, pyr_cols_kernel<N>, tw_size(N), buf_len(N), buf_len(N) | 1};
+  return PyrKernels{pyr_rows_kernel<N>, pyr_cols_kernel<N>, tw_size(N), buf_len(N), buf_len(N) | 1,
+                    pyr_batch_kernel<N>};
 }
 
 #define PAS_PYR_SIZES(X) X(16) X(24) X(32) X(40) X(48) X(64) X(80) X(96) X(120) X(128) X(160) \
@@ -583,7 +702,7 @@ size_t rows_smem(pas_pyr_t y, int rows, int s_chunk) {
                            (size_t)rows * (y->p.Np + y->kern.pitch));
 }
 
-static void launch_rows(pas_pyr_t y, const float* d_opd, cudaStream_t st, bool pdl = false) {
+static RowArgs make_row_args(pas_pyr_t y, const float* d_opd) {
   const pas_pyr_params& p = y->p;
   RowArgs ra;
   ra.opd = d_opd;
@@ -600,12 +719,17 @@ static void launch_rows(pas_pyr_t y, const float* d_opd, cudaStream_t st, bool p
   ra.inv_lo = y->inv_lo;
   ra.n_s = y->n_s;
   ra.s_chunk = y->s_chunk;
-  dim3 gr((p.Np + y->rows - 1) / y->rows, y->n_schunks);
+  return ra;
+}
+
+static void launch_rows(pas_pyr_t y, const float* d_opd, cudaStream_t st, bool pdl = false) {
+  const RowArgs ra = make_row_args(y, d_opd);
+  dim3 gr((y->p.Np + y->rows - 1) / y->rows, y->n_schunks);
   launch_k(y->kern.rows, gr, dim3(y->rows * 32), rows_smem(y, y->rows, y->s_chunk), st, pdl, ra);
 }
 
-static void launch_cols(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream_t st,
-                        const LoopExtra* fa_extra, bool increment_ctr) {
+static ColArgs make_col_args(pas_pyr_t y, float* d_frame, float* d_slopes, const LoopExtra* fa_extra,
+                             bool increment_ctr) {
   const pas_pyr_params& p = y->p;
   ColArgs ca;
   ca.H = y->d_H;
@@ -645,6 +769,12 @@ static void launch_cols(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream
   fa.n_sub = p.n_sub;
   fa.local_norm = p.local_norm;
   fa.wfe = fa_extra ? *fa_extra : LoopExtra();
+  return ca;
+}
+
+static void launch_cols(pas_pyr_t y, float* d_frame, float* d_slopes, cudaStream_t st,
+                        const LoopExtra* fa_extra, bool increment_ctr) {
+  const ColArgs ca = make_col_args(y, d_frame, d_slopes, fa_extra, increment_ctr);
   dim3 gc(y->nd, y->G * y->H);
   const int warps = y->b / y->H;
   // the columns pass starts after the rows pass has finished: launched early, its
@@ -687,6 +817,194 @@ pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_
   launch_slopes(y, d_frame, d_slopes, st, fa_extra, increment_ctr, pdl);
   return check_launch(y->ctx, "pas_pyr_measure launch");
 }
+
+// ------------------------------------------------- persistent batched launch (host)
+
+struct PyrBatchGroup {
+  int N = 0;
+  void (*kern)(BatchPyrArgs) = nullptr;
+  BatchPyrArgs args{};
+  int grid = 0, threads = 0;
+  size_t smem = 0;
+};
+
+struct PyrBatch {
+  pas_ctx_t ctx = nullptr;
+  std::vector<pas_pyr_t> pyr;
+  std::vector<float*> frame, slopes;
+  std::vector<LoopExtra> extra;
+  std::vector<PyrBatchGroup> groups;
+  std::vector<int> group_of;        // member -> group
+  void* d_mem = nullptr;            // argument arrays of every group
+  unsigned int* d_counters = nullptr;  // per group: ticket, rows_done[L]; zeroed per launch
+  size_t counter_bytes = 0;
+  unsigned int* d_err = nullptr;
+  long long* d_wait_limit = nullptr;
+};
+
+void pyr_batch_destroy(PyrBatch* b) {
+  if (!b) return;
+  dev_free(b->d_mem);
+  dev_free(b->d_counters);
+  dev_free(b->d_err);
+  dev_free(b->d_wait_limit);
+  delete b;
+}
+
+pas_status pyr_batch_create(pas_ctx_t ctx, int n, const pas_pyr_t* y, const float* const* opd, float* const* frame,
+                            float* const* slopes, const LoopExtra* extra, PyrBatch** out) {
+  *out = nullptr;
+  PAS_CHECK_ARG(ctx, n >= 1, "persistent pyramid batch: at least one pyramid");
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j)
+      PAS_CHECK_ARG(ctx, y[i] != y[j], "persistent pyramid batch: a pyramid object appears twice");
+  PyrBatch* b = new PyrBatch();
+  b->ctx = ctx;
+  b->pyr.assign(y, y + n);
+  b->frame.assign(frame, frame + n);
+  b->slopes.assign(slopes, slopes + n);
+  b->extra.assign(extra, extra + n);
+  b->group_of.assign(n, -1);
+  // one group per transform length, members in batch order
+  std::vector<std::vector<int>> members;
+  for (int i = 0; i < n; ++i) {
+    int g = -1;
+    for (size_t k = 0; k < b->groups.size(); ++k)
+      if (b->groups[k].N == y[i]->p.N) g = (int)k;
+    if (g < 0) {
+      g = (int)b->groups.size();
+      b->groups.emplace_back();
+      b->groups.back().N = y[i]->p.N;
+      b->groups.back().kern = y[i]->kern.batch;
+      members.emplace_back();
+    }
+    members[g].push_back(i);
+    b->group_of[i] = g;
+  }
+  const size_t G = b->groups.size();
+  size_t arg_bytes = 0, n_counters = 0;
+  for (size_t g = 0; g < G; ++g) {
+    const size_t L = members[g].size();
+    arg_bytes += L * (sizeof(RowArgs) + sizeof(ColArgs) + sizeof(BatchLoopGeo)) + 3 * 256;
+    n_counters += 1 + L;
+  }
+  b->counter_bytes = sizeof(unsigned int) * n_counters;
+  pas_status st = dev_alloc(ctx, &b->d_mem, arg_bytes);
+  if (st == PAS_OK) st = dev_alloc(ctx, (void**)&b->d_counters, b->counter_bytes);
+  if (st == PAS_OK) st = dev_alloc(ctx, (void**)&b->d_err, sizeof(unsigned int));
+  if (st == PAS_OK) st = dev_alloc(ctx, (void**)&b->d_wait_limit, sizeof(long long));
+  if (st != PAS_OK) {
+    pyr_batch_destroy(b);
+    return st;
+  }
+  std::vector<unsigned char> host(arg_bytes, 0);
+  size_t off = 0, ctr = 0;
+  auto carve = [&](size_t bytes) {
+    const size_t at = off;
+    off += (bytes + 255) & ~size_t(255);
+    return at;
+  };
+  cudaError_t e = cudaSuccess;
+  for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
+    PyrBatchGroup& grp = b->groups[g];
+    const size_t L = members[g].size();
+    const size_t o_ra = carve(L * sizeof(RowArgs)), o_ca = carve(L * sizeof(ColArgs)),
+                 o_geo = carve(L * sizeof(BatchLoopGeo));
+    RowArgs* ra = reinterpret_cast<RowArgs*>(host.data() + o_ra);
+    ColArgs* ca = reinterpret_cast<ColArgs*>(host.data() + o_ca);
+    BatchLoopGeo* geo = reinterpret_cast<BatchLoopGeo*>(host.data() + o_geo);
+    int warps = 1, tickets = 0;
+    size_t smem = 0;
+    for (size_t k = 0; k < L; ++k) {
+      const int i = members[g][k];
+      pas_pyr_t p = y[i];
+      ra[k] = make_row_args(p, opd[i]);
+      ca[k] = make_col_args(p, frame[i], slopes[i], &extra[i], false);
+      BatchLoopGeo& q = geo[k];
+      q.rows = p->rows;
+      q.nbx = (p->p.Np + p->rows - 1) / p->rows;
+      q.row_base = tickets;
+      q.n_row = q.nbx * p->n_schunks;
+      tickets += q.n_row;
+      q.nd = p->nd;
+      q.bw = p->b / p->H;
+      q.n_col = p->nd * p->G * p->H;
+      warps = std::max(warps, std::max(q.rows, q.bw));
+      smem = std::max(smem, std::max(rows_smem(p, p->rows, p->s_chunk), cols_smem(p, q.bw)));
+    }
+    const int n_row_tickets = tickets;
+    for (size_t k = 0; k < L; ++k) {
+      geo[k].col_base = tickets;
+      tickets += geo[k].n_col;
+    }
+    BatchPyrArgs& a = grp.args;
+    unsigned char* dm = static_cast<unsigned char*>(b->d_mem);
+    a.ra = reinterpret_cast<const RowArgs*>(dm + o_ra);
+    a.ca = reinterpret_cast<const ColArgs*>(dm + o_ca);
+    a.geo = reinterpret_cast<const BatchLoopGeo*>(dm + o_geo);
+    a.ticket = b->d_counters + ctr;
+    a.rows_done = b->d_counters + ctr + 1;
+    ctr += 1 + L;
+    a.err = b->d_err;
+    a.wait_limit = b->d_wait_limit;
+    a.n_loops = (int)L;
+    a.n_row_tickets = n_row_tickets;
+    a.n_tickets = tickets;
+    a.first_ticket = 0;
+    grp.threads = 32 * warps;
+    grp.smem = smem;
+    if (smem > SMEM_MAX) {
+      pyr_batch_destroy(b);
+      return set_error(ctx, PAS_EINVAL, "persistent pyramid batch: %zu bytes of shared memory per CTA", smem);
+    }
+    e = raise_dyn_smem((const void*)grp.kern, smem);
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, grp.kern, grp.threads, smem);
+    if (e == cudaSuccess && occ < 1) {
+      pyr_batch_destroy(b);
+      return set_error(ctx, PAS_EINVAL, "persistent pyramid batch: a CTA of %d threads does not fit an SM",
+                       grp.threads);
+    }
+    grp.grid = std::max(1, std::min(tickets, occ * std::max(1, ctx->sm_count)));
+  }
+  const long long limit = PAS_BATCH_WAIT_DEFAULT;
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_mem, host.data(), arg_bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_wait_limit, &limit, sizeof(limit), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, b->counter_bytes);
+  if (e != cudaSuccess) {
+    pyr_batch_destroy(b);
+    return set_error(ctx, PAS_ECUDA, "persistent pyramid batch: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return PAS_OK;
+}
+
+// Both passes of every member on `st`: the counters are zeroed, then one persistent
+// launch per transform length (in group order). columns_only: the queue starts at
+// the columns-pass tickets, the rows pass is withheld (a diagnostic of the waits).
+pas_status pyr_batch_launch(PyrBatch* b, cudaStream_t st, bool columns_only) {
+  cudaError_t e = cudaMemsetAsync(b->d_counters, 0, b->counter_bytes, st);
+  for (size_t g = 0; g < b->groups.size() && e == cudaSuccess; ++g) {
+    const PyrBatchGroup& grp = b->groups[g];
+    BatchPyrArgs a = grp.args;
+    if (columns_only) a.first_ticket = a.n_row_tickets;
+    e = launch_k(grp.kern, dim3(grp.grid), dim3(grp.threads), grp.smem, st, false, a);
+  }
+  if (e != cudaSuccess) return set_error(b->ctx, PAS_ECUDA, "persistent pyramid batch launch: %s", cudaGetErrorString(e));
+  return PAS_OK;
+}
+
+// Member i's slopes kernel on `st` (after pyr_batch_launch); pdl: it follows a
+// kernel of `st` programmatically.
+pas_status pyr_batch_slopes(PyrBatch* b, int i, cudaStream_t st, bool pdl) {
+  launch_slopes(b->pyr[i], b->frame[i], b->slopes[i], st, &b->extra[i], false, pdl);
+  return check_launch(b->ctx, "persistent pyramid batch: slopes launch");
+}
+
+int pyr_batch_n_groups(const PyrBatch* b) { return (int)b->groups.size(); }
+unsigned int* pyr_batch_err(PyrBatch* b) { return b->d_err; }
+long long* pyr_batch_wait_limit(PyrBatch* b) { return b->d_wait_limit; }
 
 int pyr_n_pupil(pas_pyr_t y) { return y->n_pupil; }
 int pyr_n_valid(pas_pyr_t y) { return y->n_valid; }

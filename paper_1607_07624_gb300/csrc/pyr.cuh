@@ -32,6 +32,20 @@ pas_status pyr_launch(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_
 // Noiseless frame and slopes of d_opd on `st` (the sensor's reference subtracted),
 // whatever noise the object is set to: calibration measurements.
 pas_status pyr_measure_noiseless(pas_pyr_t y, const float* d_opd, float* d_frame, float* d_slopes, cudaStream_t st);
+// Persistent batched launch of several pyramids' rows and columns passes (one
+// launch per transform length; each task is one CTA of the pyramid's own launches,
+// so the frames equal those measured alone). Per member: its OPD, frame and slopes
+// buffers and loop fields (as pyr_launch takes them, counter not incremented).
+struct PyrBatch;
+constexpr long long PAS_BATCH_WAIT_DEFAULT = 1ll << 21;  // polls: about a second
+pas_status pyr_batch_create(pas_ctx_t ctx, int n, const pas_pyr_t* y, const float* const* opd, float* const* frame,
+                            float* const* slopes, const LoopExtra* extra, PyrBatch** out);
+pas_status pyr_batch_launch(PyrBatch* b, cudaStream_t st, bool columns_only = false);
+pas_status pyr_batch_slopes(PyrBatch* b, int i, cudaStream_t st, bool pdl);
+int pyr_batch_n_groups(const PyrBatch* b);
+unsigned int* pyr_batch_err(PyrBatch* b);
+long long* pyr_batch_wait_limit(PyrBatch* b);
+void pyr_batch_destroy(PyrBatch* b);
 int pyr_n_valid(pas_pyr_t y);
 int pyr_n_pupil(pas_pyr_t y);
 int pyr_nd(pas_pyr_t y);

@@ -23,6 +23,7 @@ _lib = C.CDLL(LIB_PATH)
 PAS_OK, PAS_EINVAL, PAS_ENOMEM, PAS_ECUDA, PAS_ETIMEOUT, PAS_ESTATE = range(6)
 PAS_FP32, PAS_BF16 = 0, 1
 PAS_LOOP_KERNELS = 5          # kernels of one loop step (the header's define)
+PAS_BATCH_PERSISTENT = 1      # pas_batch_create_ex flag
 STATUS_NAMES = {0: "PAS_OK", 1: "PAS_EINVAL", 2: "PAS_ENOMEM", 3: "PAS_ECUDA", 4: "PAS_ETIMEOUT",
                 5: "PAS_ESTATE"}
 
@@ -145,6 +146,11 @@ _SIGS = {
     "pas_batch_n_groups": (i32, [vp]),
     "pas_batch_kernels_per_step": (i32, [vp]),
     "pas_batch_check": (C.c_int, [vp, C.POINTER(C.c_uint32)]),
+    "pas_batch_create_ex": (C.c_int, [vp, vp, i32, C.c_uint32, P(vp)]),
+    "pas_batch_n_persistent": (i32, [vp]),
+    "pas_batch_n_residual_groups": (i32, [vp]),
+    "pas_batch_set_wait_limit": (C.c_int, [vp, i64]),
+    "pas_batch_probe_waits": (C.c_int, [vp, C.POINTER(C.c_uint32)]),
     "pas_calib_interaction_matrix": (C.c_int, [vp, vp, vp, C.c_double, vp]),
     "pas_pinv_f64": (C.c_int, [vp, vp, i32, i32, C.c_double, vp, vp, C.POINTER(i32), C.POINTER(i32)]),
     "pas_gemm_f64": (C.c_int, [vp, vp, C.c_int64, C.c_int64, vp, C.c_int64, C.c_int64, vp, i32, i32, i32, vp,
@@ -586,6 +592,33 @@ def pas_batch_create(ctx, loops):
     h = vp()
     _check(_lib.pas_batch_create(ctx, arr, len(loops), C.byref(h)), ctx)
     return h
+
+
+def pas_batch_create_ex(ctx, loops, flags=0):
+    """pas_batch_create with flags (PAS_BATCH_PERSISTENT)."""
+    arr = (vp * len(loops))(*[l.value if isinstance(l, vp) else l for l in loops])
+    h = vp()
+    _check(_lib.pas_batch_create_ex(ctx, arr, len(loops), int(flags), C.byref(h)), ctx)
+    return h
+
+
+def pas_batch_n_persistent(batch) -> int:
+    return int(_lib.pas_batch_n_persistent(batch))
+
+
+def pas_batch_n_residual_groups(batch) -> int:
+    return int(_lib.pas_batch_n_residual_groups(batch))
+
+
+def pas_batch_set_wait_limit(batch, ctx, polls):
+    _check(_lib.pas_batch_set_wait_limit(batch, int(polls)), ctx)
+
+
+def pas_batch_probe_waits(batch):
+    """Run the wait diagnostic; returns (status, fault bits) without raising."""
+    f = C.c_uint32()
+    st = int(_lib.pas_batch_probe_waits(batch, C.byref(f)))
+    return st, f.value
 
 
 def pas_batch_step(batch, ctx, n_steps=1):

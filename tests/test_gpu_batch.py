@@ -9,23 +9,26 @@ from synth.configs import with_
 pytestmark = pytest.mark.gpu
 
 
-def _systems():
+def _systems(share_dm=True):
+    """Three realisations of the 64 px system (sharing one DM object unless share_dm is
+    false) and a smaller loop."""
     from paper_1607_07624_gb300.system import SCAOSystem
     cfg = get_config("scao_8m_64px")
     first = SCAOSystem(cfg, autotune=False, wfe_history=256)
     out = [first]
     for seed in (2001, 2002):
         out.append(SCAOSystem(with_(cfg, seed=seed), basis=first.basis, R=first.R, autotune=False,
-                              wfe_history=256))
+                              wfe_history=256, dm=first.dm if share_dm else None))
     small = tiny_config(Np=32, N=64, n_sub=8, K=8, n_modes=20, mod_radius=2.0, S=128)
     out.append(SCAOSystem(small, autotune=False, wfe_history=256))
     return out
 
 
-def test_batch_steps_reproduce_single_loops():
+@pytest.mark.parametrize("share_dm", [False, True])
+def test_batch_steps_reproduce_single_loops(share_dm):
     import torch
     from paper_1607_07624_gb300 import pas
-    systems = _systems()
+    systems = _systems(share_dm)
     batch = None
     try:
         n = 40
@@ -37,6 +40,7 @@ def test_batch_steps_reproduce_single_loops():
         ctx = systems[0].ctx
         batch = pas.pas_batch_create(ctx, [s.loop for s in systems])
         assert pas.pas_batch_size(batch) == len(systems)
+        assert pas.pas_batch_n_residual_groups(batch) == (1 if share_dm else 0)
         pas.pas_batch_step(batch, ctx, n)
         torch.cuda.synchronize()
         for s, r in zip(systems, ref):
@@ -61,6 +65,15 @@ def test_batch_rejects_duplicates_and_null():
             pas.pas_batch_create(s.ctx, [s.loop, s.loop])
         with pytest.raises(pas.PasError):
             pas.pas_batch_create(s.ctx, [])
+        # a second loop on the same pyramid object: the sensors' intermediates would race
+        other = pas.pas_loop_create(s.ctx, s.atmo, s.pyr, s.rec, s.dm, s.d_gain, 1, 16)
+        try:
+            with pytest.raises(pas.PasError, match="sensor"):
+                pas.pas_batch_create(s.ctx, [s.loop, other])
+            with pytest.raises(pas.PasError, match="flag"):
+                pas.pas_batch_create_ex(s.ctx, [s.loop], 2)
+        finally:
+            pas.pas_loop_destroy(other)
     finally:
         s.close()
 
@@ -111,4 +124,165 @@ def test_loops_sharing_a_bf16_reconstructor_get_one_tensor_core_product():
         if batch is not None:
             pas.pas_batch_destroy(batch)
         for s in alone + systems[1:] + systems[:1]:
+            s.close()
+
+
+def _mixed_systems():
+    """Pyramid loops of two transform lengths (one with an integrating detector) and a
+    Shack-Hartmann loop."""
+    from paper_1607_07624_gb300.system import SCAOSystem
+    out = _systems()
+    small = tiny_config(Np=32, N=64, n_sub=8, K=8, n_modes=20, mod_radius=2.0, S=128)
+    out.append(SCAOSystem(with_(small, seed=77), autotune=False, wfe_history=256, detector_steps=2))
+    out.append(SCAOSystem(with_(small, seed=78), autotune=False, wfe_history=256, sensor="sh"))
+    return out
+
+
+def _run_alone(systems, n):
+    ref = []
+    for s in systems:
+        s.step(n)
+        ref.append((s.wfe_nm(n), s.loop_cmd.cpu().numpy().copy()))
+        s.set_state(0, np.zeros((s.delay, s.n_modes), np.float32))
+    return ref
+
+
+def test_persistent_batch_reproduces_single_loops():
+    """One persistent launch per transform length runs every pyramid loop's rows and
+    columns passes from one task queue; each loop's WFE history and command equal
+    those of the loop stepped alone, bit for bit."""
+    import torch
+    from paper_1607_07624_gb300 import pas
+    systems = _mixed_systems()
+    batch = None
+    try:
+        n = 40
+        ref = _run_alone(systems, n)
+        ctx = systems[0].ctx
+        batch = pas.pas_batch_create_ex(ctx, [s.loop for s in systems], pas.PAS_BATCH_PERSISTENT)
+        assert pas.pas_batch_n_persistent(batch) == 2          # N = 128 and N = 64
+        # 5 pyramid loops: residual + slopes + reconstruction; the SH loop whole (3); the
+        # three loops sharing a DM: one gather and one residual kernel in place of 3
+        assert pas.pas_batch_n_residual_groups(batch) == 1
+        assert pas.pas_batch_kernels_per_step(batch) == 5 * 3 + 3 + 2 - 3 + 2
+        pas.pas_batch_step(batch, ctx, n)
+        torch.cuda.synchronize()
+        assert pas.pas_batch_check(batch, ctx) == 0
+        for s, (w, c) in zip(systems, ref):
+            st, _ = pas.pas_loop_step(s.loop, s.ctx, 0, stats=True)
+            assert st == n
+            assert np.array_equal(s.wfe_nm(n), w)
+            assert np.array_equal(s.loop_cmd.cpu().numpy(), c)
+    finally:
+        if batch is not None:
+            pas.pas_batch_destroy(batch)
+        for s in systems:
+            s.close()
+
+
+def test_persistent_batch_wait_runs_out_and_the_context_stays_usable():
+    """With the rows pass withheld every columns task waits for a count that nothing
+    advances: the bounded wait gives up (limit 0 and 64 polls), the launch completes,
+    PAS_ETIMEOUT is reported once, and the batch then steps as before."""
+    import torch
+    from paper_1607_07624_gb300 import pas
+    systems = _systems()
+    batch = None
+    try:
+        n = 12
+        ref = _run_alone(systems, n)
+        ctx = systems[0].ctx
+        batch = pas.pas_batch_create_ex(ctx, [s.loop for s in systems], pas.PAS_BATCH_PERSISTENT)
+        for limit in (0, 64):
+            pas.pas_batch_set_wait_limit(batch, ctx, limit)
+            st, fault = pas.pas_batch_probe_waits(batch)
+            assert st == pas.PAS_ETIMEOUT and fault & 0x100
+            assert pas.pas_batch_check(batch, ctx) == 0       # reported once
+        with pytest.raises(pas.PasError):
+            pas.pas_batch_set_wait_limit(batch, ctx, -1)
+        pas.pas_batch_set_wait_limit(batch, ctx, 1 << 21)
+        for s in systems:   # the probe left the loops' states as they were
+            st, _ = pas.pas_loop_step(s.loop, s.ctx, 0, stats=True)
+            assert st == 0
+        pas.pas_batch_step(batch, ctx, n)
+        torch.cuda.synchronize()
+        assert pas.pas_batch_check(batch, ctx) == 0
+        for s, (w, c) in zip(systems, ref):
+            assert np.array_equal(s.wfe_nm(n), w)
+            assert np.array_equal(s.loop_cmd.cpu().numpy(), c)
+    finally:
+        if batch is not None:
+            pas.pas_batch_destroy(batch)
+        for s in systems:
+            s.close()
+
+
+def test_persistent_batch_with_shared_bf16_reconstructor_matches_graph_branches():
+    """Persistent pyramid launch and tensor-core group reconstruction together give
+    the same commands as the batch of graph branches, bit for bit."""
+    import torch
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    cfg = get_config("scao_8m_64px")
+    first = SCAOSystem(cfg, autotune=False, wfe_history=64, recon_precision=pas.PAS_BF16)
+    systems, batches = [first], []
+    try:
+        for seed in (2001, 2002, 2003):
+            systems.append(SCAOSystem(with_(cfg, seed=seed), basis=first.basis, R=first.R, rec=first.rec,
+                                      autotune=False, wfe_history=64))
+        ctx = first.ctx
+        out = []
+        for flags in (0, pas.PAS_BATCH_PERSISTENT):
+            b = pas.pas_batch_create_ex(ctx, [s.loop for s in systems], flags)
+            batches.append(b)
+            assert pas.pas_batch_n_groups(b) == 1
+            pas.pas_batch_step(b, ctx, 30)
+            torch.cuda.synchronize()
+            assert pas.pas_batch_check(b, ctx) == 0
+            out.append([(s.wfe_nm(30), s.loop_cmd.cpu().numpy().copy()) for s in systems])
+            for s in systems:
+                s.set_state(0, np.zeros((s.delay, s.n_modes), np.float32))
+            pas.pas_batch_destroy(b)
+            batches.pop()
+        for (w0, c0), (w1, c1) in zip(*out):
+            assert np.array_equal(w0, w1) and np.array_equal(c0, c1)
+    finally:
+        for b in batches:
+            pas.pas_batch_destroy(b)
+        for s in systems[1:] + systems[:1]:
+            s.close()
+
+
+@pytest.mark.parametrize("precision,n_loops", [("fp32", 9), ("bf16", 5)])
+def test_shared_dm_residual_batches_reproduce_single_loops(precision, n_loops):
+    """Loops sharing one DM object get their residuals from one basis pass (8 loops per
+    CTA for a float32 basis, 4 for bf16: a partial last chunk here). An off-axis loop
+    joins the group; a source at finite height keeps its own residual kernel. Every
+    loop's WFE history and command equal those of the loop stepped alone."""
+    import torch
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    cfg = with_(get_config("scao_8m_64px"), n_steps=20)
+    prec = pas.PAS_BF16 if precision == "bf16" else pas.PAS_FP32
+    first = SCAOSystem(cfg, autotune=False, wfe_history=64, dm_precision=prec)
+    systems, batch = [first], None
+    try:
+        for i in range(1, n_loops):
+            source = (2.0, 30.0) if i == 1 else (1.0, 60.0, 90e3) if i == 2 else None
+            systems.append(SCAOSystem(with_(cfg, seed=3000 + i), basis=first.basis, R=first.R, dm=first.dm,
+                                      autotune=False, wfe_history=64, source=source))
+        n = 20
+        ref = _run_alone(systems, n)
+        ctx = first.ctx
+        batch = pas.pas_batch_create(ctx, [s.loop for s in systems])
+        assert pas.pas_batch_n_residual_groups(batch) == 1
+        pas.pas_batch_step(batch, ctx, n)
+        torch.cuda.synchronize()
+        for s, (w, c) in zip(systems, ref):
+            assert np.array_equal(s.wfe_nm(n), w)
+            assert np.array_equal(s.loop_cmd.cpu().numpy(), c)
+    finally:
+        if batch is not None:
+            pas.pas_batch_destroy(batch)
+        for s in systems[1:] + systems[:1]:
             s.close()
