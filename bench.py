@@ -617,7 +617,11 @@ def bench_batched_workload(timed, n_steps=30):
                            "loop_steps_per_s": len(systems) * n_steps / (ms * 1e-3),
                            "kernels_per_step": pas.pas_batch_kernels_per_step(batch),
                            "persistent_launches_per_step": pas.pas_batch_n_persistent(batch),
-                           "tensor_core_reconstruction_groups": pas.pas_batch_n_groups(batch)}
+                           "tensor_core_reconstruction_groups": pas.pas_batch_n_groups(batch),
+                           "shared_dm_residual_groups": pas.pas_batch_n_residual_groups(batch)}
+            if flags:
+                modes[name]["persistent_geometry"] = [pas.pas_batch_persistent_geometry(batch, ctx, g)
+                                                      for g in range(pas.pas_batch_n_persistent(batch))]
             pas.pas_batch_destroy(batch)
             batch = None
         best = max(modes, key=lambda k: modes[k]["loop_steps_per_s"])

@@ -433,6 +433,12 @@ pas_status pas_batch_check(pas_batch_t batch, uint32_t* h_fault);
 /* Persistent launches per step (one per transform length), 0 for a batch created
  * without PAS_BATCH_PERSISTENT, -1 for a NULL handle. Host only. */
 int32_t pas_batch_n_persistent(pas_batch_t batch);
+/* Geometry of persistent launch g (0 <= g < pas_batch_n_persistent), h_geo[8]: transform
+ * length N, CTAs, threads per CTA, dynamic shared bytes per CTA, pupil rows per rows
+ * task, sin values per rows task (at most), rows tasks, columns tasks. The columns tasks
+ * keep each loop's own geometry; the rows tasks' geometry (which does not change the
+ * result) is chosen for the launch's CTA. Host only. */
+pas_status pas_batch_persistent_geometry(pas_batch_t batch, int32_t g, int32_t* h_geo);
 /* Groups of loops sharing a DM object whose residuals are computed together; -1 for a
  * NULL handle. Host only. */
 int32_t pas_batch_n_residual_groups(pas_batch_t batch);

@@ -421,7 +421,8 @@ struct pas_batch_s {
   pas::PyrBatch* pyr_batch = nullptr;
   std::vector<int> member;
   std::vector<cudaEvent_t> res_join;
-  cudaEvent_t fork2 = nullptr;
+  std::vector<cudaStream_t> pstreams;  // one per persistent launch
+  std::vector<cudaEvent_t> pdone;
   // loops sharing a DM object: one batched residual per group (one basis pass)
   std::vector<std::vector<int>> rgroups;
   std::vector<int> rgroup_of;
@@ -445,7 +446,10 @@ void pas_batch_destroy(pas_batch_t b) {
   for (pas::BatchRecGroup* g : b->rec_groups) pas::batch_rec_destroy(g);
   for (cudaEvent_t e : b->res_join)
     if (e) cudaEventDestroy(e);
-  if (b->fork2) cudaEventDestroy(b->fork2);
+  for (cudaStream_t s : b->pstreams)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->pdone)
+    if (e) cudaEventDestroy(e);
   pas::pyr_batch_destroy(b->pyr_batch);
   for (pas::ResBatch* r : b->res_batches) pas::res_batch_destroy(r);
   for (cudaStream_t s : b->rstreams)
@@ -608,8 +612,14 @@ pas_status pas_batch_create_ex(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops
       }
     }
     b->res_join.assign(n_loops, nullptr);
-    e = cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming);
     for (int i = 0; i < n_loops && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->res_join[i], cudaEventDisableTiming);
+    const int np = b->pyr_batch ? pas::pyr_batch_n_groups(b->pyr_batch) : 0;
+    b->pstreams.assign(np, nullptr);
+    b->pdone.assign(np, nullptr);
+    for (int g = 0; g < np && e == cudaSuccess; ++g) {
+      e = cudaStreamCreateWithFlags(&b->pstreams[g], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->pdone[g], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
       pas_batch_destroy(b);
       return pas::set_error(ctx, PAS_ECUDA, "pas_batch_create: %s", cudaGetErrorString(e));
@@ -648,11 +658,10 @@ pas_status pas_batch_create_ex(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops
   for (int i = 0; i < n_loops && e == cudaSuccess && st == PAS_OK; ++i) {
     const int rg = b->rgroup_of[i];
     e = cudaStreamWaitEvent(b->streams[i], rg >= 0 ? b->rdone[rg] : b->fork, 0);
-    if (b->member[i] >= 0) {  // its residual; the persistent launch follows every one
+    if (b->member[i] >= 0) {  // its residual; its persistent launch follows
       if (rg >= 0) continue;
       if (e == cudaSuccess) st = enqueue_residual(b->loops[i], b->streams[i]);
       if (e == cudaSuccess && st == PAS_OK) e = cudaEventRecord(b->res_join[i], b->streams[i]);
-      if (e == cudaSuccess && st == PAS_OK) e = cudaStreamWaitEvent(cs, b->res_join[i], 0);
       continue;
     }
     if (e == cudaSuccess) st = loop_enqueue(b->loops[i], b->streams[i], nullptr, group_of[i] >= 0, rg >= 0);
@@ -660,11 +669,21 @@ pas_status pas_batch_create_ex(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops
     if (e == cudaSuccess && st == PAS_OK && group_of[i] < 0) e = cudaStreamWaitEvent(cs, b->join[i], 0);
   }
   if (b->pyr_batch && e == cudaSuccess && st == PAS_OK) {
-    st = pas::pyr_batch_launch(b->pyr_batch, cs);
-    if (st == PAS_OK) e = cudaEventRecord(b->fork2, cs);
+    // one persistent launch per transform length, on a stream of its own after the
+    // residuals of its loops; each loop's slopes and reconstruction after its launch
+    for (size_t g = 0; g < b->pstreams.size() && e == cudaSuccess && st == PAS_OK; ++g) {
+      for (int i = 0; i < n_loops && e == cudaSuccess; ++i) {
+        if (b->member[i] < 0 || pas::pyr_batch_group_of(b->pyr_batch, b->member[i]) != (int)g) continue;
+        const int rg = b->rgroup_of[i];
+        e = cudaStreamWaitEvent(b->pstreams[g], rg >= 0 ? b->rdone[rg] : b->res_join[i], 0);
+      }
+      if (e == cudaSuccess) st = pas::pyr_batch_launch_group(b->pyr_batch, (int)g, b->pstreams[g]);
+      if (e == cudaSuccess && st == PAS_OK) e = cudaEventRecord(b->pdone[g], b->pstreams[g]);
+      if (e == cudaSuccess && st == PAS_OK) e = cudaStreamWaitEvent(cs, b->pdone[g], 0);
+    }
     for (int i = 0; i < n_loops && e == cudaSuccess && st == PAS_OK; ++i) {
       if (b->member[i] < 0) continue;
-      e = cudaStreamWaitEvent(b->streams[i], b->fork2, 0);
+      e = cudaStreamWaitEvent(b->streams[i], b->pdone[pas::pyr_batch_group_of(b->pyr_batch, b->member[i])], 0);
       if (e == cudaSuccess) st = pas::pyr_batch_slopes(b->pyr_batch, b->member[i], b->streams[i], false);
       if (e == cudaSuccess && st == PAS_OK && group_of[i] < 0) st = enqueue_recon(b->loops[i], b->streams[i], true);
       if (e == cudaSuccess && st == PAS_OK) e = cudaEventRecord(b->join[i], b->streams[i]);
@@ -728,6 +747,14 @@ pas_status pas_batch_check(pas_batch_t b, uint32_t* h_fault) {
   if (h_fault) *h_fault = f | (w ? 0x100u : 0u);
   if (f) return pas::set_error(b->ctx, PAS_ETIMEOUT, "batched reconstruction: a product's wait gave up (%u)", f);
   if (w) return pas::set_error(b->ctx, PAS_ETIMEOUT, "persistent pyramid launch: a columns task's wait gave up");
+  return PAS_OK;
+}
+
+pas_status pas_batch_persistent_geometry(pas_batch_t b, int32_t g, int32_t* h_geo) {
+  if (!b || !h_geo) return pas::set_global_error(PAS_EINVAL, "pas_batch_persistent_geometry: NULL argument");
+  PAS_CHECK_ARG(b->ctx, b->pyr_batch && g >= 0 && g < pas::pyr_batch_n_groups(b->pyr_batch),
+                "pas_batch_persistent_geometry: no such persistent launch");
+  pas::pyr_batch_geometry(b->pyr_batch, g, h_geo);
   return PAS_OK;
 }
 

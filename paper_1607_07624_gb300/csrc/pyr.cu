@@ -826,6 +826,8 @@ struct PyrBatchGroup {
   BatchPyrArgs args{};
   int grid = 0, threads = 0;
   size_t smem = 0;
+  int rows = 1, row_chunk = 1;  // rows-task geometry chosen for the shared CTA
+  size_t counter_off = 0;       // its counters: ticket, rows_done[L]
 };
 
 struct PyrBatch {
@@ -913,24 +915,85 @@ pas_status pyr_batch_create(pas_ctx_t ctx, int n, const pas_pyr_t* y, const floa
     RowArgs* ra = reinterpret_cast<RowArgs*>(host.data() + o_ra);
     ColArgs* ca = reinterpret_cast<ColArgs*>(host.data() + o_ca);
     BatchLoopGeo* geo = reinterpret_cast<BatchLoopGeo*>(host.data() + o_geo);
-    int warps = 1, tickets = 0;
-    size_t smem = 0;
+    // The columns tasks keep each loop's own geometry (it fixes the order of the
+    // modulation-group sums); the CTA has the widest columns task's warps. The rows
+    // tasks' geometry does not change H (each transform is one warp's, whatever the
+    // CTA), so it is chosen for the shared CTA: the (rows, sin-chunk) pair with the
+    // least modelled time, each phase's work over its working warps per SM (at most
+    // 16 of them keep the issue slots busy).
+    int warps = 1;
+    size_t smem_c = 0;
+    double w_rows = 0.0, w_cols = 0.0, bw_sum = 0.0;
+    int n_s_max = 1;
     for (size_t k = 0; k < L; ++k) {
+      pas_pyr_t p = y[members[g][k]];
+      const int bw = p->b / p->H;
+      warps = std::max(warps, bw);
+      smem_c = std::max(smem_c, cols_smem(p, bw));
+      w_rows += (double)p->n_s * p->p.Np;
+      w_cols += (double)p->p.K * p->nd * p->b;
+      bw_sum += bw;
+      n_s_max = std::max(n_s_max, p->n_s);
+    }
+    int best_rows = 1, best_chunk = 1;
+    size_t best_smem = 0;
+    double best_t = -1.0;
+    // the opt-in shared memory of a CTA less the kernel's static shared memory
+    size_t smem_lim = 0;
+    {
+      cudaFuncAttributes fa;
+      int optin = 0;
+      e = cudaFuncGetAttributes(&fa, (const void*)grp.kern);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+      if (e == cudaSuccess) smem_lim = std::min(SMEM_MAX, (size_t)optin - fa.sharedSizeBytes);
+      if (e == cudaSuccess) e = raise_dyn_smem((const void*)grp.kern, smem_lim);
+    }
+    for (int rows = 1; rows <= std::min(warps, MAX_ROWS_PER_CTA) && e == cudaSuccess; rows *= 2) {
+      for (int c = 1; c <= n_s_max && e == cudaSuccess; ++c) {
+        size_t sm = smem_c;
+        for (size_t k = 0; k < L; ++k) {
+          pas_pyr_t p = y[members[g][k]];
+          const int nby = (p->n_s + c - 1) / c;
+          sm = std::max(sm, rows_smem(p, rows, (p->n_s + nby - 1) / nby));
+        }
+        if (sm > smem_lim) continue;
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, grp.kern, 32 * warps, sm);
+        if (e != cudaSuccess || occ < 1) continue;
+        // the OPD phasor is formed once per chunk: n_s / c of them per row
+        const double rows_work = w_rows * (1.0 + 0.25 / c);
+        const double t = rows_work / std::min(16.0, (double)occ * rows) +
+                         w_cols / std::min(16.0, occ * bw_sum / (double)L);
+        if (best_t < 0.0 || t < best_t) {
+          best_t = t;
+          best_rows = rows;
+          best_chunk = c;
+          best_smem = sm;
+        }
+      }
+    }
+    if (e == cudaSuccess && best_t < 0.0) {
+      pyr_batch_destroy(b);
+      return set_error(ctx, PAS_EINVAL, "persistent pyramid batch: no CTA shape fits an SM");
+    }
+    int tickets = 0;
+    const size_t smem = best_smem;
+    for (size_t k = 0; k < L && e == cudaSuccess; ++k) {
       const int i = members[g][k];
       pas_pyr_t p = y[i];
       ra[k] = make_row_args(p, opd[i]);
       ca[k] = make_col_args(p, frame[i], slopes[i], &extra[i], false);
+      const int nby = (p->n_s + best_chunk - 1) / best_chunk;
+      ra[k].s_chunk = (p->n_s + nby - 1) / nby;
       BatchLoopGeo& q = geo[k];
-      q.rows = p->rows;
-      q.nbx = (p->p.Np + p->rows - 1) / p->rows;
+      q.rows = best_rows;
+      q.nbx = (p->p.Np + best_rows - 1) / best_rows;
       q.row_base = tickets;
-      q.n_row = q.nbx * p->n_schunks;
+      q.n_row = q.nbx * nby;
       tickets += q.n_row;
       q.nd = p->nd;
       q.bw = p->b / p->H;
       q.n_col = p->nd * p->G * p->H;
-      warps = std::max(warps, std::max(q.rows, q.bw));
-      smem = std::max(smem, std::max(rows_smem(p, p->rows, p->s_chunk), cols_smem(p, q.bw)));
     }
     const int n_row_tickets = tickets;
     for (size_t k = 0; k < L; ++k) {
@@ -944,6 +1007,7 @@ pas_status pyr_batch_create(pas_ctx_t ctx, int n, const pas_pyr_t* y, const floa
     a.geo = reinterpret_cast<const BatchLoopGeo*>(dm + o_geo);
     a.ticket = b->d_counters + ctr;
     a.rows_done = b->d_counters + ctr + 1;
+    grp.counter_off = ctr;
     ctr += 1 + L;
     a.err = b->d_err;
     a.wait_limit = b->d_wait_limit;
@@ -953,11 +1017,8 @@ pas_status pyr_batch_create(pas_ctx_t ctx, int n, const pas_pyr_t* y, const floa
     a.first_ticket = 0;
     grp.threads = 32 * warps;
     grp.smem = smem;
-    if (smem > SMEM_MAX) {
-      pyr_batch_destroy(b);
-      return set_error(ctx, PAS_EINVAL, "persistent pyramid batch: %zu bytes of shared memory per CTA", smem);
-    }
-    e = raise_dyn_smem((const void*)grp.kern, smem);
+    grp.rows = best_rows;
+    grp.row_chunk = best_chunk;
     int occ = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, grp.kern, grp.threads, smem);
     if (e == cudaSuccess && occ < 1) {
@@ -983,16 +1044,36 @@ pas_status pyr_batch_create(pas_ctx_t ctx, int n, const pas_pyr_t* y, const floa
 // Both passes of every member on `st`: the counters are zeroed, then one persistent
 // launch per transform length (in group order). columns_only: the queue starts at
 // the columns-pass tickets, the rows pass is withheld (a diagnostic of the waits).
-pas_status pyr_batch_launch(PyrBatch* b, cudaStream_t st, bool columns_only) {
-  cudaError_t e = cudaMemsetAsync(b->d_counters, 0, b->counter_bytes, st);
-  for (size_t g = 0; g < b->groups.size() && e == cudaSuccess; ++g) {
-    const PyrBatchGroup& grp = b->groups[g];
-    BatchPyrArgs a = grp.args;
-    if (columns_only) a.first_ticket = a.n_row_tickets;
-    e = launch_k(grp.kern, dim3(grp.grid), dim3(grp.threads), grp.smem, st, false, a);
-  }
+pas_status pyr_batch_launch_group(PyrBatch* b, int g, cudaStream_t st, bool columns_only) {
+  const PyrBatchGroup& grp = b->groups[g];
+  BatchPyrArgs a = grp.args;
+  if (columns_only) a.first_ticket = a.n_row_tickets;
+  cudaError_t e = cudaMemsetAsync(b->d_counters + grp.counter_off, 0, sizeof(unsigned int) * (1 + a.n_loops), st);
+  if (e == cudaSuccess) e = launch_k(grp.kern, dim3(grp.grid), dim3(grp.threads), grp.smem, st, false, a);
   if (e != cudaSuccess) return set_error(b->ctx, PAS_ECUDA, "persistent pyramid batch launch: %s", cudaGetErrorString(e));
   return PAS_OK;
+}
+
+pas_status pyr_batch_launch(PyrBatch* b, cudaStream_t st, bool columns_only) {
+  for (size_t g = 0; g < b->groups.size(); ++g) {
+    const pas_status s = pyr_batch_launch_group(b, (int)g, st, columns_only);
+    if (s != PAS_OK) return s;
+  }
+  return PAS_OK;
+}
+
+int pyr_batch_group_of(const PyrBatch* b, int i) { return b->group_of[i]; }
+
+void pyr_batch_geometry(const PyrBatch* b, int g, int* h) {
+  const PyrBatchGroup& grp = b->groups[g];
+  h[0] = grp.N;
+  h[1] = grp.grid;
+  h[2] = grp.threads;
+  h[3] = (int)grp.smem;
+  h[4] = grp.rows;
+  h[5] = grp.row_chunk;
+  h[6] = grp.args.n_row_tickets;
+  h[7] = grp.args.n_tickets - grp.args.n_row_tickets;
 }
 
 // Member i's slopes kernel on `st` (after pyr_batch_launch); pdl: it follows a

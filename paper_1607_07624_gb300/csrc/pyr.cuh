@@ -41,6 +41,12 @@ constexpr long long PAS_BATCH_WAIT_DEFAULT = 1ll << 21;  // polls: about a secon
 pas_status pyr_batch_create(pas_ctx_t ctx, int n, const pas_pyr_t* y, const float* const* opd, float* const* frame,
                             float* const* slopes, const LoopExtra* extra, PyrBatch** out);
 pas_status pyr_batch_launch(PyrBatch* b, cudaStream_t st, bool columns_only = false);
+// Group g alone (its counters zeroed first); the groups are independent.
+pas_status pyr_batch_launch_group(PyrBatch* b, int g, cudaStream_t st, bool columns_only = false);
+int pyr_batch_group_of(const PyrBatch* b, int i);  // member i's group (transform length)
+// h[8]: N, CTAs, threads per CTA, shared bytes, rows per rows task, sin chunk,
+// rows tasks, columns tasks of group g
+void pyr_batch_geometry(const PyrBatch* b, int g, int* h);
 pas_status pyr_batch_slopes(PyrBatch* b, int i, cudaStream_t st, bool pdl);
 int pyr_batch_n_groups(const PyrBatch* b);
 unsigned int* pyr_batch_err(PyrBatch* b);

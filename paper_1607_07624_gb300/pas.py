@@ -149,6 +149,7 @@ _SIGS = {
     "pas_batch_create_ex": (C.c_int, [vp, vp, i32, C.c_uint32, P(vp)]),
     "pas_batch_n_persistent": (i32, [vp]),
     "pas_batch_n_residual_groups": (i32, [vp]),
+    "pas_batch_persistent_geometry": (C.c_int, [vp, i32, P(i32)]),
     "pas_batch_set_wait_limit": (C.c_int, [vp, i64]),
     "pas_batch_probe_waits": (C.c_int, [vp, C.POINTER(C.c_uint32)]),
     "pas_calib_interaction_matrix": (C.c_int, [vp, vp, vp, C.c_double, vp]),
@@ -604,6 +605,14 @@ def pas_batch_create_ex(ctx, loops, flags=0):
 
 def pas_batch_n_persistent(batch) -> int:
     return int(_lib.pas_batch_n_persistent(batch))
+
+
+def pas_batch_persistent_geometry(batch, ctx, g):
+    """Dict of persistent launch g's geometry."""
+    h = (i32 * 8)()
+    _check(_lib.pas_batch_persistent_geometry(batch, int(g), h), ctx)
+    keys = ("N", "ctas", "threads", "smem_bytes", "rows_per_task", "sin_per_task", "rows_tasks", "columns_tasks")
+    return dict(zip(keys, [int(v) for v in h]))
 
 
 def pas_batch_n_residual_groups(batch) -> int:

@@ -161,6 +161,11 @@ def test_persistent_batch_reproduces_single_loops():
         ctx = systems[0].ctx
         batch = pas.pas_batch_create_ex(ctx, [s.loop for s in systems], pas.PAS_BATCH_PERSISTENT)
         assert pas.pas_batch_n_persistent(batch) == 2          # N = 128 and N = 64
+        geo = [pas.pas_batch_persistent_geometry(batch, ctx, g) for g in range(2)]
+        assert sorted(g_["N"] for g_ in geo) == [64, 128]
+        for g_ in geo:
+            assert g_["threads"] % 32 == 0 and g_["ctas"] >= 1 and g_["columns_tasks"] > 0
+            assert g_["rows_per_task"] in (1, 2, 4, 8) and g_["rows_per_task"] * 32 <= g_["threads"]
         # 5 pyramid loops: residual + slopes + reconstruction; the SH loop whole (3); the
         # three loops sharing a DM: one gather and one residual kernel in place of 3
         assert pas.pas_batch_n_residual_groups(batch) == 1
