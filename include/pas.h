@@ -141,6 +141,31 @@ pas_status pas_atmo_create_view(pas_atmo_t base, const double* h_ox, const doubl
  * outside (0, 1] or a non-finite offset. */
 pas_status pas_atmo_create_cone_view(pas_atmo_t base, const double* h_ox, const double* h_oy,
                                      const double* h_scale, pas_atmo_t* out);
+/* Tap staging of the loop's residual kernel (Sec. GPU acceleration: the layers are
+ * sampled where the pupil pixels see them): for a source at infinity the two screen rows
+ * each pupil-row segment of a 64-pixel tile samples are copied by TMA (one-row boxes,
+ * from the segment's first column rounded down to 16 bytes, a second box from column 0
+ * where the columns wrap around the periodic screen) while the tile's basis streams.
+ * pas_atmo_tma: 1 when it applies to this object (S a multiple of 4 and >= 68, screens
+ * 16-byte aligned, no cone effect), 0 when the 4-byte asynchronous copies are used, -1
+ * for NULL. The values are the same either way, bit for bit. Host only. */
+int32_t pas_atmo_tma(pas_atmo_t atmo);
+/* Which staging loops created afterwards on this object use: PAS_TAPS_AUTO (default:
+ * TMA where pas_atmo_tma is 1 and the DM has at least 1000 modes, the 4-byte copies
+ * otherwise), PAS_TAPS_TMA (PAS_EINVAL where pas_atmo_tma is 0), PAS_TAPS_COPY. Views
+ * created afterwards inherit it. Host only. */
+#define PAS_TAPS_AUTO 0
+#define PAS_TAPS_TMA 1
+#define PAS_TAPS_COPY 2
+pas_status pas_atmo_set_tap_staging(pas_atmo_t atmo, int32_t mode);
+/* Tries of the staging's mbarrier wait before it gives up, flags the object and waits
+ * again with the long bound (default 2^22, seconds; 0 gives up at once, without
+ * testing). Taken by loops created afterwards. Host only. */
+pas_status pas_atmo_set_wait_limit(pas_atmo_t atmo, uint32_t tries);
+/* Synchronous: PAS_ETIMEOUT if a staging wait of a residual on this atmosphere (or a
+ * view of it) gave up since the last check (the flag is cleared); h_fault optional:
+ * bit 0 a first wait gave up, bit 1 the second too. */
+pas_status pas_atmo_check(pas_atmo_t atmo, uint32_t* h_fault);
 void pas_atmo_destroy(pas_atmo_t atmo);
 
 /* ------------------------------------------------------ modulated pyramid

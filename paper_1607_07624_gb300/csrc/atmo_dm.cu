@@ -10,6 +10,7 @@
 #include "atmo_dm.cuh"
 #include "internal.h"
 #include "pdl.cuh"
+#include "tc.cuh"
 
 namespace pas {
 
@@ -158,6 +159,15 @@ __global__ void atmo_kernel(AtmoArgs a, const long long* d_step, long long h_ste
 constexpr int RES_THREADS = 256;
 constexpr int RES_U = 5;            // loads in flight per thread
 
+// Floats of the residual kernel's shared head: the command, which the ROWS partial
+// sums per pixel and the L bilinear values per pixel replace after the stream.
+template <typename T>
+__host__ __device__ inline int res_head(int n_m, int L) {
+  constexpr int rows = RES_THREADS / (RES_TILE / (16 / (int)sizeof(T)));
+  const int post = (rows + L) * RES_TILE;
+  return n_m > post ? n_m : (post > 1 ? post : 1);
+}
+
 __device__ __forceinline__ uint4 ld_stream16(const void* p) {
   uint4 v;
   asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
@@ -189,6 +199,16 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
                "l"(src)
                : "memory");
 }
+// One box of 2 rows x RES_BOX floats of layer z from screen row y, column x (a
+// multiple of 4) into shared memory (128-byte aligned), counted on `bar` in bytes.
+__device__ __forceinline__ void tma_load_box(float* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          tc::smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(tc::smem_addr(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
@@ -199,17 +219,27 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // hides under the stream; otherwise the atmosphere is read from opd_atm (or zero).
 // CONE: a source at finite height; each (layer, pixel) has its own taps and
 // weights (cone_shift), the weights kept in shared memory after the taps.
-template <typename T, bool CONE>
-__global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(ResArgs a) {
+// TMA (sources at infinity, a.tma): the taps come as tensor copies instead: per layer
+// and pupil-row segment of the tile, one box of the two screen rows it samples,
+// RES_BOX floats from the segment's first column rounded down to 16 bytes, issued by
+// one thread on one mbarrier before the basis stream and read back after it. Taps
+// past the screen's last row or column (the periodic screen wraps there; the box
+// holds the fill value) are read from global memory instead.
+template <typename T, bool CONE, bool TMA>
+__global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(const __grid_constant__ ResArgs a) {
   constexpr int VEC = 16 / (int)sizeof(T);         // pixels per 16-byte load
   constexpr int COLS = RES_TILE / VEC;              // loads per mode row
   constexpr int ROWS = RES_THREADS / COLS;          // modes per CTA-wide load
-  extern __shared__ float c_s[];                    // [n_m], then the taps [L][4][RES_TILE]
-  __shared__ float red[ROWS][RES_TILE];
+  // [P] the command (after the stream: the ROWS partial sums [ROWS][RES_TILE], then
+  // with TMA the bilinear values [L][RES_TILE]), then the taps [L][4][RES_TILE] or the
+  // boxes
+  extern __shared__ float c_s[];
   __shared__ int s_flat[RES_TILE];
   __shared__ double wred[2][RES_THREADS / 32];
   __shared__ int six[PAS_MAX_LAYERS], siy[PAS_MAX_LAYERS];
   __shared__ float sfx[PAS_MAX_LAYERS], sfy[PAS_MAX_LAYERS];
+  __shared__ int4 s_seg[TMA ? RES_SEG_MAX : 1];
+  __shared__ __align__(8) uint64_t tbar;
   const int tid = threadIdx.x;
   const T* MT = nullptr;
   if constexpr (sizeof(T) == 4) MT = a.MT;
@@ -226,6 +256,14 @@ __global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(ResArgs a) {
   const int base = blockIdx.x * RES_TILE;
   const int L = a.atmo.L;
   if (tid < RES_TILE) s_flat[tid] = base + tid < a.n_pix ? a.pix[base + tid] : 0;  // constant
+  if constexpr (TMA) {
+    if (tid < a.seg_max) s_seg[tid] = a.seg[(size_t)blockIdx.x * a.seg_max + tid];  // constant
+    if (tid == 0) {
+      tc::mbar_init(&tbar, 1);
+      tc::fence_barrier_init();
+    }
+    if (tid == 32) tc::prefetch_tensormap(&a.tmap);
+  }
   pdl_trigger();
   pdl_wait();
   const long long step = a.d_step ? *a.d_step : a.h_step;
@@ -237,9 +275,38 @@ __global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(ResArgs a) {
   }
   for (int m = tid; m < n_m; m += RES_THREADS) c_s[m] = cmd[m];
   __syncthreads();
-  float* taps = c_s + max(a.n_m, 1);
+  float* taps = c_s + res_head<T>(a.n_m, L);
   float* wts = taps + L * 4 * RES_TILE;             // CONE: [L][2][RES_TILE] weights
-  if (L > 0) {
+  // TMA: boxes [L][seg_max][RES_BOX_PITCH] (2 rows of RES_BOX), from the first
+  // 128-byte boundary after the command
+  float* boxes = nullptr;
+  if constexpr (TMA) {
+    const uint32_t sa = tc::smem_addr(taps);
+    boxes = taps + (((sa + 127u) & ~127u) - sa) / 4u;
+  }
+  const int S = a.atmo.S;
+  if constexpr (TMA) {
+    // thread 0 announces the bytes; thread t < L seg_max copies box (t / seg_max,
+    // t % seg_max) (a copy that lands before the announcement leaves the phase open:
+    // it completes on thread 0's arrival)
+    if (tid == 0 && L > 0) {
+      int ns = 0;
+      for (int sg = 0; sg < a.seg_max; ++sg) ns += s_seg[sg].z > 0 ? 1 : 0;
+      tc::mbar_arrive_expect_tx(&tbar, (uint32_t)(L * ns) * 2u * RES_BOX * 4u);
+    }
+    if (tid < L * a.seg_max) {
+      const int l = tid / a.seg_max, sg = tid - l * a.seg_max;
+      const int4 q = s_seg[sg];
+      if (q.z > 0) {
+        int c = q.y + siy[l];
+        if (c >= S) c -= S;
+        int row = q.x + six[l];
+        if (row >= S) row -= S;
+        tma_load_box(boxes + (size_t)tid * RES_BOX_PITCH, &a.tmap, &tbar, c & ~3, row, l);
+      }
+    }
+  }
+  if (!TMA && L > 0) {
     const int S = a.atmo.S;
     for (int t = tid; t < L * RES_TILE; t += RES_THREADS) {
       const int l = t / RES_TILE, q = t - l * RES_TILE;
@@ -281,9 +348,46 @@ __global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(ResArgs a) {
       if (mn < n_m) v[u] = ld_stream16(blk + (size_t)mn * RES_TILE);
     }
   }
+  __syncthreads();  // every thread is done with the command
+  float* red = c_s;
 #pragma unroll
-  for (int i = 0; i < VEC; ++i) red[row][col * VEC + i] = acc[i];
-  if (L > 0) {
+  for (int i = 0; i < VEC; ++i) red[row * RES_TILE + col * VEC + i] = acc[i];
+  if constexpr (TMA) {
+    // the boxes have landed (the threads that read them wait; a wait that gives up
+    // flags the atmosphere and waits again, with the long bound, so that no copy is
+    // in flight when the CTA moves on)
+    if (L > 0 && !tc::mbar_wait(&tbar, 0, a.wait_limit)) {
+      if (a.err) atomicOr(a.err, 1u);
+      if (!tc::mbar_wait(&tbar, 0, tc::WAIT_LIMIT) && a.err) atomicOr(a.err, 2u);
+    }
+    // each (layer, pixel) pair's bilinear value, [L][RES_TILE] after the partial sums:
+    // the pixel's segment, its column offset in the segment's box, taps past the
+    // screen's last row or column from global memory
+    float* bil = c_s + ROWS * RES_TILE;
+    for (int t = tid; t < L * RES_TILE; t += RES_THREADS) {
+      const int l = t / RES_TILE, px = t - l * RES_TILE;
+      if (base + px < a.n_pix) {
+        int si = 0;
+        for (int sg = 1; sg < a.seg_max; ++sg)
+          if (s_seg[sg].z > 0 && px >= s_seg[sg].w) si = sg;
+        const int4 q = s_seg[si];
+        int c = q.y + siy[l];
+        if (c >= S) c -= S;
+        int r0 = q.x + six[l];
+        if (r0 >= S) r0 -= S;
+        const int x0 = c & ~3, u0 = c - x0 + (px - q.w);
+        const float* bx = boxes + (size_t)(l * a.seg_max + si) * RES_BOX_PITCH;
+        const float* sc = a.atmo.screens + (size_t)l * S * S;
+        auto tap = [&](int r, int u) {
+          const int rr = r0 + r, cc = x0 + u;
+          if (rr < S && cc < S) return bx[r * RES_BOX + u];
+          return __ldg(sc + (size_t)(rr < S ? rr : rr - S) * S + (cc < S ? cc : cc - S));
+        };
+        bil[t] = bilinear(sfx[l], sfy[l], tap(0, u0), tap(1, u0), tap(0, u0 + 1), tap(1, u0 + 1));
+      }
+    }
+  }
+  if (!TMA && L > 0) {
     // each (layer, pixel) pair's bilinear value replaces its first tap
     cp_async_wait_all();
     __syncthreads();
@@ -310,14 +414,17 @@ __global__ void __launch_bounds__(RES_THREADS, 5) residual_kernel(ResArgs a) {
   if (px < RES_TILE && p < a.n_pix) {
     const int flat = s_flat[px];
     float atm = 0.f;
-    if (L > 0) {
+    if (TMA && L > 0) {
+      const float* bil = c_s + ROWS * RES_TILE;
+      for (int l = 0; l < L; ++l) atm = __fadd_rn(atm, bil[l * RES_TILE + px]);
+    } else if (L > 0) {
       for (int l = 0; l < L; ++l) atm = __fadd_rn(atm, taps[l * 4 * RES_TILE + px]);
     } else if (a.opd_atm) {
       atm = a.opd_atm[flat];
     }
     float dm = 0.f;
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) dm += red[r][px];
+    for (int r = 0; r < ROWS; ++r) dm += red[r * RES_TILE + px];
     const float r = atm - a.dm_sign * dm;
     a.out[flat] = r;
     s1 = r;
@@ -371,23 +478,24 @@ int residual_tiles(int n_pix) { return (n_pix + RES_TILE - 1) / RES_TILE; }
 
 // The residual kernel streams its basis through registers, not the L1 cache: its
 // launch bounds (at most 51 registers) and a shared-memory carveout preference keep
-// five CTAs resident per SM (one wave for the 700 tiles of a 240 px pupil).
-template <typename T, bool CONE>
+// five CTAs resident per SM (one wave for the 700 tiles of a 240 px pupil); the rest of
+// the unified memory stays L1, where the loads in flight land.
+template <typename T, bool CONE, bool TMA>
 static cudaError_t residual_prepare(size_t smem) {
   static bool carveout_set = false;
-  cudaError_t e = raise_dyn_smem((const void*)residual_kernel<T, CONE>, smem);
+  cudaError_t e = raise_dyn_smem((const void*)residual_kernel<T, CONE, TMA>, smem);
   if (e == cudaSuccess && !carveout_set) {
-    e = cudaFuncSetAttribute((const void*)residual_kernel<T, CONE>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             50);
+    e = cudaFuncSetAttribute((const void*)residual_kernel<T, CONE, TMA>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 50);
     carveout_set = e == cudaSuccess;
   }
   return e;
 }
 
-template <typename T, bool CONE>
+template <typename T, bool CONE, bool TMA>
 static cudaError_t residual_start(const ResArgs& a, int tiles, size_t smem, cudaStream_t st, bool pdl) {
-  cudaError_t e = residual_prepare<T, CONE>(smem);
-  if (e == cudaSuccess) e = launch_k(residual_kernel<T, CONE>, dim3(tiles), dim3(RES_THREADS), smem, st, pdl, a);
+  cudaError_t e = residual_prepare<T, CONE, TMA>(smem);
+  if (e == cudaSuccess) e = launch_k(residual_kernel<T, CONE, TMA>, dim3(tiles), dim3(RES_THREADS), smem, st, pdl, a);
   return e;
 }
 
@@ -397,15 +505,20 @@ pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, boo
   if (a.atmo.L < 0 || a.atmo.L > PAS_MAX_LAYERS)
     return set_error(ctx, PAS_EINVAL, "residual kernel: 0 <= layers <= %d", PAS_MAX_LAYERS);
   const bool cone = a.atmo.L > 0 && a.atmo.cone;
+  const bool tma = a.atmo.L > 0 && !cone && a.tma && a.seg && a.seg_max >= 1 && a.seg_max <= RES_SEG_MAX;
+  const int head = a.MTb ? res_head<__nv_bfloat16>(a.n_m, a.atmo.L) : res_head<float>(a.n_m, a.atmo.L);
   const size_t smem =
-      sizeof(float) * ((size_t)std::max(a.n_m, 1) + (size_t)a.atmo.L * (cone ? 6 : 4) * RES_TILE);
+      tma ? sizeof(float) * ((size_t)head + 32 + (size_t)a.atmo.L * a.seg_max * RES_BOX_PITCH)
+          : sizeof(float) * ((size_t)head + (size_t)a.atmo.L * (cone ? 6 : 4) * RES_TILE);
   cudaError_t e;
   if (a.MTb)
-    e = cone ? residual_start<__nv_bfloat16, true>(a, tiles, smem, st, pdl)
-             : residual_start<__nv_bfloat16, false>(a, tiles, smem, st, pdl);
+    e = cone  ? residual_start<__nv_bfloat16, true, false>(a, tiles, smem, st, pdl)
+        : tma ? residual_start<__nv_bfloat16, false, true>(a, tiles, smem, st, pdl)
+              : residual_start<__nv_bfloat16, false, false>(a, tiles, smem, st, pdl);
   else
-    e = cone ? residual_start<float, true>(a, tiles, smem, st, pdl)
-             : residual_start<float, false>(a, tiles, smem, st, pdl);
+    e = cone  ? residual_start<float, true, false>(a, tiles, smem, st, pdl)
+        : tma ? residual_start<float, false, true>(a, tiles, smem, st, pdl)
+              : residual_start<float, false, false>(a, tiles, smem, st, pdl);
   if (e != cudaSuccess) return set_error(ctx, PAS_ECUDA, "residual kernel launch: %s", cudaGetErrorString(e));
   return PAS_OK;
 }
@@ -733,6 +846,22 @@ pas_status pas_atmo_create(pas_ctx_t ctx, const pas_atmo_params* p, const float*
     a->args.vx[l] = l < p->n_layers ? p->vx[l] : 0.0;
     a->args.vy[l] = l < p->n_layers ? p->vy[l] : 0.0;
   }
+  pas_status st = pas::dev_alloc(ctx, (void**)&a->d_err, sizeof(unsigned int));
+  if (st != PAS_OK) {
+    delete a;
+    return st;
+  }
+  a->owns_err = true;
+  cudaError_t e = cudaMemset(a->d_err, 0, sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    pas_atmo_destroy(a);
+    return pas::set_error(ctx, PAS_ECUDA, "pas_atmo_create: %s", cudaGetErrorString(e));
+  }
+  // the screens as [L][S][S] floats for two-row boxes of the tap staging: a row pitch
+  // of whole 16-byte units, a box no wider than a row, a 16-byte aligned start
+  if (p->S % 4 == 0 && p->S >= pas::RES_BOX && (reinterpret_cast<uintptr_t>(d_screens) & 15) == 0)
+    a->tma = pas::make_tmap_rows_f32(&a->tmap, d_screens, (uint64_t)p->S, (uint64_t)p->n_layers,
+                                     (uint32_t)pas::RES_BOX);
   *out = a;
   return PAS_OK;
 }
@@ -756,6 +885,7 @@ pas_status pas_atmo_create_cone_view(pas_atmo_t base, const double* h_ox, const 
       PAS_CHECK_ARG(base->ctx, h_scale[l] > 0.0 && h_scale[l] <= 1.0, "pas_atmo_create_cone_view: scales in (0, 1]");
   }
   pas_atmo_t a = new pas_atmo_s(*base);
+  a->owns_err = false;  // the base's error word
   a->args.cone = 0;
   for (int l = 0; l < PAS_MAX_LAYERS; ++l) {
     // the view's pupil position p maps to c + (p - c) s_base + o_base in the base
@@ -774,13 +904,46 @@ pas_status pas_atmo_create_view(pas_atmo_t base, const double* h_ox, const doubl
   return pas_atmo_create_cone_view(base, h_ox, h_oy, nullptr, out);
 }
 
-void pas_atmo_destroy(pas_atmo_t a) { delete a; }
+void pas_atmo_destroy(pas_atmo_t a) {
+  if (!a) return;
+  if (a->owns_err) pas::dev_free(a->d_err);
+  delete a;
+}
+
+int32_t pas_atmo_tma(pas_atmo_t a) { return a ? (a->tma && !a->args.cone ? 1 : 0) : -1; }
+
+pas_status pas_atmo_set_tap_staging(pas_atmo_t a, int32_t mode) {
+  if (!a) return pas::set_global_error(PAS_EINVAL, "pas_atmo_set_tap_staging: NULL atmosphere");
+  PAS_CHECK_ARG(a->ctx, mode == PAS_TAPS_AUTO || mode == PAS_TAPS_TMA || mode == PAS_TAPS_COPY,
+                "pas_atmo_set_tap_staging: mode PAS_TAPS_AUTO, PAS_TAPS_TMA or PAS_TAPS_COPY");
+  PAS_CHECK_ARG(a->ctx, mode != PAS_TAPS_TMA || pas_atmo_tma(a) == 1,
+                "pas_atmo_set_tap_staging: these screens or this source do not allow TMA staging");
+  a->taps = mode;
+  return PAS_OK;
+}
+
+pas_status pas_atmo_set_wait_limit(pas_atmo_t a, uint32_t tries) {
+  if (!a) return pas::set_global_error(PAS_EINVAL, "pas_atmo_set_wait_limit: NULL atmosphere");
+  a->wait_limit = tries;
+  return PAS_OK;
+}
+
+pas_status pas_atmo_check(pas_atmo_t a, uint32_t* h_fault) {
+  if (!a) return pas::set_global_error(PAS_EINVAL, "pas_atmo_check: NULL atmosphere");
+  unsigned int f = 0;
+  PAS_CUDA_TRY(a->ctx, cudaMemcpy(&f, a->d_err, sizeof(f), cudaMemcpyDeviceToHost));
+  if (f) PAS_CUDA_TRY(a->ctx, cudaMemset(a->d_err, 0, sizeof(unsigned int)));
+  if (h_fault) *h_fault = f;
+  if (f) return pas::set_error(a->ctx, PAS_ETIMEOUT, "atmosphere tap staging: a wait gave up (%u)", f);
+  return PAS_OK;
+}
 
 void pas_dm_destroy(pas_dm_t d) {
   if (!d) return;
   pas::dev_free(d->d_MT);
   pas::dev_free(d->d_MTb);
   pas::dev_free(d->d_pix);
+  pas::dev_free(d->d_seg);
   delete d;
 }
 
@@ -834,6 +997,45 @@ pas_status pas_dm_create(pas_ctx_t ctx, const float* h_M, int32_t n_pix, int32_t
     e = cudaMemcpy(d->d_MT, MT.data(), sizeof(float) * MT.size(), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = cudaMemcpy(d->d_pix, pix.data(), sizeof(int32_t) * n_pix, cudaMemcpyHostToDevice);
+  // each tile's runs of consecutive pixels of one pupil row (the TMA tap staging's
+  // segments); a tile with more than RES_SEG_MAX keeps the 4-byte copies for all
+  std::vector<int4> seg;
+  int smax = 0;
+  for (int t = 0; t < tiles; ++t) {
+    int ns = 0;
+    for (int q = 0; q < pas::RES_TILE && t * pas::RES_TILE + q < n_pix; ++q) {
+      const int f = pix[t * pas::RES_TILE + q], i = f / Np, j = f - i * Np;
+      if (q > 0) {
+        const int g = pix[t * pas::RES_TILE + q - 1];
+        if (g / Np == i && g - (g / Np) * Np == j - 1) continue;
+      }
+      ++ns;
+    }
+    smax = std::max(smax, ns);
+  }
+  if (e == cudaSuccess && smax >= 1 && smax <= pas::RES_SEG_MAX) {
+    seg.assign((size_t)tiles * smax, make_int4(0, 0, 0, 0));
+    for (int t = 0; t < tiles; ++t) {
+      int ns = -1;
+      for (int q = 0; q < pas::RES_TILE && t * pas::RES_TILE + q < n_pix; ++q) {
+        const int f = pix[t * pas::RES_TILE + q], i = f / Np, j = f - i * Np;
+        bool cont = false;
+        if (q > 0) {
+          const int g = pix[t * pas::RES_TILE + q - 1];
+          cont = g / Np == i && g - (g / Np) * Np == j - 1;
+        }
+        if (!cont) seg[(size_t)t * smax + ++ns] = make_int4(i, j, 0, q);
+        seg[(size_t)t * smax + ns].z += 1;
+      }
+    }
+    st = pas::dev_alloc(ctx, (void**)&d->d_seg, sizeof(int4) * seg.size());
+    if (st != PAS_OK) {
+      pas_dm_destroy(d);
+      return st;
+    }
+    e = cudaMemcpy(d->d_seg, seg.data(), sizeof(int4) * seg.size(), cudaMemcpyHostToDevice);
+    d->seg_max = smax;
+  }
   if (e != cudaSuccess) {
     pas_dm_destroy(d);
     return pas::set_error(ctx, PAS_ECUDA, "pas_dm_create: %s", cudaGetErrorString(e));

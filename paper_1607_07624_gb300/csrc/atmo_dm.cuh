@@ -1,5 +1,6 @@
 // Shared declarations of the atmosphere / DM objects and their kernels.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include "internal.h"
 
@@ -35,7 +36,30 @@ struct ResArgs {
   float dm_sign = 1.0f;            // out = atm - dm_sign * M c
   float* out = nullptr;            // [Np][Np], pupil pixels written
   double2* wfe_part = nullptr;     // per-CTA (sum r, sum r^2) or null
+  // TMA staging of the layer taps (sources at infinity): the screens' tensor map
+  // (boxes of 2 rows x RES_BOX floats), the tile's pupil-row segments, the wait
+  // bound and the atmosphere's error word. tma = 0: 4-byte asynchronous copies.
+  CUtensorMap tmap;
+  int tma = 0;
+  const int4* seg = nullptr;       // [tiles][seg_max] (row i, first column, pixels, first tile pixel)
+  int seg_max = 0;
+  unsigned int* err = nullptr;
+  uint32_t wait_limit = 0;
 };
+
+// Floats per row of a TMA box of the tap staging: a segment of at most RES_TILE pupil
+// pixels needs RES_TILE + 1 columns from a start rounded down to 16 bytes.
+constexpr int RES_BOX = RES_TILE + 4;
+// Shared-memory stride of one box (2 rows): the destinations of tensor copies on 128
+// bytes.
+constexpr int RES_BOX_PITCH = 160;
+// Most pupil-row segments of a tile with TMA staging (more: 4-byte copies).
+constexpr int RES_SEG_MAX = 8;
+// PAS_TAPS_AUTO stages by TMA from this many modes up, where a tile's basis stream
+// hides the boxes' latency (measured on GB300: equal times at 4000 modes, 216 and 408
+// us for bf16 and float32 bases; at 400 modes, one wave of short CTAs, the 4-byte
+// copies 0.2-0.3 us ahead of 14.6 and 19.2 us).
+constexpr int RES_TMA_MIN_MODES = 1000;
 
 // One loop of a batched residual (loops sharing one DM object).
 struct ResBatchLoop {
@@ -67,6 +91,10 @@ pas_status res_batch_create(pas_ctx_t ctx, pas_dm_t dm, int B, const ResBatchLoo
 pas_status res_batch_launch(ResBatch* r, cudaStream_t st);
 void res_batch_destroy(ResBatch* r);
 
+// Tensor map of L screens of S x S floats for boxes of 2 rows x `box` floats (false if
+// the encoder rejects it or is unavailable).
+bool make_tmap_rows_f32(CUtensorMap* map, const float* base, uint64_t S, uint64_t L, uint32_t box);
+
 // pdl: launch as a programmatic dependent of the preceding kernel in `st`.
 pas_status residual_launch(pas_ctx_t ctx, const ResArgs& a, cudaStream_t st, bool pdl = false);
 // Number of CTAs (and of residual-WFE partials) of residual_launch for n_pix pixels.
@@ -79,6 +107,14 @@ pas_status dm_project_launch(pas_dm_t dm, const float* opd, float* coeffs, cudaS
 struct pas_atmo_s {
   pas_ctx_t ctx = nullptr;
   pas::AtmoArgs args;
+  // the screens as a tensor of [L][S][S] floats for TMA boxes of two rows (when S is a
+  // multiple of 4 no smaller than a box and the screens start on 16 bytes)
+  CUtensorMap tmap;
+  bool tma = false;
+  unsigned int* d_err = nullptr;  // owned by the base object, shared by its views
+  bool owns_err = false;
+  uint32_t wait_limit = 1u << 22;
+  int taps = PAS_TAPS_AUTO;       // pas_atmo_set_tap_staging
 };
 
 struct pas_dm_s {
@@ -89,6 +125,10 @@ struct pas_dm_s {
   __nv_bfloat16* d_MTb = nullptr;   // PAS_BF16 basis
   pas_precision prec = PAS_FP32;
   int32_t* d_pix = nullptr;
+  // per residual tile: its pupil-row segments (row, first column, pixels, first tile
+  // pixel), seg_max per tile, unused entries with 0 pixels
+  int4* d_seg = nullptr;
+  int seg_max = 0;
 };
 
 namespace pas {
@@ -101,6 +141,19 @@ inline ResArgs make_res_args(pas_dm_t d) {
   a.n_pad = d->n_pad;
   a.n_m = d->n_modes;
   a.Np = d->Np;
+  a.seg = d->d_seg;
+  a.seg_max = d->seg_max;
   return a;
+}
+
+// The atmosphere of a residual: its layers, and the TMA staging of their taps when
+// the screens allow it and the source is at infinity.
+inline void res_args_set_atmo(ResArgs& a, pas_atmo_t at) {
+  a.atmo = at->args;
+  const bool want = at->taps == PAS_TAPS_TMA || (at->taps == PAS_TAPS_AUTO && a.n_m >= RES_TMA_MIN_MODES);
+  a.tma = want && at->tma && !at->args.cone && a.seg != nullptr ? 1 : 0;
+  if (a.tma) a.tmap = at->tmap;
+  a.err = at->d_err;
+  a.wait_limit = at->wait_limit;
 }
 }  // namespace pas

@@ -48,7 +48,7 @@ struct pas_loop_s {
 // the wind-shifted layers at its pupil pixels while its other warps stream the basis).
 static pas_status enqueue_residual(pas_loop_t L, cudaStream_t st) {
   pas::ResArgs ra = pas::make_res_args(L->dm);
-  ra.atmo = L->atmo->args;
+  pas::res_args_set_atmo(ra, L->atmo);
   ra.opd_atm = nullptr;
   ra.cmd_ring = L->d_ring;
   ra.delay = L->delay;

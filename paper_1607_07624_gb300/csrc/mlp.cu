@@ -68,6 +68,20 @@ bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool make_tmap_rows_f32(CUtensorMap* map, const float* base, uint64_t S, uint64_t L, uint32_t box) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || !base || S < 2 || L == 0 || (S * 4) % 16 != 0 || box > S || (box * 4) % 16 != 0 ||
+      (reinterpret_cast<uintptr_t>(base) & 15) != 0)
+    return false;
+  cuuint64_t dims[3] = {S, S, L};
+  cuuint64_t strides[2] = {S * 4, S * S * 4};
+  cuuint32_t boxd[3] = {box, 2, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, boxd, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int gemm_pick_bn(int M, int N, int sms) {
   const int tm = (M + 127) / 128;
   int best = 128;

@@ -24,6 +24,7 @@ PAS_OK, PAS_EINVAL, PAS_ENOMEM, PAS_ECUDA, PAS_ETIMEOUT, PAS_ESTATE = range(6)
 PAS_FP32, PAS_BF16 = 0, 1
 PAS_LOOP_KERNELS = 5          # kernels of one loop step (the header's define)
 PAS_BATCH_PERSISTENT = 1      # pas_batch_create_ex flag
+PAS_TAPS_AUTO, PAS_TAPS_TMA, PAS_TAPS_COPY = 0, 1, 2   # pas_atmo_set_tap_staging
 STATUS_NAMES = {0: "PAS_OK", 1: "PAS_EINVAL", 2: "PAS_ENOMEM", 3: "PAS_ECUDA", 4: "PAS_ETIMEOUT",
                 5: "PAS_ESTATE"}
 
@@ -147,6 +148,10 @@ _SIGS = {
     "pas_batch_kernels_per_step": (i32, [vp]),
     "pas_batch_check": (C.c_int, [vp, C.POINTER(C.c_uint32)]),
     "pas_batch_create_ex": (C.c_int, [vp, vp, i32, C.c_uint32, P(vp)]),
+    "pas_atmo_tma": (i32, [vp]),
+    "pas_atmo_set_tap_staging": (C.c_int, [vp, i32]),
+    "pas_atmo_set_wait_limit": (C.c_int, [vp, C.c_uint32]),
+    "pas_atmo_check": (C.c_int, [vp, C.POINTER(C.c_uint32)]),
     "pas_batch_n_persistent": (i32, [vp]),
     "pas_batch_n_residual_groups": (i32, [vp]),
     "pas_batch_persistent_geometry": (C.c_int, [vp, i32, P(i32)]),
@@ -773,3 +778,23 @@ def pas_batch_check(batch, ctx):
     f = C.c_uint32()
     _check(_lib.pas_batch_check(batch, C.byref(f)), ctx)
     return f.value
+
+
+def pas_atmo_tma(atmo) -> int:
+    """1 when the residual's tap staging uses TMA boxes for this atmosphere."""
+    return int(_lib.pas_atmo_tma(atmo))
+
+
+def pas_atmo_set_wait_limit(atmo, ctx, tries):
+    _check(_lib.pas_atmo_set_wait_limit(atmo, int(tries)), ctx)
+
+
+def pas_atmo_check(atmo):
+    """(status, fault bits) of the tap staging's waits, without raising."""
+    f = C.c_uint32()
+    st = int(_lib.pas_atmo_check(atmo, C.byref(f)))
+    return st, f.value
+
+
+def pas_atmo_set_tap_staging(atmo, ctx, mode):
+    _check(_lib.pas_atmo_set_tap_staging(atmo, int(mode)), ctx)

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from synth import get_config, tiny_config
+from synth.configs import with_
 from synth.inputs import random_matrix, random_vector
 
 pytestmark = pytest.mark.gpu
@@ -229,3 +230,107 @@ def test_detector_noise_draws_match_the_kernel_model(env):
     torch.cuda.synchronize()
     o = nz.apply_noise(fr.astype(np.float64), photons, npup, 0.0, seed, 3)
     assert np.mean(d_out.cpu().numpy() == o) >= 0.999
+
+
+def _loop_views(loop, ctx, n_modes, hist):
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import DevView
+    bufs = pas.pas_loop_buffers(loop, ctx)
+    return DevView.tensor(bufs["wfe"], (hist,), "<f8"), DevView.tensor(bufs["cmd"], (n_modes,))
+
+
+@pytest.mark.parametrize("source", [None, (3.0, 40.0)])
+def test_tma_tap_staging_equals_the_4byte_copies(source):
+    """The residual's TMA tap staging (a box of the two screen rows per pupil-row segment,
+    taps past the screen's edge from global memory) against the 4-byte copies, on one
+    atmosphere and on screens that start 4 bytes into a buffer (which cannot take TMA
+    boxes): with winds that carry the footprint around the 128-pixel screens in both
+    axes, every step's residual WFE and the command are bit-identical, on axis and off
+    axis."""
+    import torch
+    from paper_1607_07624_gb300 import pas, calib
+    from paper_1607_07624_gb300.system import SCAOSystem
+    from synth.configs import LayerSpec
+    cfg = with_(tiny_config(Np=64, N=128, n_sub=8, K=8, n_modes=30, S=128),
+                layers=(LayerSpec(0.7, 0.0, 530.0, 30.0), LayerSpec(0.3, 4000.0, 410.0, 200.0)))
+    s = SCAOSystem(cfg, autotune=False, wfe_history=64, source=source, build_loop=False)
+    n = s.d_screens.numel()
+    buf = torch.zeros(n + 4, device="cuda", dtype=torch.float32)
+    buf[1:1 + n].copy_(s.d_screens.reshape(-1))
+    vel = calib.wind_shift_px(cfg)
+    atmo_m = pas.pas_atmo_create(s.ctx, len(cfg.layers), cfg.S, cfg.Np, vel[:, 0], vel[:, 1], buf[1:1 + n])
+    view_m = None
+    if source is not None:
+        off = np.array(calib.footprint_offsets_px([ly.height_m for ly in cfg.layers], source[0], source[1], cfg.dx),
+                       dtype=np.float64).reshape(-1, 2)
+        view_m = pas.pas_atmo_create_view(atmo_m, s.ctx, off[:, 0], off[:, 1])
+    pyrs, loops = [], []
+    try:
+        assert pas.pas_atmo_tma(s.atmo) == 1 and pas.pas_atmo_tma(view_m or atmo_m) == 0
+        with pytest.raises(pas.PasError):
+            pas.pas_atmo_set_tap_staging(view_m or atmo_m, s.ctx, pas.PAS_TAPS_TMA)
+        for atmo, mode in ((s.atmo, pas.PAS_TAPS_TMA), (s.atmo, pas.PAS_TAPS_COPY), (view_m or atmo_m, None)):
+            if mode is not None:
+                pas.pas_atmo_set_tap_staging(atmo, s.ctx, mode)
+            # a sensor per loop (its intermediates), all of one geometry and reference
+            pyr = pas.pas_pyr_create(s.ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius, cfg.wavelength_nm,
+                                     cfg.obs, s.valid)
+            pas.pas_pyr_set_reference(pyr, s.ctx, s.d_sn)
+            pyrs.append(pyr)
+            loops.append(pas.pas_loop_create(s.ctx, atmo, pyr, s.rec, s.dm, s.d_gain, s.delay, 64))
+        n_steps = 60   # about 4 px per step: the footprints wrap around the screen twice
+        for loop in loops:
+            pas.pas_loop_step(loop, s.ctx, n_steps)
+        torch.cuda.synchronize()
+        views = [_loop_views(loop, s.ctx, s.n_modes, 64) for loop in loops]
+        w0, c0 = views[0][0].cpu().numpy(), views[0][1].cpu().numpy()
+        assert np.all(np.isfinite(w0)) and w0[:n_steps].min() > 0.0
+        for w, c in views[1:]:
+            assert np.array_equal(w.cpu().numpy(), w0)
+            assert np.array_equal(c.cpu().numpy(), c0)
+        assert pas.pas_atmo_check(s.atmo_base)[0] == pas.PAS_OK
+    finally:
+        for loop in loops:
+            pas.pas_loop_destroy(loop)
+        for pyr in pyrs:
+            pas.pas_pyr_destroy(pyr)
+        if view_m is not None:
+            pas.pas_atmo_destroy(view_m)
+        pas.pas_atmo_destroy(atmo_m)
+        s.close()
+
+
+def test_tma_tap_staging_wait_gives_up_and_is_reported():
+    """A staging wait limit of 0 gives up at once: the residual kernel flags the
+    atmosphere, waits for its copies with the long bound and computes the same values;
+    pas_atmo_check reports PAS_ETIMEOUT once, and the context stays usable."""
+    import torch
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    cfg = tiny_config(Np=64, N=128, n_sub=8, K=8, n_modes=30, S=128)
+    ref = SCAOSystem(cfg, autotune=False, wfe_history=64, build_loop=False)
+    s = SCAOSystem(cfg, autotune=False, wfe_history=64, build_loop=False, R=ref.R, basis=ref.basis)
+    loop = None
+    try:
+        pas.pas_atmo_set_tap_staging(ref.atmo, ref.ctx, pas.PAS_TAPS_TMA)
+        ref_loop = pas.pas_loop_create(ref.ctx, ref.atmo, ref.pyr, ref.rec, ref.dm, ref.d_gain, ref.delay, 64)
+        ref.loop = ref_loop
+        ref.loop_cmd = _loop_views(ref_loop, ref.ctx, ref.n_modes, 64)[1]
+        pas.pas_atmo_set_tap_staging(s.atmo, s.ctx, pas.PAS_TAPS_TMA)
+        pas.pas_atmo_set_wait_limit(s.atmo, s.ctx, 0)
+        loop = pas.pas_loop_create(s.ctx, s.atmo, s.pyr, s.rec, s.dm, s.d_gain, ref.delay, 64)
+        pas.pas_loop_step(ref_loop, ref.ctx, 10)
+        pas.pas_loop_step(loop, s.ctx, 10)
+        torch.cuda.synchronize()
+        st, fault = pas.pas_atmo_check(s.atmo)
+        assert st == pas.PAS_ETIMEOUT and fault == 1
+        assert pas.pas_atmo_check(s.atmo) == (pas.PAS_OK, 0)
+        from paper_1607_07624_gb300.system import DevView
+        cmd = DevView.tensor(pas.pas_loop_buffers(loop, s.ctx)["cmd"], (ref.n_modes,)).cpu().numpy()
+        assert np.array_equal(ref.loop_cmd.cpu().numpy(), cmd)
+        assert pas.pas_atmo_check(ref.atmo)[0] == pas.PAS_OK
+    finally:
+        if loop is not None:
+            pas.pas_loop_destroy(loop)
+        s.close()
+        ref.close()
