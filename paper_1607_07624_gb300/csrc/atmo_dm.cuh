@@ -148,12 +148,14 @@ inline ResArgs make_res_args(pas_dm_t d) {
 
 // The atmosphere of a residual: its layers, and the TMA staging of their taps when
 // the screens allow it and the source is at infinity.
-inline void res_args_set_atmo(ResArgs& a, pas_atmo_t at) {
+// taps, wait_limit: the staging mode and wait bound the caller took from the
+// atmosphere when it was set up (a loop keeps those of its creation).
+inline void res_args_set_atmo(ResArgs& a, pas_atmo_t at, int taps, uint32_t wait_limit) {
   a.atmo = at->args;
-  const bool want = at->taps == PAS_TAPS_TMA || (at->taps == PAS_TAPS_AUTO && a.n_m >= RES_TMA_MIN_MODES);
+  const bool want = taps == PAS_TAPS_TMA || (taps == PAS_TAPS_AUTO && a.n_m >= RES_TMA_MIN_MODES);
   a.tma = want && at->tma && !at->args.cone && a.seg != nullptr ? 1 : 0;
   if (a.tma) a.tmap = at->tmap;
   a.err = at->d_err;
-  a.wait_limit = at->wait_limit;
+  a.wait_limit = wait_limit;
 }
 }  // namespace pas

@@ -25,6 +25,8 @@ struct pas_loop_s {
   pas_mlp_t mlp = nullptr;  // learned reconstructor in place of rec (optional)
   int delay = 1, hist = 1, n_m = 0, n_slopes = 0, nd = 0, Np = 0, n_tiles = 0;
   int n_int = 1;            // detector steps per frame (pas_loop_set_integration)
+  int taps = PAS_TAPS_AUTO;         // the atmosphere's tap staging and wait bound at creation
+  uint32_t tap_wait_limit = 0;
   float* d_acc = nullptr;   // [nd*nd] the integrating detector's accumulator
   float* d_opd = nullptr;
   float* d_frame = nullptr;
@@ -48,7 +50,7 @@ struct pas_loop_s {
 // the wind-shifted layers at its pupil pixels while its other warps stream the basis).
 static pas_status enqueue_residual(pas_loop_t L, cudaStream_t st) {
   pas::ResArgs ra = pas::make_res_args(L->dm);
-  pas::res_args_set_atmo(ra, L->atmo);
+  pas::res_args_set_atmo(ra, L->atmo, L->taps, L->tap_wait_limit);
   ra.opd_atm = nullptr;
   ra.cmd_ring = L->d_ring;
   ra.delay = L->delay;
@@ -160,6 +162,8 @@ static pas_status loop_create(pas_ctx_t ctx, pas_atmo_t atmo, pas_pyr_t pyr, pas
   pas_loop_t L = new pas_loop_s();
   L->ctx = ctx;
   L->atmo = atmo;
+  L->taps = atmo->taps;
+  L->tap_wait_limit = atmo->wait_limit;
   L->pyr = pyr;
   L->sh = sh;
   L->rec = rec;
