@@ -151,9 +151,10 @@ pas_status pas_atmo_create_cone_view(pas_atmo_t base, const double* h_ox, const 
  * for NULL. The values are the same either way, bit for bit. Host only. */
 int32_t pas_atmo_tma(pas_atmo_t atmo);
 /* Which staging loops created afterwards on this object use: PAS_TAPS_AUTO (default:
- * TMA where pas_atmo_tma is 1 and the DM has at least 1000 modes, the 4-byte copies
- * otherwise), PAS_TAPS_TMA (PAS_EINVAL where pas_atmo_tma is 0), PAS_TAPS_COPY. Views
- * created afterwards inherit it. Host only. */
+ * TMA where pas_atmo_tma is 1 and the DM has a float32 basis of at least 1000 modes,
+ * whose stream hides the boxes' latency; the 4-byte copies otherwise), PAS_TAPS_TMA
+ * (PAS_EINVAL where pas_atmo_tma is 0), PAS_TAPS_COPY. Views created afterwards
+ * inherit it. Host only. */
 #define PAS_TAPS_AUTO 0
 #define PAS_TAPS_TMA 1
 #define PAS_TAPS_COPY 2

@@ -55,10 +55,11 @@ constexpr int RES_BOX = RES_TILE + 4;
 constexpr int RES_BOX_PITCH = 160;
 // Most pupil-row segments of a tile with TMA staging (more: 4-byte copies).
 constexpr int RES_SEG_MAX = 8;
-// PAS_TAPS_AUTO stages by TMA from this many modes up, where a tile's basis stream
-// hides the boxes' latency (measured on GB300: equal times at 4000 modes, 216 and 408
-// us for bf16 and float32 bases; at 400 modes, one wave of short CTAs, the 4-byte
-// copies 0.2-0.3 us ahead of 14.6 and 19.2 us).
+// PAS_TAPS_AUTO stages by TMA for a float32 basis from this many modes up, where a
+// tile's basis stream hides the boxes' latency. Measured on GB300 (TMA against the
+// 4-byte copies): 408.9 against 409.0 us at 4000 modes with a float32 basis; 220.4
+// against 216.2 us with a bf16 one (half the stream); 19.6 against 19.0 and 15.1
+// against 14.9 us at 400 modes (one wave of short CTAs).
 constexpr int RES_TMA_MIN_MODES = 1000;
 
 // One loop of a batched residual (loops sharing one DM object).
@@ -152,7 +153,8 @@ inline ResArgs make_res_args(pas_dm_t d) {
 // atmosphere when it was set up (a loop keeps those of its creation).
 inline void res_args_set_atmo(ResArgs& a, pas_atmo_t at, int taps, uint32_t wait_limit) {
   a.atmo = at->args;
-  const bool want = taps == PAS_TAPS_TMA || (taps == PAS_TAPS_AUTO && a.n_m >= RES_TMA_MIN_MODES);
+  const bool want =
+      taps == PAS_TAPS_TMA || (taps == PAS_TAPS_AUTO && a.MT != nullptr && a.n_m >= RES_TMA_MIN_MODES);
   a.tma = want && at->tma && !at->args.cone && a.seg != nullptr ? 1 : 0;
   if (a.tma) a.tmap = at->tmap;
   a.err = at->d_err;
