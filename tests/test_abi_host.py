@@ -207,3 +207,11 @@ def test_static_measure_binding_rejects_wrong_tensors_before_the_call():
     with pytest.raises(pas.PasError) as e:
         pas.pas_pyr_measure_static(Np, N, K, n_sub, 2.0, 750.0, 0.1, opd, fr)
     assert e.value.status == pas.PAS_EINVAL and "d_opd" in str(e.value)
+
+
+def test_profile_cases_command_line():
+    """The profiling driver's command line parses on a host without a GPU."""
+    from paper_1607_07624_gb300 import profile_cases
+    with pytest.raises(SystemExit) as e:
+        profile_cases.main(["--help"])
+    assert e.value.code == 0
