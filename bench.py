@@ -537,8 +537,10 @@ def bench_extended(timed, n_frames=100):
 
 def bench_batch(timed, n_loops=64, n_steps=100):
     """Monte-Carlo batch: n_loops realisations of the 64 px workload (own screens
-    each; basis, reconstructor and launch geometry shared) stepped by one graph
-    launch per step. Returns the whole batch's loop-steps/s next to one loop's."""
+    each; DM object, reconstructor matrix and launch geometry shared, so the batch
+    computes their residuals in one basis pass) stepped by one graph launch per step,
+    as graph branches and with the persistent pyramid launch. Returns the whole batch's
+    loop-steps/s for the faster, both modes beside it."""
     import numpy as np
     from paper_1607_07624_gb300 import pas
     from paper_1607_07624_gb300.system import SCAOSystem
@@ -550,21 +552,31 @@ def bench_batch(timed, n_loops=64, n_steps=100):
     try:
         for i in range(1, n_loops):
             systems.append(SCAOSystem(with_(cfg, seed=cfg.seed + 7919 * i), basis=systems[0].basis, R=systems[0].R,
-                                      autotune=tuple(systems[0].tuning), wfe_history=max(256, n_steps + 64)))
-        batch = pas.pas_batch_create(systems[0].ctx, [s.loop for s in systems])
-        pas.pas_batch_step(batch, systems[0].ctx, 5)
-        for s in systems:
-            s.set_state(0, np.zeros((s.delay, s.n_modes), np.float32))
-        ms = timed(lambda: pas.pas_batch_step(batch, systems[0].ctx, 1), n_steps)
-        wfe = np.array([s.wfe_nm(n_steps) for s in systems])
-        return {"workload": f"{n_loops} realisations of {cfg.name} (own screens each)",
-                "loop_steps_per_s": n_loops * n_steps / (ms * 1e-3), "batch_steps_per_s": n_steps / (ms * 1e-3),
-                "graph_launches_per_step": 1, "kernels_per_step": pas.PAS_LOOP_KERNELS * n_loops,
+                                      dm=systems[0].dm, autotune=tuple(systems[0].tuning),
+                                      wfe_history=max(256, n_steps + 64)))
+        modes, wfe = {}, None
+        for name, flags in (("graph_branches", 0), ("persistent", pas.PAS_BATCH_PERSISTENT)):
+            batch = pas.pas_batch_create_ex(systems[0].ctx, [s.loop for s in systems], flags)
+            pas.pas_batch_step(batch, systems[0].ctx, 5)
+            for s in systems:
+                s.set_state(0, np.zeros((s.delay, s.n_modes), np.float32))
+            ms = timed(lambda: pas.pas_batch_step(batch, systems[0].ctx, 1), n_steps)
+            pas.pas_batch_check(batch, systems[0].ctx)
+            modes[name] = {"loop_steps_per_s": n_loops * n_steps / (ms * 1e-3),
+                           "batch_steps_per_s": n_steps / (ms * 1e-3),
+                           "kernels_per_step": pas.pas_batch_kernels_per_step(batch)}
+            if wfe is None:
+                wfe = np.array([s.wfe_nm(n_steps) for s in systems])
+            pas.pas_batch_destroy(batch)
+            batch = None
+        best = max(modes, key=lambda k: modes[k]["loop_steps_per_s"])
+        return {"workload": f"{n_loops} realisations of {cfg.name} (own screens each)", "mode": best, **modes[best],
+                "graph_launches_per_step": 1, "modes": modes,
                 "wfe_nm_mean_over_realisations": float(wfe[:, n_steps // 5:].mean())}
     finally:
         if batch is not None:
             pas.pas_batch_destroy(batch)
-        for s in systems:
+        for s in systems[1:] + systems[:1]:
             s.close()
 
 

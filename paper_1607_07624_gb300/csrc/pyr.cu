@@ -583,13 +583,18 @@ pyr_batch_kernel(BatchPyrArgs a) {
       const int r = t - g.row_base;
       const int by = r / g.nbx;
       rows_task<N>(a.ra[l], r - by * g.nbx, by, g.n_row / g.nbx, g.rows);
-      __threadfence();  // this task's part of H, before the count that publishes it
+      // this task's part of H, written by all threads, published by one release: the
+      // barrier orders the writes before thread 0's fence (cumulative) and count
       __syncthreads();
-      if (threadIdx.x == 0) atomicAdd(a.rows_done + l, 1u);
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(a.rows_done + l, 1u);
+      }
     } else {
+      // thread 0's acquire load of the count, then the barrier after the claim, order
+      // this task's reads of H after the rows tasks' writes
       const int c = t - g.col_base;
       const int gh = c / g.nd;
-      __threadfence();
       cols_task<N, true>(a.ca[l], c - gh * g.nd, gh, g.bw, s_skip != 0);
     }
   }
