@@ -278,7 +278,7 @@ void pas_pyr_destroy(pas_pyr_t pyr);
  * number of CTAs sharing one detector column's b = N / (2 n_sub) fine columns
  * (smaller CTAs, more of them resident per SM). */
 typedef struct {
-    int32_t rows_per_cta;   /* 1, 2, 4 or 8 */
+    int32_t rows_per_cta;   /* 1, 2, 4, 8, or 16 where that CTA's shared memory fits */
     int32_t row_chunks;     /* 1 .. number of distinct sin(theta_k) */
     int32_t col_groups;     /* 1 .. K */
     int32_t col_split;      /* 1, or a divisor <= 8 of b when b is an integer */
@@ -287,7 +287,7 @@ pas_status pas_pyr_get_tuning(pas_pyr_t pyr, pas_pyr_tuning* h_out);
 /* Values are rounded to the nearest realisable split; results do not depend on
  * the geometry beyond float32 summation order of the modulation groups. */
 pas_status pas_pyr_set_tuning(pas_pyr_t pyr, const pas_pyr_tuning* h_t);
-/* Autotuner: times each candidate geometry (rows_per_cta 2/4/8 x every chunk
+/* Autotuner: times each candidate geometry (rows_per_cta 2/4/8/16 x every chunk
  * count; every column group count x every column split) with CUDA events over
  * `iters` launches on d_opd (device [Np][Np]), keeps the fastest and writes it
  * to h_out (may be NULL). Synchronous; overwrites the object's internal frame; do not call while

@@ -35,6 +35,10 @@
 namespace pas {
 
 constexpr int MAX_ROWS_PER_CTA = 8;  // rows pass: one warp per pupil row
+// A rows-pass CTA of 16 rows (512 threads at the 128-register cap: the whole register
+// file of an SM), where its shared memory fits: the per-warp phasor row and transpose
+// buffer, not the registers, then bound the warps per SM.
+constexpr int ROWS_WIDE = 16;
 constexpr size_t SMEM_MAX = 227 * 1024;  // opt-in dynamic shared memory of one CTA
 
 struct RowArgs {
@@ -649,6 +653,7 @@ struct pas_pyr_s {
   int frac = 0;  // non-integer fine pixels per detector pixel
   int rows = 4, s_chunk = 1, n_schunks = 1;
   int s_chunk_max = 1;   // largest rows-pass chunk whose shared memory fits a CTA
+  int s_chunk_wide = 0;  // the same for a CTA of ROWS_WIDE rows (0: it does not fit)
   int K_mod = 0, n_src = 1;  // modulation points and source points (p.K = K_mod n_src)
   int64_t T_obs = 0;
   float inv_hi = 0.f, inv_lo = 0.f;
@@ -1242,6 +1247,10 @@ static pas_status pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int3
   while (y->s_chunk_max > 1 && pas::rows_smem(y, pas::MAX_ROWS_PER_CTA, y->s_chunk_max) > pas::SMEM_MAX)
     --y->s_chunk_max;
   y->smem_rows = pas::rows_smem(y, pas::MAX_ROWS_PER_CTA, y->s_chunk_max);  // largest candidate
+  y->s_chunk_wide = std::min(y->n_s, y->s_chunk_max);
+  while (y->s_chunk_wide > 0 && pas::rows_smem(y, pas::ROWS_WIDE, y->s_chunk_wide) > pas::SMEM_MAX) --y->s_chunk_wide;
+  if (y->s_chunk_wide > 0)
+    y->smem_rows = std::max(y->smem_rows, pas::rows_smem(y, pas::ROWS_WIDE, y->s_chunk_wide));
   y->smem_cols = pas::cols_smem(y, b);  // largest: one CTA per detector column and group
   for (int H = 2; H <= 8; ++H)
     if (pas::split_ok(y, H)) y->h_max = H;
@@ -1385,12 +1394,14 @@ pas_status pas_pyr_get_tuning(pas_pyr_t y, pas_pyr_tuning* out) {
 pas_status pas_pyr_set_tuning(pas_pyr_t y, const pas_pyr_tuning* t) {
   if (!y || !t) return pas::set_global_error(PAS_EINVAL, "pas_pyr_set_tuning: NULL argument");
   const int r = t->rows_per_cta;
-  PAS_CHECK_ARG(y->ctx, (r == 1 || r == 2 || r == 4 || r == 8) && t->row_chunks >= 1 &&
-                t->row_chunks <= y->n_s && (y->n_s + t->row_chunks - 1) / t->row_chunks <= y->s_chunk_max &&
+  const int chunk = t->row_chunks >= 1 ? (y->n_s + t->row_chunks - 1) / t->row_chunks : 0;
+  const bool rows_ok = r == 1 || r == 2 || r == 4 || r == 8 || (r == pas::ROWS_WIDE && chunk <= y->s_chunk_wide);
+  PAS_CHECK_ARG(y->ctx, rows_ok && t->row_chunks >= 1 &&
+                t->row_chunks <= y->n_s && chunk <= y->s_chunk_max &&
                 t->col_groups >= 1 && t->col_groups <= y->p.K && pas::split_ok(y, t->col_split),
-                "pas_pyr_set_tuning: rows_per_cta in {1,2,4,8}, 1 <= row_chunks <= distinct sin values (chunks "
-                "within shared memory), 1 <= col_groups <= K, col_split 1 or a divisor <= 8 of the fine pixels "
-                "per detector pixel");
+                "pas_pyr_set_tuning: rows_per_cta in {1,2,4,8} (16 where its chunk's shared memory fits), 1 <= "
+                "row_chunks <= distinct sin values (chunks within shared memory), 1 <= col_groups <= K, col_split "
+                "1 or a divisor <= 8 of the fine pixels per detector pixel");
   y->rows = r;
   y->s_chunk = (y->n_s + t->row_chunks - 1) / t->row_chunks;
   y->n_schunks = (y->n_s + y->s_chunk - 1) / y->s_chunk;
@@ -1433,12 +1444,13 @@ pas_status pas_pyr_autotune(pas_pyr_t y, const float* d_opd, int32_t iters, pas_
   // rows pass
   float best = 1e30f;
   pas_pyr_tuning bt{y->rows, y->n_schunks, y->G, y->H};
-  const int rows_c[3] = {2, 4, 8};
+  const int rows_c[4] = {2, 4, 8, pas::ROWS_WIDE};
   for (int r : rows_c) {
     int last_chunk = -1;
+    const int cmax = r == pas::ROWS_WIDE ? y->s_chunk_wide : y->s_chunk_max;
     for (int nc = 1; nc <= y->n_s; ++nc) {
       const int chunk = (y->n_s + nc - 1) / nc;
-      if (chunk == last_chunk || chunk > y->s_chunk_max) continue;
+      if (chunk == last_chunk || chunk > cmax) continue;
       last_chunk = chunk;
       y->rows = r;
       y->s_chunk = chunk;

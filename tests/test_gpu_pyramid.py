@@ -215,7 +215,8 @@ def test_autotune_and_tunings_give_the_same_frame(env):
     try:
         nv = pas.pas_pyr_n_valid(pyr)
         frames = []
-        for t in [(1, 1, 1), (2, 3, 4), (8, 7, 12), (4, 2, 5), (2, 3, 4, 2), (4, 2, 6, 4), (8, 1, 12, 4)]:
+        for t in [(1, 1, 1), (2, 3, 4), (8, 7, 12), (4, 2, 5), (2, 3, 4, 2), (4, 2, 6, 4), (8, 1, 12, 4),
+                  (16, 1, 12), (16, 7, 5, 2)]:
             pas.pas_pyr_set_tuning(pyr, ctx, *t)
             fr = torch.zeros(cfg.n_det, cfg.n_det, device="cuda")
             sl = torch.zeros(2 * nv, device="cuda")
@@ -225,7 +226,7 @@ def test_autotune_and_tunings_give_the_same_frame(env):
         for f in frames[1:]:
             assert np.max(np.abs(f - frames[0])) <= 1e-6 * np.max(frames[0])
         best = pas.pas_pyr_autotune(pyr, ctx, opd, 2)
-        assert best[0] in (2, 4, 8) and 1 <= best[1] and 1 <= best[2] <= cfg.K
+        assert best[0] in (2, 4, 8, 16) and 1 <= best[1] and 1 <= best[2] <= cfg.K
         b = cfg.N // cfg.n_det
         assert best[3] >= 1 and b % best[3] == 0
         assert pas.pas_pyr_get_tuning(pyr, ctx) == best
@@ -233,6 +234,33 @@ def test_autotune_and_tunings_give_the_same_frame(env):
             pas.pas_pyr_set_tuning(pyr, ctx, 3, 1, 1)
         with pytest.raises(pas.PasError):
             pas.pas_pyr_set_tuning(pyr, ctx, 4, 1, 1, 3)    # 3 does not divide b = 4
+    finally:
+        pas.pas_pyr_destroy(pyr)
+
+
+@pytest.mark.parametrize("name,rows", [("scao_lbt_240px", [(2, 1), (4, 7), (8, 13), (16, 3), (16, 13)]),
+                                       ("scao_elt_480px", [(2, 17), (4, 5), (8, 5), (16, 3), (16, 6)])])
+def test_rows_pass_geometry_leaves_the_frame_bit_identical(env, name, rows):
+    """The rows pass's geometry (pupil rows per CTA, 16 included, and sin values per
+    CTA) changes which warp transforms which row, not the arithmetic: with the columns
+    geometry fixed, frame and slopes are bit-identical (the persistent batched launch
+    relies on it)."""
+    torch, pas, ctx = env
+    cfg = get_config(name)
+    opd = torch.as_tensor(random_opd_nm(cfg.Np, 200.0, seed=23).astype(np.float32)).cuda()
+    pyr = pas.pas_pyr_create(ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius, cfg.wavelength_nm, cfg.obs)
+    try:
+        nv = pas.pas_pyr_n_valid(pyr)
+        out = []
+        for r, chunks in rows:
+            pas.pas_pyr_set_tuning(pyr, ctx, r, chunks, 5, 1)
+            fr = torch.zeros(cfg.n_det, cfg.n_det, device="cuda")
+            sl = torch.zeros(2 * nv, device="cuda")
+            pas.pas_pyr_measure(pyr, ctx, opd, fr, sl)
+            torch.cuda.synchronize()
+            out.append((fr.cpu().numpy(), sl.cpu().numpy()))
+        for fr, sl in out[1:]:
+            assert np.array_equal(fr, out[0][0]) and np.array_equal(sl, out[0][1])
     finally:
         pas.pas_pyr_destroy(pyr)
 
