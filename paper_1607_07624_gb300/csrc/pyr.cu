@@ -360,12 +360,14 @@ __global__ void tilt_table_kernel(const float* alpha, const float* amp, int K, i
 // warps 0 .. bw-1 (the fine columns it transforms; further warps take part in the
 // barriers only). skip: transform nothing (a persistent launch whose wait for the
 // rows pass gave up still keeps the column handshake in step).
-// H through the read-only cache (written by an earlier kernel), or through L2 alone
-// (COH: written by other CTAs of the same persistent launch)
+// H through the read-only cache (written by an earlier kernel), or (COH: written by
+// other CTAs of the same persistent launch) by plain cached loads, which the task's
+// acquire of its loop's rows-pass count (thread 0) and the barrier after it order after
+// those writes
 template <bool COH>
 __device__ __forceinline__ float2 ld_h(const float2* p) {
   if constexpr (COH)
-    return __ldcg(p);
+    return __ldca(p);
   else
     return __ldg(p);
 }
@@ -935,6 +937,7 @@ pas_status pyr_batch_create(pas_ctx_t ctx, int n, const pas_pyr_t* y, const floa
     size_t smem_c = 0;
     double w_rows = 0.0, w_cols = 0.0, bw_sum = 0.0;
     int n_s_max = 1;
+    double n_col_tasks = 0.0;
     for (size_t k = 0; k < L; ++k) {
       pas_pyr_t p = y[members[g][k]];
       const int bw = p->b / p->H;
@@ -944,6 +947,7 @@ pas_status pyr_batch_create(pas_ctx_t ctx, int n, const pas_pyr_t* y, const floa
       w_cols += (double)p->p.K * p->nd * p->b;
       bw_sum += bw;
       n_s_max = std::max(n_s_max, p->n_s);
+      n_col_tasks += (double)p->nd * p->G * p->H;
     }
     int best_rows = 1, best_chunk = 1;
     size_t best_smem = 0;
@@ -970,10 +974,19 @@ pas_status pyr_batch_create(pas_ctx_t ctx, int n, const pas_pyr_t* y, const floa
         int occ = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, grp.kern, 32 * warps, sm);
         if (e != cudaSuccess || occ < 1) continue;
-        // the OPD phasor is formed once per chunk: n_s / c of them per row
+        // the OPD phasor is formed once per chunk: n_s / c of them per row; a phase
+        // keeps at most as many CTAs busy per SM as it has tasks per SM
         const double rows_work = w_rows * (1.0 + 0.25 / c);
-        const double t = rows_work / std::min(16.0, (double)occ * rows) +
-                         w_cols / std::min(16.0, occ * bw_sum / (double)L);
+        double n_row_tasks = 0.0;
+        for (size_t k = 0; k < L; ++k) {
+          pas_pyr_t p = y[members[g][k]];
+          n_row_tasks += (double)((p->p.Np + rows - 1) / rows) * ((p->n_s + c - 1) / c);
+        }
+        const double sms = std::max(1, ctx->sm_count);
+        const double ctas_r = std::min((double)occ, n_row_tasks / sms);
+        const double ctas_c = std::min((double)occ, n_col_tasks / sms);
+        const double t = rows_work / std::min(16.0, ctas_r * rows) +
+                         w_cols / std::min(16.0, ctas_c * bw_sum / (double)L);
         if (best_t < 0.0 || t < best_t) {
           best_t = t;
           best_rows = rows;
