@@ -239,8 +239,8 @@ def _loop_views(loop, ctx, n_modes, hist):
     return DevView.tensor(bufs["wfe"], (hist,), "<f8"), DevView.tensor(bufs["cmd"], (n_modes,))
 
 
-@pytest.mark.parametrize("source", [None, (3.0, 40.0)])
-def test_tma_tap_staging_equals_the_4byte_copies(source):
+@pytest.mark.parametrize("source,n_layers", [(None, 2), ((3.0, 40.0), 2), (None, 16)])
+def test_tma_tap_staging_equals_the_4byte_copies(source, n_layers):
     """The residual's TMA tap staging (a box of the two screen rows per pupil-row segment,
     taps past the screen's edge from global memory) against the 4-byte copies, on one
     atmosphere and on screens that start 4 bytes into a buffer (which cannot take TMA
@@ -251,8 +251,11 @@ def test_tma_tap_staging_equals_the_4byte_copies(source):
     from paper_1607_07624_gb300 import pas, calib
     from paper_1607_07624_gb300.system import SCAOSystem
     from synth.configs import LayerSpec
-    cfg = with_(tiny_config(Np=64, N=128, n_sub=8, K=8, n_modes=30, S=128),
-                layers=(LayerSpec(0.7, 0.0, 530.0, 30.0), LayerSpec(0.3, 4000.0, 410.0, 200.0)))
+    if n_layers == 2:
+        layers = (LayerSpec(0.7, 0.0, 530.0, 30.0), LayerSpec(0.3, 4000.0, 410.0, 200.0))
+    else:   # the most layers an atmosphere takes: 16 x 4 segments of boxes per tile
+        layers = tuple(LayerSpec(1.0 / n_layers, 500.0 * l, 150.0 + 27.0 * l, 23.0 * l) for l in range(n_layers))
+    cfg = with_(tiny_config(Np=64, N=128, n_sub=8, K=8, n_modes=30, S=128), layers=layers)
     s = SCAOSystem(cfg, autotune=False, wfe_history=64, source=source, build_loop=False)
     n = s.d_screens.numel()
     buf = torch.zeros(n + 4, device="cuda", dtype=torch.float32)
