@@ -104,6 +104,9 @@ bool gemm_prepare(GemmOp* op, const __nv_bfloat16* A, int lda, const __nv_bfloat
   op->N = N;
   op->K = K;
   op->bn = gemm_pick_bn(M, N, sms);
+  // at least two tiles per SM: persistent CTAs, the epilogue of one tile under the
+  // products of the next
+  gemm_set_persist(op, sms);
   return make_tmap_bf16(&op->a, A, (uint64_t)M, (uint64_t)K, (uint64_t)lda, 128) &&
          make_tmap_bf16(&op->b, B, (uint64_t)N, (uint64_t)K, (uint64_t)ldb, (uint32_t)op->bn);
 }
@@ -1011,6 +1014,7 @@ pas_status pas_gemm_bf16_waits(pas_ctx_t ctx, int32_t M, int32_t N, int32_t K, c
     return pas::set_error(ctx, PAS_EINVAL, "pas_gemm_bf16: tensor map rejected (16-byte alignment)");
   if (tile_n) {  // a fixed tile width
     op.bn = tile_n;
+    pas::gemm_set_persist(&op, ctx->sm_count);
     if (!pas::make_tmap_bf16(&op.b, d_B, (uint64_t)N, (uint64_t)K, (uint64_t)ldb, (uint32_t)tile_n))
       return pas::set_error(ctx, PAS_EINVAL, "pas_gemm_bf16: tensor map rejected");
   }

@@ -5,6 +5,7 @@ wavefront error of a random system means nothing.
 
     python -m paper_1607_07624_gb300.profile_cases scao_elt_480px --basis fp32 --steps 4
     python -m paper_1607_07624_gb300.profile_cases scao_8m_64px --batch 16 --persistent
+    python -m paper_1607_07624_gb300.profile_cases gemm --gemm 8192 --steps 3
 
 Kernel launches: with --batch 0 every step launches the loop's kernels once, in step order
 (residual, rows pass, columns pass, slopes, reconstructor), so ``ncu -k regex:<kernel> -s
@@ -33,11 +34,30 @@ def _random_system(cfg, basis_prec, recon_prec, tuning, seed, dm=None, rec=None,
                       autotune=tuning, build_loop=False, wfe_history=64)
 
 
+def _gemm(n, steps, seed):
+    ctx = pas.pas_ctx_create(torch.cuda.current_stream())
+    try:
+        gen = torch.Generator(device="cuda").manual_seed(seed)
+        A = torch.randn(n, n, device="cuda", generator=gen).to(torch.bfloat16)
+        B = torch.randn(n, n, device="cuda", generator=gen).to(torch.bfloat16)
+        C = torch.empty(n, n, device="cuda")
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for _ in range(steps):
+            pas.pas_gemm_bf16(ctx, n, n, n, A, n, B, n, C, n, err)
+        torch.cuda.synchronize()
+        print(f"gemm {n}^3 x {steps}: error word {int(err.item())}")
+        return 0 if int(err.item()) == 0 else 1
+    finally:
+        pas.pas_ctx_destroy(ctx)
+
+
 def main(argv=None):
     from synth import get_config
     from synth.configs import with_
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("workload", help="scao_8m_64px, scao_lbt_240px or scao_elt_480px")
+    ap.add_argument("workload", help="scao_8m_64px, scao_lbt_240px or scao_elt_480px (or gemm with --gemm)")
+    ap.add_argument("--gemm", type=int, default=0, help="instead of a loop: --steps tensor-core products "
+                    "C = A B^T of n x n bf16 matrices (seeded normal entries), float32 C")
     ap.add_argument("--basis", default="fp32", choices=sorted(_PREC))
     ap.add_argument("--recon", default="fp32", choices=sorted(_PREC))
     ap.add_argument("--taps", default="auto", choices=sorted(_TAPS), help="the residual's tap staging")
@@ -50,6 +70,8 @@ def main(argv=None):
     ap.add_argument("--persistent", action="store_true", help="the batch with PAS_BATCH_PERSISTENT")
     ap.add_argument("--seed", type=int, default=1)
     a = ap.parse_args(argv)
+    if a.gemm > 0:
+        return _gemm(a.gemm, a.steps, a.seed)
     cfg = get_config(a.workload)
     tuning = tuple(int(x) for x in a.tuning.split(",")) if a.tuning else False
     systems, loops, batch = [], [], None

@@ -69,7 +69,10 @@ def slopes_like(n, B, seed):
                                         (400, 8, 1424, 16), (3578, 24, 14312, 32), (300, 5, 72, 16),
                                         # many waves of 128 x 256 tiles in the grouped order (odd row-tile
                                         # count, ragged N)
-                                        (4096, 4096, 512, 0), (4224, 4000, 520, 0)])
+                                        (4096, 4096, 512, 0), (4224, 4000, 520, 0),
+                                        # persistent CTAs (two or more tiles per SM): 128- and
+                                        # 256-wide tiles, ragged edges
+                                        (4096, 4096, 512, 128), (4000, 4200, 1000, 0)])
 def test_gemm_bf16_matches_fp64(env, M, N, K, tile):
     torch, pas, ctx = env
     g = rng(1000 + M + N + K)
@@ -92,7 +95,30 @@ def test_gemm_bf16_matches_fp64(env, M, N, K, tile):
     assert np.all(np.abs(got - ref) <= 1e-5 * (np.abs(a) @ np.abs(b).T) + 1e-30)
 
 
-def test_gemm_wait_that_gives_up_unwinds_and_reports(env):
+def test_gemm_persistent_256_by_256_tiles_match_fp64_on_sampled_rows(env):
+    """A product large enough for persistent CTAs with 256 x 256 tiles (ragged in M and
+    N: a second 128-row half past the matrix reads zeros): 600 sampled rows against FP64
+    with float32 accumulation of exact bf16 products."""
+    torch, pas, ctx = env
+    g = rng(91)
+    M, N, K = 6000, 7000, 320
+    A = torch.as_tensor(g.standard_normal((M, K)).astype(np.float32)).to(torch.bfloat16).cuda()
+    B = torch.as_tensor(g.standard_normal((N, K)).astype(np.float32)).to(torch.bfloat16).cuda()
+    C = torch.full((M, N), float("nan"), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    pas.pas_gemm_bf16(ctx, M, N, K, A, K, B, K, C, N, err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    rows = np.unique(np.concatenate([g.integers(0, M, 560), np.arange(M - 40, M)]))
+    a = A[torch.as_tensor(rows).cuda()].float().cpu().numpy().astype(np.float64)
+    b = B.float().cpu().numpy().astype(np.float64)
+    got = C[torch.as_tensor(rows).cuda()].cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - a @ b.T) <= 1e-5 * (np.abs(a) @ np.abs(b).T) + 1e-30)
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 384, 1024), (4096, 4096, 512), (6000, 7000, 320)])
+def test_gemm_wait_that_gives_up_unwinds_and_reports(env, M, N, K):
     """Every pipeline wait of the tensor-core GEMM made to give up at once (wait
     limit 0, a barrier no copy has reached yet): the product-issue and epilogue bits
     are set, the unwinding (copies in flight drained, products completed, tensor
@@ -100,7 +126,6 @@ def test_gemm_wait_that_gives_up_unwinds_and_reports(env):
     same GEMM with the default bound is then exact."""
     torch, pas, ctx = env
     g = rng(77)
-    M, N, K = 256, 384, 1024
     A = torch.as_tensor(g.standard_normal((M, K)).astype(np.float32)).to(torch.bfloat16).cuda()
     B = torch.as_tensor(g.standard_normal((N, K)).astype(np.float32)).to(torch.bfloat16).cuda()
     C = torch.zeros(M, N, device="cuda")
