@@ -406,6 +406,17 @@ void pas_loop_destroy(pas_loop_t loop);
 #define PAS_LOOP_KERNELS 5
 pas_status pas_loop_profile(pas_loop_t loop, int32_t n_steps, float* h_ms, int32_t cap,
                             int32_t* n_kernels);
+/* A PSF camera inside the loop's step graph (Table 2: loop.add(psf); Table 1 camera): from
+ * step start_step on, every step's PSF of the loop's residual OPD (the sensing direction) is
+ * added to d_psf (device float32 [N][N], N = pas_psf_size) and its Strehl ratio written to
+ * d_sr[t mod sr_len] (device float64, or NULL) for step t. The camera's two passes run on a
+ * stream of the loop's own after the residual kernel, beside the sensor, and join before the
+ * reconstruction. psf = NULL detaches. The camera's pupil must be the loop's (PAS_EINVAL);
+ * buffers are borrowed and must outlive the attachment. Synchronises the context stream;
+ * the step graph is captured again at the next step. Persistent batches refuse loops with
+ * a camera; graph-branch batches step it with the loop. */
+pas_status pas_loop_attach_camera(pas_loop_t loop, pas_psf_t psf, float* d_psf, double* d_sr, int32_t sr_len,
+                                  int64_t start_step);
 /* Name of kernel `idx` of pas_loop_profile (static string), NULL if out of range. */
 const char* pas_loop_kernel_name(int32_t idx);
 

@@ -11,6 +11,7 @@
 #include "batchrec.cuh"
 #include "internal.h"
 #include "mlp.cuh"
+#include "psf.cuh"
 #include "pyr.cuh"
 #include "recon.cuh"
 #include "sh.cuh"
@@ -27,6 +28,16 @@ struct pas_loop_s {
   int n_int = 1;            // detector steps per frame (pas_loop_set_integration)
   int taps = PAS_TAPS_AUTO;         // the atmosphere's tap staging and wait bound at creation
   uint32_t tap_wait_limit = 0;
+  // a PSF camera inside the step (pas_loop_attach_camera): its two passes run on a
+  // stream of their own after the residual, beside the sensor, and join before the
+  // reconstruction (which advances the step counter they read)
+  pas_psf_t cam = nullptr;
+  float* d_cam_psf = nullptr;
+  double* d_cam_sr = nullptr;
+  int cam_sr_len = 1;
+  long long cam_start = 0;
+  cudaStream_t cam_stream = nullptr;
+  cudaEvent_t cam_fork = nullptr, cam_join = nullptr;
   float* d_acc = nullptr;   // [nd*nd] the integrating detector's accumulator
   float* d_opd = nullptr;
   float* d_frame = nullptr;
@@ -107,6 +118,16 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
   if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
   pas_status s = skip_residual ? PAS_OK : enqueue_residual(L, st);
   if (s != PAS_OK) return s;
+  if (L->cam) {  // the camera images this step's residual beside the sensor
+    cudaError_t e = cudaEventRecord(L->cam_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(L->cam_stream, L->cam_fork, 0);
+    if (e != cudaSuccess) return pas::set_error(L->ctx, PAS_ECUDA, "loop camera fork: %s", cudaGetErrorString(e));
+    s = pas::psf_launch(L->cam, L->d_opd, L->d_cam_psf, 1, L->d_cam_sr, L->d_step, L->cam_start, L->cam_sr_len,
+                        L->cam_stream);
+    if (s != PAS_OK) return s;
+    e = cudaEventRecord(L->cam_join, L->cam_stream);
+    if (e != cudaSuccess) return pas::set_error(L->ctx, PAS_ECUDA, "loop camera join: %s", cudaGetErrorString(e));
+  }
   const pas::LoopExtra fa = loop_extra(L);
   const bool pdl_sensor = pdl && !skip_residual;
   if (L->sh)
@@ -115,9 +136,13 @@ static pas_status loop_enqueue(pas_loop_t L, cudaStream_t st, cudaEvent_t* ev = 
     s = pas::pyr_launch(L->pyr, L->d_opd, L->d_frame, L->d_slopes, st, &fa, false, ev ? ev + 1 : nullptr,
                         pdl_sensor);
   if (s != PAS_OK) return s;
+  if (L->cam) {
+    const cudaError_t e = cudaStreamWaitEvent(st, L->cam_join, 0);
+    if (e != cudaSuccess) return pas::set_error(L->ctx, PAS_ECUDA, "loop camera join: %s", cudaGetErrorString(e));
+  }
   if (skip_recon) return PAS_OK;
   if (ev) cudaEventRecordWithFlags(ev[4], st, cudaEventRecordExternal);
-  s = enqueue_recon(L, st, pdl);
+  s = enqueue_recon(L, st, pdl && !L->cam);
   if (ev) cudaEventRecordWithFlags(ev[5], st, cudaEventRecordExternal);
   return s;
 }
@@ -132,6 +157,9 @@ void pas_loop_destroy(pas_loop_t L) {
   if (L->prof_graph) cudaGraphDestroy(L->prof_graph);
   for (int i = 0; i <= PAS_LOOP_KERNELS; ++i)
     if (L->prof_ev[i]) cudaEventDestroy(L->prof_ev[i]);
+  if (L->cam_fork) cudaEventDestroy(L->cam_fork);
+  if (L->cam_join) cudaEventDestroy(L->cam_join);
+  if (L->cam_stream) cudaStreamDestroy(L->cam_stream);
   pas::dev_free(L->d_opd);
   pas::dev_free(L->d_frame);
   pas::dev_free(L->d_slopes);
@@ -341,6 +369,29 @@ pas_status pas_loop_set_integration(pas_loop_t L, int32_t n_int) {
   if (L->d_acc) PAS_CUDA_TRY(L->ctx, cudaMemset(L->d_acc, 0, sizeof(float) * L->nd * L->nd));
   loop_drop_graphs(L);
   L->n_int = n_int;
+  return PAS_OK;
+}
+
+pas_status pas_loop_attach_camera(pas_loop_t L, pas_psf_t psf, float* d_psf, double* d_sr, int32_t sr_len,
+                                  int64_t start_step) {
+  if (!L) return pas::set_global_error(PAS_EINVAL, "pas_loop_attach_camera: NULL loop");
+  if (psf) {
+    PAS_CHECK_ARG(L->ctx, d_psf != nullptr && sr_len >= 1 && start_step >= 0,
+                  "pas_loop_attach_camera: a PSF buffer, sr_len >= 1, start_step >= 0");
+    PAS_CHECK_ARG(L->ctx, pas::psf_np(psf) == L->Np, "pas_loop_attach_camera: camera and loop pupil sizes differ");
+  }
+  PAS_CUDA_TRY(L->ctx, cudaStreamSynchronize(L->ctx->stream));
+  if (psf && !L->cam_stream) {
+    PAS_CUDA_TRY(L->ctx, cudaStreamCreateWithFlags(&L->cam_stream, cudaStreamNonBlocking));
+    PAS_CUDA_TRY(L->ctx, cudaEventCreateWithFlags(&L->cam_fork, cudaEventDisableTiming));
+    PAS_CUDA_TRY(L->ctx, cudaEventCreateWithFlags(&L->cam_join, cudaEventDisableTiming));
+  }
+  loop_drop_graphs(L);
+  L->cam = psf;
+  L->d_cam_psf = psf ? d_psf : nullptr;
+  L->d_cam_sr = psf ? d_sr : nullptr;
+  L->cam_sr_len = psf ? sr_len : 1;
+  L->cam_start = psf ? start_step : 0;
   return PAS_OK;
 }
 
@@ -600,6 +651,10 @@ pas_status pas_batch_create_ex(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops
     for (int i = 0; i < n_loops; ++i) {
       pas_loop_t L = b->loops[i];
       if (!L->pyr) continue;
+      if (L->cam) {
+        pas_batch_destroy(b);
+        return pas::set_error(ctx, PAS_EINVAL, "pas_batch_create: a loop with an attached camera in a persistent batch");
+      }
       b->member[i] = (int)py.size();
       py.push_back(L->pyr);
       opd.push_back(L->d_opd);
@@ -634,7 +689,8 @@ pas_status pas_batch_create_ex(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops
     // a persistent member launches its residual and slopes kernels (and its
     // reconstruction unless its group's product does it)
     const int whole = b->member[i] >= 0 ? 3 : b->loops[i]->sh ? 3 : PAS_LOOP_KERNELS;
-    b->kernels_per_step += whole - (group_of[i] >= 0 ? 1 : 0) - (b->rgroup_of[i] >= 0 ? 1 : 0);
+    b->kernels_per_step += whole - (group_of[i] >= 0 ? 1 : 0) - (b->rgroup_of[i] >= 0 ? 1 : 0) +
+                           (b->loops[i]->cam ? 2 : 0);
   }
   b->kernels_per_step += 3 * (int)b->groups.size() + 2 * (int)b->rgroups.size();
   if (b->pyr_batch) b->kernels_per_step += pas::pyr_batch_n_groups(b->pyr_batch);

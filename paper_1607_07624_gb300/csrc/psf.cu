@@ -24,6 +24,7 @@
 #include "internal.h"
 #include "pdl.cuh"
 #include "phasor.cuh"
+#include "psf.cuh"
 
 namespace pas {
 
@@ -37,10 +38,15 @@ struct PsfArgs {
   const float2* rot;    // [nd][Np] exp(-2 pi i r n / N)
   float2* H;            // [N][Np] spectra of the pupil columns along axis 0
   float* psf;           // [N][N]
-  double* strehl;       // scalar or null
+  double* strehl;       // scalar or null (with `step`: a ring of sr_len entries)
   int nd, T_obs, accumulate;
   float inv_hi, inv_lo;  // 1/lambda split in two floats
   float norm;            // 1 / (sum A)^2
+  // a camera inside a loop's step: nothing before step `start`; the Strehl ratio of
+  // step t goes to strehl[t mod sr_len]
+  const long long* step = nullptr;
+  long long start = 0;
+  int sr_len = 1;
 };
 
 template <int NP>
@@ -59,6 +65,7 @@ __global__ void __launch_bounds__(PSF_COLS_WARPS * 32) psf_cols_kernel(PsfArgs a
   int* pos_s = reinterpret_cast<int*>(smem + TWN);
   float2* bufs = smem + TWN + (NP + 1) / 2;  // after pos_s (NP ints)
   pdl_trigger();
+  if (a.step && *a.step < a.start) return;  // the camera has not started (uniform)
   psf_stage_tables<NP>(a, tw_s, pos_s);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -99,8 +106,13 @@ __global__ void psf_rows_kernel(PsfArgs a) {
   float2* bufs = smem + TWN + (NP + 1) / 2;
   const int nd = a.nd, N = nd * NP;
   float* row = reinterpret_cast<float*>(bufs + nd * PITCH);  // [N]
+  pdl_wait();  // H (and the step counter's value) come from the predecessors
+  long long t = 0;
+  if (a.step) {
+    t = *a.step;
+    if (t < a.start) return;  // uniform
+  }
   psf_stage_tables<NP>(a, tw_s, pos_s);
-  pdl_wait();  // H comes from the first pass
   __syncthreads();
   const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = blockIdx.x;
@@ -119,7 +131,7 @@ __global__ void psf_rows_kernel(PsfArgs a) {
     const float val = row[q];
     out[q] = a.accumulate ? __fadd_rn(out[q], val) : val;
   }
-  if (a.strehl && p == N / 2 && threadIdx.x == 0) *a.strehl = (double)row[N / 2];
+  if (a.strehl && p == N / 2 && threadIdx.x == 0) a.strehl[a.step ? t % a.sr_len : 0] = (double)row[N / 2];
 }
 
 struct PsfKernels {
@@ -233,9 +245,13 @@ pas_status pas_psf_create(pas_ctx_t ctx, int32_t Np, int32_t nd, double waveleng
 
 int32_t pas_psf_size(pas_psf_t P) { return P ? P->N : -1; }
 
-pas_status pas_psf_compute(pas_psf_t P, const float* d_opd, float* d_psf, int32_t accumulate, double* d_strehl) {
-  if (!P || !d_opd || !d_psf) return pas::set_global_error(PAS_EINVAL, "pas_psf_compute: NULL argument");
-  pas::PsfArgs a;
+}  // extern "C"
+
+namespace pas {
+
+pas_status psf_launch(pas_psf_t P, const float* d_opd, float* d_psf, int accumulate, double* d_strehl,
+                      const long long* d_step, long long start, int sr_len, cudaStream_t st) {
+  PsfArgs a;
   a.opd = d_opd;
   a.tw = P->d_tw;
   a.pos = P->d_pos;
@@ -249,13 +265,25 @@ pas_status pas_psf_compute(pas_psf_t P, const float* d_opd, float* d_psf, int32_
   a.inv_hi = P->inv_hi;
   a.inv_lo = P->inv_lo;
   a.norm = P->norm;
-  cudaStream_t st = P->ctx->stream;
-  cudaError_t e = pas::launch_k(P->kern.cols, dim3((P->Np + pas::PSF_COLS_WARPS - 1) / pas::PSF_COLS_WARPS, P->nd),
-                                dim3(pas::PSF_COLS_WARPS * 32), P->smem_cols, st, false, a);
-  if (e == cudaSuccess)
-    e = pas::launch_k(P->kern.rows, dim3(P->N), dim3(P->nd * 32), P->smem_rows, st, true, a);
-  if (e != cudaSuccess) return pas::set_error(P->ctx, PAS_ECUDA, "pas_psf_compute launch: %s", cudaGetErrorString(e));
+  a.step = d_step;
+  a.start = start;
+  a.sr_len = sr_len;
+  cudaError_t e = launch_k(P->kern.cols, dim3((P->Np + PSF_COLS_WARPS - 1) / PSF_COLS_WARPS, P->nd),
+                           dim3(PSF_COLS_WARPS * 32), P->smem_cols, st, false, a);
+  if (e == cudaSuccess) e = launch_k(P->kern.rows, dim3(P->N), dim3(P->nd * 32), P->smem_rows, st, true, a);
+  if (e != cudaSuccess) return set_error(P->ctx, PAS_ECUDA, "PSF camera launch: %s", cudaGetErrorString(e));
   return PAS_OK;
+}
+
+int psf_np(pas_psf_t P) { return P->Np; }
+
+}  // namespace pas
+
+extern "C" {
+
+pas_status pas_psf_compute(pas_psf_t P, const float* d_opd, float* d_psf, int32_t accumulate, double* d_strehl) {
+  if (!P || !d_opd || !d_psf) return pas::set_global_error(PAS_EINVAL, "pas_psf_compute: NULL argument");
+  return pas::psf_launch(P, d_opd, d_psf, accumulate, d_strehl, nullptr, 0, 1, P->ctx->stream);
 }
 
 }  // extern "C"

@@ -149,6 +149,7 @@ _SIGS = {
     "pas_batch_check": (C.c_int, [vp, C.POINTER(C.c_uint32)]),
     "pas_batch_create_ex": (C.c_int, [vp, vp, i32, C.c_uint32, P(vp)]),
     "pas_atmo_tma": (i32, [vp]),
+    "pas_loop_attach_camera": (C.c_int, [vp, vp, vp, vp, i32, i64]),
     "pas_atmo_set_tap_staging": (C.c_int, [vp, i32]),
     "pas_atmo_set_wait_limit": (C.c_int, [vp, C.c_uint32]),
     "pas_atmo_check": (C.c_int, [vp, C.POINTER(C.c_uint32)]),
@@ -798,3 +799,11 @@ def pas_atmo_check(atmo):
 
 def pas_atmo_set_tap_staging(atmo, ctx, mode):
     _check(_lib.pas_atmo_set_tap_staging(atmo, int(mode)), ctx)
+
+
+def pas_loop_attach_camera(loop, ctx, psf, d_psf=None, d_sr=None, start_step=0):
+    """The PSF camera inside the loop's step graph (psf None: detach). d_sr: float64
+    CUDA tensor ring of Strehl ratios (entry t mod its length for step t) or None."""
+    n = int(d_sr.numel()) if d_sr is not None else 1
+    _check(_lib.pas_loop_attach_camera(loop, psf, _ptr(d_psf) if d_psf is not None else None,
+                                       _ptr(d_sr) if d_sr is not None else None, n, int(start_step)), ctx)

@@ -201,7 +201,7 @@ class SCAOSystem:
 
     def step(self, n=1, stats=False):
         cam = getattr(self, "camera", None)
-        if cam is None:
+        if cam is None or getattr(self, "_cam_in_graph", False):
             out = P.pas_loop_step(self.loop, self.ctx, n, stats)
             self._t = getattr(self, "_t", 0) + n
             return out
@@ -227,13 +227,17 @@ class SCAOSystem:
         return P.pas_loop_step(self.loop, self.ctx, 0, True) if stats else None
 
     # ---------------------------------------------------------------- camera
-    def attach_camera(self, nd=8, wavelength_nm=1650.0, start_step=0, sr_history=None, direction="science"):
+    def attach_camera(self, nd=8, wavelength_nm=1650.0, start_step=0, sr_history=None, direction="science",
+                      in_graph=True):
         """PSF camera on the loop's residual (Table 1 camera: imaging wavelength,
         padding nd, integration start): from loop step `start_step` on, every step's
         PSF ([N][N], N = nd Np, peak 1 for a flat wavefront at (N/2, N/2)) is added to
         `int_psf` and its Strehl ratio written to `sr` (float64 ring; entry t mod its
         length belongs to step t). direction: "science" (on axis) or "wfs" (the guide
-        star's direction); they differ only with an off-axis source. Returns N."""
+        star's direction); they differ only with an off-axis source. Where the camera
+        images the loop's own residual (on axis, or direction "wfs") it runs inside the
+        step graph (in_graph, pas_loop_attach_camera); otherwise one call per step after
+        it. Returns N."""
         if direction not in ("science", "wfs"):
             raise ValueError(f"direction must be 'science' or 'wfs', not {direction!r}")
         self.detach_camera()
@@ -254,14 +258,20 @@ class SCAOSystem:
         self.sr = torch.zeros(sr_history or getattr(self, "wfe_history", 1024), device=self.dev,
                               dtype=torch.float64)
         self.camera_start = int(start_step)
+        self._cam_in_graph = bool(in_graph) and self._cmd_queue is None and self.loop is not None
+        if self._cam_in_graph:
+            P.pas_loop_attach_camera(self.loop, self.ctx, self.camera, self.int_psf, self.sr, self.camera_start)
         return N
 
     def detach_camera(self):
         cam = getattr(self, "camera", None)
         if cam is not None:
+            if getattr(self, "_cam_in_graph", False) and self.loop is not None:
+                P.pas_loop_attach_camera(self.loop, self.ctx, None)
             torch.cuda.synchronize()
             P.pas_psf_destroy(cam)
         self.camera = None
+        self._cam_in_graph = False
         self._cmd_queue = None
 
     def step_eager(self, n=1):

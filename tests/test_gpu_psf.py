@@ -133,3 +133,38 @@ def test_camera_in_the_closed_loop_matches_oracle(env):
         s.step(2)                       # without the camera the loop runs on
     finally:
         s.close()
+
+
+def test_camera_inside_the_step_graph_equals_the_camera_called_per_step(env):
+    """The camera inside the loop's step graph (its passes beside the sensor, the step
+    counter read on the device) gives the integrated PSF and the Strehl ring of the camera
+    called after every step, bit for bit, and the loop's own WFE is unchanged by it; a
+    persistent batch refuses the loop while the camera is attached, and the camera
+    detaches cleanly."""
+    torch, pas, ctx = env
+    from paper_1607_07624_gb300.system import SCAOSystem
+    cfg = get_config("scao_8m_64px")
+    a = SCAOSystem(cfg, wfe_history=64, autotune=False)
+    b = SCAOSystem(cfg, wfe_history=64, autotune=False, basis=a.basis, R=a.R)
+    try:
+        a.attach_camera(nd=4, wavelength_nm=LAM, start_step=3, in_graph=True)
+        b.attach_camera(nd=4, wavelength_nm=LAM, start_step=3, in_graph=False)
+        assert a._cam_in_graph and not b._cam_in_graph
+        a.step(12)
+        b.step(12)
+        torch.cuda.synchronize()
+        assert np.array_equal(a.int_psf.cpu().numpy(), b.int_psf.cpu().numpy())
+        assert np.array_equal(a.sr.cpu().numpy(), b.sr.cpu().numpy())
+        assert np.all(a.sr.cpu().numpy()[:3] == 0.0) and np.all(a.sr.cpu().numpy()[3:12] > 0.0)
+        assert np.array_equal(a.wfe_nm(12), b.wfe_nm(12))
+        with pytest.raises(pas.PasError, match="camera"):
+            pas.pas_batch_create_ex(a.ctx, [a.loop], pas.PAS_BATCH_PERSISTENT)
+        a.detach_camera()
+        a.step(2)
+        b.detach_camera()
+        b.step(2)
+        torch.cuda.synchronize()
+        assert np.array_equal(a.wfe_nm(14), b.wfe_nm(14))
+    finally:
+        b.close()
+        a.close()
