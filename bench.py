@@ -427,8 +427,8 @@ def bench_psf(timed, sysg=None, n_frames=100):
                "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                             "frac": ach / FP32_PEAK_TFLOPS}}
         if sysg is not None:
-            # the headline loop with the camera integrating every step (graph launch +
-            # the camera's two kernels per step), then the loop state is restored
+            # the LBT-class loop with the camera integrating every step (the camera's two
+            # kernels on a branch of the loop's step graph), then the loop state is restored
             zeros = np.zeros((sysg.delay, sysg.n_modes), dtype=np.float32)
             sysg.attach_camera(nd=nd, wavelength_nm=1650.0, start_step=0)
             try:
