@@ -152,4 +152,56 @@ __device__ __forceinline__ void four_step_mask(float2* T, const float2* tw4, con
   __syncwarp();  // T is reused by the next call
 }
 
+// ----------------------------------------------- forward transforms in pairs
+// Two forward DFTs of length N = 15 R (R = 16: N = 240, R = 32: N = 480) by one warp,
+// with no mask and no inverse (the PSF camera's padded transforms). With
+// n = n1 + R n2 (n1 < R, n2 < 15) and k = 15 k1 + k2 (k1 < R, k2 < 15):
+//
+//   X[15 k1 + k2] = sum_n1 W_R^(n1 k1) W_N^(n1 k2) [sum_n2 x[n1 + R n2] W_15^(n2 k2)]
+//
+// Lane n1 of a group of R lanes takes the 15-point DFT of its elements (R = 16: lanes
+// 0-15 transform 0 and lanes 16-31 transform 1; R = 32: every lane holds both), scales
+// by W_N^(n1 k2), and one shared-memory transpose hands the 30 columns (transform,
+// k2) to lanes 0-29, which take the R-point DFT over n1.
+// T: this warp's pair_buf(N) float2 (column c at c (R + 1): no bank conflicts either
+// way); tw[(k2 - 1) R + n1] = W_N^(n1 k2), k2 = 1..14 (pair_tw_size(N) entries).
+// load(t, n): element n of transform t; store(t, m, v): frequency m of transform t,
+// called by lanes 0-29 for m = 15 k1 + k2, k1 = 0..R-1.
+__host__ __device__ constexpr bool pair_ok(int N) { return N == 240 || N == 480; }
+__host__ __device__ constexpr int pair_r(int N) { return N / 15; }
+__host__ __device__ constexpr int pair_buf(int N) { return 30 * (pair_r(N) + 1); }
+__host__ __device__ constexpr int pair_tw_size(int N) { return 14 * pair_r(N); }
+
+template <int N, class Load, class Store>
+__device__ __forceinline__ void pair_forward(float2* T, const float2* tw, int lane, Load& load, Store& store) {
+  constexpr int Q = 15, R = pair_r(N), P = R + 1, TL = R == 32 ? 2 : 1;
+  static_assert(R == 16 || R == 32, "N = 240 or 480");
+  const int n1 = lane & (R - 1), g = lane / R;
+#pragma unroll
+  for (int tl = 0; tl < TL; ++tl) {
+    const int t = TL == 2 ? tl : g;
+    float2 v[Q];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) v[n2] = load(t, n1 + R * n2);
+    Bfly<15, false>::run(v);
+#pragma unroll
+    for (int k2 = 1; k2 < Q; ++k2) v[k2] = cmul(v[k2], __ldg(tw + (k2 - 1) * R + n1));
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) T[(t * Q + k2) * P + n1] = v[k2];
+  }
+  __syncwarp();
+  if (lane < 2 * Q) {
+    const int t = lane >= Q ? 1 : 0, k2 = lane - Q * t;
+    const float2* col = T + lane * P;
+    float2 w[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) w[i] = col[i];
+    if constexpr (R == 16) Bfly<16, false>::run(w);
+    else dft32<false>(w);
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) store(t, Q * k1 + k2, w[k1]);
+  }
+  __syncwarp();  // T is reused by the next call
+}
+
 }  // namespace pas

@@ -18,6 +18,17 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Prefetch the 128-byte line holding p into L1 (and L2).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Prefetch bytes [p, p + n) line by line into L1, the CTA's threads sharing the lines.
+__device__ __forceinline__ void prefetch_l1_span(const void* p, size_t n) {
+  const char* c = static_cast<const char*>(p);
+  for (size_t o = (size_t)threadIdx.x * 128; o < n; o += (size_t)blockDim.x * 128) prefetch_l1(c + o);
+}
+
 // Launch with or without the programmatic-serialization attribute.
 template <typename... KArgs, typename... Args>
 cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,

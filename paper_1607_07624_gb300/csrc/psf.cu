@@ -14,12 +14,16 @@
 // length Np (fft.cuh), one per residue r: first along axis 0 for the Np pupil
 // columns (spectrum written transposed, H[p][j]), then along axis 1 for the N
 // frequency rows, whose nd residues meet in shared memory and leave as one
-// coalesced row of |F|^2.
+// coalesced row of |F|^2. Pupils of 240 and 480 px run two transforms per warp
+// through the four-step engine of fft4.cuh (pair_forward); the others one per warp
+// through the pass-by-pass engine.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <vector>
 
 #include "fft.cuh"
+#include "fft4.cuh"
 #include "fft_host.h"
 #include "internal.h"
 #include "pdl.cuh"
@@ -53,6 +57,43 @@ template <int NP>
 __device__ __forceinline__ void psf_stage_tables(const PsfArgs& a, float2* tw_s, int* pos_s) {
   for (int t = threadIdx.x; t < tw_size(NP); t += blockDim.x) tw_s[t] = a.tw[t];
   for (int t = threadIdx.x; t < NP; t += blockDim.x) pos_s[t] = a.pos[t];
+}
+
+// One row of |F|^2 (sum A)^-2 from shared memory to the PSF, written or added: as
+// float4 where both rows are 16-byte aligned (every N = nd Np a multiple of 4), the old
+// values of an integrated PSF loaded RW at a time before their adds, so that RW memory
+// latencies overlap instead of one per element.
+__device__ __forceinline__ void psf_write_row(float* out, const float* row, int N, bool acc) {
+  constexpr int RW = 4;
+  if ((N & 3) == 0 && ((reinterpret_cast<uintptr_t>(out) | reinterpret_cast<uintptr_t>(row)) & 15) == 0) {
+    const int n4 = N >> 2;
+    float4* o4 = reinterpret_cast<float4*>(out);
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+    for (int q0 = threadIdx.x; q0 < n4; q0 += RW * blockDim.x) {
+      float4 old[RW];
+#pragma unroll
+      for (int u = 0; u < RW; ++u) {
+        const int q = q0 + u * blockDim.x;
+        old[u] = acc && q < n4 ? o4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < RW; ++u) {
+        const int q = q0 + u * blockDim.x;
+        if (q < n4) {
+          float4 v = r4[q];
+          if (acc)
+            v = make_float4(__fadd_rn(old[u].x, v.x), __fadd_rn(old[u].y, v.y), __fadd_rn(old[u].z, v.z),
+                            __fadd_rn(old[u].w, v.w));
+          o4[q] = v;
+        }
+      }
+    }
+    return;
+  }
+  for (int q = threadIdx.x; q < N; q += blockDim.x) {
+    const float val = row[q];
+    out[q] = acc ? __fadd_rn(out[q], val) : val;
+  }
 }
 
 // Pass 1: CTA (column block, residue r), one warp per pupil column j, transform
@@ -126,11 +167,95 @@ __global__ void psf_rows_kernel(PsfArgs a) {
     row[nd * m + r] = __fmul_rn(__fmaf_rn(v.x, v.x, __fmul_rn(v.y, v.y)), a.norm);
   }
   __syncthreads();
-  float* out = a.psf + (size_t)p * N;
-  for (int q = threadIdx.x; q < N; q += blockDim.x) {
-    const float val = row[q];
-    out[q] = a.accumulate ? __fadd_rn(out[q], val) : val;
+  psf_write_row(a.psf + (size_t)p * N, row, N, a.accumulate != 0);
+  if (a.strehl && p == N / 2 && threadIdx.x == 0) a.strehl[a.step ? t % a.sr_len : 0] = (double)row[N / 2];
+}
+
+// Pupils of 240 and 480 px: the same two passes with two transforms per warp
+// (pair_forward, fft4.cuh: frequencies in natural order, no position table).
+// Pass 1: CTA = PSF_PAIR_COLS pupil columns x every residue. The CTA forms the field
+// A e^{i phi} (-1)^(i+j) of its columns once in shared memory (one phasor per pixel
+// for all nd residues); warp w takes column j0 + w / nw and residues 2 (w % nw) and
+// 2 (w % nw) + 1 (nw = ceil(nd / 2); a missing second residue of an odd nd transforms
+// zeros and stores nothing); lanes write H[nd m + r][j] directly.
+constexpr int PSF_PAIR_COLS = 2;
+
+template <int NP>
+__global__ void __launch_bounds__(PSF_PAIR_COLS * 8 * 32) psf_cols_pair_kernel(PsfArgs a) {
+  extern __shared__ float2 smem[];
+  pdl_trigger();
+  if (a.step && *a.step < a.start) return;  // the camera has not started (uniform)
+  const int nd = a.nd, nw = (nd + 1) / 2;
+  const int j0 = blockIdx.x * PSF_PAIR_COLS;
+  // the constant tables the transforms read (L1), fetched under the field's latency
+  prefetch_l1_span(a.rot, sizeof(float2) * (size_t)nd * NP);
+  prefetch_l1_span(a.tw, sizeof(float2) * pair_tw_size(NP));
+  float2* E = smem;                                    // [PSF_PAIR_COLS][NP]
+  float2* Tb = smem + PSF_PAIR_COLS * NP;              // [warps][pair_buf]
+  for (int e = threadIdx.x; e < PSF_PAIR_COLS * NP; e += blockDim.x) {
+    const int c = e / NP, x = e - c * NP, j = j0 + c;
+    const int ai = 2 * x - NP + 1, bj = 2 * j - NP + 1;
+    const int d2 = ai * ai + bj * bj;
+    float2 v = make_float2(0.f, 0.f);
+    if (j < NP && d2 <= NP * NP && d2 >= a.T_obs) {
+      v = opd_phasor(__ldg(a.opd + (size_t)x * NP + j), a.inv_hi, a.inv_lo);
+      if ((x + j) & 1) v = make_float2(-v.x, -v.y);
+    }
+    E[e] = v;
   }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = warp / nw, rp = warp - c * nw, j = j0 + c;
+  float2* T = Tb + warp * pair_buf(NP);
+  const float2* Ec = E + c * NP;
+  auto load = [&](int t, int x) -> float2 {
+    const int r = 2 * rp + t;
+    if (r >= nd) return make_float2(0.f, 0.f);
+    return cmul(Ec[x], __ldg(a.rot + (size_t)r * NP + x));
+  };
+  auto store = [&](int t, int m, float2 v) {
+    const int r = 2 * rp + t;
+    if (r < nd && j < NP) a.H[((size_t)nd * m + r) * NP + j] = v;
+  };
+  pair_forward<NP>(T, a.tw, lane, load, store);
+}
+
+// Pass 2: CTA = one frequency row p, warp w = residues 2w and 2w + 1 (a missing
+// second residue of an odd nd transforms zeros and stores nothing); |F|^2 (sum A)^-2
+// gathered in shared memory at q = nd m + r and written (or added) as one row.
+template <int NP>
+__global__ void __launch_bounds__(256) psf_rows_pair_kernel(PsfArgs a) {
+  extern __shared__ float2 smem[];
+  const int nd = a.nd, N = nd * NP, nw = (nd + 1) / 2;
+  float* row = reinterpret_cast<float*>(smem + nw * pair_buf(NP));  // [N]
+  // before the wait, for an integrated PSF: this row's old values into L2 (the previous
+  // frame's rows pass completed before this frame's columns pass started)
+  if (a.accumulate) {
+    const char* o = reinterpret_cast<const char*>(a.psf + (size_t)blockIdx.x * N);
+    for (int l = threadIdx.x * 128; l < N * 4; l += blockDim.x * 128) prefetch_l2(o + l);
+  }
+  pdl_wait();  // H (and the step counter's value) come from the predecessors
+  long long t = 0;
+  if (a.step) {
+    t = *a.step;
+    if (t < a.start) return;  // uniform
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x;
+  float2* T = smem + warp * pair_buf(NP);
+  const float2* Hrow = a.H + (size_t)p * NP;
+  auto load = [&](int tt, int x) -> float2 {
+    const int r = 2 * warp + tt;
+    if (r >= nd) return make_float2(0.f, 0.f);
+    return cmul(__ldg(Hrow + x), __ldg(a.rot + (size_t)r * NP + x));
+  };
+  auto store = [&](int tt, int m, float2 v) {
+    const int r = 2 * warp + tt;
+    if (r < nd) row[nd * m + r] = __fmul_rn(__fmaf_rn(v.x, v.x, __fmul_rn(v.y, v.y)), a.norm);
+  };
+  pair_forward<NP>(T, a.tw, lane, load, store);
+  __syncthreads();
+  psf_write_row(a.psf + (size_t)p * N, row, N, a.accumulate != 0);
   if (a.strehl && p == N / 2 && threadIdx.x == 0) a.strehl[a.step ? t % a.sr_len : 0] = (double)row[N / 2];
 }
 
@@ -138,21 +263,41 @@ struct PsfKernels {
   void (*cols)(PsfArgs);
   void (*rows)(PsfArgs);
   int tw_n, pitch;
+  bool pair;  // pair_forward kernels: tw_n = pair_tw_size, pitch = pair_buf per warp
 };
 
-#define PAS_PSF_PUPILS(X) X(48) X(64) X(120) X(128) X(240) X(256) X(480)
+#define PAS_PSF_PUPILS(X) X(48) X(64) X(120) X(128) X(256)
 
 static bool lookup_psf_kernels(int Np, PsfKernels* k) {
   switch (Np) {
-#define PAS_CASE(n)                                                                      \
-  case n:                                                                                \
-    *k = PsfKernels{psf_cols_kernel<n>, psf_rows_kernel<n>, tw_size(n), buf_len(n) | 1}; \
+    case 240:
+      *k = PsfKernels{psf_cols_pair_kernel<240>, psf_rows_pair_kernel<240>, pair_tw_size(240), pair_buf(240), true};
+      return true;
+    case 480:
+      *k = PsfKernels{psf_cols_pair_kernel<480>, psf_rows_pair_kernel<480>, pair_tw_size(480), pair_buf(480), true};
+      return true;
+#define PAS_CASE(n)                                                                             \
+  case n:                                                                                       \
+    *k = PsfKernels{psf_cols_kernel<n>, psf_rows_kernel<n>, tw_size(n), buf_len(n) | 1, false}; \
     return true;
     PAS_PSF_PUPILS(PAS_CASE)
 #undef PAS_CASE
     default:
       return false;
   }
+}
+
+// W_N^(n1 k2) = exp(-2 pi i n1 k2 / N) at [(k2 - 1) R + n1], k2 = 1..14, n1 < R = N / 15
+// (pair_forward's table), float32 of the double value.
+static std::vector<float2> pair_twiddles(int N) {
+  const int R = pair_r(N);
+  std::vector<float2> tw((size_t)pair_tw_size(N));
+  for (int k2 = 1; k2 < 15; ++k2)
+    for (int n1 = 0; n1 < R; ++n1) {
+      const double a = -2.0 * M_PI * (double)(n1 * k2) / (double)N;
+      tw[(size_t)(k2 - 1) * R + n1] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+  return tw;
 }
 
 }  // namespace pas
@@ -205,13 +350,21 @@ pas_status pas_psf_create(pas_ctx_t ctx, int32_t Np, int32_t nd, double waveleng
   P->inv_hi = (float)inv;
   P->inv_lo = (float)(inv - (double)P->inv_hi);
   P->norm = (float)(1.0 / ((double)n_pup * (double)n_pup));
-  const size_t tables = sizeof(float2) * ((size_t)kern.tw_n + (size_t)(Np + 1) / 2);
-  P->smem_cols = tables + sizeof(float2) * (size_t)pas::PSF_COLS_WARPS * kern.pitch;
-  P->smem_rows = tables + sizeof(float2) * ((size_t)nd * kern.pitch + (size_t)(N + 1) / 2);
-
-  std::vector<float2> tw = pas::fft_twiddles(Np);
-  std::vector<int> pos(Np);
-  for (int p = 0; p < Np; ++p) pos[pas::fft_freq_at(Np, p)] = p;
+  std::vector<float2> tw;
+  std::vector<int> pos(Np, 0);
+  if (kern.pair) {
+    // no staged tables: per warp one transpose buffer; the rows pass adds its row
+    P->smem_cols = sizeof(float2) * ((size_t)pas::PSF_PAIR_COLS * Np +
+                                     (size_t)pas::PSF_PAIR_COLS * ((nd + 1) / 2) * kern.pitch);
+    P->smem_rows = sizeof(float2) * ((size_t)((nd + 1) / 2) * kern.pitch + (size_t)(N + 1) / 2);
+    tw = pas::pair_twiddles(Np);
+  } else {
+    const size_t tables = sizeof(float2) * ((size_t)kern.tw_n + (size_t)(Np + 1) / 2);
+    P->smem_cols = tables + sizeof(float2) * (size_t)pas::PSF_COLS_WARPS * kern.pitch;
+    P->smem_rows = tables + sizeof(float2) * ((size_t)nd * kern.pitch + (size_t)(N + 1) / 2);
+    tw = pas::fft_twiddles(Np);
+    for (int p = 0; p < Np; ++p) pos[pas::fft_freq_at(Np, p)] = p;
+  }
   std::vector<float2> rot((size_t)nd * Np);
   for (int r = 0; r < nd; ++r)
     for (int n = 0; n < Np; ++n) {
@@ -268,9 +421,17 @@ pas_status psf_launch(pas_psf_t P, const float* d_opd, float* d_psf, int accumul
   a.step = d_step;
   a.start = start;
   a.sr_len = sr_len;
-  cudaError_t e = launch_k(P->kern.cols, dim3((P->Np + PSF_COLS_WARPS - 1) / PSF_COLS_WARPS, P->nd),
-                           dim3(PSF_COLS_WARPS * 32), P->smem_cols, st, false, a);
-  if (e == cudaSuccess) e = launch_k(P->kern.rows, dim3(P->N), dim3(P->nd * 32), P->smem_rows, st, true, a);
+  cudaError_t e;
+  if (P->kern.pair) {
+    e = launch_k(P->kern.cols, dim3((P->Np + PSF_PAIR_COLS - 1) / PSF_PAIR_COLS),
+                 dim3(PSF_PAIR_COLS * ((P->nd + 1) / 2) * 32), P->smem_cols, st, false, a);
+    if (e == cudaSuccess)
+      e = launch_k(P->kern.rows, dim3(P->N), dim3((P->nd + 1) / 2 * 32), P->smem_rows, st, true, a);
+  } else {
+    e = launch_k(P->kern.cols, dim3((P->Np + PSF_COLS_WARPS - 1) / PSF_COLS_WARPS, P->nd),
+                 dim3(PSF_COLS_WARPS * 32), P->smem_cols, st, false, a);
+    if (e == cudaSuccess) e = launch_k(P->kern.rows, dim3(P->N), dim3(P->nd * 32), P->smem_rows, st, true, a);
+  }
   if (e != cudaSuccess) return set_error(P->ctx, PAS_ECUDA, "PSF camera launch: %s", cudaGetErrorString(e));
   return PAS_OK;
 }

@@ -30,11 +30,22 @@ __device__ inline double block_sum(double v, double* red) {
 
 // Called by every thread of one CTA (it synchronises the CTA).
 __device__ inline void wfe_finalize(const LoopExtra& w, double* red) {
+  // thread t adds partials t, t + blockDim.x, ... in that order; eight loads are in
+  // flight before the adds (one latency per eight partials, not per partial)
+  constexpr int U = 8;
   double s1 = 0.0, s2 = 0.0;
-  for (int t = threadIdx.x; t < w.n_wfe_part; t += blockDim.x) {
-    const double2 p = w.wfe_part[t];
-    s1 += p.x;
-    s2 += p.y;
+  for (int t0 = threadIdx.x; t0 < w.n_wfe_part; t0 += U * blockDim.x) {
+    double2 p[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = t0 + u * blockDim.x;
+      p[u] = t < w.n_wfe_part ? w.wfe_part[t] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      s1 += p[u].x;
+      s2 += p[u].y;
+    }
   }
   s1 = block_sum(s1, red);
   s2 = block_sum(s2, red);

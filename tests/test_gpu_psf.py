@@ -54,7 +54,9 @@ def gpu_psf(env, Np, nd, obs, opd32, accumulate_with=None):
 
 @pytest.mark.parametrize("Np,nd,obs,kind", [(64, 2, 0.1, "small"), (64, 4, 0.1, "open"), (64, 8, 0.0, "small"),
                                             (48, 8, 0.25, "open"), (64, 3, 0.1, "open"), (120, 4, 0.1, "small"), (240, 4, 0.1, "open"),
-                                            (240, 8, 0.1, "small"), (240, 8, 0.1, "open")])
+                                            (240, 8, 0.1, "small"), (240, 8, 0.1, "open"), (240, 3, 0.1, "open"),
+                                            (240, 5, 0.0, "small"), (240, 16, 0.1, "small"), (480, 2, 0.1, "open"),
+                                            (480, 4, 0.1, "small"), (480, 3, 0.2, "open")])
 def test_psf_matches_oracle(env, Np, nd, obs, kind):
     from oracle import psf as ps
     if kind == "small":
