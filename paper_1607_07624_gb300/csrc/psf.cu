@@ -96,6 +96,37 @@ __device__ __forceinline__ void psf_write_row(float* out, const float* row, int 
   }
 }
 
+// The paired rows pass keeps its row padded by one word per 32 (entry q at q + q / 32):
+// its lanes store frequencies nd apart, which would otherwise meet in a few banks. The
+// write-out reads four consecutive entries (never split by the padding) per float4.
+__device__ __forceinline__ int psf_pad(int q) { return q + (q >> 5); }
+
+__device__ __forceinline__ void psf_write_row_padded(float* out, const float* row, int N, bool acc) {
+  constexpr int RW = 4;
+  const int n4 = N >> 2;  // N = nd Np, Np 240 or 480: a multiple of 4; rows 16-byte aligned
+  float4* o4 = reinterpret_cast<float4*>(out);
+  for (int q0 = threadIdx.x; q0 < n4; q0 += RW * blockDim.x) {
+    float4 old[RW];
+#pragma unroll
+    for (int u = 0; u < RW; ++u) {
+      const int q = q0 + u * blockDim.x;
+      old[u] = acc && q < n4 ? o4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < RW; ++u) {
+      const int q = q0 + u * blockDim.x;
+      if (q < n4) {
+        const float* r = row + psf_pad(4 * q);
+        float4 v = make_float4(r[0], r[1], r[2], r[3]);
+        if (acc)
+          v = make_float4(__fadd_rn(old[u].x, v.x), __fadd_rn(old[u].y, v.y), __fadd_rn(old[u].z, v.z),
+                          __fadd_rn(old[u].w, v.w));
+        o4[q] = v;
+      }
+    }
+  }
+}
+
 // Pass 1: CTA (column block, residue r), one warp per pupil column j, transform
 // along axis 0 of A e^{i phi} (-1)^(i+j) e^{-2 pi i r i / N}.
 template <int NP>
@@ -173,12 +204,12 @@ __global__ void psf_rows_kernel(PsfArgs a) {
 
 // Pupils of 240 and 480 px: the same two passes with two transforms per warp
 // (pair_forward, fft4.cuh: frequencies in natural order, no position table).
-// Pass 1: CTA = PSF_PAIR_COLS pupil columns x every residue. The CTA forms the field
+// Pass 1: CTA = PSF_PAIR_COLS pupil column(s) x every residue. The CTA forms the field
 // A e^{i phi} (-1)^(i+j) of its columns once in shared memory (one phasor per pixel
 // for all nd residues); warp w takes column j0 + w / nw and residues 2 (w % nw) and
 // 2 (w % nw) + 1 (nw = ceil(nd / 2); a missing second residue of an odd nd transforms
 // zeros and stores nothing); lanes write H[nd m + r][j] directly.
-constexpr int PSF_PAIR_COLS = 2;
+constexpr int PSF_PAIR_COLS = 1;
 
 template <int NP>
 __global__ void __launch_bounds__(PSF_PAIR_COLS * 8 * 32) psf_cols_pair_kernel(PsfArgs a) {
@@ -220,9 +251,11 @@ __global__ void __launch_bounds__(PSF_PAIR_COLS * 8 * 32) psf_cols_pair_kernel(P
   pair_forward<NP>(T, a.tw, lane, load, store);
 }
 
-// Pass 2: CTA = one frequency row p, warp w = residues 2w and 2w + 1 (a missing
-// second residue of an odd nd transforms zeros and stores nothing); |F|^2 (sum A)^-2
-// gathered in shared memory at q = nd m + r and written (or added) as one row.
+// Pass 2: CTA = one frequency row p, warp w = residues w and w + nw (nw = ceil(nd / 2);
+// a missing second residue of an odd nd transforms zeros and stores nothing: with
+// residues nw apart the pair's 30 lanes store to 30 distinct banks at nd = 8);
+// |F|^2 (sum A)^-2 gathered in shared memory at q = nd m + r (padded) and written (or
+// added) as one row.
 template <int NP>
 __global__ void __launch_bounds__(256) psf_rows_pair_kernel(PsfArgs a) {
   extern __shared__ float2 smem[];
@@ -245,18 +278,19 @@ __global__ void __launch_bounds__(256) psf_rows_pair_kernel(PsfArgs a) {
   float2* T = smem + warp * pair_buf(NP);
   const float2* Hrow = a.H + (size_t)p * NP;
   auto load = [&](int tt, int x) -> float2 {
-    const int r = 2 * warp + tt;
+    const int r = warp + nw * tt;
     if (r >= nd) return make_float2(0.f, 0.f);
     return cmul(__ldg(Hrow + x), __ldg(a.rot + (size_t)r * NP + x));
   };
   auto store = [&](int tt, int m, float2 v) {
-    const int r = 2 * warp + tt;
-    if (r < nd) row[nd * m + r] = __fmul_rn(__fmaf_rn(v.x, v.x, __fmul_rn(v.y, v.y)), a.norm);
+    const int r = warp + nw * tt;
+    if (r < nd) row[psf_pad(nd * m + r)] = __fmul_rn(__fmaf_rn(v.x, v.x, __fmul_rn(v.y, v.y)), a.norm);
   };
   pair_forward<NP>(T, a.tw, lane, load, store);
   __syncthreads();
-  psf_write_row(a.psf + (size_t)p * N, row, N, a.accumulate != 0);
-  if (a.strehl && p == N / 2 && threadIdx.x == 0) a.strehl[a.step ? t % a.sr_len : 0] = (double)row[N / 2];
+  psf_write_row_padded(a.psf + (size_t)p * N, row, N, a.accumulate != 0);
+  if (a.strehl && p == N / 2 && threadIdx.x == 0)
+    a.strehl[a.step ? t % a.sr_len : 0] = (double)row[psf_pad(N / 2)];
 }
 
 struct PsfKernels {
@@ -356,7 +390,7 @@ pas_status pas_psf_create(pas_ctx_t ctx, int32_t Np, int32_t nd, double waveleng
     // no staged tables: per warp one transpose buffer; the rows pass adds its row
     P->smem_cols = sizeof(float2) * ((size_t)pas::PSF_PAIR_COLS * Np +
                                      (size_t)pas::PSF_PAIR_COLS * ((nd + 1) / 2) * kern.pitch);
-    P->smem_rows = sizeof(float2) * ((size_t)((nd + 1) / 2) * kern.pitch + (size_t)(N + 1) / 2);
+    P->smem_rows = sizeof(float2) * ((size_t)((nd + 1) / 2) * kern.pitch) + sizeof(float) * ((size_t)N + N / 32 + 1);
     tw = pas::pair_twiddles(Np);
   } else {
     const size_t tables = sizeof(float2) * ((size_t)kern.tw_n + (size_t)(Np + 1) / 2);

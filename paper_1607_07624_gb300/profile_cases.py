@@ -6,6 +6,7 @@ wavefront error of a random system means nothing.
     python -m paper_1607_07624_gb300.profile_cases scao_elt_480px --basis fp32 --steps 4
     python -m paper_1607_07624_gb300.profile_cases scao_8m_64px --batch 16 --persistent
     python -m paper_1607_07624_gb300.profile_cases gemm --gemm 8192 --steps 3
+    python -m paper_1607_07624_gb300.profile_cases psf --psf 240,8 --steps 4
 
 Kernel launches: with --batch 0 every step launches the loop's kernels once, in step order
 (residual, rows pass, columns pass, slopes, reconstructor), so ``ncu -k regex:<kernel> -s
@@ -51,13 +52,38 @@ def _gemm(n, steps, seed):
         pas.pas_ctx_destroy(ctx)
 
 
+def _psf(spec, steps, seed):
+    """--steps integrated PSF frames (1650 nm) of a seeded 150 nm RMS residual."""
+    import numpy as np
+    from synth.inputs import random_opd_nm
+    Np, nd = (int(x) for x in spec.split(","))
+    ctx = pas.pas_ctx_create(torch.cuda.current_stream())
+    h = pas.pas_psf_create(ctx, Np, nd, 1650.0, 0.1)
+    try:
+        N = pas.pas_psf_size(h)
+        opd = torch.as_tensor(random_opd_nm(Np, 150.0, seed=seed).astype(np.float32)).cuda()
+        acc = torch.zeros(N, N, device="cuda")
+        sr = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for _ in range(steps):
+            pas.pas_psf_compute(h, ctx, opd, acc, True, sr)
+        torch.cuda.synchronize()
+        print(f"psf {N}x{N} x {steps}: Strehl {float(sr.item()):.4f}")
+        return 0
+    finally:
+        pas.pas_psf_destroy(h)
+        pas.pas_ctx_destroy(ctx)
+
+
 def main(argv=None):
     from synth import get_config
     from synth.configs import with_
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("workload", help="scao_8m_64px, scao_lbt_240px or scao_elt_480px (or gemm with --gemm)")
+    ap.add_argument("workload", help="scao_8m_64px, scao_lbt_240px or scao_elt_480px (or gemm with --gemm, "
+                    "psf with --psf)")
     ap.add_argument("--gemm", type=int, default=0, help="instead of a loop: --steps tensor-core products "
                     "C = A B^T of n x n bf16 matrices (seeded normal entries), float32 C")
+    ap.add_argument("--psf", default="", help="instead of a loop: --steps integrated frames of the PSF camera "
+                    "for pupil,padding (e.g. 240,8)")
     ap.add_argument("--basis", default="fp32", choices=sorted(_PREC))
     ap.add_argument("--recon", default="fp32", choices=sorted(_PREC))
     ap.add_argument("--taps", default="auto", choices=sorted(_TAPS), help="the residual's tap staging")
@@ -72,6 +98,8 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if a.gemm > 0:
         return _gemm(a.gemm, a.steps, a.seed)
+    if a.psf:
+        return _psf(a.psf, a.steps, a.seed)
     cfg = get_config(a.workload)
     tuning = tuple(int(x) for x in a.tuning.split(",")) if a.tuning else False
     systems, loops, batch = [], [], None
