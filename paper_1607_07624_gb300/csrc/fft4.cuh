@@ -1,20 +1,21 @@
 // Four-step FFT -> mask -> inverse FFT inside one warp, for the pyramid's transform
-// lengths N = 32 Q with Q = 15 (N = 480, two transforms per warp) or Q = 30 (N = 960,
-// one transform per warp). With n = n1 + 32 n2 and k = Q k1 + k2:
+// lengths N = 32 Q with Q = 8 (N = 256, four transforms per warp), Q = 15 (N = 480, two)
+// or Q = 30 (N = 960, one). With n = n1 + 32 n2 and k = Q k1 + k2:
 //
 //   X[Q k1 + k2] = sum_n1 W_32^(n1 k1) W_N^(n1 k2) [sum_n2 x[n1 + 32 n2] W_Q^(n2 k2)]
 //
 // so lane n1 takes the Q-point DFT of its own elements in registers, multiplies by
-// W_N^(n1 k2), and one shared-memory transpose hands column k2 to lane k2 (30 columns
-// per warp: 2 x 15 or 1 x 30), which does the 32-point DFT over n1, the pyramid mask of
+// W_N^(n1 k2), and one shared-memory transpose hands column k2 to lane k2 (Q TPW
+// columns per warp: 4 x 8, 2 x 15 or 1 x 30), which does the 32-point DFT over n1, the pyramid mask of
 // frequency Q k1 + k2, and the 32-point inverse DFT in registers; the transpose back
 // and the conjugate steps in reverse give x'[n1 + 32 n2] in lane n1. Against the
 // pass-by-pass engine (fft.cuh) each element crosses shared memory twice per direction
 // pair instead of once per radix pass, and the 32-point stage runs with no twiddle
 // loads.
 //
-// Shared memory of a warp: T[30][33] float2 (column c at c*33: both transposes are
-// free of bank conflicts). Tables shared by the CTA: tw4[(k2-1)*32 + n1] = W_N^(n1 k2)
+// Shared memory of a warp: four_buf(N) float2, the transpose buffer T[columns][33]
+// (column c at c*33: both transposes are free of bank conflicts), at least TPW N long
+// (the callers' staging). Tables shared by the CTA: tw4[(k2-1)*32 + n1] = W_N^(n1 k2)
 // for k2 = 1..Q-1, mk4[k2*33 + k1] = mask(Q k1 + k2) (the mask at natural frequency u,
 // divided by N).
 #pragma once
@@ -25,12 +26,14 @@
 namespace pas {
 
 constexpr int F4_PITCH = 33;     // float2 per column of the transpose buffer
-constexpr int F4_COLS = 30;      // columns per warp
-constexpr int F4_BUF = F4_COLS * F4_PITCH;
 
-__host__ __device__ constexpr bool four_step_ok(int N) { return N == 480 || N == 960; }
+__host__ __device__ constexpr bool four_step_ok(int N) { return N == 256 || N == 480 || N == 960; }
 __host__ __device__ constexpr int four_q(int N) { return N / 32; }
-__host__ __device__ constexpr int four_tpw(int N) { return N == 480 ? 2 : 1; }  // transforms per warp
+__host__ __device__ constexpr int four_tpw(int N) { return N == 256 ? 4 : N == 480 ? 2 : 1; }  // transforms per warp
+__host__ __device__ constexpr int four_cols(int N) { return four_q(N) * four_tpw(N); }         // columns per warp
+__host__ __device__ constexpr int four_buf(int N) {
+  return four_cols(N) * F4_PITCH > four_tpw(N) * N ? four_cols(N) * F4_PITCH : four_tpw(N) * N;
+}
 __host__ __device__ constexpr int four_tw_size(int N) { return (four_q(N) - 1) * 32; }
 __host__ __device__ constexpr int four_mask_size(int N) { return four_q(N) * F4_PITCH; }
 
@@ -92,21 +95,22 @@ __device__ __forceinline__ void dft30(float2* x) {
 
 template <int Q, bool INV>
 __device__ __forceinline__ void dft_q(float2* x) {
-  if constexpr (Q == 15) Bfly<15, INV>::run(x);
+  if constexpr (Q == 8) Bfly<8, INV>::run(x);
+  else if constexpr (Q == 15) Bfly<15, INV>::run(x);
   else dft30<INV>(x);
 }
 
 // FFT -> mask -> inverse FFT of four_tpw(N) length-N vectors by one warp.
 // load(t, j): element lane + 32 j of transform t; store(t, j, v): output element
 // lane + 32 j of transform t (t and j are compile-time constants in the unrolled calls).
-// T: this warp's F4_BUF float2 of shared memory; tw4, mk4: the CTA's tables.
+// T: this warp's four_buf(N) float2 of shared memory; tw4, mk4: the CTA's tables.
 template <int N, class Load, class Store>
 __device__ __forceinline__ void four_step_mask(float2* T, const float2* tw4, const float2* mk4, int lane, Load& load,
                                                Store& store) {
-  constexpr int Q = four_q(N), TPW = four_tpw(N);
-  static_assert(Q * TPW == F4_COLS, "30 columns per warp");
+  constexpr int Q = four_q(N), TPW = four_tpw(N), COLS = four_cols(N);
+  static_assert(COLS <= 32, "one column per lane");
   {
-    float2 v[F4_COLS];
+    float2 v[COLS];
 #pragma unroll
     for (int t = 0; t < TPW; ++t)
 #pragma unroll
@@ -118,10 +122,10 @@ __device__ __forceinline__ void four_step_mask(float2* T, const float2* tw4, con
       for (int k2 = 1; k2 < Q; ++k2) v[t * Q + k2] = cmul(v[t * Q + k2], tw4[(k2 - 1) * 32 + lane]);
     }
 #pragma unroll
-    for (int c = 0; c < F4_COLS; ++c) T[c * F4_PITCH + lane] = v[c];
+    for (int c = 0; c < COLS; ++c) T[c * F4_PITCH + lane] = v[c];
   }
   __syncwarp();
-  if (lane < F4_COLS) {
+  if (lane < COLS) {
     const int k2 = lane % Q;
     float2* col = T + lane * F4_PITCH;
     float2 w[32];
@@ -136,9 +140,9 @@ __device__ __forceinline__ void four_step_mask(float2* T, const float2* tw4, con
   }
   __syncwarp();
   {
-    float2 v[F4_COLS];
+    float2 v[COLS];
 #pragma unroll
-    for (int c = 0; c < F4_COLS; ++c) v[c] = T[c * F4_PITCH + lane];
+    for (int c = 0; c < COLS; ++c) v[c] = T[c * F4_PITCH + lane];
     __syncwarp();  // T is read: `store` may write into it
 #pragma unroll
     for (int t = 0; t < TPW; ++t) {

@@ -124,7 +124,7 @@ __device__ __forceinline__ void rows_task(const RowArgs& a, int bx, int by, int 
   constexpr bool FOUR = four_step_ok(N);
   constexpr int TWN = FOUR ? four_tw_size(N) : tw_size(N);
   constexpr int MKN = FOUR ? four_mask_size(N) : buf_len(N);
-  constexpr int PITCH = FOUR ? F4_BUF : (buf_len(N) | 1);
+  constexpr int PITCH = FOUR ? four_buf(N) : (buf_len(N) | 1);
   extern __shared__ float2 smem[];
   float2* tw_s = smem;
   float2* mk_s = smem + TWN;
@@ -379,7 +379,7 @@ __device__ __forceinline__ void cols_task(const ColArgs& a, int q, int gh, int b
   constexpr bool FOUR = four_step_ok(N);
   constexpr int TWN = FOUR ? four_tw_size(N) : tw_size(N);
   constexpr int MKN = FOUR ? four_mask_size(N) : buf_len(N);
-  constexpr int PITCH = FOUR ? F4_BUF : (buf_len(N) | 1);
+  constexpr int PITCH = FOUR ? four_buf(N) : (buf_len(N) | 1);
   extern __shared__ float2 smem[];
   float2* tw_s = smem;
   float2* mk_s = smem + TWN;
@@ -698,7 +698,7 @@ cudaError_t raise_dyn_smem(const void* func, size_t bytes) {
 // columns pass with `warps` fine columns per CTA
 size_t cols_smem(pas_pyr_t y, int warps) {
   if (four_step_ok(y->p.N))
-    return sizeof(float2) * ((size_t)four_tw_size(y->p.N) + four_mask_size(y->p.N) + (size_t)warps * F4_BUF);
+    return sizeof(float2) * ((size_t)four_tw_size(y->p.N) + four_mask_size(y->p.N) + (size_t)warps * four_buf(y->p.N));
   return sizeof(float2) * ((size_t)y->kern.tw_n + y->kern.buf_n + (size_t)warps * y->kern.pitch);
 }
 
@@ -709,7 +709,7 @@ static bool split_ok(pas_pyr_t y, int H) { return H == 1 || (!y->frac && H >= 1 
 size_t rows_smem(pas_pyr_t y, int rows, int s_chunk) {
   if (four_step_ok(y->p.N))
     return sizeof(float2) * ((size_t)four_tw_size(y->p.N) + four_mask_size(y->p.N) + (size_t)s_chunk * y->p.Np +
-                             (size_t)rows * (y->p.Np + F4_BUF));
+                             (size_t)rows * (y->p.Np + four_buf(y->p.N)));
   return sizeof(float2) * ((size_t)y->kern.tw_n + y->kern.buf_n + (size_t)s_chunk * y->p.Np +
                            (size_t)rows * (y->p.Np + y->kern.pitch));
 }
@@ -1334,7 +1334,8 @@ static pas_status pyr_create(pas_ctx_t ctx, const pas_pyr_params* pp, const int3
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern.cols, b * 32, y->smem_cols);
   if (e == cudaSuccess)
-    pas::pick_modulation_groups(p.K, y->nd, std::max(1, occ) * std::max(1, ctx->sm_count), &y->kper, &y->G);
+    pas::pick_modulation_groups(p.K, y->nd, std::max(1, occ) * std::max(1, ctx->sm_count), &y->kper, &y->G,
+                                pas::four_step_ok(p.N) ? pas::four_tpw(p.N) : 1);
   if (e != cudaSuccess) {
     pas_pyr_destroy(y);
     return pas::set_error(ctx, PAS_ECUDA, "pas_pyr_create: %s", cudaGetErrorString(e));
@@ -1686,7 +1687,8 @@ extern "C" pas_status pas_pyr_measure_static(const pas_pyr_params* pp, const int
     e = raise_dyn_smem((const void*)kern.cols, y.smem_cols);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern.cols, b * 32, y.smem_cols);
     if (e != cudaSuccess) return set_global_error(PAS_ECUDA, "pas_pyr_measure_static: %s", cudaGetErrorString(e));
-    pick_modulation_groups(p.K, nd, std::max(1, occ) * std::max(1, sms), &y.kper, &y.G);
+    pick_modulation_groups(p.K, nd, std::max(1, occ) * std::max(1, sms), &y.kper, &y.G,
+                           four_step_ok(p.N) ? four_tpw(p.N) : 1);
   }
   y.d_H = reinterpret_cast<float2*>(carve(sizeof(float2) * (size_t)n_s * p.N * p.Np));
   y.d_part = reinterpret_cast<float*>(carve(sizeof(float) * (size_t)y.G * nd * nd));

@@ -108,14 +108,14 @@ inline void quadrant_valid_map(int n_sub, const int32_t* valid, int n_valid, uns
 }
 
 // Modulation grouping of the columns pass: nd x G CTAs, each warp doing
-// kper = ceil(K / G) transforms; G minimises (waves of CTAs) x kper for `slots`
-// resident CTAs on the GPU.
-inline void pick_modulation_groups(int K, int nd, int slots, int* kper_out, int* G_out) {
+// kper = ceil(K / G) transforms in ceil(kper / tpw) engine calls (tpw transforms per
+// call); G minimises (waves of CTAs) x calls for `slots` resident CTAs on the GPU.
+inline void pick_modulation_groups(int K, int nd, int slots, int* kper_out, int* G_out, int tpw = 1) {
   double best = 1e30;
   for (int G = 1; G <= K; ++G) {
     const int kper = (K + G - 1) / G, Gc = (K + kper - 1) / kper;
     const int waves = (nd * Gc + slots - 1) / slots;
-    const double cost = (double)waves * kper + 1e-3 * Gc;
+    const double cost = (double)waves * ((kper + tpw - 1) / tpw) + 1e-3 * Gc;  // engine calls per warp
     if (cost < best) {
       best = cost;
       *kper_out = kper;

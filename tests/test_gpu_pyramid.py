@@ -84,8 +84,11 @@ TINY = [
     tiny_config(Np=80, N=160, n_sub=20, K=16, obs=0.3),
     tiny_config(Np=96, N=192, n_sub=16, K=8),
     tiny_config(Np=120, N=240, n_sub=24, K=10),
-    # the four-step engine's lengths: two transforms per warp at N = 480 (odd K leaves a
-    # warp's last pair half empty), one at N = 960
+    # the four-step engine's lengths: four transforms per warp at N = 256 (K = 7 and 2
+    # leave a call partly empty), two at N = 480 (odd K leaves a warp's last pair half
+    # empty), one at N = 960
+    tiny_config(Np=128, N=256, n_sub=16, K=7, mod_radius=3.0),
+    tiny_config(Np=128, N=256, n_sub=32, K=2),
     tiny_config(Np=240, N=480, n_sub=30, K=5, mod_radius=3.0),
     tiny_config(Np=480, N=960, n_sub=96, K=3, mod_radius=4.0),
 ]
@@ -261,6 +264,37 @@ def test_rows_pass_geometry_leaves_the_frame_bit_identical(env, name, rows):
             out.append((fr.cpu().numpy(), sl.cpu().numpy()))
         for fr, sl in out[1:]:
             assert np.array_equal(fr, out[0][0]) and np.array_equal(sl, out[0][1])
+    finally:
+        pas.pas_pyr_destroy(pyr)
+
+
+def test_four_step_256_geometry_leaves_the_frame_bit_identical(env):
+    """N = 256 (four transforms per engine call): rows-pass geometries whose sin chunks
+    leave calls partly empty give the same frame and slopes bit for bit, and every
+    columns-pass grouping (kper 12, 4, 3, 1) matches the oracle."""
+    from oracle import optics as op
+    torch, pas, ctx = env
+    cfg = tiny_config(Np=128, N=256, n_sub=16, K=12, mod_radius=3.0)
+    opd32 = random_opd_nm(cfg.Np, 200.0, seed=29).astype(np.float32)
+    opd = torch.as_tensor(opd32).cuda()
+    valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
+    fr_o, sl_o = oracle_measure(cfg, opd32, valid)
+    pyr = pas.pas_pyr_create(ctx, cfg.Np, cfg.N, cfg.K, cfg.n_sub, cfg.mod_radius, cfg.wavelength_nm, cfg.obs)
+    try:
+        nv = pas.pas_pyr_n_valid(pyr)
+        assert nv == valid.size
+        out = {}
+        for r, chunks, groups in [(2, 1, 3), (4, 7, 3), (8, 3, 3), (16, 2, 3), (4, 2, 1), (4, 2, 4), (4, 2, 12)]:
+            pas.pas_pyr_set_tuning(pyr, ctx, r, chunks, groups, 1)
+            fr = torch.zeros(cfg.n_det, cfg.n_det, device="cuda")
+            sl = torch.zeros(2 * nv, device="cuda")
+            pas.pas_pyr_measure(pyr, ctx, opd, fr, sl)
+            torch.cuda.synchronize()
+            out.setdefault(groups, []).append((fr.cpu().numpy(), sl.cpu().numpy()))
+        for fr, sl in out[3][1:]:
+            assert np.array_equal(fr, out[3][0][0]) and np.array_equal(sl, out[3][0][1])
+        for runs in out.values():
+            check(cfg, runs[0][0].astype(np.float64), runs[0][1].astype(np.float64), fr_o, sl_o)
     finally:
         pas.pas_pyr_destroy(pyr)
 
