@@ -426,8 +426,9 @@ const char* pas_loop_kernel_name(int32_t idx);
  * step as a parallel branch (the paper runs its Monte-Carlo cases as separate
  * simulations; this is the GPU-side batching of them). The loops keep their own
  * state, buffers and statistics (pas_loop_step(loop, 0, &stats) reads them) and
- * must not be stepped, re-configured (pas_loop_set_mlp, pas_loop_set_integration) or destroyed while the
- * batch exists. Creation synchronises every loop's stream and captures the graph
+ * must not be stepped or destroyed while the batch exists; re-configuring one
+ * (pas_loop_set_mlp, pas_loop_set_integration, pas_loop_attach_camera) returns PAS_ESTATE
+ * until every batch holding it is destroyed. Creation synchronises every loop's stream and captures the graph
  * on `ctx`'s private stream; steps run on `ctx`'s stream. Two loops of a batch may
  * share atmosphere, DM and reconstructor objects but not a sensor object (PAS_EINVAL).
  * Loops that share one DM object (realisations of one system) and whose sources are at

@@ -25,6 +25,7 @@ struct pas_loop_s {
   pas_dm_t dm = nullptr;
   pas_mlp_t mlp = nullptr;  // learned reconstructor in place of rec (optional)
   int delay = 1, hist = 1, n_m = 0, n_slopes = 0, nd = 0, Np = 0, n_tiles = 0;
+  int batches = 0;          // live batches whose captured graph holds this loop's step
   int n_int = 1;            // detector steps per frame (pas_loop_set_integration)
   int taps = PAS_TAPS_AUTO;         // the atmosphere's tap staging and wait bound at creation
   uint32_t tap_wait_limit = 0;
@@ -356,8 +357,18 @@ static void loop_drop_graphs(pas_loop_t L) {
   L->prof_graph = nullptr;
 }
 
+// A batch captured its loops' steps at creation: re-configuring a member would leave
+// the batch's graph stepping the old configuration (or reading a detached camera's
+// buffers).
+#define PAS_LOOP_NOT_BATCHED(L, what)                                                                 \
+  do {                                                                                              \
+    if ((L)->batches > 0)                                                                           \
+      return pas::set_error((L)->ctx, PAS_ESTATE, what ": the loop belongs to a batch (destroy it first)"); \
+  } while (0)
+
 pas_status pas_loop_set_integration(pas_loop_t L, int32_t n_int) {
   if (!L) return pas::set_global_error(PAS_EINVAL, "pas_loop_set_integration: NULL loop");
+  PAS_LOOP_NOT_BATCHED(L, "pas_loop_set_integration");
   PAS_CHECK_ARG(L->ctx, n_int >= 1 && n_int <= (1 << 20), "pas_loop_set_integration: 1 <= n_int <= 2^20");
   if (n_int > 1 && L->mlp)
     return pas::set_error(L->ctx, PAS_ESTATE, "pas_loop_set_integration: a loop with the linear reconstructor only");
@@ -375,6 +386,7 @@ pas_status pas_loop_set_integration(pas_loop_t L, int32_t n_int) {
 pas_status pas_loop_attach_camera(pas_loop_t L, pas_psf_t psf, float* d_psf, double* d_sr, int32_t sr_len,
                                   int64_t start_step) {
   if (!L) return pas::set_global_error(PAS_EINVAL, "pas_loop_attach_camera: NULL loop");
+  PAS_LOOP_NOT_BATCHED(L, "pas_loop_attach_camera");
   if (psf) {
     PAS_CHECK_ARG(L->ctx, d_psf != nullptr && sr_len >= 1 && start_step >= 0,
                   "pas_loop_attach_camera: a PSF buffer, sr_len >= 1, start_step >= 0");
@@ -397,6 +409,7 @@ pas_status pas_loop_attach_camera(pas_loop_t L, pas_psf_t psf, float* d_psf, dou
 
 pas_status pas_loop_set_mlp(pas_loop_t L, pas_mlp_t m) {
   if (!L) return pas::set_global_error(PAS_EINVAL, "pas_loop_set_mlp: NULL loop");
+  PAS_LOOP_NOT_BATCHED(L, "pas_loop_set_mlp");
   if (m)
     PAS_CHECK_ARG(L->ctx, m->sz[0] == L->n_slopes && m->sz[m->L] == L->n_m,
                   "pas_loop_set_mlp: network sizes must be [2 n_valid, ..., n_modes]");
@@ -484,10 +497,13 @@ struct pas_batch_s {
   std::vector<pas::ResBatch*> res_batches;
   std::vector<cudaStream_t> rstreams;
   std::vector<cudaEvent_t> rdone;
+  bool registered = false;  // the loops count this batch (pas_loop_s::batches)
 };
 
 void pas_batch_destroy(pas_batch_t b) {
   if (!b) return;
+  if (b->registered)
+    for (pas_loop_t L : b->loops) --L->batches;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (cudaStream_t s : b->streams)
@@ -768,6 +784,8 @@ pas_status pas_batch_create_ex(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops
     if (st != PAS_OK) return st;
     return pas::set_error(ctx, PAS_ECUDA, "pas_batch_create capture: %s", cudaGetErrorString(e));
   }
+  for (pas_loop_t L : b->loops) ++L->batches;
+  b->registered = true;
   *out = b;
   return PAS_OK;
 }

@@ -78,6 +78,35 @@ def test_batch_rejects_duplicates_and_null():
         s.close()
 
 
+def test_a_loop_held_by_a_batch_cannot_be_reconfigured():
+    """The batch's graph holds its loops' steps as captured: re-configuring a member
+    (integrating detector, camera, network) is refused until the batch is gone."""
+    import torch
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    s = SCAOSystem(tiny_config(Np=48, N=96, n_sub=8, K=8, n_modes=20, mod_radius=2.0, S=128), autotune=False,
+                   wfe_history=16)
+    psf = pas.pas_psf_create(s.ctx, 48, 2, 1650.0, s.cfg.obs)
+    try:
+        acc = torch.zeros(96, 96, device="cuda")
+        b1 = pas.pas_batch_create(s.ctx, [s.loop])
+        b2 = pas.pas_batch_create(s.ctx, [s.loop])
+        for b in (b1, b2):
+            with pytest.raises(pas.PasError, match="batch"):
+                pas.pas_loop_set_integration(s.loop, s.ctx, 2)
+            with pytest.raises(pas.PasError, match="batch"):
+                pas.pas_loop_attach_camera(s.loop, s.ctx, psf, acc)
+            pas.pas_batch_destroy(b)
+        pas.pas_loop_set_integration(s.loop, s.ctx, 2)
+        pas.pas_loop_attach_camera(s.loop, s.ctx, psf, acc)
+        pas.pas_loop_step(s.loop, s.ctx, 3)
+        torch.cuda.synchronize()
+        pas.pas_loop_attach_camera(s.loop, s.ctx, None)
+    finally:
+        pas.pas_psf_destroy(psf)
+        s.close()
+
+
 def test_loops_sharing_a_bf16_reconstructor_get_one_tensor_core_product():
     """Five realisations of the 64 px workload share one bf16 reconstructor object: the
     batch reconstructs them with one tensor-core product (R S^T, float32 accumulation)
