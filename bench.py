@@ -324,20 +324,22 @@ def bench_lbt(args, timed, barrier, flush, world, dist, peaks, no_mlp=False):
     return r, mlp_info
 
 
-def bench_equal_wfe(timed, n_timed=300):
-    """North-star comparison where the loop settles: the LBT-class optics (240 px, 3
-    layers, magnitude-10 noise) with 200 KL modes (with 400 the linear loop drifts). The
-    FP32 loop and the loop with a bfloat16 DM basis and reconstructor run the
-    workload's 2000 steps from the same start; reported: their steps/s (L2 flushed
-    between timed steps) and mean residual WFE after a 20 % burn-in."""
+def bench_equal_wfe(timed, n_timed=300, workload="scao_lbt_240px", n_modes=200):
+    """North-star comparison where the loop settles: by default the LBT-class optics
+    (240 px, 3 layers, magnitude-10 noise) with 200 KL modes (with 400 the linear loop
+    drifts); also the ELT-scale optics (480 px, 6 layers, noiseless) with 1000 modes
+    (with 4000 it drifts). The FP32 loop and the loop with a bfloat16 DM basis and
+    reconstructor run the workload's steps from the same start; reported: their steps/s
+    (L2 flushed between timed steps) and mean residual WFE after a 20 % burn-in."""
     import numpy as np
     from paper_1607_07624_gb300 import pas
     from paper_1607_07624_gb300.system import SCAOSystem
     from synth import get_config
     from synth.configs import with_
-    cfg = with_(get_config("scao_lbt_240px"), n_modes=200)
+    cfg = with_(get_config(workload), n_modes=n_modes)
     n = cfg.n_steps
-    out = {"workload": f"{cfg.name} with {cfg.n_modes} KL modes, {n} steps, magnitude {cfg.magnitude} noise"}
+    noise = f"magnitude {cfg.magnitude} noise" if cfg.magnitude is not None else "noiseless"
+    out = {"workload": f"{cfg.name} with {cfg.n_modes} {cfg.basis} modes, {n} steps, {noise}"}
     a = SCAOSystem(cfg, wfe_history=n)
     try:
         b = SCAOSystem(cfg, basis=a.basis, R=a.R, recon_precision=pas.PAS_BF16, dm_precision=pas.PAS_BF16,
@@ -1032,10 +1034,12 @@ def main():
                                                           no_mlp=args.no_mlp)
         except Exception as e:
             extra["scao_lbt_240px"] = {"error": str(e)}
-        try:
-            extra["equal_wfe_bf16_vs_fp32"] = bench_equal_wfe(timed)
-        except Exception as e:
-            extra["equal_wfe_bf16_vs_fp32"] = {"error": str(e)}
+        for key, kw in (("equal_wfe_bf16_vs_fp32", {}),
+                        ("equal_wfe_bf16_vs_fp32_elt", {"workload": "scao_elt_480px", "n_modes": 1000})):
+            try:
+                extra[key] = bench_equal_wfe(timed, **kw)
+            except Exception as e:
+                extra[key] = {"error": str(e)}
         try:
             extra["other_workloads"] = bench_other_workloads(timed, peaks)
         except Exception as e:
