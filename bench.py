@@ -542,7 +542,9 @@ def bench_batch(timed, n_loops=64, n_steps=100):
     each; DM object, reconstructor matrix and launch geometry shared, so the batch
     computes their residuals in one basis pass) stepped by one graph launch per step,
     as graph branches and with the persistent pyramid launch. Returns the whole batch's
-    loop-steps/s for the faster, both modes beside it."""
+    loop-steps/s for the faster, both modes beside it. Also the batched BF16 loop: the
+    same realisations sharing one bf16 reconstructor object (one tensor-core product per
+    step for all of them), its rate and its residual WFE against the FP32 batch's."""
     import numpy as np
     from paper_1607_07624_gb300 import pas
     from paper_1607_07624_gb300.system import SCAOSystem
@@ -572,14 +574,54 @@ def bench_batch(timed, n_loops=64, n_steps=100):
             pas.pas_batch_destroy(batch)
             batch = None
         best = max(modes, key=lambda k: modes[k]["loop_steps_per_s"])
-        return {"workload": f"{n_loops} realisations of {cfg.name} (own screens each)", "mode": best, **modes[best],
-                "graph_launches_per_step": 1, "modes": modes,
-                "wfe_nm_mean_over_realisations": float(wfe[:, n_steps // 5:].mean())}
+        out = {"workload": f"{n_loops} realisations of {cfg.name} (own screens each)", "mode": best, **modes[best],
+               "graph_launches_per_step": 1, "modes": modes,
+               "wfe_nm_mean_over_realisations": float(wfe[:, n_steps // 5:].mean())}
+        out["bf16_shared_reconstructor"] = _bench_batch_bf16(timed, cfg, systems, n_steps, wfe)
+        return out
     finally:
         if batch is not None:
             pas.pas_batch_destroy(batch)
         for s in systems[1:] + systems[:1]:
             s.close()
+
+
+def _bench_batch_bf16(timed, cfg, systems, n_steps, wfe_fp32):
+    """The Monte-Carlo batch's realisations again (same seeds, basis, DM object) with one
+    shared bf16 reconstructor object: graph branches plus one tensor-core product per
+    step. Reports loop-steps/s and the WFE against the FP32 batch (mean after a 20 %
+    burn-in, over realisations, and the largest per-realisation difference)."""
+    import numpy as np
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    from synth.configs import with_
+    first = systems[0]
+    rec = pas.pas_recon_create(first.ctx, first.R, pas.PAS_BF16)
+    twins, batch = [], None
+    try:
+        for i, s in enumerate(systems):
+            twins.append(SCAOSystem(with_(cfg, seed=cfg.seed + 7919 * i) if i else cfg, basis=first.basis, R=first.R,
+                                    dm=first.dm, rec=rec, autotune=tuple(first.tuning), wfe_history=s.wfe_history))
+        batch = pas.pas_batch_create(first.ctx, [t.loop for t in twins])
+        pas.pas_batch_step(batch, first.ctx, 5)
+        for t in twins:
+            t.set_state(0, np.zeros((t.delay, t.n_modes), np.float32))
+        ms = timed(lambda: pas.pas_batch_step(batch, first.ctx, 1), n_steps)
+        pas.pas_batch_check(batch, first.ctx)
+        w = np.array([t.wfe_nm(n_steps) for t in twins])
+        b0 = n_steps // 5
+        per = w[:, b0:].mean(axis=1) - wfe_fp32[:, b0:].mean(axis=1)
+        return {"loop_steps_per_s": len(twins) * n_steps / (ms * 1e-3),
+                "kernels_per_step": pas.pas_batch_kernels_per_step(batch),
+                "tensor_core_reconstruction_groups": pas.pas_batch_n_groups(batch),
+                "wfe_nm_mean_bf16": float(w[:, b0:].mean()), "wfe_nm_mean_fp32": float(wfe_fp32[:, b0:].mean()),
+                "wfe_diff_nm_max_over_realisations": float(np.abs(per).max())}
+    finally:
+        if batch is not None:
+            pas.pas_batch_destroy(batch)
+        for t in twins:
+            t.close()
+        pas.pas_recon_destroy(rec)
 
 
 def bench_batched_workload(timed, n_steps=30):
