@@ -42,26 +42,51 @@ __global__ void advance_steps_kernel(long long* const* step, int B) {
   if (b < B) *step[b] += 1;
 }
 
-// Epilogue: rows are modes, columns are loops.
+// Epilogue: rows are modes, columns are loops. The per-loop pointers, step counters
+// and gains are read-only during the product: each group of 4 columns loads them level
+// by level (pointers, then the values they point to), so a thread waits 3 memory
+// latencies per 4 columns instead of one per dependent load of every column.
 struct EpiBatchIntegrate {
   BatchRecState st;
   const float* scale;  // [n_m] per-row scale of the bf16 reconstructor
   int n_m, B;
   __device__ void store(int m, int col, const float (&v)[16]) const {
-    const float sc = scale[m];
+    constexpr int CH = 4;
+    const float sc = __ldg(scale + m);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int b = col + j;
-      if (b < B) {
-        const float dm = v[j] * sc;
-        const long long t = *st.step[b];
-        const int d = st.delay[b];
-        float* ring = st.ring[b];
-        const float prev = ring[(size_t)((t - 1 + d) % d) * n_m + m];
-        const float c = fmaf(st.gain[b][m], dm, prev);
-        ring[(size_t)(t % d) * n_m + m] = c;
-        st.cmd[b][m] = c;
-        st.dmodes[b][m] = dm;
+    for (int j0 = 0; j0 < 16; j0 += CH) {
+      float* ring[CH];
+      const float* gain[CH];
+      const long long* stp[CH];
+      int d[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int b = min(col + j0 + u, B - 1);
+        ring[u] = st.ring[b];
+        gain[u] = st.gain[b];
+        stp[u] = st.step[b];
+        d[u] = __ldg(st.delay + b);
+      }
+      long long t[CH];
+      float g[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        t[u] = __ldg(stp[u]);
+        g[u] = __ldg(gain[u] + m);
+      }
+      float prev[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) prev[u] = ring[u][(size_t)((t[u] - 1 + d[u]) % d[u]) * n_m + m];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int b = col + j0 + u;
+        if (b < B) {
+          const float dm = v[j0 + u] * sc;
+          const float c = fmaf(g[u], dm, prev[u]);
+          ring[u][(size_t)(t[u] % d[u]) * n_m + m] = c;
+          st.cmd[b][m] = c;
+          st.dmodes[b][m] = dm;
+        }
       }
     }
   }
