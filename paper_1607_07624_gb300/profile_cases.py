@@ -7,6 +7,7 @@ wavefront error of a random system means nothing.
     python -m paper_1607_07624_gb300.profile_cases scao_8m_64px --batch 16 --persistent
     python -m paper_1607_07624_gb300.profile_cases gemm --gemm 8192 --steps 3
     python -m paper_1607_07624_gb300.profile_cases psf --psf 240,8 --steps 4
+    python -m paper_1607_07624_gb300.profile_cases mlp --mlp 1424,1024,1024,1024,400 --steps 20
 
 Kernel launches: with --batch 0 every step launches the loop's kernels once, in step order
 (residual, rows pass, columns pass, slopes, reconstructor), so ``ncu -k regex:<kernel> -s
@@ -74,16 +75,48 @@ def _psf(spec, steps, seed):
         pas.pas_ctx_destroy(ctx)
 
 
+def _mlp(spec, batch, steps, seed):
+    """--steps Adam steps (one captured graph replay each, after 5 that capture it) of the
+    learned reconstructor with layer sizes `spec` on a seeded normal data set of 65536
+    pairs, batch `batch`."""
+    from .learned import MLPReconstructor
+    sizes = [int(x) for x in spec.split(",")]
+    ctx = pas.pas_ctx_create(torch.cuda.current_stream())
+    mlp = None
+    try:
+        mlp = MLPReconstructor(ctx, sizes, max_batch=batch, seed=seed)
+        gen = torch.Generator(device="cuda").manual_seed(seed)
+        n_data = 65536
+        S = torch.randn(n_data, sizes[0], device="cuda", generator=gen)
+        Y = torch.randn(n_data, sizes[-1], device="cuda", generator=gen)
+        idx = torch.randint(0, n_data, (max(steps, 5) * batch,), device="cuda", generator=gen, dtype=torch.int32)
+        lr = torch.full((max(steps, 5),), 1e-4, device="cuda")
+        loss = torch.zeros(max(steps, 5), device="cuda")
+        pas.pas_mlp_train(mlp.h, ctx, S, Y, n_data, batch, idx, lr, 5, loss)
+        pas.pas_mlp_train(mlp.h, ctx, S, Y, n_data, batch, idx, lr, steps, loss)
+        torch.cuda.synchronize()
+        pas.pas_mlp_check(mlp.h, ctx)
+        print(f"mlp {sizes} batch {batch} x {steps} steps: last loss {float(loss[steps - 1].item()):.4f}")
+        return 0
+    finally:
+        if mlp is not None:
+            mlp.close()
+        pas.pas_ctx_destroy(ctx)
+
+
 def main(argv=None):
     from synth import get_config
     from synth.configs import with_
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("workload", help="scao_8m_64px, scao_lbt_240px or scao_elt_480px (or gemm with --gemm, "
-                    "psf with --psf)")
+                    "psf with --psf, mlp with --mlp)")
     ap.add_argument("--gemm", type=int, default=0, help="instead of a loop: --steps tensor-core products "
                     "C = A B^T of n x n bf16 matrices (seeded normal entries), float32 C")
     ap.add_argument("--psf", default="", help="instead of a loop: --steps integrated frames of the PSF camera "
                     "for pupil,padding (e.g. 240,8)")
+    ap.add_argument("--mlp", default="", help="instead of a loop: --steps training steps of the learned "
+                    "reconstructor with these layer sizes (e.g. 1424,1024,1024,1024,400)")
+    ap.add_argument("--batch-size", type=int, default=1024, help="training batch of --mlp")
     ap.add_argument("--basis", default="fp32", choices=sorted(_PREC))
     ap.add_argument("--recon", default="fp32", choices=sorted(_PREC))
     ap.add_argument("--taps", default="auto", choices=sorted(_TAPS), help="the residual's tap staging")
@@ -100,6 +133,8 @@ def main(argv=None):
         return _gemm(a.gemm, a.steps, a.seed)
     if a.psf:
         return _psf(a.psf, a.steps, a.seed)
+    if a.mlp:
+        return _mlp(a.mlp, a.batch_size, a.steps, a.seed)
     cfg = get_config(a.workload)
     tuning = tuple(int(x) for x in a.tuning.split(",")) if a.tuning else False
     systems, loops, batch = [], [], None
