@@ -325,7 +325,7 @@ def bench_lbt(args, timed, barrier, flush, world, dist, peaks, no_mlp=False):
 
 
 def bench_equal_wfe(timed, n_timed=300, workload="scao_lbt_240px", n_modes=200):
-    """North-star comparison where the loop settles: by default the LBT-class optics
+    """BF16 against FP32 at equal residual WFE where the loop settles: by default the LBT-class optics
     (240 px, 3 layers, magnitude-10 noise) with 200 KL modes (with 400 the linear loop
     drifts); also the ELT-scale optics (480 px, 6 layers, noiseless) with 1000 modes
     (with 4000 it drifts). The FP32 loop and the loop with a bfloat16 DM basis and
