@@ -107,24 +107,26 @@ def test_bad_arguments_are_rejected(env):
         pas.pas_psf_destroy(h)
 
 
-def test_camera_in_the_closed_loop_matches_oracle(env):
+@pytest.mark.parametrize("name,nd", [("scao_8m_64px", 4), ("scao_lbt_240px", 3)])
+def test_camera_in_the_closed_loop_matches_oracle(env, name, nd):
     """SCAOSystem.attach_camera: from the start step on, each step's PSF of the loop's
     residual is integrated and its Strehl ratio recorded (against the oracle on the
-    same float32 residuals, copied after every step)."""
+    same float32 residuals, copied after every step). At 240 px the camera runs the
+    paired transforms (odd padding: a warp's second residue empty)."""
     torch, pas, ctx = env
     from oracle import psf as ps
     from paper_1607_07624_gb300.system import SCAOSystem
-    cfg = get_config("scao_8m_64px")
+    cfg = get_config(name)
     s = SCAOSystem(cfg, wfe_history=64)
     try:
-        N = s.attach_camera(nd=4, wavelength_nm=LAM, start_step=2)
-        assert N == 4 * cfg.Np
+        N = s.attach_camera(nd=nd, wavelength_nm=LAM, start_step=2)
+        assert N == nd * cfg.Np
         opds = []
         for _ in range(6):
             s.step(1)
             torch.cuda.synchronize()
             opds.append(s.loop_opd.cpu().numpy().astype(np.float64))
-        ref = ps.integrated_psf(opds, LAM, cfg.obs, 4, start=2)
+        ref = ps.integrated_psf(opds, LAM, cfg.obs, nd, start=2)
         P = s.int_psf.cpu().numpy().astype(np.float64)
         assert np.max(np.abs(P - ref)) <= 1e-5 * ref.max()
         sr = s.sr.cpu().numpy()
@@ -137,7 +139,8 @@ def test_camera_in_the_closed_loop_matches_oracle(env):
         s.close()
 
 
-def test_camera_inside_the_step_graph_equals_the_camera_called_per_step(env):
+@pytest.mark.parametrize("name,nd", [("scao_8m_64px", 4), ("scao_lbt_240px", 2)])
+def test_camera_inside_the_step_graph_equals_the_camera_called_per_step(env, name, nd):
     """The camera inside the loop's step graph (its passes beside the sensor, the step
     counter read on the device) gives the integrated PSF and the Strehl ring of the camera
     called after every step, bit for bit, and the loop's own WFE is unchanged by it; a
@@ -145,12 +148,12 @@ def test_camera_inside_the_step_graph_equals_the_camera_called_per_step(env):
     detaches cleanly."""
     torch, pas, ctx = env
     from paper_1607_07624_gb300.system import SCAOSystem
-    cfg = get_config("scao_8m_64px")
+    cfg = get_config(name)
     a = SCAOSystem(cfg, wfe_history=64, autotune=False)
     b = SCAOSystem(cfg, wfe_history=64, autotune=False, basis=a.basis, R=a.R)
     try:
-        a.attach_camera(nd=4, wavelength_nm=LAM, start_step=3, in_graph=True)
-        b.attach_camera(nd=4, wavelength_nm=LAM, start_step=3, in_graph=False)
+        a.attach_camera(nd=nd, wavelength_nm=LAM, start_step=3, in_graph=True)
+        b.attach_camera(nd=nd, wavelength_nm=LAM, start_step=3, in_graph=False)
         assert a._cam_in_graph and not b._cam_in_graph
         a.step(12)
         b.step(12)
