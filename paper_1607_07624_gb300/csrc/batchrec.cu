@@ -12,12 +12,14 @@
 
 #include "batchrec.cuh"
 #include "gemm.cuh"
+#include "mlp.cuh"
 
 namespace pas {
 
 struct BatchRecGroup {
   pas_ctx_t ctx = nullptr;
   pas_recon_t rec = nullptr;
+  pas_mlp_t mlp = nullptr;       // a shared network instead of rec: one batched forward
   int B = 0;
   __nv_bfloat16* d_S = nullptr;  // [B][n_s_pad]
   void** d_ptrs = nullptr;       // the pointer arrays of BatchRecState, contiguous
@@ -40,6 +42,30 @@ __global__ void gather_slopes_bf16_kernel(const float* const* slopes, int n_s, i
 __global__ void advance_steps_kernel(long long* const* step, int B) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < B) *step[b] += 1;
+}
+
+// A shared network's outputs out[b][m] (its last layer, float32) as each loop's modal
+// update: the integrator of the single-vector chain's last layer, a non-finite output
+// replaced by 0 with fault bit 0 set.
+__global__ void mlp_batch_integrate_kernel(const float* out, int ldo, int n_m, int B, BatchRecState st,
+                                           unsigned* fault) {
+  const size_t tot = (size_t)B * n_m;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(t / n_m), m = (int)(t - (size_t)b * n_m);
+    float z = out[(size_t)b * ldo + m];
+    if (!isfinite(z)) {
+      atomicOr(fault, 1u);
+      z = 0.f;
+    }
+    const long long ts = *st.step[b];
+    const int d = st.delay[b];
+    float* ring = st.ring[b];
+    const float prev = ring[(size_t)((ts - 1 + d) % d) * n_m + m];
+    const float c = fmaf(st.gain[b][m], z, prev);
+    ring[(size_t)(ts % d) * n_m + m] = c;
+    st.cmd[b][m] = c;
+    st.dmodes[b][m] = z;
+  }
 }
 
 // Epilogue: rows are modes, columns are loops. The per-loop pointers, step counters
@@ -94,24 +120,15 @@ struct EpiBatchIntegrate {
 
 static int pick_bn(int B) { return B <= 16 ? 16 : B <= 32 ? 32 : B <= 64 ? 64 : 128; }
 
-pas_status batch_rec_create(pas_ctx_t ctx, pas_recon_t rec, int B, const float* const* slopes, float* const* ring,
-                            const float* const* gain, float* const* cmd, float* const* dmodes,
-                            long long* const* step, const int* delay, BatchRecGroup** out) {
-  *out = nullptr;
-  PAS_CHECK_ARG(ctx, rec && rec->prec == PAS_BF16 && rec->d_Rb, "batched reconstruction: a bf16 reconstructor");
-  PAS_CHECK_ARG(ctx, B >= 1 && B <= 128, "batched reconstruction: 1 to 128 loops per group");
-  BatchRecGroup* g = new BatchRecGroup();
-  g->ctx = ctx;
-  g->rec = rec;
-  g->B = B;
-  pas_status s = dev_alloc(ctx, (void**)&g->d_S, sizeof(__nv_bfloat16) * (size_t)B * rec->n_s_pad);
-  if (s == PAS_OK) s = dev_alloc(ctx, (void**)&g->d_ptrs, sizeof(void*) * 6 * (size_t)B);
-  if (s == PAS_OK) s = dev_alloc(ctx, (void**)&g->d_delay, sizeof(int) * B);
-  if (s == PAS_OK) s = dev_alloc(ctx, (void**)&g->d_err, sizeof(unsigned int));
-  if (s != PAS_OK) {
-    batch_rec_destroy(g);
-    return s;
-  }
+// The group's per-loop pointer arrays on the device (g->st).
+static pas_status group_pointers(BatchRecGroup* g, const float* const* slopes, float* const* ring,
+                                 const float* const* gain, float* const* cmd, float* const* dmodes,
+                                 long long* const* step, const int* delay) {
+  const int B = g->B;
+  pas_status s = dev_alloc(g->ctx, (void**)&g->d_ptrs, sizeof(void*) * 6 * (size_t)B);
+  if (s == PAS_OK) s = dev_alloc(g->ctx, (void**)&g->d_delay, sizeof(int) * B);
+  if (s == PAS_OK) s = dev_alloc(g->ctx, (void**)&g->d_err, sizeof(unsigned int));
+  if (s != PAS_OK) return s;
   std::vector<void*> h(6 * (size_t)B);
   for (int b = 0; b < B; ++b) {
     h[0 * B + b] = const_cast<float*>(slopes[b]);
@@ -124,10 +141,7 @@ pas_status batch_rec_create(pas_ctx_t ctx, pas_recon_t rec, int B, const float* 
   cudaError_t e = cudaMemcpy(g->d_ptrs, h.data(), sizeof(void*) * h.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_delay, delay, sizeof(int) * B, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(g->d_err, 0, sizeof(unsigned int));
-  if (e != cudaSuccess) {
-    batch_rec_destroy(g);
-    return set_error(ctx, PAS_ECUDA, "batched reconstruction: %s", cudaGetErrorString(e));
-  }
+  if (e != cudaSuccess) return set_error(g->ctx, PAS_ECUDA, "batched reconstruction: %s", cudaGetErrorString(e));
   g->st.slopes = reinterpret_cast<const float* const*>(g->d_ptrs);
   g->st.ring = reinterpret_cast<float* const*>(g->d_ptrs + (size_t)B);
   g->st.gain = reinterpret_cast<const float* const*>(g->d_ptrs + 2 * (size_t)B);
@@ -135,6 +149,45 @@ pas_status batch_rec_create(pas_ctx_t ctx, pas_recon_t rec, int B, const float* 
   g->st.dmodes = reinterpret_cast<float* const*>(g->d_ptrs + 4 * (size_t)B);
   g->st.step = reinterpret_cast<long long* const*>(g->d_ptrs + 5 * (size_t)B);
   g->st.delay = g->d_delay;
+  return PAS_OK;
+}
+
+pas_status batch_mlp_create(pas_ctx_t ctx, pas_mlp_t mlp, int B, const float* const* slopes, float* const* ring,
+                            const float* const* gain, float* const* cmd, float* const* dmodes,
+                            long long* const* step, const int* delay, BatchRecGroup** out) {
+  *out = nullptr;
+  PAS_CHECK_ARG(ctx, mlp != nullptr, "batched inference: a network");
+  PAS_CHECK_ARG(ctx, B >= 1 && B <= std::min(128, mlp->max_batch),
+                "batched inference: 1 to min(128, the network's batch size) loops per group");
+  BatchRecGroup* g = new BatchRecGroup();
+  g->ctx = ctx;
+  g->mlp = mlp;
+  g->B = B;
+  pas_status s = group_pointers(g, slopes, ring, gain, cmd, dmodes, step, delay);
+  if (s != PAS_OK) {
+    batch_rec_destroy(g);
+    return s;
+  }
+  *out = g;
+  return PAS_OK;
+}
+
+pas_status batch_rec_create(pas_ctx_t ctx, pas_recon_t rec, int B, const float* const* slopes, float* const* ring,
+                            const float* const* gain, float* const* cmd, float* const* dmodes,
+                            long long* const* step, const int* delay, BatchRecGroup** out) {
+  *out = nullptr;
+  PAS_CHECK_ARG(ctx, rec && rec->prec == PAS_BF16 && rec->d_Rb, "batched reconstruction: a bf16 reconstructor");
+  PAS_CHECK_ARG(ctx, B >= 1 && B <= 128, "batched reconstruction: 1 to 128 loops per group");
+  BatchRecGroup* g = new BatchRecGroup();
+  g->ctx = ctx;
+  g->rec = rec;
+  g->B = B;
+  pas_status s = dev_alloc(ctx, (void**)&g->d_S, sizeof(__nv_bfloat16) * (size_t)B * rec->n_s_pad);
+  if (s == PAS_OK) s = group_pointers(g, slopes, ring, gain, cmd, dmodes, step, delay);
+  if (s != PAS_OK) {
+    batch_rec_destroy(g);
+    return s;
+  }
   // C[n_m][B] = R[n_m][n_s_pad] * S[B][n_s_pad]^T (both K-major, zero row padding)
   const int K = rec->n_s_pad;
   g->op.M = rec->n_modes;
@@ -151,6 +204,18 @@ pas_status batch_rec_create(pas_ctx_t ctx, pas_recon_t rec, int B, const float* 
 }
 
 pas_status batch_rec_launch(BatchRecGroup* g, cudaStream_t st) {
+  if (g->mlp) {
+    pas_mlp_t m = g->mlp;
+    pas_status s = mlp_batch_forward(m, g->B, g->st.slopes, st);
+    if (s != PAS_OK) return s;
+    const int n_m = m->sz[m->L];
+    const int blocks = (int)std::min<size_t>(1024, ((size_t)g->B * n_m + 255) / 256);
+    mlp_batch_integrate_kernel<<<blocks, 256, 0, st>>>(m->d_out, m->ld[m->L], n_m, g->B, g->st, m->d_fault);
+    advance_steps_kernel<<<(g->B + 127) / 128, 128, 0, st>>>(g->st.step, g->B);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(g->ctx, PAS_ECUDA, "batched inference launch: %s", cudaGetErrorString(e));
+    return PAS_OK;
+  }
   const int n_s = g->rec->n_slopes, K = g->rec->n_s_pad;
   const int blocks = (int)std::min<size_t>(1024, ((size_t)g->B * K + 255) / 256);
   gather_slopes_bf16_kernel<<<blocks, 256, 0, st>>>(g->st.slopes, n_s, K, g->B, g->d_S);
@@ -168,7 +233,9 @@ pas_status batch_rec_launch(BatchRecGroup* g, cudaStream_t st) {
   return PAS_OK;
 }
 
-unsigned int* batch_rec_err(BatchRecGroup* g) { return g->d_err; }
+unsigned int* batch_rec_err(BatchRecGroup* g) { return g->mlp ? g->mlp->d_err : g->d_err; }
+
+int batch_rec_kernels(BatchRecGroup* g) { return g->mlp ? g->mlp->L + 3 : 3; }
 
 void batch_rec_destroy(BatchRecGroup* g) {
   if (!g) return;

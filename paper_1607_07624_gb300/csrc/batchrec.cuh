@@ -28,11 +28,22 @@ pas_status batch_rec_create(pas_ctx_t ctx, pas_recon_t rec, int B, const float* 
                             float* const* ring, const float* const* gain, float* const* cmd,
                             float* const* dmodes, long long* const* step, const int* delay,
                             BatchRecGroup** out);
+// The same for B loops that share one network (pas_mlp_t, B <= its batch size): each step
+// one batched forward of their slopes through the tensor-core layers (bf16 activations,
+// float32 accumulation), then each loop's integrator on its output, as the single-vector
+// chain's last layer applies it.
+pas_status batch_mlp_create(pas_ctx_t ctx, pas_mlp_t mlp, int B, const float* const* slopes,
+                            float* const* ring, const float* const* gain, float* const* cmd,
+                            float* const* dmodes, long long* const* step, const int* delay,
+                            BatchRecGroup** out);
 // Enqueue on `st`: gather the B slope vectors as bf16, the product with the fused
-// integrator, then advance the B step counters.
+// integrator (or the network's batched forward and the integrator), then advance the B
+// step counters.
 pas_status batch_rec_launch(BatchRecGroup* g, cudaStream_t st);
-// Error word of the product's bounded waits (non-zero: a wait gave up).
+// Error word of the product's (the network's GEMMs') bounded waits (non-zero: a wait gave up).
 unsigned int* batch_rec_err(BatchRecGroup* g);
+// Kernels one launch enqueues.
+int batch_rec_kernels(BatchRecGroup* g);
 void batch_rec_destroy(BatchRecGroup* g);
 
 }  // namespace pas

@@ -581,7 +581,27 @@ pas_status pas_batch_create_ex(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops
       b->groups.push_back(part);
     }
   }
-  for (const std::vector<int>& grp : b->groups) {
+  const size_t n_rec_groups = b->groups.size();
+  // loops that share one network: one batched forward per step. A network keeps one
+  // set of intermediates, so its loops must all fit one group.
+  for (int i = 0; i < n_loops; ++i) {
+    pas_loop_t L = b->loops[i];
+    if (group_of[i] >= 0 || !L->mlp) continue;
+    std::vector<int> members{i};
+    for (int j = i + 1; j < n_loops; ++j)
+      if (b->loops[j]->mlp == L->mlp) members.push_back(j);
+    if (members.size() < 2) continue;
+    if ((int)members.size() > std::min(128, L->mlp->max_batch)) {
+      pas_batch_destroy(b);
+      return pas::set_error(ctx, PAS_EINVAL,
+                            "pas_batch_create: %zu loops share a network of batch size %d (at most min(128, it))",
+                            members.size(), L->mlp->max_batch);
+    }
+    for (int k : members) group_of[k] = (int)b->groups.size();
+    b->groups.push_back(members);
+  }
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    const std::vector<int>& grp = b->groups[gi];
     std::vector<const float*> sl;
     std::vector<float*> ring, cmd, dm;
     std::vector<const float*> gain;
@@ -598,8 +618,12 @@ pas_status pas_batch_create_ex(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops
       delay.push_back(L->delay);
     }
     pas::BatchRecGroup* g = nullptr;
-    pas_status sg = pas::batch_rec_create(ctx, b->loops[grp[0]]->rec, (int)grp.size(), sl.data(), ring.data(),
-                                          gain.data(), cmd.data(), dm.data(), step.data(), delay.data(), &g);
+    pas_status sg =
+        gi < n_rec_groups
+            ? pas::batch_rec_create(ctx, b->loops[grp[0]]->rec, (int)grp.size(), sl.data(), ring.data(), gain.data(),
+                                    cmd.data(), dm.data(), step.data(), delay.data(), &g)
+            : pas::batch_mlp_create(ctx, b->loops[grp[0]]->mlp, (int)grp.size(), sl.data(), ring.data(), gain.data(),
+                                    cmd.data(), dm.data(), step.data(), delay.data(), &g);
     if (sg != PAS_OK) {
       pas_batch_destroy(b);
       return sg;
@@ -705,10 +729,12 @@ pas_status pas_batch_create_ex(pas_ctx_t ctx, pas_loop_t* loops, int32_t n_loops
     // a persistent member launches its residual and slopes kernels (and its
     // reconstruction unless its group's product does it)
     const int whole = b->member[i] >= 0 ? 3 : b->loops[i]->sh ? 3 : PAS_LOOP_KERNELS;
-    b->kernels_per_step += whole - (group_of[i] >= 0 ? 1 : 0) - (b->rgroup_of[i] >= 0 ? 1 : 0) +
+    const int recon = b->loops[i]->mlp ? b->loops[i]->mlp->L : 1;  // a network: one launch per layer
+    b->kernels_per_step += whole - 1 + (group_of[i] >= 0 ? 0 : recon) - (b->rgroup_of[i] >= 0 ? 1 : 0) +
                            (b->loops[i]->cam ? 2 : 0);
   }
-  b->kernels_per_step += 3 * (int)b->groups.size() + 2 * (int)b->rgroups.size();
+  for (pas::BatchRecGroup* g : b->rec_groups) b->kernels_per_step += pas::batch_rec_kernels(g);
+  b->kernels_per_step += 2 * (int)b->rgroups.size();
   if (b->pyr_batch) b->kernels_per_step += pas::pyr_batch_n_groups(b->pyr_batch);
   // one graph per step: every loop's step is a branch of its own (fork on the
   // context's capture stream, one stream per loop, join back); a group's product

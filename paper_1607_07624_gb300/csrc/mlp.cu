@@ -247,6 +247,29 @@ __global__ void mlp_input_kernel(const float* S, int n_data, const int* idx, con
   }
 }
 
+// The same for B vectors given by pointer (the slopes of a batch's loops):
+// X[b][i] = (S_b[i] - mean[i]) * istd[i] in bf16, and X^T.
+__global__ void mlp_gather_input_kernel(const float* const* S, int B, int n_in, const float* mean,
+                                        const float* istd, __nv_bfloat16* X, int ldx, __nv_bfloat16* Xt, int ldt) {
+  __shared__ float tile[32][33];
+  const int i0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+  const int tx = threadIdx.x;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int b = b0 + r, i = i0 + tx;
+    float x = 0.f;
+    if (b < B && i < n_in) {
+      x = (S[b][i] - mean[i]) * istd[i];
+      X[(size_t)b * ldx + i] = __float2bfloat16_rn(x);
+    }
+    tile[r][tx] = x;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, b = b0 + tx;
+    if (i < n_in && b < B) Xt[(size_t)i * ldt + b] = __float2bfloat16_rn(tile[tx][r]);
+  }
+}
+
 // dZ = 2 (out - y) / (B n_out) (bf16, and dZ^T); loss = mean (out - y)^2 into
 // loss[*iter], summed in a fixed order by the last CTA.
 __global__ void mlp_loss_kernel(const float* out, int ldo, const float* Y, int n_data, const int* idx,
@@ -571,6 +594,8 @@ static pas_status gemm_err(pas_mlp_t m, const char* what, cudaError_t e) {
   return set_error(m->ctx, PAS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+static pas_status mlp_layers_enqueue(pas_mlp_t m, int B, cudaStream_t st);
+
 // Forward pass on the samples S[idx[*iter * B + b]] (idx null: the first B rows).
 static pas_status mlp_forward_enqueue(pas_mlp_t m, int B, const float* S, int n_data, const int* idx,
                                       const int* iter, cudaStream_t st) {
@@ -580,6 +605,12 @@ static pas_status mlp_forward_enqueue(pas_mlp_t m, int B, const float* S, int n_
                            iter, B, n_in, (const float*)m->d_mean, (const float*)m->d_istd, m->d_X, m->ld[0], m->d_Xt,
                            m->ldb, m->d_err);
   if (e != cudaSuccess) return gemm_err(m, "MLP input", e);
+  return mlp_layers_enqueue(m, B, st);
+}
+
+// The forward GEMMs on the standardised inputs already in d_X: d_out [B][ld out].
+static pas_status mlp_layers_enqueue(pas_mlp_t m, int B, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
   for (int l = 0; l < m->L; ++l) {
     const __nv_bfloat16* A = l == 0 ? m->d_X : m->d_H[l - 1];
     GemmOp op;
@@ -595,6 +626,16 @@ static pas_status mlp_forward_enqueue(pas_mlp_t m, int B, const float* S, int n_
     if (e != cudaSuccess) return gemm_err(m, "MLP forward GEMM", e);
   }
   return PAS_OK;
+}
+
+pas_status mlp_batch_forward(pas_mlp_t m, int B, const float* const* d_slopes, cudaStream_t st) {
+  if (B < 1 || B > m->max_batch) return set_error(m->ctx, PAS_EINVAL, "MLP batch forward: 1 <= B <= max_batch");
+  const int n_in = m->sz[0];
+  mlp_gather_input_kernel<<<dim3((n_in + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(
+      d_slopes, B, n_in, m->d_mean, m->d_istd, m->d_X, m->ld[0], m->d_Xt, m->ldb);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return gemm_err(m, "MLP batch input", e);
+  return mlp_layers_enqueue(m, B, st);
 }
 
 // Loss, backward pass and bias gradients into d_g (loss into loss[*iter]).

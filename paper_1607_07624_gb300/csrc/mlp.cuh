@@ -59,4 +59,8 @@ struct pas_mlp_s {
 namespace pas {
 // Enqueue the single-vector inference chain with the loop's integrator in the last layer.
 pas_status mlp_loop_launch(pas_mlp_t m, const ReconArgs& integ, cudaStream_t st, bool pdl);
+// Enqueue the forward pass of B vectors given by device pointers (d_slopes: a device
+// array of B pointers to n_in floats), standardised and cast to bf16 on the way in, through
+// the tensor-core layers: the outputs land in m->d_out [B][m->ld[m->L]] (float32).
+pas_status mlp_batch_forward(pas_mlp_t m, int B, const float* const* d_slopes, cudaStream_t st);
 }

@@ -156,6 +156,81 @@ def test_loops_sharing_a_bf16_reconstructor_get_one_tensor_core_product():
             s.close()
 
 
+def test_loops_sharing_a_network_get_one_batched_forward():
+    """Four realisations of the 64 px workload share one network (one layer W = R, b = 0,
+    the linear reconstructor as a network): the batch runs one batched forward through the
+    tensor-core layers per step (bf16 inputs and activations) and each loop's integrator on
+    its output. After one step each loop's update equals R s (1 % of the RMS: the bf16
+    rounding of inputs and weights); over 40 steps the loops follow the same loops stepped
+    alone with their own single-vector chains (per-step WFE within 2 nm). More loops than
+    the network's batch size are refused."""
+    import torch
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    cfg = with_(get_config("scao_8m_64px"), K=24)
+    first = SCAOSystem(cfg, autotune=False, wfe_history=64)
+    R = first.R.astype(np.float64)
+    params = np.concatenate([R.ravel(), np.zeros(R.shape[0])]).astype(np.float32)
+    sizes = [R.shape[1], R.shape[0]]
+    systems, alone, nets, batch = [first], [], [], None
+    try:
+        for seed in (2001, 2002, 2003):
+            systems.append(SCAOSystem(with_(cfg, seed=seed), basis=first.basis, R=first.R, autotune=False,
+                                      wfe_history=64))
+        shared = pas.pas_mlp_create(first.ctx, sizes, 4)
+        nets.append(shared)
+        pas.pas_mlp_set_params(shared, first.ctx, params)
+        for s in systems:
+            pas.pas_loop_set_mlp(s.loop, s.ctx, shared)
+            a = SCAOSystem(s.cfg, basis=first.basis, R=first.R, autotune=False, wfe_history=64)
+            own = pas.pas_mlp_create(a.ctx, sizes, 1)
+            nets.append(own)
+            pas.pas_mlp_set_params(own, a.ctx, params)
+            pas.pas_loop_set_mlp(a.loop, a.ctx, own)
+            alone.append(a)
+        ctx = first.ctx
+        batch = pas.pas_batch_create(ctx, [s.loop for s in systems])
+        assert pas.pas_batch_n_groups(batch) == 1
+        assert pas.pas_batch_kernels_per_step(batch) == 4 * 4 + (1 + 3)
+        pas.pas_batch_step(batch, ctx, 1)
+        torch.cuda.synchronize()
+        assert pas.pas_batch_check(batch, ctx) == 0
+        for s in systems:
+            st, _ = pas.pas_loop_step(s.loop, s.ctx, 0, stats=True)
+            assert st == 1
+            ref = R @ s.loop_slopes.cpu().numpy().astype(np.float64)
+            got = s.loop_dmodes.cpu().numpy().astype(np.float64)
+            assert np.sqrt(np.mean((got - ref) ** 2)) <= 0.01 * np.sqrt(np.mean(ref ** 2))
+            assert np.allclose(s.loop_cmd.cpu().numpy(), cfg.gain * s.loop_dmodes.cpu().numpy(), rtol=1e-6,
+                               atol=1e-6)
+        pas.pas_batch_step(batch, ctx, 39)
+        torch.cuda.synchronize()
+        assert pas.pas_mlp_check(shared, ctx) == 0
+        for s, a in zip(systems, alone):
+            a.step(40)
+            assert np.max(np.abs(s.wfe_nm(40) - a.wfe_nm(40))) <= 2.0
+        pas.pas_batch_destroy(batch)
+        batch = None
+        # a fifth loop on the same network: more than its batch size of 4
+        extra = SCAOSystem(with_(cfg, seed=2004), basis=first.basis, R=first.R, autotune=False, wfe_history=64)
+        try:
+            pas.pas_loop_set_mlp(extra.loop, extra.ctx, shared)
+            with pytest.raises(pas.PasError, match="share a network"):
+                pas.pas_batch_create(ctx, [s.loop for s in systems] + [extra.loop])
+            pas.pas_loop_set_mlp(extra.loop, extra.ctx, None)
+        finally:
+            extra.close()
+    finally:
+        if batch is not None:
+            pas.pas_batch_destroy(batch)
+        for s in alone + systems:
+            pas.pas_loop_set_mlp(s.loop, s.ctx, None)
+        for m in nets:
+            pas.pas_mlp_destroy(m)
+        for s in alone + systems[1:] + systems[:1]:
+            s.close()
+
+
 def _mixed_systems():
     """Pyramid loops of two transform lengths (one with an integrating detector) and a
     Shack-Hartmann loop."""
