@@ -797,11 +797,55 @@ def bench_mlp(sysg, peaks, timed, n_train=50, batch=1024):
     ms_loop = timed(lambda: sysg.step(1), n_loop)
     torch.cuda.nvtx.range_pop()
     chain = pas.pas_loop_profile(sysg.loop, ctx, 20).get("recon_kernel")
+    try:
+        batched = _bench_batched_network(sysg, mlp, timed)
+    except Exception as e:  # reported, never fatal
+        batched = {"error": str(e)}
     pas.pas_loop_set_mlp(sysg.loop, ctx, None)
     mlp.close()
     return {"sizes": sizes, "train": train, "gemm": gemm,
             "loop_steps_per_s_with_network": n_loop / (ms_loop * 1e-3),
-            "network_chain_ms_in_loop": chain}
+            "network_chain_ms_in_loop": chain, "batched": batched}
+
+
+def _bench_batched_network(sysg, mlp, timed, n_loops=8, n_steps=50):
+    """n_loops realisations of this system (own screens; basis, R, DM object and launch
+    geometry shared) stepped as one batch, one graph launch per step: all of them with one
+    shared network (one batched tensor-core forward per step, bf16 activations) and, for
+    comparison, all with the linear FP32 reconstructor. Loop-steps/s, L2 flushed between
+    steps."""
+    import numpy as np
+    from paper_1607_07624_gb300 import pas
+    from paper_1607_07624_gb300.system import SCAOSystem
+    from synth.configs import with_
+    cfg = sysg.cfg
+    twins = []
+    try:
+        for i in range(1, n_loops):
+            twins.append(SCAOSystem(with_(cfg, seed=cfg.seed + 7919 * i), basis=sysg.basis, R=sysg.R, dm=sysg.dm,
+                                    autotune=tuple(sysg.tuning), wfe_history=256))
+        members = [sysg] + twins
+        out = {"loops": n_loops}
+        for name in ("shared_network", "linear_fp32"):
+            for s in members:
+                pas.pas_loop_set_mlp(s.loop, s.ctx, mlp.h if name == "shared_network" else None)
+            batch = pas.pas_batch_create(sysg.ctx, [s.loop for s in members])
+            try:
+                for s in members:
+                    s.set_state(0, np.zeros((s.delay, s.n_modes), np.float32))
+                pas.pas_batch_step(batch, sysg.ctx, 5)
+                ms = timed(lambda: pas.pas_batch_step(batch, sysg.ctx, 1), n_steps)
+                pas.pas_batch_check(batch, sysg.ctx)
+                out[name] = {"loop_steps_per_s": n_loops * n_steps / (ms * 1e-3),
+                             "kernels_per_step": pas.pas_batch_kernels_per_step(batch),
+                             "batched_groups": pas.pas_batch_n_groups(batch)}
+            finally:
+                pas.pas_batch_destroy(batch)
+        return out
+    finally:
+        for s in twins:
+            pas.pas_loop_set_mlp(s.loop, s.ctx, None)
+            s.close()
 
 
 def measure_fp32_peak(stream, reps=20, iters=4096, blocks_per_sm=8):
