@@ -461,6 +461,11 @@ int32_t pas_batch_size(pas_batch_t batch);
  * and one tensor-core product C = R S^T (float32 accumulation) gives every loop's
  * modal update, the integrator applied per loop in the product's epilogue (R is read
  * once per step instead of once per loop). Groups of up to 128 loops, in loop order.
+ * Loops that share one network (pas_loop_set_mlp) form one group likewise: one batched
+ * forward of their slopes through the tensor-core layers per step (bf16 inputs and
+ * activations, float32 accumulation), then each loop's integrator on its output; more
+ * loops sharing a network than min(128, its batch size) is PAS_EINVAL (the network keeps
+ * one set of intermediates).
  * pas_batch_n_groups: how many such groups; pas_batch_kernels_per_step: kernels one
  * step launches; pas_batch_check: synchronous, PAS_ETIMEOUT if a product's bounded
  * wait gave up since the last check (h_fault optional: the flag bits). */
