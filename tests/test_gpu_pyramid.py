@@ -89,6 +89,7 @@ TINY = [
     # empty), one at N = 960
     tiny_config(Np=128, N=256, n_sub=16, K=7, mod_radius=3.0),
     tiny_config(Np=128, N=256, n_sub=32, K=2),
+    tiny_config(Np=320, N=640, n_sub=40, K=7, mod_radius=3.0),   # pass-by-pass engine, odd K
     tiny_config(Np=240, N=480, n_sub=30, K=5, mod_radius=3.0),
     tiny_config(Np=480, N=960, n_sub=96, K=3, mod_radius=4.0),
 ]
@@ -268,13 +269,16 @@ def test_rows_pass_geometry_leaves_the_frame_bit_identical(env, name, rows):
         pas.pas_pyr_destroy(pyr)
 
 
-def test_four_step_256_geometry_leaves_the_frame_bit_identical(env):
-    """N = 256 (four transforms per engine call): rows-pass geometries whose sin chunks
-    leave calls partly empty give the same frame and slopes bit for bit, and every
-    columns-pass grouping (kper 12, 4, 3, 1) matches the oracle."""
+@pytest.mark.parametrize("Np,N,n_sub,rows", [(128, 256, 16, [(2, 1), (4, 7), (8, 3), (16, 2)]),
+                                             (320, 640, 40, [(2, 1), (4, 7), (8, 3), (8, 2)])])
+def test_launch_geometry_leaves_the_frame_bit_identical(env, Np, N, n_sub, rows):
+    """N = 256 (the four-step engine, four transforms per call: sin chunks that leave calls
+    partly empty) and N = 640 (the pass-by-pass engine): rows-pass geometries give the same
+    frame and slopes bit for bit, and every columns-pass grouping (kper 12, 4, 3, 1)
+    matches the oracle."""
     from oracle import optics as op
     torch, pas, ctx = env
-    cfg = tiny_config(Np=128, N=256, n_sub=16, K=12, mod_radius=3.0)
+    cfg = tiny_config(Np=Np, N=N, n_sub=n_sub, K=12, mod_radius=3.0)
     opd32 = random_opd_nm(cfg.Np, 200.0, seed=29).astype(np.float32)
     opd = torch.as_tensor(opd32).cuda()
     valid = op.valid_subapertures(cfg.Np, cfg.obs, cfg.n_sub)
@@ -284,7 +288,7 @@ def test_four_step_256_geometry_leaves_the_frame_bit_identical(env):
         nv = pas.pas_pyr_n_valid(pyr)
         assert nv == valid.size
         out = {}
-        for r, chunks, groups in [(2, 1, 3), (4, 7, 3), (8, 3, 3), (16, 2, 3), (4, 2, 1), (4, 2, 4), (4, 2, 12)]:
+        for r, chunks, groups in [(r, c, 3) for r, c in rows] + [(4, 2, 1), (4, 2, 4), (4, 2, 12)]:
             pas.pas_pyr_set_tuning(pyr, ctx, r, chunks, groups, 1)
             fr = torch.zeros(cfg.n_det, cfg.n_det, device="cuda")
             sl = torch.zeros(2 * nv, device="cuda")
