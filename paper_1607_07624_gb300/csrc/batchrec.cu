@@ -22,6 +22,7 @@ struct BatchRecGroup {
   pas_mlp_t mlp = nullptr;       // a shared network instead of rec: one batched forward
   int B = 0;
   __nv_bfloat16* d_S = nullptr;  // [B][n_s_pad]
+  float* d_part = nullptr;       // split product: [splits][n_m][B] partial sums
   void** d_ptrs = nullptr;       // the pointer arrays of BatchRecState, contiguous
   int* d_delay = nullptr;
   unsigned int* d_err = nullptr;
@@ -118,6 +119,39 @@ struct EpiBatchIntegrate {
   }
 };
 
+// Split reduction (few row tiles, long rows): each K range's product [n_m][B] goes to
+// its own slice of the workspace; a second kernel adds the slices in range order and
+// applies the integrator of EpiBatchIntegrate.
+struct EpiSplitPart {
+  float* part;
+  int M, N;
+  __device__ void store(int row, int col, const float (&v)[16]) const {
+    float* o = part + ((size_t)blockIdx.z * M + row) * N + col;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (col + j < N) o[j] = v[j];
+  }
+};
+
+__global__ void split_integrate_kernel(const float* part, int splits, int n_m, int B, const float* scale,
+                                       BatchRecState st) {
+  const size_t tot = (size_t)n_m * B;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(t / B), b = (int)(t - (size_t)m * B);
+    float acc = 0.f;
+    for (int z = 0; z < splits; ++z) acc += part[((size_t)z * n_m + m) * B + b];
+    const float dm = acc * scale[m];
+    const long long ts = *st.step[b];
+    const int d = st.delay[b];
+    float* ring = st.ring[b];
+    const float prev = ring[(size_t)((ts - 1 + d) % d) * n_m + m];
+    const float c = fmaf(st.gain[b][m], dm, prev);
+    ring[(size_t)(ts % d) * n_m + m] = c;
+    st.cmd[b][m] = c;
+    st.dmodes[b][m] = dm;
+  }
+}
+
 static int pick_bn(int B) { return B <= 16 ? 16 : B <= 32 ? 32 : B <= 64 ? 64 : 128; }
 
 // The group's per-loop pointer arrays on the device (g->st).
@@ -199,6 +233,17 @@ pas_status batch_rec_create(pas_ctx_t ctx, pas_recon_t rec, int B, const float* 
     batch_rec_destroy(g);
     return set_error(ctx, PAS_EINVAL, "batched reconstruction: tensor map rejected");
   }
+  // fewer output tiles than SMs: split K so that about one CTA per SM streams R
+  const int tiles = ((rec->n_modes + 127) / 128) * ((B + g->op.bn - 1) / g->op.bn);
+  const int nk = (K + 63) / 64;
+  g->op.splits = std::max(1, std::min(nk, ctx->sm_count / std::max(1, tiles)));
+  if (g->op.splits > 1) {
+    s = dev_alloc(ctx, (void**)&g->d_part, sizeof(float) * (size_t)g->op.splits * rec->n_modes * B);
+    if (s != PAS_OK) {
+      batch_rec_destroy(g);
+      return s;
+    }
+  }
   *out = g;
   return PAS_OK;
 }
@@ -220,7 +265,15 @@ pas_status batch_rec_launch(BatchRecGroup* g, cudaStream_t st) {
   const int blocks = (int)std::min<size_t>(1024, ((size_t)g->B * K + 255) / 256);
   gather_slopes_bf16_kernel<<<blocks, 256, 0, st>>>(g->st.slopes, n_s, K, g->B, g->d_S);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && g->op.splits > 1) {
+    e = gemm_launch(g->op, EpiSplitPart{g->d_part, g->rec->n_modes, g->B}, st, g->d_err, false);
+    if (e == cudaSuccess) {
+      const int n = g->rec->n_modes * g->B;
+      split_integrate_kernel<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(g->d_part, g->op.splits, g->rec->n_modes,
+                                                                            g->B, g->rec->d_scale, g->st);
+      e = cudaGetLastError();
+    }
+  } else if (e == cudaSuccess) {
     EpiBatchIntegrate ep{g->st, g->rec->d_scale, g->rec->n_modes, g->B};
     e = gemm_launch(g->op, ep, st, g->d_err, false);
   }
@@ -235,11 +288,12 @@ pas_status batch_rec_launch(BatchRecGroup* g, cudaStream_t st) {
 
 unsigned int* batch_rec_err(BatchRecGroup* g) { return g->mlp ? g->mlp->d_err : g->d_err; }
 
-int batch_rec_kernels(BatchRecGroup* g) { return g->mlp ? g->mlp->L + 3 : 3; }
+int batch_rec_kernels(BatchRecGroup* g) { return g->mlp ? g->mlp->L + 3 : g->op.splits > 1 ? 4 : 3; }
 
 void batch_rec_destroy(BatchRecGroup* g) {
   if (!g) return;
   dev_free(g->d_S);
+  dev_free(g->d_part);
   dev_free(g->d_ptrs);
   dev_free(g->d_delay);
   dev_free(g->d_err);

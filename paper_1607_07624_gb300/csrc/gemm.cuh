@@ -1,7 +1,8 @@
 // BF16 tensor-core GEMM for sm_100-family GPUs: C = A * B^T with A [M][K] and
 // B [N][K] both row-major (K contiguous), float32 accumulation in tensor memory.
 //
-// One CTA computes one 128 x BN tile of C with four warps:
+// One CTA computes one 128 x BN tile of C (or, with the reduction split into gridDim.z
+// ranges of K, one range's partial of it) with four warps:
 //   warp 0 lane 0  issues TMA tile loads (64-element K slices, 128-byte swizzle)
 //                  into a STAGES-deep ring of shared-memory slots;
 //   warp 1 lane 0  issues tcgen05.mma (128 x BN x 16 per instruction) into a
@@ -65,7 +66,11 @@ __global__ void __launch_bounds__(128, 1)
     m_tile = in_band / width;
   }
   const int n0 = n_tile * BN, m0 = m_tile * 128;
-  const int nk = (K + 63) / 64;
+  // split K (gridDim.z > 1): CTA z takes 64-element slices [kb0, kb0 + nk) of the
+  // reduction and its epilogue stores a partial product (the epilogue reads blockIdx.z)
+  const int nk_all = (K + 63) / 64;
+  const int kb0 = (int)(((long long)nk_all * blockIdx.z) / gridDim.z);
+  const int nk = (int)(((long long)nk_all * (blockIdx.z + 1)) / gridDim.z) - kb0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -103,8 +108,8 @@ __global__ void __launch_bounds__(128, 1)
       if (abort_flag) break;
       uint8_t* a = sm + (size_t)s * C::STAGE_BYTES;
       tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
-      tc::tma_load_2d(a, &tmA, &full[s], kb * 64, m0);
-      tc::tma_load_2d(a + C::A_BYTES, &tmB, &full[s], kb * 64, n0);
+      tc::tma_load_2d(a, &tmA, &full[s], (kb0 + kb) * 64, m0);
+      tc::tma_load_2d(a + C::A_BYTES, &tmB, &full[s], (kb0 + kb) * 64, n0);
       last_round[s] = round;
     }
   } else if (warp == 1 && lane == 0) {
@@ -360,6 +365,7 @@ struct GemmOp {
   int M = 0, N = 0, K = 0, bn = 128;
   int persist = 0;  // > 0: this many persistent CTAs (gemm_bf16_tc_persist_kernel)
   int mh = 1;       // persistent tiles of mh x 128 rows
+  int splits = 1;   // one CTA per tile: K ranges per tile (gridDim.z), at most ceil(K / 64)
 };
 
 // Persistent CTAs for an M x N output in tiles of width bn: one per SM once there
@@ -401,7 +407,7 @@ cudaError_t gemm_launch_bn(const GemmOp& op, const Epi& epi, cudaStream_t st, un
   auto kern = gemm_bf16_tc_kernel<BN, STAGES, Epi>;
   cudaError_t e = raise_dyn_smem((const void*)kern, C::SMEM);
   if (e != cudaSuccess) return e;
-  dim3 grid((op.N + BN - 1) / BN, (op.M + 127) / 128);
+  dim3 grid((op.N + BN - 1) / BN, (op.M + 127) / 128, op.splits > 1 ? op.splits : 1);
   return launch_k(kern, grid, dim3(128), C::SMEM, st, pdl, op.a, op.b, op.M, op.N, op.K, epi, err, wait_limit);
 }
 

@@ -130,7 +130,8 @@ def test_loops_sharing_a_bf16_reconstructor_get_one_tensor_core_product():
         ctx = first.ctx
         batch = pas.pas_batch_create(ctx, [s.loop for s in systems])
         assert pas.pas_batch_n_groups(batch) == 1
-        assert pas.pas_batch_kernels_per_step(batch) == 5 * 4 + 3
+        # one row tile of R: the product splits its reduction (partials, then the integrator)
+        assert pas.pas_batch_kernels_per_step(batch) == 5 * 4 + 4
         pas.pas_batch_step(batch, ctx, 1)
         torch.cuda.synchronize()
         assert pas.pas_batch_check(batch, ctx) == 0
