@@ -22,7 +22,8 @@ struct BatchRecGroup {
   pas_mlp_t mlp = nullptr;       // a shared network instead of rec: one batched forward
   int B = 0;
   __nv_bfloat16* d_S = nullptr;  // [B][n_s_pad]
-  float* d_part = nullptr;       // split product: [splits][n_m][B] partial sums
+  float* d_part = nullptr;       // split product: [splits][n_m][B] partial sums (a network: its layers')
+  size_t part_len = 0;           // floats of d_part
   void** d_ptrs = nullptr;       // the pointer arrays of BatchRecState, contiguous
   int* d_delay = nullptr;
   unsigned int* d_err = nullptr;
@@ -120,19 +121,8 @@ struct EpiBatchIntegrate {
 };
 
 // Split reduction (few row tiles, long rows): each K range's product [n_m][B] goes to
-// its own slice of the workspace; a second kernel adds the slices in range order and
-// applies the integrator of EpiBatchIntegrate.
-struct EpiSplitPart {
-  float* part;
-  int M, N;
-  __device__ void store(int row, int col, const float (&v)[16]) const {
-    float* o = part + ((size_t)blockIdx.z * M + row) * N + col;
-#pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if (col + j < N) o[j] = v[j];
-  }
-};
-
+// its own slice of the workspace (EpiSplitPart); this kernel adds the slices in range
+// order and applies the integrator of EpiBatchIntegrate.
 __global__ void split_integrate_kernel(const float* part, int splits, int n_m, int B, const float* scale,
                                        BatchRecState st) {
   const size_t tot = (size_t)n_m * B;
@@ -198,6 +188,8 @@ pas_status batch_mlp_create(pas_ctx_t ctx, pas_mlp_t mlp, int B, const float* co
   g->mlp = mlp;
   g->B = B;
   pas_status s = group_pointers(g, slopes, ring, gain, cmd, dmodes, step, delay);
+  g->part_len = mlp_split_workspace(mlp, B);
+  if (s == PAS_OK && g->part_len > 0) s = dev_alloc(ctx, (void**)&g->d_part, sizeof(float) * g->part_len);
   if (s != PAS_OK) {
     batch_rec_destroy(g);
     return s;
@@ -251,7 +243,7 @@ pas_status batch_rec_create(pas_ctx_t ctx, pas_recon_t rec, int B, const float* 
 pas_status batch_rec_launch(BatchRecGroup* g, cudaStream_t st) {
   if (g->mlp) {
     pas_mlp_t m = g->mlp;
-    pas_status s = mlp_batch_forward(m, g->B, g->st.slopes, st);
+    pas_status s = mlp_batch_forward(m, g->B, g->st.slopes, g->d_part, g->part_len, st);
     if (s != PAS_OK) return s;
     const int n_m = m->sz[m->L];
     const int blocks = (int)std::min<size_t>(1024, ((size_t)g->B * n_m + 255) / 256);
@@ -288,7 +280,10 @@ pas_status batch_rec_launch(BatchRecGroup* g, cudaStream_t st) {
 
 unsigned int* batch_rec_err(BatchRecGroup* g) { return g->mlp ? g->mlp->d_err : g->d_err; }
 
-int batch_rec_kernels(BatchRecGroup* g) { return g->mlp ? g->mlp->L + 3 : g->op.splits > 1 ? 4 : 3; }
+int batch_rec_kernels(BatchRecGroup* g) {
+  if (g->mlp) return mlp_batch_forward_kernels(g->mlp, g->B, g->part_len) + 2;
+  return g->op.splits > 1 ? 4 : 3;
+}
 
 void batch_rec_destroy(BatchRecGroup* g) {
   if (!g) return;

@@ -351,6 +351,20 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 0) tc::tmem_dealloc(tmem, C::TMEM_COLS);
 }
 
+// Epilogue of a product whose reduction is split over gridDim.z ranges of K: range z
+// stores its partial C into part[z][M][N] (float32); a later kernel adds the ranges in
+// order.
+struct EpiSplitPart {
+  float* part;
+  int M, N;
+  __device__ void store(int row, int col, const float (&v)[16]) const {
+    float* o = part + ((size_t)blockIdx.z * M + row) * N + col;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (col + j < N) o[j] = v[j];
+  }
+};
+
 // Host side ------------------------------------------------------------------
 
 // Tensor map of a row-major bf16 matrix [rows][cols] with leading dimension ld

@@ -628,14 +628,102 @@ static pas_status mlp_layers_enqueue(pas_mlp_t m, int B, cudaStream_t st) {
   return PAS_OK;
 }
 
-pas_status mlp_batch_forward(pas_mlp_t m, int B, const float* const* d_slopes, cudaStream_t st) {
+// A split layer's partials [splits][B][n_out] summed in range order, plus the bias; a
+// hidden layer then stores Z, H and H^T as EpiHidden does, the output layer out as EpiOut.
+__global__ void mlp_split_finish_kernel(const float* part, int splits, int B, int n_out, const float* bias, int hidden,
+                                        float* Z, __nv_bfloat16* H, __nv_bfloat16* Ht, int ld, int ldt, float* out) {
+  const size_t tot = (size_t)B * n_out;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(t / n_out), o = (int)(t - (size_t)b * n_out);
+    float acc = 0.f;
+    for (int z = 0; z < splits; ++z) acc += part[((size_t)z * B + b) * n_out + o];
+    const float zv = acc + bias[o];
+    if (hidden) {
+      const float h = gelu_f(zv);
+      Z[(size_t)b * ld + o] = zv;
+      H[(size_t)b * ld + o] = __float2bfloat16_rn(h);
+      Ht[(size_t)o * ldt + b] = __float2bfloat16_rn(h);
+    } else {
+      out[(size_t)b * ld + o] = zv;
+    }
+  }
+}
+
+// K ranges of a layer's product for B rows: about one CTA per SM when the layer has
+// fewer output tiles than SMs (1: no split).
+static int layer_splits(pas_mlp_t m, const GemmOp& op) {
+  if (op.persist > 0) return 1;
+  const int tiles = ((op.M + 127) / 128) * ((op.N + op.bn - 1) / op.bn);
+  const int nk = (op.K + 63) / 64;
+  return std::max(1, std::min(nk, m->ctx->sm_count / std::max(1, tiles)));
+}
+
+size_t mlp_split_workspace(pas_mlp_t m, int B) {
+  size_t need = 0;
+  for (int l = 0; l < m->L; ++l) {
+    GemmOp op;
+    op.M = B;
+    op.N = m->sz[l + 1];
+    op.K = m->sz[l];
+    op.bn = gemm_pick_bn(B, op.N, m->ctx->sm_count);
+    gemm_set_persist(&op, m->ctx->sm_count);
+    const int sp = layer_splits(m, op);
+    if (sp > 1) need = std::max(need, (size_t)sp * B * op.N);
+  }
+  return need;
+}
+
+pas_status mlp_batch_forward(pas_mlp_t m, int B, const float* const* d_slopes, float* part, size_t part_len,
+                             cudaStream_t st) {
   if (B < 1 || B > m->max_batch) return set_error(m->ctx, PAS_EINVAL, "MLP batch forward: 1 <= B <= max_batch");
   const int n_in = m->sz[0];
   mlp_gather_input_kernel<<<dim3((n_in + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, st>>>(
       d_slopes, B, n_in, m->d_mean, m->d_istd, m->d_X, m->ld[0], m->d_Xt, m->ldb);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return gemm_err(m, "MLP batch input", e);
-  return mlp_layers_enqueue(m, B, st);
+  if (!part) return mlp_layers_enqueue(m, B, st);
+  for (int l = 0; l < m->L; ++l) {
+    const __nv_bfloat16* A = l == 0 ? m->d_X : m->d_H[l - 1];
+    GemmOp op;
+    if (!gemm_prepare(&op, A, m->ld[l], m->d_W[l], m->ld[l], B, m->sz[l + 1], m->sz[l], m->ctx->sm_count))
+      return set_error(m->ctx, PAS_ECUDA, "MLP forward layer %d: tensor map rejected", l);
+    const bool hidden = l < m->L - 1;
+    const int sp = layer_splits(m, op);
+    if (sp > 1 && (size_t)sp * B * m->sz[l + 1] <= part_len) {
+      op.splits = sp;
+      e = gemm_launch(op, EpiSplitPart{part, B, m->sz[l + 1]}, st, m->d_err, true);
+      if (e == cudaSuccess) {
+        const int n = B * m->sz[l + 1];
+        mlp_split_finish_kernel<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(
+            part, sp, B, m->sz[l + 1], m->d_p + m->offb[l], hidden ? 1 : 0, hidden ? m->d_Z[l] : nullptr,
+            hidden ? m->d_H[l] : nullptr, hidden ? m->d_Ht[l] : nullptr, m->ld[l + 1], m->ldb, m->d_out);
+        e = cudaGetLastError();
+      }
+    } else if (hidden) {
+      EpiHidden ep{m->d_p + m->offb[l], m->d_Z[l], m->d_H[l], m->d_Ht[l], m->ld[l + 1], m->ldb, m->sz[l + 1]};
+      e = gemm_launch(op, ep, st, m->d_err, true);
+    } else {
+      EpiOut ep{m->d_p + m->offb[l], m->d_out, m->ld[l + 1], m->sz[l + 1]};
+      e = gemm_launch(op, ep, st, m->d_err, true);
+    }
+    if (e != cudaSuccess) return gemm_err(m, "MLP batch forward GEMM", e);
+  }
+  return PAS_OK;
+}
+
+int mlp_batch_forward_kernels(pas_mlp_t m, int B, size_t part_len) {
+  int n = 1;  // the input gather
+  for (int l = 0; l < m->L; ++l) {
+    GemmOp op;
+    op.M = B;
+    op.N = m->sz[l + 1];
+    op.K = m->sz[l];
+    op.bn = gemm_pick_bn(B, op.N, m->ctx->sm_count);
+    gemm_set_persist(&op, m->ctx->sm_count);
+    const int sp = layer_splits(m, op);
+    n += sp > 1 && (size_t)sp * B * op.N <= part_len ? 2 : 1;
+  }
+  return n;
 }
 
 // Loss, backward pass and bias gradients into d_g (loss into loss[*iter]).

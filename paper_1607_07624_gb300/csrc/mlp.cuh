@@ -61,6 +61,13 @@ namespace pas {
 pas_status mlp_loop_launch(pas_mlp_t m, const ReconArgs& integ, cudaStream_t st, bool pdl);
 // Enqueue the forward pass of B vectors given by device pointers (d_slopes: a device
 // array of B pointers to n_in floats), standardised and cast to bf16 on the way in, through
-// the tensor-core layers: the outputs land in m->d_out [B][m->ld[m->L]] (float32).
-pas_status mlp_batch_forward(pas_mlp_t m, int B, const float* const* d_slopes, cudaStream_t st);
+// the tensor-core layers: the outputs land in m->d_out [B][m->ld[m->L]] (float32). A layer
+// with fewer output tiles than SMs splits its reduction over K when `part` (part_len
+// floats, mlp_split_workspace(m, B) of them) is given: partials, then a kernel that adds
+// them in order and applies the bias and activation.
+pas_status mlp_batch_forward(pas_mlp_t m, int B, const float* const* d_slopes, float* part, size_t part_len,
+                             cudaStream_t st);
+size_t mlp_split_workspace(pas_mlp_t m, int B);
+// Kernels one mlp_batch_forward launches.
+int mlp_batch_forward_kernels(pas_mlp_t m, int B, size_t part_len);
 }

@@ -192,7 +192,8 @@ def test_loops_sharing_a_network_get_one_batched_forward():
         ctx = first.ctx
         batch = pas.pas_batch_create(ctx, [s.loop for s in systems])
         assert pas.pas_batch_n_groups(batch) == 1
-        assert pas.pas_batch_kernels_per_step(batch) == 4 * 4 + (1 + 3)
+        # gather, the layer's product split over K and its finishing sum, integrators, counters
+        assert pas.pas_batch_kernels_per_step(batch) == 4 * 4 + (1 + 2 + 2)
         pas.pas_batch_step(batch, ctx, 1)
         torch.cuda.synchronize()
         assert pas.pas_batch_check(batch, ctx) == 0
